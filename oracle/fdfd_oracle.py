@@ -1,0 +1,221 @@
+"""CPU oracle for the FDFD design-iteration hot path (complex128, SciPy SuperLU).
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+definition that the CUDA path is checked against.  Only the test suite, the
+smoke check of the package entry file and the CPU-baseline leg of the
+benchmark may import it.  The product path never calls it and shares no code
+with it: it is written from the paper's equations, not from the CUDA sources.
+
+What it computes (paper, Sec. II):
+  * Eq. 1-2: the 2D TM (Ez) frequency-domain operator
+        (-omega^2 eps0 eps_r + mu0^-1 curl curl) E = -i omega J
+    discretised on a Yee grid with stretched-coordinate PML.  Multiplying by
+    mu0 dx^2 gives the dimensionless operator used throughout:
+        A = -dx^2 Lap_s - (k0 dx)^2 diag(eps_r),  k0 = omega / c,
+    where Lap_s is the PML-stretched 5-point Laplacian with a zero (PEC)
+    field one cell beyond the grid on every side.
+  * Eq. 5: E = A^-1 b by a direct sparse LU (SuperLU is the library step).
+  * Eq. 4 and 6: the adjoint solve A^T E_adj = (dF/dE)^T on the same factor.
+  * Eq. 3: dF/dtheta_i = -2 Re{E_adj^T (dA/dtheta_i) E}; with
+    dA/deps_p = -(k0 dx)^2 e_p e_p^T this is 2 (k0 dx)^2 Re(E_adj[p] E[p]).
+  * Objective: mode overlap o = g^T E on a monitor line, F = sum |o|^2, whose
+    Wirtinger derivative (E* held fixed) gives dF/dE = conj(o) g^T.
+
+Readings where the paper is silent (it gives no discretisation): Yee 5-point
+stencil, eps sampled at Ez nodes, PEC behind the PML, polynomial grading m = 3
+with target reflection R = 1e-8, PML cells counted inside the grid, e^{+i w t}
+time convention (from the -i omega J right-hand side of Eq. 1), so that
+s = 1 - i sigma / (omega eps0) absorbs outgoing waves.
+
+Pins (tests/test_oracle.py): dense LAPACK solve on small grids, plane-wave
+dispersion of the Yee stencil, plate-mode propagation constant and PML
+absorption, reciprocity of the symmetrised operator, the bilinear transpose
+identity, manufactured solutions, and central finite differences of F.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+LN_R_DEFAULT = float(np.log(1e-8))
+PML_ORDER_DEFAULT = 3.0
+
+
+# ---------------------------------------------------------------------------
+# Eq. 1-2: stretched-coordinate PML and the discrete operator
+# ---------------------------------------------------------------------------
+def pml_stretch(n: int, npml: int, k0dx: float, ln_R: float = LN_R_DEFAULT,
+                order: float = PML_ORDER_DEFAULT):
+    """Stretch factors s along one axis of n cells.
+
+    Positions are in cell units: the domain spans [0, n], cell i has its centre
+    at i + 0.5, and the half point between cells i and i+1 sits at i + 1.  The
+    PML layer on each side is npml cells thick; depth d in [0, 1] grows
+    polynomially toward the outer wall:
+        sigma / (omega eps0) = -(order + 1) ln(R) / (2 k0dx npml) * d^order
+        s = 1 - i sigma / (omega eps0).
+    Returns (s_c, s_h): s_c[i] at cell centres (length n) and s_h[t] at the
+    half points t = 0..n (s_h[t] lies between cells t-1 and t).
+    """
+    def s_at(u):
+        u = np.asarray(u, dtype=np.float64)
+        if npml <= 0:
+            return np.ones_like(u, dtype=np.complex128)
+        d = np.maximum(np.maximum(npml - u, u - (n - npml)), 0.0) / npml
+        smax = -(order + 1.0) * ln_R / (2.0 * k0dx * npml)
+        return 1.0 - 1j * smax * d ** order
+
+    s_c = s_at(np.arange(n) + 0.5)
+    s_h = s_at(np.arange(n + 1, dtype=np.float64))
+    return s_c, s_h
+
+
+def _npml_xy(npml):
+    if isinstance(npml, (tuple, list)):
+        return int(npml[0]), int(npml[1])
+    return int(npml), int(npml)
+
+
+def assemble(nx: int, ny: int, eps: np.ndarray, k0dx: float, npml,
+             ln_R: float = LN_R_DEFAULT, order: float = PML_ORDER_DEFAULT) -> sp.csr_matrix:
+    """Dimensionless FDFD operator A (complex128 CSR, n = i*ny + j), Eq. 1-2.
+
+    npml is the PML thickness in cells, either one int for both axes or a
+    pair (npml_x, npml_y).
+
+    Row (i, j):
+      A[(i,j),(i,j)]   = (1/sx_c[i]) (1/sx_h[i+1] + 1/sx_h[i])
+                       + (1/sy_c[j]) (1/sy_h[j+1] + 1/sy_h[j]) - k0dx^2 eps[i,j]
+      A[(i,j),(i+-1,j)] = -1 / (sx_c[i] sx_h[i+1 or i])   (dropped beyond the grid: PEC)
+      A[(i,j),(i,j+-1)] = -1 / (sy_c[j] sy_h[j+1 or j])
+    """
+    eps = np.asarray(eps, dtype=np.float64).reshape(nx, ny)
+    px, py = _npml_xy(npml)
+    sxc, sxh = pml_stretch(nx, px, k0dx, ln_R, order)
+    syc, syh = pml_stretch(ny, py, k0dx, ln_R, order)
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    row = (I * ny + J).ravel()
+    xp = (-1.0 / (sxc[:, None] * sxh[1:, None]) * np.ones((1, ny)))     # to (i+1, j)
+    xm = (-1.0 / (sxc[:, None] * sxh[:-1, None]) * np.ones((1, ny)))    # to (i-1, j)
+    yp = (-1.0 / (syc[None, :] * syh[None, 1:]) * np.ones((nx, 1)))     # to (i, j+1)
+    ym = (-1.0 / (syc[None, :] * syh[None, :-1]) * np.ones((nx, 1)))    # to (i, j-1)
+    diag = -(xp + xm) - (yp + ym) - k0dx ** 2 * eps
+    rows = [row]
+    cols = [row]
+    vals = [diag.ravel()]
+    for off_i, off_j, v in ((1, 0, xp), (-1, 0, xm), (0, 1, yp), (0, -1, ym)):
+        ii, jj = I + off_i, J + off_j
+        ok = ((ii >= 0) & (ii < nx) & (jj >= 0) & (jj < ny)).ravel()
+        rows.append(row[ok])
+        cols.append((ii * ny + jj).ravel()[ok])
+        vals.append(v.ravel()[ok])
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nx * ny, nx * ny)).tocsr()
+    return A
+
+
+def symmetrizer(nx: int, ny: int, k0dx: float, npml, ln_R: float = LN_R_DEFAULT,
+                order: float = PML_ORDER_DEFAULT) -> np.ndarray:
+    """Diagonal D = sx_c[i] sy_c[j] for which D A is complex symmetric (reciprocity)."""
+    px, py = _npml_xy(npml)
+    sxc, _ = pml_stretch(nx, px, k0dx, ln_R, order)
+    syc, _ = pml_stretch(ny, py, k0dx, ln_R, order)
+    return (sxc[:, None] * syc[None, :]).ravel()
+
+
+# ---------------------------------------------------------------------------
+# Eq. 5-6: direct solves on one factorisation (forward and transpose)
+# ---------------------------------------------------------------------------
+class Factor:
+    """Sparse LU of A (SuperLU, complex128); solve() is Eq. 5, solve_T() Eq. 6."""
+
+    def __init__(self, A: sp.spmatrix):
+        self.A = A.tocsc()
+        self.lu = spla.splu(self.A, permc_spec="MMD_AT_PLUS_A")
+
+    def solve(self, b: np.ndarray) -> np.ndarray:
+        return self.lu.solve(np.asarray(b, dtype=np.complex128))
+
+    def solve_T(self, b: np.ndarray) -> np.ndarray:
+        """Solves A^T x = b (plain transpose, not conjugate)."""
+        return self.lu.solve(np.asarray(b, dtype=np.complex128), trans="T")
+
+
+# ---------------------------------------------------------------------------
+# Eq. 3-4: objective, adjoint source and pixel gradient
+# ---------------------------------------------------------------------------
+def overlap(E: np.ndarray, g: np.ndarray) -> complex:
+    """o = g^T E (no conjugation on g), E and g flat of length nx*ny."""
+    return complex(np.sum(g * E))
+
+
+def adjoint_source(E: np.ndarray, g: np.ndarray, weight: float = 1.0) -> np.ndarray:
+    """(dF/dE)^T for F = weight |g^T E|^2 (Wirtinger, E* fixed): weight conj(o) g."""
+    return weight * np.conj(overlap(E, g)) * g
+
+
+def grad_eps(E: np.ndarray, E_adj: np.ndarray, k0dx: float) -> np.ndarray:
+    """dF/deps_p = -2 Re{E_adj[p] (dA/deps_p) E[p]} = 2 k0dx^2 Re(E_adj[p] E[p]), Eq. 3."""
+    return 2.0 * k0dx ** 2 * np.real(E_adj * E)
+
+
+def design_box_of(v: np.ndarray, nx: int, ny: int, box) -> np.ndarray:
+    x0, y0, w, h = box
+    return v.reshape(nx, ny)[x0:x0 + w, y0:y0 + h]
+
+
+def design_iteration(wl, rho: np.ndarray, eps_of_rho, delta_eps: float):
+    """One forward + adjoint iteration (Sec. II), all wavelengths and sources.
+
+    wl: a workloads.Workload.  Returns (F, dF/drho [w, h], fields) with
+    F = sum_{omega, s} |g_{omega,s}^T E_{omega,s}|^2 and fields[(w, s)] = (E, E_adj).
+    """
+    eps = eps_of_rho(rho)
+    F = 0.0
+    g_eps = np.zeros(wl.box[2:4])
+    fields = {}
+    for w, k0dx in enumerate(wl.k0dx()):
+        fac = Factor(assemble(wl.nx, wl.ny, eps, k0dx, wl.npml))
+        for s in range(wl.n_src):
+            b = wl.source_dense(s)
+            g = wl.monitor_dense(w, s)
+            E = fac.solve(b)
+            o = overlap(E, g)
+            F += abs(o) ** 2
+            E_adj = fac.solve_T(adjoint_source(E, g))
+            g_eps += design_box_of(grad_eps(E, E_adj, k0dx), wl.nx, wl.ny, wl.box)
+            fields[(w, s)] = (E, E_adj)
+    return F, delta_eps * g_eps, fields
+
+
+# ---------------------------------------------------------------------------
+# Optimiser updates applied between iterations (outside the timed hot path)
+# ---------------------------------------------------------------------------
+def sign_step(rho: np.ndarray, grad: np.ndarray, step: float) -> np.ndarray:
+    """Ascent step rho += step * sign(grad), sign(0) = 0, clipped to [0, 1]."""
+    return np.clip(rho + step * np.sign(grad), 0.0, 1.0)
+
+
+def adam_step(rho, grad, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Adam (Kingma & Ba 2015) ascent on F; state = dict(m, v, t)."""
+    t = state.get("t", 0) + 1
+    m = beta1 * state.get("m", np.zeros_like(rho)) + (1 - beta1) * grad
+    v = beta2 * state.get("v", np.zeros_like(rho)) + (1 - beta2) * grad * grad
+    mh = m / (1 - beta1 ** t)
+    vh = v / (1 - beta2 ** t)
+    state.update(t=t, m=m, v=v)
+    return np.clip(rho + lr * mh / (np.sqrt(vh) + eps), 0.0, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Error metrics used by the parity tests
+# ---------------------------------------------------------------------------
+def rel_err(x, ref) -> float:
+    x = np.asarray(x).ravel()
+    ref = np.asarray(ref).ravel()
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def residual_rel(A: sp.spmatrix, x: np.ndarray, b: np.ndarray) -> float:
+    return float(np.linalg.norm(A @ x - b) / np.linalg.norm(b))

@@ -1,0 +1,185 @@
+"""Pins for the CPU oracle: each checks it against something other than itself.
+
+Every test here runs on the CPU.  A plausible slip anywhere in the oracle (a
+dropped PML term, a sign of the eps term, a swapped half-point index, a
+conjugate in place of a transpose, a wrong gradient constant) fails at least
+one of them; the mapping is given in each docstring.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fdfd_oracle as O
+
+
+def _rand_eps(nx, ny, seed):
+    rng = np.random.default_rng(seed)
+    return W.EPS_SIO2 + W.DELTA_EPS * rng.uniform(0, 1, size=(nx, ny))
+
+
+@pytest.mark.parametrize("nx,ny,npml", [(12, 17, 3), (9, 6, 2), (20, 20, 4)])
+def test_dense_lapack_solve(nx, ny, npml):
+    """SuperLU forward and transpose solves equal dense LAPACK solves (Eq. 5, 6)."""
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 1), k0dx, npml)
+    b = W.random_complex(nx * ny, 2)
+    fac = O.Factor(A)
+    Ad = A.toarray()
+    x_ref = np.linalg.solve(Ad, b)
+    xt_ref = np.linalg.solve(Ad.T, b)
+    assert O.rel_err(fac.solve(b), x_ref) < 1e-11
+    assert O.rel_err(fac.solve_T(b), xt_ref) < 1e-11
+
+
+def test_plane_wave_dispersion():
+    """A homogeneous-medium plane wave obeying the Yee dispersion relation
+    4 sin^2(kx/2) + 4 sin^2(ky/2) = (k0 dx)^2 eps  is annihilated by A at interior
+    nodes (pins the 4 / -1 stencil and the sign of the -(k0 dx)^2 eps term)."""
+    nx, ny = 30, 26
+    eps = 2.085
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    kx = 0.21
+    ky = 2 * np.arcsin(np.sqrt((k0dx ** 2 * eps - 4 * np.sin(kx / 2) ** 2) / 4))
+    A = O.assemble(nx, ny, np.full((nx, ny), eps), k0dx, 0)
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    E = np.exp(-1j * (kx * I + ky * J)).ravel()
+    r = (A @ E).reshape(nx, ny)[1:-1, 1:-1]
+    assert np.max(np.abs(r)) < 1e-13
+    # a wavevector off the dispersion shell leaves a residual of order (dk)*k
+    E2 = np.exp(-1j * (kx * I + 1.05 * ky * J)).ravel()
+    r2 = (A @ E2).reshape(nx, ny)[1:-1, 1:-1]
+    assert np.min(np.abs(r2)) > 1e-3
+
+
+def test_plate_mode_propagation_and_pml():
+    """Parallel-plate guide: PEC walls in y (no y-PML), PML only in x.  The lowest
+    discrete plate mode sin(pi (j+1)/(ny+1)) propagates with the closed-form Yee
+    wavenumber 4 sin^2(kx/2) = (k0dx)^2 eps - 4 sin^2(pi / (2 (ny+1))), away from the
+    source, and the right PML absorbs it (small standing-wave ripple, strong decay).
+    Pins PEC placement (ghost cell one beyond the grid), the e^{-i kx x} outgoing
+    convention, the PML sign and its axis."""
+    nx, ny, npml = 260, 7, 20
+    eps = 12.11
+    k0dx = 2 * np.pi * 0.04 / 1.55
+    A = O.assemble(nx, ny, np.full((nx, ny), eps), k0dx, (npml, 0))
+    mode = np.sin(np.pi * (np.arange(ny) + 1) / (ny + 1))
+    b = np.zeros((nx, ny), complex)
+    i_s = 40
+    b[i_s, :] = mode
+    E = O.Factor(A).solve(b.ravel()).reshape(nx, ny)
+    # the field stays in the lowest mode
+    Em = E @ mode / (mode @ mode)
+    assert np.max(np.abs(E - Em[:, None] * mode[None, :])) < 1e-10 * np.max(np.abs(E))
+    kx = 2 * np.arcsin(np.sqrt((k0dx ** 2 * eps - 4 * np.sin(np.pi / (2 * (ny + 1))) ** 2) / 4))
+    ratio = Em[i_s + 20:nx - npml - 20 + 1] / Em[i_s + 20 - 1:nx - npml - 20]
+    assert np.max(np.abs(ratio - np.exp(-1j * kx))) < 1e-4
+    # decay inside the right PML, and a small ripple (reflection) in the interior
+    assert abs(Em[nx - 2]) < 1e-5 * abs(Em[nx - npml - 1])
+    amp = np.abs(Em[i_s + 20:nx - npml - 20])
+    assert (amp.max() - amp.min()) / amp.mean() < 1e-4
+
+
+def test_symmetrized_operator_is_symmetric():
+    """D A is complex symmetric for D = sx_c sy_c (the discrete form of reciprocity)."""
+    nx, ny, npml = 15, 11, 4
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 3), k0dx, npml)
+    D = O.symmetrizer(nx, ny, k0dx, npml)
+    S = (np.diag(D) @ A.toarray())
+    assert np.max(np.abs(S - S.T)) < 1e-14 * np.max(np.abs(S))
+    assert np.max(np.abs(A.toarray() - A.toarray().T)) > 1e-3   # A itself is not symmetric in the PML
+
+
+def test_reciprocity():
+    """x_a(source e_b) = x_b(source e_a) for points a, b outside the PML."""
+    nx, ny, npml = 24, 21, 5
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 4), k0dx, npml)
+    fac = O.Factor(A)
+    pts = [(npml + 1) * ny + npml + 2, (nx - npml - 2) * ny + ny // 2, 12 * ny + 9]
+    for a in pts:
+        for b in pts:
+            ea = np.zeros(nx * ny, complex)
+            eb = np.zeros(nx * ny, complex)
+            ea[a] = 1
+            eb[b] = 1
+            xa = fac.solve(eb)[a]
+            xb = fac.solve(ea)[b]
+            assert abs(xa - xb) < 1e-12 * max(abs(xa), 1e-30)
+
+
+def test_bilinear_transpose_identity():
+    """c^T (A^-1 b) = (A^-T c)^T b: solve_T is the plain transpose, not the adjoint."""
+    nx, ny, npml = 18, 14, 4
+    k0dx = 2 * np.pi * 0.05 / 1.31
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 5), k0dx, npml)
+    fac = O.Factor(A)
+    b = W.random_complex(nx * ny, 6)
+    c = W.random_complex(nx * ny, 7)
+    lhs = c @ fac.solve(b)
+    rhs = fac.solve_T(c) @ b
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # the conjugate-transpose solve does not satisfy it (A is not Hermitian)
+    wrong = fac.lu.solve(c, trans="H") @ b
+    assert abs(wrong - lhs) > 1e-3 * abs(lhs)
+
+
+def test_manufactured_solution():
+    nx, ny, npml = 33, 29, 6
+    k0dx = 2 * np.pi * 0.04 / 1.55
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 8), k0dx, npml)
+    x_star = W.random_complex(nx * ny, 9)
+    b = A @ x_star
+    x = O.Factor(A).solve(b)
+    assert O.rel_err(x, x_star) < 1e-10
+
+
+@pytest.mark.parametrize("n_omega,n_src", [(1, 1), (2, 2)])
+def test_gradient_central_differences(n_omega, n_src):
+    """Adjoint gradient (Eq. 3, 4) equals central finite differences of F in rho."""
+    wl = W.make_small(22, 19, 4, (7, 6, 7, 6), n_omega=n_omega, n_src=n_src, seed=11)
+    F0, g, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    h = 1e-4
+    fd = np.zeros_like(wl.rho)
+    for idx in np.ndindex(wl.rho.shape):
+        rp = wl.rho.copy()
+        rm = wl.rho.copy()
+        rp[idx] += h
+        rm[idx] -= h
+        Fp, _, _ = O.design_iteration(wl, rp, wl.eps_full, W.DELTA_EPS)
+        Fm, _, _ = O.design_iteration(wl, rm, wl.eps_full, W.DELTA_EPS)
+        fd[idx] = (Fp - Fm) / (2 * h)
+    assert O.rel_err(g, fd) < 1e-6
+
+
+def test_gradient_sign_and_scale_special_case():
+    """One design pixel, monitor = that pixel: F = |E_p|^2.  With A E = b,
+    dE/deps_p = (k0dx)^2 G_pp E_p where G = A^-1, so dF/deps_p =
+    2 (k0dx)^2 Re(conj(E_p) G_pp E_p) -- checked against the oracle's Eq. 3 path."""
+    nx, ny, npml = 16, 15, 4
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    eps = _rand_eps(nx, ny, 12)
+    A = O.assemble(nx, ny, eps, k0dx, npml)
+    fac = O.Factor(A)
+    p = 8 * ny + 7
+    b = W.random_complex(nx * ny, 13)
+    E = fac.solve(b)
+    g = np.zeros(nx * ny, complex)
+    g[p] = 1
+    E_adj = fac.solve_T(O.adjoint_source(E, g))
+    grad = O.grad_eps(E, E_adj, k0dx)[p]
+    ep = np.zeros(nx * ny, complex)
+    ep[p] = 1
+    Gpp = fac.solve(ep)[p]
+    expect = 2 * k0dx ** 2 * np.real(np.conj(E[p]) * Gpp * E[p])
+    assert abs(grad - expect) < 1e-10 * abs(expect)
+
+
+def test_c1_oracle_iteration_runs():
+    wl = W.make("c1")
+    F, g, fields = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    assert np.isfinite(F) and F > 0
+    assert g.shape == (40, 40) and np.all(np.isfinite(g))
+    E, Ea = fields[(0, 0)]
+    A = O.assemble(wl.nx, wl.ny, wl.eps_full(), wl.k0dx()[0], wl.npml)
+    assert O.residual_rel(A, E, wl.source_dense(0)) < 1e-12
