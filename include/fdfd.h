@@ -1,0 +1,200 @@
+/*
+ * fdfd.h -- C ABI of libfdfd: cached direct solves of the 2D TM (Ez)
+ * finite-difference frequency-domain system for adjoint inverse design, on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: "Computational Scaling in Inverse Photonic Design Through
+ * Factorization Caching" (arXiv 2307.05388).  Section numbers and equation
+ * numbers below refer to it.
+ *
+ * Operator (Eq. 1-2).  The paper's
+ *     (-omega^2 eps0 eps_r + mu0^-1 curl curl) E = -i omega J
+ * is discretised on a Yee grid of nx x ny cells of size dx with a
+ * stretched-coordinate PML of npml cells on every side (counted inside the
+ * grid) and a zero field one cell beyond the grid (PEC).  The library works
+ * with the dimensionless operator obtained by multiplying by mu0 dx^2:
+ *     A = -dx^2 Lap_s - (k0 dx)^2 diag(eps_r),   k0 = omega / c,
+ *     A[(i,j),(i+-1,j)] = -1 / (sx(i+1/2) sx(i+1/2 +- 1/2)),  same in y,
+ *     A[(i,j),(i,j)]    = -(sum of the four neighbour coefficients) - (k0 dx)^2 eps[i,j],
+ *     s(u) = 1 - i [-(order+1) ln R / (2 k0 dx npml)] d(u)^order,  d = depth / npml,
+ * with cell (i, j) centred at ((i + 1/2) dx, (j + 1/2) dx) and the time
+ * convention e^{+i omega t} implied by the -i omega J right-hand side.  The
+ * unknown of cell (i, j) has flat index n = i*ny + j.  A right-hand side b is
+ * the caller's (for Eq. 2 it is -i omega mu0 dx^2 J).
+ *
+ * Method (Sec. II).  Symbolic factorisation once per grid (nested-dissection
+ * ordering aligned to the design box, elimination tree, fronts), reused for
+ * every wavelength and iteration; numeric factorisation per wavelength
+ * (batched dense complex LU of same-level fronts with extend-add); the
+ * adjoint solve A^T x = b reuses the same factors (Eq. 6); a design update
+ * refactors only the fronts whose subtree holds a design pixel; many
+ * right-hand sides share one factorisation.  In the default mixed mode the
+ * factors are complex FP32 and every solve is refined by flexible GMRES with
+ * FP64 residuals and updates, so that results match a complex128 direct solve.
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device memory owned by the caller, read or
+ *    written on the context's CUDA stream (asynchronously: synchronise the
+ *    stream before reading results on the host).  Pointers named *_host are
+ *    host memory, read before the call returns.
+ *  - Complex numbers are interleaved (re, im) doubles, i.e. CUDA double2.
+ *  - Field arrays have layout [n_omega][nrhs][nx*ny] (system s = w*nrhs + r).
+ *  - Design arrays have layout [w][h]: pixel (i, j) of the box, at grid cell
+ *    (x0 + i, y0 + j), has index i*h + j.
+ *  - Every call returns a status; fdfd_last_error() gives a one-line reason.
+ *    No call aborts the process.  A failed call leaves the context usable
+ *    unless the status is FDFD_ERR_CUDA.
+ */
+#ifndef FDFD_H_
+#define FDFD_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdfd_ctx fdfd_ctx;
+
+typedef enum {
+  FDFD_OK = 0,
+  FDFD_ERR_ARG = 1,            /* invalid argument (sizes, null pointers, box outside grid) */
+  FDFD_ERR_STATE = 2,          /* call out of order (e.g. solve before factor) */
+  FDFD_ERR_OOM = 3,            /* device memory allocation failed */
+  FDFD_ERR_CUDA = 4,           /* a CUDA runtime error; text in fdfd_last_error */
+  FDFD_ERR_PIVOT = 5,          /* pivot growth above the bound even in FP64 */
+  FDFD_ERR_NOT_CONVERGED = 6,  /* refinement stopped above the tolerance; best x returned */
+  FDFD_ERR_TIMEOUT = 7         /* reserved for bounded device waits */
+} fdfd_status;
+
+typedef struct { int nx, ny; } fdfd_grid;
+
+/* PML thickness in cells (npml_x, npml_y; 0 disables that axis), ln of the
+ * target normal-incidence reflection (default ln 1e-8) and grading order
+ * (default 3). */
+typedef struct { int npml_x, npml_y; double ln_R; double order; } fdfd_pml;
+
+/* design region in cells: [x0, x0+w) x [y0, y0+h); w = h = 0 for none */
+typedef struct { int x0, y0, w, h; } fdfd_box;
+
+typedef enum {
+  FDFD_MODE_MIXED = 0,         /* cached complex FP32 factors + FP64 FGMRES refinement */
+  FDFD_MODE_F64 = 1,           /* cached complex FP64 factors, no refinement */
+  FDFD_MODE_PLAIN = 2          /* no caching (paper's reference arm, Sec. III): every solve
+                                  re-runs the symbolic phase and a full FP64 factorisation */
+} fdfd_mode;
+
+typedef struct {
+  int mode;                    /* fdfd_mode */
+  double ir_tol;               /* FGMRES stop: ||b - A x|| <= ir_tol ||b|| per system (default 1e-12) */
+  int ir_max_iter;             /* FGMRES iterations per solve across restarts (default 40);
+                                  0 returns the raw FP32-factor solution */
+  int gmres_restart;           /* Krylov vectors per cycle, 1..16 (default 8) */
+  double growth_bound;         /* largest |L| entry tolerated in an FP32 front before the whole
+                                  factorisation is redone in FP64 (default 1e6) */
+  int leaf_area;               /* nested-dissection leaf size in cells (default 32) */
+} fdfd_options;
+
+typedef struct {
+  long long sf;                /* symbolic factorisations performed */
+  long long nf;                /* numeric factorisations (one per wavelength, full or design refactor) */
+  long long bs;                /* back substitutions (one per system solved: wavelength x rhs) */
+  long long sweeps;            /* triangular sweep pairs executed (including refinement) */
+  long long ir_iters;          /* FGMRES iterations in the last solve (max over systems) */
+  double ir_resid;             /* largest relative residual at the end of the last solve */
+  long long fallbacks;         /* factorisations redone in FP64 after pivot growth */
+  double growth;               /* largest |L| entry in the last factorisation */
+  int n_fronts, n_levels, max_front;
+  long long factor_entries;    /* stored L and U entries per wavelength */
+  long long store_bytes;       /* device bytes of front storage (all wavelengths) */
+  double flops_factor;         /* full factorisation flops per wavelength (8 per complex FMA) */
+  double flops_design;         /* flops of a design refactor per wavelength */
+} fdfd_stats;
+
+/* Fills *opt with the defaults listed above. */
+void fdfd_default_options(fdfd_options* opt);
+
+/* Creates a context (host only, no device work yet).
+ * k0_host: [n_omega] free-space wavenumbers k0 = omega / c, in inverse units of
+ * dx (e.g. 2 pi / lambda with lambda and dx in micrometres).  cuda_stream: the
+ * cudaStream_t all work is issued on (NULL = legacy default stream).  The
+ * context owns every device buffer it allocates; the caller owns *out and
+ * frees it with fdfd_destroy.  opt may be NULL (defaults). */
+fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
+                        fdfd_pml pml, fdfd_box design, const fdfd_options* opt, void* cuda_stream);
+
+/* Symbolic phase (Sec. II, Fig. 1): nested-dissection ordering aligned to the
+ * design box, elimination tree, fronts and index maps, computed on the host and
+ * uploaded once.  Idempotent: a second call does nothing (in plain mode it is
+ * repeated inside every solve instead). */
+fdfd_status fdfd_analyze(fdfd_ctx* ctx);
+
+/* Numeric factorisation of A(eps) for every wavelength (Sec. II).
+ * eps_dev: [nx*ny] relative permittivity (device, read once; the context keeps
+ * a copy).  Runs the symbolic phase first if it has not run. */
+fdfd_status fdfd_factor(fdfd_ctx* ctx, const double* eps_dev);
+
+/* Design update: replaces the permittivity of the design box by eps_design_dev
+ * ([w*h], device) and refactors only the fronts whose subtree holds a design
+ * pixel, reusing the cached factors and update matrices of every other front.
+ * The result is bit-identical to fdfd_factor on the full updated eps.
+ * Requires an earlier fdfd_factor. */
+fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev);
+
+/* Solves A x = b (transpose = 0, Eq. 5) or A^T x = b (transpose = 1, Eq. 4/6)
+ * for all wavelengths and nrhs right-hand sides on the cached factors.
+ * b_dev, x_dev: [n_omega][nrhs][nx*ny] complex128 (device); x may not alias b.
+ * Returns FDFD_ERR_NOT_CONVERGED (x holds the last iterate) when the mixed-mode
+ * refinement stops above ir_tol. */
+fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose);
+
+/* Mode-overlap objective and its adjoint source (Eq. 4):
+ *   o_s = sum_j g_s[j] x_s[col_s*ny + j],   F = sum_s weight_s |o_s|^2,
+ *   b_adj_s = weight_s conj(o_s) g_s on column col_s, zero elsewhere
+ * (the Wirtinger derivative dF/dE with E* held fixed, transposed).
+ * x_dev: [n_omega][nrhs][nx*ny]; cols_dev: [n_omega*nrhs] int; g_dev:
+ * [n_omega*nrhs][ny] complex128; weight_dev: [n_omega*nrhs] or NULL (all 1);
+ * o_dev: [n_omega*nrhs] complex128 out; F_dev: one double out; b_adj_dev:
+ * [n_omega][nrhs][nx*ny] out or NULL. */
+fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev,
+                           const double* g_dev, const double* weight_dev, double* o_dev, double* F_dev,
+                           double* b_adj_dev);
+
+/* Pixel gradient (Eq. 3) over the design box:
+ *   grad[p] (+)= sum_s weight_s * 2 (k0 dx)^2 Re(x_adj_s[p] x_fwd_s[p]),
+ * i.e. dF/deps_p = -2 Re{x_adj^T (dA/deps_p) x_fwd} with dA/deps_p = -(k0 dx)^2 e_p e_p^T,
+ * given x_adj = A^-T (dF/dx)^T.  x_fwd_dev, x_adj_dev: [n_omega][nrhs][nx*ny];
+ * weight_dev: [n_omega*nrhs] or NULL; grad_dev: [w*h]; accumulate = 1 adds. */
+fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_adj_dev, int nrhs,
+                      const double* weight_dev, double* grad_dev, int accumulate);
+
+/* Applies the FP64 operator: y = A x (transpose 0) or A^T x, all systems. */
+fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose);
+
+/* Replaces the solve options (ir_tol, ir_max_iter, gmres_restart) at run time.
+ * mode, growth_bound and leaf_area are fixed at creation and ignored here. */
+fdfd_status fdfd_set_options(fdfd_ctx* ctx, const fdfd_options* opt);
+
+/* Counters and sizes (synchronises the context's stream). */
+fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* out);
+
+/* Symbolic plan introspection for host-side tests (valid after fdfd_analyze):
+ * per front its pivot count k, boundary count m, parent (-1 root), level and
+ * design flag; idx receives the grid cells of every front ([k pivots | m
+ * boundary] concatenated in front order, sum of (k+m) entries).  Any output
+ * pointer may be NULL.  Host memory. */
+fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k_host, int* m_host, int* parent_host, int* level_host,
+                             int* design_host, int* idx_host);
+
+/* Resets the SF/NF/BS counters. */
+void fdfd_reset_counters(fdfd_ctx* ctx);
+
+/* Text of the last error on this context ("" if none); valid until the next call. */
+const char* fdfd_last_error(const fdfd_ctx* ctx);
+
+/* Frees every device and host buffer of the context (synchronises its stream). */
+void fdfd_destroy(fdfd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDFD_H_ */

@@ -1,0 +1,7 @@
+"""GB300-native cached direct solves for FDFD adjoint inverse design (arXiv 2307.05388).
+
+The compute path is libfdfd.so (CUDA, sm_103a) behind the C ABI in include/fdfd.h;
+`fdfd` is its Python binding and `autograd` the torch.autograd.Function built on it.
+Importing `fdfd` raises when the library has not been built.
+"""
+__all__ = ["fdfd", "autograd", "build"]

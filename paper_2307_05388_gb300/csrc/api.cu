@@ -1,0 +1,816 @@
+// C ABI of libfdfd (declared in include/fdfd.h): context, level scheduling of
+// the multifrontal factorisation and of the triangular sweeps, the FGMRES
+// refinement driver and the operation counters of the paper's Sec. III-IV.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fdfd.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace fdfd;
+
+namespace fdfd {
+cudaError_t launch_growth_max(const float* growth, long long count, float* out, cudaStream_t s);
+}
+
+namespace {
+
+struct LevelList {
+  int task_off = 0, ntasks = 0;      // build tasks (int2) offset / count
+  int small_off = 0, nsmall = 0, nmax_small = 0;
+  int large_off = 0, nlarge = 0, nmax_large = 0, kmax_large = 0;
+};
+
+struct SolveList {
+  int off = 0, nf = 0, nmax = 0, kmax = 0;
+};
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc((void**)p, bytes);
+}
+
+}  // namespace
+
+struct fdfd_ctx {
+  int nx = 0, ny = 0;
+  double dx = 0;
+  int n_omega = 0;
+  std::vector<double> k0dx;
+  fdfd_pml pml{};
+  fdfd_box box{};
+  fdfd_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int device = -1;
+
+  Plan plan;
+  bool analyzed = false;
+  bool uploaded = false;
+
+  // device copy of the plan
+  FrontDesc* d_fronts = nullptr;
+  int* d_children = nullptr;
+  int* d_idx = nullptr;
+  int* d_inv = nullptr;
+  int* d_orig_ptr = nullptr;
+  int* d_orig_col = nullptr;
+  int* d_orig_code = nullptr;
+  int* d_lists = nullptr;          // all per-level lists (ints; build tasks as int pairs)
+  std::vector<int> h_lists;
+  std::vector<LevelList> lv_full[2], lv_design[2];   // [precision 0 = c64, 1 = c128]
+  std::vector<SolveList> lv_solve;
+
+  // coefficients and permittivity
+  double2 *d_cxm = nullptr, *d_cxp = nullptr, *d_cym = nullptr, *d_cyp = nullptr;
+  double* d_k0dx = nullptr;
+  double* d_k0dx2 = nullptr;
+  double* d_eps = nullptr;
+  bool have_eps = false;
+
+  // factor storage
+  float2* d_store32 = nullptr;
+  double2* d_store64 = nullptr;
+  int* d_perm32 = nullptr;
+  int* d_perm64 = nullptr;
+  float* d_growth = nullptr;
+  float* d_growth_max = nullptr;
+  float* h_growth_max = nullptr;   // pinned
+  bool valid32 = false, valid64 = false;
+  bool growth_pending = false;
+
+  // solve workspace
+  int ws_nrhs = 0;
+  void* d_vb = nullptr;            // front vectors, sized for double2
+  void* d_bT = nullptr;            // rhs / solution in factor precision
+  void* d_xT = nullptr;
+  // FGMRES workspace
+  int gm_nrhs = 0, gm_m = 0;
+  double2 *d_V = nullptr, *d_Z = nullptr, *d_r = nullptr, *d_w = nullptr;
+  double2 *d_h = nullptr, *d_h2 = nullptr, *d_hn = nullptr, *d_bd = nullptr;
+  double2 *d_H = nullptr, *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr, *d_ycoef = nullptr;
+  double2* d_partial = nullptr;
+  double *d_vscale = nullptr, *d_resid = nullptr, *d_bnorm = nullptr;
+  int *d_active = nullptr, *d_nj = nullptr;
+  int* h_active = nullptr;          // pinned
+  double* h_resid = nullptr;        // pinned
+
+  // counters
+  long long sf = 0, nf = 0, bs = 0, sweeps = 0, fallbacks = 0;
+  long long last_iters = 0;
+  double last_resid = 0;
+  double last_growth = 0;
+};
+
+namespace {
+
+fdfd_status fail(fdfd_ctx* c, fdfd_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CK(expr)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? FDFD_ERR_OOM : FDFD_ERR_CUDA,    \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+#define CKS(expr)                              \
+  do {                                         \
+    fdfd_status s_ = (expr);                   \
+    if (s_ != FDFD_OK) return s_;              \
+  } while (0)
+
+void free_ptr(void* p) {
+  if (p) cudaFree(p);
+}
+
+void free_plan_device(fdfd_ctx* c) {
+  free_ptr(c->d_fronts); free_ptr(c->d_children); free_ptr(c->d_idx); free_ptr(c->d_inv);
+  free_ptr(c->d_orig_ptr); free_ptr(c->d_orig_col); free_ptr(c->d_orig_code); free_ptr(c->d_lists);
+  c->d_fronts = nullptr; c->d_children = c->d_idx = c->d_inv = c->d_orig_ptr = c->d_orig_col = nullptr;
+  c->d_orig_code = c->d_lists = nullptr;
+  c->uploaded = false;
+}
+
+void free_factor(fdfd_ctx* c) {
+  free_ptr(c->d_store32); free_ptr(c->d_store64); free_ptr(c->d_perm32); free_ptr(c->d_perm64);
+  free_ptr(c->d_growth);
+  c->d_store32 = nullptr; c->d_store64 = nullptr; c->d_perm32 = c->d_perm64 = nullptr; c->d_growth = nullptr;
+  c->valid32 = c->valid64 = false;
+}
+
+void free_ws(fdfd_ctx* c) {
+  free_ptr(c->d_vb); free_ptr(c->d_bT); free_ptr(c->d_xT);
+  c->d_vb = c->d_bT = c->d_xT = nullptr;
+  c->ws_nrhs = 0;
+}
+
+void free_gm(fdfd_ctx* c) {
+  void* ps[] = {c->d_V, c->d_Z, c->d_r, c->d_w, c->d_h, c->d_h2, c->d_hn, c->d_bd, c->d_H, c->d_cs,
+                c->d_sn, c->d_g, c->d_ycoef, c->d_partial, c->d_vscale, c->d_resid, c->d_bnorm,
+                c->d_active, c->d_nj};
+  for (void* p : ps) free_ptr(p);
+  c->d_V = c->d_Z = c->d_r = c->d_w = c->d_h = c->d_h2 = c->d_hn = c->d_bd = nullptr;
+  c->d_H = c->d_cs = c->d_sn = c->d_g = c->d_ycoef = c->d_partial = nullptr;
+  c->d_vscale = c->d_resid = c->d_bnorm = nullptr;
+  c->d_active = c->d_nj = nullptr;
+  c->gm_nrhs = c->gm_m = 0;
+}
+
+long long n_cells(const fdfd_ctx* c) { return (long long)c->nx * c->ny; }
+
+// Host symbolic phase (no device work).
+fdfd_status analyze_host(fdfd_ctx* ctx) {
+  std::string e = build_plan(ctx->nx, ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w, ctx->box.h,
+                             ctx->opt.leaf_area, &ctx->plan);
+  if (!e.empty()) return fail(ctx, FDFD_ERR_ARG, "symbolic phase: " + e);
+  for (const auto& d : ctx->plan.fronts)
+    if (d.nchild > 2) return fail(ctx, FDFD_ERR_ARG, "symbolic phase: front with more than two children");
+  ctx->analyzed = true;
+  ctx->sf += 1;
+  return FDFD_OK;
+}
+
+template <typename P>
+fdfd_status upload(fdfd_ctx* ctx, P** dst, const std::vector<P>& v) {
+  CK(dalloc(dst, v.size() * sizeof(P)));
+  if (!v.empty())
+    CK(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(P), cudaMemcpyHostToDevice, ctx->stream));
+  return FDFD_OK;
+}
+
+// Uploads the plan and builds the per-level launch lists.  The host vectors
+// are kept alive by the context until the next upload, so the asynchronous
+// copies may still be in flight when this returns.
+fdfd_status upload_plan(fdfd_ctx* ctx) {
+  if (ctx->uploaded) CK(cudaStreamSynchronize(ctx->stream));   // old plan may still be in use
+  free_plan_device(ctx);
+  const Plan& p = ctx->plan;
+  CKS(upload(ctx, &ctx->d_fronts, p.fronts));
+  CKS(upload(ctx, &ctx->d_children, p.children));
+  CKS(upload(ctx, &ctx->d_idx, p.idx));
+  CKS(upload(ctx, &ctx->d_inv, p.inv));
+  CKS(upload(ctx, &ctx->d_orig_ptr, p.orig_ptr));
+  CKS(upload(ctx, &ctx->d_orig_col, p.orig_col));
+  CKS(upload(ctx, &ctx->d_orig_code, p.orig_code));
+  std::vector<int> lists;
+  const int L = p.n_levels;
+  for (int prec = 0; prec < 2; ++prec) {
+    const int small_n = lu_small_max_n(prec == 0 ? 8 : 16);
+    for (int design = 0; design < 2; ++design) {
+      std::vector<LevelList>& out = design ? ctx->lv_design[prec] : ctx->lv_full[prec];
+      out.assign(L, LevelList{});
+      for (int l = 0; l < L; ++l) {
+        LevelList& ll = out[l];
+        std::vector<int> fl;
+        for (int f : p.level_fronts[l])
+          if (!design || p.fronts[f].design) fl.push_back(f);
+        ll.task_off = (int)lists.size();
+        for (int f : fl)
+          for (int r0 = 0; r0 < p.fronts[f].n; r0 += 8) { lists.push_back(f); lists.push_back(r0); ll.ntasks++; }
+        ll.small_off = (int)lists.size();
+        for (int f : fl)
+          if (p.fronts[f].n <= small_n) {
+            lists.push_back(f); ll.nsmall++; ll.nmax_small = std::max(ll.nmax_small, p.fronts[f].n);
+          }
+        ll.large_off = (int)lists.size();
+        for (int f : fl)
+          if (p.fronts[f].n > small_n) {
+            lists.push_back(f); ll.nlarge++;
+            ll.nmax_large = std::max(ll.nmax_large, p.fronts[f].n);
+            ll.kmax_large = std::max(ll.kmax_large, p.fronts[f].k);
+          }
+        if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
+      }
+    }
+  }
+  ctx->lv_solve.assign(L, SolveList{});
+  for (int l = 0; l < L; ++l) {
+    SolveList& sl = ctx->lv_solve[l];
+    sl.off = (int)lists.size();
+    for (int f : p.level_fronts[l]) {
+      lists.push_back(f); sl.nf++;
+      sl.nmax = std::max(sl.nmax, p.fronts[f].n);
+      sl.kmax = std::max(sl.kmax, p.fronts[f].k);
+    }
+  }
+  ctx->h_lists.swap(lists);
+  CKS(upload(ctx, &ctx->d_lists, ctx->h_lists));
+  ctx->uploaded = true;
+  return FDFD_OK;
+}
+
+// Device runtime: kernel attributes, stencil coefficient tables, eps buffer.
+fdfd_status ensure_runtime(fdfd_ctx* ctx) {
+  if (ctx->device < 0) {
+    CK(cudaGetDevice(&ctx->device));
+    CK(factor_init_attributes());
+    CK(solve_init_attributes());
+    CK(dalloc(&ctx->d_cxm, sizeof(double2) * ctx->n_omega * ctx->nx));
+    CK(dalloc(&ctx->d_cxp, sizeof(double2) * ctx->n_omega * ctx->nx));
+    CK(dalloc(&ctx->d_cym, sizeof(double2) * ctx->n_omega * ctx->ny));
+    CK(dalloc(&ctx->d_cyp, sizeof(double2) * ctx->n_omega * ctx->ny));
+    CK(dalloc(&ctx->d_k0dx, sizeof(double) * ctx->n_omega));
+    CK(dalloc(&ctx->d_k0dx2, sizeof(double) * ctx->n_omega));
+    CK(dalloc(&ctx->d_eps, sizeof(double) * n_cells(ctx)));
+    CK(dalloc(&ctx->d_growth_max, sizeof(float)));
+    CK(cudaMallocHost((void**)&ctx->h_growth_max, sizeof(float)));
+    CK(cudaMemcpyAsync(ctx->d_k0dx, ctx->k0dx.data(), sizeof(double) * ctx->n_omega, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    launch_coef(ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx2, ctx->d_k0dx, ctx->n_omega,
+                ctx->nx, ctx->ny, ctx->pml.npml_x, ctx->pml.npml_y, ctx->pml.ln_R, ctx->pml.order, ctx->stream);
+    CK(cudaGetLastError());
+  }
+  return FDFD_OK;
+}
+
+// Runtime plus the symbolic plan on the device (analysed on first use).
+fdfd_status ensure_device(fdfd_ctx* ctx) {
+  CKS(ensure_runtime(ctx));
+  if (!ctx->analyzed) CKS(analyze_host(ctx));
+  if (!ctx->uploaded) CKS(upload_plan(ctx));
+  return FDFD_OK;
+}
+
+DevPlan dev_plan(const fdfd_ctx* c) {
+  DevPlan P;
+  P.fronts = c->d_fronts; P.children = c->d_children; P.idx = c->d_idx; P.inv = c->d_inv;
+  P.orig_ptr = c->d_orig_ptr; P.orig_col = c->d_orig_col; P.orig_code = c->d_orig_code;
+  P.nx = c->nx; P.ny = c->ny;
+  return P;
+}
+
+DevCoef dev_coef(const fdfd_ctx* c) {
+  DevCoef C;
+  C.cxm = c->d_cxm; C.cxp = c->d_cxp; C.cym = c->d_cym; C.cyp = c->d_cyp;
+  C.k0dx2 = c->d_k0dx2; C.eps = c->d_eps; C.nx = c->nx; C.ny = c->ny;
+  return C;
+}
+
+fdfd_status ensure_store(fdfd_ctx* ctx, int prec) {
+  const Plan& p = ctx->plan;
+  const size_t nfr = p.fronts.size();
+  if (!ctx->d_growth) CK(dalloc(&ctx->d_growth, sizeof(float) * nfr * ctx->n_omega));
+  if (prec == 0 && !ctx->d_store32) {
+    CK(dalloc(&ctx->d_store32, sizeof(float2) * (size_t)p.store_total * ctx->n_omega));
+    CK(dalloc(&ctx->d_perm32, sizeof(int) * (size_t)std::max(1, p.perm_total) * ctx->n_omega));
+  }
+  if (prec == 1 && !ctx->d_store64) {
+    CK(dalloc(&ctx->d_store64, sizeof(double2) * (size_t)p.store_total * ctx->n_omega));
+    CK(dalloc(&ctx->d_perm64, sizeof(int) * (size_t)std::max(1, p.perm_total) * ctx->n_omega));
+  }
+  return FDFD_OK;
+}
+
+// Level-by-level numeric factorisation of the listed fronts, for wavelengths [w0, w0+nw).
+template <typename T>
+fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = -1) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  CKS(ensure_store(ctx, prec));
+  const Plan& p = ctx->plan;
+  FactorLaunch fa;
+  fa.P = dev_plan(ctx);
+  fa.C = dev_coef(ctx);
+  fa.store = prec == 0 ? (void*)ctx->d_store32 : (void*)ctx->d_store64;
+  fa.store_stride = p.store_total;
+  fa.perm = prec == 0 ? ctx->d_perm32 : ctx->d_perm64;
+  fa.perm_stride = std::max(1, p.perm_total);
+  fa.growth = ctx->d_growth;
+  fa.n_fronts = (int)p.fronts.size();
+  fa.n_omega = nw < 0 ? ctx->n_omega : nw;
+  fa.w0 = w0;
+  const std::vector<LevelList>& lv = design_only ? ctx->lv_design[prec] : ctx->lv_full[prec];
+  const int nb = lu_panel_width(sizeof(T));
+  cudaStream_t s = ctx->stream;
+  for (int l = 0; l < p.n_levels; ++l) {
+    const LevelList& ll = lv[l];
+    launch_build<T>(fa, reinterpret_cast<const int2*>(ctx->d_lists + ll.task_off), ll.ntasks, s);
+    launch_lu_small<T>(fa, ctx->d_lists + ll.small_off, ll.nsmall, ll.nmax_small, s);
+    for (int j0 = 0; j0 < ll.kmax_large; j0 += nb) {
+      const int* fl = ctx->d_lists + ll.large_off;
+      launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, s);
+      launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s);
+      launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s);
+    }
+  }
+  CK(cudaGetLastError());
+  CK(launch_growth_max(ctx->d_growth, (long long)p.fronts.size() * ctx->n_omega, ctx->d_growth_max, s));
+  CK(cudaMemcpyAsync(ctx->h_growth_max, ctx->d_growth_max, sizeof(float), cudaMemcpyDeviceToHost, s));
+  return FDFD_OK;
+}
+
+fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
+  if (ctx->ws_nrhs >= nrhs) return FDFD_OK;
+  free_ws(ctx);
+  const size_t S = (size_t)ctx->n_omega * nrhs;
+  CK(dalloc(&ctx->d_vb, sizeof(double2) * S * (size_t)ctx->plan.vec_total));
+  CK(dalloc(&ctx->d_bT, sizeof(double2) * S * (size_t)n_cells(ctx)));
+  CK(dalloc(&ctx->d_xT, sizeof(double2) * S * (size_t)n_cells(ctx)));
+  ctx->ws_nrhs = nrhs;
+  return FDFD_OK;
+}
+
+// Triangular sweeps on factor precision T: out = A^-1 in (or A^-T in).
+template <typename T>
+fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out, int w0 = 0,
+                   int nw = -1, int r0 = 0, int nr = -1) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const Plan& p = ctx->plan;
+  SolveLaunch sa;
+  sa.P = dev_plan(ctx);
+  sa.store = prec == 0 ? (const void*)ctx->d_store32 : (const void*)ctx->d_store64;
+  sa.store_stride = p.store_total;
+  sa.perm = prec == 0 ? ctx->d_perm32 : ctx->d_perm64;
+  sa.perm_stride = std::max(1, p.perm_total);
+  sa.vb = ctx->d_vb;
+  sa.vec_stride = p.vec_total;
+  sa.n_omega = nw < 0 ? ctx->n_omega : nw;
+  sa.nrhs = nrhs;
+  sa.w0 = w0;
+  sa.r0 = r0;
+  sa.nr = nr < 0 ? nrhs : nr;
+  sa.n = n_cells(ctx);
+  cudaStream_t s = ctx->stream;
+  const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
+  for (int l = 0; l < p.n_levels; ++l) {
+    const SolveList& sl = ctx->lv_solve[l];
+    launch_sweep<T>(sa, fwd, ctx->d_lists + sl.off, sl.nf, sl.nmax, sl.kmax, in, out, s);
+  }
+  for (int l = p.n_levels - 1; l >= 0; --l) {
+    const SolveList& sl = ctx->lv_solve[l];
+    launch_sweep<T>(sa, bwd, ctx->d_lists + sl.off, sl.nf, sl.nmax, sl.kmax, in, out, s);
+  }
+  CK(cudaGetLastError());
+  ctx->sweeps += 1;
+  return FDFD_OK;
+}
+
+// Applies the cached factors M^-1 to FP64 vectors: dst = M^-1 src (all systems).
+fdfd_status precond(fdfd_ctx* ctx, int nrhs, int transpose, const double2* src, double2* dst) {
+  const long long N = n_cells(ctx);
+  const int S = ctx->n_omega * nrhs;
+  if (ctx->valid64) {
+    return sweeps<double2>(ctx, nrhs, transpose, src, dst);
+  }
+  launch_cvt_from64<float2>(reinterpret_cast<float2*>(ctx->d_bT), src, nullptr, N, S, ctx->stream);
+  CKS(sweeps<float2>(ctx, nrhs, transpose, ctx->d_bT, ctx->d_xT));
+  launch_cvt_to64<float2>(dst, reinterpret_cast<const float2*>(ctx->d_xT), nullptr, N, S, ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
+fdfd_status ensure_gm(fdfd_ctx* ctx, int nrhs, int m) {
+  if (ctx->gm_nrhs >= nrhs && ctx->gm_m >= m) return FDFD_OK;
+  free_gm(ctx);
+  const size_t S = (size_t)ctx->n_omega * nrhs;
+  const size_t N = (size_t)n_cells(ctx);
+  const int D = multidot_max_vectors();
+  const int nblk = multidot_blocks((long long)N);
+  CK(dalloc(&ctx->d_V, sizeof(double2) * (m + 1) * S * N));
+  CK(dalloc(&ctx->d_Z, sizeof(double2) * m * S * N));
+  CK(dalloc(&ctx->d_r, sizeof(double2) * S * N));
+  CK(dalloc(&ctx->d_w, sizeof(double2) * S * N));
+  CK(dalloc(&ctx->d_h, sizeof(double2) * S * D));
+  CK(dalloc(&ctx->d_h2, sizeof(double2) * S * D));
+  CK(dalloc(&ctx->d_hn, sizeof(double2) * S * D));
+  CK(dalloc(&ctx->d_bd, sizeof(double2) * S * D));
+  CK(dalloc(&ctx->d_H, sizeof(double2) * S * m * (m + 1)));
+  CK(dalloc(&ctx->d_cs, sizeof(double2) * S * m));
+  CK(dalloc(&ctx->d_sn, sizeof(double2) * S * m));
+  CK(dalloc(&ctx->d_g, sizeof(double2) * S * (m + 1)));
+  CK(dalloc(&ctx->d_ycoef, sizeof(double2) * S * D));
+  CK(dalloc(&ctx->d_partial, sizeof(double2) * S * D * nblk));
+  CK(dalloc(&ctx->d_vscale, sizeof(double) * S));
+  CK(dalloc(&ctx->d_resid, sizeof(double) * S));
+  CK(dalloc(&ctx->d_bnorm, sizeof(double) * S));
+  CK(dalloc(&ctx->d_active, sizeof(int) * S));
+  CK(dalloc(&ctx->d_nj, sizeof(int) * S));
+  if (!ctx->h_active) {
+    CK(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4096));
+    CK(cudaMallocHost((void**)&ctx->h_resid, sizeof(double) * 4096));
+  }
+  ctx->gm_nrhs = nrhs;
+  ctx->gm_m = m;
+  return FDFD_OK;
+}
+
+namespace kadd {
+__global__ void add_kernel(double2* a, const double2* b, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) { a[t].x += b[t].x; a[t].y += b[t].y; }
+}
+}  // namespace kadd
+
+fdfd_status any_active(fdfd_ctx* ctx, int S, bool* any, double* maxres) {
+  CK(cudaMemcpyAsync(ctx->h_active, ctx->d_active, sizeof(int) * S, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_resid, ctx->d_resid, sizeof(double) * S, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *any = false;
+  *maxres = 0;
+  for (int i = 0; i < S; ++i) {
+    if (ctx->h_active[i]) *any = true;
+    const double r = ctx->h_resid[i];
+    if (!(r <= *maxres)) *maxres = r;
+  }
+  return FDFD_OK;
+}
+
+// Flexible GMRES, right-preconditioned by the cached LU, FP64 residuals and updates.
+fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int transpose) {
+  const int m = std::max(1, std::min(ctx->opt.gmres_restart, multidot_max_vectors() - 1));
+  CKS(ensure_gm(ctx, nrhs, m));
+  const int S = ctx->n_omega * nrhs;
+  if (S > 4096) return fail(ctx, FDFD_ERR_ARG, "too many systems for one solve (max 4096)");
+  const long long N = n_cells(ctx);
+  const size_t vs = (size_t)S * N;   // stride between Krylov vectors
+  const int D = multidot_max_vectors();
+  const int nblk = multidot_blocks(N);
+  const double tol = ctx->opt.ir_tol;
+  const DevCoef C = dev_coef(ctx);
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * vs, s));
+  CK(cudaMemcpyAsync(ctx->d_r, b, sizeof(double2) * vs, cudaMemcpyDeviceToDevice, s));
+  launch_multidot(b, 0, 1, b, N, S, ctx->d_partial, nblk, ctx->d_bd, D, s);
+  long long total = 0;
+  double res = 0;
+  bool converged = false;
+  for (int cycle = 0;; ++cycle) {
+    if (cycle > 0) launch_stencil(C, ctx->n_omega, nrhs, transpose, x, b, ctx->d_r, 1, s);
+    launch_multidot(ctx->d_r, 0, 1, ctx->d_r, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s);
+    gm_start(ctx->d_hn, D, ctx->d_bd, D, S, tol, m, ctx->d_g, ctx->d_vscale, ctx->d_active, ctx->d_resid,
+             ctx->d_bnorm, cycle == 0 ? 1 : 0, s);
+    CK(cudaGetLastError());
+    bool any;
+    CKS(any_active(ctx, S, &any, &res));
+    if (!any) { converged = true; break; }
+    if (total >= ctx->opt.ir_max_iter) break;
+    gm_scale(ctx->d_V, ctx->d_r, ctx->d_vscale, N, S, s);
+    CK(cudaMemsetAsync(ctx->d_nj, 0, sizeof(int) * S, s));
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double2* Vj = ctx->d_V + (size_t)j * vs;
+      double2* Zj = ctx->d_Z + (size_t)j * vs;
+      CKS(precond(ctx, nrhs, transpose, Vj, Zj));
+      launch_stencil(C, ctx->n_omega, nrhs, transpose, Zj, nullptr, ctx->d_w, 0, s);
+      // classical Gram-Schmidt, applied twice
+      launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h, D, s);
+      launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h, D, ctx->d_w, N, S, ctx->d_active, s);
+      launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h2, D, s);
+      launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h2, D, ctx->d_w, N, S, ctx->d_active, s);
+      kadd::add_kernel<<<(S * D + 127) / 128, 128, 0, s>>>(ctx->d_h, ctx->d_h2, S * D);
+      launch_multidot(ctx->d_w, 0, 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s);
+      gm_count(ctx->d_active, ctx->d_nj, S, s);
+      gm_givens(ctx->d_h, D, ctx->d_hn, D, S, j, m, tol, ctx->d_H, ctx->d_cs, ctx->d_sn, ctx->d_g,
+                ctx->d_vscale, ctx->d_active, ctx->d_resid, ctx->d_bnorm, s);
+      CK(cudaGetLastError());
+      ++total;
+      jdone = j + 1;
+      CKS(any_active(ctx, S, &any, &res));
+      if (!any || total >= ctx->opt.ir_max_iter) break;
+      if (j + 1 < m) gm_scale(ctx->d_V + (size_t)(j + 1) * vs, ctx->d_w, ctx->d_vscale, N, S, s);
+    }
+    gm_solve(ctx->d_H, ctx->d_g, S, m, ctx->d_nj, ctx->d_ycoef, s);
+    launch_multiaxpy(ctx->d_Z, (long long)vs, jdone, ctx->d_ycoef, D, x, N, S, nullptr, s);
+    CK(cudaGetLastError());
+  }
+  ctx->last_iters = total;
+  ctx->last_resid = res;
+  if (!converged)
+    return fail(ctx, FDFD_ERR_NOT_CONVERGED,
+                "refinement stopped at relative residual " + std::to_string(res) + " after " +
+                    std::to_string(total) + " iterations");
+  return FDFD_OK;
+}
+
+// Checks the pivot growth of the last FP32 factorisation; refactors in FP64 if needed.
+fdfd_status settle_growth(fdfd_ctx* ctx) {
+  if (!ctx->growth_pending) return FDFD_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->growth_pending = false;
+  const float g = *ctx->h_growth_max;
+  ctx->last_growth = g;
+  if (!(g <= ctx->opt.growth_bound)) {
+    ctx->fallbacks += 1;
+    CKS(factor_levels<double2>(ctx, false));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const float g64 = *ctx->h_growth_max;
+    ctx->last_growth = g64;
+    if (!std::isfinite(g64))
+      return fail(ctx, FDFD_ERR_PIVOT, "zero or non-finite pivot in the FP64 factorisation");
+    ctx->valid64 = true;
+  }
+  return FDFD_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void fdfd_default_options(fdfd_options* o) {
+  if (!o) return;
+  o->mode = FDFD_MODE_MIXED;
+  o->ir_tol = 1e-12;
+  o->ir_max_iter = 40;
+  o->gmres_restart = 8;
+  o->growth_bound = 1e6;
+  o->leaf_area = 32;
+}
+
+fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
+                        fdfd_pml pml, fdfd_box design, const fdfd_options* opt, void* cuda_stream) {
+  if (!out) return FDFD_ERR_ARG;
+  *out = nullptr;
+  if (grid.nx <= 0 || grid.ny <= 0 || n_omega <= 0 || !k0_host || !(dx > 0)) return FDFD_ERR_ARG;
+  if (pml.npml_x < 0 || pml.npml_y < 0 || 2 * pml.npml_x > grid.nx || 2 * pml.npml_y > grid.ny)
+    return FDFD_ERR_ARG;
+  if (design.w < 0 || design.h < 0) return FDFD_ERR_ARG;
+  if (design.w > 0 && design.h > 0 &&
+      (design.x0 < 0 || design.y0 < 0 || design.x0 + design.w > grid.nx || design.y0 + design.h > grid.ny))
+    return FDFD_ERR_ARG;
+  if ((long long)grid.nx * grid.ny * 5 >= (1LL << 31)) return FDFD_ERR_ARG;
+  for (int w = 0; w < n_omega; ++w)
+    if (!(k0_host[w] > 0)) return FDFD_ERR_ARG;
+  fdfd_ctx* c = new fdfd_ctx();
+  c->nx = grid.nx;
+  c->ny = grid.ny;
+  c->dx = dx;
+  c->n_omega = n_omega;
+  for (int w = 0; w < n_omega; ++w) c->k0dx.push_back(k0_host[w] * dx);
+  c->pml = pml;
+  if (!(c->pml.order > 0)) c->pml.order = 3.0;
+  if (!(c->pml.ln_R < 0)) c->pml.ln_R = std::log(1e-8);
+  c->box = design;
+  if (design.w == 0 || design.h == 0) c->box = fdfd_box{0, 0, 0, 0};
+  fdfd_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  if (c->opt.gmres_restart < 1) c->opt.gmres_restart = 1;
+  if (c->opt.gmres_restart > 16) c->opt.gmres_restart = 16;
+  if (c->opt.leaf_area < 1) c->opt.leaf_area = 32;
+  if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_analyze(fdfd_ctx* ctx) {
+  if (!ctx) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->analyzed) return FDFD_OK;
+  return analyze_host(ctx);
+}
+
+fdfd_status fdfd_factor(fdfd_ctx* ctx, const double* eps_dev) {
+  if (!ctx || !eps_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  CKS(ensure_runtime(ctx));
+  CK(cudaMemcpyAsync(ctx->d_eps, eps_dev, sizeof(double) * n_cells(ctx), cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->have_eps = true;
+  ctx->valid32 = ctx->valid64 = false;
+  if (ctx->opt.mode == FDFD_MODE_PLAIN) return FDFD_OK;   // factorised inside every solve
+  CKS(ensure_device(ctx));
+  if (ctx->opt.mode == FDFD_MODE_F64) {
+    CKS(factor_levels<double2>(ctx, false));
+    ctx->valid64 = true;
+    ctx->growth_pending = false;
+  } else {
+    CKS(factor_levels<float2>(ctx, false));
+    ctx->valid32 = true;
+    ctx->growth_pending = true;
+  }
+  ctx->nf += ctx->n_omega;
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev) {
+  if (!ctx || !eps_design_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_refactor_design before fdfd_factor");
+  if (ctx->box.w == 0) return fail(ctx, FDFD_ERR_STATE, "context has no design box");
+  CKS(ensure_runtime(ctx));
+  launch_scatter_design(ctx->d_eps, eps_design_dev, ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w, ctx->box.h,
+                        ctx->stream);
+  CK(cudaGetLastError());
+  if (ctx->opt.mode == FDFD_MODE_PLAIN) return FDFD_OK;
+  CKS(ensure_device(ctx));
+  if (ctx->opt.mode == FDFD_MODE_F64) {
+    if (!ctx->valid64) return fail(ctx, FDFD_ERR_STATE, "no cached factorisation");
+    CKS(factor_levels<double2>(ctx, true));
+  } else {
+    if (!ctx->valid32) return fail(ctx, FDFD_ERR_STATE, "no cached factorisation");
+    CKS(factor_levels<float2>(ctx, true));
+    ctx->valid64 = false;
+    ctx->growth_pending = true;
+  }
+  ctx->nf += ctx->n_omega;
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose) {
+  if (!ctx || !b_dev || !x_dev || nrhs <= 0 || b_dev == x_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_solve before fdfd_factor");
+  const double2* b = reinterpret_cast<const double2*>(b_dev);
+  double2* x = reinterpret_cast<double2*>(x_dev);
+  const long long N = n_cells(ctx);
+  const int S = ctx->n_omega * nrhs;
+  if (ctx->opt.mode == FDFD_MODE_PLAIN) {
+    // The paper's uncached arm: every system gets its own symbolic and numeric factorisation.
+    CKS(ensure_runtime(ctx));
+    for (int r = 0; r < nrhs; ++r) {
+      for (int w = 0; w < ctx->n_omega; ++w) {
+        CKS(analyze_host(ctx));
+        CKS(upload_plan(ctx));
+        CKS(ensure_ws(ctx, nrhs));
+        CKS(factor_levels<double2>(ctx, false, w, 1));
+        ctx->nf += 1;
+        CKS(sweeps<double2>(ctx, nrhs, transpose, b, x, w, 1, r, 1));
+        ctx->bs += 1;
+      }
+    }
+    ctx->last_iters = 0;
+    (void)S;
+    return FDFD_OK;
+  }
+  CKS(ensure_device(ctx));
+  CKS(ensure_ws(ctx, nrhs));
+  CKS(settle_growth(ctx));
+  ctx->bs += S;
+  if (ctx->valid64 && (ctx->opt.mode == FDFD_MODE_F64)) {
+    CKS(sweeps<double2>(ctx, nrhs, transpose, b, x));
+    ctx->last_iters = 0;
+    return FDFD_OK;
+  }
+  if (ctx->opt.ir_max_iter == 0) {
+    // raw solve on the cached factors, no refinement
+    return precond(ctx, nrhs, transpose, b, x);
+  }
+  (void)N;
+  return fgmres(ctx, b, x, nrhs, transpose);
+}
+
+fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev, const double* g_dev,
+                           const double* weight_dev, double* o_dev, double* F_dev, double* b_adj_dev) {
+  if (!ctx || !x_dev || nrhs <= 0 || !cols_dev || !g_dev || !o_dev || !F_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  launch_objective(reinterpret_cast<const double2*>(x_dev), n_cells(ctx), ctx->ny, cols_dev,
+                   reinterpret_cast<const double2*>(g_dev), weight_dev, ctx->n_omega * nrhs,
+                   reinterpret_cast<double2*>(o_dev), F_dev, reinterpret_cast<double2*>(b_adj_dev), ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_adj_dev, int nrhs,
+                      const double* weight_dev, double* grad_dev, int accumulate) {
+  if (!ctx || !x_fwd_dev || !x_adj_dev || nrhs <= 0 || !grad_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->box.w == 0) return fail(ctx, FDFD_ERR_STATE, "context has no design box");
+  CKS(ensure_runtime(ctx));
+  launch_grad(reinterpret_cast<const double2*>(x_fwd_dev), reinterpret_cast<const double2*>(x_adj_dev),
+              n_cells(ctx), ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w, ctx->box.h, ctx->n_omega, nrhs,
+              ctx->d_k0dx2, weight_dev, grad_dev, accumulate, ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose) {
+  if (!ctx || !x_dev || !y_dev || nrhs <= 0 || x_dev == y_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_apply before fdfd_factor");
+  CKS(ensure_runtime(ctx));
+  launch_stencil(dev_coef(ctx), ctx->n_omega, nrhs, transpose, reinterpret_cast<const double2*>(x_dev), nullptr,
+                 reinterpret_cast<double2*>(y_dev), 0, ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_set_options(fdfd_ctx* ctx, const fdfd_options* opt) {
+  if (!ctx || !opt) return FDFD_ERR_ARG;
+  ctx->opt.ir_tol = opt->ir_tol;
+  ctx->opt.ir_max_iter = std::max(0, opt->ir_max_iter);
+  ctx->opt.gmres_restart = std::max(1, std::min(16, opt->gmres_restart));
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* o) {
+  if (!ctx || !o) return FDFD_ERR_ARG;
+  if (ctx->device >= 0) CK(cudaStreamSynchronize(ctx->stream));
+  std::memset(o, 0, sizeof(*o));
+  o->sf = ctx->sf;
+  o->nf = ctx->nf;
+  o->bs = ctx->bs;
+  o->sweeps = ctx->sweeps;
+  o->ir_iters = ctx->last_iters;
+  o->ir_resid = ctx->last_resid;
+  o->fallbacks = ctx->fallbacks;
+  o->growth = ctx->last_growth;
+  if (ctx->analyzed) {
+    const Plan& p = ctx->plan;
+    o->n_fronts = (int)p.fronts.size();
+    o->n_levels = p.n_levels;
+    o->max_front = p.max_front;
+    o->factor_entries = p.factor_entries;
+    o->flops_factor = p.flops_factor;
+    o->flops_design = p.flops_design;
+    long long b = 0;
+    if (ctx->d_store32) b += (long long)p.store_total * ctx->n_omega * 8;
+    if (ctx->d_store64) b += (long long)p.store_total * ctx->n_omega * 16;
+    o->store_bytes = b;
+  }
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k, int* m, int* parent, int* level, int* design, int* idx) {
+  if (!ctx) return FDFD_ERR_ARG;
+  if (!ctx->analyzed) return fail(ctx, FDFD_ERR_STATE, "plan requested before fdfd_analyze");
+  const Plan& p = ctx->plan;
+  for (size_t f = 0; f < p.fronts.size(); ++f) {
+    const FrontDesc& d = p.fronts[f];
+    if (k) k[f] = d.k;
+    if (m) m[f] = d.m;
+    if (parent) parent[f] = d.parent;
+    if (level) level[f] = d.level;
+    if (design) design[f] = d.design;
+  }
+  if (idx) std::memcpy(idx, p.idx.data(), sizeof(int) * p.idx.size());
+  return FDFD_OK;
+}
+
+void fdfd_reset_counters(fdfd_ctx* ctx) {
+  if (!ctx) return;
+  ctx->sf = ctx->nf = ctx->bs = ctx->sweeps = ctx->fallbacks = 0;
+}
+
+const char* fdfd_last_error(const fdfd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void fdfd_destroy(fdfd_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->device >= 0) cudaStreamSynchronize(ctx->stream);
+  free_plan_device(ctx);
+  free_factor(ctx);
+  free_ws(ctx);
+  free_gm(ctx);
+  void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
+                ctx->d_growth_max};
+  for (void* p : ps) free_ptr(p);
+  if (ctx->h_growth_max) cudaFreeHost(ctx->h_growth_max);
+  if (ctx->h_active) cudaFreeHost(ctx->h_active);
+  if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,460 @@
+// Numeric multifrontal factorisation (paper Sec. II, "numerical factorization").
+//
+// Every front f is a dense (k+m) x (k+m) matrix, row-major with row stride ld,
+// ordered [k pivots | m boundary variables]:
+//     [F11 F12]      P F11 = L11 U11,  U12 = L11^-1 P F12,
+//     [F21 F22]      L21 = F21 U11^-1,  S = F22 - L21 U12.
+// After factorisation the front holds L11\U11 (unit L), U12, L21 and, in its
+// trailing m x m block, the update matrix S that the parent extend-adds.  S is
+// never modified afterwards, so the fronts of an unchanged subtree remain valid
+// update sources for a later design refactor.
+//
+// Pivoting is partial, restricted to the k fully-summed rows of the front.
+// The largest |L| entry of each front is recorded as its pivot-growth figure.
+// All reductions run in a fixed order: a factorisation is a deterministic
+// function of its inputs, bit for bit.
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace fdfd {
+
+namespace {
+
+constexpr int kBuildWarps = 8;
+
+// ---------------------------------------------------------------------------
+// Front build: F = originals + sum over children of their update matrices,
+// gathered through the children's inverse extend-add maps (no atomics).
+// One warp per front row, 8 rows per CTA.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBuildWarps * 32)
+build_kernel(FactorLaunch a, const int2* __restrict__ tasks) {
+  const int w = blockIdx.y + a.w0;
+  const int2 t = tasks[blockIdx.x];
+  const int f = t.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const FrontDesc d = a.P.fronts[f];
+  const int r = t.y + warp;
+  if (r >= d.n) return;
+  T* st = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride;
+  T* F = st + d.st_off + (size_t)r * d.ld;
+  // up to two children (nested dissection splits into at most two parts)
+  const T* S0 = nullptr;
+  const T* S1 = nullptr;
+  const int* inv0 = nullptr;
+  const int* inv1 = nullptr;
+  int ld0 = 0, ld1 = 0;
+  if (d.nchild > 0) {
+    const FrontDesc c = a.P.fronts[a.P.children[d.child0]];
+    const int ia = a.P.inv[c.inv_off + r];
+    if (ia >= 0) {
+      S0 = st + c.st_off + (size_t)(c.k + ia) * c.ld + c.k;
+      inv0 = a.P.inv + c.inv_off;
+      ld0 = c.ld;
+    }
+  }
+  if (d.nchild > 1) {
+    const FrontDesc c = a.P.fronts[a.P.children[d.child0 + 1]];
+    const int ia = a.P.inv[c.inv_off + r];
+    if (ia >= 0) {
+      S1 = st + c.st_off + (size_t)(c.k + ia) * c.ld + c.k;
+      inv1 = a.P.inv + c.inv_off;
+      ld1 = c.ld;
+    }
+  }
+  (void)ld0; (void)ld1;
+  const int e0 = a.P.orig_ptr[d.orig_off + r], e1 = a.P.orig_ptr[d.orig_off + r + 1];
+  for (int b = lane; b < d.n; b += 32) {
+    T acc = czero<T>();
+    if (S0) { const int ib = inv0[b]; if (ib >= 0) acc = cadd(acc, S0[ib]); }
+    if (S1) { const int ib = inv1[b]; if (ib >= 0) acc = cadd(acc, S1[ib]); }
+    for (int e = e0; e < e1; ++e)
+      if (a.P.orig_col[e] == b) acc = cadd(acc, cfrom<T>(stencil_entry(a.C, w, a.P.orig_code[e])));
+    F[b] = acc;
+  }
+}
+
+// max that lets a NaN win, so that a poisoned front is always flagged
+template <typename R>
+__device__ __forceinline__ R nanmax(R a, R b) {
+  if (a != a) return a;
+  if (b != b) return b;
+  return a > b ? a : b;
+}
+
+// warp argmax of |v|^2 with ties going to the smaller index
+template <typename R>
+__device__ __forceinline__ void warp_argmax(R& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    R ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small fronts: the whole front in shared memory, one CTA per front.
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 256;
+constexpr int kSmallMaxK = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads)
+lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
+  using R = typename RealOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);
+  __shared__ int pm[kSmallMaxK];
+  __shared__ int s_piv;
+  __shared__ R s_red[kSmallThreads / 32];
+  const int w = blockIdx.y + a.w0;
+  const int f = flist[blockIdx.x];
+  const FrontDesc d = a.P.fronts[f];
+  const int n = d.n, k = d.k;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    S[e] = F[(size_t)r * d.ld + c];
+  }
+  for (int i = tid; i < k; i += blockDim.x) pm[i] = i;
+  __syncthreads();
+  R gmax = 0;
+  for (int j = 0; j < k; ++j) {
+    if (warp == 0) {
+      R best = -1;
+      int bi = j;
+      for (int r = j + lane; r < k; r += 32) {
+        const R v = cabs2(S[r * n + j]);
+        if (v > best) { best = v; bi = r; }
+      }
+      warp_argmax(best, bi);
+      if (lane == 0) s_piv = bi;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != j) {
+      for (int c = tid; c < n; c += blockDim.x) {
+        const T x = S[j * n + c];
+        S[j * n + c] = S[piv * n + c];
+        S[piv * n + c] = x;
+      }
+      if (tid == 0) { const int x = pm[j]; pm[j] = pm[piv]; pm[piv] = x; }
+    }
+    __syncthreads();
+    const T inv = crcp(S[j * n + j]);
+    for (int r = j + 1 + tid; r < n; r += blockDim.x) {
+      const T l = cmul(S[r * n + j], inv);
+      S[r * n + j] = l;
+      gmax = nanmax(gmax, cabs2(l));
+    }
+    if (S[j * n + j].x == 0 && S[j * n + j].y == 0) gmax = INFINITY;
+    __syncthreads();
+    const int ty = tid >> 5, tx = tid & 31;
+    for (int r = j + 1 + ty; r < n; r += kSmallThreads / 32) {
+      const T l = S[r * n + j];
+      for (int c = j + 1 + tx; c < n; c += 32) S[r * n + c] = cfms(l, S[j * n + c], S[r * n + c]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    F[(size_t)r * d.ld + c] = S[e];
+  }
+  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  for (int i = tid; i < k; i += blockDim.x) P[i] = pm[i];
+  // growth: block max of |L| (fixed reduction order)
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) s_red[warp] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    R g = 0;
+    for (int i = 0; i < kSmallThreads / 32; ++i) g = nanmax(g, s_red[i]);
+    a.growth[(size_t)w * a.n_fronts + f] = (float)sqrt((double)g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Large fronts, blocked right-looking LU.  One panel step at column j0:
+//   panel: factor columns [j0, j0+nb) over rows [j0, n) (one CTA per front),
+//   trsm:  U rows [j0, j0+nb) of columns [j0+nb, n) (one CTA per 128 columns),
+//   gemm:  trailing update of [j0+nb, n)^2 (one CTA per 64 x 64 tile).
+// ---------------------------------------------------------------------------
+constexpr int kPanelThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads)
+lu_panel_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  using R = typename RealOf<T>::type;
+  __shared__ R s_v[kPanelThreads / 32];
+  __shared__ int s_i[kPanelThreads / 32];
+  __shared__ int s_piv;
+  const int w = blockIdx.y + a.w0;
+  const int f = flist[blockIdx.x];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int n = d.n, k = d.k, ld = d.ld;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (j0 == 0) {
+    for (int i = tid; i < k; i += blockDim.x) P[i] = i;
+    __syncthreads();
+  }
+  R gmax = 0;
+  for (int j = j0; j < j0 + nb; ++j) {
+    R best = -1;
+    int bi = j;
+    for (int r = j + tid; r < k; r += blockDim.x) {
+      const R v = cabs2(F[(size_t)r * ld + j]);
+      if (v > best) { best = v; bi = r; }
+    }
+    warp_argmax(best, bi);
+    if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      R bv = s_v[0];
+      int bidx = s_i[0];
+      for (int i = 1; i < kPanelThreads / 32; ++i)
+        if (s_v[i] > bv || (s_v[i] == bv && s_i[i] < bidx)) { bv = s_v[i]; bidx = s_i[i]; }
+      s_piv = bidx;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != j) {
+      for (int c = tid; c < n; c += blockDim.x) {
+        const T x = F[(size_t)j * ld + c];
+        F[(size_t)j * ld + c] = F[(size_t)piv * ld + c];
+        F[(size_t)piv * ld + c] = x;
+      }
+      if (tid == 0) { const int x = P[j]; P[j] = P[piv]; P[piv] = x; }
+    }
+    __syncthreads();
+    const T pv = F[(size_t)j * ld + j];
+    const T inv = crcp(pv);
+    if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
+    for (int r = j + 1 + tid; r < n; r += blockDim.x) {
+      const T l = cmul(F[(size_t)r * ld + j], inv);
+      F[(size_t)r * ld + j] = l;
+      gmax = nanmax(gmax, cabs2(l));
+    }
+    __syncthreads();
+    const int cols = j0 + nb - (j + 1);
+    if (cols > 0) {
+      // rank-1 update of the panel columns (j, j0+nb): thread -> (row, col)
+      for (long long e = tid; e < (long long)(n - j - 1) * cols; e += blockDim.x) {
+        const int r = j + 1 + (int)(e / cols), c = j + 1 + (int)(e % cols);
+        F[(size_t)r * ld + c] = cfms(F[(size_t)r * ld + j], F[(size_t)j * ld + c], F[(size_t)r * ld + c]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) s_v[warp] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    R g = 0;
+    for (int i = 0; i < kPanelThreads / 32; ++i) g = nanmax(g, s_v[i]);
+    float* gp = a.growth + (size_t)w * a.n_fronts + f;
+    const float gv = (float)sqrt((double)g);
+    *gp = (j0 == 0) ? gv : nanmax(*gp, gv);
+  }
+}
+
+constexpr int kTrsmCols = 128;
+constexpr int kMaxNb = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(kTrsmCols)
+lu_trsm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  __shared__ T Ls[kMaxNb][kMaxNb + 1];
+  const int w = blockIdx.z + a.w0;
+  const int f = flist[blockIdx.y];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int c = j0 + nb + blockIdx.x * kTrsmCols + threadIdx.x;
+  if (j0 + nb + blockIdx.x * kTrsmCols >= d.n) return;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, l = e - i * nb;
+    Ls[i][l] = F[(size_t)(j0 + i) * d.ld + j0 + l];
+  }
+  __syncthreads();
+  if (c >= d.n) return;
+  T x[kMaxNb];
+#pragma unroll
+  for (int i = 0; i < kMaxNb; ++i)
+    if (i < nb) x[i] = F[(size_t)(j0 + i) * d.ld + c];
+#pragma unroll
+  for (int i = 1; i < kMaxNb; ++i) {
+    if (i < nb) {
+      T v = x[i];
+#pragma unroll
+      for (int l = 0; l < kMaxNb; ++l)
+        if (l < i) v = cfms(Ls[i][l], x[l], v);
+      x[i] = v;
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < kMaxNb; ++i)
+    if (i < nb) F[(size_t)(j0 + i) * d.ld + c] = x[i];
+}
+
+constexpr int kGemmTile = 64;
+template <typename T> struct GemmKc;
+template <> struct GemmKc<float2> { static constexpr int v = 32; };
+template <> struct GemmKc<double2> { static constexpr int v = 16; };
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  constexpr int KC = GemmKc<T>::v;
+  __shared__ T As[kGemmTile][KC + 1];
+  __shared__ T Bs[KC][kGemmTile];
+  const int w = blockIdx.z + a.w0;
+  const int f = flist[blockIdx.y];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int base = j0 + nb;
+  const int rem = d.n - base;
+  if (rem <= 0) return;
+  const int nt = (rem + kGemmTile - 1) / kGemmTile;
+  if ((int)blockIdx.x >= nt * nt) return;
+  const int ti = blockIdx.x / nt, tj = blockIdx.x - ti * nt;
+  const int r0 = base + ti * kGemmTile, c0 = base + tj * kGemmTile;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = czero<T>();
+  for (int kc = 0; kc < nb; kc += KC) {
+    for (int e = tid; e < kGemmTile * KC; e += 256) {
+      const int r = e / KC, kk = e - r * KC;
+      const int gr = r0 + r, gk = kc + kk;
+      As[r][kk] = (gr < d.n && gk < nb) ? F[(size_t)gr * d.ld + j0 + gk] : czero<T>();
+    }
+    for (int e = tid; e < kGemmTile * KC; e += 256) {
+      const int kk = e / kGemmTile, c = e - kk * kGemmTile;
+      const int gc = c0 + c, gk = kc + kk;
+      Bs[kk][c] = (gc < d.n && gk < nb) ? F[(size_t)(j0 + gk) * d.ld + gc] : czero<T>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[ty + 16 * i][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gr = r0 + ty + 16 * i;
+    if (gr >= d.n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = c0 + tx + 16 * j;
+      if (gc < d.n) {
+        T* p = F + (size_t)gr * d.ld + gc;
+        *p = csub(*p, acc[i][j]);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int lu_small_max_n(int elem_bytes) { return elem_bytes == 8 ? 96 : 64; }
+
+namespace {
+__global__ void growth_max_kernel(const float* g, long long count, float* out) {
+  __shared__ float red[32];
+  float v = 0.f;
+  for (long long t = threadIdx.x; t < count; t += blockDim.x) v = nanmax(v, g[t]);
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r = nanmax(r, red[i]);
+    *out = r;
+  }
+}
+}  // namespace
+
+cudaError_t launch_growth_max(const float* growth, long long count, float* out, cudaStream_t s) {
+  growth_max_kernel<<<1, 1024, 0, s>>>(growth, count, out);
+  return cudaGetLastError();
+}
+
+cudaError_t factor_init_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 96 * 8);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              64 * 64 * 16);
+}
+int lu_panel_width(int elem_bytes) { (void)elem_bytes; return kMaxNb; }
+
+template <typename T>
+void launch_build(const FactorLaunch& a, const int2* tasks, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  build_kernel<T><<<dim3(ntasks, a.n_omega), kBuildWarps * 32, 0, s>>>(a, tasks);
+}
+
+template <typename T>
+void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, cudaStream_t s) {
+  if (nf <= 0) return;
+  const size_t smem = (size_t)nmax * nmax * sizeof(T);
+  lu_small_kernel<T><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
+}
+
+template <typename T>
+void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, cudaStream_t s) {
+  if (nf <= 0) return;
+  lu_panel_kernel<T><<<dim3(nf, a.n_omega), kPanelThreads, 0, s>>>(a, flist, j0, nb);
+}
+
+template <typename T>
+void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int nmax,
+                    cudaStream_t s) {
+  const int cols = nmax - j0 - 1;
+  if (nf <= 0 || cols <= 0) return;
+  const int gx = (cols + kTrsmCols - 1) / kTrsmCols;
+  lu_trsm_kernel<T><<<dim3(gx, nf, a.n_omega), kTrsmCols, 0, s>>>(a, flist, j0, nb);
+}
+
+template <typename T>
+void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int nmax,
+                    cudaStream_t s) {
+  const int rem = nmax - j0 - 1;
+  if (nf <= 0 || rem <= 0) return;
+  const int nt = (rem + kGemmTile - 1) / kGemmTile;
+  lu_gemm_kernel<T><<<dim3(nt * nt, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb);
+}
+
+#define FDFD_INST(T)                                                                              \
+  template void launch_build<T>(const FactorLaunch&, const int2*, int, cudaStream_t);            \
+  template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
+  template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, cudaStream_t); \
+  template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
+  template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t);
+FDFD_INST(float2)
+FDFD_INST(double2)
+#undef FDFD_INST
+
+}  // namespace fdfd

@@ -1,0 +1,103 @@
+// Launchers of the CUDA kernels (host-callable, defined in the .cu files).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace fdfd {
+
+// ---- assembly.cu: stencil coefficients (Eq. 1-2 with SC-PML) ---------------
+void launch_coef(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2,
+                 const double* k0dx_dev, int n_omega, int nx, int ny, int npml_x, int npml_y,
+                 double ln_R, double order, cudaStream_t s);
+void launch_scatter_design(double* eps, const double* eps_design, int ny, int x0, int y0, int w,
+                           int h, cudaStream_t s);
+
+// ---- factor.cu: multifrontal numeric factorisation -----------------------
+struct FactorLaunch {
+  DevPlan P;
+  DevCoef C;
+  void* store;             // float2* or double2*, [n_omega][store_stride]
+  long long store_stride;
+  int* perm;               // [n_omega][perm_stride]
+  int perm_stride;
+  float* growth;           // [n_omega][n_fronts]: max |L| entry (inf when a pivot is zero)
+  int n_fronts;
+  int n_omega;             // wavelengths launched: [w0, w0 + n_omega)
+  int w0;
+};
+// max over growth[0..count) (NaN wins) into *out
+cudaError_t launch_growth_max(const float* growth, long long count, float* out, cudaStream_t s);
+// build (assemble originals + extend-add children) rows listed in tasks (front, row0)
+template <typename T> void launch_build(const FactorLaunch& a, const int2* tasks, int ntasks, cudaStream_t s);
+// whole-front LU in shared memory, one CTA per front
+template <typename T> void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax,
+                                           cudaStream_t s);
+// blocked right-looking LU of large fronts: one panel step at column j0
+template <typename T> void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                           int nb, cudaStream_t s);
+template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                          int nb, int nmax, cudaStream_t s);
+template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                          int nb, int nmax, cudaStream_t s);
+int lu_small_max_n(int elem_bytes);
+cudaError_t factor_init_attributes();   // once per device, before the first factorisation
+int lu_panel_width(int elem_bytes);
+
+// ---- solve.cu: level-scheduled triangular sweeps ---------------------------
+struct SolveLaunch {
+  DevPlan P;
+  const void* store;       // factor storage (T), [n_omega][store_stride]
+  long long store_stride;
+  const int* perm;
+  int perm_stride;
+  void* vb;                // front vectors (T), [n_sys][vec_stride]
+  long long vec_stride;
+  int n_omega, nrhs;       // wavelengths launched [w0, w0 + n_omega); nrhs = layout stride
+  int w0, r0, nr;          // right-hand sides processed: [r0, r0 + nr)
+  long long n;             // unknowns per system
+};
+// sweep: 0 = L (forward, non-transposed), 1 = U (backward, non-transposed),
+//        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
+// in: right-hand side (sweeps 0, 2) [n_sys][n]; out: solution (sweeps 1, 3) [n_sys][n].
+template <typename T> void launch_sweep(const SolveLaunch& a, int sweep, const int* flist, int nf,
+                                        int nmax, int kmax, const void* in, void* out, cudaStream_t s);
+
+// ---- vec.cu: FP64 refinement, objective, gradient ---------------------------
+// y = A x (op = 0) or r = b - A x (op = 1), FP64 matrix-free stencil, all systems.
+void launch_stencil(const DevCoef& c, int n_omega, int nrhs, int transpose, const double2* x,
+                    const double2* b, double2* y, int op, cudaStream_t s);
+template <typename T> void launch_cvt_from64(T* dst, const double2* src, const double* scale,
+                                             long long n, int nsys, cudaStream_t s);
+template <typename T> void launch_cvt_to64(double2* dst, const T* src, const double* scale,
+                                           long long n, int nsys, cudaStream_t s);
+// batched dot products h[s][i] = sum conj(V_i[s]) w[s], i < nv (V_i at V + i*vstride)
+void launch_multidot(const double2* V, long long vstride, int nv, const double2* w, long long n,
+                     int nsys, double2* partial, int nblk, double2* out, int out_ld, cudaStream_t s);
+// w[s] -= sum_i h[s][i] V_i[s]
+void launch_multiaxpy(const double2* V, long long vstride, int nv, const double2* h, int h_ld,
+                      double2* w, long long n, int nsys, const int* active, cudaStream_t s);
+int multidot_blocks(long long n);
+int multidot_max_vectors();
+
+// FGMRES bookkeeping (one thread per system); see vec.cu
+void gm_start(const double2* rr, int rr_ld, const double2* bb, int bb_ld, int nsys, double tol, int m,
+              double2* g, double* vscale, int* active, double* resid, double* bnorm, int first, cudaStream_t s);
+void gm_givens(const double2* h, int h_ld, const double2* hn, int hn_ld, int nsys, int j, int m, double tol,
+               double2* H, double2* cs, double2* sn, double2* g, double* vscale, int* active, double* resid,
+               const double* bnorm, cudaStream_t s);
+void gm_solve(const double2* H, const double2* g, int nsys, int m, const int* njs, double2* ny_out,
+              cudaStream_t s);
+void gm_scale(double2* dst, const double2* src, const double* scale, long long n, int nsys, cudaStream_t s);
+void gm_count(const int* active, int* nj, int nsys, cudaStream_t s);
+
+// objective o = g^T x on a monitor column, F = sum weight |o|^2, adjoint source weight conj(o) g
+void launch_objective(const double2* x, long long N, int ny, const int* cols, const double2* gline,
+                      const double* weight, int nsys, double2* o, double* F, double2* badj, cudaStream_t s);
+// dF/deps over the design box: sum weight * 2 (k0dx)^2 Re(x_adj x_fwd)
+void launch_grad(const double2* xf, const double2* xa, long long N, int ny, int x0, int y0, int w, int h,
+                 int n_omega, int nrhs, const double* k0dx2, const double* weight, double* grad, int accumulate,
+                 cudaStream_t s);
+cudaError_t solve_init_attributes();
+
+}  // namespace fdfd

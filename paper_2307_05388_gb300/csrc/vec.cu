@@ -1,0 +1,446 @@
+// Operator assembly tables (Eq. 1-2 with stretched-coordinate PML), the FP64
+// matrix-free stencil used by the refinement, FGMRES vector kernels, the
+// mode-overlap objective with its adjoint source (Eq. 4) and the pixel
+// gradient (Eq. 3).
+//
+// Operator (dimensionless: Eq. 1 multiplied by mu0 dx^2), row (i, j):
+//   A[(i,j),(i-1,j)] = cxm[i] = -1 / (sx(i+1/2) sx(i)),   A[(i,j),(i+1,j)] = cxp[i] = -1 / (sx(i+1/2) sx(i+1))
+//   A[(i,j),(i,j-1)] = cym[j],                            A[(i,j),(i,j+1)] = cyp[j]
+//   A[(i,j),(i,j)]   = -(cxm + cxp + cym + cyp) - (k0 dx)^2 eps[i,j]
+// with positions in cell units (cell i centred at i + 1/2) and the stretch
+//   s(u) = 1 - i * [-(order+1) ln R / (2 k0dx npml)] * d(u)^order,
+//   d(u) = max(npml - u, u - (n - npml), 0) / npml,
+// i.e. e^{+i w t} convention: s = 1 - i sigma / (omega eps0).  Neighbours
+// beyond the grid are zero (PEC behind the PML).
+#include "kernels.h"
+
+namespace fdfd {
+
+namespace {
+
+__device__ double2 stretch(double u, int n, int npml, double k0dx, double ln_R, double order) {
+  if (npml <= 0) return make_double2(1.0, 0.0);
+  double d = fmax(fmax((double)npml - u, u - (double)(n - npml)), 0.0) / (double)npml;
+  double smax = -(order + 1.0) * ln_R / (2.0 * k0dx * (double)npml);
+  double p = (order == 3.0) ? d * d * d : pow(d, order);
+  return make_double2(1.0, -smax * p);
+}
+
+__device__ double2 neg_inv_prod(double2 a, double2 b) {
+  double2 p = cmul(a, b);
+  double2 r = crcp(p);
+  return make_double2(-r.x, -r.y);
+}
+
+__global__ void coef_kernel(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2,
+                            const double* k0dx, int n_omega, int nx, int ny, int px, int py,
+                            double ln_R, double order) {
+  const int w = blockIdx.y;
+  const double kd = k0dx[w];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) k0dx2[w] = kd * kd;
+  if (t < nx) {
+    const double2 sc = stretch(t + 0.5, nx, px, kd, ln_R, order);
+    cxm[(size_t)w * nx + t] = neg_inv_prod(sc, stretch(t, nx, px, kd, ln_R, order));
+    cxp[(size_t)w * nx + t] = neg_inv_prod(sc, stretch(t + 1.0, nx, px, kd, ln_R, order));
+  }
+  if (t < ny) {
+    const double2 sc = stretch(t + 0.5, ny, py, kd, ln_R, order);
+    cym[(size_t)w * ny + t] = neg_inv_prod(sc, stretch(t, ny, py, kd, ln_R, order));
+    cyp[(size_t)w * ny + t] = neg_inv_prod(sc, stretch(t + 1.0, ny, py, kd, ln_R, order));
+  }
+}
+
+__global__ void scatter_design_kernel(double* eps, const double* ed, int ny, int x0, int y0, int w, int h) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)w * h) return;
+  const int i = (int)(t / h), j = (int)(t - (long long)i * h);
+  eps[(size_t)(x0 + i) * ny + y0 + j] = ed[t];
+}
+
+// y = A x (op 0) or y = b - A x (op 1); transpose selects A^T.
+__global__ void stencil_kernel(DevCoef c, int nrhs, int transpose, const double2* __restrict__ x,
+                               const double2* __restrict__ b, double2* __restrict__ y, int op) {
+  const int sys = blockIdx.y;
+  const int w = sys / nrhs;
+  const long long N = (long long)c.nx * c.ny;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  const int i = (int)(cell / c.ny), j = (int)(cell - (long long)i * c.ny);
+  const double2* X = x + (size_t)sys * N;
+  const double2* cxm = c.cxm + (size_t)w * c.nx;
+  const double2* cxp = c.cxp + (size_t)w * c.nx;
+  const double2* cym = c.cym + (size_t)w * c.ny;
+  const double2* cyp = c.cyp + (size_t)w * c.ny;
+  double2 dg;
+  dg.x = -(cxm[i].x + cxp[i].x + cym[j].x + cyp[j].x) - c.k0dx2[w] * c.eps[cell];
+  dg.y = -(cxm[i].y + cxp[i].y + cym[j].y + cyp[j].y);
+  double2 acc = cmul(dg, X[cell]);
+  if (!transpose) {
+    if (i > 0) acc = cfma(cxm[i], X[cell - c.ny], acc);
+    if (i + 1 < c.nx) acc = cfma(cxp[i], X[cell + c.ny], acc);
+    if (j > 0) acc = cfma(cym[j], X[cell - 1], acc);
+    if (j + 1 < c.ny) acc = cfma(cyp[j], X[cell + 1], acc);
+  } else {
+    if (i > 0) acc = cfma(cxp[i - 1], X[cell - c.ny], acc);
+    if (i + 1 < c.nx) acc = cfma(cxm[i + 1], X[cell + c.ny], acc);
+    if (j > 0) acc = cfma(cyp[j - 1], X[cell - 1], acc);
+    if (j + 1 < c.ny) acc = cfma(cym[j + 1], X[cell + 1], acc);
+  }
+  if (op == 1) {
+    const double2 bb = b[(size_t)sys * N + cell];
+    acc = make_double2(bb.x - acc.x, bb.y - acc.y);
+  }
+  y[(size_t)sys * N + cell] = acc;
+}
+
+template <typename T>
+__global__ void cvt_from64_kernel(T* dst, const double2* src, const double* scale, long long n) {
+  const int sys = blockIdx.y;
+  const double sc = scale ? scale[sys] : 1.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[(size_t)sys * n + t];
+    dst[(size_t)sys * n + t] = cfrom<T>(make_double2(v.x * sc, v.y * sc));
+  }
+}
+
+template <typename T>
+__global__ void cvt_to64_kernel(double2* dst, const T* src, const double* scale, long long n) {
+  const int sys = blockIdx.y;
+  const double sc = scale ? scale[sys] : 1.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double2 v = cto64(src[(size_t)sys * n + t]);
+    dst[(size_t)sys * n + t] = make_double2(v.x * sc, v.y * sc);
+  }
+}
+
+constexpr int kDotThreads = 256;
+constexpr int kMaxDot = 17;
+
+__global__ void __launch_bounds__(kDotThreads)
+multidot_partial_kernel(const double2* __restrict__ V, long long vstride, int nv,
+                        const double2* __restrict__ w, long long n, double2* partial, int nblk) {
+  __shared__ double2 red[kDotThreads / 32][kMaxDot];
+  const int sys = blockIdx.y;
+  double2 acc[kMaxDot];
+#pragma unroll
+  for (int i = 0; i < kMaxDot; ++i) acc[i] = make_double2(0, 0);
+  const double2* W = w + (size_t)sys * n;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)nblk * blockDim.x) {
+    const double2 wv = W[t];
+#pragma unroll
+    for (int i = 0; i < kMaxDot; ++i)
+      if (i < nv) acc[i] = cfma(cconj(V[(size_t)i * vstride + (size_t)sys * n + t]), wv, acc[i]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kMaxDot; ++i) {
+    if (i >= nv) break;
+    double2 v = acc[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double2 s = make_double2(0, 0);
+    for (int q = 0; q < kDotThreads / 32; ++q) s = cadd(s, red[q][threadIdx.x]);
+    partial[((size_t)sys * kMaxDot + threadIdx.x) * nblk + blockIdx.x] = s;
+  }
+}
+
+__global__ void multidot_final_kernel(const double2* partial, int nblk, int nv, double2* out, int out_ld) {
+  const int sys = blockIdx.x;
+  const int i = threadIdx.x;
+  if (i >= nv) return;
+  double2 s = make_double2(0, 0);
+  const double2* p = partial + ((size_t)sys * kMaxDot + i) * nblk;
+  for (int b = 0; b < nblk; ++b) s = cadd(s, p[b]);
+  out[(size_t)sys * out_ld + i] = s;
+}
+
+__global__ void multiaxpy_kernel(const double2* __restrict__ V, long long vstride, int nv,
+                                 const double2* __restrict__ h, int h_ld, double2* w, long long n,
+                                 const int* active) {
+  const int sys = blockIdx.y;
+  if (active && !active[sys]) return;
+  double2 hh[kMaxDot];
+#pragma unroll
+  for (int i = 0; i < kMaxDot; ++i) hh[i] = (i < nv) ? h[(size_t)sys * h_ld + i] : make_double2(0, 0);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double2 acc = w[(size_t)sys * n + t];
+#pragma unroll
+    for (int i = 0; i < kMaxDot; ++i)
+      if (i < nv) acc = cfms(hh[i], V[(size_t)i * vstride + (size_t)sys * n + t], acc);
+    w[(size_t)sys * n + t] = acc;
+  }
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 2048 ? b : 2048);
+}
+
+}  // namespace
+
+void launch_coef(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2,
+                 const double* k0dx_dev, int n_omega, int nx, int ny, int npml_x, int npml_y,
+                 double ln_R, double order, cudaStream_t s) {
+  const int nmax = nx > ny ? nx : ny;
+  coef_kernel<<<dim3((nmax + 127) / 128, n_omega), 128, 0, s>>>(cxm, cxp, cym, cyp, k0dx2, k0dx_dev,
+                                                               n_omega, nx, ny, npml_x, npml_y, ln_R, order);
+}
+
+void launch_scatter_design(double* eps, const double* eps_design, int ny, int x0, int y0, int w, int h,
+                           cudaStream_t s) {
+  const long long n = (long long)w * h;
+  if (n <= 0) return;
+  scatter_design_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(eps, eps_design, ny, x0, y0, w, h);
+}
+
+void launch_stencil(const DevCoef& c, int n_omega, int nrhs, int transpose, const double2* x,
+                    const double2* b, double2* y, int op, cudaStream_t s) {
+  const long long N = (long long)c.nx * c.ny;
+  stencil_kernel<<<dim3((unsigned)((N + 255) / 256), n_omega * nrhs), 256, 0, s>>>(c, nrhs, transpose, x, b, y, op);
+}
+
+template <typename T>
+void launch_cvt_from64(T* dst, const double2* src, const double* scale, long long n, int nsys, cudaStream_t s) {
+  cvt_from64_kernel<T><<<dim3(grid_for(n), nsys), 256, 0, s>>>(dst, src, scale, n);
+}
+template <typename T>
+void launch_cvt_to64(double2* dst, const T* src, const double* scale, long long n, int nsys, cudaStream_t s) {
+  cvt_to64_kernel<T><<<dim3(grid_for(n), nsys), 256, 0, s>>>(dst, src, scale, n);
+}
+template void launch_cvt_from64<float2>(float2*, const double2*, const double*, long long, int, cudaStream_t);
+template void launch_cvt_from64<double2>(double2*, const double2*, const double*, long long, int, cudaStream_t);
+template void launch_cvt_to64<float2>(double2*, const float2*, const double*, long long, int, cudaStream_t);
+template void launch_cvt_to64<double2>(double2*, const double2*, const double*, long long, int, cudaStream_t);
+
+int multidot_blocks(long long n) {
+  long long b = (n + kDotThreads * 4 - 1) / (kDotThreads * 4);
+  if (b > 304) b = 304;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+int multidot_max_vectors() { return kMaxDot; }
+
+void launch_multidot(const double2* V, long long vstride, int nv, const double2* w, long long n, int nsys,
+                     double2* partial, int nblk, double2* out, int out_ld, cudaStream_t s) {
+  multidot_partial_kernel<<<dim3(nblk, nsys), kDotThreads, 0, s>>>(V, vstride, nv, w, n, partial, nblk);
+  multidot_final_kernel<<<nsys, 32, 0, s>>>(partial, nblk, nv, out, out_ld);
+}
+
+void launch_multiaxpy(const double2* V, long long vstride, int nv, const double2* h, int h_ld, double2* w,
+                      long long n, int nsys, const int* active, cudaStream_t s) {
+  multiaxpy_kernel<<<dim3(grid_for(n), nsys), 256, 0, s>>>(V, vstride, nv, h, h_ld, w, n, active);
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES bookkeeping per system (one thread per system).
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void gm_start_kernel(const double2* rr, int rr_ld, const double2* bb, int bb_ld, int nsys,
+                                double tol, int m, double2* g, double* vscale, int* active, double* resid,
+                                double* bnorm, int first) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const double beta = sqrt(fmax(rr[(size_t)s * rr_ld].x, 0.0));
+  if (first) bnorm[s] = sqrt(fmax(bb[(size_t)s * bb_ld].x, 0.0));
+  const double bn = bnorm[s];
+  for (int i = 0; i <= m; ++i) g[(size_t)s * (m + 1) + i] = make_double2(0, 0);
+  g[(size_t)s * (m + 1)] = make_double2(beta, 0);
+  resid[s] = bn > 0 ? beta / bn : 0.0;
+  const int act = (bn > 0) && (beta > tol * bn) && (beta == beta);
+  active[s] = act;
+  vscale[s] = act ? 1.0 / beta : 0.0;
+}
+
+// h: [nsys][ld] with h[0..j] the projections and hn2 = |w|^2 in hn[s*ld2].x
+__global__ void gm_givens_kernel(const double2* h, int h_ld, const double2* hn, int hn_ld, int nsys, int j,
+                                 int m, double tol, double2* H, double2* cs, double2* sn, double2* g,
+                                 double* vscale, int* active, double* resid, const double* bnorm) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys || !active[s]) return;
+  double2* Hc = H + ((size_t)s * m + j) * (m + 1);   // column j of H
+  for (int i = 0; i <= j; ++i) Hc[i] = h[(size_t)s * h_ld + i];
+  const double hnorm = sqrt(fmax(hn[(size_t)s * hn_ld].x, 0.0));
+  Hc[j + 1] = make_double2(hnorm, 0);
+  double2* C = cs + (size_t)s * m;
+  double2* S = sn + (size_t)s * m;
+  for (int i = 0; i < j; ++i) {   // apply earlier rotations
+    const double2 x = Hc[i], y = Hc[i + 1];
+    const double c = C[i].x;
+    Hc[i] = cadd(make_double2(c * x.x, c * x.y), cmul(S[i], y));
+    Hc[i + 1] = csub(make_double2(c * y.x, c * y.y), cmul(cconj(S[i]), x));
+  }
+  const double2 a = Hc[j];
+  const double b = hnorm;
+  const double aa = sqrt(a.x * a.x + a.y * a.y);
+  double c;
+  double2 sv, r;
+  if (aa == 0.0) {
+    c = 0.0; sv = make_double2(1, 0); r = make_double2(b, 0);
+  } else {
+    const double t = sqrt(aa * aa + b * b);
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    c = aa / t;
+    sv = make_double2(ph.x * b / t, ph.y * b / t);
+    r = make_double2(ph.x * t, ph.y * t);
+  }
+  C[j] = make_double2(c, 0);
+  S[j] = sv;
+  Hc[j] = r;
+  Hc[j + 1] = make_double2(0, 0);
+  double2* G = g + (size_t)s * (m + 1);
+  const double2 gj = G[j];
+  G[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));  // -conj(s) g_j
+  G[j] = make_double2(c * gj.x, c * gj.y);
+  const double rn = sqrt(G[j + 1].x * G[j + 1].x + G[j + 1].y * G[j + 1].y);
+  const double bn = bnorm[s];
+  resid[s] = rn / bn;
+  vscale[s] = hnorm > 0 ? 1.0 / hnorm : 0.0;
+  if (!(rn > tol * bn) || !(hnorm > 0)) active[s] = 0;   // converged (or breakdown: solution exact)
+}
+
+// y = R^-1 g over the first nj columns, then x += sum_i y_i Z_i is done by multiaxpy with -y.
+__global__ void gm_solve_kernel(const double2* H, const double2* g, int nsys, int m, const int* njs,
+                                double2* ny_out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  const int nj = njs[s];
+  const double2* Hs = H + (size_t)s * m * (m + 1);
+  const double2* G = g + (size_t)s * (m + 1);
+  double2 y[kMaxDot];
+  for (int i = nj - 1; i >= 0; --i) {
+    double2 acc = G[i];
+    for (int q = i + 1; q < nj; ++q) acc = cfms(Hs[(size_t)q * (m + 1) + i], y[q], acc);
+    y[i] = cmul(acc, crcp(Hs[(size_t)i * (m + 1) + i]));
+  }
+  for (int i = 0; i < kMaxDot; ++i)
+    ny_out[(size_t)s * kMaxDot + i] = i < nj ? make_double2(-y[i].x, -y[i].y) : make_double2(0, 0);
+}
+
+__global__ void scale_vec_kernel(double2* dst, const double2* src, const double* scale, long long n) {
+  const int sys = blockIdx.y;
+  const double sc = scale[sys];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[(size_t)sys * n + t];
+    dst[(size_t)sys * n + t] = make_double2(v.x * sc, v.y * sc);
+  }
+}
+
+__global__ void count_iter_kernel(const int* active, int* nj, int nsys) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsys && active[s]) nj[s] += 1;
+}
+
+}  // namespace
+
+void gm_start(const double2* rr, int rr_ld, const double2* bb, int bb_ld, int nsys, double tol, int m,
+              double2* g, double* vscale, int* active, double* resid, double* bnorm, int first, cudaStream_t s) {
+  gm_start_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(rr, rr_ld, bb, bb_ld, nsys, tol, m, g, vscale, active, resid,
+                                                  bnorm, first);
+}
+void gm_givens(const double2* h, int h_ld, const double2* hn, int hn_ld, int nsys, int j, int m, double tol,
+               double2* H, double2* cs, double2* sn, double2* g, double* vscale, int* active, double* resid,
+               const double* bnorm, cudaStream_t s) {
+  gm_givens_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(h, h_ld, hn, hn_ld, nsys, j, m, tol, H, cs, sn, g, vscale,
+                                                   active, resid, bnorm);
+}
+void gm_solve(const double2* H, const double2* g, int nsys, int m, const int* njs, double2* ny_out,
+              cudaStream_t s) {
+  gm_solve_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(H, g, nsys, m, njs, ny_out);
+}
+void gm_scale(double2* dst, const double2* src, const double* scale, long long n, int nsys, cudaStream_t s) {
+  scale_vec_kernel<<<dim3(grid_for(n), nsys), 256, 0, s>>>(dst, src, scale, n);
+}
+void gm_count(const int* active, int* nj, int nsys, cudaStream_t s) {
+  count_iter_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(active, nj, nsys);
+}
+
+// ---------------------------------------------------------------------------
+// Objective (mode overlap), adjoint source and pixel gradient.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void overlap_kernel(const double2* __restrict__ x, long long N, int ny, const int* cols,
+                               const double2* __restrict__ gline, double2* o) {
+  __shared__ double2 red[8];
+  const int sys = blockIdx.x;
+  const double2* X = x + (size_t)sys * N + (size_t)cols[sys] * ny;
+  const double2* G = gline + (size_t)sys * ny;
+  double2 acc = make_double2(0, 0);
+  for (int j = threadIdx.x; j < ny; j += blockDim.x) acc = cfma(G[j], X[j], acc);
+  for (int off = 16; off > 0; off >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0, 0);
+    for (int q = 0; q < 8; ++q) s = cadd(s, red[q]);
+    o[sys] = s;
+  }
+}
+
+__global__ void objective_kernel(const double2* o, const double* weight, int nsys, double* F) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0;
+  for (int q = 0; q < nsys; ++q) s += (weight ? weight[q] : 1.0) * (o[q].x * o[q].x + o[q].y * o[q].y);
+  *F = s;
+}
+
+__global__ void adjoint_source_kernel(const double2* o, const double* weight, long long N, int ny, const int* cols,
+                                      const double2* __restrict__ gline, double2* badj) {
+  const int sys = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ny) return;
+  const double wt = weight ? weight[sys] : 1.0;
+  const double2 oc = make_double2(wt * o[sys].x, -wt * o[sys].y);
+  badj[(size_t)sys * N + (size_t)cols[sys] * ny + j] = cmul(oc, gline[(size_t)sys * ny + j]);
+}
+
+__global__ void grad_kernel(const double2* __restrict__ xf, const double2* __restrict__ xa, long long N, int ny,
+                            int x0, int y0, int w, int h, int n_omega, int nrhs, const double* k0dx2,
+                            const double* weight, double* grad, int accumulate) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)w * h) return;
+  const int i = (int)(t / h), j = (int)(t - (long long)i * h);
+  const size_t cell = (size_t)(x0 + i) * ny + y0 + j;
+  double acc = 0;
+  for (int om = 0; om < n_omega; ++om)
+    for (int r = 0; r < nrhs; ++r) {
+      const size_t sys = (size_t)om * nrhs + r;
+      const double2 p = cmul(xa[sys * N + cell], xf[sys * N + cell]);
+      acc += (weight ? weight[sys] : 1.0) * 2.0 * k0dx2[om] * p.x;
+    }
+  grad[t] = accumulate ? grad[t] + acc : acc;
+}
+
+}  // namespace
+
+void launch_objective(const double2* x, long long N, int ny, const int* cols, const double2* gline,
+                      const double* weight, int nsys, double2* o, double* F, double2* badj, cudaStream_t s) {
+  overlap_kernel<<<nsys, 256, 0, s>>>(x, N, ny, cols, gline, o);
+  objective_kernel<<<1, 32, 0, s>>>(o, weight, nsys, F);
+  if (badj) {
+    cudaMemsetAsync(badj, 0, sizeof(double2) * (size_t)nsys * N, s);
+    adjoint_source_kernel<<<dim3((ny + 255) / 256, nsys), 256, 0, s>>>(o, weight, N, ny, cols, gline, badj);
+  }
+}
+
+void launch_grad(const double2* xf, const double2* xa, long long N, int ny, int x0, int y0, int w, int h,
+                 int n_omega, int nrhs, const double* k0dx2, const double* weight, double* grad, int accumulate,
+                 cudaStream_t s) {
+  const long long n = (long long)w * h;
+  if (n <= 0) return;
+  grad_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xf, xa, N, ny, x0, y0, w, h, n_omega, nrhs, k0dx2,
+                                                          weight, grad, accumulate);
+}
+
+}  // namespace fdfd
