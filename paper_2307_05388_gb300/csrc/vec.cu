@@ -371,7 +371,12 @@ __global__ void overlap_kernel(const double2* __restrict__ x, long long N, int n
                                const double2* __restrict__ gline, double2* o) {
   __shared__ double2 red[8];
   const int sys = blockIdx.x;
-  const double2* X = x + (size_t)sys * N + (size_t)cols[sys] * ny;
+  const int col = cols[sys];
+  if (col < 0 || (long long)(col + 1) * ny > N) {   // monitor column outside the grid
+    if (threadIdx.x == 0) o[sys] = make_double2(NAN, NAN);
+    return;
+  }
+  const double2* X = x + (size_t)sys * N + (size_t)col * ny;
   const double2* G = gline + (size_t)sys * ny;
   double2 acc = make_double2(0, 0);
   for (int j = threadIdx.x; j < ny; j += blockDim.x) acc = cfma(G[j], X[j], acc);
@@ -399,7 +404,7 @@ __global__ void adjoint_source_kernel(const double2* o, const double* weight, lo
                                       const double2* __restrict__ gline, double2* badj) {
   const int sys = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ny) return;
+  if (j >= ny || cols[sys] < 0 || (long long)(cols[sys] + 1) * ny > N) return;
   const double wt = weight ? weight[sys] : 1.0;
   const double2 oc = make_double2(wt * o[sys].x, -wt * o[sys].y);
   badj[(size_t)sys * N + (size_t)cols[sys] * ny + j] = cmul(oc, gline[(size_t)sys * ny + j]);
