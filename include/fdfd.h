@@ -184,6 +184,23 @@ fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* out);
 fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k_host, int* m_host, int* parent_host, int* level_host,
                              int* design_host, int* idx_host);
 
+/* Per-kernel profile: while enabled, every kernel launch of the solver is
+ * bracketed by CUDA events on the context's stream and its algorithmic work
+ * (flops at 8 per complex multiply-add, and the bytes the method must move) is
+ * recorded.  Enabling (or disabling) clears the records.  Profiling adds event
+ * records between launches, so time the unprofiled path separately. */
+typedef struct {
+  char name[32];               /* kernel class, e.g. "lu_gemm", "sweep_L" */
+  long long launches;
+  double ms;                   /* summed event time of its launches */
+  double flops;                /* summed algorithmic flops */
+  double bytes;                /* summed algorithmic bytes */
+} fdfd_kernel_profile;
+fdfd_status fdfd_profile_enable(fdfd_ctx* ctx, int on);
+/* Writes up to max_out kernel classes to out and their count to *n_out
+ * (synchronises the context's stream).  out is host memory. */
+fdfd_status fdfd_profile_get(fdfd_ctx* ctx, fdfd_kernel_profile* out, int max_out, int* n_out);
+
 /* Resets the SF/NF/BS counters. */
 void fdfd_reset_counters(fdfd_ctx* ctx);
 

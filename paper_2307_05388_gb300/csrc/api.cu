@@ -104,6 +104,13 @@ struct fdfd_ctx {
   int* h_active = nullptr;          // pinned
   double* h_resid = nullptr;        // pinned
 
+  // per-kernel profile (CUDA events around every launch when enabled)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct ProfRec { int kind; size_t e0, e1; double flops, bytes; };
+  std::vector<ProfRec> prof_recs;
+
   // counters
   long long sf = 0, nf = 0, bs = 0, sweeps = 0, fallbacks = 0;
   long long last_iters = 0;
@@ -135,6 +142,40 @@ fdfd_status fail(fdfd_ctx* c, fdfd_status st, const std::string& msg) {
 void free_ptr(void* p) {
   if (p) cudaFree(p);
 }
+
+enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_SWEEP_L, PK_SWEEP_U,
+                PK_SWEEP_UT, PK_SWEEP_LT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT, PK_COUNT };
+const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm",
+                                          "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "stencil_f64",
+                                          "gmres_dot", "gmres_axpy", "precision_cvt"};
+
+size_t prof_event(fdfd_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+    c->ev_pool.push_back(e);
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+  return c->ev_used++;
+}
+
+// Brackets one kernel launch with events when profiling is on; flops and bytes
+// are the launch's algorithmic work (what the method must do, not what ran).
+struct Prof {
+  fdfd_ctx* c;
+  int kind;
+  double flops, bytes;
+  size_t e0 = (size_t)-1;
+  Prof(fdfd_ctx* ctx, int k, double f, double b) : c(ctx), kind(k), flops(f), bytes(b) {
+    if (c->prof_on) e0 = prof_event(c);
+  }
+  ~Prof() {
+    if (c->prof_on && e0 != (size_t)-1) {
+      size_t e1 = prof_event(c);
+      if (e1 != (size_t)-1) c->prof_recs.push_back({kind, e0, e1, flops, bytes});
+    }
+  }
+};
 
 void free_plan_device(fdfd_ctx* c) {
   free_ptr(c->d_fronts); free_ptr(c->d_children); free_ptr(c->d_idx); free_ptr(c->d_inv);
@@ -334,15 +375,55 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   const std::vector<LevelList>& lv = design_only ? ctx->lv_design[prec] : ctx->lv_full[prec];
   const int nb = lu_panel_width(sizeof(T));
   cudaStream_t s = ctx->stream;
+  const double es = sizeof(T), nwd = fa.n_omega;
+  const int* hl = ctx->h_lists.data();
   for (int l = 0; l < p.n_levels; ++l) {
     const LevelList& ll = lv[l];
-    launch_build<T>(fa, reinterpret_cast<const int2*>(ctx->d_lists + ll.task_off), ll.ntasks, s);
-    launch_lu_small<T>(fa, ctx->d_lists + ll.small_off, ll.nsmall, ll.nmax_small, s);
+    {
+      double by = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.ntasks; ++t) {
+          const FrontDesc& d = p.fronts[hl[ll.task_off + 2 * t]];
+          const int rows = std::min(8, d.n - hl[ll.task_off + 2 * t + 1]);
+          by += es * rows * d.n;                                   // front rows written
+          for (int ci = 0; ci < d.nchild; ++ci) {                  // child update rows read
+            const FrontDesc& c = p.fronts[p.children[d.child0 + ci]];
+            by += es * (double)c.m * c.m * rows / std::max(1, d.n);
+          }
+        }
+      Prof pr(ctx, PK_BUILD, 0, by * nwd);
+      launch_build<T>(fa, reinterpret_cast<const int2*>(ctx->d_lists + ll.task_off), ll.ntasks, s);
+    }
+    {
+      double fl = 0, by = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.nsmall; ++t) {
+          const FrontDesc& d = p.fronts[hl[ll.small_off + t]];
+          for (int j = 0; j < d.k; ++j) fl += 8.0 * (double)(d.n - j - 1) * (d.n - j - 1);
+          by += 2.0 * es * d.n * d.n;
+        }
+      Prof pr(ctx, PK_LU_SMALL, fl * nwd, by * nwd);
+      launch_lu_small<T>(fa, ctx->d_lists + ll.small_off, ll.nsmall, ll.nmax_small, s);
+    }
     for (int j0 = 0; j0 < ll.kmax_large; j0 += nb) {
       const int* fl = ctx->d_lists + ll.large_off;
-      launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, s);
-      launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s);
-      launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s);
+      double pf = 0, pb = 0, tf = 0, tb = 0, gf = 0, gb = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.nlarge; ++t) {
+          const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
+          if (j0 >= d.k) continue;
+          const int b = std::min(nb, d.k - j0);
+          for (int j = j0; j < j0 + b; ++j) pf += 8.0 * (double)(d.n - j - 1) * (j0 + b - j);
+          pb += 2.0 * es * (double)(d.n - j0) * b;
+          const double rem = d.n - j0 - b;
+          tf += 8.0 * 0.5 * b * (b - 1) * rem;
+          tb += 2.0 * es * b * rem;
+          gf += 8.0 * b * rem * rem;
+          gb += es * (2.0 * rem * rem + 2.0 * rem * b);
+        }
+      { Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd); launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, s); }
+      { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
+      { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
     }
   }
   CK(cudaGetLastError());
@@ -384,12 +465,29 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   sa.n = n_cells(ctx);
   cudaStream_t s = ctx->stream;
   const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
+  const double es = sizeof(T), nsys = (double)sa.n_omega * sa.nr;
+  auto work = [&](const SolveList& sl, bool lower, double* fl, double* by) {
+    *fl = *by = 0;
+    if (!ctx->prof_on) return;
+    for (int t = 0; t < sl.nf; ++t) {
+      const FrontDesc& d = p.fronts[ctx->h_lists[sl.off + t]];
+      const double ent = lower ? 0.5 * d.k * (d.k - 1.0) + (double)d.m * d.k : 0.5 * d.k * (d.k + 1.0) + (double)d.m * d.k;
+      *fl += 8.0 * ent * nsys;
+      *by += es * ent * nsys + 3.0 * es * d.n * nsys;   // factor entries once per rhs + front vectors
+    }
+  };
   for (int l = 0; l < p.n_levels; ++l) {
     const SolveList& sl = ctx->lv_solve[l];
+    double fl, by;
+    work(sl, !transpose, &fl, &by);
+    Prof pr(ctx, transpose ? PK_SWEEP_UT : PK_SWEEP_L, fl, by);
     launch_sweep<T>(sa, fwd, ctx->d_lists + sl.off, sl.nf, sl.nmax, sl.kmax, in, out, s);
   }
   for (int l = p.n_levels - 1; l >= 0; --l) {
     const SolveList& sl = ctx->lv_solve[l];
+    double fl, by;
+    work(sl, transpose, &fl, &by);
+    Prof pr(ctx, transpose ? PK_SWEEP_LT : PK_SWEEP_U, fl, by);
     launch_sweep<T>(sa, bwd, ctx->d_lists + sl.off, sl.nf, sl.nmax, sl.kmax, in, out, s);
   }
   CK(cudaGetLastError());
@@ -404,9 +502,15 @@ fdfd_status precond(fdfd_ctx* ctx, int nrhs, int transpose, const double2* src, 
   if (ctx->valid64) {
     return sweeps<double2>(ctx, nrhs, transpose, src, dst);
   }
-  launch_cvt_from64<float2>(reinterpret_cast<float2*>(ctx->d_bT), src, nullptr, N, S, ctx->stream);
+  {
+    Prof pr(ctx, PK_CVT, 0, 24.0 * N * S);
+    launch_cvt_from64<float2>(reinterpret_cast<float2*>(ctx->d_bT), src, nullptr, N, S, ctx->stream);
+  }
   CKS(sweeps<float2>(ctx, nrhs, transpose, ctx->d_bT, ctx->d_xT));
-  launch_cvt_to64<float2>(dst, reinterpret_cast<const float2*>(ctx->d_xT), nullptr, N, S, ctx->stream);
+  {
+    Prof pr(ctx, PK_CVT, 0, 24.0 * N * S);
+    launch_cvt_to64<float2>(dst, reinterpret_cast<const float2*>(ctx->d_xT), nullptr, N, S, ctx->stream);
+  }
   CK(cudaGetLastError());
   return FDFD_OK;
 }
@@ -487,7 +591,10 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   double res = 0;
   bool converged = false;
   for (int cycle = 0;; ++cycle) {
-    if (cycle > 0) launch_stencil(C, ctx->n_omega, nrhs, transpose, x, b, ctx->d_r, 1, s);
+    if (cycle > 0) {
+      Prof pr(ctx, PK_STENCIL, 48.0 * N * S, 56.0 * N * S);
+      launch_stencil(C, ctx->n_omega, nrhs, transpose, x, b, ctx->d_r, 1, s);
+    }
     launch_multidot(ctx->d_r, 0, 1, ctx->d_r, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s);
     gm_start(ctx->d_hn, D, ctx->d_bd, D, S, tol, m, ctx->d_g, ctx->d_vscale, ctx->d_active, ctx->d_resid,
              ctx->d_bnorm, cycle == 0 ? 1 : 0, s);
@@ -503,12 +610,21 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
       double2* Vj = ctx->d_V + (size_t)j * vs;
       double2* Zj = ctx->d_Z + (size_t)j * vs;
       CKS(precond(ctx, nrhs, transpose, Vj, Zj));
-      launch_stencil(C, ctx->n_omega, nrhs, transpose, Zj, nullptr, ctx->d_w, 0, s);
+      {
+        Prof pr(ctx, PK_STENCIL, 48.0 * N * S, 40.0 * N * S);
+        launch_stencil(C, ctx->n_omega, nrhs, transpose, Zj, nullptr, ctx->d_w, 0, s);
+      }
       // classical Gram-Schmidt, applied twice
-      launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h, D, s);
-      launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h, D, ctx->d_w, N, S, ctx->d_active, s);
-      launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h2, D, s);
-      launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h2, D, ctx->d_w, N, S, ctx->d_active, s);
+      const double dotb = 16.0 * (j + 2) * N * S, dotf = 8.0 * (j + 1) * N * S;
+      const double axb = 16.0 * (j + 3) * N * S;
+      { Prof pr(ctx, PK_DOT, dotf, dotb);
+        launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h, D, s); }
+      { Prof pr(ctx, PK_AXPY, dotf, axb);
+        launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h, D, ctx->d_w, N, S, ctx->d_active, s); }
+      { Prof pr(ctx, PK_DOT, dotf, dotb);
+        launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h2, D, s); }
+      { Prof pr(ctx, PK_AXPY, dotf, axb);
+        launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h2, D, ctx->d_w, N, S, ctx->d_active, s); }
       kadd::add_kernel<<<(S * D + 127) / 128, 128, 0, s>>>(ctx->d_h, ctx->d_h2, S * D);
       launch_multidot(ctx->d_w, 0, 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s);
       gm_count(ctx->d_active, ctx->d_nj, S, s);
@@ -790,6 +906,35 @@ fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k, int* m, int* parent, int* le
   return FDFD_OK;
 }
 
+fdfd_status fdfd_profile_enable(fdfd_ctx* ctx, int on) {
+  if (!ctx) return FDFD_ERR_ARG;
+  if (ctx->device >= 0) CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof_on = on != 0;
+  ctx->prof_recs.clear();
+  ctx->ev_used = 0;
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_profile_get(fdfd_ctx* ctx, fdfd_kernel_profile* out, int max_out, int* n_out) {
+  if (!ctx || !n_out || (max_out > 0 && !out)) return FDFD_ERR_ARG;
+  if (ctx->device >= 0) CK(cudaStreamSynchronize(ctx->stream));
+  fdfd_kernel_profile acc[PK_COUNT];
+  std::memset(acc, 0, sizeof(acc));
+  for (int k = 0; k < PK_COUNT; ++k) std::snprintf(acc[k].name, sizeof(acc[k].name), "%s", kProfNames[k]);
+  for (const auto& r : ctx->prof_recs) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_pool[r.e0], ctx->ev_pool[r.e1]));
+    acc[r.kind].launches += 1;
+    acc[r.kind].ms += ms;
+    acc[r.kind].flops += r.flops;
+    acc[r.kind].bytes += r.bytes;
+  }
+  int n = 0;
+  for (int k = 0; k < PK_COUNT && n < max_out; ++k) out[n++] = acc[k];
+  *n_out = PK_COUNT;
+  return FDFD_OK;
+}
+
 void fdfd_reset_counters(fdfd_ctx* ctx) {
   if (!ctx) return;
   ctx->sf = ctx->nf = ctx->bs = ctx->sweeps = ctx->fallbacks = 0;
@@ -807,6 +952,7 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
                 ctx->d_growth_max};
   for (void* p : ps) free_ptr(p);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->h_growth_max) cudaFreeHost(ctx->h_growth_max);
   if (ctx->h_active) cudaFreeHost(ctx->h_active);
   if (ctx->h_resid) cudaFreeHost(ctx->h_resid);

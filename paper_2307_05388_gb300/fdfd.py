@@ -25,7 +25,8 @@ MODE_MIXED, MODE_F64, MODE_PLAIN = 0, 1, 2
 # Every symbol include/fdfd.h declares (the CPU test checks the library exports them).
 EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
-           "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy"]
+           "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
+           "fdfd_profile_enable", "fdfd_profile_get"]
 
 
 class Grid(C.Structure):
@@ -56,6 +57,11 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelProfile(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"libfdfd.so not built at {path}; run paper_2307_05388_gb300.build.build()")
@@ -74,6 +80,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_set_options.argtypes = [vp, C.POINTER(Options)]
     lib.fdfd_stats_get.argtypes = [vp, C.POINTER(Stats)]
     lib.fdfd_plan_fronts.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.fdfd_profile_enable.argtypes = [vp, i]
+    lib.fdfd_profile_get.argtypes = [vp, C.POINTER(KernelProfile), i, C.POINTER(C.c_int)]
     lib.fdfd_reset_counters.argtypes = [vp]
     lib.fdfd_reset_counters.restype = None
     lib.fdfd_last_error.argtypes = [vp]
@@ -82,7 +90,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_destroy.restype = None
     for name in ("fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design", "fdfd_solve",
                  "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
-                 "fdfd_plan_fronts"):
+                 "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -224,6 +232,16 @@ class Solver:
         s = Stats()
         self._check(_lib.fdfd_stats_get(self._h, C.byref(s)), "fdfd_stats_get")
         return s.as_dict()
+
+    def profile(self, on: bool = True):
+        self._check(_lib.fdfd_profile_enable(self._h, int(bool(on))), "fdfd_profile_enable")
+
+    def profile_get(self) -> dict:
+        buf = (KernelProfile * 64)()
+        n = C.c_int()
+        self._check(_lib.fdfd_profile_get(self._h, buf, 64, C.byref(n)), "fdfd_profile_get")
+        return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, flops=buf[i].flops,
+                                           bytes=buf[i].bytes) for i in range(min(n.value, 64))}
 
     def reset_counters(self):
         _lib.fdfd_reset_counters(self._h)
