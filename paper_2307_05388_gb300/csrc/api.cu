@@ -144,10 +144,10 @@ void free_ptr(void* p) {
 }
 
 enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_SWEEP_L, PK_SWEEP_U,
-                PK_SWEEP_UT, PK_SWEEP_LT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT, PK_COUNT };
+                PK_SWEEP_UT, PK_SWEEP_LT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT, PK_OTHER, PK_COUNT };
 const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "stencil_f64",
-                                          "gmres_dot", "gmres_axpy", "precision_cvt"};
+                                          "gmres_dot", "gmres_axpy", "precision_cvt", "other"};
 
 size_t prof_event(fdfd_ctx* c) {
   if (c->ev_used == c->ev_pool.size()) {
@@ -427,6 +427,7 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
     }
   }
   CK(cudaGetLastError());
+  Prof pr_g(ctx, PK_OTHER, 0, 4.0 * p.fronts.size() * ctx->n_omega);
   CK(launch_growth_max(ctx->d_growth, (long long)p.fronts.size() * ctx->n_omega, ctx->d_growth_max, s));
   CK(cudaMemcpyAsync(ctx->h_growth_max, ctx->d_growth_max, sizeof(float), cudaMemcpyDeviceToHost, s));
   return FDFD_OK;
@@ -586,7 +587,8 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   cudaStream_t s = ctx->stream;
   CK(cudaMemsetAsync(x, 0, sizeof(double2) * vs, s));
   CK(cudaMemcpyAsync(ctx->d_r, b, sizeof(double2) * vs, cudaMemcpyDeviceToDevice, s));
-  launch_multidot(b, 0, 1, b, N, S, ctx->d_partial, nblk, ctx->d_bd, D, s);
+  { Prof pr(ctx, PK_DOT, 8.0 * N * S, 16.0 * N * S);
+    launch_multidot(b, 0, 1, b, N, S, ctx->d_partial, nblk, ctx->d_bd, D, s); }
   long long total = 0;
   double res = 0;
   bool converged = false;
@@ -595,15 +597,17 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
       Prof pr(ctx, PK_STENCIL, 48.0 * N * S, 56.0 * N * S);
       launch_stencil(C, ctx->n_omega, nrhs, transpose, x, b, ctx->d_r, 1, s);
     }
-    launch_multidot(ctx->d_r, 0, 1, ctx->d_r, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s);
+    { Prof pr(ctx, PK_DOT, 8.0 * N * S, 16.0 * N * S);
+      launch_multidot(ctx->d_r, 0, 1, ctx->d_r, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s); }
+    { Prof pr(ctx, PK_OTHER, 0, 0);
     gm_start(ctx->d_hn, D, ctx->d_bd, D, S, tol, m, ctx->d_g, ctx->d_vscale, ctx->d_active, ctx->d_resid,
-             ctx->d_bnorm, cycle == 0 ? 1 : 0, s);
+             ctx->d_bnorm, cycle == 0 ? 1 : 0, s); }
     CK(cudaGetLastError());
     bool any;
     CKS(any_active(ctx, S, &any, &res));
     if (!any) { converged = true; break; }
     if (total >= ctx->opt.ir_max_iter) break;
-    gm_scale(ctx->d_V, ctx->d_r, ctx->d_vscale, N, S, s);
+    { Prof pr(ctx, PK_OTHER, 0, 32.0 * N * S); gm_scale(ctx->d_V, ctx->d_r, ctx->d_vscale, N, S, s); }
     CK(cudaMemsetAsync(ctx->d_nj, 0, sizeof(int) * S, s));
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
@@ -625,20 +629,26 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
         launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h2, D, s); }
       { Prof pr(ctx, PK_AXPY, dotf, axb);
         launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h2, D, ctx->d_w, N, S, ctx->d_active, s); }
-      kadd::add_kernel<<<(S * D + 127) / 128, 128, 0, s>>>(ctx->d_h, ctx->d_h2, S * D);
-      launch_multidot(ctx->d_w, 0, 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s);
-      gm_count(ctx->d_active, ctx->d_nj, S, s);
+      { Prof pr(ctx, PK_OTHER, 0, 0); kadd::add_kernel<<<(S * D + 127) / 128, 128, 0, s>>>(ctx->d_h, ctx->d_h2, S * D); }
+      { Prof pr(ctx, PK_DOT, 8.0 * N * S, 16.0 * N * S);
+        launch_multidot(ctx->d_w, 0, 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s); }
+      { Prof pr(ctx, PK_OTHER, 0, 0); gm_count(ctx->d_active, ctx->d_nj, S, s); }
+      { Prof pr(ctx, PK_OTHER, 0, 0);
       gm_givens(ctx->d_h, D, ctx->d_hn, D, S, j, m, tol, ctx->d_H, ctx->d_cs, ctx->d_sn, ctx->d_g,
-                ctx->d_vscale, ctx->d_active, ctx->d_resid, ctx->d_bnorm, s);
+                ctx->d_vscale, ctx->d_active, ctx->d_resid, ctx->d_bnorm, s); }
       CK(cudaGetLastError());
       ++total;
       jdone = j + 1;
       CKS(any_active(ctx, S, &any, &res));
       if (!any || total >= ctx->opt.ir_max_iter) break;
-      if (j + 1 < m) gm_scale(ctx->d_V + (size_t)(j + 1) * vs, ctx->d_w, ctx->d_vscale, N, S, s);
+      if (j + 1 < m) {
+        Prof pr(ctx, PK_OTHER, 0, 32.0 * N * S);
+        gm_scale(ctx->d_V + (size_t)(j + 1) * vs, ctx->d_w, ctx->d_vscale, N, S, s);
+      }
     }
-    gm_solve(ctx->d_H, ctx->d_g, S, m, ctx->d_nj, ctx->d_ycoef, s);
-    launch_multiaxpy(ctx->d_Z, (long long)vs, jdone, ctx->d_ycoef, D, x, N, S, nullptr, s);
+    { Prof pr(ctx, PK_OTHER, 0, 0); gm_solve(ctx->d_H, ctx->d_g, S, m, ctx->d_nj, ctx->d_ycoef, s); }
+    { Prof pr(ctx, PK_AXPY, 8.0 * jdone * N * S, 16.0 * (jdone + 2) * N * S);
+      launch_multiaxpy(ctx->d_Z, (long long)vs, jdone, ctx->d_ycoef, D, x, N, S, nullptr, s); }
     CK(cudaGetLastError());
   }
   ctx->last_iters = total;
@@ -758,6 +768,7 @@ fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev) {
   if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_refactor_design before fdfd_factor");
   if (ctx->box.w == 0) return fail(ctx, FDFD_ERR_STATE, "context has no design box");
   CKS(ensure_runtime(ctx));
+  Prof pr_s(ctx, PK_OTHER, 0, 16.0 * ctx->box.w * ctx->box.h);
   launch_scatter_design(ctx->d_eps, eps_design_dev, ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w, ctx->box.h,
                         ctx->stream);
   CK(cudaGetLastError());
@@ -823,6 +834,7 @@ fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const i
                            const double* weight_dev, double* o_dev, double* F_dev, double* b_adj_dev) {
   if (!ctx || !x_dev || nrhs <= 0 || !cols_dev || !g_dev || !o_dev || !F_dev) return FDFD_ERR_ARG;
   ctx->err.clear();
+  Prof pr(ctx, PK_OTHER, 0, 0);
   launch_objective(reinterpret_cast<const double2*>(x_dev), n_cells(ctx), ctx->ny, cols_dev,
                    reinterpret_cast<const double2*>(g_dev), weight_dev, ctx->n_omega * nrhs,
                    reinterpret_cast<double2*>(o_dev), F_dev, reinterpret_cast<double2*>(b_adj_dev), ctx->stream);
@@ -836,6 +848,7 @@ fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_ad
   ctx->err.clear();
   if (ctx->box.w == 0) return fail(ctx, FDFD_ERR_STATE, "context has no design box");
   CKS(ensure_runtime(ctx));
+  Prof pr(ctx, PK_OTHER, 0, 0);
   launch_grad(reinterpret_cast<const double2*>(x_fwd_dev), reinterpret_cast<const double2*>(x_adj_dev),
               n_cells(ctx), ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w, ctx->box.h, ctx->n_omega, nrhs,
               ctx->d_k0dx2, weight_dev, grad_dev, accumulate, ctx->stream);
