@@ -29,8 +29,13 @@ struct LevelList {
 };
 
 struct SolveList {
-  int off = 0, nf = 0, nmax = 0, kmax = 0;
+  int off = 0, nf = 0, nmax = 0, kmax = 0;    // triangular list (all fronts of the level)
+  int mt_off = 0, nmt = 0, kt_off = 0, nkt = 0;  // rectangular tasks of large fronts
+  int mbig = 0, kbig = 0;
 };
+
+// Fronts above this size leave their off-diagonal block to the rectangular kernels.
+constexpr int kSolveBigN = 128;
 
 template <typename P>
 cudaError_t dalloc(P** p, size_t bytes) {
@@ -144,9 +149,10 @@ void free_ptr(void* p) {
 }
 
 enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_SWEEP_L, PK_SWEEP_U,
-                PK_SWEEP_UT, PK_SWEEP_LT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT, PK_OTHER, PK_COUNT };
+                PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT, PK_OTHER,
+                PK_COUNT };
 const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm",
-                                          "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "stencil_f64",
+                                          "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "precision_cvt", "other"};
 
 size_t prof_event(fdfd_ctx* c) {
@@ -278,13 +284,32 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
     }
   }
   ctx->lv_solve.assign(L, SolveList{});
+  const int rb = sweep_rect_block();
   for (int l = 0; l < L; ++l) {
     SolveList& sl = ctx->lv_solve[l];
     sl.off = (int)lists.size();
     for (int f : p.level_fronts[l]) {
-      lists.push_back(f); sl.nf++;
-      sl.nmax = std::max(sl.nmax, p.fronts[f].n);
-      sl.kmax = std::max(sl.kmax, p.fronts[f].k);
+      const FrontDesc& d = p.fronts[f];
+      const bool big = d.n > kSolveBigN;
+      lists.push_back(big ? (int)(0x80000000u | (unsigned)f) : f);
+      sl.nf++;
+      sl.nmax = std::max(sl.nmax, d.n);
+      sl.kmax = std::max(sl.kmax, d.k);
+    }
+    if (lists.size() % 2) lists.push_back(0);
+    sl.mt_off = (int)lists.size();          // blocks over the m boundary rows / columns
+    for (int f : p.level_fronts[l]) {
+      const FrontDesc& d = p.fronts[f];
+      if (d.n <= kSolveBigN) continue;
+      for (int t0 = 0; t0 < d.m; t0 += rb) { lists.push_back(f); lists.push_back(t0); sl.nmt++; }
+      sl.mbig = std::max(sl.mbig, d.m);
+      sl.kbig = std::max(sl.kbig, d.k);
+    }
+    sl.kt_off = (int)lists.size();          // blocks over the k pivot rows / columns
+    for (int f : p.level_fronts[l]) {
+      const FrontDesc& d = p.fronts[f];
+      if (d.n <= kSolveBigN) continue;
+      for (int a0 = 0; a0 < d.k; a0 += rb) { lists.push_back(f); lists.push_back(a0); sl.nkt++; }
     }
   }
   ctx->h_lists.swap(lists);
@@ -467,29 +492,56 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   cudaStream_t s = ctx->stream;
   const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
   const double es = sizeof(T), nsys = (double)sa.n_omega * sa.nr;
-  auto work = [&](const SolveList& sl, bool lower, double* fl, double* by) {
+  // algorithmic work: each factor entry of the swept triangle (and of the
+  // off-diagonal block) read once per right-hand side, 8 flops per entry
+  auto tri_work = [&](const SolveList& sl, bool lower, double* fl, double* by) {
     *fl = *by = 0;
     if (!ctx->prof_on) return;
     for (int t = 0; t < sl.nf; ++t) {
-      const FrontDesc& d = p.fronts[ctx->h_lists[sl.off + t]];
-      const double ent = lower ? 0.5 * d.k * (d.k - 1.0) + (double)d.m * d.k : 0.5 * d.k * (d.k + 1.0) + (double)d.m * d.k;
+      const int e = ctx->h_lists[sl.off + t];
+      const FrontDesc& d = p.fronts[e & 0x7fffffff];
+      double ent = lower ? 0.5 * d.k * (d.k - 1.0) : 0.5 * d.k * (d.k + 1.0);
+      if (e >= 0) ent += (double)d.m * d.k;
       *fl += 8.0 * ent * nsys;
-      *by += es * ent * nsys + 3.0 * es * d.n * nsys;   // factor entries once per rhs + front vectors
+      *by += es * ent * nsys + 3.0 * es * d.n * nsys;
     }
   };
+  auto rect_work = [&](const SolveList& sl, double* fl, double* by) {
+    *fl = *by = 0;
+    if (!ctx->prof_on) return;
+    for (int t = 0; t < sl.nmt; ++t) {
+      const FrontDesc& d = p.fronts[ctx->h_lists[sl.mt_off + 2 * t]];
+      const double rows = std::min(sweep_rect_block(), d.m - ctx->h_lists[sl.mt_off + 2 * t + 1]);
+      *fl += 8.0 * rows * d.k * nsys;
+      *by += es * rows * d.k * nsys;
+    }
+  };
+  const int* dl = ctx->d_lists;
   for (int l = 0; l < p.n_levels; ++l) {
     const SolveList& sl = ctx->lv_solve[l];
     double fl, by;
-    work(sl, !transpose, &fl, &by);
-    Prof pr(ctx, transpose ? PK_SWEEP_UT : PK_SWEEP_L, fl, by);
-    launch_sweep<T>(sa, fwd, ctx->d_lists + sl.off, sl.nf, sl.nmax, sl.kmax, in, out, s);
+    tri_work(sl, !transpose, &fl, &by);
+    {
+      Prof pr(ctx, transpose ? PK_SWEEP_UT : PK_SWEEP_L, fl, by);
+      launch_sweep_tri<T>(sa, fwd, dl + sl.off, sl.nf, sl.nmax, in, out, s);
+    }
+    if (sl.nmt > 0) {
+      rect_work(sl, &fl, &by);
+      Prof pr(ctx, PK_SWEEP_RECT, fl, by);
+      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.mt_off), sl.nmt, sl.kbig, out, s);
+    }
   }
   for (int l = p.n_levels - 1; l >= 0; --l) {
     const SolveList& sl = ctx->lv_solve[l];
     double fl, by;
-    work(sl, transpose, &fl, &by);
+    if (sl.nkt > 0) {
+      rect_work(sl, &fl, &by);
+      Prof pr(ctx, PK_SWEEP_RECT, fl, by);
+      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.kt_off), sl.nkt, sl.mbig, out, s);
+    }
+    tri_work(sl, transpose, &fl, &by);
     Prof pr(ctx, transpose ? PK_SWEEP_LT : PK_SWEEP_U, fl, by);
-    launch_sweep<T>(sa, bwd, ctx->d_lists + sl.off, sl.nf, sl.nmax, sl.kmax, in, out, s);
+    launch_sweep_tri<T>(sa, bwd, dl + sl.off, sl.nf, sl.nmax, in, out, s);
   }
   CK(cudaGetLastError());
   ctx->sweeps += 1;
@@ -768,9 +820,11 @@ fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev) {
   if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_refactor_design before fdfd_factor");
   if (ctx->box.w == 0) return fail(ctx, FDFD_ERR_STATE, "context has no design box");
   CKS(ensure_runtime(ctx));
-  Prof pr_s(ctx, PK_OTHER, 0, 16.0 * ctx->box.w * ctx->box.h);
-  launch_scatter_design(ctx->d_eps, eps_design_dev, ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w, ctx->box.h,
-                        ctx->stream);
+  {
+    Prof pr_s(ctx, PK_OTHER, 0, 16.0 * ctx->box.w * ctx->box.h);
+    launch_scatter_design(ctx->d_eps, eps_design_dev, ctx->ny, ctx->box.x0, ctx->box.y0, ctx->box.w,
+                          ctx->box.h, ctx->stream);
+  }
   CK(cudaGetLastError());
   if (ctx->opt.mode == FDFD_MODE_PLAIN) return FDFD_OK;
   CKS(ensure_device(ctx));

@@ -60,8 +60,15 @@ struct SolveLaunch {
 // sweep: 0 = L (forward, non-transposed), 1 = U (backward, non-transposed),
 //        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
 // in: right-hand side (sweeps 0, 2) [n_sys][n]; out: solution (sweeps 1, 3) [n_sys][n].
-template <typename T> void launch_sweep(const SolveLaunch& a, int sweep, const int* flist, int nf,
-                                        int nmax, int kmax, const void* in, void* out, cudaStream_t s);
+// Triangular part, one CTA per listed front (bit 31 of an entry marks a front
+// whose off-diagonal block is left to launch_sweep_rect).  nmax: largest front.
+template <typename T> void launch_sweep_tri(const SolveLaunch& a, int sweep, const int* flist, int nf,
+                                            int nmax, const void* in, void* out, cudaStream_t s);
+// Off-diagonal block of large fronts, tasks = (front, first row/column), blocks
+// of sweep_rect_block(); vmax: largest vector the tasks multiply (k or m).
+template <typename T> void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,
+                                             int vmax, void* out, cudaStream_t s);
+int sweep_rect_block();
 
 // ---- vec.cu: FP64 refinement, objective, gradient ---------------------------
 // y = A x (op = 0) or r = b - A x (op = 1), FP64 matrix-free stencil, all systems.

@@ -11,18 +11,25 @@
 // where v gathers the front's entries of the right-hand side plus the update
 // vectors u of its children (through the same inverse extend-add maps as the
 // factorisation), and x_m are the already final values of the boundary
-// variables.  Levels run bottom-up for L / U^T and top-down for U / L^T.  Each
-// CTA owns one front of one system; every read of the factor is coalesced
-// along a row of the row-major front, and each factor entry is read once per
-// right-hand side.
+// variables.  Levels run bottom-up for L / U^T and top-down for U / L^T.
+//
+// Work split per level: a triangular kernel (one CTA per front and system)
+// does the gather and the dense triangular solve; for large fronts the
+// rectangular products (L21 y, U12 x_m, U12^T w, L21^T x_m) are split over
+// many CTAs of a second kernel, 32 rows or 32 columns each, so that the big
+// fronts at the top of the tree stream their factor with the whole GPU.
+// Every factor read is coalesced along a row of the row-major front and each
+// factor entry is read once per right-hand side; reductions run in a fixed
+// order (deterministic results).
 #include "kernels.h"
 
 namespace fdfd {
 
 namespace {
 
-constexpr int kSolveThreads = 256;
-constexpr int kWarps = kSolveThreads / 32;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRect = 32;           // rows (or columns) per rectangular task
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -40,8 +47,21 @@ __device__ __forceinline__ T shfl(T v, int src) {
   return v;
 }
 
-// v[a] for a < n: rhs entry (pivot rows only) plus the children's update vectors.
-// src maps the front-local slot to the local row whose value it receives.
+// sum_{c in [c0, c1)} row[c] * vec[c], lanes striding the row (coalesced), warp-reduced
+template <typename T>
+__device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, int c0, int c1, int lane) {
+  T a0 = czero<T>(), a1 = czero<T>();
+  int c = c0 + lane;
+  for (; c + 32 < c1; c += 64) {
+    const T r0 = row[c], r1 = row[c + 32];
+    a0 = cfma(r0, vec[c], a0);
+    a1 = cfma(r1, vec[c + 32], a1);
+  }
+  if (c < c1) a0 = cfma(row[c], vec[c], a0);
+  return warp_sum(cadd(a0, a1));
+}
+
+// v[s] for s < n: rhs entry (pivot rows only) plus the children's update vectors.
 template <typename T>
 __device__ __forceinline__ void gather_front(const SolveLaunch& a, const FrontDesc& d, const T* rhs,
                                              const T* vbs, const int* Pm, bool permute, T* vs) {
@@ -58,13 +78,21 @@ __device__ __forceinline__ void gather_front(const SolveLaunch& a, const FrontDe
   }
 }
 
+// ---------------------------------------------------------------------------
+// Triangular part (and, for small fronts, the whole front).
+// list entries: front id, with bit 31 set when a rectangular task list covers
+// the front's off-diagonal block.
+// ---------------------------------------------------------------------------
 template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kSolveThreads)
-sweep_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ in, T* __restrict__ out) {
+__global__ void __launch_bounds__(kThreads)
+tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ in, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T Ds[32][33];
   T* vs = reinterpret_cast<T*>(smem_raw);
   const int w = blockIdx.y + a.w0;
-  const int f = flist[blockIdx.x];
+  const int entry = flist[blockIdx.x];
+  const bool big = entry < 0;
+  const int f = entry & 0x7fffffff;
   const FrontDesc d = a.P.fronts[f];
   const int n = d.n, k = d.k, m = d.m, ld = d.ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -74,78 +102,82 @@ sweep_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
+    T* vf = vbs + d.v_off;
     if (SWEEP == 0) {
-      // ---- L: forward substitution on P v, then the L21 update ----------------
+      // ---- L: y = L11^-1 (P v)_k; small fronts also u = v_m - L21 y ---------------
       gather_front(a, d, in + sys * a.n, vbs, Pm, true, vs);
       __syncthreads();
       for (int kb = 0; kb < k; kb += 32) {
         const int bs = min(32, k - kb);
+        for (int e = tid; e < bs * 32; e += kThreads) {
+          const int i = e >> 5, j = e & 31;
+          if (j < bs) Ds[i][j] = F[(size_t)(kb + i) * ld + kb + j];
+        }
         for (int rr = warp; rr < bs; rr += kWarps) {
-          const int row = kb + rr;
-          T acc = czero<T>();
-          for (int c = lane; c < kb; c += 32) acc = cfma(F[(size_t)row * ld + c], vs[c], acc);
-          acc = warp_sum(acc);
-          if (lane == 0) vs[row] = csub(vs[row], acc);
+          const T acc = warp_dot(F + (size_t)(kb + rr) * ld, vs, 0, kb, lane);
+          if (lane == 0) vs[kb + rr] = csub(vs[kb + rr], acc);
         }
         __syncthreads();
         if (warp == 0) {
           T yi = lane < bs ? vs[kb + lane] : czero<T>();
           for (int jj = 0; jj < bs - 1; ++jj) {
             const T yj = shfl(yi, jj);
-            if (lane > jj && lane < bs) yi = cfms(F[(size_t)(kb + lane) * ld + kb + jj], yj, yi);
+            if (lane > jj && lane < bs) yi = cfms(Ds[lane][jj], yj, yi);
           }
           if (lane < bs) vs[kb + lane] = yi;
         }
         __syncthreads();
       }
-      for (int t = warp; t < m; t += kWarps) {
-        const int row = k + t;
-        T acc = czero<T>();
-        for (int c = lane; c < k; c += 32) acc = cfma(F[(size_t)row * ld + c], vs[c], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) vs[row] = csub(vs[row], acc);
+      if (!big) {
+        for (int t = warp; t < m; t += kWarps) {
+          const T acc = warp_dot(F + (size_t)(k + t) * ld, vs, 0, k, lane);
+          if (lane == 0) vs[k + t] = csub(vs[k + t], acc);
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      for (int s = tid; s < n; s += blockDim.x) vbs[d.v_off + s] = vs[s];
+      for (int s = tid; s < n; s += kThreads) vf[s] = vs[s];
     } else if (SWEEP == 1) {
-      // ---- U: x_k = U11^-1 (y - U12 x_m) ------------------------------------
+      // ---- U: x_k = U11^-1 (y - U12 x_m); big fronts had U12 x_m subtracted --------
       T* xo = out + sys * a.n;
-      for (int s = tid; s < k; s += blockDim.x) vs[s] = vbs[d.v_off + s];
-      for (int t = tid; t < m; t += blockDim.x) vs[k + t] = xo[idx[k + t]];
+      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
+      if (!big)
+        for (int t = tid; t < m; t += kThreads) vs[k + t] = xo[idx[k + t]];
       __syncthreads();
-      for (int row = warp; row < k; row += kWarps) {
-        T acc = czero<T>();
-        for (int t = lane; t < m; t += 32) acc = cfma(F[(size_t)row * ld + k + t], vs[k + t], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) vs[row] = csub(vs[row], acc);
+      if (!big) {
+        for (int row = warp; row < k; row += kWarps) {
+          const T acc = warp_dot(F + (size_t)row * ld, vs, k, n, lane);
+          if (lane == 0) vs[row] = csub(vs[row], acc);
+        }
+        __syncthreads();
       }
-      __syncthreads();
       for (int kb = ((k - 1) / 32) * 32; kb >= 0; kb -= 32) {
         const int bs = min(32, k - kb);
+        for (int e = tid; e < bs * 32; e += kThreads) {
+          const int i = e >> 5, j = e & 31;
+          if (j < bs) Ds[i][j] = F[(size_t)(kb + i) * ld + kb + j];
+        }
         for (int rr = warp; rr < bs; rr += kWarps) {
-          const int row = kb + rr;
-          T acc = czero<T>();
-          for (int c = kb + bs + lane; c < k; c += 32) acc = cfma(F[(size_t)row * ld + c], vs[c], acc);
-          acc = warp_sum(acc);
-          if (lane == 0) vs[row] = csub(vs[row], acc);
+          const T acc = warp_dot(F + (size_t)(kb + rr) * ld, vs, kb + bs, k, lane);
+          if (lane == 0) vs[kb + rr] = csub(vs[kb + rr], acc);
         }
         __syncthreads();
         if (warp == 0) {
           T zi = lane < bs ? vs[kb + lane] : czero<T>();
           for (int jj = bs - 1; jj >= 0; --jj) {
-            if (lane == jj) zi = cmul(zi, crcp(F[(size_t)(kb + jj) * ld + kb + jj]));
+            if (lane == jj) zi = cmul(zi, crcp(Ds[jj][jj]));
             const T xj = shfl(zi, jj);
-            if (lane < jj) zi = cfms(F[(size_t)(kb + lane) * ld + kb + jj], xj, zi);
+            if (lane < jj) zi = cfms(Ds[lane][jj], xj, zi);
           }
           if (lane < bs) vs[kb + lane] = zi;
         }
         __syncthreads();
       }
-      for (int s = tid; s < k; s += blockDim.x) xo[idx[s]] = vs[s];
+      for (int s = tid; s < k; s += kThreads) xo[idx[s]] = vs[s];
     } else if (SWEEP == 2) {
-      // ---- U^T: w = U11^-T v_k, u = v_m - U12^T w ----------------------------
+      // ---- U^T: w = U11^-T v_k; small fronts also u = v_m - U12^T w ---------------
       gather_front(a, d, in + sys * a.n, vbs, Pm, false, vs);
       __syncthreads();
+      const int cend = big ? k : n;
       for (int kb = 0; kb < k; kb += 32) {
         const int bs = min(32, k - kb);
         if (warp == 0) {
@@ -158,26 +190,35 @@ sweep_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__
           if (lane < bs) vs[kb + lane] = wi;
         }
         __syncthreads();
-        for (int c = kb + bs + tid; c < n; c += blockDim.x) {
+        for (int c = kb + bs + tid; c < cend; c += kThreads) {
+          T a0 = vs[c], a1 = czero<T>();
+          int bb = 0;
+          for (; bb + 1 < bs; bb += 2) {
+            const T f0 = F[(size_t)(kb + bb) * ld + c], f1 = F[(size_t)(kb + bb + 1) * ld + c];
+            a0 = cfms(f0, vs[kb + bb], a0);
+            a1 = cfms(f1, vs[kb + bb + 1], a1);
+          }
+          if (bb < bs) a0 = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], a0);
+          vs[c] = cadd(a0, a1);
+        }
+        __syncthreads();
+      }
+      for (int s = tid; s < n; s += kThreads) vf[s] = vs[s];
+    } else {
+      // ---- L^T: x_k = P^T L11^-T (w - L21^T x_m); big fronts had L21^T x_m subtracted --
+      T* xo = out + sys * a.n;
+      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
+      if (!big)
+        for (int t = tid; t < m; t += kThreads) vs[k + t] = xo[idx[k + t]];
+      __syncthreads();
+      if (!big) {
+        for (int c = tid; c < k; c += kThreads) {
           T acc = vs[c];
-          for (int bb = 0; bb < bs; ++bb) acc = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], acc);
+          for (int t = 0; t < m; ++t) acc = cfms(F[(size_t)(k + t) * ld + c], vs[k + t], acc);
           vs[c] = acc;
         }
         __syncthreads();
       }
-      for (int s = tid; s < n; s += blockDim.x) vbs[d.v_off + s] = vs[s];
-    } else {
-      // ---- L^T: x_k = P^T L11^-T (w - L21^T x_m) ------------------------------
-      T* xo = out + sys * a.n;
-      for (int s = tid; s < k; s += blockDim.x) vs[s] = vbs[d.v_off + s];
-      for (int t = tid; t < m; t += blockDim.x) vs[k + t] = xo[idx[k + t]];
-      __syncthreads();
-      for (int c = tid; c < k; c += blockDim.x) {
-        T acc = vs[c];
-        for (int t = 0; t < m; ++t) acc = cfms(F[(size_t)(k + t) * ld + c], vs[k + t], acc);
-        vs[c] = acc;
-      }
-      __syncthreads();
       for (int kb = ((k - 1) / 32) * 32; kb >= 0; kb -= 32) {
         const int bs = min(32, k - kb);
         if (warp == 0) {
@@ -189,15 +230,95 @@ sweep_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__
           if (lane < bs) vs[kb + lane] = qi;
         }
         __syncthreads();
-        for (int c = tid; c < kb; c += blockDim.x) {
-          T acc = vs[c];
-          for (int bb = 0; bb < bs; ++bb) acc = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], acc);
-          vs[c] = acc;
+        for (int c = tid; c < kb; c += kThreads) {
+          T a0 = vs[c], a1 = czero<T>();
+          int bb = 0;
+          for (; bb + 1 < bs; bb += 2) {
+            const T f0 = F[(size_t)(kb + bb) * ld + c], f1 = F[(size_t)(kb + bb + 1) * ld + c];
+            a0 = cfms(f0, vs[kb + bb], a0);
+            a1 = cfms(f1, vs[kb + bb + 1], a1);
+          }
+          if (bb < bs) a0 = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], a0);
+          vs[c] = cadd(a0, a1);
         }
         __syncthreads();
       }
-      for (int s = tid; s < k; s += blockDim.x) xo[idx[Pm[s]]] = vs[s];
+      for (int s = tid; s < k; s += kThreads) xo[idx[Pm[s]]] = vs[s];
     }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rectangular part of large fronts; task = (front, first row or column).
+//   SWEEP 0: rows t of L21:   u[t]  = v[k+t] - L21[t,:] y        (y = vf[0..k))
+//   SWEEP 1: rows a of U12:   z[a]  = y[a]   - U12[a,:] x_m      (x_m gathered from out)
+//   SWEEP 2: cols t of U12:   u[t]  = v[k+t] - U12[:,t]^T w      (w = vf[0..k))
+//   SWEEP 3: cols a of L21:   q[a]  = w[a]   - L21[:,a]^T x_m
+// ---------------------------------------------------------------------------
+template <typename T, int SWEEP>
+__global__ void __launch_bounds__(kThreads)
+rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[kWarps][32];
+  T* vs = reinterpret_cast<T*>(smem_raw);
+  const int w = blockIdx.y + a.w0;
+  const int2 task = tasks[blockIdx.x];
+  const FrontDesc d = a.P.fronts[task.x];
+  const int k = d.k, m = d.m, n = d.n, ld = d.ld;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int* idx = a.P.idx + d.idx_off;
+  const int s0 = task.y;
+  for (int r = a.r0; r < a.r0 + a.nr; ++r) {
+    const size_t sys = (size_t)w * a.nrhs + r;
+    T* vf = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride + d.v_off;
+    const T* xo = out + sys * a.n;
+    // the vector the block multiplies: y / w (forward) or x_m (backward)
+    if (SWEEP == 0 || SWEEP == 2) {
+      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
+    } else {
+      for (int t = tid; t < m; t += kThreads) vs[t] = xo[idx[k + t]];
+    }
+    __syncthreads();
+    if (SWEEP == 0 || SWEEP == 1) {
+      const int rows = SWEEP == 0 ? m : k;
+      for (int rr = warp; rr < kRect; rr += kWarps) {
+        const int row = s0 + rr;
+        if (row >= rows) break;
+        const T* Frow = SWEEP == 0 ? F + (size_t)(k + row) * ld : F + (size_t)row * ld + k;
+        const T acc = warp_dot(Frow, vs, 0, SWEEP == 0 ? k : m, lane);
+        if (lane == 0) {
+          const int slot = SWEEP == 0 ? k + row : row;
+          vf[slot] = csub(vf[slot], acc);
+        }
+      }
+    } else {
+      // column block: lane = column, warps split the rows, fixed-order reduction
+      const int cols = SWEEP == 2 ? m : k;
+      const int rows = SWEEP == 2 ? k : m;
+      const int c = s0 + lane;
+      T a0 = czero<T>(), a1 = czero<T>();
+      if (c < cols) {
+        const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
+        int i = warp;
+        for (; i + kWarps < rows; i += 2 * kWarps) {
+          const T f0 = base[(size_t)i * ld], f1 = base[(size_t)(i + kWarps) * ld];
+          a0 = cfma(f0, vs[i], a0);
+          a1 = cfma(f1, vs[i + kWarps], a1);
+        }
+        if (i < rows) a0 = cfma(base[(size_t)i * ld], vs[i], a0);
+      }
+      red[warp][lane] = cadd(a0, a1);
+      __syncthreads();
+      if (warp == 0 && c < cols) {
+        T s = red[0][lane];
+        for (int q = 1; q < kWarps; ++q) s = cadd(s, red[q][lane]);
+        const int slot = SWEEP == 2 ? k + c : c;
+        vf[slot] = csub(vf[slot], s);
+      }
+    }
+    (void)n;
     __syncthreads();
   }
 }
@@ -205,37 +326,58 @@ sweep_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__
 }  // namespace
 
 template <typename T>
-void launch_sweep(const SolveLaunch& a, int sweep, const int* flist, int nf, int nmax, int kmax,
-                  const void* in, void* out, cudaStream_t s) {
-  (void)kmax;
+void launch_sweep_tri(const SolveLaunch& a, int sweep, const int* flist, int nf, int nmax, const void* in,
+                      void* out, cudaStream_t s) {
   if (nf <= 0) return;
   const size_t smem = (size_t)nmax * sizeof(T);
   const T* i = reinterpret_cast<const T*>(in);
   T* o = reinterpret_cast<T*>(out);
   dim3 grid(nf, a.n_omega);
   switch (sweep) {
-    case 0: sweep_kernel<T, 0><<<grid, kSolveThreads, smem, s>>>(a, flist, i, o); break;
-    case 1: sweep_kernel<T, 1><<<grid, kSolveThreads, smem, s>>>(a, flist, i, o); break;
-    case 2: sweep_kernel<T, 2><<<grid, kSolveThreads, smem, s>>>(a, flist, i, o); break;
-    default: sweep_kernel<T, 3><<<grid, kSolveThreads, smem, s>>>(a, flist, i, o); break;
+    case 0: tri_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
+    case 1: tri_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
+    case 2: tri_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
+    default: tri_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
   }
 }
+
+template <typename T>
+void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks, int vmax, void* out,
+                       cudaStream_t s) {
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)vmax * sizeof(T);
+  T* o = reinterpret_cast<T*>(out);
+  dim3 grid(ntasks, a.n_omega);
+  switch (sweep) {
+    case 0: rect_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
+    case 1: rect_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
+    case 2: rect_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
+    default: rect_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
+  }
+}
+
+int sweep_rect_block() { return kRect; }
 
 cudaError_t solve_init_attributes() {
   const int lim = 160 * 1024;
   cudaError_t e = cudaSuccess;
-#define FDFD_ATTR(T, S)                                                                          \
-  if (e == cudaSuccess)                                                                          \
-    e = cudaFuncSetAttribute(sweep_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  FDFD_ATTR(float2, 0) FDFD_ATTR(float2, 1) FDFD_ATTR(float2, 2) FDFD_ATTR(float2, 3)
-  FDFD_ATTR(double2, 0) FDFD_ATTR(double2, 1) FDFD_ATTR(double2, 2) FDFD_ATTR(double2, 3)
+#define FDFD_ATTR(K, T, S)                                                                       \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  FDFD_ATTR(tri_kernel, float2, 0) FDFD_ATTR(tri_kernel, float2, 1) FDFD_ATTR(tri_kernel, float2, 2)
+  FDFD_ATTR(tri_kernel, float2, 3) FDFD_ATTR(tri_kernel, double2, 0) FDFD_ATTR(tri_kernel, double2, 1)
+  FDFD_ATTR(tri_kernel, double2, 2) FDFD_ATTR(tri_kernel, double2, 3)
+  FDFD_ATTR(rect_kernel, float2, 0) FDFD_ATTR(rect_kernel, float2, 1) FDFD_ATTR(rect_kernel, float2, 2)
+  FDFD_ATTR(rect_kernel, float2, 3) FDFD_ATTR(rect_kernel, double2, 0) FDFD_ATTR(rect_kernel, double2, 1)
+  FDFD_ATTR(rect_kernel, double2, 2) FDFD_ATTR(rect_kernel, double2, 3)
 #undef FDFD_ATTR
   return e;
 }
 
-template void launch_sweep<float2>(const SolveLaunch&, int, const int*, int, int, int, const void*,
-                                   void*, cudaStream_t);
-template void launch_sweep<double2>(const SolveLaunch&, int, const int*, int, int, int, const void*,
-                                    void*, cudaStream_t);
+template void launch_sweep_tri<float2>(const SolveLaunch&, int, const int*, int, int, const void*, void*,
+                                       cudaStream_t);
+template void launch_sweep_tri<double2>(const SolveLaunch&, int, const int*, int, int, const void*, void*,
+                                        cudaStream_t);
+template void launch_sweep_rect<float2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
+template void launch_sweep_rect<double2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
 
 }  // namespace fdfd
