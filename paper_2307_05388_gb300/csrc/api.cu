@@ -25,7 +25,7 @@ namespace {
 struct LevelList {
   int task_off = 0, ntasks = 0;      // build tasks (int2) offset / count
   int small_off = 0, nsmall = 0, nmax_small = 0;
-  int large_off = 0, nlarge = 0, nmax_large = 0, kmax_large = 0;
+  int large_off = 0, nlarge = 0, nmax_large = 0, kmax_large = 0, mmax_large = 0;
 };
 
 struct SolveList {
@@ -278,6 +278,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
             lists.push_back(f); ll.nlarge++;
             ll.nmax_large = std::max(ll.nmax_large, p.fronts[f].n);
             ll.kmax_large = std::max(ll.kmax_large, p.fronts[f].k);
+            ll.mmax_large = std::max(ll.mmax_large, p.fronts[f].m);
           }
         if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
       }
@@ -432,21 +433,30 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
     }
     for (int j0 = 0; j0 < ll.kmax_large; j0 += nb) {
       const int* fl = ctx->d_lists + ll.large_off;
-      double pf = 0, pb = 0, tf = 0, tb = 0, gf = 0, gb = 0;
+      double pf = 0, pb = 0, lf = 0, lb = 0, tf = 0, tb = 0, gf = 0, gb = 0;
       if (ctx->prof_on)
         for (int t = 0; t < ll.nlarge; ++t) {
           const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
           if (j0 >= d.k) continue;
           const int b = std::min(nb, d.k - j0);
-          for (int j = j0; j < j0 + b; ++j) pf += 8.0 * (double)(d.n - j - 1) * (j0 + b - j);
-          pb += 2.0 * es * (double)(d.n - j0) * b;
+          for (int j = j0; j < j0 + b; ++j) pf += 8.0 * (double)(d.k - j - 1) * (j0 + b - j);
+          pb += 2.0 * es * (double)(d.k - j0) * b;
+          lf += 8.0 * 0.5 * b * (b + 1.0) * d.m;
+          lb += 2.0 * es * b * (double)d.m;
           const double rem = d.n - j0 - b;
           tf += 8.0 * 0.5 * b * (b - 1) * rem;
           tb += 2.0 * es * b * rem;
           gf += 8.0 * b * rem * rem;
           gb += es * (2.0 * rem * rem + 2.0 * rem * b);
         }
-      { Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd); launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, s); }
+      {
+        Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd);
+        launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
+      }
+      if (ll.mmax_large > 0) {
+        Prof pr(ctx, PK_LU_TRSM, lf * nwd, lb * nwd);
+        launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, s);
+      }
       { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
     }

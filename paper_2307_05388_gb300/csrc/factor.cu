@@ -237,7 +237,7 @@ lu_panel_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax
     const T pv = F[(size_t)j * ld + j];
     const T inv = crcp(pv);
     if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
-    for (int r = j + 1 + tid; r < n; r += blockDim.x) {
+    for (int r = j + 1 + tid; r < k; r += blockDim.x) {
       const T l = cmul(F[(size_t)r * ld + j], inv);
       F[(size_t)r * ld + j] = l;
       gmax = nanmax(gmax, cabs2(l));
@@ -245,8 +245,8 @@ lu_panel_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax
     __syncthreads();
     const int cols = j0 + nb - (j + 1);
     if (cols > 0) {
-      // rank-1 update of the panel columns (j, j0+nb): thread -> (row, col)
-      for (long long e = tid; e < (long long)(n - j - 1) * cols; e += blockDim.x) {
+      // rank-1 update of the panel columns (j, j0+nb), pivot rows only: thread -> (row, col)
+      for (long long e = tid; e < (long long)(k - j - 1) * cols; e += blockDim.x) {
         const int r = j + 1 + (int)(e / cols), c = j + 1 + (int)(e % cols);
         F[(size_t)r * ld + c] = cfms(F[(size_t)r * ld + j], F[(size_t)j * ld + c], F[(size_t)r * ld + c]);
       }
@@ -267,6 +267,165 @@ lu_panel_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax
 
 constexpr int kTrsmCols = 128;
 constexpr int kMaxNb = 32;
+
+// Panel of the k - j0 pivot-candidate rows staged in shared memory (one CTA
+// per front).  Per column: block argmax, swap of the two panel rows, then one
+// warp per row scales and updates the row (lane = column).  The row swaps are
+// applied to the columns outside the panel afterwards, in order.
+constexpr int kPanelSmemThreads = 256;
+constexpr int kPanelSmemBytes = 200 * 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kPanelSmemThreads)
+lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  using R = typename RealOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ps = reinterpret_cast<T*>(smem_raw);
+  constexpr int NW = kPanelSmemThreads / 32;
+  __shared__ R s_v[NW];
+  __shared__ int s_i[NW];
+  __shared__ int s_swap[kMaxNb];
+  const int w = blockIdx.y + a.w0;
+  const int f = flist[blockIdx.x];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int n = d.n, k = d.k, ld = d.ld;
+  const int R_ = k - j0, ldp = nb + 1;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (j0 == 0)
+    for (int i = tid; i < k; i += kPanelSmemThreads) P[i] = i;
+  for (int e = tid; e < R_ * nb; e += kPanelSmemThreads) {
+    const int r = e / nb, c = e - r * nb;
+    Ps[r * ldp + c] = F[(size_t)(j0 + r) * ld + j0 + c];
+  }
+  __syncthreads();
+  R gmax = 0;
+  for (int jj = 0; jj < nb; ++jj) {
+    R best = -1;
+    int bi = jj;
+    for (int r = jj + tid; r < R_; r += kPanelSmemThreads) {
+      const R v = cabs2(Ps[r * ldp + jj]);
+      if (v > best) { best = v; bi = r; }
+    }
+    warp_argmax(best, bi);
+    if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
+    __syncthreads();
+    R bv = s_v[0];
+    int piv = s_i[0];
+    for (int i = 1; i < NW; ++i)
+      if (s_v[i] > bv || (s_v[i] == bv && s_i[i] < piv)) { bv = s_v[i]; piv = s_i[i]; }
+    if (piv != jj && tid < nb) {
+      const T x = Ps[jj * ldp + tid];
+      Ps[jj * ldp + tid] = Ps[piv * ldp + tid];
+      Ps[piv * ldp + tid] = x;
+    }
+    if (tid == 0) s_swap[jj] = piv;
+    __syncthreads();
+    const T pv = Ps[jj * ldp + jj];
+    const T inv = crcp(pv);
+    if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
+    const T urow = lane < nb ? Ps[jj * ldp + lane] : czero<T>();
+    for (int r = jj + 1 + warp; r < R_; r += NW) {
+      const T l = cmul(Ps[r * ldp + jj], inv);
+      __syncwarp();                       // every lane has read the column entry before lane jj overwrites it
+      if (lane == jj) Ps[r * ldp + jj] = l;
+      else if (lane > jj && lane < nb) Ps[r * ldp + lane] = cfms(l, urow, Ps[r * ldp + lane]);
+      if (lane == 0) gmax = nanmax(gmax, cabs2(l));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < R_ * nb; e += kPanelSmemThreads) {
+    const int r = e / nb, c = e - r * nb;
+    F[(size_t)(j0 + r) * ld + j0 + c] = Ps[r * ldp + c];
+  }
+  // swaps on the columns outside the panel: each thread owns whole columns
+  for (int c = tid; c < n; c += kPanelSmemThreads) {
+    if (c >= j0 && c < j0 + nb) continue;
+    for (int jj = 0; jj < nb; ++jj) {
+      const int piv = s_swap[jj];
+      if (piv == jj) continue;
+      T* a0 = F + (size_t)(j0 + jj) * ld + c;
+      T* a1 = F + (size_t)(j0 + piv) * ld + c;
+      const T x = *a0;
+      *a0 = *a1;
+      *a1 = x;
+    }
+  }
+  if (tid == 0)
+    for (int jj = 0; jj < nb; ++jj) {
+      const int piv = s_swap[jj];
+      if (piv != jj) { const int x = P[j0 + jj]; P[j0 + jj] = P[j0 + piv]; P[j0 + piv] = x; }
+    }
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) s_v[warp] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    R g = 0;
+    for (int i = 0; i < NW; ++i) g = nanmax(g, s_v[i]);
+    float* gp = a.growth + (size_t)w * a.n_fronts + f;
+    const float gv = (float)sqrt((double)g);
+    *gp = (j0 == 0) ? gv : nanmax(*gp, gv);
+  }
+}
+
+// Boundary rows of the panel: L21[:, j0:j0+nb] = A21[:, j0:j0+nb] U_jj^-1 (right
+// triangular solve with the panel's upper block), 64 rows per CTA.
+constexpr int kL21Rows = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  using R = typename RealOf<T>::type;
+  __shared__ T Us[kMaxNb][kMaxNb + 1];
+  __shared__ T Xs[kL21Rows][kMaxNb + 1];
+  __shared__ R s_g[8];
+  const int w = blockIdx.z + a.w0;
+  const int f = flist[blockIdx.y];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int r0 = d.k + blockIdx.x * kL21Rows;
+  if (r0 >= d.n) return;
+  const int rows = min(kL21Rows, d.n - r0);
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nb * nb; e += 256) {
+    const int i = e / nb, c = e - i * nb;
+    Us[i][c] = F[(size_t)(j0 + i) * d.ld + j0 + c];
+  }
+  for (int e = tid; e < rows * nb; e += 256) {
+    const int i = e / nb, c = e - i * nb;
+    Xs[i][c] = F[(size_t)(r0 + i) * d.ld + j0 + c];
+  }
+  __syncthreads();
+  R gmax = 0;
+  if (tid < rows) {
+    for (int j = 0; j < nb; ++j) {
+      T x = Xs[tid][j];
+      for (int l = 0; l < j; ++l) x = cfms(Xs[tid][l], Us[l][j], x);
+      x = cmul(x, crcp(Us[j][j]));
+      Xs[tid][j] = x;
+      gmax = nanmax(gmax, cabs2(x));
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * nb; e += 256) {
+    const int i = e / nb, c = e - i * nb;
+    F[(size_t)(r0 + i) * d.ld + j0 + c] = Xs[i][c];
+  }
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if ((tid & 31) == 0) s_g[tid >> 5] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    R g = 0;
+    for (int i = 0; i < 8; ++i) g = nanmax(g, s_g[i]);
+    // max of non-negative floats (NaN included) is order independent as an int max
+    atomicMax(reinterpret_cast<int*>(a.growth + (size_t)w * a.n_fronts + f), __float_as_int((float)sqrt((double)g)));
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kTrsmCols)
@@ -405,8 +564,13 @@ cudaError_t factor_init_attributes() {
   cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 96 * 8);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              64 * 64 * 16);
+  e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_panel_smem_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kPanelSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(lu_panel_smem_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kPanelSmemBytes);
 }
 int lu_panel_width(int elem_bytes) { (void)elem_bytes; return kMaxNb; }
 
@@ -424,9 +588,19 @@ void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, 
 }
 
 template <typename T>
-void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, cudaStream_t s) {
-  if (nf <= 0) return;
-  lu_panel_kernel<T><<<dim3(nf, a.n_omega), kPanelThreads, 0, s>>>(a, flist, j0, nb);
+void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int kmax, cudaStream_t s) {
+  if (nf <= 0 || j0 >= kmax) return;
+  const size_t smem = (size_t)(kmax - j0) * (nb + 1) * sizeof(T);
+  if (smem <= (size_t)kPanelSmemBytes)
+    lu_panel_smem_kernel<T><<<dim3(nf, a.n_omega), kPanelSmemThreads, smem, s>>>(a, flist, j0, nb);
+  else
+    lu_panel_kernel<T><<<dim3(nf, a.n_omega), kPanelThreads, 0, s>>>(a, flist, j0, nb);
+}
+
+template <typename T>
+void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int mmax, cudaStream_t s) {
+  if (nf <= 0 || mmax <= 0) return;
+  lu_l21_kernel<T><<<dim3((mmax + kL21Rows - 1) / kL21Rows, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb);
 }
 
 template <typename T>
@@ -450,7 +624,8 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
 #define FDFD_INST(T)                                                                              \
   template void launch_build<T>(const FactorLaunch&, const int2*, int, cudaStream_t);            \
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
-  template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, cudaStream_t); \
+  template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
+  template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t);
 FDFD_INST(float2)

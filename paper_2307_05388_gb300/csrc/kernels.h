@@ -33,9 +33,13 @@ template <typename T> void launch_build(const FactorLaunch& a, const int2* tasks
 // whole-front LU in shared memory, one CTA per front
 template <typename T> void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax,
                                            cudaStream_t s);
-// blocked right-looking LU of large fronts: one panel step at column j0
+// blocked right-looking LU of large fronts: one panel step at column j0.
+// panel: pivot-candidate rows [j0, k) of columns [j0, j0+nb) (kmax = largest k listed);
+// l21: boundary rows [k, n) of the panel (mmax = largest m listed).
 template <typename T> void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0,
-                                           int nb, cudaStream_t s);
+                                           int nb, int kmax, cudaStream_t s);
+template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                         int nb, int mmax, cudaStream_t s);
 template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
