@@ -91,7 +91,8 @@ struct fdfd_ctx {
   float* d_growth_max = nullptr;
   float* h_growth_max = nullptr;   // pinned
   bool valid32 = false, valid64 = false;
-  bool growth_pending = false;
+  bool growth_pending = false;     // growth of the last FP32 factorisation not yet checked
+  bool growth_ready = false;       // ... and its pinned copy has landed
 
   // solve workspace
   int ws_nrhs = 0;
@@ -119,6 +120,7 @@ struct fdfd_ctx {
   // counters
   long long sf = 0, nf = 0, bs = 0, sweeps = 0, fallbacks = 0;
   long long last_iters = 0;
+  long long gm_expect = 1;          // FGMRES iterations the previous solve needed
   double last_resid = 0;
   double last_growth = 0;
 };
@@ -624,6 +626,7 @@ fdfd_status any_active(fdfd_ctx* ctx, int S, bool* any, double* maxres) {
   CK(cudaMemcpyAsync(ctx->h_active, ctx->d_active, sizeof(int) * S, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_resid, ctx->d_resid, sizeof(double) * S, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->growth_pending) ctx->growth_ready = true;
   *any = false;
   *maxres = 0;
   for (int i = 0; i < S; ++i) {
@@ -665,9 +668,13 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
     gm_start(ctx->d_hn, D, ctx->d_bd, D, S, tol, m, ctx->d_g, ctx->d_vscale, ctx->d_active, ctx->d_resid,
              ctx->d_bnorm, cycle == 0 ? 1 : 0, s); }
     CK(cudaGetLastError());
-    bool any;
-    CKS(any_active(ctx, S, &any, &res));
-    if (!any) { converged = true; break; }
+    bool any = true;
+    // The first cycle starts from x = 0 (r = b), so nothing can have converged
+    // yet; later cycles start from the true FP64 residual and decide.
+    if (cycle > 0 || ctx->opt.ir_max_iter == 0) {
+      CKS(any_active(ctx, S, &any, &res));
+      if (!any) { converged = true; break; }
+    }
     if (total >= ctx->opt.ir_max_iter) break;
     { Prof pr(ctx, PK_OTHER, 0, 32.0 * N * S); gm_scale(ctx->d_V, ctx->d_r, ctx->d_vscale, N, S, s); }
     CK(cudaMemsetAsync(ctx->d_nj, 0, sizeof(int) * S, s));
@@ -701,8 +708,14 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
       CK(cudaGetLastError());
       ++total;
       jdone = j + 1;
-      CKS(any_active(ctx, S, &any, &res));
-      if (!any || total >= ctx->opt.ir_max_iter) break;
+      // The host looks at the convergence flags only once the iteration count
+      // reaches what the previous solve needed; meanwhile the device-side flags
+      // already freeze converged systems (zero search directions, no updates).
+      if (total >= ctx->gm_expect || j + 1 == m || total >= ctx->opt.ir_max_iter) {
+        CKS(any_active(ctx, S, &any, &res));
+        if (!any) break;
+      }
+      if (total >= ctx->opt.ir_max_iter) break;
       if (j + 1 < m) {
         Prof pr(ctx, PK_OTHER, 0, 32.0 * N * S);
         gm_scale(ctx->d_V + (size_t)(j + 1) * vs, ctx->d_w, ctx->d_vscale, N, S, s);
@@ -715,6 +728,7 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   }
   ctx->last_iters = total;
   ctx->last_resid = res;
+  ctx->gm_expect = std::max<long long>(1, total);
   if (!converged)
     return fail(ctx, FDFD_ERR_NOT_CONVERGED,
                 "refinement stopped at relative residual " + std::to_string(res) + " after " +
@@ -723,13 +737,18 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
 }
 
 // Checks the pivot growth of the last FP32 factorisation; refactors in FP64 if needed.
-fdfd_status settle_growth(fdfd_ctx* ctx) {
+// The growth figure is copied to pinned host memory at the end of the
+// factorisation; any later stream synchronisation makes it readable.
+fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr) {
+  if (fell_back) *fell_back = false;
   if (!ctx->growth_pending) return FDFD_OK;
-  CK(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->growth_ready) CK(cudaStreamSynchronize(ctx->stream));
   ctx->growth_pending = false;
+  ctx->growth_ready = false;
   const float g = *ctx->h_growth_max;
   ctx->last_growth = g;
   if (!(g <= ctx->opt.growth_bound)) {
+    if (fell_back) *fell_back = true;
     ctx->fallbacks += 1;
     CKS(factor_levels<double2>(ctx, false));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -879,7 +898,6 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
   }
   CKS(ensure_device(ctx));
   CKS(ensure_ws(ctx, nrhs));
-  CKS(settle_growth(ctx));
   ctx->bs += S;
   if (ctx->valid64 && (ctx->opt.mode == FDFD_MODE_F64)) {
     CKS(sweeps<double2>(ctx, nrhs, transpose, b, x));
@@ -888,10 +906,19 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
   }
   if (ctx->opt.ir_max_iter == 0) {
     // raw solve on the cached factors, no refinement
+    CKS(settle_growth(ctx));
     return precond(ctx, nrhs, transpose, b, x);
   }
   (void)N;
-  return fgmres(ctx, b, x, nrhs, transpose);
+  // Refinement first: its synchronisations make the growth figure of a fresh
+  // FP32 factorisation readable for free.  A front with too much growth sends
+  // the whole factorisation to FP64 and the solve is repeated on it.
+  const fdfd_status st = fgmres(ctx, b, x, nrhs, transpose);
+  if (st != FDFD_OK && st != FDFD_ERR_NOT_CONVERGED) return st;
+  bool fell_back = false;
+  CKS(settle_growth(ctx, &fell_back));
+  if (fell_back) return fgmres(ctx, b, x, nrhs, transpose);
+  return st;
 }
 
 fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev, const double* g_dev,

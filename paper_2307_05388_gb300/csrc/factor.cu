@@ -303,20 +303,25 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   }
   __syncthreads();
   R gmax = 0;
-  for (int jj = 0; jj < nb; ++jj) {
+  {  // argmax of the first panel column
     R best = -1;
-    int bi = jj;
-    for (int r = jj + tid; r < R_; r += kPanelSmemThreads) {
-      const R v = cabs2(Ps[r * ldp + jj]);
+    int bi = 0;
+    for (int r = tid; r < R_; r += kPanelSmemThreads) {
+      const R v = cabs2(Ps[r * ldp]);
       if (v > best) { best = v; bi = r; }
     }
     warp_argmax(best, bi);
     if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
     __syncthreads();
+  }
+  constexpr int U = 4;                    // rows in flight per warp
+  for (int jj = 0; jj < nb; ++jj) {
+    // pivot of column jj from the per-warp partial maxima (ties to the smaller row)
     R bv = s_v[0];
     int piv = s_i[0];
     for (int i = 1; i < NW; ++i)
       if (s_v[i] > bv || (s_v[i] == bv && s_i[i] < piv)) { bv = s_v[i]; piv = s_i[i]; }
+    if (piv < jj) piv = jj;                // every candidate row was empty
     if (piv != jj && tid < nb) {
       const T x = Ps[jj * ldp + tid];
       Ps[jj * ldp + tid] = Ps[piv * ldp + tid];
@@ -328,12 +333,40 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     const T inv = crcp(pv);
     if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
     const T urow = lane < nb ? Ps[jj * ldp + lane] : czero<T>();
-    for (int r = jj + 1 + warp; r < R_; r += NW) {
-      const T l = cmul(Ps[r * ldp + jj], inv);
-      __syncwarp();                       // every lane has read the column entry before lane jj overwrites it
-      if (lane == jj) Ps[r * ldp + jj] = l;
-      else if (lane > jj && lane < nb) Ps[r * ldp + lane] = cfms(l, urow, Ps[r * ldp + lane]);
-      if (lane == 0) gmax = nanmax(gmax, cabs2(l));
+    const int nx = jj + 1;                 // next column: its argmax is gathered on the way
+    R best = -1;
+    int bi = nx;
+    for (int r = jj + 1 + warp; r < R_; r += U * NW) {
+      T l[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ru = r + u * NW;
+        l[u] = ru < R_ ? cmul(Ps[ru * ldp + jj], inv) : czero<T>();
+      }
+      __syncwarp();                        // every lane has read its column entries before lane jj overwrites them
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ru = r + u * NW;
+        if (ru >= R_) break;
+        if (lane == jj) {
+          Ps[ru * ldp + jj] = l[u];
+        } else if (lane > jj && lane < nb) {
+          const T nv = cfms(l[u], urow, Ps[ru * ldp + lane]);
+          Ps[ru * ldp + lane] = nv;
+          if (lane == nx) {
+            const R v = cabs2(nv);
+            if (v > best) { best = v; bi = ru; }
+          }
+        }
+        if (lane == 0) gmax = nanmax(gmax, cabs2(l[u]));
+      }
+    }
+    if (nx < nb) {
+      // lane nx holds this warp's partial maximum of the next column (rows in
+      // increasing order per warp, so ties keep the smaller row)
+      const R wb = __shfl_sync(0xffffffffu, best, nx);
+      const int wi = __shfl_sync(0xffffffffu, bi, nx);
+      if (lane == 0) { s_v[warp] = wb; s_i[warp] = wi; }
     }
     __syncthreads();
   }

@@ -163,8 +163,9 @@ tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ i
         __syncthreads();
         if (warp == 0) {
           T zi = lane < bs ? vs[kb + lane] : czero<T>();
+          const T dj = lane < bs ? crcp(Ds[lane][lane]) : czero<T>();
           for (int jj = bs - 1; jj >= 0; --jj) {
-            if (lane == jj) zi = cmul(zi, crcp(Ds[jj][jj]));
+            if (lane == jj) zi = cmul(zi, dj);
             const T xj = shfl(zi, jj);
             if (lane < jj) zi = cfms(Ds[lane][jj], xj, zi);
           }
@@ -181,13 +182,20 @@ tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ i
       for (int kb = 0; kb < k; kb += 32) {
         const int bs = min(32, k - kb);
         if (warp == 0) {
+          // stage the diagonal block (row by row, coalesced) so the dependent chain
+          // below touches only shared memory and registers
+          for (int i = 0; i < bs; ++i)
+            if (lane < bs) Ds[i][lane] = F[(size_t)(kb + i) * ld + kb + lane];
+          __syncwarp();
+          const T dj = lane < bs ? crcp(Ds[lane][lane]) : czero<T>();
           T wi = lane < bs ? vs[kb + lane] : czero<T>();
           for (int bb = 0; bb < bs; ++bb) {
-            if (lane == bb) wi = cmul(wi, crcp(F[(size_t)(kb + bb) * ld + kb + bb]));
+            if (lane == bb) wi = cmul(wi, dj);
             const T wb = shfl(wi, bb);
-            if (lane > bb && lane < bs) wi = cfms(F[(size_t)(kb + bb) * ld + kb + lane], wb, wi);
+            if (lane > bb && lane < bs) wi = cfms(Ds[bb][lane], wb, wi);
           }
           if (lane < bs) vs[kb + lane] = wi;
+          __syncwarp();
         }
         __syncthreads();
         for (int c = kb + bs + tid; c < cend; c += kThreads) {
@@ -222,12 +230,16 @@ tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ i
       for (int kb = ((k - 1) / 32) * 32; kb >= 0; kb -= 32) {
         const int bs = min(32, k - kb);
         if (warp == 0) {
+          for (int i = 0; i < bs; ++i)
+            if (lane < bs) Ds[i][lane] = F[(size_t)(kb + i) * ld + kb + lane];
+          __syncwarp();
           T qi = lane < bs ? vs[kb + lane] : czero<T>();
           for (int bb = bs - 1; bb > 0; --bb) {
             const T qb = shfl(qi, bb);
-            if (lane < bb) qi = cfms(F[(size_t)(kb + bb) * ld + kb + lane], qb, qi);
+            if (lane < bb) qi = cfms(Ds[bb][lane], qb, qi);
           }
           if (lane < bs) vs[kb + lane] = qi;
+          __syncwarp();
         }
         __syncthreads();
         for (int c = tid; c < kb; c += kThreads) {
