@@ -673,7 +673,7 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
     // yet; later cycles start from the true FP64 residual and decide.
     if (cycle > 0 || ctx->opt.ir_max_iter == 0) {
       CKS(any_active(ctx, S, &any, &res));
-      if (!any) { converged = true; break; }
+      if (!any) { converged = res <= tol; break; }   // a NaN residual is never converged
     }
     if (total >= ctx->opt.ir_max_iter) break;
     { Prof pr(ctx, PK_OTHER, 0, 32.0 * N * S); gm_scale(ctx->d_V, ctx->d_r, ctx->d_vscale, N, S, s); }
