@@ -89,6 +89,8 @@ struct fdfd_ctx {
   int* d_perm64 = nullptr;
   float* d_growth = nullptr;
   float* d_growth_max = nullptr;
+  int* d_swp = nullptr;            // panel row-swap scratch
+  int max_nlarge = 0;              // longest large-front list of any level
   float* h_growth_max = nullptr;   // pinned
   bool valid32 = false, valid64 = false;
   bool growth_pending = false;     // growth of the last FP32 factorisation not yet checked
@@ -120,7 +122,7 @@ struct fdfd_ctx {
   // counters
   long long sf = 0, nf = 0, bs = 0, sweeps = 0, fallbacks = 0;
   long long last_iters = 0;
-  long long gm_expect = 1;          // FGMRES iterations the previous solve needed
+  long long gm_expect[2] = {1, 1};  // FGMRES iterations the previous solve needed [transpose]
   double last_resid = 0;
   double last_growth = 0;
 };
@@ -196,6 +198,8 @@ void free_plan_device(fdfd_ctx* c) {
 void free_factor(fdfd_ctx* c) {
   free_ptr(c->d_store32); free_ptr(c->d_store64); free_ptr(c->d_perm32); free_ptr(c->d_perm64);
   free_ptr(c->d_growth);
+  free_ptr(c->d_swp);
+  c->d_swp = nullptr;
   c->d_store32 = nullptr; c->d_store64 = nullptr; c->d_perm32 = c->d_perm64 = nullptr; c->d_growth = nullptr;
   c->valid32 = c->valid64 = false;
 }
@@ -282,6 +286,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
             ll.kmax_large = std::max(ll.kmax_large, p.fronts[f].k);
             ll.mmax_large = std::max(ll.mmax_large, p.fronts[f].m);
           }
+        ctx->max_nlarge = std::max(ctx->max_nlarge, ll.nlarge);
         if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
       }
     }
@@ -372,6 +377,8 @@ fdfd_status ensure_store(fdfd_ctx* ctx, int prec) {
   const Plan& p = ctx->plan;
   const size_t nfr = p.fronts.size();
   if (!ctx->d_growth) CK(dalloc(&ctx->d_growth, sizeof(float) * nfr * ctx->n_omega));
+  if (!ctx->d_swp)
+    CK(dalloc(&ctx->d_swp, sizeof(int) * (size_t)kSwapScratchInts * std::max(1, ctx->max_nlarge) * ctx->n_omega));
   if (prec == 0 && !ctx->d_store32) {
     CK(dalloc(&ctx->d_store32, sizeof(float2) * (size_t)p.store_total * ctx->n_omega));
     CK(dalloc(&ctx->d_perm32, sizeof(int) * (size_t)std::max(1, p.perm_total) * ctx->n_omega));
@@ -400,6 +407,8 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   fa.n_fronts = (int)p.fronts.size();
   fa.n_omega = nw < 0 ? ctx->n_omega : nw;
   fa.w0 = w0;
+  fa.swp = ctx->d_swp;
+  fa.swp_stride = std::max(1, ctx->max_nlarge);
   const std::vector<LevelList>& lv = design_only ? ctx->lv_design[prec] : ctx->lv_full[prec];
   const int nb = lu_panel_width(sizeof(T));
   cudaStream_t s = ctx->stream;
@@ -455,9 +464,9 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
         Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd);
         launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
       }
-      if (ll.mmax_large > 0) {
+      {
         Prof pr(ctx, PK_LU_TRSM, lf * nwd, lb * nwd);
-        launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, s);
+        launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, ll.nmax_large, s);
       }
       { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
@@ -711,7 +720,7 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
       // The host looks at the convergence flags only once the iteration count
       // reaches what the previous solve needed; meanwhile the device-side flags
       // already freeze converged systems (zero search directions, no updates).
-      if (total >= ctx->gm_expect || j + 1 == m || total >= ctx->opt.ir_max_iter) {
+      if (total >= ctx->gm_expect[transpose ? 1 : 0] || j + 1 == m || total >= ctx->opt.ir_max_iter) {
         CKS(any_active(ctx, S, &any, &res));
         if (!any) break;
       }
@@ -728,7 +737,7 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   }
   ctx->last_iters = total;
   ctx->last_resid = res;
-  ctx->gm_expect = std::max<long long>(1, total);
+  ctx->gm_expect[transpose ? 1 : 0] = std::max<long long>(1, total);
   if (!converged)
     return fail(ctx, FDFD_ERR_NOT_CONVERGED,
                 "refinement stopped at relative residual " + std::to_string(res) + " after " +

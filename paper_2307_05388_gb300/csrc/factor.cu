@@ -22,6 +22,7 @@ namespace fdfd {
 namespace {
 
 constexpr int kBuildWarps = 8;
+constexpr int kSwpInts = kSwapScratchInts;   // per panel: count + up to 64 (dst, src) row pairs
 
 // ---------------------------------------------------------------------------
 // Front build: F = originals + sum over children of their update matrices,
@@ -253,6 +254,7 @@ lu_panel_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax
     }
     __syncthreads();
   }
+  if (tid == 0) a.swp[((size_t)blockIdx.y * a.swp_stride + blockIdx.x) * kSwpInts] = 0;  // swaps done here
   for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   if (lane == 0) s_v[warp] = gmax;
   __syncthreads();
@@ -374,24 +376,36 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     const int r = e / nb, c = e - r * nb;
     F[(size_t)(j0 + r) * ld + j0 + c] = Ps[r * ldp + c];
   }
-  // swaps on the columns outside the panel: each thread owns whole columns
-  for (int c = tid; c < n; c += kPanelSmemThreads) {
-    if (c >= j0 && c < j0 + nb) continue;
+  __syncthreads();
+  // Net effect of the panel's row swaps on the columns outside the panel:
+  // row j0 + dst receives the old row j0 + src, for at most 2 nb pairs.  The
+  // shared panel buffer is reused as the position map; the swaps themselves are
+  // applied by the column-block CTAs of the next launch (lu_l21_swap_kernel).
+  int* map = reinterpret_cast<int*>(smem_raw);
+  for (int r = tid; r < R_; r += kPanelSmemThreads) map[r] = r;
+  __syncthreads();
+  if (tid == 0) {
     for (int jj = 0; jj < nb; ++jj) {
       const int piv = s_swap[jj];
-      if (piv == jj) continue;
-      T* a0 = F + (size_t)(j0 + jj) * ld + c;
-      T* a1 = F + (size_t)(j0 + piv) * ld + c;
-      const T x = *a0;
-      *a0 = *a1;
-      *a1 = x;
+      if (piv != jj) {
+        const int x = map[jj]; map[jj] = map[piv]; map[piv] = x;
+        const int y = P[j0 + jj]; P[j0 + jj] = P[j0 + piv]; P[j0 + piv] = y;
+      }
     }
+    int* out = a.swp + ((size_t)blockIdx.y * a.swp_stride + blockIdx.x) * kSwpInts;
+    int cnt = 0;
+    for (int t = 0; t < 2 * nb; ++t) {
+      const int p = t < nb ? t : s_swap[t - nb];
+      if (t >= nb) {
+        if (p < nb) continue;                           // already listed
+        bool dup = false;
+        for (int q = 0; q < t - nb; ++q) dup |= (s_swap[q] == p);
+        if (dup) continue;
+      }
+      if (map[p] != p) { out[1 + 2 * cnt] = p; out[2 + 2 * cnt] = map[p]; ++cnt; }
+    }
+    out[0] = cnt;
   }
-  if (tid == 0)
-    for (int jj = 0; jj < nb; ++jj) {
-      const int piv = s_swap[jj];
-      if (piv != jj) { const int x = P[j0 + jj]; P[j0 + jj] = P[j0 + piv]; P[j0 + piv] = x; }
-    }
   for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   if (lane == 0) s_v[warp] = gmax;
   __syncthreads();
@@ -408,9 +422,11 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
 // triangular solve with the panel's upper block), 64 rows per CTA.
 constexpr int kL21Rows = 64;
 
+// CTAs with blockIdx.x >= nl21 instead apply the panel's net row permutation
+// (pairs written by lu_panel_smem_kernel) to 32 columns outside the panel.
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, int nl21) {
   using R = typename RealOf<T>::type;
   __shared__ T Us[kMaxNb][kMaxNb + 1];
   __shared__ T Xs[kL21Rows][kMaxNb + 1];
@@ -420,6 +436,25 @@ lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) 
   const FrontDesc d = a.P.fronts[f];
   if (j0 >= d.k) return;
   const int nb = min(nbmax, d.k - j0);
+  if ((int)blockIdx.x >= nl21) {
+    // ---- row swaps on columns [c0, c0 + 32) of the non-panel columns -------
+    const int* pr = a.swp + ((size_t)blockIdx.z * a.swp_stride + blockIdx.y) * kSwpInts;
+    const int cnt = pr[0];
+    const int cb = (blockIdx.x - nl21) * 32;
+    if (cnt == 0 || cb >= d.n - nb) return;
+    T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+    T* buf = &Xs[0][0];                    // 64 x 33 entries: one row of 32 columns per pair
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int ci = cb + lane;
+    const int c = ci < j0 ? ci : ci + nb;  // skip the panel columns
+    const bool ok = ci < d.n - nb;
+    for (int t = wp; t < cnt; t += 8)
+      if (ok) buf[t * (kMaxNb + 1) + lane] = F[(size_t)(j0 + pr[2 + 2 * t]) * d.ld + c];
+    __syncthreads();
+    for (int t = wp; t < cnt; t += 8)
+      if (ok) F[(size_t)(j0 + pr[1 + 2 * t]) * d.ld + c] = buf[t * (kMaxNb + 1) + lane];
+    return;
+  }
   const int r0 = d.k + blockIdx.x * kL21Rows;
   if (r0 >= d.n) return;
   const int rows = min(kL21Rows, d.n - r0);
@@ -631,9 +666,12 @@ void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0, in
 }
 
 template <typename T>
-void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int mmax, cudaStream_t s) {
-  if (nf <= 0 || mmax <= 0) return;
-  lu_l21_kernel<T><<<dim3((mmax + kL21Rows - 1) / kL21Rows, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb);
+void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int mmax, int nmax,
+                   cudaStream_t s) {
+  if (nf <= 0) return;
+  const int nl21 = (mmax + kL21Rows - 1) / kL21Rows;
+  const int nswap = (nmax + 31) / 32;
+  lu_l21_kernel<T><<<dim3(nl21 + nswap, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb, nl21);
 }
 
 template <typename T>
@@ -658,7 +696,7 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
   template void launch_build<T>(const FactorLaunch&, const int2*, int, cudaStream_t);            \
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
   template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
-  template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
+  template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t);
 FDFD_INST(float2)

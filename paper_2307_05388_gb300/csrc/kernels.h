@@ -25,6 +25,8 @@ struct FactorLaunch {
   int n_fronts;
   int n_omega;             // wavelengths launched: [w0, w0 + n_omega)
   int w0;
+  int* swp;                // panel row-swap scratch: [n_omega launched][swp_stride][130]
+  int swp_stride;          // >= number of fronts in one large-front list
 };
 // max over growth[0..count) (NaN wins) into *out
 cudaError_t launch_growth_max(const float* growth, long long count, float* out, cudaStream_t s);
@@ -39,7 +41,8 @@ template <typename T> void launch_lu_small(const FactorLaunch& a, const int* fli
 template <typename T> void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0,
                                            int nb, int kmax, cudaStream_t s);
 template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0,
-                                         int nb, int mmax, cudaStream_t s);
+                                         int nb, int mmax, int nmax, cudaStream_t s);
+constexpr int kSwapScratchInts = 130;   // ints of swap scratch per (wavelength, listed front)
 template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
