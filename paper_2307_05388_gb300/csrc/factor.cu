@@ -274,7 +274,7 @@ constexpr int kMaxNb = 32;
 // per front).  Per column: block argmax, swap of the two panel rows, then one
 // warp per row scales and updates the row (lane = column).  The row swaps are
 // applied to the columns outside the panel afterwards, in order.
-constexpr int kPanelSmemThreads = 256;
+constexpr int kPanelSmemThreads = 512;
 constexpr int kPanelSmemBytes = 200 * 1024;
 
 template <typename T>
@@ -339,28 +339,25 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     R best = -1;
     int bi = nx;
     for (int r = jj + 1 + warp; r < R_; r += U * NW) {
-      T l[U];
+      T l[U], cur[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int ru = r + u * NW;
-        l[u] = ru < R_ ? cmul(Ps[ru * ldp + jj], inv) : czero<T>();
+        const bool ok = ru < R_;
+        l[u] = ok ? cmul(Ps[ru * ldp + jj], inv) : czero<T>();
+        cur[u] = (ok && lane < nb) ? Ps[ru * ldp + lane] : czero<T>();
       }
-      __syncwarp();                        // every lane has read its column entries before lane jj overwrites them
+      __syncwarp();                        // every lane has read its entries before any lane writes
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int ru = r + u * NW;
-        if (ru >= R_) break;
-        if (lane == jj) {
-          Ps[ru * ldp + jj] = l[u];
-        } else if (lane > jj && lane < nb) {
-          const T nv = cfms(l[u], urow, Ps[ru * ldp + lane]);
-          Ps[ru * ldp + lane] = nv;
-          if (lane == nx) {
-            const R v = cabs2(nv);
-            if (v > best) { best = v; bi = ru; }
-          }
+        if (ru < R_) {                     // warp-uniform
+          const T nv = lane == jj ? l[u] : (lane > jj ? cfms(l[u], urow, cur[u]) : cur[u]);
+          if (lane < nb) Ps[ru * ldp + lane] = nv;
+          const R v = cabs2(nv);
+          if (lane == nx && v > best) { best = v; bi = ru; }
+          gmax = nanmax(gmax, cabs2(l[u]));
         }
-        if (lane == 0) gmax = nanmax(gmax, cabs2(l[u]));
       }
     }
     if (nx < nb) {
@@ -398,6 +395,165 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
       const int p = t < nb ? t : s_swap[t - nb];
       if (t >= nb) {
         if (p < nb) continue;                           // already listed
+        bool dup = false;
+        for (int q = 0; q < t - nb; ++q) dup |= (s_swap[q] == p);
+        if (dup) continue;
+      }
+      if (map[p] != p) { out[1 + 2 * cnt] = p; out[2 + 2 * cnt] = map[p]; ++cnt; }
+    }
+    out[0] = cnt;
+  }
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) s_v[warp] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    R g = 0;
+    for (int i = 0; i < NW; ++i) g = nanmax(g, s_v[i]);
+    float* gp = a.growth + (size_t)w * a.n_fronts + f;
+    const float gv = (float)sqrt((double)g);
+    *gp = (j0 == 0) ? gv : nanmax(*gp, gv);
+  }
+}
+
+// Panel with the pivot-candidate rows held in registers: warp w owns rows
+// w, w + 16, w + 32, ... (RPW of them), lane c holds column c.  Per column: the
+// pivot row (and the row it displaces) go through shared memory once, every
+// warp updates its rows in registers with the pivot row broadcast, and lane
+// jj+1 collects the next column's argmax on the way (2 barriers per column).
+constexpr int kRegWarps = 16;
+
+template <typename T>
+__device__ __forceinline__ T shfl_c(T v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ T pick(const T (&v)[N], int s) {
+  T r = v[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i)
+    if (i == s) r = v[i];
+  return r;
+}
+template <typename T, int N>
+__device__ __forceinline__ void put(T (&v)[N], int s, T x) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i == s) v[i] = x;
+}
+
+template <typename T, int RPW>
+__global__ void __launch_bounds__(kRegWarps * 32)
+lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  using R = typename RealOf<T>::type;
+  constexpr int NW = kRegWarps;
+  __shared__ T prow[32];
+  __shared__ T srow[32];
+  __shared__ R s_v[NW];
+  __shared__ int s_i[NW];
+  __shared__ int s_swap[kMaxNb];
+  __shared__ int map[NW * RPW];
+  const int w = blockIdx.y + a.w0;
+  const int f = flist[blockIdx.x];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int k = d.k, ld = d.ld;
+  const int R_ = k - j0;                       // <= NW * RPW (checked by the launcher)
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (j0 == 0)
+    for (int i = tid; i < k; i += NW * 32) P[i] = i;
+  T row[RPW];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = warp + i * NW;
+    row[i] = (r < R_ && lane < nb) ? F[(size_t)(j0 + r) * ld + j0 + lane] : czero<T>();
+  }
+  {  // argmax of column 0 (held by lane 0)
+    R best = -1;
+    int bi = 0;
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      const int r = warp + i * NW;
+      if (r < R_) {
+        const R v = cabs2(row[i]);
+        if (v > best) { best = v; bi = r; }
+      }
+    }
+    best = __shfl_sync(0xffffffffu, best, 0);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
+  }
+  __syncthreads();
+  R gmax = 0;
+  for (int jj = 0; jj < nb; ++jj) {
+    R bv = s_v[0];
+    int piv = s_i[0];
+#pragma unroll
+    for (int i = 1; i < NW; ++i)
+      if (s_v[i] > bv || (s_v[i] == bv && s_i[i] < piv)) { bv = s_v[i]; piv = s_i[i]; }
+    if (piv < jj) piv = jj;
+    const int ow_j = jj % NW, sl_j = jj / NW, ow_p = piv % NW, sl_p = piv / NW;
+    if (warp == ow_p) prow[lane] = pick(row, sl_p);
+    if (piv != jj && warp == ow_j) srow[lane] = pick(row, sl_j);
+    if (tid == 0) s_swap[jj] = piv;
+    __syncthreads();
+    if (piv != jj) {
+      if (warp == ow_j) put(row, sl_j, prow[lane]);
+      if (warp == ow_p) put(row, sl_p, srow[lane]);
+    }
+    const T ur = prow[lane];
+    const T pv = prow[jj];
+    const T inv = crcp(pv);
+    if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
+    const int nx = jj + 1;
+    R best = -1;
+    int bi = nx;
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      const int r = warp + i * NW;
+      if (r > jj && r < R_) {                   // warp-uniform
+        const T l = cmul(shfl_c(row[i], jj), inv);
+        const T upd = cfms(l, ur, row[i]);
+        row[i] = lane == jj ? l : (lane > jj ? upd : row[i]);
+        gmax = nanmax(gmax, cabs2(l));
+        const R v = cabs2(row[i]);
+        if (lane == nx && v > best) { best = v; bi = r; }
+      }
+    }
+    if (nx < nb) {
+      best = __shfl_sync(0xffffffffu, best, nx);
+      bi = __shfl_sync(0xffffffffu, bi, nx);
+      if (lane == 0) { s_v[warp] = best; s_i[warp] = bi; }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = warp + i * NW;
+    if (r < R_ && lane < nb) F[(size_t)(j0 + r) * ld + j0 + lane] = row[i];
+  }
+  // net row permutation of the panel for the columns outside it (see lu_panel_smem_kernel)
+  for (int r = tid; r < R_; r += NW * 32) map[r] = r;
+  __syncthreads();
+  if (tid == 0) {
+    for (int jj = 0; jj < nb; ++jj) {
+      const int piv = s_swap[jj];
+      if (piv != jj) {
+        const int x = map[jj]; map[jj] = map[piv]; map[piv] = x;
+        const int y = P[j0 + jj]; P[j0 + jj] = P[j0 + piv]; P[j0 + piv] = y;
+      }
+    }
+    int* out = a.swp + ((size_t)blockIdx.y * a.swp_stride + blockIdx.x) * kSwpInts;
+    int cnt = 0;
+    for (int t = 0; t < 2 * nb; ++t) {
+      const int p = t < nb ? t : s_swap[t - nb];
+      if (t >= nb) {
+        if (p < nb) continue;
         bool dup = false;
         for (int q = 0; q < t - nb; ++q) dup |= (s_swap[q] == p);
         if (dup) continue;
@@ -658,6 +814,10 @@ void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, 
 template <typename T>
 void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int kmax, cudaStream_t s) {
   if (nf <= 0 || j0 >= kmax) return;
+  const int rows = kmax - j0;
+  const dim3 grid(nf, a.n_omega), blk(kRegWarps * 32);
+  if (rows <= kRegWarps * 8) { lu_panel_reg_kernel<T, 8><<<grid, blk, 0, s>>>(a, flist, j0, nb); return; }
+  if (rows <= kRegWarps * 16) { lu_panel_reg_kernel<T, 16><<<grid, blk, 0, s>>>(a, flist, j0, nb); return; }
   const size_t smem = (size_t)(kmax - j0) * (nb + 1) * sizeof(T);
   if (smem <= (size_t)kPanelSmemBytes)
     lu_panel_smem_kernel<T><<<dim3(nf, a.n_omega), kPanelSmemThreads, smem, s>>>(a, flist, j0, nb);
