@@ -47,18 +47,39 @@ __device__ __forceinline__ T shfl(T v, int src) {
   return v;
 }
 
-// sum_{c in [c0, c1)} row[c] * vec[c], lanes striding the row (coalesced), warp-reduced
+// sum_{c in [c0, c1)} row[c] * vec[c], lanes striding the row (coalesced), warp-reduced.
+// Eight loads per lane are issued before they are used, so that a single
+// front's row keeps enough bytes in flight to cover the memory latency.
 template <typename T>
 __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, int c0, int c1, int lane) {
-  T a0 = czero<T>(), a1 = czero<T>();
+  constexpr int UN = 8;
+  T acc[2] = {czero<T>(), czero<T>()};
   int c = c0 + lane;
-  for (; c + 32 < c1; c += 64) {
-    const T r0 = row[c], r1 = row[c + 32];
-    a0 = cfma(r0, vec[c], a0);
-    a1 = cfma(r1, vec[c + 32], a1);
+  for (; c + 32 * (UN - 1) < c1; c += 32 * UN) {
+    T r[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) r[u] = row[c + 32 * u];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) acc[u & 1] = cfma(r[u], vec[c + 32 * u], acc[u & 1]);
   }
-  if (c < c1) a0 = cfma(row[c], vec[c], a0);
-  return warp_sum(cadd(a0, a1));
+  for (; c < c1; c += 32) acc[0] = cfma(row[c], vec[c], acc[0]);
+  return warp_sum(cadd(acc[0], acc[1]));
+}
+
+// vs[c] -= sum_{bb < bs} F[(kb + bb) * ld + c] * vs[kb + bb]: one column per thread,
+// all bs (<= 32) loads of the column issued before the multiply-adds.
+template <typename T>
+__device__ __forceinline__ void col_update(const T* __restrict__ F, int ld, int kb, int bs, int c, T* vs) {
+  T f[32];
+#pragma unroll
+  for (int bb = 0; bb < 32; ++bb) f[bb] = bb < bs ? F[(size_t)(kb + bb) * ld + c] : czero<T>();
+  T a0 = vs[c], a1 = czero<T>();
+#pragma unroll
+  for (int bb = 0; bb < 32; bb += 2) {
+    if (bb < bs) a0 = cfms(f[bb], vs[kb + bb], a0);
+    if (bb + 1 < bs) a1 = cfms(f[bb + 1], vs[kb + bb + 1], a1);
+  }
+  vs[c] = cadd(a0, a1);
 }
 
 // v[s] for s < n: rhs entry (pivot rows only) plus the children's update vectors.
@@ -198,17 +219,7 @@ tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ i
           __syncwarp();
         }
         __syncthreads();
-        for (int c = kb + bs + tid; c < cend; c += kThreads) {
-          T a0 = vs[c], a1 = czero<T>();
-          int bb = 0;
-          for (; bb + 1 < bs; bb += 2) {
-            const T f0 = F[(size_t)(kb + bb) * ld + c], f1 = F[(size_t)(kb + bb + 1) * ld + c];
-            a0 = cfms(f0, vs[kb + bb], a0);
-            a1 = cfms(f1, vs[kb + bb + 1], a1);
-          }
-          if (bb < bs) a0 = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], a0);
-          vs[c] = cadd(a0, a1);
-        }
+        for (int c = kb + bs + tid; c < cend; c += kThreads) col_update(F, ld, kb, bs, c, vs);
         __syncthreads();
       }
       for (int s = tid; s < n; s += kThreads) vf[s] = vs[s];
@@ -242,17 +253,7 @@ tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ i
           __syncwarp();
         }
         __syncthreads();
-        for (int c = tid; c < kb; c += kThreads) {
-          T a0 = vs[c], a1 = czero<T>();
-          int bb = 0;
-          for (; bb + 1 < bs; bb += 2) {
-            const T f0 = F[(size_t)(kb + bb) * ld + c], f1 = F[(size_t)(kb + bb + 1) * ld + c];
-            a0 = cfms(f0, vs[kb + bb], a0);
-            a1 = cfms(f1, vs[kb + bb + 1], a1);
-          }
-          if (bb < bs) a0 = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], a0);
-          vs[c] = cadd(a0, a1);
-        }
+        for (int c = tid; c < kb; c += kThreads) col_update(F, ld, kb, bs, c, vs);
         __syncthreads();
       }
       for (int s = tid; s < k; s += kThreads) xo[idx[Pm[s]]] = vs[s];
@@ -312,14 +313,20 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
       const int c = s0 + lane;
       T a0 = czero<T>(), a1 = czero<T>();
       if (c < cols) {
+        constexpr int UN = 8;
         const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
         int i = warp;
-        for (; i + kWarps < rows; i += 2 * kWarps) {
-          const T f0 = base[(size_t)i * ld], f1 = base[(size_t)(i + kWarps) * ld];
-          a0 = cfma(f0, vs[i], a0);
-          a1 = cfma(f1, vs[i + kWarps], a1);
+        for (; i + (UN - 1) * kWarps < rows; i += UN * kWarps) {
+          T fr[UN];
+#pragma unroll
+          for (int u = 0; u < UN; ++u) fr[u] = base[(size_t)(i + u * kWarps) * ld];
+#pragma unroll
+          for (int u = 0; u < UN; u += 2) {
+            a0 = cfma(fr[u], vs[i + u * kWarps], a0);
+            a1 = cfma(fr[u + 1], vs[i + (u + 1) * kWarps], a1);
+          }
         }
-        if (i < rows) a0 = cfma(base[(size_t)i * ld], vs[i], a0);
+        for (; i < rows; i += kWarps) a0 = cfma(base[(size_t)i * ld], vs[i], a0);
       }
       red[warp][lane] = cadd(a0, a1);
       __syncthreads();
