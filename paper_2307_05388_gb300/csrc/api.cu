@@ -780,7 +780,7 @@ extern "C" {
 void fdfd_default_options(fdfd_options* o) {
   if (!o) return;
   o->mode = FDFD_MODE_MIXED;
-  o->ir_tol = 1e-12;
+  o->ir_tol = 1e-10;
   o->ir_max_iter = 40;
   o->gmres_restart = 8;
   o->growth_bound = 1e6;

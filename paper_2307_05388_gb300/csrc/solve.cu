@@ -67,18 +67,23 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, i
 }
 
 // vs[c] -= sum_{bb < bs} F[(kb + bb) * ld + c] * vs[kb + bb]: one column per thread,
-// all bs (<= 32) loads of the column issued before the multiply-adds.
+// loads issued eight at a time ahead of their multiply-adds.
 template <typename T>
 __device__ __forceinline__ void col_update(const T* __restrict__ F, int ld, int kb, int bs, int c, T* vs) {
-  T f[32];
-#pragma unroll
-  for (int bb = 0; bb < 32; ++bb) f[bb] = bb < bs ? F[(size_t)(kb + bb) * ld + c] : czero<T>();
+  constexpr int UN = 8;
   T a0 = vs[c], a1 = czero<T>();
+  int bb = 0;
+  for (; bb + UN <= bs; bb += UN) {
+    T f[UN];
 #pragma unroll
-  for (int bb = 0; bb < 32; bb += 2) {
-    if (bb < bs) a0 = cfms(f[bb], vs[kb + bb], a0);
-    if (bb + 1 < bs) a1 = cfms(f[bb + 1], vs[kb + bb + 1], a1);
+    for (int u = 0; u < UN; ++u) f[u] = F[(size_t)(kb + bb + u) * ld + c];
+#pragma unroll
+    for (int u = 0; u < UN; u += 2) {
+      a0 = cfms(f[u], vs[kb + bb + u], a0);
+      a1 = cfms(f[u + 1], vs[kb + bb + u + 1], a1);
+    }
   }
+  for (; bb < bs; ++bb) a0 = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], a0);
   vs[c] = cadd(a0, a1);
 }
 
