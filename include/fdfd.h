@@ -48,6 +48,8 @@
 #ifndef FDFD_H_
 #define FDFD_H_
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -209,6 +211,34 @@ const char* fdfd_last_error(const fdfd_ctx* ctx);
 
 /* Frees every device and host buffer of the context (synchronises its stream). */
 void fdfd_destroy(fdfd_ctx* ctx);
+
+/* Solve on the cached factors without allocating any device memory.
+ * (The paper has no counterpart: this is a library convenience.)
+ *
+ * For callers that cannot call cudaMalloc at solve time: code that must not
+ * let the allocator synchronise the device inside a latency-critical loop,
+ * processes whose device memory is budgeted or owned by another allocator
+ * pool, and embedding applications that forbid allocation after set-up.
+ *
+ * Computes x = (P^T L U)^-1 b (transpose = 0) or x = (P^T L U)^-T b
+ * (transpose = 1) with the cached factorisation: the raw forward and backward
+ * sweeps only, without refinement (the same result as fdfd_solve with
+ * ir_max_iter = 0).  b_dev, x_dev: [n_omega][nrhs][nx*ny] complex128 (device,
+ * caller-owned); x may not alias b.  All temporary storage lives in one fixed
+ * device array of fdfd_noalloc_scratch_bytes() bytes (32 MiB) that every GPU
+ * loading this library holds until the process exits; a solve whose front
+ * vectors and precision-conversion buffers do not fit is rejected with
+ * FDFD_ERR_ARG before any device work.  The first call on a device looks up
+ * the array's device address (with that device current); make that first call
+ * before any stream capture.  Every call shares the array and leaves its last
+ * contents there (nothing in it needs to start at zero); calls that overlap on
+ * the GPU race on it and must be serialised by the caller.  Requires an earlier
+ * fdfd_factor (FDFD_ERR_STATE otherwise); if that FP32 factorisation exceeded
+ * the growth bound, returns FDFD_ERR_PIVOT (fdfd_solve redoes it in FP64, which
+ * allocates). */
+fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose);
+/* Size in bytes of the fixed scratch array used by fdfd_solve_raw_noalloc. */
+size_t fdfd_noalloc_scratch_bytes(void);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1070,6 +1071,129 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   if (ctx->h_active) cudaFreeHost(ctx->h_active);
   if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
   delete ctx;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Solve on the cached factors without allocating device memory
+// ===========================================================================
+//
+// Some callers cannot call cudaMalloc at solve time: a real-time design loop
+// that must not synchronise the device (cudaMalloc and cudaFree can), a host
+// process running under an allocator budget or a pool it does not own, or an
+// embedding application that forbids allocation after its set-up phase.  For
+// them this entry point applies the cached factorisation once (the raw
+// forward and backward sweeps, no refinement) with all of its temporary
+// storage in the fixed device array below instead of the context's buffers.
+//
+// The array is a static __device__ object: every GPU that loads this library
+// holds its 32 MiB until the process exits.  Its device address is looked up
+// once per device, on the first call made with that device current; make that
+// first call before any stream capture.  All calls share the one array and
+// nothing in it needs to start at zero (every entry is written before it is
+// read); calls that overlap on the GPU (two streams, two host threads, two
+// contexts) race on it and must be serialised by the caller.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32u << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+template <typename T>
+void sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out, void* vb) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const Plan& p = ctx->plan;
+  SolveLaunch sa;
+  sa.P = dev_plan(ctx);
+  sa.store = prec == 0 ? (const void*)ctx->d_store32 : (const void*)ctx->d_store64;
+  sa.store_stride = p.store_total;
+  sa.perm = prec == 0 ? ctx->d_perm32 : ctx->d_perm64;
+  sa.perm_stride = std::max(1, p.perm_total);
+  sa.vb = vb;
+  sa.vec_stride = p.vec_total;
+  sa.n_omega = ctx->n_omega;
+  sa.nrhs = nrhs;
+  sa.w0 = 0;
+  sa.r0 = 0;
+  sa.nr = nrhs;
+  sa.n = n_cells(ctx);
+  const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
+  const int* dl = ctx->d_lists;
+  for (int l = 0; l < p.n_levels; ++l) {
+    const SolveList& sl = ctx->lv_solve[l];
+    launch_sweep_tri<T>(sa, fwd, dl + sl.off, sl.nf, sl.nmax, in, out, ctx->stream);
+    if (sl.nmt > 0)
+      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.mt_off), sl.nmt, sl.kbig, out, ctx->stream);
+  }
+  for (int l = p.n_levels - 1; l >= 0; --l) {
+    const SolveList& sl = ctx->lv_solve[l];
+    if (sl.nkt > 0)
+      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.kt_off), sl.nkt, sl.mbig, out, ctx->stream);
+    launch_sweep_tri<T>(sa, bwd, dl + sl.off, sl.nf, sl.nmax, in, out, ctx->stream);
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" {
+
+size_t fdfd_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
+fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose) {
+  if (!ctx || !b_dev || !x_dev || nrhs <= 0 || b_dev == x_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->uploaded || !(ctx->valid32 || ctx->valid64) || ctx->opt.mode == FDFD_MODE_PLAIN)
+    return fail(ctx, FDFD_ERR_STATE, "fdfd_solve_raw_noalloc needs a cached factorisation (fdfd_factor first)");
+  const bool use64 = ctx->valid64;
+  const size_t S = (size_t)ctx->n_omega * nrhs;
+  const size_t N = (size_t)n_cells(ctx);
+  const size_t es = use64 ? sizeof(double2) : sizeof(float2);
+  const size_t vb_bytes = align256(S * (size_t)ctx->plan.vec_total * es);
+  const size_t cvt_bytes = use64 ? 0 : 2 * align256(S * N * sizeof(float2));
+  if (vb_bytes + cvt_bytes > kNoAllocScratchBytes)
+    return fail(ctx, FDFD_ERR_ARG,
+                "fdfd_solve_raw_noalloc: this solve needs " + std::to_string(vb_bytes + cvt_bytes) +
+                    " bytes of scratch; the fixed device array holds " + std::to_string(kNoAllocScratchBytes));
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(ctx, FDFD_ERR_ARG, "fdfd_solve_raw_noalloc: device index out of range");
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      // one-time set-up on this device: the host-side symbol is not a device
+      // address, so ask the runtime where the array lives on the current device
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = reinterpret_cast<unsigned char*>(g_noalloc_addr[dev]);
+  }
+  if (ctx->growth_pending && !use64) {
+    // the factorisation's growth figure decides whether FP32 factors may be used;
+    // this call cannot redo the factorisation in FP64 (that allocates)
+    if (!ctx->growth_ready) CK(cudaStreamSynchronize(ctx->stream));
+    if (!(*ctx->h_growth_max <= ctx->opt.growth_bound))
+      return fail(ctx, FDFD_ERR_PIVOT,
+                  "fdfd_solve_raw_noalloc: FP32 factors exceed the growth bound; call fdfd_solve once first");
+  }
+  if (use64) {
+    sweeps_in<double2>(ctx, nrhs, transpose, b_dev, x_dev, scratch);
+  } else {
+    float2* bT = reinterpret_cast<float2*>(scratch + vb_bytes);
+    float2* xT = reinterpret_cast<float2*>(scratch + vb_bytes + cvt_bytes / 2);
+    launch_cvt_from64<float2>(bT, reinterpret_cast<const double2*>(b_dev), nullptr, (long long)N, (int)S, ctx->stream);
+    sweeps_in<float2>(ctx, nrhs, transpose, bT, xT, scratch);
+    launch_cvt_to64<float2>(reinterpret_cast<double2*>(x_dev), xT, nullptr, (long long)N, (int)S, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  return FDFD_OK;
 }
 
 }  // extern "C"

@@ -26,7 +26,7 @@ MODE_MIXED, MODE_F64, MODE_PLAIN = 0, 1, 2
 EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
-           "fdfd_profile_enable", "fdfd_profile_get"]
+           "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes"]
 
 
 class Grid(C.Structure):
@@ -84,6 +84,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_profile_get.argtypes = [vp, C.POINTER(KernelProfile), i, C.POINTER(C.c_int)]
     lib.fdfd_reset_counters.argtypes = [vp]
     lib.fdfd_reset_counters.restype = None
+    lib.fdfd_solve_raw_noalloc.argtypes = [vp, vp, vp, i, i]
+    lib.fdfd_solve_raw_noalloc.restype = C.c_int
+    lib.fdfd_noalloc_scratch_bytes.argtypes = []
+    lib.fdfd_noalloc_scratch_bytes.restype = C.c_size_t
     lib.fdfd_last_error.argtypes = [vp]
     lib.fdfd_last_error.restype = C.c_char_p
     lib.fdfd_destroy.argtypes = [vp]
