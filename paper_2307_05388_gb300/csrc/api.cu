@@ -30,13 +30,10 @@ struct LevelList {
 };
 
 struct SolveList {
-  int off = 0, nf = 0, nmax = 0, kmax = 0;    // triangular list (all fronts of the level)
-  int mt_off = 0, nmt = 0, kt_off = 0, nkt = 0;  // rectangular tasks of large fronts
+  int off = 0, nf = 0, nmax = 0, kmax = 0;       // inverse-block tasks (every front of the level)
+  int mt_off = 0, nmt = 0, kt_off = 0, nkt = 0;  // off-diagonal tasks (fronts with boundary rows)
   int mbig = 0, kbig = 0;
 };
-
-// Fronts above this size leave their off-diagonal block to the rectangular kernels.
-constexpr int kSolveBigN = 128;
 
 template <typename P>
 cudaError_t dalloc(P** p, size_t bytes) {
@@ -88,6 +85,8 @@ struct fdfd_ctx {
   double2* d_store64 = nullptr;
   int* d_perm32 = nullptr;
   int* d_perm64 = nullptr;
+  float2* d_inv32 = nullptr;       // triangular inverses of the pivot blocks
+  double2* d_inv64 = nullptr;
   float* d_growth = nullptr;
   float* d_growth_max = nullptr;
   int* d_swp = nullptr;            // panel row-swap scratch
@@ -153,10 +152,10 @@ void free_ptr(void* p) {
   if (p) cudaFree(p);
 }
 
-enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_SWEEP_L, PK_SWEEP_U,
-                PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT, PK_OTHER,
-                PK_COUNT };
-const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm",
+enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_INV, PK_SWEEP_L,
+                PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT,
+                PK_OTHER, PK_COUNT };
+const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm", "lu_inv",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "precision_cvt", "other"};
 
@@ -198,6 +197,8 @@ void free_plan_device(fdfd_ctx* c) {
 
 void free_factor(fdfd_ctx* c) {
   free_ptr(c->d_store32); free_ptr(c->d_store64); free_ptr(c->d_perm32); free_ptr(c->d_perm64);
+  free_ptr(c->d_inv32); free_ptr(c->d_inv64);
+  c->d_inv32 = nullptr; c->d_inv64 = nullptr;
   free_ptr(c->d_growth);
   free_ptr(c->d_swp);
   c->d_swp = nullptr;
@@ -296,28 +297,26 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   const int rb = sweep_rect_block();
   for (int l = 0; l < L; ++l) {
     SolveList& sl = ctx->lv_solve[l];
-    sl.off = (int)lists.size();
+    if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
+    sl.off = (int)lists.size();                 // inverse-block tasks of every front
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
-      const bool big = d.n > kSolveBigN;
-      lists.push_back(big ? (int)(0x80000000u | (unsigned)f) : f);
-      sl.nf++;
+      for (int b0 = 0; b0 < d.k; b0 += rb) { lists.push_back(f); lists.push_back(b0); sl.nf++; }
       sl.nmax = std::max(sl.nmax, d.n);
       sl.kmax = std::max(sl.kmax, d.k);
     }
-    if (lists.size() % 2) lists.push_back(0);
-    sl.mt_off = (int)lists.size();          // blocks over the m boundary rows / columns
+    sl.mt_off = (int)lists.size();              // off-diagonal tasks over the m boundary rows / columns
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
-      if (d.n <= kSolveBigN) continue;
+      if (d.m == 0) continue;
       for (int t0 = 0; t0 < d.m; t0 += rb) { lists.push_back(f); lists.push_back(t0); sl.nmt++; }
       sl.mbig = std::max(sl.mbig, d.m);
       sl.kbig = std::max(sl.kbig, d.k);
     }
-    sl.kt_off = (int)lists.size();          // blocks over the k pivot rows / columns
+    sl.kt_off = (int)lists.size();              // off-diagonal tasks over the k pivot rows / columns
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
-      if (d.n <= kSolveBigN) continue;
+      if (d.m == 0) continue;
       for (int a0 = 0; a0 < d.k; a0 += rb) { lists.push_back(f); lists.push_back(a0); sl.nkt++; }
     }
   }
@@ -383,10 +382,12 @@ fdfd_status ensure_store(fdfd_ctx* ctx, int prec) {
   if (prec == 0 && !ctx->d_store32) {
     CK(dalloc(&ctx->d_store32, sizeof(float2) * (size_t)p.store_total * ctx->n_omega));
     CK(dalloc(&ctx->d_perm32, sizeof(int) * (size_t)std::max(1, p.perm_total) * ctx->n_omega));
+    CK(dalloc(&ctx->d_inv32, sizeof(float2) * (size_t)p.inv_total * ctx->n_omega));
   }
   if (prec == 1 && !ctx->d_store64) {
     CK(dalloc(&ctx->d_store64, sizeof(double2) * (size_t)p.store_total * ctx->n_omega));
     CK(dalloc(&ctx->d_perm64, sizeof(int) * (size_t)std::max(1, p.perm_total) * ctx->n_omega));
+    CK(dalloc(&ctx->d_inv64, sizeof(double2) * (size_t)p.inv_total * ctx->n_omega));
   }
   return FDFD_OK;
 }
@@ -410,6 +411,8 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   fa.w0 = w0;
   fa.swp = ctx->d_swp;
   fa.swp_stride = std::max(1, ctx->max_nlarge);
+  fa.istore = prec == 0 ? (void*)ctx->d_inv32 : (void*)ctx->d_inv64;
+  fa.istore_stride = p.inv_total;
   const std::vector<LevelList>& lv = design_only ? ctx->lv_design[prec] : ctx->lv_full[prec];
   const int nb = lu_panel_width(sizeof(T));
   cudaStream_t s = ctx->stream;
@@ -472,6 +475,18 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
     }
+    if (ll.nlarge > 0) {
+      // triangular inverses of the level's large fronts (2/3 k^3 complex multiply-adds each)
+      double vf = 0, vb = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.nlarge; ++t) {
+          const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
+          vf += 8.0 * (2.0 / 6.0) * (double)d.k * d.k * d.k;
+          vb += es * 2.0 * (double)d.k * d.k;
+        }
+      Prof pr(ctx, PK_LU_INV, vf * nwd, vb * nwd);
+      launch_lu_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
+    }
   }
   CK(cudaGetLastError());
   Prof pr_g(ctx, PK_OTHER, 0, 4.0 * p.fronts.size() * ctx->n_omega);
@@ -503,6 +518,8 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   sa.store_stride = p.store_total;
   sa.perm = prec == 0 ? ctx->d_perm32 : ctx->d_perm64;
   sa.perm_stride = std::max(1, p.perm_total);
+  sa.istore = prec == 0 ? (const void*)ctx->d_inv32 : (const void*)ctx->d_inv64;
+  sa.istore_stride = p.inv_total;
   sa.vb = ctx->d_vb;
   sa.vec_stride = p.vec_total;
   sa.n_omega = nw < 0 ? ctx->n_omega : nw;
@@ -514,29 +531,34 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   cudaStream_t s = ctx->stream;
   const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
   const double es = sizeof(T), nsys = (double)sa.n_omega * sa.nr;
-  // algorithmic work: each factor entry of the swept triangle (and of the
-  // off-diagonal block) read once per right-hand side, 8 flops per entry
+  const int rb = sweep_rect_block();
+  // algorithmic work: every entry of the swept triangle (and of the off-diagonal
+  // block) read once per right-hand side, 8 flops per entry, plus the vectors
   auto tri_work = [&](const SolveList& sl, bool lower, double* fl, double* by) {
     *fl = *by = 0;
     if (!ctx->prof_on) return;
     for (int t = 0; t < sl.nf; ++t) {
-      const int e = ctx->h_lists[sl.off + t];
-      const FrontDesc& d = p.fronts[e & 0x7fffffff];
-      double ent = lower ? 0.5 * d.k * (d.k - 1.0) : 0.5 * d.k * (d.k + 1.0);
-      if (e >= 0) ent += (double)d.m * d.k;
+      const FrontDesc& d = p.fronts[ctx->h_lists[sl.off + 2 * t]];
+      const int b0 = ctx->h_lists[sl.off + 2 * t + 1];
+      const int b1 = std::min(d.k, b0 + rb);
+      double ent = 0;   // entries of this task's rows (or columns) inside the triangle
+      for (int r = b0; r < b1; ++r) ent += lower ? r : (d.k - r);
       *fl += 8.0 * ent * nsys;
-      *by += es * ent * nsys + 3.0 * es * d.n * nsys;
+      *by += es * (ent + (b1 - b0)) * nsys;
     }
   };
-  auto rect_work = [&](const SolveList& sl, double* fl, double* by) {
+  auto rect_work = [&](const SolveList& sl, int off, int cnt, bool over_m, double* fl, double* by) {
     *fl = *by = 0;
     if (!ctx->prof_on) return;
-    for (int t = 0; t < sl.nmt; ++t) {
-      const FrontDesc& d = p.fronts[ctx->h_lists[sl.mt_off + 2 * t]];
-      const double rows = std::min(sweep_rect_block(), d.m - ctx->h_lists[sl.mt_off + 2 * t + 1]);
-      *fl += 8.0 * rows * d.k * nsys;
-      *by += es * rows * d.k * nsys;
+    for (int t = 0; t < cnt; ++t) {
+      const FrontDesc& d = p.fronts[ctx->h_lists[off + 2 * t]];
+      const int s0 = ctx->h_lists[off + 2 * t + 1];
+      const double rows = std::min(rb, (over_m ? d.m : d.k) - s0);
+      const double other = over_m ? d.k : d.m;
+      *fl += 8.0 * rows * other * nsys;
+      *by += es * rows * (other + 1) * nsys;
     }
+    (void)sl;
   };
   const int* dl = ctx->d_lists;
   for (int l = 0; l < p.n_levels; ++l) {
@@ -545,10 +567,10 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
     tri_work(sl, !transpose, &fl, &by);
     {
       Prof pr(ctx, transpose ? PK_SWEEP_UT : PK_SWEEP_L, fl, by);
-      launch_sweep_tri<T>(sa, fwd, dl + sl.off, sl.nf, sl.nmax, in, out, s);
+      launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, s);
     }
     if (sl.nmt > 0) {
-      rect_work(sl, &fl, &by);
+      rect_work(sl, sl.mt_off, sl.nmt, true, &fl, &by);
       Prof pr(ctx, PK_SWEEP_RECT, fl, by);
       launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.mt_off), sl.nmt, sl.kbig, out, s);
     }
@@ -557,13 +579,13 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
     const SolveList& sl = ctx->lv_solve[l];
     double fl, by;
     if (sl.nkt > 0) {
-      rect_work(sl, &fl, &by);
+      rect_work(sl, sl.kt_off, sl.nkt, false, &fl, &by);
       Prof pr(ctx, PK_SWEEP_RECT, fl, by);
       launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.kt_off), sl.nkt, sl.mbig, out, s);
     }
     tri_work(sl, transpose, &fl, &by);
     Prof pr(ctx, transpose ? PK_SWEEP_LT : PK_SWEEP_U, fl, by);
-    launch_sweep_tri<T>(sa, bwd, dl + sl.off, sl.nf, sl.nmax, in, out, s);
+    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, s);
   }
   CK(cudaGetLastError());
   ctx->sweeps += 1;
@@ -1112,6 +1134,8 @@ void sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out
   sa.store_stride = p.store_total;
   sa.perm = prec == 0 ? ctx->d_perm32 : ctx->d_perm64;
   sa.perm_stride = std::max(1, p.perm_total);
+  sa.istore = prec == 0 ? (const void*)ctx->d_inv32 : (const void*)ctx->d_inv64;
+  sa.istore_stride = p.inv_total;
   sa.vb = vb;
   sa.vec_stride = p.vec_total;
   sa.n_omega = ctx->n_omega;
@@ -1124,7 +1148,7 @@ void sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out
   const int* dl = ctx->d_lists;
   for (int l = 0; l < p.n_levels; ++l) {
     const SolveList& sl = ctx->lv_solve[l];
-    launch_sweep_tri<T>(sa, fwd, dl + sl.off, sl.nf, sl.nmax, in, out, ctx->stream);
+    launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, ctx->stream);
     if (sl.nmt > 0)
       launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.mt_off), sl.nmt, sl.kbig, out, ctx->stream);
   }
@@ -1132,7 +1156,7 @@ void sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out
     const SolveList& sl = ctx->lv_solve[l];
     if (sl.nkt > 0)
       launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.kt_off), sl.nkt, sl.mbig, out, ctx->stream);
-    launch_sweep_tri<T>(sa, bwd, dl + sl.off, sl.nf, sl.nmax, in, out, ctx->stream);
+    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, ctx->stream);
   }
 }
 

@@ -161,9 +161,37 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
     }
     __syncthreads();
   }
+  // Triangular inverses, one row of each per step: row i of L11^-1 (strictly
+  // lower, unit diagonal implied) from rows < i, and row k-1-i of U11^-1 (upper
+  // with diagonal) from rows > k-1-i.  The two never touch each other's entries.
+  T* X = S + n * n;
+  for (int i = 0; i < k; ++i) {
+    for (int j = tid; j < i; j += blockDim.x) {
+      T acc = S[i * n + j];
+      for (int l = j + 1; l < i; ++l) acc = cfma(S[i * n + l], X[l * k + j], acc);
+      X[i * k + j] = csub(czero<T>(), acc);
+    }
+    const int ii = k - 1 - i;
+    const T dinv = crcp(S[ii * n + ii]);
+    for (int j = ii + tid; j < k; j += blockDim.x) {
+      if (j == ii) {
+        X[ii * k + ii] = dinv;
+      } else {
+        T acc = czero<T>();
+        for (int l = ii + 1; l <= j; ++l) acc = cfma(S[ii * n + l], X[l * k + j], acc);
+        X[ii * k + j] = csub(czero<T>(), cmul(dinv, acc));
+      }
+    }
+    __syncthreads();
+  }
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
     F[(size_t)r * d.ld + c] = S[e];
+  }
+  T* Xg = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int r = e / k, c = e - r * k;
+    Xg[(size_t)r * d.ldk + c] = X[e];
   }
   int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   for (int i = tid; i < k; i += blockDim.x) P[i] = pm[i];
@@ -574,6 +602,107 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
   }
 }
 
+// Triangular inverses of a factored large front, written to the inverse store
+// (L11^-1 strictly below the diagonal, U11^-1 on and above it).  One CTA per
+// 32-column block of one triangle; it walks its column block one 32-row block
+// at a time: a product with the rows already inverted (read back from global
+// memory), then a substitution inside the diagonal block by one warp (lane =
+// column).  Different CTAs write disjoint entries.
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
+  __shared__ T Dg[32][33];
+  __shared__ T Acc[32][33];
+  const int w = blockIdx.z + a.w0;
+  const int f = flist[blockIdx.y];
+  const FrontDesc d = a.P.fronts[f];
+  const bool upper = (int)blockIdx.x >= nblk;
+  const int cb = (upper ? (int)blockIdx.x - nblk : (int)blockIdx.x) * 32;
+  const int k = d.k;
+  if (cb >= k) return;
+  const int ld = d.ld, ldk = d.ldk;
+  const int cw = min(32, k - cb);
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = cb + tx;
+  const T one = cmk(typename RealOf<T>::type(1), typename RealOf<T>::type(0));
+  if (!upper) {
+    // X[r][c] = delta_rc - sum_{l in [c, r)} L[r][l] X[l][c], X[c][c] = 1, X[l][c] = 0 for l < c
+    for (int rb = cb; rb < k; rb += 32) {
+      const int rh = min(32, k - rb);
+      for (int i = ty; i < rh; i += 8) {
+        const int r = rb + i;
+        T acc = czero<T>();
+        if (tx < cw) {
+          for (int l = cb; l < rb; ++l) {
+            const T xl = l > c ? X[(size_t)l * ldk + c] : (l == c ? one : czero<T>());
+            acc = cfma(F[(size_t)r * ld + l], xl, acc);
+          }
+        }
+        Acc[i][tx] = csub(r == c ? one : czero<T>(), acc);
+      }
+      for (int e = threadIdx.x; e < rh * 32; e += 256) {
+        const int i = e >> 5, j = e & 31;
+        if (j < rh) Dg[i][j] = F[(size_t)(rb + i) * ld + rb + j];
+      }
+      __syncthreads();
+      if (ty == 0 && tx < cw) {
+        T xc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          if (i < rh) {
+            T v = Acc[i][tx];
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < i) v = cfms(Dg[i][j], xc[j], v);
+            xc[i] = v;
+            if (rb + i > c) X[(size_t)(rb + i) * ldk + c] = v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    // X[r][c] = (delta_rc - sum_{l in (r, c]} U[r][l] X[l][c]) / U[r][r] for r <= c
+    for (int rb = cb; rb >= 0; rb -= 32) {
+      const int rh = min(32, k - rb);
+      for (int i = ty; i < rh; i += 8) {
+        const int r = rb + i;
+        T acc = czero<T>();
+        if (tx < cw)
+          for (int l = rb + 32; l <= c; ++l) acc = cfma(F[(size_t)r * ld + l], X[(size_t)l * ldk + c], acc);
+        Acc[i][tx] = csub(r == c ? one : czero<T>(), acc);
+      }
+      for (int e = threadIdx.x; e < rh * 32; e += 256) {
+        const int i = e >> 5, j = e & 31;
+        if (j < rh) Dg[i][j] = F[(size_t)(rb + i) * ld + rb + j];
+      }
+      __syncthreads();
+      if (ty == 0 && tx < cw) {
+        T xc[32];
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {
+          if (i < rh) {
+            const int r = rb + i;
+            T v = czero<T>();
+            if (r <= c) {
+              v = Acc[i][tx];
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j > i && j < rh && rb + j <= c) v = cfms(Dg[i][j], xc[j], v);
+              v = cmul(v, crcp(Dg[i][i]));
+              X[(size_t)r * ldk + c] = v;
+            }
+            xc[i] = v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Boundary rows of the panel: L21[:, j0:j0+nb] = A21[:, j0:j0+nb] U_jj^-1 (right
 // triangular solve with the panel's upper block), 64 rows per CTA.
 constexpr int kL21Rows = 64;
@@ -785,10 +914,12 @@ cudaError_t launch_growth_max(const float* growth, long long count, float* out, 
 }
 
 cudaError_t factor_init_attributes() {
+  // small fronts: the front plus its k x k inverse block (k <= n)
   cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 96 * 8);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 96 * 96 * 8);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
+  e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           2 * 64 * 64 * 16);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_panel_smem_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kPanelSmemBytes);
@@ -807,7 +938,7 @@ void launch_build(const FactorLaunch& a, const int2* tasks, int ntasks, cudaStre
 template <typename T>
 void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, cudaStream_t s) {
   if (nf <= 0) return;
-  const size_t smem = (size_t)nmax * nmax * sizeof(T);
+  const size_t smem = 2 * (size_t)nmax * nmax * sizeof(T);
   lu_small_kernel<T><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
 }
 
@@ -823,6 +954,13 @@ void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0, in
     lu_panel_smem_kernel<T><<<dim3(nf, a.n_omega), kPanelSmemThreads, smem, s>>>(a, flist, j0, nb);
   else
     lu_panel_kernel<T><<<dim3(nf, a.n_omega), kPanelThreads, 0, s>>>(a, flist, j0, nb);
+}
+
+template <typename T>
+void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s) {
+  if (nf <= 0 || kmax <= 0) return;
+  const int nblk = (kmax + 31) / 32;
+  lu_inv_kernel<T><<<dim3(2 * nblk, nf, a.n_omega), 256, 0, s>>>(a, flist, nblk);
 }
 
 template <typename T>
@@ -857,6 +995,7 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
   template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, cudaStream_t); \
+  template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t);
 FDFD_INST(float2)

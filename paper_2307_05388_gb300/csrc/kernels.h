@@ -27,7 +27,12 @@ struct FactorLaunch {
   int w0;
   int* swp;                // panel row-swap scratch: [n_omega launched][swp_stride][130]
   int swp_stride;          // >= number of fronts in one large-front list
+  void* istore;            // triangular inverses (same type as store), [n_omega][istore_stride]
+  long long istore_stride;
 };
+// L11^-1 (strictly lower part) and U11^-1 (upper part) of the listed large fronts,
+// one CTA per (front, 32-column block, triangle); kmax = largest k listed.
+template <typename T> void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s);
 // max over growth[0..count) (NaN wins) into *out
 cudaError_t launch_growth_max(const float* growth, long long count, float* out, cudaStream_t s);
 // build (assemble originals + extend-add children) rows listed in tasks (front, row0)
@@ -58,6 +63,8 @@ struct SolveLaunch {
   long long store_stride;
   const int* perm;
   int perm_stride;
+  const void* istore;      // triangular inverses (T), [n_omega][istore_stride]
+  long long istore_stride;
   void* vb;                // front vectors (T), [n_sys][vec_stride]
   long long vec_stride;
   int n_omega, nrhs;       // wavelengths launched [w0, w0 + n_omega); nrhs = layout stride
@@ -67,10 +74,10 @@ struct SolveLaunch {
 // sweep: 0 = L (forward, non-transposed), 1 = U (backward, non-transposed),
 //        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
 // in: right-hand side (sweeps 0, 2) [n_sys][n]; out: solution (sweeps 1, 3) [n_sys][n].
-// Triangular part, one CTA per listed front (bit 31 of an entry marks a front
-// whose off-diagonal block is left to launch_sweep_rect).  nmax: largest front.
-template <typename T> void launch_sweep_tri(const SolveLaunch& a, int sweep, const int* flist, int nf,
-                                            int nmax, const void* in, void* out, cudaStream_t s);
+// Products with the stored triangular inverses, tasks = (front, first row or
+// column of the k range) in blocks of sweep_rect_block(); kmax: largest k listed.
+template <typename T> void launch_sweep_tri(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,
+                                            int kmax, const void* in, void* out, cudaStream_t s);
 // Off-diagonal block of large fronts, tasks = (front, first row/column), blocks
 // of sweep_rect_block(); vmax: largest vector the tasks multiply (k or m).
 template <typename T> void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,

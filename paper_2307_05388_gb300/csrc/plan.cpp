@@ -175,11 +175,14 @@ std::string build_plan(int nx, int ny, int bx0, int by0, int bw, int bh, int lea
     d.level = lv;
   }
   // index lists, offsets
-  long long st = 0, vo = 0;
+  long long st = 0, vo = 0, iv = 0;
   int io = 0, po = 0;
   for (int f = 0; f < nn; ++f) {
     FrontDesc& d = p.fronts[f];
     const Node& nd = B.nodes[order[f]];
+    d.ldk = (int)round_up(d.k, 4);
+    d.iv_off = iv;
+    iv += round_up((long long)d.k * d.ldk, 64);
     d.idx_off = io;
     for (int c : nd.piv) p.idx.push_back(c);
     for (int c : bnd[f]) p.idx.push_back(c);
@@ -193,6 +196,7 @@ std::string build_plan(int nx, int ny, int bx0, int by0, int bw, int bh, int lea
     p.max_front = std::max(p.max_front, d.n);
   }
   p.store_total = st;
+  p.inv_total = iv;
   p.vec_total = vo;
   p.perm_total = po;
 

@@ -36,7 +36,8 @@ struct FrontDesc {           // plain-old-data, uploaded to the device as is
   int nchild;
   int level;                 // 0 for leaves; parent level > child level
   int design;                // 1 if the subtree holds a design pixel (refactored on design change)
-  int pad;
+  int ldk;                   // row stride of the k x k inverse block (k rounded up to 4)
+  long long iv_off;          // element offset of the inverse block (L11^-1 strictly lower, U11^-1 upper)
 };
 
 struct Plan {
@@ -54,6 +55,7 @@ struct Plan {
   int n_levels = 0;
   std::vector<std::vector<int>> level_fronts;  // front ids per level
   long long store_total = 0;          // elements of front storage per omega
+  long long inv_total = 0;            // elements of the triangular-inverse storage per omega
   long long vec_total = 0;            // elements of front vectors per RHS per omega
   int perm_total = 0;
   double flops_factor = 0;            // complex LU flops (8 real flops per complex FMA)

@@ -3,24 +3,24 @@
 // (transpose) solve A^T x = b reuses the same factors as U^T then L^T, so no
 // second factorisation is needed (the first caching idea of Sec. II).
 //
-// Per front, with the factored front [L11\U11 U12; L21 S] and row permutation P:
-//   L   : y = L11^-1 (P v)_k,          u = v_m - L21 y
-//   U   : x_k = U11^-1 (y - U12 x_m)
-//   U^T : w = U11^-T v_k,              u = v_m - U12^T w
-//   L^T : x_k = P^T L11^-T (w - L21^T x_m)
+// Per front, with the factored front [L11\U11 U12; L21 S], its row permutation
+// P and the triangular inverses X_L = L11^-1, X_U = U11^-1 stored at
+// factorisation time:
+//   L   : y = X_L (P v)_k,                 u = v_m - L21 y
+//   U   : x_k = X_U (y - U12 x_m)
+//   U^T : w = X_U^T v_k,                   u = v_m - U12^T w
+//   L^T : x_k = P^T X_L^T (w - L21^T x_m)
 // where v gathers the front's entries of the right-hand side plus the update
 // vectors u of its children (through the same inverse extend-add maps as the
-// factorisation), and x_m are the already final values of the boundary
+// factorisation) and x_m are the already final values of the boundary
 // variables.  Levels run bottom-up for L / U^T and top-down for U / L^T.
 //
-// Work split per level: a triangular kernel (one CTA per front and system)
-// does the gather and the dense triangular solve; for large fronts the
-// rectangular products (L21 y, U12 x_m, U12^T w, L21^T x_m) are split over
-// many CTAs of a second kernel, 32 rows or 32 columns each, so that the big
-// fronts at the top of the tree stream their factor with the whole GPU.
-// Every factor read is coalesced along a row of the row-major front and each
-// factor entry is read once per right-hand side; reductions run in a fixed
-// order (deterministic results).
+// With the inverses every step is a matrix-vector product, so each front is
+// cut into tasks of 32 rows (or 32 columns) of its k x k inverse block
+// ("tri" launch) and of its off-diagonal block ("rect" launch), and the whole
+// GPU streams the factor with no sequential substitution chain.  Every factor
+// read is coalesced along a row, each factor entry is read once per
+// right-hand side, and reductions run in a fixed order (deterministic).
 #include "kernels.h"
 
 namespace fdfd {
@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRect = 32;           // rows (or columns) per rectangular task
+constexpr int kBlk = 32;            // rows (or columns) per task
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -40,16 +40,9 @@ __device__ __forceinline__ T warp_sum(T v) {
   }
   return v;
 }
-template <typename T>
-__device__ __forceinline__ T shfl(T v, int src) {
-  v.x = __shfl_sync(0xffffffffu, v.x, src);
-  v.y = __shfl_sync(0xffffffffu, v.y, src);
-  return v;
-}
 
 // sum_{c in [c0, c1)} row[c] * vec[c], lanes striding the row (coalesced), warp-reduced.
-// Eight loads per lane are issued before they are used, so that a single
-// front's row keeps enough bytes in flight to cover the memory latency.
+// Eight loads per lane are issued before they are used.
 template <typename T>
 __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, int c0, int c1, int lane) {
   constexpr int UN = 8;
@@ -66,213 +59,122 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, i
   return warp_sum(cadd(acc[0], acc[1]));
 }
 
-// vs[c] -= sum_{bb < bs} F[(kb + bb) * ld + c] * vs[kb + bb]: one column per thread,
-// loads issued eight at a time ahead of their multiply-adds.
-template <typename T>
-__device__ __forceinline__ void col_update(const T* __restrict__ F, int ld, int kb, int bs, int c, T* vs) {
-  constexpr int UN = 8;
-  T a0 = vs[c], a1 = czero<T>();
-  int bb = 0;
-  for (; bb + UN <= bs; bb += UN) {
-    T f[UN];
+// Column block product: lane = column, warps split the rows [r0, r1) of a
+// row-major block with stride ld; column c = c0 + lane uses only rows r with
+// lo(c) <= r < hi(c) (triangle masks).  Returns the per-lane column sum,
+// reduced over warps in a fixed order (valid in warp 0).
+template <typename T, typename Mask>
+__device__ __forceinline__ T col_dot(const T* __restrict__ base, int ld, const T* vec, int r0, int r1,
+                                     bool live, Mask inside, T (*red)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int UN = 4;
+  T a0 = czero<T>(), a1 = czero<T>();
+  if (live) {
+    int r = r0 + warp;
+    for (; r + (UN - 1) * kWarps < r1; r += UN * kWarps) {
+      T f[UN];
 #pragma unroll
-    for (int u = 0; u < UN; ++u) f[u] = F[(size_t)(kb + bb + u) * ld + c];
+      for (int u = 0; u < UN; ++u) f[u] = base[(size_t)(r + u * kWarps) * ld];
 #pragma unroll
-    for (int u = 0; u < UN; u += 2) {
-      a0 = cfms(f[u], vs[kb + bb + u], a0);
-      a1 = cfms(f[u + 1], vs[kb + bb + u + 1], a1);
+      for (int u = 0; u < UN; ++u)
+        if (inside(r + u * kWarps)) {
+          if (u & 1) a1 = cfma(f[u], vec[r + u * kWarps], a1);
+          else a0 = cfma(f[u], vec[r + u * kWarps], a0);
+        }
     }
+    for (; r < r1; r += kWarps)
+      if (inside(r)) a0 = cfma(base[(size_t)r * ld], vec[r], a0);
   }
-  for (; bb < bs; ++bb) a0 = cfms(F[(size_t)(kb + bb) * ld + c], vs[kb + bb], a0);
-  vs[c] = cadd(a0, a1);
+  red[warp][lane] = cadd(a0, a1);
+  __syncthreads();
+  T s = red[0][lane];
+  if (warp == 0)
+    for (int q = 1; q < kWarps; ++q) s = cadd(s, red[q][lane]);
+  return s;
 }
 
-// v[s] for s < n: rhs entry (pivot rows only) plus the children's update vectors.
+// Right-hand side entries of the front's pivot rows plus the children's
+// update vectors, for local slots s (permuted through P when asked).
 template <typename T>
-__device__ __forceinline__ void gather_front(const SolveLaunch& a, const FrontDesc& d, const T* rhs,
-                                             const T* vbs, const int* Pm, bool permute, T* vs) {
-  const int* idx = a.P.idx + d.idx_off;
-  for (int s = threadIdx.x; s < d.n; s += blockDim.x) {
-    const int src = (permute && s < d.k) ? Pm[s] : s;
-    T v = src < d.k ? rhs[idx[src]] : czero<T>();
-    for (int ci = 0; ci < d.nchild; ++ci) {
-      const FrontDesc c = a.P.fronts[a.P.children[d.child0 + ci]];
-      const int t = a.P.inv[c.inv_off + src];
-      if (t >= 0) v = cadd(v, vbs[c.v_off + c.k + t]);
-    }
-    vs[s] = v;
+__device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& d, const T* rhs, const T* vbs,
+                                         int src) {
+  T v = (rhs && src < d.k) ? rhs[a.P.idx[d.idx_off + src]] : czero<T>();
+  for (int ci = 0; ci < d.nchild; ++ci) {
+    const FrontDesc c = a.P.fronts[a.P.children[d.child0 + ci]];
+    const int t = a.P.inv[c.inv_off + src];
+    if (t >= 0) v = cadd(v, vbs[c.v_off + c.k + t]);
   }
+  return v;
 }
 
 // ---------------------------------------------------------------------------
-// Triangular part (and, for small fronts, the whole front).
-// list entries: front id, with bit 31 set when a rectangular task list covers
-// the front's off-diagonal block.
+// Inverse-block products; task = (front, first row or column of the k range).
+//   SWEEP 0: rows r:    y[r]  = (P v)_r + sum_{b<r} X_L[r][b] (P v)_b
+//   SWEEP 1: rows a:    x[a]  = sum_{b>=a} X_U[a][b] z[b]          (z = vf[0..k))
+//   SWEEP 2: cols a:    w[a]  = sum_{b<=a} X_U[b][a] v_b
+//   SWEEP 3: cols a:    q[a]  = t[a] + sum_{b>a} X_L[b][a] t[b]    (t = vf[0..k)), x[P a] = q[a]
 // ---------------------------------------------------------------------------
 template <typename T, int SWEEP>
 __global__ void __launch_bounds__(kThreads)
-tri_kernel(SolveLaunch a, const int* __restrict__ flist, const T* __restrict__ in, T* __restrict__ out) {
+tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ in, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T Ds[32][33];
+  __shared__ T red[kWarps][32];
   T* vs = reinterpret_cast<T*>(smem_raw);
   const int w = blockIdx.y + a.w0;
-  const int entry = flist[blockIdx.x];
-  const bool big = entry < 0;
-  const int f = entry & 0x7fffffff;
-  const FrontDesc d = a.P.fronts[f];
-  const int n = d.n, k = d.k, m = d.m, ld = d.ld;
+  const int2 task = tasks[blockIdx.x];
+  const FrontDesc d = a.P.fronts[task.x];
+  const int k = d.k, ldk = d.ldk;
+  const int b0 = task.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   const int* idx = a.P.idx + d.idx_off;
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
-    if (SWEEP == 0) {
-      // ---- L: y = L11^-1 (P v)_k; small fronts also u = v_m - L21 y ---------------
-      gather_front(a, d, in + sys * a.n, vbs, Pm, true, vs);
-      __syncthreads();
-      for (int kb = 0; kb < k; kb += 32) {
-        const int bs = min(32, k - kb);
-        for (int e = tid; e < bs * 32; e += kThreads) {
-          const int i = e >> 5, j = e & 31;
-          if (j < bs) Ds[i][j] = F[(size_t)(kb + i) * ld + kb + j];
-        }
-        for (int rr = warp; rr < bs; rr += kWarps) {
-          const T acc = warp_dot(F + (size_t)(kb + rr) * ld, vs, 0, kb, lane);
-          if (lane == 0) vs[kb + rr] = csub(vs[kb + rr], acc);
-        }
-        __syncthreads();
-        if (warp == 0) {
-          T yi = lane < bs ? vs[kb + lane] : czero<T>();
-          for (int jj = 0; jj < bs - 1; ++jj) {
-            const T yj = shfl(yi, jj);
-            if (lane > jj && lane < bs) yi = cfms(Ds[lane][jj], yj, yi);
-          }
-          if (lane < bs) vs[kb + lane] = yi;
-        }
-        __syncthreads();
-      }
-      if (!big) {
-        for (int t = warp; t < m; t += kWarps) {
-          const T acc = warp_dot(F + (size_t)(k + t) * ld, vs, 0, k, lane);
-          if (lane == 0) vs[k + t] = csub(vs[k + t], acc);
-        }
-        __syncthreads();
-      }
-      for (int s = tid; s < n; s += kThreads) vf[s] = vs[s];
-    } else if (SWEEP == 1) {
-      // ---- U: x_k = U11^-1 (y - U12 x_m); big fronts had U12 x_m subtracted --------
-      T* xo = out + sys * a.n;
-      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
-      if (!big)
-        for (int t = tid; t < m; t += kThreads) vs[k + t] = xo[idx[k + t]];
-      __syncthreads();
-      if (!big) {
-        for (int row = warp; row < k; row += kWarps) {
-          const T acc = warp_dot(F + (size_t)row * ld, vs, k, n, lane);
-          if (lane == 0) vs[row] = csub(vs[row], acc);
-        }
-        __syncthreads();
-      }
-      for (int kb = ((k - 1) / 32) * 32; kb >= 0; kb -= 32) {
-        const int bs = min(32, k - kb);
-        for (int e = tid; e < bs * 32; e += kThreads) {
-          const int i = e >> 5, j = e & 31;
-          if (j < bs) Ds[i][j] = F[(size_t)(kb + i) * ld + kb + j];
-        }
-        for (int rr = warp; rr < bs; rr += kWarps) {
-          const T acc = warp_dot(F + (size_t)(kb + rr) * ld, vs, kb + bs, k, lane);
-          if (lane == 0) vs[kb + rr] = csub(vs[kb + rr], acc);
-        }
-        __syncthreads();
-        if (warp == 0) {
-          T zi = lane < bs ? vs[kb + lane] : czero<T>();
-          const T dj = lane < bs ? crcp(Ds[lane][lane]) : czero<T>();
-          for (int jj = bs - 1; jj >= 0; --jj) {
-            if (lane == jj) zi = cmul(zi, dj);
-            const T xj = shfl(zi, jj);
-            if (lane < jj) zi = cfms(Ds[lane][jj], xj, zi);
-          }
-          if (lane < bs) vs[kb + lane] = zi;
-        }
-        __syncthreads();
-      }
-      for (int s = tid; s < k; s += kThreads) xo[idx[s]] = vs[s];
-    } else if (SWEEP == 2) {
-      // ---- U^T: w = U11^-T v_k; small fronts also u = v_m - U12^T w ---------------
-      gather_front(a, d, in + sys * a.n, vbs, Pm, false, vs);
-      __syncthreads();
-      const int cend = big ? k : n;
-      for (int kb = 0; kb < k; kb += 32) {
-        const int bs = min(32, k - kb);
-        if (warp == 0) {
-          // stage the diagonal block (row by row, coalesced) so the dependent chain
-          // below touches only shared memory and registers
-          for (int i = 0; i < bs; ++i)
-            if (lane < bs) Ds[i][lane] = F[(size_t)(kb + i) * ld + kb + lane];
-          __syncwarp();
-          const T dj = lane < bs ? crcp(Ds[lane][lane]) : czero<T>();
-          T wi = lane < bs ? vs[kb + lane] : czero<T>();
-          for (int bb = 0; bb < bs; ++bb) {
-            if (lane == bb) wi = cmul(wi, dj);
-            const T wb = shfl(wi, bb);
-            if (lane > bb && lane < bs) wi = cfms(Ds[bb][lane], wb, wi);
-          }
-          if (lane < bs) vs[kb + lane] = wi;
-          __syncwarp();
-        }
-        __syncthreads();
-        for (int c = kb + bs + tid; c < cend; c += kThreads) col_update(F, ld, kb, bs, c, vs);
-        __syncthreads();
-      }
-      for (int s = tid; s < n; s += kThreads) vf[s] = vs[s];
+    if (SWEEP == 0 || SWEEP == 2) {
+      const T* rhs = in + sys * a.n;
+      for (int s = tid; s < k; s += kThreads) vs[s] = gather_slot(a, d, rhs, vbs, SWEEP == 0 ? Pm[s] : s);
     } else {
-      // ---- L^T: x_k = P^T L11^-T (w - L21^T x_m); big fronts had L21^T x_m subtracted --
-      T* xo = out + sys * a.n;
       for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
-      if (!big)
-        for (int t = tid; t < m; t += kThreads) vs[k + t] = xo[idx[k + t]];
-      __syncthreads();
-      if (!big) {
-        for (int c = tid; c < k; c += kThreads) {
-          T acc = vs[c];
-          for (int t = 0; t < m; ++t) acc = cfms(F[(size_t)(k + t) * ld + c], vs[k + t], acc);
-          vs[c] = acc;
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    if (SWEEP == 0) {
+      for (int rr = warp; rr < kBlk; rr += kWarps) {
+        const int row = b0 + rr;
+        if (row >= k) break;
+        const T acc = warp_dot(X + (size_t)row * ldk, vs, 0, row, lane);
+        if (lane == 0) vf[row] = cadd(vs[row], acc);
       }
-      for (int kb = ((k - 1) / 32) * 32; kb >= 0; kb -= 32) {
-        const int bs = min(32, k - kb);
-        if (warp == 0) {
-          for (int i = 0; i < bs; ++i)
-            if (lane < bs) Ds[i][lane] = F[(size_t)(kb + i) * ld + kb + lane];
-          __syncwarp();
-          T qi = lane < bs ? vs[kb + lane] : czero<T>();
-          for (int bb = bs - 1; bb > 0; --bb) {
-            const T qb = shfl(qi, bb);
-            if (lane < bb) qi = cfms(Ds[bb][lane], qb, qi);
-          }
-          if (lane < bs) vs[kb + lane] = qi;
-          __syncwarp();
-        }
-        __syncthreads();
-        for (int c = tid; c < kb; c += kThreads) col_update(F, ld, kb, bs, c, vs);
-        __syncthreads();
+    } else if (SWEEP == 1) {
+      T* xo = out + sys * a.n;
+      for (int rr = warp; rr < kBlk; rr += kWarps) {
+        const int row = b0 + rr;
+        if (row >= k) break;
+        const T acc = warp_dot(X + (size_t)row * ldk, vs, row, k, lane);
+        if (lane == 0) xo[idx[row]] = acc;
       }
-      for (int s = tid; s < k; s += kThreads) xo[idx[Pm[s]]] = vs[s];
+    } else if (SWEEP == 2) {
+      const int c = b0 + lane;
+      const T s = col_dot(X + c, ldk, vs, 0, min(b0 + kBlk, k), c < k, [&](int b) { return b <= c; }, red);
+      if (warp == 0 && c < k) vf[c] = s;
+    } else {
+      const int c = b0 + lane;
+      T* xo = out + sys * a.n;
+      const T s = col_dot(X + c, ldk, vs, b0 + 1, k, c < k, [&](int b) { return b > c; }, red);
+      if (warp == 0 && c < k) xo[idx[Pm[c]]] = cadd(vs[c], s);
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// Rectangular part of large fronts; task = (front, first row or column).
-//   SWEEP 0: rows t of L21:   u[t]  = v[k+t] - L21[t,:] y        (y = vf[0..k))
-//   SWEEP 1: rows a of U12:   z[a]  = y[a]   - U12[a,:] x_m      (x_m gathered from out)
-//   SWEEP 2: cols t of U12:   u[t]  = v[k+t] - U12[:,t]^T w      (w = vf[0..k))
-//   SWEEP 3: cols a of L21:   q[a]  = w[a]   - L21[:,a]^T x_m
+// Off-diagonal blocks; task = (front, first row or column).
+//   SWEEP 0: rows t of L21:   u[t] = g_t - L21[t,:] y          (g_t gathered, y = vf[0..k))
+//   SWEEP 1: rows a of U12:   z[a] = y[a] - U12[a,:] x_m       (x_m gathered from out)
+//   SWEEP 2: cols t of U12:   u[t] = g_t - U12[:,t]^T w        (w = vf[0..k))
+//   SWEEP 3: cols a of L21:   t[a] = w[a] - L21[:,a]^T x_m
 // ---------------------------------------------------------------------------
 template <typename T, int SWEEP>
 __global__ void __launch_bounds__(kThreads)
@@ -283,16 +185,16 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
   const int w = blockIdx.y + a.w0;
   const int2 task = tasks[blockIdx.x];
   const FrontDesc d = a.P.fronts[task.x];
-  const int k = d.k, m = d.m, n = d.n, ld = d.ld;
+  const int k = d.k, m = d.m, ld = d.ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int* idx = a.P.idx + d.idx_off;
   const int s0 = task.y;
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
-    T* vf = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride + d.v_off;
+    T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
+    T* vf = vbs + d.v_off;
     const T* xo = out + sys * a.n;
-    // the vector the block multiplies: y / w (forward) or x_m (backward)
     if (SWEEP == 0 || SWEEP == 2) {
       for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
     } else {
@@ -300,49 +202,27 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
     }
     __syncthreads();
     if (SWEEP == 0 || SWEEP == 1) {
-      const int rows = SWEEP == 0 ? m : k;
-      for (int rr = warp; rr < kRect; rr += kWarps) {
+      for (int rr = warp; rr < kBlk; rr += kWarps) {
         const int row = s0 + rr;
-        if (row >= rows) break;
+        if (row >= (SWEEP == 0 ? m : k)) break;
         const T* Frow = SWEEP == 0 ? F + (size_t)(k + row) * ld : F + (size_t)row * ld + k;
         const T acc = warp_dot(Frow, vs, 0, SWEEP == 0 ? k : m, lane);
         if (lane == 0) {
-          const int slot = SWEEP == 0 ? k + row : row;
-          vf[slot] = csub(vf[slot], acc);
+          if (SWEEP == 0) vf[k + row] = csub(gather_slot(a, d, (const T*)nullptr, vbs, k + row), acc);
+          else vf[row] = csub(vf[row], acc);
         }
       }
     } else {
-      // column block: lane = column, warps split the rows, fixed-order reduction
       const int cols = SWEEP == 2 ? m : k;
       const int rows = SWEEP == 2 ? k : m;
       const int c = s0 + lane;
-      T a0 = czero<T>(), a1 = czero<T>();
-      if (c < cols) {
-        constexpr int UN = 8;
-        const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
-        int i = warp;
-        for (; i + (UN - 1) * kWarps < rows; i += UN * kWarps) {
-          T fr[UN];
-#pragma unroll
-          for (int u = 0; u < UN; ++u) fr[u] = base[(size_t)(i + u * kWarps) * ld];
-#pragma unroll
-          for (int u = 0; u < UN; u += 2) {
-            a0 = cfma(fr[u], vs[i + u * kWarps], a0);
-            a1 = cfma(fr[u + 1], vs[i + (u + 1) * kWarps], a1);
-          }
-        }
-        for (; i < rows; i += kWarps) a0 = cfma(base[(size_t)i * ld], vs[i], a0);
-      }
-      red[warp][lane] = cadd(a0, a1);
-      __syncthreads();
+      const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
+      const T s = col_dot(base, ld, vs, 0, rows, c < cols, [](int) { return true; }, red);
       if (warp == 0 && c < cols) {
-        T s = red[0][lane];
-        for (int q = 1; q < kWarps; ++q) s = cadd(s, red[q][lane]);
-        const int slot = SWEEP == 2 ? k + c : c;
-        vf[slot] = csub(vf[slot], s);
+        if (SWEEP == 2) vf[k + c] = csub(gather_slot(a, d, (const T*)nullptr, vbs, k + c), s);
+        else vf[c] = csub(vf[c], s);
       }
     }
-    (void)n;
     __syncthreads();
   }
 }
@@ -350,18 +230,18 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
 }  // namespace
 
 template <typename T>
-void launch_sweep_tri(const SolveLaunch& a, int sweep, const int* flist, int nf, int nmax, const void* in,
+void launch_sweep_tri(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks, int kmax, const void* in,
                       void* out, cudaStream_t s) {
-  if (nf <= 0) return;
-  const size_t smem = (size_t)nmax * sizeof(T);
+  if (ntasks <= 0) return;
+  const size_t smem = (size_t)kmax * sizeof(T);
   const T* i = reinterpret_cast<const T*>(in);
   T* o = reinterpret_cast<T*>(out);
-  dim3 grid(nf, a.n_omega);
+  dim3 grid(ntasks, a.n_omega);
   switch (sweep) {
-    case 0: tri_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
-    case 1: tri_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
-    case 2: tri_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
-    default: tri_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, flist, i, o); break;
+    case 0: tri_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
+    case 1: tri_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
+    case 2: tri_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
+    default: tri_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
   }
 }
 
@@ -380,7 +260,7 @@ void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int n
   }
 }
 
-int sweep_rect_block() { return kRect; }
+int sweep_rect_block() { return kBlk; }
 
 cudaError_t solve_init_attributes() {
   const int lim = 160 * 1024;
@@ -397,9 +277,9 @@ cudaError_t solve_init_attributes() {
   return e;
 }
 
-template void launch_sweep_tri<float2>(const SolveLaunch&, int, const int*, int, int, const void*, void*,
+template void launch_sweep_tri<float2>(const SolveLaunch&, int, const int2*, int, int, const void*, void*,
                                        cudaStream_t);
-template void launch_sweep_tri<double2>(const SolveLaunch&, int, const int*, int, int, const void*, void*,
+template void launch_sweep_tri<double2>(const SolveLaunch&, int, const int2*, int, int, const void*, void*,
                                         cudaStream_t);
 template void launch_sweep_rect<float2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
 template void launch_sweep_rect<double2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
