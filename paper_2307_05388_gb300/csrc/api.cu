@@ -29,10 +29,17 @@ struct LevelList {
   int large_off = 0, nlarge = 0, nmax_large = 0, kmax_large = 0, mmax_large = 0;
 };
 
+struct TaskList {
+  int off = 0, n = 0;      // int2 (front, first row or column) tasks at d_lists + off
+};
+
+// Sweep tasks of one level; index 0 = row tasks (sweeps L, U), 1 = column tasks (U^T, L^T).
 struct SolveList {
-  int off = 0, nf = 0, nmax = 0, kmax = 0;       // inverse-block tasks (every front of the level)
-  int mt_off = 0, nmt = 0, kt_off = 0, nkt = 0;  // off-diagonal tasks (fronts with boundary rows)
-  int mbig = 0, kbig = 0;
+  TaskList tri[2];         // inverse-block products, every front of the level
+  TaskList rect_m[2];      // off-diagonal block split over the m boundary rows/columns
+  TaskList rect_k[2];      // off-diagonal block split over the k pivot rows/columns
+  int kmax = 0;            // largest k of the level
+  int kbig = 0, mbig = 0;  // largest k and m among fronts with boundary rows
 };
 
 template <typename P>
@@ -53,6 +60,12 @@ struct fdfd_ctx {
   fdfd_box box{};
   fdfd_options opt{};
   cudaStream_t stream = nullptr;
+  // CUDA graphs of fixed launch sequences (factorisations, sweep pairs on the
+  // internal buffers), captured on a private stream joined to `stream` by events
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  struct GraphEntry { int key; cudaGraphExec_t exec; };
+  std::vector<GraphEntry> graphs;
   std::string err;
   int device = -1;
 
@@ -206,7 +219,15 @@ void free_factor(fdfd_ctx* c) {
   c->valid32 = c->valid64 = false;
 }
 
+// Captured graphs bake in buffer addresses and plan lists: drop them whenever
+// either changes.
+void drop_graphs(fdfd_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
 void free_ws(fdfd_ctx* c) {
+  drop_graphs(c);
   free_ptr(c->d_vb); free_ptr(c->d_bT); free_ptr(c->d_xT);
   c->d_vb = c->d_bT = c->d_xT = nullptr;
   c->ws_nrhs = 0;
@@ -250,6 +271,7 @@ fdfd_status upload(fdfd_ctx* ctx, P** dst, const std::vector<P>& v) {
 // are kept alive by the context until the next upload, so the asynchronous
 // copies may still be in flight when this returns.
 fdfd_status upload_plan(fdfd_ctx* ctx) {
+  drop_graphs(ctx);
   if (ctx->uploaded) CK(cudaStreamSynchronize(ctx->stream));   // old plan may still be in use
   free_plan_device(ctx);
   const Plan& p = ctx->plan;
@@ -294,30 +316,32 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
     }
   }
   ctx->lv_solve.assign(L, SolveList{});
-  const int rb = sweep_rect_block();
+  // task lists (front, first row/column): [0] row tasks, [1] column tasks
+  auto add_tasks = [&](TaskList& tl, int l, bool need_m, bool over_m, int step) {
+    if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
+    tl.off = (int)lists.size();
+    for (int f : p.level_fronts[l]) {
+      const FrontDesc& d = p.fronts[f];
+      if (need_m && d.m == 0) continue;
+      const int len = over_m ? d.m : d.k;
+      for (int s0 = 0; s0 < len; s0 += step) { lists.push_back(f); lists.push_back(s0); tl.n++; }
+    }
+  };
+  const int steps[2] = {sweep_row_block(), sweep_col_block()};
   for (int l = 0; l < L; ++l) {
     SolveList& sl = ctx->lv_solve[l];
-    if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
-    sl.off = (int)lists.size();                 // inverse-block tasks of every front
+    for (int t = 0; t < 2; ++t) {
+      add_tasks(sl.tri[t], l, false, false, steps[t]);     // inverse blocks of every front
+      add_tasks(sl.rect_m[t], l, true, true, steps[t]);    // off-diagonal block, over boundary rows/cols
+      add_tasks(sl.rect_k[t], l, true, false, steps[t]);   // off-diagonal block, over pivot rows/cols
+    }
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
-      for (int b0 = 0; b0 < d.k; b0 += rb) { lists.push_back(f); lists.push_back(b0); sl.nf++; }
-      sl.nmax = std::max(sl.nmax, d.n);
       sl.kmax = std::max(sl.kmax, d.k);
-    }
-    sl.mt_off = (int)lists.size();              // off-diagonal tasks over the m boundary rows / columns
-    for (int f : p.level_fronts[l]) {
-      const FrontDesc& d = p.fronts[f];
-      if (d.m == 0) continue;
-      for (int t0 = 0; t0 < d.m; t0 += rb) { lists.push_back(f); lists.push_back(t0); sl.nmt++; }
-      sl.mbig = std::max(sl.mbig, d.m);
-      sl.kbig = std::max(sl.kbig, d.k);
-    }
-    sl.kt_off = (int)lists.size();              // off-diagonal tasks over the k pivot rows / columns
-    for (int f : p.level_fronts[l]) {
-      const FrontDesc& d = p.fronts[f];
-      if (d.m == 0) continue;
-      for (int a0 = 0; a0 < d.k; a0 += rb) { lists.push_back(f); lists.push_back(a0); sl.nkt++; }
+      if (d.m > 0) {
+        sl.mbig = std::max(sl.mbig, d.m);
+        sl.kbig = std::max(sl.kbig, d.k);
+      }
     }
   }
   ctx->h_lists.swap(lists);
@@ -531,71 +555,126 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   cudaStream_t s = ctx->stream;
   const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
   const double es = sizeof(T), nsys = (double)sa.n_omega * sa.nr;
-  const int rb = sweep_rect_block();
+  const int tt = transpose ? 1 : 0;                       // row tasks (L, U) or column tasks (U^T, L^T)
+  const int step = tt ? sweep_col_block() : sweep_row_block();
   // algorithmic work: every entry of the swept triangle (and of the off-diagonal
   // block) read once per right-hand side, 8 flops per entry, plus the vectors
-  auto tri_work = [&](const SolveList& sl, bool lower, double* fl, double* by) {
+  auto tri_work = [&](const TaskList& tl, bool lower, double* fl, double* by) {
     *fl = *by = 0;
     if (!ctx->prof_on) return;
-    for (int t = 0; t < sl.nf; ++t) {
-      const FrontDesc& d = p.fronts[ctx->h_lists[sl.off + 2 * t]];
-      const int b0 = ctx->h_lists[sl.off + 2 * t + 1];
-      const int b1 = std::min(d.k, b0 + rb);
+    for (int t = 0; t < tl.n; ++t) {
+      const FrontDesc& d = p.fronts[ctx->h_lists[tl.off + 2 * t]];
+      const int b0 = ctx->h_lists[tl.off + 2 * t + 1];
+      const int b1 = std::min(d.k, b0 + step);
       double ent = 0;   // entries of this task's rows (or columns) inside the triangle
       for (int r = b0; r < b1; ++r) ent += lower ? r : (d.k - r);
       *fl += 8.0 * ent * nsys;
       *by += es * (ent + (b1 - b0)) * nsys;
     }
   };
-  auto rect_work = [&](const SolveList& sl, int off, int cnt, bool over_m, double* fl, double* by) {
+  auto rect_work = [&](const TaskList& tl, bool over_m, double* fl, double* by) {
     *fl = *by = 0;
     if (!ctx->prof_on) return;
-    for (int t = 0; t < cnt; ++t) {
-      const FrontDesc& d = p.fronts[ctx->h_lists[off + 2 * t]];
-      const int s0 = ctx->h_lists[off + 2 * t + 1];
-      const double rows = std::min(rb, (over_m ? d.m : d.k) - s0);
+    for (int t = 0; t < tl.n; ++t) {
+      const FrontDesc& d = p.fronts[ctx->h_lists[tl.off + 2 * t]];
+      const int s0 = ctx->h_lists[tl.off + 2 * t + 1];
+      const double rows = std::min(step, (over_m ? d.m : d.k) - s0);
       const double other = over_m ? d.k : d.m;
       *fl += 8.0 * rows * other * nsys;
       *by += es * rows * (other + 1) * nsys;
     }
-    (void)sl;
   };
   const int* dl = ctx->d_lists;
   for (int l = 0; l < p.n_levels; ++l) {
     const SolveList& sl = ctx->lv_solve[l];
     double fl, by;
-    tri_work(sl, !transpose, &fl, &by);
+    tri_work(sl.tri[tt], !transpose, &fl, &by);
     {
       Prof pr(ctx, transpose ? PK_SWEEP_UT : PK_SWEEP_L, fl, by);
-      launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, s);
+      launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in,
+                          out, s);
     }
-    if (sl.nmt > 0) {
-      rect_work(sl, sl.mt_off, sl.nmt, true, &fl, &by);
+    if (sl.rect_m[tt].n > 0) {
+      rect_work(sl.rect_m[tt], true, &fl, &by);
       Prof pr(ctx, PK_SWEEP_RECT, fl, by);
-      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.mt_off), sl.nmt, sl.kbig, out, s);
+      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.rect_m[tt].off), sl.rect_m[tt].n,
+                           sl.kbig, out, s);
     }
   }
   for (int l = p.n_levels - 1; l >= 0; --l) {
     const SolveList& sl = ctx->lv_solve[l];
     double fl, by;
-    if (sl.nkt > 0) {
-      rect_work(sl, sl.kt_off, sl.nkt, false, &fl, &by);
+    if (sl.rect_k[tt].n > 0) {
+      rect_work(sl.rect_k[tt], false, &fl, &by);
       Prof pr(ctx, PK_SWEEP_RECT, fl, by);
-      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.kt_off), sl.nkt, sl.mbig, out, s);
+      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.rect_k[tt].off), sl.rect_k[tt].n,
+                           sl.mbig, out, s);
     }
-    tri_work(sl, transpose, &fl, &by);
+    tri_work(sl.tri[tt], transpose, &fl, &by);
     Prof pr(ctx, transpose ? PK_SWEEP_LT : PK_SWEEP_U, fl, by);
-    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, s);
+    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in,
+                        out, s);
   }
   CK(cudaGetLastError());
-  ctx->sweeps += 1;
   return FDFD_OK;
+}
+
+// Runs `body`, which issues its work on ctx->stream, as a CUDA graph keyed by
+// `key`: captured (on the private stream) the first time, replayed afterwards,
+// joined to the caller's stream by events.  While profiling, runs it directly
+// so that every launch keeps its own events.
+template <typename Body>
+fdfd_status run_graph(fdfd_ctx* ctx, int key, Body&& body) {
+  if (ctx->prof_on) return body();
+  if (!ctx->gstream) {
+    CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->gev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->gev_out, cudaEventDisableTiming));
+  }
+  cudaGraphExec_t exec = nullptr;
+  for (const auto& g : ctx->graphs)
+    if (g.key == key) exec = g.exec;
+  if (!exec) {
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->gstream;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+    fdfd_status st = FDFD_OK;
+    if (e == cudaSuccess) st = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->gstream, &g) : e;
+    ctx->stream = user;
+    if (st != FDFD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    CK(e);
+    CK(e2);
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    ctx->graphs.push_back({key, exec});
+  }
+  CK(cudaEventRecord(ctx->gev_in, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev_in, 0));
+  CK(cudaGraphLaunch(exec, ctx->gstream));
+  CK(cudaEventRecord(ctx->gev_out, ctx->gstream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->gev_out, 0));
+  return FDFD_OK;
+}
+
+// Full or design factorisation of every wavelength, replayed from a graph.
+template <typename T>
+fdfd_status factor_all(fdfd_ctx* ctx, bool design_only) {
+  CKS(ensure_store(ctx, sizeof(T) == 8 ? 0 : 1));      // allocations stay outside the capture
+  const int key = (sizeof(T) == 8 ? 0 : 2) + (design_only ? 1 : 0);
+  return run_graph(ctx, key, [&]() { return factor_levels<T>(ctx, design_only); });
 }
 
 // Applies the cached factors M^-1 to FP64 vectors: dst = M^-1 src (all systems).
 fdfd_status precond(fdfd_ctx* ctx, int nrhs, int transpose, const double2* src, double2* dst) {
   const long long N = n_cells(ctx);
   const int S = ctx->n_omega * nrhs;
+  ctx->sweeps += 1;
   if (ctx->valid64) {
     return sweeps<double2>(ctx, nrhs, transpose, src, dst);
   }
@@ -603,7 +682,9 @@ fdfd_status precond(fdfd_ctx* ctx, int nrhs, int transpose, const double2* src, 
     Prof pr(ctx, PK_CVT, 0, 24.0 * N * S);
     launch_cvt_from64<float2>(reinterpret_cast<float2*>(ctx->d_bT), src, nullptr, N, S, ctx->stream);
   }
-  CKS(sweeps<float2>(ctx, nrhs, transpose, ctx->d_bT, ctx->d_xT));
+  // the sweep pair always runs on the internal buffers, so one graph per (nrhs, transpose)
+  CKS(run_graph(ctx, 16 + 2 * nrhs + (transpose ? 1 : 0),
+                [&]() { return sweeps<float2>(ctx, nrhs, transpose, ctx->d_bT, ctx->d_xT); }));
   {
     Prof pr(ctx, PK_CVT, 0, 24.0 * N * S);
     launch_cvt_to64<float2>(dst, reinterpret_cast<const float2*>(ctx->d_xT), nullptr, N, S, ctx->stream);
@@ -863,11 +944,11 @@ fdfd_status fdfd_factor(fdfd_ctx* ctx, const double* eps_dev) {
   if (ctx->opt.mode == FDFD_MODE_PLAIN) return FDFD_OK;   // factorised inside every solve
   CKS(ensure_device(ctx));
   if (ctx->opt.mode == FDFD_MODE_F64) {
-    CKS(factor_levels<double2>(ctx, false));
+    CKS(factor_all<double2>(ctx, false));
     ctx->valid64 = true;
     ctx->growth_pending = false;
   } else {
-    CKS(factor_levels<float2>(ctx, false));
+    CKS(factor_all<float2>(ctx, false));
     ctx->valid32 = true;
     ctx->growth_pending = true;
   }
@@ -891,10 +972,10 @@ fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev) {
   CKS(ensure_device(ctx));
   if (ctx->opt.mode == FDFD_MODE_F64) {
     if (!ctx->valid64) return fail(ctx, FDFD_ERR_STATE, "no cached factorisation");
-    CKS(factor_levels<double2>(ctx, true));
+    CKS(factor_all<double2>(ctx, true));
   } else {
     if (!ctx->valid32) return fail(ctx, FDFD_ERR_STATE, "no cached factorisation");
-    CKS(factor_levels<float2>(ctx, true));
+    CKS(factor_all<float2>(ctx, true));
     ctx->valid64 = false;
     ctx->growth_pending = true;
   }
@@ -921,6 +1002,7 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
         CKS(factor_levels<double2>(ctx, false, w, 1));
         ctx->nf += 1;
         CKS(sweeps<double2>(ctx, nrhs, transpose, b, x, w, 1, r, 1));
+        ctx->sweeps += 1;
         ctx->bs += 1;
       }
     }
@@ -933,6 +1015,7 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
   ctx->bs += S;
   if (ctx->valid64 && (ctx->opt.mode == FDFD_MODE_F64)) {
     CKS(sweeps<double2>(ctx, nrhs, transpose, b, x));
+    ctx->sweeps += 1;
     ctx->last_iters = 0;
     return FDFD_OK;
   }
@@ -1089,6 +1172,13 @@ void fdfd_destroy(fdfd_ctx* ctx) {
                 ctx->d_growth_max};
   for (void* p : ps) free_ptr(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  drop_graphs(ctx);
+  if (ctx->gstream) {
+    cudaStreamSynchronize(ctx->gstream);
+    cudaStreamDestroy(ctx->gstream);
+    cudaEventDestroy(ctx->gev_in);
+    cudaEventDestroy(ctx->gev_out);
+  }
   if (ctx->h_growth_max) cudaFreeHost(ctx->h_growth_max);
   if (ctx->h_active) cudaFreeHost(ctx->h_active);
   if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
@@ -1145,18 +1235,23 @@ void sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out
   sa.nr = nrhs;
   sa.n = n_cells(ctx);
   const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
+  const int tt = transpose ? 1 : 0;
   const int* dl = ctx->d_lists;
   for (int l = 0; l < p.n_levels; ++l) {
     const SolveList& sl = ctx->lv_solve[l];
-    launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, ctx->stream);
-    if (sl.nmt > 0)
-      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.mt_off), sl.nmt, sl.kbig, out, ctx->stream);
+    launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in, out,
+                        ctx->stream);
+    if (sl.rect_m[tt].n > 0)
+      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.rect_m[tt].off), sl.rect_m[tt].n, sl.kbig,
+                           out, ctx->stream);
   }
   for (int l = p.n_levels - 1; l >= 0; --l) {
     const SolveList& sl = ctx->lv_solve[l];
-    if (sl.nkt > 0)
-      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.kt_off), sl.nkt, sl.mbig, out, ctx->stream);
-    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.off), sl.nf, sl.kmax, in, out, ctx->stream);
+    if (sl.rect_k[tt].n > 0)
+      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.rect_k[tt].off), sl.rect_k[tt].n, sl.mbig,
+                           out, ctx->stream);
+    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in, out,
+                        ctx->stream);
   }
 }
 

@@ -611,8 +611,14 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
 template <typename T>
 __global__ void __launch_bounds__(256)
 lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
-  __shared__ T Dg[32][33];
-  __shared__ T Acc[32][33];
+  // two 32 x 33 tiles: (Ls, Xs) during the products, then (Acc, Dg) for the
+  // diagonal block; every switch is separated by a barrier
+  __shared__ T tile0[32][33];
+  __shared__ T tile1[32][33];
+  T (&Ls)[32][33] = tile0;
+  T (&Acc)[32][33] = tile0;
+  T (&Xs)[32][33] = tile1;
+  T (&Dg)[32][33] = tile1;
   const int w = blockIdx.z + a.w0;
   const int f = flist[blockIdx.y];
   const FrontDesc d = a.P.fronts[f];
@@ -631,16 +637,27 @@ lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
     // X[r][c] = delta_rc - sum_{l in [c, r)} L[r][l] X[l][c], X[c][c] = 1, X[l][c] = 0 for l < c
     for (int rb = cb; rb < k; rb += 32) {
       const int rh = min(32, k - rb);
-      for (int i = ty; i < rh; i += 8) {
-        const int r = rb + i;
-        T acc = czero<T>();
-        if (tx < cw) {
-          for (int l = cb; l < rb; ++l) {
-            const T xl = l > c ? X[(size_t)l * ldk + c] : (l == c ? one : czero<T>());
-            acc = cfma(F[(size_t)r * ld + l], xl, acc);
-          }
+      T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+      for (int l0 = cb; l0 < rb; l0 += 32) {      // rows already inverted, 32 at a time via shared memory
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+          const int i = e >> 5, j = e & 31;
+          Ls[i][j] = (i < rh) ? F[(size_t)(rb + i) * ld + l0 + j] : czero<T>();
+          const int l = l0 + i, cc = cb + j;
+          Xs[i][j] = (j < cw) ? (l > cc ? X[(size_t)l * ldk + cc] : (l == cc ? one : czero<T>())) : czero<T>();
         }
-        Acc[i][tx] = csub(r == c ? one : czero<T>(), acc);
+        __syncthreads();
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+          const T xv = Xs[j][tx];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = cfma(Ls[ty + 8 * q][j], xv, acc[q]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = ty + 8 * q;
+        if (i < rh) Acc[i][tx] = csub(rb + i == c ? one : czero<T>(), acc[q]);
       }
       for (int e = threadIdx.x; e < rh * 32; e += 256) {
         const int i = e >> 5, j = e & 31;
@@ -667,12 +684,27 @@ lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
     // X[r][c] = (delta_rc - sum_{l in (r, c]} U[r][l] X[l][c]) / U[r][r] for r <= c
     for (int rb = cb; rb >= 0; rb -= 32) {
       const int rh = min(32, k - rb);
-      for (int i = ty; i < rh; i += 8) {
-        const int r = rb + i;
-        T acc = czero<T>();
-        if (tx < cw)
-          for (int l = rb + 32; l <= c; ++l) acc = cfma(F[(size_t)r * ld + l], X[(size_t)l * ldk + c], acc);
-        Acc[i][tx] = csub(r == c ? one : czero<T>(), acc);
+      T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+      for (int l0 = rb + 32; l0 < cb + cw; l0 += 32) {   // rows below, already inverted (l <= c)
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+          const int i = e >> 5, j = e & 31;
+          Ls[i][j] = (i < rh && l0 + j < k) ? F[(size_t)(rb + i) * ld + l0 + j] : czero<T>();
+          const int l = l0 + i, cc = cb + j;
+          Xs[i][j] = (j < cw && l < k && l <= cc) ? X[(size_t)l * ldk + cc] : czero<T>();
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+          const T xv = Xs[j][tx];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = cfma(Ls[ty + 8 * q][j], xv, acc[q]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = ty + 8 * q;
+        if (i < rh) Acc[i][tx] = csub(rb + i == c ? one : czero<T>(), acc[q]);
       }
       for (int e = threadIdx.x; e < rh * 32; e += 256) {
         const int i = e >> 5, j = e & 31;

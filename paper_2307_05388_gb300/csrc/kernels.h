@@ -75,14 +75,17 @@ struct SolveLaunch {
 //        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
 // in: right-hand side (sweeps 0, 2) [n_sys][n]; out: solution (sweeps 1, 3) [n_sys][n].
 // Products with the stored triangular inverses, tasks = (front, first row or
-// column of the k range) in blocks of sweep_rect_block(); kmax: largest k listed.
+// column of the k range); sweeps 0 and 1 take row tasks of sweep_row_block() rows,
+// sweeps 2 and 3 column tasks of sweep_col_block() columns; kmax: largest k listed.
 template <typename T> void launch_sweep_tri(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,
                                             int kmax, const void* in, void* out, cudaStream_t s);
 // Off-diagonal block of large fronts, tasks = (front, first row/column), blocks
-// of sweep_rect_block(); vmax: largest vector the tasks multiply (k or m).
+// (row tasks for sweeps 0 and 1, column tasks for 2 and 3); vmax: largest vector
+// the tasks multiply (k or m).
 template <typename T> void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,
                                              int vmax, void* out, cudaStream_t s);
-int sweep_rect_block();
+int sweep_row_block();
+int sweep_col_block();
 
 // ---- vec.cu: FP64 refinement, objective, gradient ---------------------------
 // y = A x (op = 0) or r = b - A x (op = 1), FP64 matrix-free stencil, all systems.

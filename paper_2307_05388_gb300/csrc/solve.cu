@@ -16,8 +16,9 @@
 // variables.  Levels run bottom-up for L / U^T and top-down for U / L^T.
 //
 // With the inverses every step is a matrix-vector product, so each front is
-// cut into tasks of 32 rows (or 32 columns) of its k x k inverse block
-// ("tri" launch) and of its off-diagonal block ("rect" launch), and the whole
+// cut into tasks of 8 rows (one per warp) or 32 columns (one per lane) of its
+// k x k inverse block ("tri" launch) and of its off-diagonal block ("rect"
+// launch), and the whole
 // GPU streams the factor with no sequential substitution chain.  Every factor
 // read is coalesced along a row, each factor entry is read once per
 // right-hand side, and reductions run in a fixed order (deterministic).
@@ -29,7 +30,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kBlk = 32;            // rows (or columns) per task
+constexpr int kRowBlk = kWarps;     // rows per row-type task (one per warp)
+constexpr int kColBlk = 32;         // columns per column-type task (one per lane)
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -141,7 +143,7 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
     }
     __syncthreads();
     if (SWEEP == 0) {
-      for (int rr = warp; rr < kBlk; rr += kWarps) {
+      for (int rr = warp; rr < kRowBlk; rr += kWarps) {
         const int row = b0 + rr;
         if (row >= k) break;
         const T acc = warp_dot(X + (size_t)row * ldk, vs, 0, row, lane);
@@ -149,7 +151,7 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
       }
     } else if (SWEEP == 1) {
       T* xo = out + sys * a.n;
-      for (int rr = warp; rr < kBlk; rr += kWarps) {
+      for (int rr = warp; rr < kRowBlk; rr += kWarps) {
         const int row = b0 + rr;
         if (row >= k) break;
         const T acc = warp_dot(X + (size_t)row * ldk, vs, row, k, lane);
@@ -157,7 +159,7 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
       }
     } else if (SWEEP == 2) {
       const int c = b0 + lane;
-      const T s = col_dot(X + c, ldk, vs, 0, min(b0 + kBlk, k), c < k, [&](int b) { return b <= c; }, red);
+      const T s = col_dot(X + c, ldk, vs, 0, min(b0 + kColBlk, k), c < k, [&](int b) { return b <= c; }, red);
       if (warp == 0 && c < k) vf[c] = s;
     } else {
       const int c = b0 + lane;
@@ -202,7 +204,7 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
     }
     __syncthreads();
     if (SWEEP == 0 || SWEEP == 1) {
-      for (int rr = warp; rr < kBlk; rr += kWarps) {
+      for (int rr = warp; rr < kRowBlk; rr += kWarps) {
         const int row = s0 + rr;
         if (row >= (SWEEP == 0 ? m : k)) break;
         const T* Frow = SWEEP == 0 ? F + (size_t)(k + row) * ld : F + (size_t)row * ld + k;
@@ -260,7 +262,8 @@ void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int n
   }
 }
 
-int sweep_rect_block() { return kBlk; }
+int sweep_row_block() { return kRowBlk; }
+int sweep_col_block() { return kColBlk; }
 
 cudaError_t solve_init_attributes() {
   const int lim = 160 * 1024;
