@@ -33,12 +33,15 @@ struct TaskList {
   int off = 0, n = 0;      // int2 (front, first row or column) tasks at d_lists + off
 };
 
+// Fronts up to this size are swept by one CTA each (no split into tasks).
+constexpr int kSolveWholeFront = 128;
+
 // Sweep tasks of one level; index 0 = row tasks (sweeps L, U), 1 = column tasks (U^T, L^T).
 struct SolveList {
   TaskList tri[2];         // inverse-block products, every front of the level
   TaskList rect_m[2];      // off-diagonal block split over the m boundary rows/columns
   TaskList rect_k[2];      // off-diagonal block split over the k pivot rows/columns
-  int kmax = 0;            // largest k of the level
+  int kmax = 0;            // shared-memory vector entries the tri launch needs
   int kbig = 0, mbig = 0;  // largest k and m among fronts with boundary rows
 };
 
@@ -316,13 +319,20 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
     }
   }
   ctx->lv_solve.assign(L, SolveList{});
-  // task lists (front, first row/column): [0] row tasks, [1] column tasks
-  auto add_tasks = [&](TaskList& tl, int l, bool need_m, bool over_m, int step) {
+  // task lists (front, first row/column): [0] row tasks, [1] column tasks.
+  // A small front is one whole-front task (front | bit 31); a large front is
+  // split into row or column tasks in both launches.
+  auto small = [](const FrontDesc& d) { return d.n <= kSolveWholeFront; };
+  auto add_tasks = [&](TaskList& tl, int l, bool rect, bool over_m, int step) {
     if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
     tl.off = (int)lists.size();
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
-      if (need_m && d.m == 0) continue;
+      if (small(d)) {
+        if (!rect) { lists.push_back((int)(0x80000000u | (unsigned)f)); lists.push_back(0); tl.n++; }
+        continue;
+      }
+      if (rect && d.m == 0) continue;
       const int len = over_m ? d.m : d.k;
       for (int s0 = 0; s0 < len; s0 += step) { lists.push_back(f); lists.push_back(s0); tl.n++; }
     }
@@ -331,14 +341,14 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   for (int l = 0; l < L; ++l) {
     SolveList& sl = ctx->lv_solve[l];
     for (int t = 0; t < 2; ++t) {
-      add_tasks(sl.tri[t], l, false, false, steps[t]);     // inverse blocks of every front
+      add_tasks(sl.tri[t], l, false, false, steps[t]);     // inverse blocks (whole small fronts)
       add_tasks(sl.rect_m[t], l, true, true, steps[t]);    // off-diagonal block, over boundary rows/cols
       add_tasks(sl.rect_k[t], l, true, false, steps[t]);   // off-diagonal block, over pivot rows/cols
     }
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
-      sl.kmax = std::max(sl.kmax, d.k);
-      if (d.m > 0) {
+      sl.kmax = std::max(sl.kmax, small(d) ? d.n + d.k : d.k);   // shared-memory vectors of the tri launch
+      if (!small(d) && d.m > 0) {
         sl.mbig = std::max(sl.mbig, d.m);
         sl.kbig = std::max(sl.kbig, d.k);
       }
@@ -563,11 +573,14 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
     *fl = *by = 0;
     if (!ctx->prof_on) return;
     for (int t = 0; t < tl.n; ++t) {
-      const FrontDesc& d = p.fronts[ctx->h_lists[tl.off + 2 * t]];
-      const int b0 = ctx->h_lists[tl.off + 2 * t + 1];
-      const int b1 = std::min(d.k, b0 + step);
+      const int e = ctx->h_lists[tl.off + 2 * t];
+      const FrontDesc& d = p.fronts[e & 0x7fffffff];
+      const bool whole = e < 0;
+      const int b0 = whole ? 0 : ctx->h_lists[tl.off + 2 * t + 1];
+      const int b1 = whole ? d.k : std::min(d.k, b0 + step);
       double ent = 0;   // entries of this task's rows (or columns) inside the triangle
       for (int r = b0; r < b1; ++r) ent += lower ? r : (d.k - r);
+      if (whole) ent += (double)d.k * d.m;   // whole-front tasks also do the off-diagonal block
       *fl += 8.0 * ent * nsys;
       *by += es * (ent + (b1 - b0)) * nsys;
     }

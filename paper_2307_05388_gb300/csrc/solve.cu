@@ -116,6 +116,85 @@ __device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& 
 //   SWEEP 2: cols a:    w[a]  = sum_{b<=a} X_U[b][a] v_b
 //   SWEEP 3: cols a:    q[a]  = t[a] + sum_{b>a} X_L[b][a] t[b]    (t = vf[0..k)), x[P a] = q[a]
 // ---------------------------------------------------------------------------
+// A task whose front index has bit 31 set covers a whole small front: one CTA
+// does the inverse-block and the off-diagonal products (no rectangular tasks).
+template <typename T, int SWEEP>
+__device__ __forceinline__ void whole_front(const SolveLaunch& a, const FrontDesc& d, int w, const T* __restrict__ in,
+                                            T* __restrict__ out, T* vs, T (*red)[32]) {
+  const int k = d.k, m = d.m, n = d.n, ldk = d.ldk, ld = d.ld;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int* idx = a.P.idx + d.idx_off;
+  T* ws = vs + n;                                  // second vector: k entries
+  for (int r = a.r0; r < a.r0 + a.nr; ++r) {
+    const size_t sys = (size_t)w * a.nrhs + r;
+    T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
+    T* vf = vbs + d.v_off;
+    T* xo = out + sys * a.n;
+    if (SWEEP == 0 || SWEEP == 2) {
+      const T* rhs = in + sys * a.n;
+      for (int s = tid; s < n; s += kThreads)
+        vs[s] = gather_slot(a, d, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
+    } else {
+      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
+      for (int t = tid; t < m; t += kThreads) vs[k + t] = xo[idx[k + t]];
+    }
+    __syncthreads();
+    if (SWEEP == 0) {                              // y = X_L (P v)_k;  u = v_m - L21 y
+      for (int row = warp; row < k; row += kWarps) {
+        const T acc = warp_dot(X + (size_t)row * ldk, vs, 0, row, lane);
+        if (lane == 0) ws[row] = cadd(vs[row], acc);
+      }
+      __syncthreads();
+      for (int t = warp; t < m; t += kWarps) {
+        const T acc = warp_dot(F + (size_t)(k + t) * ld, ws, 0, k, lane);
+        if (lane == 0) vf[k + t] = csub(vs[k + t], acc);
+      }
+      for (int s = tid; s < k; s += kThreads) vf[s] = ws[s];
+    } else if (SWEEP == 1) {                       // z = y - U12 x_m;  x_k = X_U z
+      for (int row = warp; row < k; row += kWarps) {
+        const T acc = warp_dot(F + (size_t)row * ld + k, vs + k, 0, m, lane);
+        if (lane == 0) ws[row] = csub(vs[row], acc);
+      }
+      __syncthreads();
+      for (int row = warp; row < k; row += kWarps) {
+        const T acc = warp_dot(X + (size_t)row * ldk, ws, row, k, lane);
+        if (lane == 0) xo[idx[row]] = acc;
+      }
+    } else if (SWEEP == 2) {                       // w = X_U^T v_k;  u = v_m - U12^T w
+      for (int c0 = 0; c0 < k; c0 += 32) {
+        const int c = c0 + lane;
+        const T s = col_dot(X + c, ldk, vs, 0, min(c0 + 32, k), c < k, [&](int b) { return b <= c; }, red);
+        if (warp == 0 && c < k) ws[c] = s;
+        __syncthreads();
+      }
+      for (int c0 = 0; c0 < m; c0 += 32) {
+        const int c = c0 + lane;
+        const T s = col_dot(F + k + c, ld, ws, 0, k, c < m, [](int) { return true; }, red);
+        if (warp == 0 && c < m) vf[k + c] = csub(vs[k + c], s);
+        __syncthreads();
+      }
+      for (int s = tid; s < k; s += kThreads) vf[s] = ws[s];
+    } else {                                       // t = w - L21^T x_m;  x_k = P^T X_L^T t
+      for (int c0 = 0; c0 < k; c0 += 32) {
+        const int c = c0 + lane;
+        const T s = col_dot(F + (size_t)k * ld + c, ld, vs + k, 0, m, c < k, [](int) { return true; }, red);
+        if (warp == 0 && c < k) ws[c] = csub(vs[c], s);
+        __syncthreads();
+      }
+      for (int c0 = 0; c0 < k; c0 += 32) {
+        const int c = c0 + lane;
+        const T s = col_dot(X + c, ldk, ws, c0 + 1, k, c < k, [&](int b) { return b > c; }, red);
+        if (warp == 0 && c < k) xo[idx[Pm[c]]] = cadd(ws[c], s);
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T, int SWEEP>
 __global__ void __launch_bounds__(kThreads)
 tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ in, T* __restrict__ out) {
@@ -124,6 +203,10 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
   T* vs = reinterpret_cast<T*>(smem_raw);
   const int w = blockIdx.y + a.w0;
   const int2 task = tasks[blockIdx.x];
+  if (task.x < 0) {
+    whole_front<T, SWEEP>(a, a.P.fronts[task.x & 0x7fffffff], w, in, out, vs, red);
+    return;
+  }
   const FrontDesc d = a.P.fronts[task.x];
   const int k = d.k, ldk = d.ldk;
   const int b0 = task.y;
