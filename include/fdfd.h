@@ -93,6 +93,10 @@ typedef struct {
   double growth_bound;         /* largest |L| entry tolerated in an FP32 front before the whole
                                   factorisation is redone in FP64 (default 1e6) */
   int leaf_area;               /* nested-dissection leaf size in cells (default 32) */
+  int pivoting;                /* row pivoting in large fronts: 0 = partial pivoting over all the
+                                  front's pivot rows, 1 = partial pivoting within each 32 x 32
+                                  diagonal block of the panel (faster; rows below are eliminated
+                                  against it).  Small fronts always use full partial pivoting. */
 } fdfd_options;
 
 typedef struct {

@@ -498,13 +498,15 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           gf += 8.0 * b * rem * rem;
           gb += es * (2.0 * rem * rem + 2.0 * rem * b);
         }
+      const bool local_piv = ctx->opt.pivoting == 1;
       {
         Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd);
-        launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
+        if (local_piv) launch_lu_panel_diag<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
+        else launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
       }
       {
         Prof pr(ctx, PK_LU_TRSM, lf * nwd, lb * nwd);
-        launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, ll.nmax_large, s);
+        launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, ll.nmax_large, local_piv ? 1 : 0, s);
       }
       { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
@@ -902,6 +904,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->gmres_restart = 8;
   o->growth_bound = 1e6;
   o->leaf_area = 32;
+  o->pivoting = 0;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -934,6 +937,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.gmres_restart < 1) c->opt.gmres_restart = 1;
   if (c->opt.gmres_restart > 16) c->opt.gmres_restart = 16;
   if (c->opt.leaf_area < 1) c->opt.leaf_area = 32;
+  if (c->opt.pivoting != 1) c->opt.pivoting = 0;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   *out = c;

@@ -602,6 +602,84 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
   }
 }
 
+// Panel with pivoting restricted to its nb x nb diagonal block: one warp LU-
+// factors the block in shared memory (warp-synchronous, no block barriers);
+// every row below it, pivot rows included, is then eliminated against the
+// block by lu_l21_kernel (rows from j0 + nb).  Row swaps stay inside the block.
+template <typename T>
+__global__ void __launch_bounds__(32)
+lu_panel_diag_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+  using R = typename RealOf<T>::type;
+  __shared__ T Ps[kMaxNb][kMaxNb + 1];
+  __shared__ int s_swap[kMaxNb];
+  __shared__ int map[kMaxNb];
+  const int w = blockIdx.y + a.w0;
+  const int f = flist[blockIdx.x];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(nbmax, d.k - j0);
+  const int k = d.k, ld = d.ld;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int lane = threadIdx.x;
+  if (j0 == 0)
+    for (int i = lane; i < k; i += 32) P[i] = i;
+  for (int i = 0; i < nb; ++i)
+    if (lane < nb) Ps[i][lane] = F[(size_t)(j0 + i) * ld + j0 + lane];
+  __syncwarp();
+  R gmax = 0;
+  for (int jj = 0; jj < nb; ++jj) {
+    R v = (lane >= jj && lane < nb) ? cabs2(Ps[lane][jj]) : R(-1);
+    int bi = lane;
+    warp_argmax(v, bi);
+    const int piv = bi < jj ? jj : bi;
+    if (piv != jj && lane < nb) {
+      const T x = Ps[jj][lane];
+      Ps[jj][lane] = Ps[piv][lane];
+      Ps[piv][lane] = x;
+    }
+    if (lane == 0) s_swap[jj] = piv;
+    __syncwarp();
+    const T pv = Ps[jj][jj];
+    const T inv = crcp(pv);
+    if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
+    if (lane > jj && lane < nb) {
+      const T l = cmul(Ps[lane][jj], inv);
+      Ps[lane][jj] = l;
+      gmax = nanmax(gmax, cabs2(l));
+    }
+    __syncwarp();
+    if (lane > jj && lane < nb) {
+      const T u = Ps[jj][lane];
+      for (int r = jj + 1; r < nb; ++r) Ps[r][lane] = cfms(Ps[r][jj], u, Ps[r][lane]);
+    }
+    __syncwarp();
+  }
+  for (int i = 0; i < nb; ++i)
+    if (lane < nb) F[(size_t)(j0 + i) * ld + j0 + lane] = Ps[i][lane];
+  if (lane == 0) {
+    for (int i = 0; i < nb; ++i) map[i] = i;
+    for (int jj = 0; jj < nb; ++jj) {
+      const int piv = s_swap[jj];
+      if (piv != jj) {
+        const int x = map[jj]; map[jj] = map[piv]; map[piv] = x;
+        const int y = P[j0 + jj]; P[j0 + jj] = P[j0 + piv]; P[j0 + piv] = y;
+      }
+    }
+    int* out = a.swp + ((size_t)blockIdx.y * a.swp_stride + blockIdx.x) * kSwpInts;
+    int cnt = 0;
+    for (int p = 0; p < nb; ++p)
+      if (map[p] != p) { out[1 + 2 * cnt] = p; out[2 + 2 * cnt] = map[p]; ++cnt; }
+    out[0] = cnt;
+  }
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) {
+    float* gp = a.growth + (size_t)w * a.n_fronts + f;
+    const float gv = (float)sqrt((double)gmax);
+    *gp = (j0 == 0) ? gv : nanmax(*gp, gv);
+  }
+}
+
 // Triangular inverses of a factored large front, written to the inverse store
 // (L11^-1 strictly below the diagonal, U11^-1 on and above it).  One CTA per
 // 32-column block of one triangle; it walks its column block one 32-row block
@@ -743,7 +821,7 @@ constexpr int kL21Rows = 64;
 // (pairs written by lu_panel_smem_kernel) to 32 columns outside the panel.
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, int nl21) {
+lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, int nl21, int below) {
   using R = typename RealOf<T>::type;
   __shared__ T Us[kMaxNb][kMaxNb + 1];
   __shared__ T Xs[kL21Rows][kMaxNb + 1];
@@ -772,7 +850,9 @@ lu_l21_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, 
       if (ok) F[(size_t)(j0 + pr[1 + 2 * t]) * d.ld + c] = buf[t * (kMaxNb + 1) + lane];
     return;
   }
-  const int r0 = d.k + blockIdx.x * kL21Rows;
+  // rows eliminated against the panel's diagonal block: the boundary rows, or
+  // (block-local pivoting) every row below the block
+  const int r0 = (below ? j0 + nb : d.k) + blockIdx.x * kL21Rows;
   if (r0 >= d.n) return;
   const int rows = min(kL21Rows, d.n - r0);
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
@@ -996,12 +1076,20 @@ void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cu
 }
 
 template <typename T>
+void launch_lu_panel_diag(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int kmax,
+                          cudaStream_t s) {
+  if (nf <= 0 || j0 >= kmax) return;
+  lu_panel_diag_kernel<T><<<dim3(nf, a.n_omega), 32, 0, s>>>(a, flist, j0, nb);
+}
+
+template <typename T>
 void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int mmax, int nmax,
-                   cudaStream_t s) {
+                   int below, cudaStream_t s) {
   if (nf <= 0) return;
-  const int nl21 = (mmax + kL21Rows - 1) / kL21Rows;
+  const int rows = below ? nmax - j0 : mmax;
+  const int nl21 = (rows + kL21Rows - 1) / kL21Rows;
   const int nswap = (nmax + 31) / 32;
-  lu_l21_kernel<T><<<dim3(nl21 + nswap, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb, nl21);
+  lu_l21_kernel<T><<<dim3(nl21 + nswap, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb, nl21, below);
 }
 
 template <typename T>
@@ -1026,7 +1114,8 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
   template void launch_build<T>(const FactorLaunch&, const int2*, int, cudaStream_t);            \
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
   template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
-  template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, cudaStream_t); \
+  template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, int, cudaStream_t); \
+  template void launch_lu_panel_diag<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t);

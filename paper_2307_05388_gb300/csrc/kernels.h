@@ -46,7 +46,11 @@ template <typename T> void launch_lu_small(const FactorLaunch& a, const int* fli
 template <typename T> void launch_lu_panel(const FactorLaunch& a, const int* flist, int nf, int j0,
                                            int nb, int kmax, cudaStream_t s);
 template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0,
-                                         int nb, int mmax, int nmax, cudaStream_t s);
+                                         int nb, int mmax, int nmax, int below, cudaStream_t s);
+// panel variant with pivoting restricted to its diagonal block (one warp per front);
+// pair it with launch_lu_l21(..., below = 1)
+template <typename T> void launch_lu_panel_diag(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                                int nb, int kmax, cudaStream_t s);
 constexpr int kSwapScratchInts = 130;   // ints of swap scratch per (wavelength, listed front)
 template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);

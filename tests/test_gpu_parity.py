@@ -92,6 +92,17 @@ def test_small_grids(nx, ny, npml, box, n_omega, nrhs, leaf, mode):
         assert O.rel_err(x, ref) <= (FIELD_TOL if mode == FD.MODE_MIXED else 1e-10)
 
 
+@pytest.mark.parametrize("nx,ny,npml,box,leaf", [(130, 97, 10, (20, 15, 90, 60), 32),
+                                                 (61, 45, 8, (13, 10, 30, 20), 16)])
+@pytest.mark.parametrize("mode", [FD.MODE_MIXED, FD.MODE_F64])
+def test_block_local_pivoting(nx, ny, npml, box, leaf, mode):
+    """Pivoting restricted to each panel's diagonal block still reaches the oracle."""
+    wl = W.make_small(nx, ny, npml, box, n_omega=2, n_src=1, seed=23)
+    for tr in (False, True):
+        x, ref, _ = _solve_case(wl, 2, mode, transpose=tr, leaf_area=leaf, pivoting=1)
+        assert O.rel_err(x, ref) <= (FIELD_TOL if mode == FD.MODE_MIXED else 1e-10)
+
+
 def test_refactor_design_is_bitwise_fresh_factor():
     """Cached refactor of the design fronts == full factorisation of the new eps, bit for bit."""
     wl = W.make("c1")
