@@ -95,8 +95,9 @@ typedef struct {
   int leaf_area;               /* nested-dissection leaf size in cells (default 32) */
   int pivoting;                /* row pivoting in large fronts: 0 = partial pivoting over all the
                                   front's pivot rows, 1 = partial pivoting within each 32 x 32
-                                  diagonal block of the panel (faster; rows below are eliminated
-                                  against it).  Small fronts always use full partial pivoting. */
+                                  diagonal block of the panel (default; faster, rows below are
+                                  eliminated against it).  Small fronts and the FP64 fallback
+                                  always use full partial pivoting. */
 } fdfd_options;
 
 typedef struct {

@@ -878,7 +878,12 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr) {
   if (!(g <= ctx->opt.growth_bound)) {
     if (fell_back) *fell_back = true;
     ctx->fallbacks += 1;
-    CKS(factor_levels<double2>(ctx, false));
+    // the fallback always pivots over every pivot row of each front
+    const int piv_saved = ctx->opt.pivoting;
+    ctx->opt.pivoting = 0;
+    const fdfd_status fst = factor_levels<double2>(ctx, false);
+    ctx->opt.pivoting = piv_saved;
+    CKS(fst);
     CK(cudaStreamSynchronize(ctx->stream));
     const float g64 = *ctx->h_growth_max;
     ctx->last_growth = g64;
@@ -904,7 +909,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->gmres_restart = 8;
   o->growth_bound = 1e6;
   o->leaf_area = 32;
-  o->pivoting = 0;
+  o->pivoting = 1;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -937,7 +942,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.gmres_restart < 1) c->opt.gmres_restart = 1;
   if (c->opt.gmres_restart > 16) c->opt.gmres_restart = 16;
   if (c->opt.leaf_area < 1) c->opt.leaf_area = 32;
-  if (c->opt.pivoting != 1) c->opt.pivoting = 0;
+  if (c->opt.pivoting != 0) c->opt.pivoting = 1;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   *out = c;
