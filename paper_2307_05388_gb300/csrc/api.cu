@@ -168,10 +168,11 @@ void free_ptr(void* p) {
   if (p) cudaFree(p);
 }
 
-enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_INV, PK_SWEEP_L,
-                PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY, PK_CVT,
-                PK_OTHER, PK_COUNT };
-const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm", "lu_inv",
+enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
+                PK_SWEEP_L, PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY,
+                PK_CVT, PK_OTHER, PK_COUNT };
+const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm",
+                                          "lu_schur", "lu_inv",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "precision_cvt", "other"};
 
@@ -493,10 +494,11 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           lf += 8.0 * 0.5 * b * (b + 1.0) * d.m;
           lb += 2.0 * es * b * (double)d.m;
           const double rem = d.n - j0 - b;
+          const double kr = d.k - j0 - b;                  // pivot columns still to factor
           tf += 8.0 * 0.5 * b * (b - 1) * rem;
           tb += 2.0 * es * b * rem;
-          gf += 8.0 * b * rem * rem;
-          gb += es * (2.0 * rem * rem + 2.0 * rem * b);
+          gf += 8.0 * b * (rem * kr + kr * d.m);          // pivot-block rows and columns only
+          gb += es * (2.0 * (rem * kr + kr * d.m) + 2.0 * rem * b);
         }
       const bool local_piv = ctx->opt.pivoting == 1;
       {
@@ -510,6 +512,18 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       }
       { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
+    }
+    if (ll.nlarge > 0 && ll.mmax_large > 0) {
+      // update matrices of the level's large fronts: S = F22 - L21 U12 (k m^2 complex multiply-adds)
+      double sf = 0, sb = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.nlarge; ++t) {
+          const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
+          sf += 8.0 * (double)d.k * d.m * d.m;
+          sb += es * (2.0 * (double)d.m * d.m + 2.0 * (double)d.k * d.m);
+        }
+      Prof pr(ctx, PK_LU_SCHUR, sf * nwd, sb * nwd);
+      launch_schur_simt<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.mmax_large, s);
     }
     if (ll.nlarge > 0) {
       // triangular inverses of the level's large fronts (2/3 k^3 complex multiply-adds each)

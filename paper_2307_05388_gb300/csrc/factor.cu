@@ -934,24 +934,31 @@ template <typename T> struct GemmKc;
 template <> struct GemmKc<float2> { static constexpr int v = 32; };
 template <> struct GemmKc<double2> { static constexpr int v = 16; };
 
+// Two uses (SIMT complex FMA, 64 x 64 tiles):
+//   schur = 0: panel step at j0 -- trailing update restricted to the pivot-block
+//              rows and columns; the m x m update matrix S is left untouched
+//   schur = 1: once per front after its last panel -- S = F22 - L21 U12, K = k
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, int schur) {
   constexpr int KC = GemmKc<T>::v;
   __shared__ T As[kGemmTile][KC + 1];
   __shared__ T Bs[KC][kGemmTile];
   const int w = blockIdx.z + a.w0;
   const int f = flist[blockIdx.y];
   const FrontDesc d = a.P.fronts[f];
-  if (j0 >= d.k) return;
-  const int nb = min(nbmax, d.k - j0);
-  const int base = j0 + nb;
+  if (!schur && j0 >= d.k) return;
+  const int nb = schur ? d.k : min(nbmax, d.k - j0);   // contraction length
+  const int kbeg = schur ? 0 : j0;                      // first contracted column of L / row of U
+  const int base = schur ? d.k : j0 + nb;
   const int rem = d.n - base;
   if (rem <= 0) return;
   const int nt = (rem + kGemmTile - 1) / kGemmTile;
   if ((int)blockIdx.x >= nt * nt) return;
   const int ti = blockIdx.x / nt, tj = blockIdx.x - ti * nt;
   const int r0 = base + ti * kGemmTile, c0 = base + tj * kGemmTile;
+  if (!schur && r0 >= d.k && c0 >= d.k) return;        // tile inside S: deferred to the Schur product
+  j0 = kbeg;
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[4][4];
@@ -992,7 +999,7 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gc = c0 + tx + 16 * j;
-      if (gc < d.n) {
+      if (gc < d.n && (schur || gr < d.k || gc < d.k)) {
         T* p = F + (size_t)gr * d.ld + gc;
         *p = csub(*p, acc[i][j]);
       }
@@ -1107,7 +1114,14 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
   const int rem = nmax - j0 - 1;
   if (nf <= 0 || rem <= 0) return;
   const int nt = (rem + kGemmTile - 1) / kGemmTile;
-  lu_gemm_kernel<T><<<dim3(nt * nt, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb);
+  lu_gemm_kernel<T><<<dim3(nt * nt, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nb, 0);
+}
+
+template <typename T>
+void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax, cudaStream_t s) {
+  if (nf <= 0 || mmax <= 0) return;
+  const int nt = (mmax + kGemmTile - 1) / kGemmTile;
+  lu_gemm_kernel<T><<<dim3(nt * nt, nf, a.n_omega), 256, 0, s>>>(a, flist, 0, 0, 1);
 }
 
 #define FDFD_INST(T)                                                                              \
@@ -1118,7 +1132,8 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
   template void launch_lu_panel_diag<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
-  template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t);
+  template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
+  template void launch_schur_simt<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);
 FDFD_INST(float2)
 FDFD_INST(double2)
 #undef FDFD_INST

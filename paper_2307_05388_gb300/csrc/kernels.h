@@ -54,6 +54,11 @@ template <typename T> void launch_lu_panel_diag(const FactorLaunch& a, const int
 constexpr int kSwapScratchInts = 130;   // ints of swap scratch per (wavelength, listed front)
 template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
+// Update matrix of the listed large fronts after their last panel: S = F22 - L21 U12
+// (K = k), SIMT complex FMA; mmax = largest m listed.
+template <typename T> void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax,
+                                             cudaStream_t s);
+// panel-step trailing update restricted to the pivot-block rows and columns
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
 int lu_small_max_n(int elem_bytes);
