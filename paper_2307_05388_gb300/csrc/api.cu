@@ -168,10 +168,10 @@ void free_ptr(void* p) {
   if (p) cudaFree(p);
 }
 
-enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
+enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_STEP, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
                 PK_SWEEP_L, PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY,
                 PK_CVT, PK_OTHER, PK_COUNT };
-const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_panel", "lu_trsm", "lu_gemm",
+const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_step", "lu_panel", "lu_trsm", "lu_gemm",
                                           "lu_schur", "lu_inv",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "precision_cvt", "other"};
@@ -481,6 +481,7 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       Prof pr(ctx, PK_LU_SMALL, fl * nwd, by * nwd);
       launch_lu_small<T>(fa, ctx->d_lists + ll.small_off, ll.nsmall, ll.nmax_small, s);
     }
+    const bool local_piv = ctx->opt.pivoting == 1;
     for (int j0 = 0; j0 < ll.kmax_large; j0 += nb) {
       const int* fl = ctx->d_lists + ll.large_off;
       double pf = 0, pb = 0, lf = 0, lb = 0, tf = 0, tb = 0, gf = 0, gb = 0;
@@ -491,8 +492,9 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           const int b = std::min(nb, d.k - j0);
           for (int j = j0; j < j0 + b; ++j) pf += 8.0 * (double)(d.k - j - 1) * (j0 + b - j);
           pb += 2.0 * es * (double)(d.k - j0) * b;
-          lf += 8.0 * 0.5 * b * (b + 1.0) * d.m;
-          lb += 2.0 * es * b * (double)d.m;
+          const double below = ctx->opt.pivoting == 1 ? d.n - j0 - b : d.m;   // rows eliminated against the block
+          lf += 8.0 * 0.5 * b * (b + 1.0) * below;
+          lb += 2.0 * es * b * below;
           const double rem = d.n - j0 - b;
           const double kr = d.k - j0 - b;                  // pivot columns still to factor
           tf += 8.0 * 0.5 * b * (b - 1) * rem;
@@ -500,17 +502,18 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           gf += 8.0 * b * (rem * kr + kr * d.m);          // pivot-block rows and columns only
           gb += es * (2.0 * (rem * kr + kr * d.m) + 2.0 * rem * b);
         }
-      const bool local_piv = ctx->opt.pivoting == 1;
-      {
-        Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd);
-        if (local_piv) launch_lu_panel_diag<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
-        else launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s);
+      if (local_piv) {
+        // block LU, L columns, U rows and the row permutation of the step in one launch
+        Prof pr(ctx, PK_LU_STEP, (pf + lf + tf) * nwd, (pb + lb + tb) * nwd);
+        launch_lu_step_local<T>(fa, fl, ll.nlarge, j0, ll.nmax_large, s);
+      } else {
+        { Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd);
+          launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s); }
+        { Prof pr(ctx, PK_LU_TRSM, lf * nwd, lb * nwd);
+          launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, ll.nmax_large, 0, s); }
+        { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd);
+          launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       }
-      {
-        Prof pr(ctx, PK_LU_TRSM, lf * nwd, lb * nwd);
-        launch_lu_l21<T>(fa, fl, ll.nlarge, j0, nb, ll.mmax_large, ll.nmax_large, local_piv ? 1 : 0, s);
-      }
-      { Prof pr(ctx, PK_LU_TRSM, tf * nwd, tb * nwd); launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
     }
     if (ll.nlarge > 0 && ll.mmax_large > 0) {
@@ -535,7 +538,10 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           vb += es * 2.0 * (double)d.k * d.k;
         }
       Prof pr(ctx, PK_LU_INV, vf * nwd, vb * nwd);
-      launch_lu_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
+      if (ctx->opt.pivoting == 1)   // diagonal blocks already inverted by the panel steps
+        launch_lu_inv_blocked<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
+      else
+        launch_lu_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
     }
   }
   CK(cudaGetLastError());

@@ -13,6 +13,7 @@
 // The largest |L| entry of each front is recorded as its pivot-growth figure.
 // All reductions run in a fixed order: a factorisation is a deterministic
 // function of its inputs, bit for bit.
+#include <algorithm>
 #include <cfloat>
 
 #include "kernels.h"
@@ -27,7 +28,8 @@ constexpr int kSwpInts = kSwapScratchInts;   // per panel: count + up to 64 (dst
 // ---------------------------------------------------------------------------
 // Front build: F = originals + sum over children of their update matrices,
 // gathered through the children's inverse extend-add maps (no atomics).
-// One warp per front row, 8 rows per CTA.
+// One warp per front row, 8 rows per CTA.  The first task of a front also
+// clears its growth figure.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBuildWarps * 32)
@@ -37,6 +39,7 @@ build_kernel(FactorLaunch a, const int2* __restrict__ tasks) {
   const int f = t.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const FrontDesc d = a.P.fronts[f];
+  if (t.y == 0 && threadIdx.x == 0) a.growth[(size_t)w * a.n_fronts + f] = 0.f;   // accumulated by atomicMax later
   const int r = t.y + warp;
   if (r >= d.n) return;
   T* st = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride;
@@ -602,81 +605,240 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
   }
 }
 
-// Panel with pivoting restricted to its nb x nb diagonal block: one warp LU-
-// factors the block in shared memory (warp-synchronous, no block barriers);
-// every row below it, pivot rows included, is then eliminated against the
-// block by lu_l21_kernel (rows from j0 + nb).  Row swaps stay inside the block.
+// ---------------------------------------------------------------------------
+// Block-local pivoting: one launch per panel step does everything that depends
+// only on the 32 x 32 diagonal block B = F[J, J], J = [j0, j0 + nb):
+//   every CTA LU-factors B itself (warp 0, rows in registers, pivot rows chosen
+//   inside B) and forms the triangular inverses Li = L_JJ^-1, Ui = U_JJ^-1 it
+//   needs (deterministic: every CTA gets the same bits), then does one role:
+//     role D (block 0): the row permutation of J into perm, the inverse blocks
+//                       into the inverse store (they are the diagonal blocks of
+//                       L11^-1 and U11^-1), growth of the block's multipliers;
+//     role L: rows r >= j0 + nb, L[r, J] = F[r, J] Ui            (64 rows / CTA);
+//     role U: columns c >= j0 + nb, U[J, c] = Li (P F)[J, c]     (64 columns / CTA);
+//     role P: columns c < j0, F[J, c] <- (P F)[J, c]             (64 columns / CTA).
+// The factored diagonal block itself is not stored back (nothing reads it:
+// the sweeps and the inverse use Li, Ui).  Roles touch disjoint entries of F
+// and read B only, so the CTAs are independent.
+// ---------------------------------------------------------------------------
+constexpr int kStepRows = 64;
+
+// 1 / z as conj(z) / |z|^2 with a correctly rounded reciprocal (pivots here are
+// far from the over/underflow range; a zero pivot gives inf/NaN, flagged as growth)
+__device__ __forceinline__ float2 fast_crcp(float2 z) {
+  const float s = __frcp_rn(z.x * z.x + z.y * z.y);
+  return make_float2(z.x * s, -z.y * s);
+}
+__device__ __forceinline__ double2 fast_crcp(double2 z) {
+  const double s = __drcp_rn(z.x * z.x + z.y * z.y);
+  return make_double2(z.x * s, -z.y * s);
+}
+
+// LU of the nb x nb block at (j0, j0) with row pivoting inside the block, by
+// warp 0 with lane = row.  No rows are swapped: at step p the pivot is the
+// unused lane r with the largest |a_p| (one redux over packed keys: |a_p|^2 in
+// the high bits, 31 - lane in the low 5 bits, so ties go to the lower lane);
+// the other unused lanes are eliminated against it.  On return LU[p] holds
+// row p of L\U in pivot order, src[p] the block row it came from, dinv[p] =
+// 1 / U[p][p].  Returns this lane's largest |multiplier|^2 (NaN -> inf).
 template <typename T>
-__global__ void __launch_bounds__(32)
-lu_panel_diag_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax) {
+__device__ __forceinline__ typename RealOf<T>::type diag_lu_warp(const T* __restrict__ F, int ld, int j0, int nb,
+                                                                 T (*LU)[kMaxNb + 1], int* src, T* dinv) {
   using R = typename RealOf<T>::type;
-  __shared__ T Ps[kMaxNb][kMaxNb + 1];
-  __shared__ int s_swap[kMaxNb];
-  __shared__ int map[kMaxNb];
-  const int w = blockIdx.y + a.w0;
-  const int f = flist[blockIdx.x];
-  const FrontDesc d = a.P.fronts[f];
-  if (j0 >= d.k) return;
-  const int nb = min(nbmax, d.k - j0);
-  const int k = d.k, ld = d.ld;
-  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
-  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
-  const int lane = threadIdx.x;
-  if (j0 == 0)
-    for (int i = lane; i < k; i += 32) P[i] = i;
-  for (int i = 0; i < nb; ++i)
-    if (lane < nb) Ps[i][lane] = F[(size_t)(j0 + i) * ld + j0 + lane];
-  __syncwarp();
-  R gmax = 0;
-  for (int jj = 0; jj < nb; ++jj) {
-    R v = (lane >= jj && lane < nb) ? cabs2(Ps[lane][jj]) : R(-1);
-    int bi = lane;
-    warp_argmax(v, bi);
-    const int piv = bi < jj ? jj : bi;
-    if (piv != jj && lane < nb) {
-      const T x = Ps[jj][lane];
-      Ps[jj][lane] = Ps[piv][lane];
-      Ps[piv][lane] = x;
-    }
-    if (lane == 0) s_swap[jj] = piv;
-    __syncwarp();
-    const T pv = Ps[jj][jj];
-    const T inv = crcp(pv);
-    if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
-    if (lane > jj && lane < nb) {
-      const T l = cmul(Ps[lane][jj], inv);
-      Ps[lane][jj] = l;
-      gmax = nanmax(gmax, cabs2(l));
-    }
-    __syncwarp();
-    if (lane > jj && lane < nb) {
-      const T u = Ps[jj][lane];
-      for (int r = jj + 1; r < nb; ++r) Ps[r][lane] = cfms(Ps[r][jj], u, Ps[r][lane]);
-    }
-    __syncwarp();
-  }
-  for (int i = 0; i < nb; ++i)
-    if (lane < nb) F[(size_t)(j0 + i) * ld + j0 + lane] = Ps[i][lane];
-  if (lane == 0) {
-    for (int i = 0; i < nb; ++i) map[i] = i;
-    for (int jj = 0; jj < nb; ++jj) {
-      const int piv = s_swap[jj];
-      if (piv != jj) {
-        const int x = map[jj]; map[jj] = map[piv]; map[piv] = x;
-        const int y = P[j0 + jj]; P[j0 + jj] = P[j0 + piv]; P[j0 + piv] = y;
+  const int lane = threadIdx.x & 31;
+  const T one = cmk(R(1), R(0));
+  T row[kMaxNb];
+#pragma unroll
+  for (int j = 0; j < kMaxNb; ++j)
+    row[j] = (lane < nb && j < nb) ? F[(size_t)(j0 + lane) * ld + j0 + j] : (lane == j ? one : czero<T>());
+  bool used = false;
+  int myp = lane;                 // padding lanes (>= nb) keep their own position
+  T myd = one;
+  R g = 0;
+#pragma unroll
+  for (int p = 0; p < kMaxNb; ++p) {
+    if (p < nb) {
+      const float v = (float)cabs2(row[p]);
+      unsigned key = used ? 0u : ((__float_as_uint(v) & ~31u) | (unsigned)(31 - lane));
+      if (!used && !(v == v)) key = 0xffffffe0u | (unsigned)(31 - lane);   // NaN wins
+      const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+      const int r = 31 - (int)(kmax & 31u);
+      const T inv = fast_crcp(shfl_c(row[p], r));
+      if (lane == r) { used = true; myp = p; myd = inv; }
+      const bool elim = !used;
+      const T l = cmul(row[p], inv);
+      if (elim) {
+        row[p] = l;
+        const R a2 = cabs2(l);
+        g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
+      }
+#pragma unroll
+      for (int j = p + 1; j < kMaxNb; ++j) {
+        const T u = shfl_c(row[j], r);
+        if (elim) row[j] = cfms(l, u, row[j]);
       }
     }
-    int* out = a.swp + ((size_t)blockIdx.y * a.swp_stride + blockIdx.x) * kSwpInts;
-    int cnt = 0;
-    for (int p = 0; p < nb; ++p)
-      if (map[p] != p) { out[1 + 2 * cnt] = p; out[2 + 2 * cnt] = map[p]; ++cnt; }
-    out[0] = cnt;
   }
-  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  if (lane == 0) {
-    float* gp = a.growth + (size_t)w * a.n_fronts + f;
-    const float gv = (float)sqrt((double)gmax);
-    *gp = (j0 == 0) ? gv : nanmax(*gp, gv);
+#pragma unroll
+  for (int j = 0; j < kMaxNb; ++j) LU[myp][j] = row[j];
+  src[myp] = lane;
+  dinv[myp] = myd;
+  return g;
+}
+
+// Column c = lane of Li (unit lower, diagonal included) or Ui from LU in shared memory.
+template <typename T>
+__device__ __forceinline__ void tri_inverse_col(const T (*LU)[kMaxNb + 1], const T* dinv, bool upper,
+                                                T (*out)[kMaxNb + 1]) {
+  using R = typename RealOf<T>::type;
+  const int c = threadIdx.x & 31;
+  T x[kMaxNb];
+  if (!upper) {
+#pragma unroll
+    for (int i = 0; i < kMaxNb; ++i) {
+      T a0 = (i == c) ? cmk(R(1), R(0)) : czero<T>(), a1 = czero<T>();
+#pragma unroll
+      for (int l = 0; l < i; ++l) {
+        if (l & 1) a1 = cfms(LU[i][l], x[l], a1);
+        else a0 = cfms(LU[i][l], x[l], a0);
+      }
+      x[i] = cadd(a0, a1);
+      out[i][c] = x[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = kMaxNb - 1; i >= 0; --i) {
+      T a0 = (i == c) ? cmk(R(1), R(0)) : czero<T>(), a1 = czero<T>();
+#pragma unroll
+      for (int l = i + 1; l < kMaxNb; ++l) {
+        if (l & 1) a1 = cfms(LU[i][l], x[l], a1);
+        else a0 = cfms(LU[i][l], x[l], a0);
+      }
+      x[i] = cmul(cadd(a0, a1), dinv[i]);
+      out[i][c] = x[i];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu) {
+  using R = typename RealOf<T>::type;
+  using Blk = T[kMaxNb + 1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Blk* LU = reinterpret_cast<Blk*>(smem_raw);     // [32][33] each
+  Blk* Li = LU + kMaxNb;
+  Blk* Ui = Li + kMaxNb;
+  Blk* Ws = Ui + kMaxNb;                          // [64][33]: role L 64 rows x J; roles U, P: [c][p]
+  T* dinv = reinterpret_cast<T*>(Ws + kStepRows);
+  __shared__ int src[kMaxNb];
+  __shared__ R s_g[8];
+  const int w = blockIdx.z + a.w0;
+  const int f = flist[blockIdx.y];
+  const FrontDesc d = a.P.fronts[f];
+  if (j0 >= d.k) return;
+  const int nb = min(kMaxNb, d.k - j0), n = d.n, ld = d.ld;
+  const int bx = blockIdx.x;
+  // role and range; CTAs whose range is empty for this front leave before any work
+  int role, lo = 0;
+  if (bx == 0) {
+    role = 0;
+  } else if (bx <= nl) {
+    role = 1; lo = j0 + nb + (bx - 1) * kStepRows;
+    if (lo >= n) return;
+  } else if (bx <= nl + nu) {
+    role = 2; lo = j0 + nb + (bx - 1 - nl) * kStepRows;
+    if (lo >= n) return;
+  } else {
+    role = 3; lo = (bx - 1 - nl - nu) * kStepRows;
+    if (lo >= j0) return;
+  }
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  R g = 0;
+  if (warp == 0) g = diag_lu_warp<T>(F, ld, j0, nb, LU, src, dinv);
+  __syncthreads();
+  if ((role == 0 || role == 2) && warp == 0) tri_inverse_col<T>(LU, dinv, false, Li);
+  if ((role == 0 || role == 1) && warp == 1) tri_inverse_col<T>(LU, dinv, true, Ui);
+  if (role == 1) {
+    // stage rows [lo, lo + 64) of the block columns
+    for (int e = tid; e < kStepRows * kMaxNb; e += 256) {
+      const int rr = e >> 5, l = e & 31, r = lo + rr;
+      Ws[rr][l] = (r < n && l < nb) ? F[(size_t)r * ld + j0 + l] : czero<T>();
+    }
+  } else if (role >= 2) {
+    // stage the block rows, permuted, over columns [lo, lo + 64)
+    const int hi = role == 2 ? n : j0;
+    for (int e = tid; e < kStepRows * kMaxNb; e += 256) {
+      const int p = e >> 6, cc = e & 63, c = lo + cc;
+      Ws[cc][p] = (c < hi && p < nb) ? F[(size_t)(j0 + src[p]) * ld + c] : czero<T>();
+    }
+  }
+  __syncthreads();
+  if (role == 0) {
+    // rows of J move only at this step (earlier and later steps permute their own blocks)
+    if (tid < nb) a.perm[(size_t)w * a.perm_stride + d.piv_off + j0 + tid] = j0 + src[tid];
+    T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+    for (int e = tid; e < nb * nb; e += 256) {
+      const int i = e / nb, j = e - i * nb;
+      X[(size_t)(j0 + i) * d.ldk + j0 + j] = (i > j) ? Li[i][j] : Ui[i][j];
+    }
+  } else if (role == 1) {
+    // L[r][j] = sum_{l <= j} F[r][l] Ui[l][j]: thread = (column j, rows warp + 8 q)
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = czero<T>();
+#pragma unroll 8
+    for (int l = 0; l < kMaxNb; ++l) {
+      const T u = Ui[l][lane];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = cfma(Ws[warp + 8 * q][l], u, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = lo + warp + 8 * q;
+      if (r < n && lane < nb) {
+        F[(size_t)r * ld + j0 + lane] = acc[q];
+        const R a2 = cabs2(acc[q]);
+        g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
+      }
+    }
+  } else {
+    // role U: U[i][c] = sum_{l <= i} Li[i][l] (P F)[l][c];  role P: (P F)[i][c].
+    // thread = (column cc = tid & 63, rows i = (tid >> 6) + 4 q)
+    const int cc = tid & 63, ig = tid >> 6;
+    const int c = lo + cc;
+    const bool ok = c < (role == 2 ? n : j0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = ig + 4 * q;
+      T v;
+      if (role == 2) {
+        T a0 = czero<T>(), a1 = czero<T>();
+#pragma unroll
+        for (int l = 0; l < kMaxNb; ++l) {
+          if (l & 1) a1 = cfma(Li[i][l], Ws[cc][l], a1);
+          else a0 = cfma(Li[i][l], Ws[cc][l], a0);
+        }
+        v = cadd(a0, a1);   // Li is unit lower (zero above the diagonal)
+      } else {
+        v = Ws[cc][i];
+      }
+      if (ok && i < nb) F[(size_t)(j0 + i) * ld + c] = v;
+    }
+  }
+  if (role <= 1) {
+    for (int o = 16; o > 0; o >>= 1) g = nanmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if (lane == 0) s_g[warp] = g;
+    __syncthreads();
+    if (tid == 0) {
+      R gg = 0;
+      for (int i = 0; i < 8; ++i) gg = nanmax(gg, s_g[i]);
+      float gv = (float)sqrt((double)gg);
+      if (!(gv == gv)) gv = INFINITY;
+      // max of non-negative floats is order independent as an int max
+      atomicMax(reinterpret_cast<int*>(a.growth + (size_t)w * a.n_fronts + f), __float_as_int(gv));
+    }
   }
 }
 
@@ -810,6 +972,93 @@ lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
       }
       __syncthreads();
     }
+  }
+}
+
+// dynamic shared memory of lu_step_local_kernel: LU, Li, Ui, the 64 x 33 staging tile, 1/U[p][p]
+size_t step_local_smem(size_t es) { return ((size_t)(3 * kMaxNb + kStepRows) * (kMaxNb + 1) + kMaxNb) * es; }
+
+// Off-diagonal blocks of L11^-1 and U11^-1 when their 32 x 32 diagonal blocks
+// are already in the inverse store (block-local pivoting writes them at every
+// panel step).  One CTA per (32-column block cb, triangle, front) walks the
+// row blocks away from the diagonal:
+//   lower: X[rb][cb] = -Li_rb  sum_{l in [cb, rb)}    L[rb][l] X[l][cb]   (rb = cb+32, cb+64, ...)
+//   upper: X[rb][cb] = -Ui_rb  sum_{l in (rb, cb+32)} U[rb][l] X[l][cb]   (rb = cb-32, cb-64, ...)
+// (two products per step, no substitution).  Different CTAs write disjoint
+// entries and read only entries other CTAs do not write.
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_inv_blocked_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
+  using R = typename RealOf<T>::type;
+  __shared__ T tile0[32][33];
+  __shared__ T tile1[32][33];
+  const int w = blockIdx.z + a.w0;
+  const int f = flist[blockIdx.y];
+  const FrontDesc d = a.P.fronts[f];
+  const bool upper = (int)blockIdx.x >= nblk;
+  const int cb = (upper ? (int)blockIdx.x - nblk : (int)blockIdx.x) * 32;
+  const int k = d.k;
+  if (cb >= k) return;
+  const int ld = d.ld, ldk = d.ldk;
+  const int cw = min(32, k - cb);
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int c = cb + tx;
+  const T one = cmk(R(1), R(0));
+  const int step = upper ? -32 : 32;
+  for (int rb = cb + step; upper ? rb >= 0 : rb < k; rb += step) {
+    const int rh = min(32, k - rb);
+    T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+    const int l_lo = upper ? rb + 32 : cb, l_hi = upper ? cb + cw : rb;
+    for (int l0 = l_lo; l0 < l_hi; l0 += 32) {
+      for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        const int i = e >> 5, j = e & 31;
+        const int l = l0 + j;
+        tile0[i][j] = (i < rh && l < l_hi) ? F[(size_t)(rb + i) * ld + l] : czero<T>();
+        const int li = l0 + i, cc = cb + j;
+        T xv = czero<T>();
+        if (j < cw && li < l_hi) {
+          if (upper) xv = (li <= cc) ? X[(size_t)li * ldk + cc] : czero<T>();
+          else xv = (li > cc) ? X[(size_t)li * ldk + cc] : (li == cc ? one : czero<T>());
+        }
+        tile1[i][j] = xv;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        const T xv = tile1[j][tx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = cfma(tile0[ty + 8 * q][j], xv, acc[q]);
+      }
+      __syncthreads();
+    }
+    // tile1 <- acc, tile0 <- diagonal inverse block of rb (unit lower or upper)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tile1[ty + 8 * q][tx] = acc[q];
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+      const int i = e >> 5, j = e & 31;
+      T v = czero<T>();
+      if (i < rh && j < rh) {
+        if (upper) v = (j >= i) ? X[(size_t)(rb + i) * ldk + rb + j] : czero<T>();
+        else v = (j < i) ? X[(size_t)(rb + i) * ldk + rb + j] : (i == j ? one : czero<T>());
+      }
+      tile0[i][j] = v;
+    }
+    __syncthreads();
+    T out[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      const T av = tile1[t][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] = cfms(tile0[ty + 8 * q][t], av, out[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = ty + 8 * q;
+      if (i < rh && tx < cw) X[(size_t)(rb + i) * ldk + c] = out[q];
+    }
+    __syncthreads();
   }
 }
 
@@ -1040,6 +1289,12 @@ cudaError_t factor_init_attributes() {
   e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            2 * 64 * 64 * 16);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_step_local_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_local_smem(8));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_step_local_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_local_smem(16));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_panel_smem_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kPanelSmemBytes);
   if (e != cudaSuccess) return e;
@@ -1083,10 +1338,20 @@ void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cu
 }
 
 template <typename T>
-void launch_lu_panel_diag(const FactorLaunch& a, const int* flist, int nf, int j0, int nb, int kmax,
-                          cudaStream_t s) {
-  if (nf <= 0 || j0 >= kmax) return;
-  lu_panel_diag_kernel<T><<<dim3(nf, a.n_omega), 32, 0, s>>>(a, flist, j0, nb);
+void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0, int nmax, cudaStream_t s) {
+  if (nf <= 0) return;
+  const int span = std::max(0, nmax - j0 - 1);
+  const int nl = (span + kStepRows - 1) / kStepRows;
+  const int np = (j0 + kStepRows - 1) / kStepRows;
+  lu_step_local_kernel<T><<<dim3(1 + 2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
+      a, flist, j0, nl, nl);
+}
+
+template <typename T>
+void launch_lu_inv_blocked(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s) {
+  if (nf <= 0 || kmax <= 0) return;
+  const int nblk = (kmax + 31) / 32;
+  lu_inv_blocked_kernel<T><<<dim3(2 * nblk, nf, a.n_omega), 256, 0, s>>>(a, flist, nblk);
 }
 
 template <typename T>
@@ -1129,7 +1394,8 @@ void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
   template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, int, cudaStream_t); \
-  template void launch_lu_panel_diag<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
+  template void launch_lu_step_local<T>(const FactorLaunch&, const int*, int, int, int, cudaStream_t); \
+  template void launch_lu_inv_blocked<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \

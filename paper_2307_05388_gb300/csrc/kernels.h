@@ -47,10 +47,16 @@ template <typename T> void launch_lu_panel(const FactorLaunch& a, const int* fli
                                            int nb, int kmax, cudaStream_t s);
 template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist, int nf, int j0,
                                          int nb, int mmax, int nmax, int below, cudaStream_t s);
-// panel variant with pivoting restricted to its diagonal block (one warp per front);
-// pair it with launch_lu_l21(..., below = 1)
-template <typename T> void launch_lu_panel_diag(const FactorLaunch& a, const int* flist, int nf, int j0,
-                                                int nb, int kmax, cudaStream_t s);
+// Pivoting restricted to the 32 x 32 diagonal block J = [j0, j0 + 32): one launch
+// does the block's LU, the L columns below it, the U rows right of it, the row
+// permutation of earlier columns, perm, and the block's inverses into the
+// inverse store (then launch_lu_gemm for the trailing update); nmax = largest n.
+template <typename T> void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                                int nmax, cudaStream_t s);
+// L11^-1 / U11^-1 off-diagonal blocks from the diagonal blocks already in the
+// inverse store (block-local pivoting path)
+template <typename T> void launch_lu_inv_blocked(const FactorLaunch& a, const int* flist, int nf, int kmax,
+                                                 cudaStream_t s);
 constexpr int kSwapScratchInts = 130;   // ints of swap scratch per (wavelength, listed front)
 template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
