@@ -88,6 +88,14 @@ struct fdfd_ctx {
   std::vector<int> h_lists;
   std::vector<LevelList> lv_full[2], lv_design[2];   // [precision 0 = c64, 1 = c128]
   std::vector<SolveList> lv_solve;
+  // dataflow sweep queues [task type: 0 rows, 1 columns][direction: 0 bottom-up, 1 top-down]
+  struct FlowList { int off = 0, n = 0, need_all = 0, need_ph1 = 0; } flow[2][2];
+  int flow_vmax = 0;               // shared-memory vector entries of the flow kernel
+  int* d_flow_ctr = nullptr;       // queue head and per-front counters
+  int* d_flow_err = nullptr;       // set by a wait that gave up
+  int* h_flow_err = nullptr;       // pinned copy
+  int flow_grid[2] = {0, 0};       // persistent CTAs [precision 0 = c64, 1 = c128]
+  bool use_flow = true;
 
   // coefficients and permittivity
   double2 *d_cxm = nullptr, *d_cxp = nullptr, *d_cym = nullptr, *d_cyp = nullptr;
@@ -232,8 +240,9 @@ void drop_graphs(fdfd_ctx* c) {
 
 void free_ws(fdfd_ctx* c) {
   drop_graphs(c);
-  free_ptr(c->d_vb); free_ptr(c->d_bT); free_ptr(c->d_xT);
+  free_ptr(c->d_vb); free_ptr(c->d_bT); free_ptr(c->d_xT); free_ptr(c->d_flow_ctr);
   c->d_vb = c->d_bT = c->d_xT = nullptr;
+  c->d_flow_ctr = nullptr;
   c->ws_nrhs = 0;
 }
 
@@ -354,6 +363,45 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         sl.kbig = std::max(sl.kbig, d.k);
       }
     }
+    ctx->flow_vmax = std::max({ctx->flow_vmax, sl.kmax, sl.kbig, sl.mbig});
+  }
+  // Dataflow queues: the same tasks as the level lists, in dependency order,
+  // off-diagonal tasks tagged with bit 30; per-front task counts beside them.
+  const int nf = (int)p.fronts.size();
+  for (int t = 0; t < 2; ++t) {
+    for (int dir = 0; dir < 2; ++dir) {
+      auto& fl = ctx->flow[t][dir];
+      fl = fdfd_ctx::FlowList{};                 // the plan may be uploaded again (plain mode)
+      std::vector<int> all(nf, 0), ph1(nf, 0);
+      if (lists.size() % 2) lists.push_back(0);
+      fl.off = (int)lists.size();
+      auto put_tri = [&](const SolveList& sl) {
+        for (int i = 0; i < sl.tri[t].n; ++i) {
+          const int code = lists[sl.tri[t].off + 2 * i], s0 = lists[sl.tri[t].off + 2 * i + 1];
+          const int f = code & 0x7fffffff;
+          lists.push_back(code); lists.push_back(s0); fl.n++;
+          all[f]++;
+          if (code >= 0 && dir == 0) ph1[f]++;
+        }
+      };
+      auto put_rect = [&](const TaskList& tl) {
+        for (int i = 0; i < tl.n; ++i) {
+          const int f = lists[tl.off + 2 * i], s0 = lists[tl.off + 2 * i + 1];
+          lists.push_back((int)(0x40000000u | (unsigned)f)); lists.push_back(s0); fl.n++;
+          all[f]++;
+          if (dir == 1) ph1[f]++;
+        }
+      };
+      if (dir == 0) {
+        for (int l = 0; l < L; ++l) { put_tri(ctx->lv_solve[l]); put_rect(ctx->lv_solve[l].rect_m[t]); }
+      } else {
+        for (int l = L - 1; l >= 0; --l) { put_rect(ctx->lv_solve[l].rect_k[t]); put_tri(ctx->lv_solve[l]); }
+      }
+      fl.need_all = (int)lists.size();
+      lists.insert(lists.end(), all.begin(), all.end());
+      fl.need_ph1 = (int)lists.size();
+      lists.insert(lists.end(), ph1.begin(), ph1.end());
+    }
   }
   ctx->h_lists.swap(lists);
   CKS(upload(ctx, &ctx->d_lists, ctx->h_lists));
@@ -376,6 +424,10 @@ fdfd_status ensure_runtime(fdfd_ctx* ctx) {
     CK(dalloc(&ctx->d_eps, sizeof(double) * n_cells(ctx)));
     CK(dalloc(&ctx->d_growth_max, sizeof(float)));
     CK(cudaMallocHost((void**)&ctx->h_growth_max, sizeof(float)));
+    CK(dalloc(&ctx->d_flow_err, sizeof(int)));
+    CK(cudaMemsetAsync(ctx->d_flow_err, 0, sizeof(int), ctx->stream));
+    CK(cudaMallocHost((void**)&ctx->h_flow_err, sizeof(int)));
+    *ctx->h_flow_err = 0;
     CK(cudaMemcpyAsync(ctx->d_k0dx, ctx->k0dx.data(), sizeof(double) * ctx->n_omega, cudaMemcpyHostToDevice,
                        ctx->stream));
     launch_coef(ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx2, ctx->d_k0dx, ctx->n_omega,
@@ -558,6 +610,11 @@ fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
   CK(dalloc(&ctx->d_vb, sizeof(double2) * S * (size_t)ctx->plan.vec_total));
   CK(dalloc(&ctx->d_bT, sizeof(double2) * S * (size_t)n_cells(ctx)));
   CK(dalloc(&ctx->d_xT, sizeof(double2) * S * (size_t)n_cells(ctx)));
+  CK(dalloc(&ctx->d_flow_ctr, sizeof(int) * (1 + 2 * (size_t)ctx->n_omega * ctx->plan.fronts.size())));
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  for (int prec = 0; prec < 2; ++prec)
+    ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax));
   ctx->ws_nrhs = nrhs;
   return FDFD_OK;
 }
@@ -620,6 +677,36 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
     }
   };
   const int* dl = ctx->d_lists;
+  if (ctx->use_flow && ctx->d_flow_ctr) {
+    // one persistent launch per direction; counters cleared before each
+    const size_t ctr_bytes = sizeof(int) * (1 + 2 * (size_t)sa.n_omega * p.fronts.size());
+    for (int dir = 0; dir < 2; ++dir) {
+      const auto& fq = ctx->flow[tt][dir];
+      double fl = 0, by = 0;
+      for (int l = 0; l < p.n_levels; ++l) {
+        const SolveList& sl = ctx->lv_solve[l];
+        double f1, b1;
+        tri_work(sl.tri[tt], dir == 0 ? !transpose : transpose, &f1, &b1);
+        fl += f1; by += b1;
+        rect_work(dir == 0 ? sl.rect_m[tt] : sl.rect_k[tt], dir == 0, &f1, &b1);
+        fl += f1; by += b1;
+      }
+      CK(cudaMemsetAsync(ctx->d_flow_ctr, 0, ctr_bytes, s));
+      FlowQueue q;
+      q.tasks = reinterpret_cast<const int2*>(dl + fq.off);
+      q.ntasks = fq.n;
+      q.ctr = ctx->d_flow_ctr;
+      q.need_all = dl + fq.need_all;
+      q.need_ph1 = dl + fq.need_ph1;
+      q.err = ctx->d_flow_err;
+      q.n_fronts = (int)p.fronts.size();
+      const int grid = std::max(1, std::min(ctx->flow_grid[prec], fq.n * sa.n_omega));
+      Prof pr(ctx, dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U), fl, by);
+      launch_sweep_flow<T>(sa, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s);
+    }
+    CK(cudaGetLastError());
+    return FDFD_OK;
+  }
   for (int l = 0; l < p.n_levels; ++l) {
     const SolveList& sl = ctx->lv_solve[l];
     double fl, by;
@@ -770,11 +857,22 @@ __global__ void add_kernel(double2* a, const double2* b, int n) {
 }
 }  // namespace kadd
 
+// A dataflow sweep whose wait gave up leaves its error word set; report it once
+// (the pinned copy is refreshed at every synchronisation point) and clear it.
+fdfd_status check_flow_err(fdfd_ctx* ctx) {
+  if (!ctx->h_flow_err || *ctx->h_flow_err == 0) return FDFD_OK;
+  *ctx->h_flow_err = 0;
+  CK(cudaMemsetAsync(ctx->d_flow_err, 0, sizeof(int), ctx->stream));
+  return fail(ctx, FDFD_ERR_TIMEOUT, "a sweep gave up waiting for a front it depends on");
+}
+
 fdfd_status any_active(fdfd_ctx* ctx, int S, bool* any, double* maxres) {
   CK(cudaMemcpyAsync(ctx->h_active, ctx->d_active, sizeof(int) * S, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_resid, ctx->d_resid, sizeof(double) * S, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (ctx->growth_pending) ctx->growth_ready = true;
+  CKS(check_flow_err(ctx));
   *any = false;
   *maxres = 0;
   for (int i = 0; i < S; ++i) {
@@ -914,6 +1012,10 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr) {
   return FDFD_OK;
 }
 
+fdfd_status solve_direct(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose,
+                         bool* handled);
+fdfd_status solve_refined(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose);
+
 }  // namespace
 
 // ===========================================================================
@@ -1029,6 +1131,28 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
   if (!ctx || !b_dev || !x_dev || nrhs <= 0 || b_dev == x_dev) return FDFD_ERR_ARG;
   ctx->err.clear();
   if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_solve before fdfd_factor");
+  bool handled = false;
+  const fdfd_status st = solve_direct(ctx, b_dev, x_dev, nrhs, transpose, &handled);
+  if (handled) {
+    // direct paths do not synchronise: their sweep error word is copied back
+    // now and reported by the next call
+    if (ctx->h_flow_err) CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                            ctx->stream));
+    return st;
+  }
+  return solve_refined(ctx, b_dev, x_dev, nrhs, transpose);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Direct solves (plain, FP64 and raw modes); *handled = false when the
+// refined path applies instead.
+fdfd_status solve_direct(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose,
+                         bool* handled) {
+  *handled = true;
+  CKS(check_flow_err(ctx));
   const double2* b = reinterpret_cast<const double2*>(b_dev);
   double2* x = reinterpret_cast<double2*>(x_dev);
   const long long N = n_cells(ctx);
@@ -1067,6 +1191,13 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
     return precond(ctx, nrhs, transpose, b, x);
   }
   (void)N;
+  *handled = false;
+  return FDFD_OK;
+}
+
+fdfd_status solve_refined(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose) {
+  const double2* b = reinterpret_cast<const double2*>(b_dev);
+  double2* x = reinterpret_cast<double2*>(x_dev);
   // Refinement first: its synchronisations make the growth figure of a fresh
   // FP32 factorisation readable for free.  A front with too much growth sends
   // the whole factorisation to FP64 and the solve is repeated on it.
@@ -1077,6 +1208,10 @@ fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nr
   if (fell_back) return fgmres(ctx, b, x, nrhs, transpose);
   return st;
 }
+
+}  // namespace
+
+extern "C" {
 
 fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev, const double* g_dev,
                            const double* weight_dev, double* o_dev, double* F_dev, double* b_adj_dev) {
@@ -1211,7 +1346,7 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   free_ws(ctx);
   free_gm(ctx);
   void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
-                ctx->d_growth_max};
+                ctx->d_growth_max, ctx->d_flow_err};
   for (void* p : ps) free_ptr(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   drop_graphs(ctx);
@@ -1222,6 +1357,7 @@ void fdfd_destroy(fdfd_ctx* ctx) {
     cudaEventDestroy(ctx->gev_out);
   }
   if (ctx->h_growth_max) cudaFreeHost(ctx->h_growth_max);
+  if (ctx->h_flow_err) cudaFreeHost(ctx->h_flow_err);
   if (ctx->h_active) cudaFreeHost(ctx->h_active);
   if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
   delete ctx;

@@ -102,6 +102,23 @@ template <typename T> void launch_sweep_rect(const SolveLaunch& a, int sweep, co
 int sweep_row_block();
 int sweep_col_block();
 
+// One direction of a sweep pair as a single persistent launch (dataflow over
+// the elimination tree).  tasks: the direction's inverse-block, off-diagonal
+// and whole-front tasks in dependency order, x = front | 1<<31 (whole front) |
+// 1<<30 (off-diagonal task), y = first row / column.
+struct FlowQueue {
+  const int2* tasks;
+  int ntasks;              // queue entries; each runs for every launched wavelength
+  int* ctr;                // [1 + 2 * n_omega * n_fronts] ints, zero before the launch
+  const int* need_all;     // [n_fronts] tasks of each front in this queue
+  const int* need_ph1;     // [n_fronts] its phase-1 tasks (inverse-block bottom-up, off-diagonal top-down)
+  int* err;                // set to 1 by a wait that gives up (never cleared by the kernel)
+  int n_fronts;
+};
+template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax,
+                                             int grid, const void* in, void* out, cudaStream_t s);
+int flow_blocks_per_sm(int elem_bytes, int vmax);
+
 // ---- vec.cu: FP64 refinement, objective, gradient ---------------------------
 // y = A x (op = 0) or r = b - A x (op = 1), FP64 matrix-free stencil, all systems.
 void launch_stencil(const DevCoef& c, int n_omega, int nrhs, int transpose, const double2* x,

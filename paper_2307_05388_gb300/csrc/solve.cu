@@ -43,6 +43,11 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Vector entries written by other CTAs of the same launch (the dataflow sweep)
+// are read through L2 only: the per-SM L1 is not coherent.
+__device__ __forceinline__ float2 ldv(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldv(const double2* p) { return __ldcg(p); }
+
 // sum_{c in [c0, c1)} row[c] * vec[c], lanes striding the row (coalesced), warp-reduced.
 // Eight loads per lane are issued before they are used.
 template <typename T>
@@ -104,7 +109,7 @@ __device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& 
   for (int ci = 0; ci < d.nchild; ++ci) {
     const FrontDesc c = a.P.fronts[a.P.children[d.child0 + ci]];
     const int t = a.P.inv[c.inv_off + src];
-    if (t >= 0) v = cadd(v, vbs[c.v_off + c.k + t]);
+    if (t >= 0) v = cadd(v, ldv(vbs + c.v_off + c.k + t));
   }
   return v;
 }
@@ -138,8 +143,8 @@ __device__ __forceinline__ void whole_front(const SolveLaunch& a, const FrontDes
       for (int s = tid; s < n; s += kThreads)
         vs[s] = gather_slot(a, d, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
     } else {
-      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
-      for (int t = tid; t < m; t += kThreads) vs[k + t] = xo[idx[k + t]];
+      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
+      for (int t = tid; t < m; t += kThreads) vs[k + t] = ldv(xo + idx[k + t]);
     }
     __syncthreads();
     if (SWEEP == 0) {                              // y = X_L (P v)_k;  u = v_m - L21 y
@@ -195,21 +200,11 @@ __device__ __forceinline__ void whole_front(const SolveLaunch& a, const FrontDes
   }
 }
 
+// One inverse-block task of a large front (rows or columns from b0).
 template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads)
-tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ in, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[kWarps][32];
-  T* vs = reinterpret_cast<T*>(smem_raw);
-  const int w = blockIdx.y + a.w0;
-  const int2 task = tasks[blockIdx.x];
-  if (task.x < 0) {
-    whole_front<T, SWEEP>(a, a.P.fronts[task.x & 0x7fffffff], w, in, out, vs, red);
-    return;
-  }
-  const FrontDesc d = a.P.fronts[task.x];
+__device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& d, int b0, int w,
+                                         const T* __restrict__ in, T* __restrict__ out, T* vs, T (*red)[32]) {
   const int k = d.k, ldk = d.ldk;
-  const int b0 = task.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
@@ -222,7 +217,7 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
       const T* rhs = in + sys * a.n;
       for (int s = tid; s < k; s += kThreads) vs[s] = gather_slot(a, d, rhs, vbs, SWEEP == 0 ? Pm[s] : s);
     } else {
-      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
+      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
     }
     __syncthreads();
     if (SWEEP == 0) {
@@ -254,6 +249,18 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
   }
 }
 
+template <typename T, int SWEEP>
+__global__ void __launch_bounds__(kThreads)
+tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ in, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[kWarps][32];
+  T* vs = reinterpret_cast<T*>(smem_raw);
+  const int w = blockIdx.y + a.w0;
+  const int2 task = tasks[blockIdx.x];
+  if (task.x < 0) whole_front<T, SWEEP>(a, a.P.fronts[task.x & 0x7fffffff], w, in, out, vs, red);
+  else tri_task<T, SWEEP>(a, a.P.fronts[task.x], task.y, w, in, out, vs, red);
+}
+
 // ---------------------------------------------------------------------------
 // Off-diagonal blocks; task = (front, first row or column).
 //   SWEEP 0: rows t of L21:   u[t] = g_t - L21[t,:] y          (g_t gathered, y = vf[0..k))
@@ -261,29 +268,23 @@ tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ 
 //   SWEEP 2: cols t of U12:   u[t] = g_t - U12[:,t]^T w        (w = vf[0..k))
 //   SWEEP 3: cols a of L21:   t[a] = w[a] - L21[:,a]^T x_m
 // ---------------------------------------------------------------------------
+// One off-diagonal task of a large front (rows or columns from s0).
 template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads)
-rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[kWarps][32];
-  T* vs = reinterpret_cast<T*>(smem_raw);
-  const int w = blockIdx.y + a.w0;
-  const int2 task = tasks[blockIdx.x];
-  const FrontDesc d = a.P.fronts[task.x];
+__device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc& d, int s0, int w,
+                                          T* __restrict__ out, T* vs, T (*red)[32]) {
   const int k = d.k, m = d.m, ld = d.ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int* idx = a.P.idx + d.idx_off;
-  const int s0 = task.y;
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
     const T* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
-      for (int s = tid; s < k; s += kThreads) vs[s] = vf[s];
+      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
     } else {
-      for (int t = tid; t < m; t += kThreads) vs[t] = xo[idx[k + t]];
+      for (int t = tid; t < m; t += kThreads) vs[t] = ldv(xo + idx[k + t]);
     }
     __syncthreads();
     if (SWEEP == 0 || SWEEP == 1) {
@@ -294,7 +295,7 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
         const T acc = warp_dot(Frow, vs, 0, SWEEP == 0 ? k : m, lane);
         if (lane == 0) {
           if (SWEEP == 0) vf[k + row] = csub(gather_slot(a, d, (const T*)nullptr, vbs, k + row), acc);
-          else vf[row] = csub(vf[row], acc);
+          else vf[row] = csub(ldv(vf + row), acc);
         }
       }
     } else {
@@ -305,10 +306,112 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
       const T s = col_dot(base, ld, vs, 0, rows, c < cols, [](int) { return true; }, red);
       if (warp == 0 && c < cols) {
         if (SWEEP == 2) vf[k + c] = csub(gather_slot(a, d, (const T*)nullptr, vbs, k + c), s);
-        else vf[c] = csub(vf[c], s);
+        else vf[c] = csub(ldv(vf + c), s);
       }
     }
     __syncthreads();
+  }
+}
+
+template <typename T, int SWEEP>
+__global__ void __launch_bounds__(kThreads)
+rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[kWarps][32];
+  T* vs = reinterpret_cast<T*>(smem_raw);
+  const int2 task = tasks[blockIdx.x];
+  rect_task<T, SWEEP>(a, a.P.fronts[task.x], task.y, blockIdx.y + a.w0, out, vs, red);
+}
+
+// ---------------------------------------------------------------------------
+// Dataflow sweep: one persistent launch runs every task of one direction.
+// CTAs take tasks from a queue in dependency order (bottom-up levels for
+// L / U^T, top-down for U / L^T; inside a level, the phase-1 tasks of a large
+// front before its phase-2 tasks); a task first waits for the per-front
+// completion counters it depends on, then runs, then bumps its front's
+// counters.  A task only ever waits for tasks earlier in the queue, which are
+// held by running CTAs, so the queue drains whatever the residency.
+//   bottom-up: whole / inverse-block tasks wait for the children; the
+//              off-diagonal tasks of a front wait for its inverse-block tasks;
+//   top-down:  whole / off-diagonal tasks wait for the parent; the
+//              inverse-block tasks of a front wait for its off-diagonal tasks
+//              (and for the parent).
+// Every wait gives up after kSpinLimit polls: it sets *err, and the CTA stops.
+// ---------------------------------------------------------------------------
+constexpr int kSpinLimit = 1 << 21;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool wait_ge(const int* p, int need, int* err) {
+  for (int it = 0; it < kSpinLimit; ++it) {
+    if (ld_acquire(p) >= need) return true;
+    if (ld_acquire(err) != 0) return false;
+    __nanosleep(64);
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+template <typename T, int SWEEP>
+__global__ void __launch_bounds__(kThreads)
+flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[kWarps][32];
+  __shared__ int s_task, s_ok;
+  T* vs = reinterpret_cast<T*>(smem_raw);
+  constexpr bool kUp = SWEEP == 0 || SWEEP == 2;
+  const int nf = q.n_fronts;
+  int* head = q.ctr;
+  int* done = q.ctr + 1;                       // [n_omega launched][nf]
+  int* ph1 = done + (size_t)a.n_omega * nf;    // [n_omega launched][nf]
+  const int total = q.ntasks * a.n_omega;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(head, 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= total) break;
+    const int ti = t / a.n_omega, wl = t - ti * a.n_omega;
+    const int2 task = q.tasks[ti];
+    const unsigned code = (unsigned)task.x;
+    const bool whole = (code >> 31) != 0, rect = ((code >> 30) & 1u) != 0;
+    const int f = (int)(code & 0x3fffffffu);
+    const FrontDesc d = a.P.fronts[f];
+    if (tid == 0) {
+      const int* dn = done + (size_t)wl * nf;
+      bool ok = true;
+      if (kUp) {
+        if (rect) {
+          ok = wait_ge(ph1 + (size_t)wl * nf + f, q.need_ph1[f], q.err);
+        } else {
+          for (int ci = 0; ci < d.nchild && ok; ++ci) {
+            const int c = a.P.children[d.child0 + ci];
+            ok = wait_ge(dn + c, q.need_all[c], q.err);
+          }
+        }
+      } else {
+        if (d.parent >= 0) ok = wait_ge(dn + d.parent, q.need_all[d.parent], q.err);
+        if (ok && !whole && !rect) ok = wait_ge(ph1 + (size_t)wl * nf + f, q.need_ph1[f], q.err);
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int w = wl + a.w0;
+    if (whole) whole_front<T, SWEEP>(a, d, w, in, out, vs, red);
+    else if (rect) rect_task<T, SWEEP>(a, d, task.y, w, out, vs, red);
+    else tri_task<T, SWEEP>(a, d, task.y, w, in, out, vs, red);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      // phase 1: inverse-block tasks bottom-up, off-diagonal tasks top-down
+      if (!whole && (kUp ? !rect : rect)) atomicAdd(ph1 + (size_t)wl * nf + f, 1);
+      atomicAdd(done + (size_t)wl * nf + f, 1);
+    }
   }
 }
 
@@ -345,6 +448,30 @@ void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int n
   }
 }
 
+template <typename T>
+void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax, int grid, const void* in,
+                       void* out, cudaStream_t s) {
+  if (q.ntasks <= 0) return;
+  const size_t smem = (size_t)vmax * sizeof(T);
+  const T* i = reinterpret_cast<const T*>(in);
+  T* o = reinterpret_cast<T*>(out);
+  switch (sweep) {
+    case 0: flow_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
+    case 1: flow_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
+    case 2: flow_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
+    default: flow_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
+  }
+}
+
+int flow_blocks_per_sm(int elem_bytes, int vmax) {
+  int nb = 0;
+  const size_t smem = (size_t)vmax * elem_bytes;
+  const cudaError_t e = elem_bytes == 8
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1>, kThreads, smem)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1>, kThreads, smem);
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
 int sweep_row_block() { return kRowBlk; }
 int sweep_col_block() { return kColBlk; }
 
@@ -359,6 +486,9 @@ cudaError_t solve_init_attributes() {
   FDFD_ATTR(rect_kernel, float2, 0) FDFD_ATTR(rect_kernel, float2, 1) FDFD_ATTR(rect_kernel, float2, 2)
   FDFD_ATTR(rect_kernel, float2, 3) FDFD_ATTR(rect_kernel, double2, 0) FDFD_ATTR(rect_kernel, double2, 1)
   FDFD_ATTR(rect_kernel, double2, 2) FDFD_ATTR(rect_kernel, double2, 3)
+  FDFD_ATTR(flow_kernel, float2, 0) FDFD_ATTR(flow_kernel, float2, 1) FDFD_ATTR(flow_kernel, float2, 2)
+  FDFD_ATTR(flow_kernel, float2, 3) FDFD_ATTR(flow_kernel, double2, 0) FDFD_ATTR(flow_kernel, double2, 1)
+  FDFD_ATTR(flow_kernel, double2, 2) FDFD_ATTR(flow_kernel, double2, 3)
 #undef FDFD_ATTR
   return e;
 }
@@ -369,5 +499,9 @@ template void launch_sweep_tri<double2>(const SolveLaunch&, int, const int2*, in
                                         cudaStream_t);
 template void launch_sweep_rect<float2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
 template void launch_sweep_rect<double2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
+template void launch_sweep_flow<float2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
+                                        cudaStream_t);
+template void launch_sweep_flow<double2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
+                                         cudaStream_t);
 
 }  // namespace fdfd
