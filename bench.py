@@ -51,7 +51,7 @@ def workload_config(wl):
     return {"workload": f"{wl.name}: {wl.nx}x{wl.ny} grid ({wl.n:,} unknowns), dx {wl.dx * 1e3:.0f} nm, "
                         f"{wl.n_omega} wavelength(s) x {wl.n_src} source(s), {w}x{h} design box",
             "nx": wl.nx, "ny": wl.ny, "n_omega": wl.n_omega, "nrhs": wl.n_src, "design_box": [x0, y0, w, h],
-            "factor": "complex FP32 multifrontal + FP64 FGMRES refinement (tol 1e-10)",
+            "factor": "complex FP32 multifrontal + FP64 FGMRES refinement (tol 1e-9)",
             "l2": "flushed between timed steps (512 MB write)"}
 
 

@@ -86,7 +86,7 @@ typedef enum {
 
 typedef struct {
   int mode;                    /* fdfd_mode */
-  double ir_tol;               /* FGMRES stop: ||b - A x|| <= ir_tol ||b|| per system (default 1e-10) */
+  double ir_tol;               /* FGMRES stop: ||b - A x|| <= ir_tol ||b|| per system (default 1e-9) */
   int ir_max_iter;             /* FGMRES iterations per solve across restarts (default 40);
                                   0 returns the raw FP32-factor solution */
   int gmres_restart;           /* Krylov vectors per cycle, 1..16 (default 8) */

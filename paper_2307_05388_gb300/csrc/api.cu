@@ -590,8 +590,10 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           vb += es * 2.0 * (double)d.k * d.k;
         }
       Prof pr(ctx, PK_LU_INV, vf * nwd, vb * nwd);
-      if (ctx->opt.pivoting == 1)   // diagonal blocks already inverted by the panel steps
+      if (ctx->opt.pivoting == 1) {   // diagonal blocks factored by the panel steps
+        launch_lu_diag_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
         launch_lu_inv_blocked<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
+      }
       else
         launch_lu_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
     }
@@ -1026,7 +1028,7 @@ extern "C" {
 void fdfd_default_options(fdfd_options* o) {
   if (!o) return;
   o->mode = FDFD_MODE_MIXED;
-  o->ir_tol = 1e-10;
+  o->ir_tol = 1e-9;
   o->ir_max_iter = 40;
   o->gmres_restart = 8;
   o->growth_bound = 1e6;

@@ -608,18 +608,19 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
 // ---------------------------------------------------------------------------
 // Block-local pivoting: one launch per panel step does everything that depends
 // only on the 32 x 32 diagonal block B = F[J, J], J = [j0, j0 + nb):
-//   every CTA LU-factors B itself (warp 0, rows in registers, pivot rows chosen
-//   inside B) and forms the triangular inverses Li = L_JJ^-1, Ui = U_JJ^-1 it
-//   needs (deterministic: every CTA gets the same bits), then does one role:
-//     role D (block 0): the row permutation of J into perm, the inverse blocks
-//                       into the inverse store (they are the diagonal blocks of
-//                       L11^-1 and U11^-1), growth of the block's multipliers;
-//     role L: rows r >= j0 + nb, L[r, J] = F[r, J] Ui            (64 rows / CTA);
-//     role U: columns c >= j0 + nb, U[J, c] = Li (P F)[J, c]     (64 columns / CTA);
-//     role P: columns c < j0, F[J, c] <- (P F)[J, c]             (64 columns / CTA).
-// The factored diagonal block itself is not stored back (nothing reads it:
-// the sweeps and the inverse use Li, Ui).  Roles touch disjoint entries of F
-// and read B only, so the CTAs are independent.
+//   every CTA LU-factors B itself (warps 0-3, rows in registers, pivot rows
+//   chosen inside B; deterministic, so every CTA gets the same bits) while
+//   warps 4-7 stage the CTA's operand, then does one role:
+//     role D (block 0): the row permutation of J into perm, the packed L\U of B
+//                       into the diagonal block of the inverse store (inverted
+//                       there later by lu_diag_inv), growth of its multipliers;
+//     role L: rows r >= j0 + nb, L[r, J] U_JJ = F[r, J]          (64 rows / CTA);
+//     role U: columns c >= j0 + nb, L_JJ U[J, c] = (P F)[J, c]   (64 columns / CTA);
+//     role P: columns c < j0, F[J, c] <- (P F)[J, c]             (64 columns / CTA);
+//   L and U by one-thread-per-row/column substitution against the factored B.
+// The factored diagonal block is not stored back into F (nothing reads it there:
+// the sweeps and the inverse use the inverse store).  Roles touch disjoint
+// entries of F and read B only, so the CTAs are independent.
 // ---------------------------------------------------------------------------
 constexpr int kStepRows = 64;
 
@@ -635,87 +636,107 @@ __device__ __forceinline__ double2 fast_crcp(double2 z) {
 }
 
 // LU of the nb x nb block at (j0, j0) with row pivoting inside the block, by
-// warp 0 with lane = row.  No rows are swapped: at step p the pivot is the
-// unused lane r with the largest |a_p| (one redux over packed keys: |a_p|^2 in
-// the high bits, 31 - lane in the low 5 bits, so ties go to the lower lane);
-// the other unused lanes are eliminated against it.  On return LU[p] holds
-// row p of L\U in pivot order, src[p] the block row it came from, dinv[p] =
-// 1 / U[p][p].  Returns this lane's largest |multiplier|^2 (NaN -> inf).
+// warps 0-3 (lane = row; warp w holds columns 8w..8w+7 in registers).  No rows
+// are swapped: at step p the warp owning column p picks the unused lane r with
+// the largest |a_p| (one redux over packed keys: |a_p|^2 in the high bits,
+// 31 - lane in the low 5, so ties go to the lower lane) and publishes r and
+// every lane's multiplier through shared memory (double-buffered, one 128-thread
+// named barrier per step); each warp then updates its own columns.  On return
+// (after the caller's __syncthreads) LU[p] holds row p of L\U in pivot order,
+// src[p] the block row it came from, dinv[p] = 1 / U[p][p].  Returns this
+// lane's largest |multiplier|^2 (NaN -> inf).
 template <typename T>
-__device__ __forceinline__ typename RealOf<T>::type diag_lu_warp(const T* __restrict__ F, int ld, int j0, int nb,
-                                                                 T (*LU)[kMaxNb + 1], int* src, T* dinv) {
+__device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __restrict__ F, int ld, int j0, int nb,
+                                                                   T (*LU)[kMaxNb + 1], int* src, T* dinv,
+                                                                   T (*s_l)[32], int* s_r) {
   using R = typename RealOf<T>::type;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T one = cmk(R(1), R(0));
-  T row[kMaxNb];
+  T a[8];
 #pragma unroll
-  for (int j = 0; j < kMaxNb; ++j)
-    row[j] = (lane < nb && j < nb) ? F[(size_t)(j0 + lane) * ld + j0 + j] : (lane == j ? one : czero<T>());
+  for (int c = 0; c < 8; ++c) {
+    const int j = 8 * warp + c;
+    a[c] = (lane < nb && j < nb) ? F[(size_t)(j0 + lane) * ld + j0 + j] : (lane == j ? one : czero<T>());
+  }
   bool used = false;
   int myp = lane;                 // padding lanes (>= nb) keep their own position
-  T myd = one;
   R g = 0;
+  for (int p = 0; p < nb; ++p) {
+    const int buf = p & 1, cp = p & 7;
+    if ((p >> 3) == warp) {
+      T ap = a[0];
 #pragma unroll
-  for (int p = 0; p < kMaxNb; ++p) {
-    if (p < nb) {
-      const float v = (float)cabs2(row[p]);
+      for (int c = 1; c < 8; ++c)
+        if (c == cp) ap = a[c];
+      const float v = (float)cabs2(ap);
       unsigned key = used ? 0u : ((__float_as_uint(v) & ~31u) | (unsigned)(31 - lane));
       if (!used && !(v == v)) key = 0xffffffe0u | (unsigned)(31 - lane);   // NaN wins
       const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
       const int r = 31 - (int)(kmax & 31u);
-      const T inv = fast_crcp(shfl_c(row[p], r));
-      if (lane == r) { used = true; myp = p; myd = inv; }
-      const bool elim = !used;
-      const T l = cmul(row[p], inv);
+      const T inv = fast_crcp(shfl_c(ap, r));
+      const bool elim = !used && lane != r;
+      const T l = elim ? cmul(ap, inv) : czero<T>();
+      s_l[buf][lane] = l;
+      if (lane == 0) { s_r[buf] = r; src[p] = r; dinv[p] = inv; }
       if (elim) {
-        row[p] = l;
-        const R a2 = cabs2(l);
-        g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
-      }
 #pragma unroll
-      for (int j = p + 1; j < kMaxNb; ++j) {
-        const T u = shfl_c(row[j], r);
-        if (elim) row[j] = cfms(l, u, row[j]);
+        for (int c = 0; c < 8; ++c)
+          if (c == cp) a[c] = l;        // the multiplier is stored in column p
       }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const int r = s_r[buf];
+    const T l = s_l[buf][lane];
+    if (lane == r) { used = true; myp = p; }
+    {
+      const R a2 = cabs2(l);
+      g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = 8 * warp + c;
+      const T u = shfl_c(a[c], r);
+      if (j > p) a[c] = cfms(l, u, a[c]);   // l = 0 on the pivot and on used lanes
     }
   }
 #pragma unroll
-  for (int j = 0; j < kMaxNb; ++j) LU[myp][j] = row[j];
-  src[myp] = lane;
-  dinv[myp] = myd;
+  for (int c = 0; c < 8; ++c) LU[myp][8 * warp + c] = a[c];
+  if (lane >= nb && warp == 0) { src[lane] = lane; dinv[lane] = one; }   // padding rows stay in place
   return g;
 }
 
-// Column c = lane of Li (unit lower, diagonal included) or Ui from LU in shared memory.
+// Column c = lane of Li (unit lower, diagonal included) or Ui, from LU in
+// shared memory, written into out (zero outside the triangle).
 template <typename T>
 __device__ __forceinline__ void tri_inverse_col(const T (*LU)[kMaxNb + 1], const T* dinv, bool upper,
                                                 T (*out)[kMaxNb + 1]) {
   using R = typename RealOf<T>::type;
   const int c = threadIdx.x & 31;
-  T x[kMaxNb];
   if (!upper) {
-#pragma unroll
     for (int i = 0; i < kMaxNb; ++i) {
       T a0 = (i == c) ? cmk(R(1), R(0)) : czero<T>(), a1 = czero<T>();
-#pragma unroll
-      for (int l = 0; l < i; ++l) {
-        if (l & 1) a1 = cfms(LU[i][l], x[l], a1);
-        else a0 = cfms(LU[i][l], x[l], a0);
+      if (i > c) {
+        int l = c;
+        for (; l + 1 < i; l += 2) {
+          a0 = cfms(LU[i][l], out[l][c], a0);
+          a1 = cfms(LU[i][l + 1], out[l + 1][c], a1);
+        }
+        if (l < i) a0 = cfms(LU[i][l], out[l][c], a0);
       }
-      x[i] = cadd(a0, a1);
-      out[i][c] = x[i];
+      out[i][c] = (i >= c) ? cadd(a0, a1) : czero<T>();
     }
   } else {
-#pragma unroll
     for (int i = kMaxNb - 1; i >= 0; --i) {
       T a0 = (i == c) ? cmk(R(1), R(0)) : czero<T>(), a1 = czero<T>();
-#pragma unroll
-      for (int l = i + 1; l < kMaxNb; ++l) {
-        if (l & 1) a1 = cfms(LU[i][l], x[l], a1);
-        else a0 = cfms(LU[i][l], x[l], a0);
+      if (i < c) {
+        int l = i + 1;
+        for (; l + 1 <= c; l += 2) {
+          a0 = cfms(LU[i][l], out[l][c], a0);
+          a1 = cfms(LU[i][l + 1], out[l + 1][c], a1);
+        }
+        if (l <= c) a0 = cfms(LU[i][l], out[l][c], a0);
       }
-      x[i] = cmul(cadd(a0, a1), dinv[i]);
-      out[i][c] = x[i];
+      out[i][c] = (i <= c) ? cmul(cadd(a0, a1), dinv[i]) : czero<T>();
     }
   }
 }
@@ -726,12 +747,12 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   using R = typename RealOf<T>::type;
   using Blk = T[kMaxNb + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Blk* LU = reinterpret_cast<Blk*>(smem_raw);     // [32][33] each
-  Blk* Li = LU + kMaxNb;
-  Blk* Ui = Li + kMaxNb;
-  Blk* Ws = Ui + kMaxNb;                          // [64][33]: role L 64 rows x J; roles U, P: [c][p]
+  Blk* LU = reinterpret_cast<Blk*>(smem_raw);     // [32][33]
+  Blk* Ws = LU + kMaxNb;                          // [64][33]: role L 64 rows x J; roles U, P: [c][p]
   T* dinv = reinterpret_cast<T*>(Ws + kStepRows);
+  T (*s_l)[32] = reinterpret_cast<T (*)[32]>(dinv + kMaxNb);   // [2][32] multipliers of a step
   __shared__ int src[kMaxNb];
+  __shared__ int s_r[2];
   __shared__ R s_g[8];
   const int w = blockIdx.z + a.w0;
   const int f = flist[blockIdx.y];
@@ -756,75 +777,80 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   R g = 0;
-  if (warp == 0) g = diag_lu_warp<T>(F, ld, j0, nb, LU, src, dinv);
-  __syncthreads();
-  if ((role == 0 || role == 2) && warp == 0) tri_inverse_col<T>(LU, dinv, false, Li);
-  if ((role == 0 || role == 1) && warp == 1) tri_inverse_col<T>(LU, dinv, true, Ui);
-  if (role == 1) {
-    // stage rows [lo, lo + 64) of the block columns
-    for (int e = tid; e < kStepRows * kMaxNb; e += 256) {
+  if (warp < 4) {
+    g = diag_lu_4warps<T>(F, ld, j0, nb, LU, src, dinv, s_l, s_r);
+  } else if (role == 1) {
+    // meanwhile warps 4-7 stage rows [lo, lo + 64) of the block columns
+    for (int e = tid - 128; e < kStepRows * kMaxNb; e += 128) {
       const int rr = e >> 5, l = e & 31, r = lo + rr;
       Ws[rr][l] = (r < n && l < nb) ? F[(size_t)r * ld + j0 + l] : czero<T>();
     }
   } else if (role >= 2) {
-    // stage the block rows, permuted, over columns [lo, lo + 64)
+    // ... or the block rows (not yet permuted) over columns [lo, lo + 64)
     const int hi = role == 2 ? n : j0;
-    for (int e = tid; e < kStepRows * kMaxNb; e += 256) {
+    for (int e = tid - 128; e < kStepRows * kMaxNb; e += 128) {
       const int p = e >> 6, cc = e & 63, c = lo + cc;
-      Ws[cc][p] = (c < hi && p < nb) ? F[(size_t)(j0 + src[p]) * ld + c] : czero<T>();
+      Ws[cc][p] = (c < hi && p < nb) ? F[(size_t)(j0 + p) * ld + c] : czero<T>();
     }
   }
   __syncthreads();
   if (role == 0) {
-    // rows of J move only at this step (earlier and later steps permute their own blocks)
+    // rows of J move only at this step (earlier and later steps permute their own
+    // blocks); the packed L\U of the block goes to the inverse store, where
+    // lu_diag_inv later replaces it by its two triangular inverses
     if (tid < nb) a.perm[(size_t)w * a.perm_stride + d.piv_off + j0 + tid] = j0 + src[tid];
     T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
     for (int e = tid; e < nb * nb; e += 256) {
       const int i = e / nb, j = e - i * nb;
-      X[(size_t)(j0 + i) * d.ldk + j0 + j] = (i > j) ? Li[i][j] : Ui[i][j];
+      X[(size_t)(j0 + i) * d.ldk + j0 + j] = LU[i][j];
     }
   } else if (role == 1) {
-    // L[r][j] = sum_{l <= j} F[r][l] Ui[l][j]: thread = (column j, rows warp + 8 q)
-    T acc[8];
+    // L[r, J] U_JJ = F[r, J]: one thread per row, right-looking substitution
+    if (tid < kStepRows) {
+      T x[kMaxNb];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = czero<T>();
-#pragma unroll 8
-    for (int l = 0; l < kMaxNb; ++l) {
-      const T u = Ui[l][lane];
+      for (int j = 0; j < kMaxNb; ++j) x[j] = Ws[tid][j];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] = cfma(Ws[warp + 8 * q][l], u, acc[q]);
-    }
+      for (int j = 0; j < kMaxNb; ++j) {
+        x[j] = cmul(x[j], dinv[j]);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int r = lo + warp + 8 * q;
-      if (r < n && lane < nb) {
-        F[(size_t)r * ld + j0 + lane] = acc[q];
-        const R a2 = cabs2(acc[q]);
-        g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
+        for (int jj = j + 1; jj < kMaxNb; ++jj) x[jj] = cfms(x[j], LU[j][jj], x[jj]);
+      }
+      const int r = lo + tid;
+      if (r < n) {
+#pragma unroll
+        for (int j = 0; j < kMaxNb; ++j)
+          if (j < nb) {
+            F[(size_t)r * ld + j0 + j] = x[j];
+            const R a2 = cabs2(x[j]);
+            g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
+          }
       }
     }
+  } else if (role == 2) {
+    // L_JJ U[J, c] = (P F)[J, c]: one thread per column, unit-lower substitution
+    if (tid < kStepRows) {
+      const int c = lo + tid;
+      T x[kMaxNb];
+#pragma unroll
+      for (int i = 0; i < kMaxNb; ++i) x[i] = Ws[tid][src[i]];
+#pragma unroll
+      for (int i = 0; i < kMaxNb; ++i)
+#pragma unroll
+        for (int ii = i + 1; ii < kMaxNb; ++ii) x[ii] = cfms(LU[ii][i], x[i], x[ii]);
+      if (c < n)
+#pragma unroll
+        for (int i = 0; i < kMaxNb; ++i)
+          if (i < nb) F[(size_t)(j0 + i) * ld + c] = x[i];
+    }
   } else {
-    // role U: U[i][c] = sum_{l <= i} Li[i][l] (P F)[l][c];  role P: (P F)[i][c].
-    // thread = (column cc = tid & 63, rows i = (tid >> 6) + 4 q)
+    // role P: (P F)[i][c] for the columns left of the block
     const int cc = tid & 63, ig = tid >> 6;
     const int c = lo + cc;
-    const bool ok = c < (role == 2 ? n : j0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int i = ig + 4 * q;
-      T v;
-      if (role == 2) {
-        T a0 = czero<T>(), a1 = czero<T>();
-#pragma unroll
-        for (int l = 0; l < kMaxNb; ++l) {
-          if (l & 1) a1 = cfma(Li[i][l], Ws[cc][l], a1);
-          else a0 = cfma(Li[i][l], Ws[cc][l], a0);
-        }
-        v = cadd(a0, a1);   // Li is unit lower (zero above the diagonal)
-      } else {
-        v = Ws[cc][i];
-      }
-      if (ok && i < nb) F[(size_t)(j0 + i) * ld + c] = v;
+      if (c < j0 && i < nb) F[(size_t)(j0 + i) * ld + c] = Ws[cc][src[i]];
     }
   }
   if (role <= 1) {
@@ -975,8 +1001,51 @@ lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
   }
 }
 
-// dynamic shared memory of lu_step_local_kernel: LU, Li, Ui, the 64 x 33 staging tile, 1/U[p][p]
-size_t step_local_smem(size_t es) { return ((size_t)(3 * kMaxNb + kStepRows) * (kMaxNb + 1) + kMaxNb) * es; }
+// Diagonal 32 x 32 blocks of the inverse store hold packed L\U factors (written
+// by the panel steps); replaces each by L^-1 (strictly lower part, unit
+// diagonal implied) and U^-1 (upper part with the diagonal).  One CTA per
+// (block, front); warp 0 inverts L, warp 1 inverts U.
+template <typename T>
+__global__ void __launch_bounds__(64)
+lu_diag_inv_kernel(FactorLaunch a, const int* __restrict__ flist) {
+  using R = typename RealOf<T>::type;
+  using Blk = T[kMaxNb + 1];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Blk* LU = reinterpret_cast<Blk*>(smem_raw);     // [32][33] each
+  Blk* Li = LU + kMaxNb;
+  Blk* Ui = Li + kMaxNb;
+  T* dinv = reinterpret_cast<T*>(Ui + kMaxNb);
+  const int w = blockIdx.z + a.w0;
+  const FrontDesc d = a.P.fronts[flist[blockIdx.y]];
+  const int j0 = blockIdx.x * kMaxNb;
+  if (j0 >= d.k) return;
+  const int nb = min(kMaxNb, d.k - j0);
+  T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const T one = cmk(R(1), R(0));
+  for (int e = threadIdx.x; e < kMaxNb * kMaxNb; e += 64) {
+    const int i = e >> 5, j = e & 31;
+    LU[i][j] = (i < nb && j < nb) ? X[(size_t)(j0 + i) * d.ldk + j0 + j] : (i == j ? one : czero<T>());
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxNb) dinv[threadIdx.x] = fast_crcp(LU[threadIdx.x][threadIdx.x]);
+  __syncthreads();
+  if (threadIdx.x < 32) tri_inverse_col<T>(LU, dinv, false, Li);
+  else tri_inverse_col<T>(LU, dinv, true, Ui);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nb * nb; e += 64) {
+    const int i = e / nb, j = e - i * nb;
+    X[(size_t)(j0 + i) * d.ldk + j0 + j] = (i > j) ? Li[i][j] : Ui[i][j];
+  }
+}
+
+// dynamic shared memory of lu_diag_inv_kernel: LU, Li, Ui, 1/U[p][p]
+size_t diag_inv_smem(size_t es) { return ((size_t)3 * kMaxNb * (kMaxNb + 1) + kMaxNb) * es; }
+
+// dynamic shared memory of lu_step_local_kernel: LU, the 64 x 33 staging tile, 1/U[p][p],
+// the multipliers of one step (double-buffered)
+size_t step_local_smem(size_t es) {
+  return ((size_t)(kMaxNb + kStepRows) * (kMaxNb + 1) + kMaxNb + 2 * 32) * es;
+}
 
 // Off-diagonal blocks of L11^-1 and U11^-1 when their 32 x 32 diagonal blocks
 // are already in the inverse store (block-local pivoting writes them at every
@@ -1289,6 +1358,9 @@ cudaError_t factor_init_attributes() {
   e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            2 * 64 * 64 * 16);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_diag_inv_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)diag_inv_smem(16));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_step_local_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)step_local_smem(8));
   if (e != cudaSuccess) return e;
@@ -1348,6 +1420,13 @@ void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j
 }
 
 template <typename T>
+void launch_lu_diag_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s) {
+  if (nf <= 0 || kmax <= 0) return;
+  lu_diag_inv_kernel<T><<<dim3((kmax + kMaxNb - 1) / kMaxNb, nf, a.n_omega), 64, diag_inv_smem(sizeof(T)), s>>>(
+      a, flist);
+}
+
+template <typename T>
 void launch_lu_inv_blocked(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s) {
   if (nf <= 0 || kmax <= 0) return;
   const int nblk = (kmax + 31) / 32;
@@ -1396,6 +1475,7 @@ void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax
   template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, int, cudaStream_t); \
   template void launch_lu_step_local<T>(const FactorLaunch&, const int*, int, int, int, cudaStream_t); \
   template void launch_lu_inv_blocked<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
+  template void launch_lu_diag_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \

@@ -53,6 +53,9 @@ template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist
 // inverse store (then launch_lu_gemm for the trailing update); nmax = largest n.
 template <typename T> void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0,
                                                 int nmax, cudaStream_t s);
+// Diagonal blocks of the inverse store: packed L\U (from the panel steps) -> L^-1, U^-1
+template <typename T> void launch_lu_diag_inv(const FactorLaunch& a, const int* flist, int nf, int kmax,
+                                              cudaStream_t s);
 // L11^-1 / U11^-1 off-diagonal blocks from the diagonal blocks already in the
 // inverse store (block-local pivoting path)
 template <typename T> void launch_lu_inv_blocked(const FactorLaunch& a, const int* flist, int nf, int kmax,

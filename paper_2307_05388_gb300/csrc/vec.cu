@@ -117,70 +117,81 @@ __global__ void cvt_to64_kernel(double2* dst, const T* src, const double* scale,
 constexpr int kDotThreads = 256;
 constexpr int kMaxDot = 17;
 
+// Partial sums of h[s][i] = sum_t conj(V_i[s][t]) w[s][t]: one CTA per
+// (chunk of kDotPer * 256 entries, vector i, system), one accumulator per
+// thread (low register use keeps the FP64 pipes fed by many warps), CTA
+// reduction in a fixed order.
+constexpr int kDotPer = 4;
+
 __global__ void __launch_bounds__(kDotThreads)
 multidot_partial_kernel(const double2* __restrict__ V, long long vstride, int nv,
                         const double2* __restrict__ w, long long n, double2* partial, int nblk) {
-  __shared__ double2 red[kDotThreads / 32][kMaxDot];
-  const int sys = blockIdx.y;
-  double2 acc[kMaxDot];
-#pragma unroll
-  for (int i = 0; i < kMaxDot; ++i) acc[i] = make_double2(0, 0);
+  __shared__ double2 red[kDotThreads / 32];
+  const int i = blockIdx.y, sys = blockIdx.z;
   const double2* W = w + (size_t)sys * n;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)nblk * blockDim.x) {
-    const double2 wv = W[t];
+  const double2* Vi = V + (size_t)i * vstride + (size_t)sys * n;
+  const long long t0 = (long long)blockIdx.x * (kDotThreads * kDotPer) + threadIdx.x;
+  double2 vv[kDotPer], ww[kDotPer];
 #pragma unroll
-    for (int i = 0; i < kMaxDot; ++i)
-      if (i < nv) acc[i] = cfma(cconj(V[(size_t)i * vstride + (size_t)sys * n + t]), wv, acc[i]);
+  for (int u = 0; u < kDotPer; ++u) {
+    const long long t = t0 + (long long)u * kDotThreads;
+    vv[u] = t < n ? Vi[t] : make_double2(0, 0);
+    ww[u] = t < n ? W[t] : make_double2(0, 0);
   }
+  double2 acc = make_double2(0, 0);
+#pragma unroll
+  for (int u = 0; u < kDotPer; ++u) acc = cfma(cconj(vv[u]), ww[u], acc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < kMaxDot; ++i) {
-    if (i >= nv) break;
-    double2 v = acc[i];
-    for (int o = 16; o > 0; o >>= 1) {
-      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
-    if (lane == 0) red[warp][i] = v;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
   }
+  if (lane == 0) red[warp] = acc;
   __syncthreads();
-  if (threadIdx.x < nv) {
-    double2 s = make_double2(0, 0);
-    for (int q = 0; q < kDotThreads / 32; ++q) s = cadd(s, red[q][threadIdx.x]);
-    partial[((size_t)sys * kMaxDot + threadIdx.x) * nblk + blockIdx.x] = s;
+  if (threadIdx.x == 0) {
+    double2 s = red[0];
+    for (int q = 1; q < kDotThreads / 32; ++q) s = cadd(s, red[q]);
+    partial[((size_t)sys * kMaxDot + i) * nblk + blockIdx.x] = s;
   }
 }
 
+// One warp per (system, vector): lane-strided partial sums, then a shuffle tree
+// (fixed order, so the result does not depend on timing).
 __global__ void multidot_final_kernel(const double2* partial, int nblk, int nv, double2* out, int out_ld) {
   const int sys = blockIdx.x;
-  const int i = threadIdx.x;
+  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (i >= nv) return;
   double2 s = make_double2(0, 0);
   const double2* p = partial + ((size_t)sys * kMaxDot + i) * nblk;
-  for (int b = 0; b < nblk; ++b) s = cadd(s, p[b]);
-  out[(size_t)sys * out_ld + i] = s;
+  for (int b = lane; b < nblk; b += 32) s = cadd(s, p[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  if (lane == 0) out[(size_t)sys * out_ld + i] = s;
 }
 
+// w[s] -= sum_i h[s][i] V_i[s]; the coefficients sit in shared memory.
 __global__ void multiaxpy_kernel(const double2* __restrict__ V, long long vstride, int nv,
                                  const double2* __restrict__ h, int h_ld, double2* w, long long n,
                                  const int* active) {
+  __shared__ double2 hh[kMaxDot];
   const int sys = blockIdx.y;
   if (active && !active[sys]) return;
-  double2 hh[kMaxDot];
-#pragma unroll
-  for (int i = 0; i < kMaxDot; ++i) hh[i] = (i < nv) ? h[(size_t)sys * h_ld + i] : make_double2(0, 0);
+  if (threadIdx.x < nv) hh[threadIdx.x] = h[(size_t)sys * h_ld + threadIdx.x];
+  __syncthreads();
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     double2 acc = w[(size_t)sys * n + t];
-#pragma unroll
-    for (int i = 0; i < kMaxDot; ++i)
-      if (i < nv) acc = cfms(hh[i], V[(size_t)i * vstride + (size_t)sys * n + t], acc);
+    for (int i = 0; i < nv; ++i) acc = cfms(hh[i], V[(size_t)i * vstride + (size_t)sys * n + t], acc);
     w[(size_t)sys * n + t] = acc;
   }
 }
 
 int grid_for(long long n) {
   long long b = (n + 255) / 256;
-  return (int)(b < 2048 ? b : 2048);
+  return (int)(b < 4096 ? b : 4096);
 }
 
 }  // namespace
@@ -219,9 +230,9 @@ template void launch_cvt_from64<double2>(double2*, const double2*, const double*
 template void launch_cvt_to64<float2>(double2*, const float2*, const double*, long long, int, cudaStream_t);
 template void launch_cvt_to64<double2>(double2*, const double2*, const double*, long long, int, cudaStream_t);
 
+// chunks of kDotPer entries per thread
 int multidot_blocks(long long n) {
-  long long b = (n + kDotThreads * 4 - 1) / (kDotThreads * 4);
-  if (b > 304) b = 304;
+  long long b = (n + kDotThreads * kDotPer - 1) / (kDotThreads * kDotPer);
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -229,8 +240,8 @@ int multidot_max_vectors() { return kMaxDot; }
 
 void launch_multidot(const double2* V, long long vstride, int nv, const double2* w, long long n, int nsys,
                      double2* partial, int nblk, double2* out, int out_ld, cudaStream_t s) {
-  multidot_partial_kernel<<<dim3(nblk, nsys), kDotThreads, 0, s>>>(V, vstride, nv, w, n, partial, nblk);
-  multidot_final_kernel<<<nsys, 32, 0, s>>>(partial, nblk, nv, out, out_ld);
+  multidot_partial_kernel<<<dim3(nblk, nv, nsys), kDotThreads, 0, s>>>(V, vstride, nv, w, n, partial, nblk);
+  multidot_final_kernel<<<nsys, 32 * kMaxDot, 0, s>>>(partial, nblk, nv, out, out_ld);
 }
 
 void launch_multiaxpy(const double2* V, long long vstride, int nv, const double2* h, int h_ld, double2* w,
