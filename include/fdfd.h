@@ -64,7 +64,9 @@ typedef enum {
   FDFD_ERR_CUDA = 4,           /* a CUDA runtime error; text in fdfd_last_error */
   FDFD_ERR_PIVOT = 5,          /* pivot growth above the bound even in FP64 */
   FDFD_ERR_NOT_CONVERGED = 6,  /* refinement stopped above the tolerance; best x returned */
-  FDFD_ERR_TIMEOUT = 7         /* reserved for bounded device waits */
+  FDFD_ERR_TIMEOUT = 7         /* a bounded device wait of a dataflow sweep gave up (a front it
+                                  depends on never completed); reported by the call that
+                                  synchronises next, the context stays usable */
 } fdfd_status;
 
 typedef struct { int nx, ny; } fdfd_grid;
@@ -210,6 +212,17 @@ fdfd_status fdfd_profile_get(fdfd_ctx* ctx, fdfd_kernel_profile* out, int max_ou
 
 /* Resets the SF/NF/BS counters. */
 void fdfd_reset_counters(fdfd_ctx* ctx);
+
+/* Self-test of the failure path of the dataflow sweeps (the paper has no
+ * counterpart).  Every wait of a sweep task on the fronts it depends on polls
+ * a completion counter a bounded number of times (about a second) and then
+ * gives up: it sets the context's device error word and its CTA stops, so a
+ * front that never completes ends the launch with FDFD_ERR_TIMEOUT instead of
+ * hanging the GPU.  This call runs one such wait on a counter that nothing
+ * increments (one small kernel on the context's stream, synchronised) and
+ * returns FDFD_ERR_TIMEOUT when the wait gave up as designed; the error word
+ * is cleared and the context stays usable.  Any other status is a failure. */
+fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx);
 
 /* Text of the last error on this context ("" if none); valid until the next call. */
 const char* fdfd_last_error(const fdfd_ctx* ctx);

@@ -1304,6 +1304,25 @@ fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k, int* m, int* parent, int* le
   return FDFD_OK;
 }
 
+fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx) {
+  if (!ctx) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  CKS(ensure_runtime(ctx));
+  CKS(check_flow_err(ctx));
+  int* flag = nullptr;
+  CK(dalloc(&flag, sizeof(int)));
+  const cudaError_t e0 = cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream);
+  const cudaError_t e1 = e0 == cudaSuccess ? launch_wait_probe(flag, ctx->d_flow_err, ctx->stream) : e0;
+  const cudaError_t e2 = e1 == cudaSuccess ? cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int),
+                                                             cudaMemcpyDeviceToHost, ctx->stream)
+                                           : e1;
+  const cudaError_t e3 = cudaStreamSynchronize(ctx->stream);
+  cudaFree(flag);
+  CK(e2);
+  CK(e3);
+  return check_flow_err(ctx);
+}
+
 fdfd_status fdfd_profile_enable(fdfd_ctx* ctx, int on) {
   if (!ctx) return FDFD_ERR_ARG;
   if (ctx->device >= 0) CK(cudaStreamSynchronize(ctx->stream));

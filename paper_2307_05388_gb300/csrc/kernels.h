@@ -121,6 +121,8 @@ struct FlowQueue {
 template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax,
                                              int grid, const void* in, void* out, cudaStream_t s);
 int flow_blocks_per_sm(int elem_bytes, int vmax);
+// one bounded wait on a zero flag (gives up, sets *err); for the self-test entry point
+cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s);
 
 // ---- vec.cu: FP64 refinement, objective, gradient ---------------------------
 // y = A x (op = 0) or r = b - A x (op = 1), FP64 matrix-free stencil, all systems.

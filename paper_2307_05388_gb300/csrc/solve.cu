@@ -448,6 +448,17 @@ void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int n
   }
 }
 
+// One wait on *flag >= 1 (nothing sets it) by one thread: exercises the
+// bounded wait of the dataflow sweep, which must give up, set *err and return.
+__global__ void wait_probe_kernel(const int* flag, int* err) {
+  if (threadIdx.x == 0) (void)wait_ge(flag, 1, err);
+}
+
+cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(flag, err);
+  return cudaGetLastError();
+}
+
 template <typename T>
 void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax, int grid, const void* in,
                        void* out, cudaStream_t s) {

@@ -26,7 +26,8 @@ MODE_MIXED, MODE_F64, MODE_PLAIN = 0, 1, 2
 EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
-           "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes"]
+           "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
+           "fdfd_selftest_wait"]
 
 
 class Grid(C.Structure):
@@ -250,6 +251,10 @@ class Solver:
 
     def reset_counters(self):
         _lib.fdfd_reset_counters(self._h)
+
+    def selftest_wait(self) -> int:
+        """Runs one bounded sweep wait on a counter nothing sets; returns the status (7 = gave up as designed)."""
+        return int(_lib.fdfd_selftest_wait(self._h))
 
     def plan_fronts(self):
         """(k, m, parent, level, design, idx) of the symbolic plan as numpy arrays."""

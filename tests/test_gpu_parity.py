@@ -209,6 +209,23 @@ def test_nan_permittivity_reports_pivot_error():
     assert e.value.status == 5
 
 
+def test_bounded_sweep_wait_gives_up_and_context_survives():
+    """A dataflow-sweep wait on a counter nothing sets gives up (FDFD_ERR_TIMEOUT, about a
+    second) instead of hanging; the context then still solves correctly."""
+    wl = W.make("c1")
+    s = U.make_solver(wl)
+    assert s.selftest_wait() == 7
+    x, ref, _ = _solve_case(wl, 1, FD.MODE_MIXED)
+    assert O.rel_err(x, ref) <= FIELD_TOL
+    s2 = U.make_solver(wl)
+    s2.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
+    assert s2.selftest_wait() == 7
+    b = torch.from_numpy(W.random_complex((1, 1, wl.n), 5)).to(DEV)
+    x2 = s2.solve(b).cpu().numpy()
+    ref2 = _oracle_fields(wl, wl.eps_full(), False, b.cpu().numpy())
+    assert O.rel_err(x2, ref2) <= FIELD_TOL
+
+
 def test_solve_before_factor_is_state_error():
     wl = W.make_small(12, 12, 2, (3, 3, 4, 4), seed=2)
     s = U.make_solver(wl)
