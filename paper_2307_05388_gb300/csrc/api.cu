@@ -33,8 +33,6 @@ struct TaskList {
   int off = 0, n = 0;      // int2 (front, first row or column) tasks at d_lists + off
 };
 
-// Fronts up to this size are swept by one CTA each (no split into tasks).
-constexpr int kSolveWholeFront = 128;
 
 // Sweep tasks of one level; index 0 = row tasks (sweeps L, U), 1 = column tasks (U^T, L^T).
 struct SolveList {
@@ -89,13 +87,12 @@ struct fdfd_ctx {
   std::vector<LevelList> lv_full[2], lv_design[2];   // [precision 0 = c64, 1 = c128]
   std::vector<SolveList> lv_solve;
   // dataflow sweep queues [task type: 0 rows, 1 columns][direction: 0 bottom-up, 1 top-down]
-  struct FlowList { int off = 0, n = 0, need_all = 0, need_ph1 = 0; } flow[2][2];
+  struct FlowList { int off = 0, n = 0, uoff = 0, nu = 0, need_all = 0, need_ph1 = 0; } flow[2][2];
   int flow_vmax = 0;               // shared-memory vector entries of the flow kernel
   int* d_flow_ctr = nullptr;       // queue head and per-front counters
   int* d_flow_err = nullptr;       // set by a wait that gave up
   int* h_flow_err = nullptr;       // pinned copy
   int flow_grid[2] = {0, 0};       // persistent CTAs [precision 0 = c64, 1 = c128]
-  bool use_flow = true;
 
   // coefficients and permittivity
   double2 *d_cxm = nullptr, *d_cxp = nullptr, *d_cym = nullptr, *d_cyp = nullptr;
@@ -332,7 +329,8 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   // task lists (front, first row/column): [0] row tasks, [1] column tasks.
   // A small front is one whole-front task (front | bit 31); a large front is
   // split into row or column tasks in both launches.
-  auto small = [](const FrontDesc& d) { return d.n <= kSolveWholeFront; };
+  const int whole_n = flow_whole_max_n();   // fronts swept whole by one warp
+  auto small = [whole_n](const FrontDesc& d) { return d.n <= whole_n; };
   auto add_tasks = [&](TaskList& tl, int l, bool rect, bool over_m, int step) {
     if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
     tl.off = (int)lists.size();
@@ -366,37 +364,65 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
     ctx->flow_vmax = std::max({ctx->flow_vmax, sl.kmax, sl.kbig, sl.mbig});
   }
   // Dataflow queues: the same tasks as the level lists, in dependency order,
-  // off-diagonal tasks tagged with bit 30; per-front task counts beside them.
+  // off-diagonal tasks tagged with bit 30; per level the whole small fronts
+  // first, in units of up to 8 (one warp each), then the large fronts' tasks
+  // (one unit each) in phase order; per-front task counts beside them.
   const int nf = (int)p.fronts.size();
   for (int t = 0; t < 2; ++t) {
     for (int dir = 0; dir < 2; ++dir) {
       auto& fl = ctx->flow[t][dir];
       fl = fdfd_ctx::FlowList{};                 // the plan may be uploaded again (plain mode)
       std::vector<int> all(nf, 0), ph1(nf, 0);
-      if (lists.size() % 2) lists.push_back(0);
-      fl.off = (int)lists.size();
+      std::vector<int> tasks, units;
+      auto put_unit = [&](int first, int y) { units.push_back(first); units.push_back(y); };
+      auto put_whole = [&](const SolveList& sl) {
+        int first = -1, cnt = 0;
+        for (int i = 0; i < sl.tri[t].n; ++i) {
+          const int code = lists[sl.tri[t].off + 2 * i];
+          if (code >= 0) continue;                           // large-front task
+          const int f = code & 0x7fffffff;
+          if (cnt == 0) first = (int)tasks.size() / 2;
+          tasks.push_back(code); tasks.push_back(0);
+          all[f]++;
+          if (++cnt == 8) { put_unit(first, (int)(0x80000000u | 8u)); cnt = 0; }
+        }
+        if (cnt) put_unit(first, (int)(0x80000000u | (unsigned)cnt));
+      };
       auto put_tri = [&](const SolveList& sl) {
         for (int i = 0; i < sl.tri[t].n; ++i) {
           const int code = lists[sl.tri[t].off + 2 * i], s0 = lists[sl.tri[t].off + 2 * i + 1];
-          const int f = code & 0x7fffffff;
-          lists.push_back(code); lists.push_back(s0); fl.n++;
-          all[f]++;
-          if (code >= 0 && dir == 0) ph1[f]++;
+          if (code < 0) continue;                            // whole small front
+          put_unit((int)tasks.size() / 2, 1);
+          tasks.push_back(code); tasks.push_back(s0);
+          all[code]++;
+          if (dir == 0) ph1[code]++;
         }
       };
       auto put_rect = [&](const TaskList& tl) {
         for (int i = 0; i < tl.n; ++i) {
           const int f = lists[tl.off + 2 * i], s0 = lists[tl.off + 2 * i + 1];
-          lists.push_back((int)(0x40000000u | (unsigned)f)); lists.push_back(s0); fl.n++;
+          put_unit((int)tasks.size() / 2, 1);
+          tasks.push_back((int)(0x40000000u | (unsigned)f)); tasks.push_back(s0);
           all[f]++;
           if (dir == 1) ph1[f]++;
         }
       };
       if (dir == 0) {
-        for (int l = 0; l < L; ++l) { put_tri(ctx->lv_solve[l]); put_rect(ctx->lv_solve[l].rect_m[t]); }
+        for (int l = 0; l < L; ++l) {
+          put_whole(ctx->lv_solve[l]); put_tri(ctx->lv_solve[l]); put_rect(ctx->lv_solve[l].rect_m[t]);
+        }
       } else {
-        for (int l = L - 1; l >= 0; --l) { put_rect(ctx->lv_solve[l].rect_k[t]); put_tri(ctx->lv_solve[l]); }
+        for (int l = L - 1; l >= 0; --l) {
+          put_rect(ctx->lv_solve[l].rect_k[t]); put_whole(ctx->lv_solve[l]); put_tri(ctx->lv_solve[l]);
+        }
       }
+      if (lists.size() % 2) lists.push_back(0);
+      fl.off = (int)lists.size();
+      fl.n = (int)tasks.size() / 2;
+      lists.insert(lists.end(), tasks.begin(), tasks.end());
+      fl.uoff = (int)lists.size();
+      fl.nu = (int)units.size() / 2;
+      lists.insert(lists.end(), units.begin(), units.end());
       fl.need_all = (int)lists.size();
       lists.insert(lists.end(), all.begin(), all.end());
       fl.need_ph1 = (int)lists.size();
@@ -621,10 +647,9 @@ fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
   return FDFD_OK;
 }
 
-// Triangular sweeps on factor precision T: out = A^-1 in (or A^-T in).
+// Launch description of the sweeps over the cached factors of precision T.
 template <typename T>
-fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out, int w0 = 0,
-                   int nw = -1, int r0 = 0, int nr = -1) {
+SolveLaunch solve_launch(const fdfd_ctx* ctx, void* vb, int nrhs, int w0, int nw, int r0, int nr) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const Plan& p = ctx->plan;
   SolveLaunch sa;
@@ -635,7 +660,7 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   sa.perm_stride = std::max(1, p.perm_total);
   sa.istore = prec == 0 ? (const void*)ctx->d_inv32 : (const void*)ctx->d_inv64;
   sa.istore_stride = p.inv_total;
-  sa.vb = ctx->d_vb;
+  sa.vb = vb;
   sa.vec_stride = p.vec_total;
   sa.n_omega = nw < 0 ? ctx->n_omega : nw;
   sa.nrhs = nrhs;
@@ -643,6 +668,25 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
   sa.r0 = r0;
   sa.nr = nr < 0 ? nrhs : nr;
   sa.n = n_cells(ctx);
+  return sa;
+}
+
+// Persistent CTAs of the dataflow sweep for precision prec (host queries only).
+int flow_grid(fdfd_ctx* ctx, int prec) {
+  if (ctx->flow_grid[prec] > 0) return ctx->flow_grid[prec];
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm <= 0) nsm = 1;
+  ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax));
+  return ctx->flow_grid[prec];
+}
+
+// Sweep pair on factor precision T: out = A^-1 in (or A^-T in), one persistent
+// dataflow launch per direction.  ctr: counter buffer of at least
+// 1 + 2 * n_omega * n_fronts ints (cleared here before each launch).
+template <typename T>
+fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, const void* in, void* out, int* ctr) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const Plan& p = ctx->plan;
   cudaStream_t s = ctx->stream;
   const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
   const double es = sizeof(T), nsys = (double)sa.n_omega * sa.nr;
@@ -679,68 +723,43 @@ fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void*
     }
   };
   const int* dl = ctx->d_lists;
-  if (ctx->use_flow && ctx->d_flow_ctr) {
-    // one persistent launch per direction; counters cleared before each
-    const size_t ctr_bytes = sizeof(int) * (1 + 2 * (size_t)sa.n_omega * p.fronts.size());
-    for (int dir = 0; dir < 2; ++dir) {
-      const auto& fq = ctx->flow[tt][dir];
-      double fl = 0, by = 0;
-      for (int l = 0; l < p.n_levels; ++l) {
-        const SolveList& sl = ctx->lv_solve[l];
-        double f1, b1;
-        tri_work(sl.tri[tt], dir == 0 ? !transpose : transpose, &f1, &b1);
-        fl += f1; by += b1;
-        rect_work(dir == 0 ? sl.rect_m[tt] : sl.rect_k[tt], dir == 0, &f1, &b1);
-        fl += f1; by += b1;
-      }
-      CK(cudaMemsetAsync(ctx->d_flow_ctr, 0, ctr_bytes, s));
-      FlowQueue q;
-      q.tasks = reinterpret_cast<const int2*>(dl + fq.off);
-      q.ntasks = fq.n;
-      q.ctr = ctx->d_flow_ctr;
-      q.need_all = dl + fq.need_all;
-      q.need_ph1 = dl + fq.need_ph1;
-      q.err = ctx->d_flow_err;
-      q.n_fronts = (int)p.fronts.size();
-      const int grid = std::max(1, std::min(ctx->flow_grid[prec], fq.n * sa.n_omega));
-      Prof pr(ctx, dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U), fl, by);
-      launch_sweep_flow<T>(sa, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s);
+  const size_t ctr_bytes = sizeof(int) * (1 + 2 * (size_t)sa.n_omega * p.fronts.size());
+  const int grid_max = flow_grid(ctx, prec);
+  for (int dir = 0; dir < 2; ++dir) {
+    const auto& fq = ctx->flow[tt][dir];
+    double fl = 0, by = 0;
+    for (int l = 0; l < p.n_levels; ++l) {
+      const SolveList& sl = ctx->lv_solve[l];
+      double f1, b1;
+      tri_work(sl.tri[tt], dir == 0 ? !transpose : transpose, &f1, &b1);
+      fl += f1; by += b1;
+      rect_work(dir == 0 ? sl.rect_m[tt] : sl.rect_k[tt], dir == 0, &f1, &b1);
+      fl += f1; by += b1;
     }
-    CK(cudaGetLastError());
-    return FDFD_OK;
-  }
-  for (int l = 0; l < p.n_levels; ++l) {
-    const SolveList& sl = ctx->lv_solve[l];
-    double fl, by;
-    tri_work(sl.tri[tt], !transpose, &fl, &by);
-    {
-      Prof pr(ctx, transpose ? PK_SWEEP_UT : PK_SWEEP_L, fl, by);
-      launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in,
-                          out, s);
-    }
-    if (sl.rect_m[tt].n > 0) {
-      rect_work(sl.rect_m[tt], true, &fl, &by);
-      Prof pr(ctx, PK_SWEEP_RECT, fl, by);
-      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.rect_m[tt].off), sl.rect_m[tt].n,
-                           sl.kbig, out, s);
-    }
-  }
-  for (int l = p.n_levels - 1; l >= 0; --l) {
-    const SolveList& sl = ctx->lv_solve[l];
-    double fl, by;
-    if (sl.rect_k[tt].n > 0) {
-      rect_work(sl.rect_k[tt], false, &fl, &by);
-      Prof pr(ctx, PK_SWEEP_RECT, fl, by);
-      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.rect_k[tt].off), sl.rect_k[tt].n,
-                           sl.mbig, out, s);
-    }
-    tri_work(sl.tri[tt], transpose, &fl, &by);
-    Prof pr(ctx, transpose ? PK_SWEEP_LT : PK_SWEEP_U, fl, by);
-    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in,
-                        out, s);
+    CK(cudaMemsetAsync(ctr, 0, ctr_bytes, s));
+    FlowQueue q;
+    q.tasks = reinterpret_cast<const int2*>(dl + fq.off);
+    q.units = reinterpret_cast<const int2*>(dl + fq.uoff);
+    q.nunits = fq.nu;
+    q.ctr = ctr;
+    q.need_all = dl + fq.need_all;
+    q.need_ph1 = dl + fq.need_ph1;
+    q.err = ctx->d_flow_err;
+    q.n_fronts = (int)p.fronts.size();
+    const int grid = std::max(1, std::min(grid_max, fq.nu * sa.n_omega));
+    Prof pr(ctx, dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U), fl, by);
+    launch_sweep_flow<T>(sa, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s);
   }
   CK(cudaGetLastError());
   return FDFD_OK;
+}
+
+// Triangular sweeps on factor precision T with the context's buffers.
+template <typename T>
+fdfd_status sweeps(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out, int w0 = 0,
+                   int nw = -1, int r0 = 0, int nr = -1) {
+  return sweep_pair<T>(ctx, solve_launch<T>(ctx, ctx->d_vb, nrhs, w0, nw, r0, nr), transpose, in, out,
+                       ctx->d_flow_ctr);
 }
 
 // Runs `body`, which issues its work on ctx->stream, as a CUDA graph keyed by
@@ -1414,44 +1433,8 @@ void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
 template <typename T>
-void sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out, void* vb) {
-  const int prec = sizeof(T) == 8 ? 0 : 1;
-  const Plan& p = ctx->plan;
-  SolveLaunch sa;
-  sa.P = dev_plan(ctx);
-  sa.store = prec == 0 ? (const void*)ctx->d_store32 : (const void*)ctx->d_store64;
-  sa.store_stride = p.store_total;
-  sa.perm = prec == 0 ? ctx->d_perm32 : ctx->d_perm64;
-  sa.perm_stride = std::max(1, p.perm_total);
-  sa.istore = prec == 0 ? (const void*)ctx->d_inv32 : (const void*)ctx->d_inv64;
-  sa.istore_stride = p.inv_total;
-  sa.vb = vb;
-  sa.vec_stride = p.vec_total;
-  sa.n_omega = ctx->n_omega;
-  sa.nrhs = nrhs;
-  sa.w0 = 0;
-  sa.r0 = 0;
-  sa.nr = nrhs;
-  sa.n = n_cells(ctx);
-  const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
-  const int tt = transpose ? 1 : 0;
-  const int* dl = ctx->d_lists;
-  for (int l = 0; l < p.n_levels; ++l) {
-    const SolveList& sl = ctx->lv_solve[l];
-    launch_sweep_tri<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in, out,
-                        ctx->stream);
-    if (sl.rect_m[tt].n > 0)
-      launch_sweep_rect<T>(sa, fwd, reinterpret_cast<const int2*>(dl + sl.rect_m[tt].off), sl.rect_m[tt].n, sl.kbig,
-                           out, ctx->stream);
-  }
-  for (int l = p.n_levels - 1; l >= 0; --l) {
-    const SolveList& sl = ctx->lv_solve[l];
-    if (sl.rect_k[tt].n > 0)
-      launch_sweep_rect<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.rect_k[tt].off), sl.rect_k[tt].n, sl.mbig,
-                           out, ctx->stream);
-    launch_sweep_tri<T>(sa, bwd, reinterpret_cast<const int2*>(dl + sl.tri[tt].off), sl.tri[tt].n, sl.kmax, in, out,
-                        ctx->stream);
-  }
+fdfd_status sweeps_in(fdfd_ctx* ctx, int nrhs, int transpose, const void* in, void* out, void* vb, int* ctr) {
+  return sweep_pair<T>(ctx, solve_launch<T>(ctx, vb, nrhs, 0, -1, 0, -1), transpose, in, out, ctr);
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -1461,6 +1444,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 extern "C" {
 
 size_t fdfd_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
 
 fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose) {
   if (!ctx || !b_dev || !x_dev || nrhs <= 0 || b_dev == x_dev) return FDFD_ERR_ARG;
@@ -1473,9 +1457,10 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
   const size_t es = use64 ? sizeof(double2) : sizeof(float2);
   const size_t vb_bytes = align256(S * (size_t)ctx->plan.vec_total * es);
   const size_t cvt_bytes = use64 ? 0 : 2 * align256(S * N * sizeof(float2));
-  if (vb_bytes + cvt_bytes > kNoAllocScratchBytes)
+  const size_t ctr_bytes = align256(sizeof(int) * (1 + 2 * (size_t)ctx->n_omega * ctx->plan.fronts.size()));
+  if (vb_bytes + cvt_bytes + ctr_bytes > kNoAllocScratchBytes)
     return fail(ctx, FDFD_ERR_ARG,
-                "fdfd_solve_raw_noalloc: this solve needs " + std::to_string(vb_bytes + cvt_bytes) +
+                "fdfd_solve_raw_noalloc: this solve needs " + std::to_string(vb_bytes + cvt_bytes + ctr_bytes) +
                     " bytes of scratch; the fixed device array holds " + std::to_string(kNoAllocScratchBytes));
   int dev = -1;
   CK(cudaGetDevice(&dev));
@@ -1501,15 +1486,18 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
       return fail(ctx, FDFD_ERR_PIVOT,
                   "fdfd_solve_raw_noalloc: FP32 factors exceed the growth bound; call fdfd_solve once first");
   }
+  int* ctr = reinterpret_cast<int*>(scratch + vb_bytes + cvt_bytes);
   if (use64) {
-    sweeps_in<double2>(ctx, nrhs, transpose, b_dev, x_dev, scratch);
+    CKS(sweeps_in<double2>(ctx, nrhs, transpose, b_dev, x_dev, scratch, ctr));
   } else {
     float2* bT = reinterpret_cast<float2*>(scratch + vb_bytes);
     float2* xT = reinterpret_cast<float2*>(scratch + vb_bytes + cvt_bytes / 2);
     launch_cvt_from64<float2>(bT, reinterpret_cast<const double2*>(b_dev), nullptr, (long long)N, (int)S, ctx->stream);
-    sweeps_in<float2>(ctx, nrhs, transpose, bT, xT, scratch);
+    CKS(sweeps_in<float2>(ctx, nrhs, transpose, bT, xT, scratch, ctr));
     launch_cvt_to64<float2>(reinterpret_cast<double2*>(x_dev), xT, nullptr, (long long)N, (int)S, ctx->stream);
   }
+  if (ctx->h_flow_err) CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
   CK(cudaGetLastError());
   return FDFD_OK;
 }

@@ -91,27 +91,21 @@ struct SolveLaunch {
 };
 // sweep: 0 = L (forward, non-transposed), 1 = U (backward, non-transposed),
 //        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
-// in: right-hand side (sweeps 0, 2) [n_sys][n]; out: solution (sweeps 1, 3) [n_sys][n].
-// Products with the stored triangular inverses, tasks = (front, first row or
-// column of the k range); sweeps 0 and 1 take row tasks of sweep_row_block() rows,
-// sweeps 2 and 3 column tasks of sweep_col_block() columns; kmax: largest k listed.
-template <typename T> void launch_sweep_tri(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,
-                                            int kmax, const void* in, void* out, cudaStream_t s);
-// Off-diagonal block of large fronts, tasks = (front, first row/column), blocks
-// (row tasks for sweeps 0 and 1, column tasks for 2 and 3); vmax: largest vector
-// the tasks multiply (k or m).
-template <typename T> void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks,
-                                             int vmax, void* out, cudaStream_t s);
+// Large fronts are cut into row tasks of sweep_row_block() rows (sweeps 0, 1)
+// or column tasks of sweep_col_block() columns (sweeps 2, 3).
 int sweep_row_block();
 int sweep_col_block();
 
 // One direction of a sweep pair as a single persistent launch (dataflow over
 // the elimination tree).  tasks: the direction's inverse-block, off-diagonal
-// and whole-front tasks in dependency order, x = front | 1<<31 (whole front) |
-// 1<<30 (off-diagonal task), y = first row / column.
+// and whole-front tasks in dependency order (per level: whole small fronts,
+// then the large fronts' phase-1 and phase-2 tasks), x = front | 1<<31 (whole
+// front) | 1<<30 (off-diagonal task), y = first row / column.
 struct FlowQueue {
   const int2* tasks;
-  int ntasks;              // queue entries; each runs for every launched wavelength
+  const int2* units;       // what one CTA takes at a time: (first task, 1) for a large-front task, or
+                           // (first task, 0x80000000 | count) for up to 8 whole small fronts of one level
+  int nunits;              // units; each runs for every launched wavelength
   int* ctr;                // [1 + 2 * n_omega * n_fronts] ints, zero before the launch
   const int* need_all;     // [n_fronts] tasks of each front in this queue
   const int* need_ph1;     // [n_fronts] its phase-1 tasks (inverse-block bottom-up, off-diagonal top-down)
@@ -121,6 +115,7 @@ struct FlowQueue {
 template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax,
                                              int grid, const void* in, void* out, cudaStream_t s);
 int flow_blocks_per_sm(int elem_bytes, int vmax);
+int flow_whole_max_n();   // largest front the flow kernel runs as a one-warp whole-front task
 // one bounded wait on a zero flag (gives up, sets *err); for the self-test entry point
 cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s);
 

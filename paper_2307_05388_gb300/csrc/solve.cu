@@ -15,13 +15,16 @@
 // factorisation) and x_m are the already final values of the boundary
 // variables.  Levels run bottom-up for L / U^T and top-down for U / L^T.
 //
-// With the inverses every step is a matrix-vector product, so each front is
-// cut into tasks of 8 rows (one per warp) or 32 columns (one per lane) of its
-// k x k inverse block ("tri" launch) and of its off-diagonal block ("rect"
-// launch), and the whole
-// GPU streams the factor with no sequential substitution chain.  Every factor
-// read is coalesced along a row, each factor entry is read once per
-// right-hand side, and reductions run in a fixed order (deterministic).
+// With the inverses every step is a matrix-vector product.  A small front
+// (n <= 64) is one task done by one warp; a large front is cut into tasks of
+// 8 rows (one per warp) or 32 columns (one per lane) of its k x k inverse block
+// (phase 1 bottom-up) and of its off-diagonal block (the other phase).  One
+// persistent launch per direction runs every task in elimination-tree order
+// (the dataflow sweep below), so the whole GPU streams the factor with no
+// sequential substitution chain and no launch per level.  Every factor read
+// is coalesced along a row or served from L1 by a lane's own row, each factor
+// entry is read once per right-hand side, and reductions run in a fixed order
+// (deterministic).
 #include "kernels.h"
 
 namespace fdfd {
@@ -121,18 +124,49 @@ __device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& 
 //   SWEEP 2: cols a:    w[a]  = sum_{b<=a} X_U[b][a] v_b
 //   SWEEP 3: cols a:    q[a]  = t[a] + sum_{b>a} X_L[b][a] t[b]    (t = vf[0..k)), x[P a] = q[a]
 // ---------------------------------------------------------------------------
-// A task whose front index has bit 31 set covers a whole small front: one CTA
-// does the inverse-block and the off-diagonal products (no rectangular tasks).
+// A whole small front done by one warp (the dataflow sweep runs up to eight of
+// them per CTA): lane = row (L, U) or column (U^T, L^T) of each product, each
+// lane's dot product with eight loads in flight; vs is the warp's own slice
+// of n + k entries.
+template <typename T>
+__device__ __forceinline__ T lane_dot(const T* __restrict__ row, const T* vec, int c0, int c1) {
+  T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+  int c = c0;
+  for (; c + 7 < c1; c += 8) {
+    T f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) f[u] = row[c + u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u & 3] = cfma(f[u], vec[c + u], acc[u & 3]);
+  }
+  for (; c < c1; ++c) acc[0] = cfma(row[c], vec[c], acc[0]);
+  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+}
+template <typename T>
+__device__ __forceinline__ T lane_col_dot(const T* __restrict__ col, int ld, const T* vec, int r0, int r1) {
+  T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
+  int r = r0;
+  for (; r + 7 < r1; r += 8) {
+    T f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) f[u] = col[(size_t)(r + u) * ld];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u & 3] = cfma(f[u], vec[r + u], acc[u & 3]);
+  }
+  for (; r < r1; ++r) acc[0] = cfma(col[(size_t)r * ld], vec[r], acc[0]);
+  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+}
+
 template <typename T, int SWEEP>
-__device__ __forceinline__ void whole_front(const SolveLaunch& a, const FrontDesc& d, int w, const T* __restrict__ in,
-                                            T* __restrict__ out, T* vs, T (*red)[32]) {
+__device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const FrontDesc& d, int w,
+                                                 const T* __restrict__ in, T* __restrict__ out, T* vs) {
   const int k = d.k, m = d.m, n = d.n, ldk = d.ldk, ld = d.ld;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31;
   const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   const int* idx = a.P.idx + d.idx_off;
-  T* ws = vs + n;                                  // second vector: k entries
+  T* ws = vs + n;
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
@@ -140,63 +174,35 @@ __device__ __forceinline__ void whole_front(const SolveLaunch& a, const FrontDes
     T* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
       const T* rhs = in + sys * a.n;
-      for (int s = tid; s < n; s += kThreads)
-        vs[s] = gather_slot(a, d, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
+      for (int s = lane; s < n; s += 32) vs[s] = gather_slot(a, d, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
     } else {
-      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
-      for (int t = tid; t < m; t += kThreads) vs[k + t] = ldv(xo + idx[k + t]);
+      for (int s = lane; s < k; s += 32) vs[s] = ldv(vf + s);
+      for (int t = lane; t < m; t += 32) {
+        const T x = ldv(xo + idx[k + t]);
+        vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
+      }
     }
-    __syncthreads();
+    __syncwarp();
     if (SWEEP == 0) {                              // y = X_L (P v)_k;  u = v_m - L21 y
-      for (int row = warp; row < k; row += kWarps) {
-        const T acc = warp_dot(X + (size_t)row * ldk, vs, 0, row, lane);
-        if (lane == 0) ws[row] = cadd(vs[row], acc);
-      }
-      __syncthreads();
-      for (int t = warp; t < m; t += kWarps) {
-        const T acc = warp_dot(F + (size_t)(k + t) * ld, ws, 0, k, lane);
-        if (lane == 0) vf[k + t] = csub(vs[k + t], acc);
-      }
-      for (int s = tid; s < k; s += kThreads) vf[s] = ws[s];
+      for (int row = lane; row < k; row += 32) ws[row] = cadd(vs[row], lane_dot(X + (size_t)row * ldk, vs, 0, row));
+      __syncwarp();
+      for (int t = lane; t < m; t += 32) vf[k + t] = csub(vs[k + t], lane_dot(F + (size_t)(k + t) * ld, ws, 0, k));
+      for (int s = lane; s < k; s += 32) vf[s] = ws[s];
     } else if (SWEEP == 1) {                       // z = y - U12 x_m;  x_k = X_U z
-      for (int row = warp; row < k; row += kWarps) {
-        const T acc = warp_dot(F + (size_t)row * ld + k, vs + k, 0, m, lane);
-        if (lane == 0) ws[row] = csub(vs[row], acc);
-      }
-      __syncthreads();
-      for (int row = warp; row < k; row += kWarps) {
-        const T acc = warp_dot(X + (size_t)row * ldk, ws, row, k, lane);
-        if (lane == 0) xo[idx[row]] = acc;
-      }
+      for (int row = lane; row < k; row += 32) ws[row] = csub(vs[row], lane_dot(F + (size_t)row * ld + k, vs + k, 0, m));
+      __syncwarp();
+      for (int row = lane; row < k; row += 32) xo[idx[row]] = lane_dot(X + (size_t)row * ldk, ws, row, k);
     } else if (SWEEP == 2) {                       // w = X_U^T v_k;  u = v_m - U12^T w
-      for (int c0 = 0; c0 < k; c0 += 32) {
-        const int c = c0 + lane;
-        const T s = col_dot(X + c, ldk, vs, 0, min(c0 + 32, k), c < k, [&](int b) { return b <= c; }, red);
-        if (warp == 0 && c < k) ws[c] = s;
-        __syncthreads();
-      }
-      for (int c0 = 0; c0 < m; c0 += 32) {
-        const int c = c0 + lane;
-        const T s = col_dot(F + k + c, ld, ws, 0, k, c < m, [](int) { return true; }, red);
-        if (warp == 0 && c < m) vf[k + c] = csub(vs[k + c], s);
-        __syncthreads();
-      }
-      for (int s = tid; s < k; s += kThreads) vf[s] = ws[s];
-    } else {                                       // t = w - L21^T x_m;  x_k = P^T X_L^T t
-      for (int c0 = 0; c0 < k; c0 += 32) {
-        const int c = c0 + lane;
-        const T s = col_dot(F + (size_t)k * ld + c, ld, vs + k, 0, m, c < k, [](int) { return true; }, red);
-        if (warp == 0 && c < k) ws[c] = csub(vs[c], s);
-        __syncthreads();
-      }
-      for (int c0 = 0; c0 < k; c0 += 32) {
-        const int c = c0 + lane;
-        const T s = col_dot(X + c, ldk, ws, c0 + 1, k, c < k, [&](int b) { return b > c; }, red);
-        if (warp == 0 && c < k) xo[idx[Pm[c]]] = cadd(ws[c], s);
-        __syncthreads();
-      }
+      for (int c = lane; c < k; c += 32) ws[c] = lane_col_dot(X + c, ldk, vs, 0, c + 1);
+      __syncwarp();
+      for (int t = lane; t < m; t += 32) vf[k + t] = csub(vs[k + t], lane_col_dot(F + k + t, ld, ws, 0, k));
+      for (int s = lane; s < k; s += 32) vf[s] = ws[s];
+    } else {                                       // t = w - L21^T x_m;  x_k = P^T X_L^T t   (vs[k..n) = -x_m)
+      for (int c = lane; c < k; c += 32) ws[c] = cadd(vs[c], lane_col_dot(F + (size_t)k * ld + c, ld, vs + k, 0, m));
+      __syncwarp();
+      for (int c = lane; c < k; c += 32) xo[idx[Pm[c]]] = cadd(ws[c], lane_col_dot(X + c, ldk, ws, c + 1, k));
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -247,18 +253,6 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
     }
     __syncthreads();
   }
-}
-
-template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads)
-tri_kernel(SolveLaunch a, const int2* __restrict__ tasks, const T* __restrict__ in, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[kWarps][32];
-  T* vs = reinterpret_cast<T*>(smem_raw);
-  const int w = blockIdx.y + a.w0;
-  const int2 task = tasks[blockIdx.x];
-  if (task.x < 0) whole_front<T, SWEEP>(a, a.P.fronts[task.x & 0x7fffffff], w, in, out, vs, red);
-  else tri_task<T, SWEEP>(a, a.P.fronts[task.x], task.y, w, in, out, vs, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -313,16 +307,6 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
   }
 }
 
-template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads)
-rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[kWarps][32];
-  T* vs = reinterpret_cast<T*>(smem_raw);
-  const int2 task = tasks[blockIdx.x];
-  rect_task<T, SWEEP>(a, a.P.fronts[task.x], task.y, blockIdx.y + a.w0, out, vs, red);
-}
-
 // ---------------------------------------------------------------------------
 // Dataflow sweep: one persistent launch runs every task of one direction.
 // CTAs take tasks from a queue in dependency order (bottom-up levels for
@@ -340,6 +324,7 @@ rect_kernel(SolveLaunch a, const int2* __restrict__ tasks, T* __restrict__ out) 
 // ---------------------------------------------------------------------------
 constexpr int kSpinLimit = 1 << 21;
 
+
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -356,33 +341,72 @@ __device__ __forceinline__ bool wait_ge(const int* p, int need, int* err) {
   return false;
 }
 
+constexpr int kWarpSlice = 128;   // vector entries per warp for a whole small front (n + k, n <= 64)
+
 template <typename T, int SWEEP>
 __global__ void __launch_bounds__(kThreads)
 flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[kWarps][32];
-  __shared__ int s_task, s_ok;
+  __shared__ int s_unit, s_ok, s_fail;
   T* vs = reinterpret_cast<T*>(smem_raw);
   constexpr bool kUp = SWEEP == 0 || SWEEP == 2;
   const int nf = q.n_fronts;
   int* head = q.ctr;
   int* done = q.ctr + 1;                       // [n_omega launched][nf]
   int* ph1 = done + (size_t)a.n_omega * nf;    // [n_omega launched][nf]
-  const int total = q.ntasks * a.n_omega;
-  const int tid = threadIdx.x;
+  const int total = q.nunits * a.n_omega;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_fail = 0;
   for (;;) {
-    if (tid == 0) s_task = atomicAdd(head, 1);
+    if (tid == 0) s_unit = atomicAdd(head, 1);
     __syncthreads();
-    const int t = s_task;
-    if (t >= total) break;
-    const int ti = t / a.n_omega, wl = t - ti * a.n_omega;
-    const int2 task = q.tasks[ti];
+    const int u = s_unit;
+    if (u >= total) break;
+    const int ui = u / a.n_omega, wl = u - ui * a.n_omega;
+    const int w = wl + a.w0;
+    const int2 unit = q.units[ui];
+    const int* dn = done + (size_t)wl * nf;
+    if ((unsigned)unit.y & 0x80000000u) {
+      // a batch of whole small fronts of one level: one per warp, each waits for its own dependencies
+      const int cnt = unit.y & 0xff;
+      if (warp < cnt) {
+        const int2 task = q.tasks[unit.x + warp];
+        const int f = (int)((unsigned)task.x & 0x3fffffffu);
+        const FrontDesc d = a.P.fronts[f];
+        bool ok = true;
+        if (lane == 0) {
+          if (kUp) {
+            for (int ci = 0; ci < d.nchild && ok; ++ci) {
+              const int c = a.P.children[d.child0 + ci];
+              ok = wait_ge(dn + c, q.need_all[c], q.err);
+            }
+          } else if (d.parent >= 0) {
+            ok = wait_ge(dn + d.parent, q.need_all[d.parent], q.err);
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+          whole_front_warp<T, SWEEP>(a, d, w, in, out, vs + warp * kWarpSlice);
+          if (lane == 0) {
+            __threadfence();
+            atomicAdd(done + (size_t)wl * nf + f, 1);
+          }
+        } else if (lane == 0) {
+          s_fail = 1;
+        }
+      }
+      __syncthreads();
+      if (s_fail) break;
+      continue;
+    }
+    // one task of a large front for the whole CTA
+    const int2 task = q.tasks[unit.x];
     const unsigned code = (unsigned)task.x;
-    const bool whole = (code >> 31) != 0, rect = ((code >> 30) & 1u) != 0;
+    const bool rect = ((code >> 30) & 1u) != 0;
     const int f = (int)(code & 0x3fffffffu);
     const FrontDesc d = a.P.fronts[f];
     if (tid == 0) {
-      const int* dn = done + (size_t)wl * nf;
       bool ok = true;
       if (kUp) {
         if (rect) {
@@ -395,58 +419,25 @@ flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict_
         }
       } else {
         if (d.parent >= 0) ok = wait_ge(dn + d.parent, q.need_all[d.parent], q.err);
-        if (ok && !whole && !rect) ok = wait_ge(ph1 + (size_t)wl * nf + f, q.need_ph1[f], q.err);
+        if (ok && !rect) ok = wait_ge(ph1 + (size_t)wl * nf + f, q.need_ph1[f], q.err);
       }
       s_ok = ok;
     }
     __syncthreads();
     if (!s_ok) break;
-    const int w = wl + a.w0;
-    if (whole) whole_front<T, SWEEP>(a, d, w, in, out, vs, red);
-    else if (rect) rect_task<T, SWEEP>(a, d, task.y, w, out, vs, red);
+    if (rect) rect_task<T, SWEEP>(a, d, task.y, w, out, vs, red);
     else tri_task<T, SWEEP>(a, d, task.y, w, in, out, vs, red);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
       // phase 1: inverse-block tasks bottom-up, off-diagonal tasks top-down
-      if (!whole && (kUp ? !rect : rect)) atomicAdd(ph1 + (size_t)wl * nf + f, 1);
+      if (kUp ? !rect : rect) atomicAdd(ph1 + (size_t)wl * nf + f, 1);
       atomicAdd(done + (size_t)wl * nf + f, 1);
     }
   }
 }
 
 }  // namespace
-
-template <typename T>
-void launch_sweep_tri(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks, int kmax, const void* in,
-                      void* out, cudaStream_t s) {
-  if (ntasks <= 0) return;
-  const size_t smem = (size_t)kmax * sizeof(T);
-  const T* i = reinterpret_cast<const T*>(in);
-  T* o = reinterpret_cast<T*>(out);
-  dim3 grid(ntasks, a.n_omega);
-  switch (sweep) {
-    case 0: tri_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
-    case 1: tri_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
-    case 2: tri_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
-    default: tri_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, tasks, i, o); break;
-  }
-}
-
-template <typename T>
-void launch_sweep_rect(const SolveLaunch& a, int sweep, const int2* tasks, int ntasks, int vmax, void* out,
-                       cudaStream_t s) {
-  if (ntasks <= 0) return;
-  const size_t smem = (size_t)vmax * sizeof(T);
-  T* o = reinterpret_cast<T*>(out);
-  dim3 grid(ntasks, a.n_omega);
-  switch (sweep) {
-    case 0: rect_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
-    case 1: rect_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
-    case 2: rect_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
-    default: rect_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, tasks, o); break;
-  }
-}
 
 // One wait on *flag >= 1 (nothing sets it) by one thread: exercises the
 // bounded wait of the dataflow sweep, which must give up, set *err and return.
@@ -459,11 +450,16 @@ cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t flow_smem(int vmax, size_t es) {
+  const int e = vmax > kWarps * kWarpSlice ? vmax : kWarps * kWarpSlice;
+  return (size_t)e * es;
+}
+
 template <typename T>
 void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax, int grid, const void* in,
                        void* out, cudaStream_t s) {
-  if (q.ntasks <= 0) return;
-  const size_t smem = (size_t)vmax * sizeof(T);
+  if (q.nunits <= 0) return;
+  const size_t smem = flow_smem(vmax, sizeof(T));
   const T* i = reinterpret_cast<const T*>(in);
   T* o = reinterpret_cast<T*>(out);
   switch (sweep) {
@@ -476,7 +472,7 @@ void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int 
 
 int flow_blocks_per_sm(int elem_bytes, int vmax) {
   int nb = 0;
-  const size_t smem = (size_t)vmax * elem_bytes;
+  const size_t smem = flow_smem(vmax, elem_bytes);
   const cudaError_t e = elem_bytes == 8
       ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1>, kThreads, smem)
       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1>, kThreads, smem);
@@ -484,6 +480,8 @@ int flow_blocks_per_sm(int elem_bytes, int vmax) {
 }
 
 int sweep_row_block() { return kRowBlk; }
+
+int flow_whole_max_n() { return kWarpSlice / 2; }
 int sweep_col_block() { return kColBlk; }
 
 cudaError_t solve_init_attributes() {
@@ -491,12 +489,6 @@ cudaError_t solve_init_attributes() {
   cudaError_t e = cudaSuccess;
 #define FDFD_ATTR(K, T, S)                                                                       \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  FDFD_ATTR(tri_kernel, float2, 0) FDFD_ATTR(tri_kernel, float2, 1) FDFD_ATTR(tri_kernel, float2, 2)
-  FDFD_ATTR(tri_kernel, float2, 3) FDFD_ATTR(tri_kernel, double2, 0) FDFD_ATTR(tri_kernel, double2, 1)
-  FDFD_ATTR(tri_kernel, double2, 2) FDFD_ATTR(tri_kernel, double2, 3)
-  FDFD_ATTR(rect_kernel, float2, 0) FDFD_ATTR(rect_kernel, float2, 1) FDFD_ATTR(rect_kernel, float2, 2)
-  FDFD_ATTR(rect_kernel, float2, 3) FDFD_ATTR(rect_kernel, double2, 0) FDFD_ATTR(rect_kernel, double2, 1)
-  FDFD_ATTR(rect_kernel, double2, 2) FDFD_ATTR(rect_kernel, double2, 3)
   FDFD_ATTR(flow_kernel, float2, 0) FDFD_ATTR(flow_kernel, float2, 1) FDFD_ATTR(flow_kernel, float2, 2)
   FDFD_ATTR(flow_kernel, float2, 3) FDFD_ATTR(flow_kernel, double2, 0) FDFD_ATTR(flow_kernel, double2, 1)
   FDFD_ATTR(flow_kernel, double2, 2) FDFD_ATTR(flow_kernel, double2, 3)
@@ -504,12 +496,6 @@ cudaError_t solve_init_attributes() {
   return e;
 }
 
-template void launch_sweep_tri<float2>(const SolveLaunch&, int, const int2*, int, int, const void*, void*,
-                                       cudaStream_t);
-template void launch_sweep_tri<double2>(const SolveLaunch&, int, const int2*, int, int, const void*, void*,
-                                        cudaStream_t);
-template void launch_sweep_rect<float2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
-template void launch_sweep_rect<double2>(const SolveLaunch&, int, const int2*, int, int, void*, cudaStream_t);
 template void launch_sweep_flow<float2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
                                         cudaStream_t);
 template void launch_sweep_flow<double2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
