@@ -103,17 +103,41 @@ __device__ __forceinline__ T col_dot(const T* __restrict__ base, int ld, const T
   return s;
 }
 
-// Right-hand side entries of the front's pivot rows plus the children's
-// update vectors, for local slots s (permuted through P when asked).
-template <typename T>
-__device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& d, const T* rhs, const T* vbs,
-                                         int src) {
-  T v = (rhs && src < d.k) ? rhs[a.P.idx[d.idx_off + src]] : czero<T>();
-  for (int ci = 0; ci < d.nchild; ++ci) {
-    const FrontDesc c = a.P.fronts[a.P.children[d.child0 + ci]];
-    const int t = a.P.inv[c.inv_off + src];
-    if (t >= 0) v = cadd(v, ldv(vbs + c.v_off + c.k + t));
+// The two (at most) children of a front as the gathers need them: where their
+// extend-add maps start and where their update vectors sit in a system's
+// front-vector buffer.  Loaded once per task instead of once per slot.
+struct Kids {
+  int n;
+  int inv_off[2];
+  long long ubase[2];     // child's v_off + k
+};
+
+__device__ __forceinline__ Kids load_kids(const SolveLaunch& a, const FrontDesc& d) {
+  Kids c;
+  c.n = d.nchild;
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci) {
+    c.inv_off[ci] = 0;
+    c.ubase[ci] = 0;
+    if (ci < d.nchild) {
+      const FrontDesc& cd = a.P.fronts[a.P.children[d.child0 + ci]];
+      c.inv_off[ci] = cd.inv_off;
+      c.ubase[ci] = cd.v_off + cd.k;
+    }
   }
+  return c;
+}
+
+// Right-hand side entry of local slot src (pivot slots only, when rhs is given)
+// plus the children's update vectors at that slot.
+template <typename T>
+__device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& d, const Kids& kids, const T* rhs,
+                                         const T* vbs, int src) {
+  const int t0 = kids.n > 0 ? a.P.inv[kids.inv_off[0] + src] : -1;
+  const int t1 = kids.n > 1 ? a.P.inv[kids.inv_off[1] + src] : -1;
+  T v = (rhs && src < d.k) ? rhs[a.P.idx[d.idx_off + src]] : czero<T>();
+  if (t0 >= 0) v = cadd(v, ldv(vbs + kids.ubase[0] + t0));
+  if (t1 >= 0) v = cadd(v, ldv(vbs + kids.ubase[1] + t1));
   return v;
 }
 
@@ -166,6 +190,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
   const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   const int* idx = a.P.idx + d.idx_off;
+  const Kids kids = load_kids(a, d);
   T* ws = vs + n;
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
@@ -174,7 +199,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
     T* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
       const T* rhs = in + sys * a.n;
-      for (int s = lane; s < n; s += 32) vs[s] = gather_slot(a, d, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
+      for (int s = lane; s < n; s += 32) vs[s] = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
     } else {
       for (int s = lane; s < k; s += 32) vs[s] = ldv(vf + s);
       for (int t = lane; t < m; t += 32) {
@@ -215,13 +240,20 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
   const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   const int* idx = a.P.idx + d.idx_off;
+  const Kids kids = load_kids(a, d);
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
     if (SWEEP == 0 || SWEEP == 2) {
       const T* rhs = in + sys * a.n;
-      for (int s = tid; s < k; s += kThreads) vs[s] = gather_slot(a, d, rhs, vbs, SWEEP == 0 ? Pm[s] : s);
+      for (int s = tid; s < k; s += 2 * kThreads) {
+        const int s2 = s + kThreads;
+        const T g1 = gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s] : s);
+        const T g2 = s2 < k ? gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s2] : s2) : czero<T>();
+        vs[s] = g1;
+        if (s2 < k) vs[s2] = g2;
+      }
     } else {
       for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
     }
@@ -270,6 +302,7 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int* idx = a.P.idx + d.idx_off;
+  const Kids kids = load_kids(a, d);
   for (int r = a.r0; r < a.r0 + a.nr; ++r) {
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
@@ -286,22 +319,21 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
         const int row = s0 + rr;
         if (row >= (SWEEP == 0 ? m : k)) break;
         const T* Frow = SWEEP == 0 ? F + (size_t)(k + row) * ld : F + (size_t)row * ld + k;
+        // the value the product is subtracted from, fetched before the product
+        const T g = SWEEP == 0 ? gather_slot(a, d, kids, (const T*)nullptr, vbs, k + row) : ldv(vf + row);
         const T acc = warp_dot(Frow, vs, 0, SWEEP == 0 ? k : m, lane);
-        if (lane == 0) {
-          if (SWEEP == 0) vf[k + row] = csub(gather_slot(a, d, (const T*)nullptr, vbs, k + row), acc);
-          else vf[row] = csub(ldv(vf + row), acc);
-        }
+        if (lane == 0) vf[SWEEP == 0 ? k + row : row] = csub(g, acc);
       }
     } else {
       const int cols = SWEEP == 2 ? m : k;
       const int rows = SWEEP == 2 ? k : m;
       const int c = s0 + lane;
       const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
+      // the value the product is subtracted from, fetched before the product
+      T g = czero<T>();
+      if (warp == 0 && c < cols) g = SWEEP == 2 ? gather_slot(a, d, kids, (const T*)nullptr, vbs, k + c) : ldv(vf + c);
       const T s = col_dot(base, ld, vs, 0, rows, c < cols, [](int) { return true; }, red);
-      if (warp == 0 && c < cols) {
-        if (SWEEP == 2) vf[k + c] = csub(gather_slot(a, d, (const T*)nullptr, vbs, k + c), s);
-        else vf[c] = csub(ldv(vf + c), s);
-      }
+      if (warp == 0 && c < cols) vf[SWEEP == 2 ? k + c : c] = csub(g, s);
     }
     __syncthreads();
   }
