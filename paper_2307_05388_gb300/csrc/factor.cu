@@ -164,25 +164,37 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
     }
     __syncthreads();
   }
-  // Triangular inverses, one row of each per step: row i of L11^-1 (strictly
-  // lower, unit diagonal implied) from rows < i, and row k-1-i of U11^-1 (upper
-  // with diagonal) from rows > k-1-i.  The two never touch each other's entries.
+  // Triangular inverses, right-looking, into X (k x k, row stride k): the
+  // strictly lower part holds L11^-1 (unit diagonal implied), the upper part
+  // U11^-1.  X_L[i][c] = -L[i][c] - sum_{l in (c, i)} L[i][l] X_L[l][c]: start
+  // from -L and, once row l is final (step l), subtract L[i][l] X_L[l][c] from
+  // every later row.  X_U from the bottom: row t = k-1-s is final once rows
+  // below it have been folded in, X_U[t][c] = (delta_tc - acc[t][c]) / U[t][t],
+  // and then acc[r][c] += U[r][t] X_U[t][c] for every earlier row r.  The two
+  // triangles never touch each other's entries.
   T* X = S + n * n;
-  for (int i = 0; i < k; ++i) {
-    for (int j = tid; j < i; j += blockDim.x) {
-      T acc = S[i * n + j];
-      for (int l = j + 1; l < i; ++l) acc = cfma(S[i * n + l], X[l * k + j], acc);
-      X[i * k + j] = csub(czero<T>(), acc);
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e / k, c = e - i * k;
+    X[e] = (i > c) ? csub(czero<T>(), S[i * n + c]) : czero<T>();
+  }
+  __syncthreads();
+  for (int st = 0; st < k; ++st) {
+    const int t = k - 1 - st;
+    {  // finalise row t of X_U
+      const T dinv = crcp(S[t * n + t]);
+      const T one = cmk(R(1), R(0));
+      for (int c = t + tid; c < k; c += blockDim.x) X[t * k + c] = cmul(csub(c == t ? one : czero<T>(), X[t * k + c]), dinv);
     }
-    const int ii = k - 1 - i;
-    const T dinv = crcp(S[ii * n + ii]);
-    for (int j = ii + tid; j < k; j += blockDim.x) {
-      if (j == ii) {
-        X[ii * k + ii] = dinv;
+    __syncthreads();
+    // L: rows i > st, columns c < st, with the final row st;  U: rows r < t, columns c >= t
+    const int nl = (k - st - 1) * st, nu = t * (k - t);
+    for (int e = tid; e < nl + nu; e += blockDim.x) {
+      if (e < nl) {
+        const int i = st + 1 + e / st, c = e - (e / st) * st;
+        X[i * k + c] = cfms(S[i * n + st], X[st * k + c], X[i * k + c]);
       } else {
-        T acc = czero<T>();
-        for (int l = ii + 1; l <= j; ++l) acc = cfma(S[ii * n + l], X[l * k + j], acc);
-        X[ii * k + j] = csub(czero<T>(), cmul(dinv, acc));
+        const int e2 = e - nl, r = e2 / (k - t), c = t + (e2 - r * (k - t));
+        X[r * k + c] = cfma(S[r * n + t], X[t * k + c], X[r * k + c]);
       }
     }
     __syncthreads();
