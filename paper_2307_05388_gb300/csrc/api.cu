@@ -65,6 +65,10 @@ struct fdfd_ctx {
   // internal buffers), captured on a private stream joined to `stream` by events
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  // side stream of a factorisation: the inverse folds of the large fronts run
+  // there, forked after each panel step and joined at the end
+  cudaStream_t istream = nullptr;
+  cudaEvent_t iev_fork = nullptr, iev_join = nullptr;
   struct GraphEntry { int key; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;
   std::string err;
@@ -529,6 +533,10 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   const std::vector<LevelList>& lv = design_only ? ctx->lv_design[prec] : ctx->lv_full[prec];
   const int nb = lu_panel_width(sizeof(T));
   cudaStream_t s = ctx->stream;
+  // inverse folds beside the panel steps (on the main stream while profiling,
+  // so that each launch is timed on its own)
+  cudaStream_t si = (ctx->prof_on || !ctx->istream) ? s : ctx->istream;
+  bool forked = false;
   const double es = sizeof(T), nwd = fa.n_omega;
   const int* hl = ctx->h_lists.data();
   for (int l = 0; l < p.n_levels; ++l) {
@@ -581,9 +589,31 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           gb += es * (2.0 * (rem * kr + kr * d.m) + 2.0 * rem * b);
         }
       if (local_piv) {
-        // block LU, L columns, U rows and the row permutation of the step in one launch
-        Prof pr(ctx, PK_LU_STEP, (pf + lf + tf) * nwd, (pb + lb + tb) * nwd);
-        launch_lu_step_local<T>(fa, fl, ll.nlarge, j0, ll.nmax_large, s);
+        {
+          // block LU and inverses, L columns, U rows and the row permutation of the step in one launch
+          Prof pr(ctx, PK_LU_STEP, (pf + lf + tf) * nwd, (pb + lb + tb) * nwd);
+          launch_lu_step_local<T>(fa, fl, ll.nlarge, j0, ll.nmax_large, 1, s);
+        }
+        // block row J of L11^-1 and block column J of U11^-1: products with the
+        // inverse so far, then with the block's own inverse
+        double vf = 0, vb = 0;
+        if (ctx->prof_on)
+          for (int t = 0; t < ll.nlarge; ++t) {
+            const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
+            if (j0 >= d.k) continue;
+            const double b = std::min(nb, d.k - j0);
+            vf += 8.0 * 2.0 * (0.5 * b * (double)j0 * j0 + b * b * j0);
+            vb += es * 2.0 * (0.5 * (double)j0 * j0 + 2.0 * b * j0);
+          }
+        if (si != s && j0 > 0) {
+          CK(cudaEventRecord(ctx->iev_fork, s));
+          CK(cudaStreamWaitEvent(si, ctx->iev_fork, 0));
+          forked = true;
+        }
+        if (j0 > 0) {
+          Prof pr(ctx, PK_LU_INV, vf * nwd, vb * nwd);
+          launch_lu_inv_fold<T>(fa, fl, ll.nlarge, j0, si);
+        }
       } else {
         { Prof pr(ctx, PK_LU_PANEL, pf * nwd, pb * nwd);
           launch_lu_panel<T>(fa, fl, ll.nlarge, j0, nb, ll.kmax_large, s); }
@@ -606,8 +636,9 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       Prof pr(ctx, PK_LU_SCHUR, sf * nwd, sb * nwd);
       launch_schur_simt<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.mmax_large, s);
     }
-    if (ll.nlarge > 0) {
-      // triangular inverses of the level's large fronts (2/3 k^3 complex multiply-adds each)
+    if (ll.nlarge > 0 && !local_piv) {
+      // triangular inverses of the level's large fronts (2/3 k^3 complex multiply-adds each);
+      // block-local pivoting forms them inside the panel steps instead
       double vf = 0, vb = 0;
       if (ctx->prof_on)
         for (int t = 0; t < ll.nlarge; ++t) {
@@ -616,13 +647,12 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           vb += es * 2.0 * (double)d.k * d.k;
         }
       Prof pr(ctx, PK_LU_INV, vf * nwd, vb * nwd);
-      if (ctx->opt.pivoting == 1) {   // diagonal blocks factored by the panel steps
-        launch_lu_diag_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
-        launch_lu_inv_blocked<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
-      }
-      else
-        launch_lu_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
+      launch_lu_inv<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.kmax_large, s);
     }
+  }
+  if (forked) {
+    CK(cudaEventRecord(ctx->iev_join, si));
+    CK(cudaStreamWaitEvent(s, ctx->iev_join, 0));
   }
   CK(cudaGetLastError());
   Prof pr_g(ctx, PK_OTHER, 0, 4.0 * p.fronts.size() * ctx->n_omega);
@@ -773,6 +803,9 @@ fdfd_status run_graph(fdfd_ctx* ctx, int key, Body&& body) {
     CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&ctx->gev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ctx->gev_out, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&ctx->istream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->iev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->iev_join, cudaEventDisableTiming));
   }
   cudaGraphExec_t exec = nullptr;
   for (const auto& g : ctx->graphs)
@@ -1395,6 +1428,12 @@ void fdfd_destroy(fdfd_ctx* ctx) {
     cudaStreamDestroy(ctx->gstream);
     cudaEventDestroy(ctx->gev_in);
     cudaEventDestroy(ctx->gev_out);
+  }
+  if (ctx->istream) {
+    cudaStreamSynchronize(ctx->istream);
+    cudaStreamDestroy(ctx->istream);
+    cudaEventDestroy(ctx->iev_fork);
+    cudaEventDestroy(ctx->iev_join);
   }
   if (ctx->h_growth_max) cudaFreeHost(ctx->h_growth_max);
   if (ctx->h_flow_err) cudaFreeHost(ctx->h_flow_err);

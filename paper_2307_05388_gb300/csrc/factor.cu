@@ -623,9 +623,9 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
 //   every CTA LU-factors B itself (warps 0-3, rows in registers, pivot rows
 //   chosen inside B; deterministic, so every CTA gets the same bits) while
 //   warps 4-7 stage the CTA's operand, then does one role:
-//     role D (block 0): the row permutation of J into perm, the packed L\U of B
-//                       into the diagonal block of the inverse store (inverted
-//                       there later by lu_diag_inv), growth of its multipliers;
+//     role D (block 0): the row permutation of J into perm, L_JJ^-1 and U_JJ^-1
+//                       into the diagonal block of the inverse store (or the
+//                       packed L\U of B, for lu_diag_inv), growth of its multipliers;
 //     role L: rows r >= j0 + nb, L[r, J] U_JJ = F[r, J]          (64 rows / CTA);
 //     role U: columns c >= j0 + nb, L_JJ U[J, c] = (P F)[J, c]   (64 columns / CTA);
 //     role P: columns c < j0, F[J, c] <- (P F)[J, c]             (64 columns / CTA);
@@ -755,7 +755,7 @@ __device__ __forceinline__ void tri_inverse_col(const T (*LU)[kMaxNb + 1], const
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu) {
+lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu, int inv) {
   using R = typename RealOf<T>::type;
   using Blk = T[kMaxNb + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -806,28 +806,26 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     }
   }
   __syncthreads();
-  if (role == 0) {
-    // rows of J move only at this step (earlier and later steps permute their own
-    // blocks); the packed L\U of the block goes to the inverse store, where
-    // lu_diag_inv later replaces it by its two triangular inverses
-    if (tid < nb) a.perm[(size_t)w * a.perm_stride + d.piv_off + j0 + tid] = j0 + src[tid];
-    T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
-    for (int e = tid; e < nb * nb; e += 256) {
-      const int i = e / nb, j = e - i * nb;
-      X[(size_t)(j0 + i) * d.ldk + j0 + j] = LU[i][j];
+  // Role D with inv != 0: warp 0 (lane = column c) solves L_JJ x = e_c, warp 1
+  // (lane = row r) solves x U_JJ = e_r, with the same substitution code as roles
+  // U and L; the columns of L_JJ^-1 and rows of U_JJ^-1 meet in the staging tile.
+  const T one = cmk(R(1), R(0));
+  const bool sub_up = (role == 1 && tid < kStepRows) || (role == 0 && inv && warp == 1);
+  const bool sub_lo = (role == 2 && tid < kStepRows) || (role == 0 && inv && warp == 0);
+  if (role == 0 && tid < nb) a.perm[(size_t)w * a.perm_stride + d.piv_off + j0 + tid] = j0 + src[tid];
+  if (sub_up) {
+    // x U_JJ = b: one thread per row, right-looking substitution
+    T x[kMaxNb];
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j) x[j] = role == 1 ? Ws[tid][j] : (j == lane ? one : czero<T>());
+#pragma unroll
+    for (int j = 0; j < kMaxNb; ++j) {
+      x[j] = cmul(x[j], dinv[j]);
+#pragma unroll
+      for (int jj = j + 1; jj < kMaxNb; ++jj) x[jj] = cfms(x[j], LU[j][jj], x[jj]);
     }
-  } else if (role == 1) {
-    // L[r, J] U_JJ = F[r, J]: one thread per row, right-looking substitution
-    if (tid < kStepRows) {
-      T x[kMaxNb];
-#pragma unroll
-      for (int j = 0; j < kMaxNb; ++j) x[j] = Ws[tid][j];
-#pragma unroll
-      for (int j = 0; j < kMaxNb; ++j) {
-        x[j] = cmul(x[j], dinv[j]);
-#pragma unroll
-        for (int jj = j + 1; jj < kMaxNb; ++jj) x[jj] = cfms(x[j], LU[j][jj], x[jj]);
-      }
+    if (role == 1) {
+      // L[r, J] = F[r, J] U_JJ^-1
       const int r = lo + tid;
       if (r < n) {
 #pragma unroll
@@ -838,24 +836,31 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
             g = (a2 == a2) ? (a2 > g ? a2 : g) : R(INFINITY);
           }
       }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kMaxNb; ++j) Ws[kMaxNb + lane][j] = x[j];   // row lane of U_JJ^-1
     }
-  } else if (role == 2) {
-    // L_JJ U[J, c] = (P F)[J, c]: one thread per column, unit-lower substitution
-    if (tid < kStepRows) {
+  } else if (sub_lo) {
+    // L_JJ x = b: one thread per column, unit-lower substitution
+    T x[kMaxNb];
+#pragma unroll
+    for (int i = 0; i < kMaxNb; ++i) x[i] = role == 2 ? Ws[tid][src[i]] : (i == lane ? one : czero<T>());
+#pragma unroll
+    for (int i = 0; i < kMaxNb; ++i)
+#pragma unroll
+      for (int ii = i + 1; ii < kMaxNb; ++ii) x[ii] = cfms(LU[ii][i], x[i], x[ii]);
+    if (role == 2) {
+      // U[J, c] = L_JJ^-1 (P F)[J, c]
       const int c = lo + tid;
-      T x[kMaxNb];
-#pragma unroll
-      for (int i = 0; i < kMaxNb; ++i) x[i] = Ws[tid][src[i]];
-#pragma unroll
-      for (int i = 0; i < kMaxNb; ++i)
-#pragma unroll
-        for (int ii = i + 1; ii < kMaxNb; ++ii) x[ii] = cfms(LU[ii][i], x[i], x[ii]);
       if (c < n)
 #pragma unroll
         for (int i = 0; i < kMaxNb; ++i)
           if (i < nb) F[(size_t)(j0 + i) * ld + c] = x[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < kMaxNb; ++i) Ws[i][lane] = x[i];             // column lane of L_JJ^-1
     }
-  } else {
+  } else if (role == 3) {
     // role P: (P F)[i][c] for the columns left of the block
     const int cc = tid & 63, ig = tid >> 6;
     const int c = lo + cc;
@@ -863,6 +868,16 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     for (int q = 0; q < 8; ++q) {
       const int i = ig + 4 * q;
       if (c < j0 && i < nb) F[(size_t)(j0 + i) * ld + c] = Ws[cc][src[i]];
+    }
+  }
+  if (role == 0) {
+    // the diagonal block of the inverse store: L_JJ^-1 strictly below the
+    // diagonal and U_JJ^-1 on and above it (inv != 0), else the packed L\U
+    T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+    if (inv) __syncthreads();
+    for (int e = tid; e < nb * nb; e += 256) {
+      const int i = e / nb, j = e - i * nb;
+      X[(size_t)(j0 + i) * d.ldk + j0 + j] = !inv ? LU[i][j] : (i > j ? Ws[i][j] : Ws[kMaxNb + i][j]);
     }
   }
   if (role <= 1) {
@@ -1268,6 +1283,117 @@ template <> struct GemmKc<double2> { static constexpr int v = 16; };
 //   schur = 0: panel step at j0 -- trailing update restricted to the pivot-block
 //              rows and columns; the m x m update matrix S is left untouched
 //   schur = 1: once per front after its last panel -- S = F22 - L21 U12, K = k
+// Block row J of L11^-1 and block column J of U11^-1 of the listed large fronts,
+// once the diagonal block J of the inverse store holds L_JJ^-1 / U_JJ^-1 and
+// every block before J is done (block-local pivoting: rows of J never move
+// again, and nothing later writes the entries read here):
+//   lower, columns c in [c0, c0 + 32):  X[J][c] = -L_JJ^-1  sum_{l in [c, j0)} L[J][l] X[l][c]   (from L X = I)
+//   upper, rows r in [r0, r0 + 32):     X[r][J] = -(sum_{l in [r, j0)} X[r][l] U[l][J]) U_JJ^-1 (from X U = I)
+// One CTA per (32-wide chunk, triangle, front): blockIdx.x < nq lower chunk
+// q = blockIdx.x, else upper chunk q = blockIdx.x - nq.  The contraction runs
+// over 32-wide slices of l with the next slice prefetched into registers.
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_inv_fold_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nq) {
+  __shared__ T Am[32][33];   // left operand slice, then T (the sum)
+  __shared__ T Bm[32][33];   // right operand slice, then the diagonal inverse block
+  using R = typename RealOf<T>::type;
+  const int w = blockIdx.z + a.w0;
+  const FrontDesc d = a.P.fronts[flist[blockIdx.y]];
+  if (j0 >= d.k) return;
+  const bool upper = (int)blockIdx.x >= nq;
+  const int c0 = (upper ? (int)blockIdx.x - nq : (int)blockIdx.x) * 32;
+  if (c0 >= j0) return;
+  const int nb = min(kMaxNb, d.k - j0);
+  const int ld = d.ld, ldk = d.ldk;
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const T one = cmk(R(1), R(0));
+  // element e = ty + 8 q' of this thread's four: row (ty + 8 q'), column tx of a slice
+  auto fetch = [&](int l0, T* ra, T* rb) {
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const int i = ty + 8 * qq;
+      const int la = l0 + tx;            // A[i][tx]: column l of the left operand
+      T va = czero<T>();
+      if (la < j0) {
+        if (!upper) va = i < nb ? F[(size_t)(j0 + i) * ld + la] : czero<T>();
+        else {
+          const int r = c0 + i;
+          va = (la >= r) ? X[(size_t)r * ldk + la] : czero<T>();
+        }
+      }
+      ra[qq] = va;
+      const int lb = l0 + i;             // B[i][tx]: row l of the right operand
+      T vb = czero<T>();
+      if (lb < j0) {
+        if (!upper) {
+          const int c = c0 + tx;
+          vb = lb > c ? X[(size_t)lb * ldk + c] : (lb == c ? one : czero<T>());
+        } else {
+          vb = tx < nb ? F[(size_t)lb * ld + j0 + tx] : czero<T>();
+        }
+      }
+      rb[qq] = vb;
+    }
+  };
+  T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};   // T[ty + 8 q'][tx]
+  T ra[4], rb[4];
+  fetch(c0, ra, rb);
+  for (int l0 = c0; l0 < j0; l0 += 32) {
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      Am[ty + 8 * qq][tx] = ra[qq];
+      Bm[ty + 8 * qq][tx] = rb[qq];
+    }
+    __syncthreads();
+    if (l0 + 32 < j0) fetch(l0 + 32, ra, rb);
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const T bv = Bm[kk][tx];
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) acc[qq] = cfma(Am[ty + 8 * qq][kk], bv, acc[qq]);
+    }
+    __syncthreads();
+  }
+  // Am <- T, Bm <- L_JJ^-1 (unit diagonal) or U_JJ^-1, zero outside the block
+#pragma unroll
+  for (int qq = 0; qq < 4; ++qq) {
+    const int i = ty + 8 * qq, j = tx;
+    Am[i][j] = acc[qq];
+    T v = czero<T>();
+    if (i < nb && j < nb) {
+      if (!upper) v = (j < i) ? X[(size_t)(j0 + i) * ldk + j0 + j] : (i == j ? one : czero<T>());
+      else v = (j >= i) ? X[(size_t)(j0 + i) * ldk + j0 + j] : czero<T>();
+    }
+    Bm[i][j] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int qq = 0; qq < 4; ++qq) {
+    const int i = ty + 8 * qq;
+    T o0 = czero<T>(), o1 = czero<T>();
+    if (!upper) {
+      // X[J + i][c0 + tx] = -sum_t Li[i][t] T[t][tx]
+#pragma unroll 8
+      for (int t = 0; t < 32; t += 2) {
+        o0 = cfms(Bm[i][t], Am[t][tx], o0);
+        o1 = cfms(Bm[i][t + 1], Am[t + 1][tx], o1);
+      }
+      if (i < nb && c0 + tx < j0) X[(size_t)(j0 + i) * ldk + c0 + tx] = cadd(o0, o1);
+    } else {
+      // X[c0 + i][J + tx] = -sum_t T[i][t] Ui[t][tx]
+#pragma unroll 8
+      for (int t = 0; t < 32; t += 2) {
+        o0 = cfms(Am[i][t], Bm[t][tx], o0);
+        o1 = cfms(Am[i][t + 1], Bm[t + 1][tx], o1);
+      }
+      if (c0 + i < j0 && tx < nb) X[(size_t)(c0 + i) * ldk + j0 + tx] = cadd(o0, o1);
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, int schur) {
@@ -1422,13 +1548,14 @@ void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cu
 }
 
 template <typename T>
-void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0, int nmax, cudaStream_t s) {
+void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0, int nmax, int inv,
+                          cudaStream_t s) {
   if (nf <= 0) return;
   const int span = std::max(0, nmax - j0 - 1);
   const int nl = (span + kStepRows - 1) / kStepRows;
   const int np = (j0 + kStepRows - 1) / kStepRows;
   lu_step_local_kernel<T><<<dim3(1 + 2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
-      a, flist, j0, nl, nl);
+      a, flist, j0, nl, nl, inv);
 }
 
 template <typename T>
@@ -1474,6 +1601,13 @@ void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0, int
 }
 
 template <typename T>
+void launch_lu_inv_fold(const FactorLaunch& a, const int* flist, int nf, int j0, cudaStream_t s) {
+  const int nq = (j0 + 31) / 32;
+  if (nf <= 0 || nq <= 0) return;
+  lu_inv_fold_kernel<T><<<dim3(2 * nq, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nq);
+}
+
+template <typename T>
 void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax, cudaStream_t s) {
   if (nf <= 0 || mmax <= 0) return;
   const int nt = (mmax + kGemmTile - 1) / kGemmTile;
@@ -1485,12 +1619,13 @@ void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
   template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, int, cudaStream_t); \
-  template void launch_lu_step_local<T>(const FactorLaunch&, const int*, int, int, int, cudaStream_t); \
+  template void launch_lu_step_local<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_inv_blocked<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_diag_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
+  template void launch_lu_inv_fold<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_schur_simt<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);
 FDFD_INST(float2)
 FDFD_INST(double2)

@@ -49,10 +49,12 @@ template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist
                                          int nb, int mmax, int nmax, int below, cudaStream_t s);
 // Pivoting restricted to the 32 x 32 diagonal block J = [j0, j0 + 32): one launch
 // does the block's LU, the L columns below it, the U rows right of it, the row
-// permutation of earlier columns, perm, and the block's inverses into the
-// inverse store (then launch_lu_gemm for the trailing update); nmax = largest n.
+// permutation of earlier columns and perm, and writes into the diagonal block of
+// the inverse store either L_JJ^-1 / U_JJ^-1 (inv != 0) or the packed L\U (inv = 0,
+// for launch_lu_diag_inv); then launch_lu_gemm does the trailing update.
+// nmax = largest n listed.
 template <typename T> void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0,
-                                                int nmax, cudaStream_t s);
+                                                int nmax, int inv, cudaStream_t s);
 // Diagonal blocks of the inverse store: packed L\U (from the panel steps) -> L^-1, U^-1
 template <typename T> void launch_lu_diag_inv(const FactorLaunch& a, const int* flist, int nf, int kmax,
                                               cudaStream_t s);
@@ -70,6 +72,12 @@ template <typename T> void launch_schur_simt(const FactorLaunch& a, const int* f
 // panel-step trailing update restricted to the pivot-block rows and columns
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
+// block row J of L11^-1 and block column J of U11^-1 (J = [j0, j0 + 32)) after
+// launch_lu_step_local with inv != 0 wrote the diagonal block J and the folds of
+// the earlier blocks are done; reads only entries that no later step writes, so
+// it may run beside the front's later steps.
+template <typename T> void launch_lu_inv_fold(const FactorLaunch& a, const int* flist, int nf, int j0,
+                                              cudaStream_t s);
 int lu_small_max_n(int elem_bytes);
 cudaError_t factor_init_attributes();   // once per device, before the first factorisation
 int lu_panel_width(int elem_bytes);
