@@ -331,17 +331,23 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   }
   ctx->lv_solve.assign(L, SolveList{});
   // task lists (front, first row/column): [0] row tasks, [1] column tasks.
-  // A small front is one whole-front task (front | bit 31); a large front is
-  // split into row or column tasks in both launches.
+  // A small or medium front is one whole-front task (front | bit 31; y = 0 for
+  // one warp, 1 for one CTA); a large front is split into row or column tasks
+  // in both directions.
   const int whole_n = flow_whole_max_n();   // fronts swept whole by one warp
-  auto small = [whole_n](const FrontDesc& d) { return d.n <= whole_n; };
+  const int cta_n = flow_cta_max_n();       // ... or by one CTA
+  auto small = [cta_n](const FrontDesc& d) { return d.n <= cta_n; };
   auto add_tasks = [&](TaskList& tl, int l, bool rect, bool over_m, int step) {
     if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
     tl.off = (int)lists.size();
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
       if (small(d)) {
-        if (!rect) { lists.push_back((int)(0x80000000u | (unsigned)f)); lists.push_back(0); tl.n++; }
+        if (!rect) {
+          lists.push_back((int)(0x80000000u | (unsigned)f));
+          lists.push_back(d.n <= whole_n ? 0 : 1);
+          tl.n++;
+        }
         continue;
       }
       if (rect && d.m == 0) continue;
@@ -369,8 +375,9 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   }
   // Dataflow queues: the same tasks as the level lists, in dependency order,
   // off-diagonal tasks tagged with bit 30; per level the whole small fronts
-  // first, in units of up to 8 (one warp each), then the large fronts' tasks
-  // (one unit each) in phase order; per-front task counts beside them.
+  // first, in units of up to 8 (one warp each), then the whole medium fronts
+  // (one CTA each), then the large fronts' tasks (one unit each) in phase
+  // order; per-front task counts beside them.
   const int nf = (int)p.fronts.size();
   for (int t = 0; t < 2; ++t) {
     for (int dir = 0; dir < 2; ++dir) {
@@ -383,7 +390,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         int first = -1, cnt = 0;
         for (int i = 0; i < sl.tri[t].n; ++i) {
           const int code = lists[sl.tri[t].off + 2 * i];
-          if (code >= 0) continue;                           // large-front task
+          if (code >= 0 || lists[sl.tri[t].off + 2 * i + 1] != 0) continue;   // not a small front
           const int f = code & 0x7fffffff;
           if (cnt == 0) first = (int)tasks.size() / 2;
           tasks.push_back(code); tasks.push_back(0);
@@ -391,6 +398,13 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
           if (++cnt == 8) { put_unit(first, (int)(0x80000000u | 8u)); cnt = 0; }
         }
         if (cnt) put_unit(first, (int)(0x80000000u | (unsigned)cnt));
+        for (int i = 0; i < sl.tri[t].n; ++i) {               // whole medium fronts, one unit each
+          const int code = lists[sl.tri[t].off + 2 * i];
+          if (code >= 0 || lists[sl.tri[t].off + 2 * i + 1] != 1) continue;
+          put_unit((int)tasks.size() / 2, 1);
+          tasks.push_back(code); tasks.push_back(1);
+          all[code & 0x7fffffff]++;
+        }
       };
       auto put_tri = [&](const SolveList& sl) {
         for (int i = 0; i < sl.tri[t].n; ++i) {
@@ -592,7 +606,7 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
         {
           // block LU and inverses, L columns, U rows and the row permutation of the step in one launch
           Prof pr(ctx, PK_LU_STEP, (pf + lf + tf) * nwd, (pb + lb + tb) * nwd);
-          launch_lu_step_local<T>(fa, fl, ll.nlarge, j0, ll.nmax_large, 1, s);
+          launch_lu_step_local<T>(fa, fl, ll.nlarge, j0, ll.nmax_large, s);
         }
         // block row J of L11^-1 and block column J of U11^-1: products with the
         // inverse so far, then with the block's own inverse

@@ -624,14 +624,15 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
 //   chosen inside B; deterministic, so every CTA gets the same bits) while
 //   warps 4-7 stage the CTA's operand, then does one role:
 //     role D (block 0): the row permutation of J into perm, L_JJ^-1 and U_JJ^-1
-//                       into the diagonal block of the inverse store (or the
-//                       packed L\U of B, for lu_diag_inv), growth of its multipliers;
+//                       into the diagonal block of the inverse store (L_JJ^-1
+//                       strictly below the diagonal, U_JJ^-1 on and above it),
+//                       growth of its multipliers;
 //     role L: rows r >= j0 + nb, L[r, J] U_JJ = F[r, J]          (64 rows / CTA);
 //     role U: columns c >= j0 + nb, L_JJ U[J, c] = (P F)[J, c]   (64 columns / CTA);
 //     role P: columns c < j0, F[J, c] <- (P F)[J, c]             (64 columns / CTA);
 //   L and U by one-thread-per-row/column substitution against the factored B.
 // The factored diagonal block is not stored back into F (nothing reads it there:
-// the sweeps and the inverse use the inverse store).  Roles touch disjoint
+// the sweeps and lu_inv_fold use the inverse store).  Roles touch disjoint
 // entries of F and read B only, so the CTAs are independent.
 // ---------------------------------------------------------------------------
 constexpr int kStepRows = 64;
@@ -717,45 +718,9 @@ __device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __re
   return g;
 }
 
-// Column c = lane of Li (unit lower, diagonal included) or Ui, from LU in
-// shared memory, written into out (zero outside the triangle).
-template <typename T>
-__device__ __forceinline__ void tri_inverse_col(const T (*LU)[kMaxNb + 1], const T* dinv, bool upper,
-                                                T (*out)[kMaxNb + 1]) {
-  using R = typename RealOf<T>::type;
-  const int c = threadIdx.x & 31;
-  if (!upper) {
-    for (int i = 0; i < kMaxNb; ++i) {
-      T a0 = (i == c) ? cmk(R(1), R(0)) : czero<T>(), a1 = czero<T>();
-      if (i > c) {
-        int l = c;
-        for (; l + 1 < i; l += 2) {
-          a0 = cfms(LU[i][l], out[l][c], a0);
-          a1 = cfms(LU[i][l + 1], out[l + 1][c], a1);
-        }
-        if (l < i) a0 = cfms(LU[i][l], out[l][c], a0);
-      }
-      out[i][c] = (i >= c) ? cadd(a0, a1) : czero<T>();
-    }
-  } else {
-    for (int i = kMaxNb - 1; i >= 0; --i) {
-      T a0 = (i == c) ? cmk(R(1), R(0)) : czero<T>(), a1 = czero<T>();
-      if (i < c) {
-        int l = i + 1;
-        for (; l + 1 <= c; l += 2) {
-          a0 = cfms(LU[i][l], out[l][c], a0);
-          a1 = cfms(LU[i][l + 1], out[l + 1][c], a1);
-        }
-        if (l <= c) a0 = cfms(LU[i][l], out[l][c], a0);
-      }
-      out[i][c] = (i <= c) ? cmul(cadd(a0, a1), dinv[i]) : czero<T>();
-    }
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu, int inv) {
+lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu) {
   using R = typename RealOf<T>::type;
   using Blk = T[kMaxNb + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -806,12 +771,12 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     }
   }
   __syncthreads();
-  // Role D with inv != 0: warp 0 (lane = column c) solves L_JJ x = e_c, warp 1
+  // Role D: warp 0 (lane = column c) solves L_JJ x = e_c, warp 1
   // (lane = row r) solves x U_JJ = e_r, with the same substitution code as roles
   // U and L; the columns of L_JJ^-1 and rows of U_JJ^-1 meet in the staging tile.
   const T one = cmk(R(1), R(0));
-  const bool sub_up = (role == 1 && tid < kStepRows) || (role == 0 && inv && warp == 1);
-  const bool sub_lo = (role == 2 && tid < kStepRows) || (role == 0 && inv && warp == 0);
+  const bool sub_up = (role == 1 && tid < kStepRows) || (role == 0 && warp == 1);
+  const bool sub_lo = (role == 2 && tid < kStepRows) || (role == 0 && warp == 0);
   if (role == 0 && tid < nb) a.perm[(size_t)w * a.perm_stride + d.piv_off + j0 + tid] = j0 + src[tid];
   if (sub_up) {
     // x U_JJ = b: one thread per row, right-looking substitution
@@ -872,12 +837,12 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   }
   if (role == 0) {
     // the diagonal block of the inverse store: L_JJ^-1 strictly below the
-    // diagonal and U_JJ^-1 on and above it (inv != 0), else the packed L\U
+    // diagonal, U_JJ^-1 on and above it
     T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
-    if (inv) __syncthreads();
+    __syncthreads();
     for (int e = tid; e < nb * nb; e += 256) {
       const int i = e / nb, j = e - i * nb;
-      X[(size_t)(j0 + i) * d.ldk + j0 + j] = !inv ? LU[i][j] : (i > j ? Ws[i][j] : Ws[kMaxNb + i][j]);
+      X[(size_t)(j0 + i) * d.ldk + j0 + j] = i > j ? Ws[i][j] : Ws[kMaxNb + i][j];
     }
   }
   if (role <= 1) {
@@ -1028,134 +993,10 @@ lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
   }
 }
 
-// Diagonal 32 x 32 blocks of the inverse store hold packed L\U factors (written
-// by the panel steps); replaces each by L^-1 (strictly lower part, unit
-// diagonal implied) and U^-1 (upper part with the diagonal).  One CTA per
-// (block, front); warp 0 inverts L, warp 1 inverts U.
-template <typename T>
-__global__ void __launch_bounds__(64)
-lu_diag_inv_kernel(FactorLaunch a, const int* __restrict__ flist) {
-  using R = typename RealOf<T>::type;
-  using Blk = T[kMaxNb + 1];
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Blk* LU = reinterpret_cast<Blk*>(smem_raw);     // [32][33] each
-  Blk* Li = LU + kMaxNb;
-  Blk* Ui = Li + kMaxNb;
-  T* dinv = reinterpret_cast<T*>(Ui + kMaxNb);
-  const int w = blockIdx.z + a.w0;
-  const FrontDesc d = a.P.fronts[flist[blockIdx.y]];
-  const int j0 = blockIdx.x * kMaxNb;
-  if (j0 >= d.k) return;
-  const int nb = min(kMaxNb, d.k - j0);
-  T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
-  const T one = cmk(R(1), R(0));
-  for (int e = threadIdx.x; e < kMaxNb * kMaxNb; e += 64) {
-    const int i = e >> 5, j = e & 31;
-    LU[i][j] = (i < nb && j < nb) ? X[(size_t)(j0 + i) * d.ldk + j0 + j] : (i == j ? one : czero<T>());
-  }
-  __syncthreads();
-  if (threadIdx.x < kMaxNb) dinv[threadIdx.x] = fast_crcp(LU[threadIdx.x][threadIdx.x]);
-  __syncthreads();
-  if (threadIdx.x < 32) tri_inverse_col<T>(LU, dinv, false, Li);
-  else tri_inverse_col<T>(LU, dinv, true, Ui);
-  __syncthreads();
-  for (int e = threadIdx.x; e < nb * nb; e += 64) {
-    const int i = e / nb, j = e - i * nb;
-    X[(size_t)(j0 + i) * d.ldk + j0 + j] = (i > j) ? Li[i][j] : Ui[i][j];
-  }
-}
-
-// dynamic shared memory of lu_diag_inv_kernel: LU, Li, Ui, 1/U[p][p]
-size_t diag_inv_smem(size_t es) { return ((size_t)3 * kMaxNb * (kMaxNb + 1) + kMaxNb) * es; }
-
 // dynamic shared memory of lu_step_local_kernel: LU, the 64 x 33 staging tile, 1/U[p][p],
 // the multipliers of one step (double-buffered)
 size_t step_local_smem(size_t es) {
   return ((size_t)(kMaxNb + kStepRows) * (kMaxNb + 1) + kMaxNb + 2 * 32) * es;
-}
-
-// Off-diagonal blocks of L11^-1 and U11^-1 when their 32 x 32 diagonal blocks
-// are already in the inverse store (block-local pivoting writes them at every
-// panel step).  One CTA per (32-column block cb, triangle, front) walks the
-// row blocks away from the diagonal:
-//   lower: X[rb][cb] = -Li_rb  sum_{l in [cb, rb)}    L[rb][l] X[l][cb]   (rb = cb+32, cb+64, ...)
-//   upper: X[rb][cb] = -Ui_rb  sum_{l in (rb, cb+32)} U[rb][l] X[l][cb]   (rb = cb-32, cb-64, ...)
-// (two products per step, no substitution).  Different CTAs write disjoint
-// entries and read only entries other CTAs do not write.
-template <typename T>
-__global__ void __launch_bounds__(256)
-lu_inv_blocked_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
-  using R = typename RealOf<T>::type;
-  __shared__ T tile0[32][33];
-  __shared__ T tile1[32][33];
-  const int w = blockIdx.z + a.w0;
-  const int f = flist[blockIdx.y];
-  const FrontDesc d = a.P.fronts[f];
-  const bool upper = (int)blockIdx.x >= nblk;
-  const int cb = (upper ? (int)blockIdx.x - nblk : (int)blockIdx.x) * 32;
-  const int k = d.k;
-  if (cb >= k) return;
-  const int ld = d.ld, ldk = d.ldk;
-  const int cw = min(32, k - cb);
-  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
-  T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int c = cb + tx;
-  const T one = cmk(R(1), R(0));
-  const int step = upper ? -32 : 32;
-  for (int rb = cb + step; upper ? rb >= 0 : rb < k; rb += step) {
-    const int rh = min(32, k - rb);
-    T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-    const int l_lo = upper ? rb + 32 : cb, l_hi = upper ? cb + cw : rb;
-    for (int l0 = l_lo; l0 < l_hi; l0 += 32) {
-      for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-        const int i = e >> 5, j = e & 31;
-        const int l = l0 + j;
-        tile0[i][j] = (i < rh && l < l_hi) ? F[(size_t)(rb + i) * ld + l] : czero<T>();
-        const int li = l0 + i, cc = cb + j;
-        T xv = czero<T>();
-        if (j < cw && li < l_hi) {
-          if (upper) xv = (li <= cc) ? X[(size_t)li * ldk + cc] : czero<T>();
-          else xv = (li > cc) ? X[(size_t)li * ldk + cc] : (li == cc ? one : czero<T>());
-        }
-        tile1[i][j] = xv;
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int j = 0; j < 32; ++j) {
-        const T xv = tile1[j][tx];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = cfma(tile0[ty + 8 * q][j], xv, acc[q]);
-      }
-      __syncthreads();
-    }
-    // tile1 <- acc, tile0 <- diagonal inverse block of rb (unit lower or upper)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) tile1[ty + 8 * q][tx] = acc[q];
-    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-      const int i = e >> 5, j = e & 31;
-      T v = czero<T>();
-      if (i < rh && j < rh) {
-        if (upper) v = (j >= i) ? X[(size_t)(rb + i) * ldk + rb + j] : czero<T>();
-        else v = (j < i) ? X[(size_t)(rb + i) * ldk + rb + j] : (i == j ? one : czero<T>());
-      }
-      tile0[i][j] = v;
-    }
-    __syncthreads();
-    T out[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-#pragma unroll 8
-    for (int t = 0; t < 32; ++t) {
-      const T av = tile1[t][tx];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = cfms(tile0[ty + 8 * q][t], av, out[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = ty + 8 * q;
-      if (i < rh && tx < cw) X[(size_t)(rb + i) * ldk + c] = out[q];
-    }
-    __syncthreads();
-  }
 }
 
 // Boundary rows of the panel: L21[:, j0:j0+nb] = A21[:, j0:j0+nb] U_jj^-1 (right
@@ -1496,9 +1337,6 @@ cudaError_t factor_init_attributes() {
   e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            2 * 64 * 64 * 16);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lu_diag_inv_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)diag_inv_smem(16));
-  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_step_local_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)step_local_smem(8));
   if (e != cudaSuccess) return e;
@@ -1548,28 +1386,13 @@ void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cu
 }
 
 template <typename T>
-void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0, int nmax, int inv,
-                          cudaStream_t s) {
+void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0, int nmax, cudaStream_t s) {
   if (nf <= 0) return;
   const int span = std::max(0, nmax - j0 - 1);
   const int nl = (span + kStepRows - 1) / kStepRows;
   const int np = (j0 + kStepRows - 1) / kStepRows;
   lu_step_local_kernel<T><<<dim3(1 + 2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
-      a, flist, j0, nl, nl, inv);
-}
-
-template <typename T>
-void launch_lu_diag_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s) {
-  if (nf <= 0 || kmax <= 0) return;
-  lu_diag_inv_kernel<T><<<dim3((kmax + kMaxNb - 1) / kMaxNb, nf, a.n_omega), 64, diag_inv_smem(sizeof(T)), s>>>(
-      a, flist);
-}
-
-template <typename T>
-void launch_lu_inv_blocked(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s) {
-  if (nf <= 0 || kmax <= 0) return;
-  const int nblk = (kmax + 31) / 32;
-  lu_inv_blocked_kernel<T><<<dim3(2 * nblk, nf, a.n_omega), 256, 0, s>>>(a, flist, nblk);
+      a, flist, j0, nl, nl);
 }
 
 template <typename T>
@@ -1619,9 +1442,7 @@ void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax
   template void launch_lu_small<T>(const FactorLaunch&, const int*, int, int, cudaStream_t);      \
   template void launch_lu_panel<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_l21<T>(const FactorLaunch&, const int*, int, int, int, int, int, int, cudaStream_t); \
-  template void launch_lu_step_local<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
-  template void launch_lu_inv_blocked<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
-  template void launch_lu_diag_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
+  template void launch_lu_step_local<T>(const FactorLaunch&, const int*, int, int, int, cudaStream_t); \
   template void launch_lu_inv<T>(const FactorLaunch&, const int*, int, int, cudaStream_t); \
   template void launch_lu_trsm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \
   template void launch_lu_gemm<T>(const FactorLaunch&, const int*, int, int, int, int, cudaStream_t); \

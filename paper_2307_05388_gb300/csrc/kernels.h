@@ -49,19 +49,12 @@ template <typename T> void launch_lu_l21(const FactorLaunch& a, const int* flist
                                          int nb, int mmax, int nmax, int below, cudaStream_t s);
 // Pivoting restricted to the 32 x 32 diagonal block J = [j0, j0 + 32): one launch
 // does the block's LU, the L columns below it, the U rows right of it, the row
-// permutation of earlier columns and perm, and writes into the diagonal block of
-// the inverse store either L_JJ^-1 / U_JJ^-1 (inv != 0) or the packed L\U (inv = 0,
-// for launch_lu_diag_inv); then launch_lu_gemm does the trailing update.
+// permutation of earlier columns and perm, and writes L_JJ^-1 / U_JJ^-1 into the
+// diagonal block of the inverse store; then launch_lu_gemm does the trailing
+// update and launch_lu_inv_fold the rest of block row / column J of the inverses.
 // nmax = largest n listed.
 template <typename T> void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j0,
-                                                int nmax, int inv, cudaStream_t s);
-// Diagonal blocks of the inverse store: packed L\U (from the panel steps) -> L^-1, U^-1
-template <typename T> void launch_lu_diag_inv(const FactorLaunch& a, const int* flist, int nf, int kmax,
-                                              cudaStream_t s);
-// L11^-1 / U11^-1 off-diagonal blocks from the diagonal blocks already in the
-// inverse store (block-local pivoting path)
-template <typename T> void launch_lu_inv_blocked(const FactorLaunch& a, const int* flist, int nf, int kmax,
-                                                 cudaStream_t s);
+                                                int nmax, cudaStream_t s);
 constexpr int kSwapScratchInts = 130;   // ints of swap scratch per (wavelength, listed front)
 template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
@@ -73,7 +66,7 @@ template <typename T> void launch_schur_simt(const FactorLaunch& a, const int* f
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);
 // block row J of L11^-1 and block column J of U11^-1 (J = [j0, j0 + 32)) after
-// launch_lu_step_local with inv != 0 wrote the diagonal block J and the folds of
+// launch_lu_step_local wrote the diagonal block J and the folds of
 // the earlier blocks are done; reads only entries that no later step writes, so
 // it may run beside the front's later steps.
 template <typename T> void launch_lu_inv_fold(const FactorLaunch& a, const int* flist, int nf, int j0,
@@ -107,11 +100,13 @@ int sweep_col_block();
 // One direction of a sweep pair as a single persistent launch (dataflow over
 // the elimination tree).  tasks: the direction's inverse-block, off-diagonal
 // and whole-front tasks in dependency order (per level: whole small fronts,
-// then the large fronts' phase-1 and phase-2 tasks), x = front | 1<<31 (whole
-// front) | 1<<30 (off-diagonal task), y = first row / column.
+// whole medium fronts, then the large fronts' phase-1 and phase-2 tasks),
+// x = front | 1<<31 (whole front: y = 0 for one warp, y = 1 for one CTA) |
+// 1<<30 (off-diagonal task), y = first row / column.
 struct FlowQueue {
   const int2* tasks;
-  const int2* units;       // what one CTA takes at a time: (first task, 1) for a large-front task, or
+  const int2* units;       // what one CTA takes at a time: (first task, 1) for a large-front task or a
+                           // whole medium front, or
                            // (first task, 0x80000000 | count) for up to 8 whole small fronts of one level
   int nunits;              // units; each runs for every launched wavelength
   int* ctr;                // [1 + 2 * n_omega * n_fronts] ints, zero before the launch
@@ -124,6 +119,7 @@ template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, co
                                              int grid, const void* in, void* out, cudaStream_t s);
 int flow_blocks_per_sm(int elem_bytes, int vmax);
 int flow_whole_max_n();   // largest front the flow kernel runs as a one-warp whole-front task
+int flow_cta_max_n();     // largest front it runs as one whole-front task of a CTA
 // one bounded wait on a zero flag (gives up, sets *err); for the self-test entry point
 cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s);
 

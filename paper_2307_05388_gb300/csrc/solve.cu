@@ -77,7 +77,7 @@ template <typename T, typename Mask>
 __device__ __forceinline__ T col_dot(const T* __restrict__ base, int ld, const T* vec, int r0, int r1,
                                      bool live, Mask inside, T (*red)[32]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int UN = 4;
+  constexpr int UN = sizeof(T) == 8 ? 16 : 8;
   T a0 = czero<T>(), a1 = czero<T>();
   if (live) {
     int r = r0 + warp;
@@ -149,36 +149,80 @@ __device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& 
 //   SWEEP 3: cols a:    q[a]  = t[a] + sum_{b>a} X_L[b][a] t[b]    (t = vf[0..k)), x[P a] = q[a]
 // ---------------------------------------------------------------------------
 // A whole small front done by one warp (the dataflow sweep runs up to eight of
-// them per CTA): lane = row (L, U) or column (U^T, L^T) of each product, each
-// lane's dot product with eight loads in flight; vs is the warp's own slice
-// of n + k entries.
-template <typename T>
-__device__ __forceinline__ T lane_dot(const T* __restrict__ row, const T* vec, int c0, int c1) {
-  T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-  int c = c0;
-  for (; c + 7 < c1; c += 8) {
-    T f[8];
+// them per CTA), every product spread over all 32 lanes: a row product gives
+// each row 32/R lanes (R rows at a time), a column product gives each column
+// 32/C lanes that split its rows (C columns at a time), partial sums combined
+// by a fixed butterfly; vs is the warp's own slice of n + k entries.
+template <typename T, typename Lo, typename Hi, typename Out>
+__device__ __forceinline__ void warp_rows_dot(const T* __restrict__ A, int ld, int nrows, const T* vec, Lo lo, Hi hi,
+                                              Out out) {
+  constexpr int UN = sizeof(T) == 8 ? 16 : 8;
+  const int lane = threadIdx.x & 31;
+  int R = 32;
+  while (R > 1 && R / 2 >= nrows) R >>= 1;      // rows at a time
+  const int G = 32 / R;                          // lanes per row
+  const int gl = lane & (G - 1), ri = lane / G;
+  for (int i0 = 0; i0 < nrows; i0 += R) {
+    const int i = i0 + ri;
+    T a0 = czero<T>(), a1 = czero<T>();
+    if (i < nrows) {
+      const T* row = A + (size_t)i * ld;
+      const int e = hi(i);
+      int c = lo(i) + gl;
+      for (; c + (UN - 1) * G < e; c += UN * G) {
+        T f[UN];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) f[u] = row[c + u];
+        for (int u = 0; u < UN; ++u) f[u] = row[c + u * G];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u & 3] = cfma(f[u], vec[c + u], acc[u & 3]);
+        for (int u = 0; u < UN; ++u) {
+          if (u & 1) a1 = cfma(f[u], vec[c + u * G], a1);
+          else a0 = cfma(f[u], vec[c + u * G], a0);
+        }
+      }
+      for (; c < e; c += G) a0 = cfma(row[c], vec[c], a0);
+    }
+    T acc = cadd(a0, a1);
+    for (int o = 1; o < G; o <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (gl == 0 && i < nrows) out(i, acc);
   }
-  for (; c < c1; ++c) acc[0] = cfma(row[c], vec[c], acc[0]);
-  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
-template <typename T>
-__device__ __forceinline__ T lane_col_dot(const T* __restrict__ col, int ld, const T* vec, int r0, int r1) {
-  T acc[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
-  int r = r0;
-  for (; r + 7 < r1; r += 8) {
-    T f[8];
+template <typename T, typename Lo, typename Hi, typename Out>
+__device__ __forceinline__ void warp_cols_dot(const T* __restrict__ A, int ld, int ncols, const T* vec, Lo lo, Hi hi,
+                                              Out out) {
+  constexpr int UN = sizeof(T) == 8 ? 16 : 8;
+  const int lane = threadIdx.x & 31;
+  int C = 32;
+  while (C > 1 && C / 2 >= ncols) C >>= 1;      // columns at a time
+  const int S = 32 / C;                          // row slices per column
+  const int cl = lane & (C - 1), si = lane / C;
+  for (int j0 = 0; j0 < ncols; j0 += C) {
+    const int j = j0 + cl;
+    T a0 = czero<T>(), a1 = czero<T>();
+    if (j < ncols) {
+      const int e = hi(j);
+      int r = lo(j) + si;
+      for (; r + (UN - 1) * S < e; r += UN * S) {
+        T f[UN];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) f[u] = col[(size_t)(r + u) * ld];
+        for (int u = 0; u < UN; ++u) f[u] = A[(size_t)(r + u * S) * ld + j];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u & 3] = cfma(f[u], vec[r + u], acc[u & 3]);
+        for (int u = 0; u < UN; ++u) {
+          if (u & 1) a1 = cfma(f[u], vec[r + u * S], a1);
+          else a0 = cfma(f[u], vec[r + u * S], a0);
+        }
+      }
+      for (; r < e; r += S) a0 = cfma(A[(size_t)r * ld + j], vec[r], a0);
+    }
+    T acc = cadd(a0, a1);
+    for (int o = C; o < 32; o <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (si == 0 && j < ncols) out(j, acc);
   }
-  for (; r < r1; ++r) acc[0] = cfma(col[(size_t)r * ld], vec[r], acc[0]);
-  return cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
 }
 
 template <typename T, int SWEEP>
@@ -209,23 +253,31 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
     }
     __syncwarp();
     if (SWEEP == 0) {                              // y = X_L (P v)_k;  u = v_m - L21 y
-      for (int row = lane; row < k; row += 32) ws[row] = cadd(vs[row], lane_dot(X + (size_t)row * ldk, vs, 0, row));
+      warp_rows_dot(X, ldk, k, vs, [](int) { return 0; }, [](int i) { return i; },
+                    [&](int i, T acc) { ws[i] = cadd(vs[i], acc); });
       __syncwarp();
-      for (int t = lane; t < m; t += 32) vf[k + t] = csub(vs[k + t], lane_dot(F + (size_t)(k + t) * ld, ws, 0, k));
+      warp_rows_dot(F + (size_t)k * ld, ld, m, ws, [](int) { return 0; }, [&](int) { return k; },
+                    [&](int t, T acc) { vf[k + t] = csub(vs[k + t], acc); });
       for (int s = lane; s < k; s += 32) vf[s] = ws[s];
     } else if (SWEEP == 1) {                       // z = y - U12 x_m;  x_k = X_U z
-      for (int row = lane; row < k; row += 32) ws[row] = csub(vs[row], lane_dot(F + (size_t)row * ld + k, vs + k, 0, m));
+      warp_rows_dot(F + k, ld, k, vs + k, [](int) { return 0; }, [&](int) { return m; },
+                    [&](int i, T acc) { ws[i] = csub(vs[i], acc); });
       __syncwarp();
-      for (int row = lane; row < k; row += 32) xo[idx[row]] = lane_dot(X + (size_t)row * ldk, ws, row, k);
+      warp_rows_dot(X, ldk, k, ws, [](int i) { return i; }, [&](int) { return k; },
+                    [&](int i, T acc) { xo[idx[i]] = acc; });
     } else if (SWEEP == 2) {                       // w = X_U^T v_k;  u = v_m - U12^T w
-      for (int c = lane; c < k; c += 32) ws[c] = lane_col_dot(X + c, ldk, vs, 0, c + 1);
+      warp_cols_dot(X, ldk, k, vs, [](int) { return 0; }, [](int j) { return j + 1; },
+                    [&](int j, T acc) { ws[j] = acc; });
       __syncwarp();
-      for (int t = lane; t < m; t += 32) vf[k + t] = csub(vs[k + t], lane_col_dot(F + k + t, ld, ws, 0, k));
+      warp_cols_dot(F + k, ld, m, ws, [](int) { return 0; }, [&](int) { return k; },
+                    [&](int t, T acc) { vf[k + t] = csub(vs[k + t], acc); });
       for (int s = lane; s < k; s += 32) vf[s] = ws[s];
     } else {                                       // t = w - L21^T x_m;  x_k = P^T X_L^T t   (vs[k..n) = -x_m)
-      for (int c = lane; c < k; c += 32) ws[c] = cadd(vs[c], lane_col_dot(F + (size_t)k * ld + c, ld, vs + k, 0, m));
+      warp_cols_dot(F + (size_t)k * ld, ld, k, vs + k, [](int) { return 0; }, [&](int) { return m; },
+                    [&](int j, T acc) { ws[j] = cadd(vs[j], acc); });
       __syncwarp();
-      for (int c = lane; c < k; c += 32) xo[idx[Pm[c]]] = cadd(ws[c], lane_col_dot(X + c, ldk, ws, c + 1, k));
+      warp_cols_dot(X, ldk, k, ws, [](int j) { return j + 1; }, [&](int) { return k; },
+                    [&](int j, T acc) { xo[idx[Pm[j]]] = cadd(ws[j], acc); });
     }
     __syncwarp();
   }
@@ -340,6 +392,178 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
 }
 
 // ---------------------------------------------------------------------------
+// A whole medium front (64 < n <= flow_cta_max_n()) done by one CTA: both
+// products of the front in one task, separated by a CTA barrier instead of a
+// completion counter.  Row products give each row a group of G lanes (G chosen
+// so that a lane holds at most 8 entries of a row, two rows in flight per
+// group); column products give each column a lane and split the rows over the
+// warps when there are fewer than 8 column groups, reducing the partial sums in
+// a fixed order.
+// ---------------------------------------------------------------------------
+template <typename T, int G, typename Lo, typename Hi, typename Out>
+__device__ __forceinline__ void rows_dot_g(const T* __restrict__ A, int ld, int nrows, const T* vec, Lo lo, Hi hi,
+                                           Out out) {
+  constexpr int NG = kThreads / G;       // row groups in the CTA
+  constexpr int UN = 8;
+  const int sl = threadIdx.x & (G - 1), grp = threadIdx.x / G;
+  for (int base = 0; base < nrows; base += 2 * NG) {   // same trip count for every lane of a warp
+    const int i0 = base + grp, i1 = base + NG + grp;
+    const bool v0 = i0 < nrows, v1 = i1 < nrows;
+    const int h0 = v0 ? hi(i0) : 0, h1 = v1 ? hi(i1) : 0;
+    int c0 = (v0 ? lo(i0) : 0) + sl, c1 = (v1 ? lo(i1) : 0) + sl;
+    const T* r0 = A + (size_t)(v0 ? i0 : 0) * ld;
+    const T* r1 = A + (size_t)(v1 ? i1 : 0) * ld;
+    T a0 = czero<T>(), a1 = czero<T>();
+    while (c0 < h0 || c1 < h1) {
+      T f0[UN], f1[UN];
+#pragma unroll
+      for (int u = 0; u < UN; ++u) {
+        f0[u] = c0 + u * G < h0 ? r0[c0 + u * G] : czero<T>();
+        f1[u] = c1 + u * G < h1 ? r1[c1 + u * G] : czero<T>();
+      }
+#pragma unroll
+      for (int u = 0; u < UN; ++u) {
+        if (c0 + u * G < h0) a0 = cfma(f0[u], vec[c0 + u * G], a0);
+        if (c1 + u * G < h1) a1 = cfma(f1[u], vec[c1 + u * G], a1);
+      }
+      c0 += UN * G;
+      c1 += UN * G;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o);
+      a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o);
+      a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o);
+      a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o);
+    }
+    if (sl == 0) {
+      if (v0) out(i0, a0);
+      if (v1) out(i1, a1);
+    }
+  }
+}
+
+// out(i, sum_{c in [lo(i), hi(i))} A[i][c] vec[c]) for rows i < nrows; len = longest row
+template <typename T, typename Lo, typename Hi, typename Out>
+__device__ __forceinline__ void rows_dot(const T* __restrict__ A, int ld, int nrows, int len, const T* vec, Lo lo,
+                                         Hi hi, Out out) {
+  if (len <= 16) rows_dot_g<T, 2>(A, ld, nrows, vec, lo, hi, out);
+  else if (len <= 32) rows_dot_g<T, 4>(A, ld, nrows, vec, lo, hi, out);
+  else if (len <= 64) rows_dot_g<T, 8>(A, ld, nrows, vec, lo, hi, out);
+  else if (len <= 128) rows_dot_g<T, 16>(A, ld, nrows, vec, lo, hi, out);
+  else rows_dot_g<T, 32>(A, ld, nrows, vec, lo, hi, out);
+}
+
+// out(j, sum_{r in [lo(j), hi(j))} A[r][j] vec[r]) for columns j < ncols (rows < nrows)
+template <typename T, typename Lo, typename Hi, typename Out>
+__device__ __forceinline__ void cols_dot(const T* __restrict__ A, int ld, int ncols, int nrows, const T* vec, Lo lo,
+                                         Hi hi, Out out, T (*red)[32]) {
+  constexpr int UN = sizeof(T) == 8 ? 16 : 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncg = (ncols + 31) / 32;
+  const int ns = ncg >= kWarps ? 1 : kWarps / ncg;     // row slices per column group
+  const int gpr = kWarps / ns;                          // column groups per round
+  const int slen = (nrows + ns - 1) / ns;
+  for (int g0 = 0; g0 < ncg; g0 += gpr) {
+    const int gi = g0 + warp / ns, si = warp - (warp / ns) * ns;
+    const int j = gi * 32 + lane;
+    T acc0 = czero<T>(), acc1 = czero<T>();
+    if (warp / ns < gpr && gi < ncg && j < ncols) {
+      const int rb = max(lo(j), si * slen), re = min(hi(j), min(nrows, (si + 1) * slen));
+      int r = rb;
+      for (; r + UN - 1 < re; r += UN) {
+        T f[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) f[u] = A[(size_t)(r + u) * ld + j];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+          if (u & 1) acc1 = cfma(f[u], vec[r + u], acc1);
+          else acc0 = cfma(f[u], vec[r + u], acc0);
+        }
+      }
+      for (; r < re; ++r) acc0 = cfma(A[(size_t)r * ld + j], vec[r], acc0);
+    }
+    if (ns > 1) {
+      red[warp][lane] = cadd(acc0, acc1);
+      __syncthreads();
+      const int gj = g0 + warp, jj = gj * 32 + lane;
+      if (warp < gpr && gj < ncg && jj < ncols) {
+        T sum = red[warp * ns][lane];
+        for (int q = 1; q < ns; ++q) sum = cadd(sum, red[warp * ns + q][lane]);
+        out(jj, sum);
+      }
+      __syncthreads();
+    } else if (gi < ncg && j < ncols) {
+      out(j, cadd(acc0, acc1));
+    }
+  }
+}
+
+template <typename T, int SWEEP>
+__device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDesc& d, int w,
+                                             const T* __restrict__ in, T* __restrict__ out, T* vs, T (*red)[32]) {
+  const int k = d.k, m = d.m, n = d.n, ldk = d.ldk, ld = d.ld;
+  const int tid = threadIdx.x;
+  const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int* idx = a.P.idx + d.idx_off;
+  const Kids kids = load_kids(a, d);
+  T* ws = vs + n;
+  for (int r = a.r0; r < a.r0 + a.nr; ++r) {
+    const size_t sys = (size_t)w * a.nrhs + r;
+    T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
+    T* vf = vbs + d.v_off;
+    T* xo = out + sys * a.n;
+    if (SWEEP == 0 || SWEEP == 2) {
+      const T* rhs = in + sys * a.n;
+      for (int s = tid; s < n; s += 2 * kThreads) {
+        const int s2 = s + kThreads;
+        const T g1 = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
+        const T g2 = s2 < n ? gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s2 < k) ? Pm[s2] : s2) : czero<T>();
+        vs[s] = g1;
+        if (s2 < n) vs[s2] = g2;
+      }
+    } else {
+      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
+      for (int t = tid; t < m; t += kThreads) {
+        const T x = ldv(xo + idx[k + t]);
+        vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
+      }
+    }
+    __syncthreads();
+    if (SWEEP == 0) {                              // y = X_L (P v)_k;  u = v_m - L21 y
+      rows_dot(X, ldk, k, k, vs, [](int) { return 0; }, [](int i) { return i; },
+               [&](int i, T acc) { ws[i] = cadd(vs[i], acc); });
+      __syncthreads();
+      rows_dot(F + (size_t)k * ld, ld, m, k, ws, [](int) { return 0; }, [&](int) { return k; },
+               [&](int t, T acc) { vf[k + t] = csub(vs[k + t], acc); });
+      for (int s = tid; s < k; s += kThreads) vf[s] = ws[s];
+    } else if (SWEEP == 1) {                       // z = y - U12 x_m;  x_k = X_U z
+      rows_dot(F + k, ld, k, m, vs + k, [](int) { return 0; }, [&](int) { return m; },
+               [&](int i, T acc) { ws[i] = csub(vs[i], acc); });
+      __syncthreads();
+      rows_dot(X, ldk, k, k, ws, [](int i) { return i; }, [&](int) { return k; },
+               [&](int i, T acc) { xo[idx[i]] = acc; });
+    } else if (SWEEP == 2) {                       // w = X_U^T v_k;  u = v_m - U12^T w
+      cols_dot(X, ldk, k, k, vs, [](int) { return 0; }, [](int j) { return j + 1; },
+               [&](int j, T acc) { ws[j] = acc; }, red);
+      __syncthreads();
+      cols_dot(F + k, ld, m, k, ws, [](int) { return 0; }, [&](int) { return k; },
+               [&](int t, T acc) { vf[k + t] = csub(vs[k + t], acc); }, red);
+      for (int s = tid; s < k; s += kThreads) vf[s] = ws[s];
+    } else {                                       // t = w - L21^T x_m;  x_k = P^T X_L^T t   (vs[k..n) = -x_m)
+      cols_dot(F + (size_t)k * ld, ld, k, m, vs + k, [](int) { return 0; }, [&](int) { return m; },
+               [&](int j, T acc) { ws[j] = cadd(vs[j], acc); }, red);
+      __syncthreads();
+      cols_dot(X, ldk, k, k, ws, [](int j) { return j + 1; }, [&](int) { return k; },
+               [&](int j, T acc) { xo[idx[Pm[j]]] = cadd(ws[j], acc); }, red);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Dataflow sweep: one persistent launch runs every task of one direction.
 // CTAs take tasks from a queue in dependency order (bottom-up levels for
 // L / U^T, top-down for U / L^T; inside a level, the phase-1 tasks of a large
@@ -374,9 +598,16 @@ __device__ __forceinline__ bool wait_ge(const int* p, int need, int* err) {
 }
 
 constexpr int kWarpSlice = 128;   // vector entries per warp for a whole small front (n + k, n <= 64)
+constexpr int kCtaWholeMaxN = 320;   // largest front swept whole by one CTA
+
+// resident CTAs per SM the register allocation aims for (more CTAs run more
+// tasks at once; fewer leave more registers for loads in flight)
+#ifndef FDFD_FLOW_MIN_BLOCKS
+#define FDFD_FLOW_MIN_BLOCKS 4
+#endif
 
 template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, FDFD_FLOW_MIN_BLOCKS)
 flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[kWarps][32];
@@ -435,12 +666,22 @@ flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict_
     // one task of a large front for the whole CTA
     const int2 task = q.tasks[unit.x];
     const unsigned code = (unsigned)task.x;
-    const bool rect = ((code >> 30) & 1u) != 0;
+    const bool med = (code >> 31) != 0;          // a whole medium front
+    const bool rect = !med && ((code >> 30) & 1u) != 0;
     const int f = (int)(code & 0x3fffffffu);
     const FrontDesc d = a.P.fronts[f];
     if (tid == 0) {
       bool ok = true;
-      if (kUp) {
+      if (med) {
+        if (kUp) {
+          for (int ci = 0; ci < d.nchild && ok; ++ci) {
+            const int c = a.P.children[d.child0 + ci];
+            ok = wait_ge(dn + c, q.need_all[c], q.err);
+          }
+        } else if (d.parent >= 0) {
+          ok = wait_ge(dn + d.parent, q.need_all[d.parent], q.err);
+        }
+      } else if (kUp) {
         if (rect) {
           ok = wait_ge(ph1 + (size_t)wl * nf + f, q.need_ph1[f], q.err);
         } else {
@@ -457,13 +698,14 @@ flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict_
     }
     __syncthreads();
     if (!s_ok) break;
-    if (rect) rect_task<T, SWEEP>(a, d, task.y, w, out, vs, red);
+    if (med) medium_front<T, SWEEP>(a, d, w, in, out, vs, red);
+    else if (rect) rect_task<T, SWEEP>(a, d, task.y, w, out, vs, red);
     else tri_task<T, SWEEP>(a, d, task.y, w, in, out, vs, red);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
       // phase 1: inverse-block tasks bottom-up, off-diagonal tasks top-down
-      if (kUp ? !rect : rect) atomicAdd(ph1 + (size_t)wl * nf + f, 1);
+      if (!med && (kUp ? !rect : rect)) atomicAdd(ph1 + (size_t)wl * nf + f, 1);
       atomicAdd(done + (size_t)wl * nf + f, 1);
     }
   }
@@ -514,6 +756,7 @@ int flow_blocks_per_sm(int elem_bytes, int vmax) {
 int sweep_row_block() { return kRowBlk; }
 
 int flow_whole_max_n() { return kWarpSlice / 2; }
+int flow_cta_max_n() { return kCtaWholeMaxN; }
 int sweep_col_block() { return kColBlk; }
 
 cudaError_t solve_init_attributes() {
