@@ -648,6 +648,17 @@ __device__ __forceinline__ double2 fast_crcp(double2 z) {
   return make_double2(z.x * s, -z.y * s);
 }
 
+// 1 / z for a pivot: conj(z) / |z|^2 with the hardware reciprocal estimate of
+// |z|^2 refined by one Newton-Raphson step (double: the correctly rounded one)
+__device__ __forceinline__ float2 pivot_rcp(float2 z) {
+  const float dd = z.x * z.x + z.y * z.y;
+  float s0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s0) : "f"(dd));
+  const float sc = fmaf(s0, fmaf(-dd, s0, 1.0f), s0);
+  return make_float2(z.x * sc, -z.y * sc);
+}
+__device__ __forceinline__ double2 pivot_rcp(double2 z) { return fast_crcp(z); }
+
 // LU of the nb x nb block at (j0, j0) with row pivoting inside the block, by
 // warps 0-3 (lane = row; warp w holds columns 8w..8w+7 in registers).  No rows
 // are swapped: at step p the warp owning column p picks the unused lane r with
@@ -682,11 +693,12 @@ __device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __re
       for (int c = 1; c < 8; ++c)
         if (c == cp) ap = a[c];
       const float v = (float)cabs2(ap);
+      const T myinv = pivot_rcp(ap);    // every lane's candidate, formed beside the redux
       unsigned key = used ? 0u : ((__float_as_uint(v) & ~31u) | (unsigned)(31 - lane));
       if (!used && !(v == v)) key = 0xffffffe0u | (unsigned)(31 - lane);   // NaN wins
       const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
       const int r = 31 - (int)(kmax & 31u);
-      const T inv = fast_crcp(shfl_c(ap, r));
+      const T inv = shfl_c(myinv, r);
       const bool elim = !used && lane != r;
       const T l = elim ? cmul(ap, inv) : czero<T>();
       s_l[buf][lane] = l;
