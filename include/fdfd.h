@@ -245,9 +245,8 @@ void fdfd_destroy(fdfd_ctx* ctx);
  * caller-owned); x may not alias b.  All temporary storage lives in one fixed
  * device array of fdfd_noalloc_scratch_bytes() bytes (32 MiB) that every GPU
  * loading this library holds until the process exits; a solve whose front
- * vectors, precision-conversion buffers and sweep counters (4 bytes per front
- * and wavelength, twice) do not fit is rejected with FDFD_ERR_ARG before any
- * device work.  The first call on a device looks up
+ * vectors and sweep counters (4 bytes per front and wavelength, twice) do not
+ * fit is rejected with FDFD_ERR_ARG before any device work.  The first call on a device looks up
  * the array's device address (with that device current); make that first call
  * before any stream capture.  Every call shares the array and leaves its last
  * contents there (nothing in it needs to start at zero); calls that overlap on

@@ -124,8 +124,6 @@ struct fdfd_ctx {
   // solve workspace
   int ws_nrhs = 0;
   void* d_vb = nullptr;            // front vectors, sized for double2
-  void* d_bT = nullptr;            // rhs / solution in factor precision
-  void* d_xT = nullptr;
   // FGMRES workspace
   int gm_nrhs = 0, gm_m = 0;
   double2 *d_V = nullptr, *d_Z = nullptr, *d_r = nullptr, *d_w = nullptr;
@@ -134,6 +132,7 @@ struct fdfd_ctx {
   double2* d_partial = nullptr;
   double *d_vscale = nullptr, *d_resid = nullptr, *d_bnorm = nullptr;
   int *d_active = nullptr, *d_nj = nullptr;
+  int* d_gcnt = nullptr;           // per-system counters of the Arnoldi passes (zero between launches)
   int* h_active = nullptr;          // pinned
   double* h_resid = nullptr;        // pinned
 
@@ -179,11 +178,11 @@ void free_ptr(void* p) {
 
 enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_STEP, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
                 PK_SWEEP_L, PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY,
-                PK_CVT, PK_OTHER, PK_COUNT };
+                PK_ARNOLDI, PK_OTHER, PK_COUNT };
 const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_step", "lu_panel", "lu_trsm", "lu_gemm",
                                           "lu_schur", "lu_inv",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
-                                          "gmres_dot", "gmres_axpy", "precision_cvt", "other"};
+                                          "gmres_dot", "gmres_axpy", "gmres_arnoldi", "other"};
 
 size_t prof_event(fdfd_ctx* c) {
   if (c->ev_used == c->ev_pool.size()) {
@@ -241,8 +240,8 @@ void drop_graphs(fdfd_ctx* c) {
 
 void free_ws(fdfd_ctx* c) {
   drop_graphs(c);
-  free_ptr(c->d_vb); free_ptr(c->d_bT); free_ptr(c->d_xT); free_ptr(c->d_flow_ctr);
-  c->d_vb = c->d_bT = c->d_xT = nullptr;
+  free_ptr(c->d_vb); free_ptr(c->d_flow_ctr);
+  c->d_vb = nullptr;
   c->d_flow_ctr = nullptr;
   c->ws_nrhs = 0;
 }
@@ -250,12 +249,12 @@ void free_ws(fdfd_ctx* c) {
 void free_gm(fdfd_ctx* c) {
   void* ps[] = {c->d_V, c->d_Z, c->d_r, c->d_w, c->d_h, c->d_h2, c->d_hn, c->d_bd, c->d_H, c->d_cs,
                 c->d_sn, c->d_g, c->d_ycoef, c->d_partial, c->d_vscale, c->d_resid, c->d_bnorm,
-                c->d_active, c->d_nj};
+                c->d_active, c->d_nj, c->d_gcnt};
   for (void* p : ps) free_ptr(p);
   c->d_V = c->d_Z = c->d_r = c->d_w = c->d_h = c->d_h2 = c->d_hn = c->d_bd = nullptr;
   c->d_H = c->d_cs = c->d_sn = c->d_g = c->d_ycoef = c->d_partial = nullptr;
   c->d_vscale = c->d_resid = c->d_bnorm = nullptr;
-  c->d_active = c->d_nj = nullptr;
+  c->d_active = c->d_nj = c->d_gcnt = nullptr;
   c->gm_nrhs = c->gm_m = 0;
 }
 
@@ -680,8 +679,6 @@ fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
   free_ws(ctx);
   const size_t S = (size_t)ctx->n_omega * nrhs;
   CK(dalloc(&ctx->d_vb, sizeof(double2) * S * (size_t)ctx->plan.vec_total));
-  CK(dalloc(&ctx->d_bT, sizeof(double2) * S * (size_t)n_cells(ctx)));
-  CK(dalloc(&ctx->d_xT, sizeof(double2) * S * (size_t)n_cells(ctx)));
   CK(dalloc(&ctx->d_flow_ctr, sizeof(int) * (1 + 2 * (size_t)ctx->n_omega * ctx->plan.fronts.size())));
   int nsm = 0;
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -862,25 +859,10 @@ fdfd_status factor_all(fdfd_ctx* ctx, bool design_only) {
 
 // Applies the cached factors M^-1 to FP64 vectors: dst = M^-1 src (all systems).
 fdfd_status precond(fdfd_ctx* ctx, int nrhs, int transpose, const double2* src, double2* dst) {
-  const long long N = n_cells(ctx);
-  const int S = ctx->n_omega * nrhs;
   ctx->sweeps += 1;
-  if (ctx->valid64) {
-    return sweeps<double2>(ctx, nrhs, transpose, src, dst);
-  }
-  {
-    Prof pr(ctx, PK_CVT, 0, 24.0 * N * S);
-    launch_cvt_from64<float2>(reinterpret_cast<float2*>(ctx->d_bT), src, nullptr, N, S, ctx->stream);
-  }
-  // the sweep pair always runs on the internal buffers, so one graph per (nrhs, transpose)
-  CKS(run_graph(ctx, 16 + 2 * nrhs + (transpose ? 1 : 0),
-                [&]() { return sweeps<float2>(ctx, nrhs, transpose, ctx->d_bT, ctx->d_xT); }));
-  {
-    Prof pr(ctx, PK_CVT, 0, 24.0 * N * S);
-    launch_cvt_to64<float2>(dst, reinterpret_cast<const float2*>(ctx->d_xT), nullptr, N, S, ctx->stream);
-  }
-  CK(cudaGetLastError());
-  return FDFD_OK;
+  if (ctx->valid64) return sweeps<double2>(ctx, nrhs, transpose, src, dst);
+  // complex64 factors: the sweeps read src and write dst in complex128 themselves
+  return sweeps<float2>(ctx, nrhs, transpose, src, dst);
 }
 
 fdfd_status ensure_gm(fdfd_ctx* ctx, int nrhs, int m) {
@@ -903,12 +885,14 @@ fdfd_status ensure_gm(fdfd_ctx* ctx, int nrhs, int m) {
   CK(dalloc(&ctx->d_sn, sizeof(double2) * S * m));
   CK(dalloc(&ctx->d_g, sizeof(double2) * S * (m + 1)));
   CK(dalloc(&ctx->d_ycoef, sizeof(double2) * S * D));
-  CK(dalloc(&ctx->d_partial, sizeof(double2) * S * D * nblk));
+  CK(dalloc(&ctx->d_partial, sizeof(double2) * S * D * std::max(nblk, arnoldi_blocks((long long)N))));
   CK(dalloc(&ctx->d_vscale, sizeof(double) * S));
   CK(dalloc(&ctx->d_resid, sizeof(double) * S));
   CK(dalloc(&ctx->d_bnorm, sizeof(double) * S));
   CK(dalloc(&ctx->d_active, sizeof(int) * S));
   CK(dalloc(&ctx->d_nj, sizeof(int) * S));
+  CK(dalloc(&ctx->d_gcnt, sizeof(int) * S));
+  CK(cudaMemsetAsync(ctx->d_gcnt, 0, sizeof(int) * S, ctx->stream));
   if (!ctx->h_active) {
     CK(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4096));
     CK(cudaMallocHost((void**)&ctx->h_resid, sizeof(double) * 4096));
@@ -917,13 +901,6 @@ fdfd_status ensure_gm(fdfd_ctx* ctx, int nrhs, int m) {
   ctx->gm_m = m;
   return FDFD_OK;
 }
-
-namespace kadd {
-__global__ void add_kernel(double2* a, const double2* b, int n) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) { a[t].x += b[t].x; a[t].y += b[t].y; }
-}
-}  // namespace kadd
 
 // A dataflow sweep whose wait gave up leaves its error word set; report it once
 // (the pinned copy is refreshed at every synchronisation point) and clear it.
@@ -997,34 +974,30 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
       double2* Vj = ctx->d_V + (size_t)j * vs;
       double2* Zj = ctx->d_Z + (size_t)j * vs;
       CKS(precond(ctx, nrhs, transpose, Vj, Zj));
-      {
-        Prof pr(ctx, PK_STENCIL, 48.0 * N * S, 40.0 * N * S);
-        launch_stencil(C, ctx->n_omega, nrhs, transpose, Zj, nullptr, ctx->d_w, 0, s);
-      }
-      // classical Gram-Schmidt, applied twice
-      const double dotb = 16.0 * (j + 2) * N * S, dotf = 8.0 * (j + 1) * N * S;
-      const double axb = 16.0 * (j + 3) * N * S;
-      { Prof pr(ctx, PK_DOT, dotf, dotb);
-        launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h, D, s); }
-      { Prof pr(ctx, PK_AXPY, dotf, axb);
-        launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h, D, ctx->d_w, N, S, ctx->d_active, s); }
-      { Prof pr(ctx, PK_DOT, dotf, dotb);
-        launch_multidot(ctx->d_V, (long long)vs, j + 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_h2, D, s); }
-      { Prof pr(ctx, PK_AXPY, dotf, axb);
-        launch_multiaxpy(ctx->d_V, (long long)vs, j + 1, ctx->d_h2, D, ctx->d_w, N, S, ctx->d_active, s); }
-      { Prof pr(ctx, PK_OTHER, 0, 0); kadd::add_kernel<<<(S * D + 127) / 128, 128, 0, s>>>(ctx->d_h, ctx->d_h2, S * D); }
-      { Prof pr(ctx, PK_DOT, 8.0 * N * S, 16.0 * N * S);
-        launch_multidot(ctx->d_w, 0, 1, ctx->d_w, N, S, ctx->d_partial, nblk, ctx->d_hn, D, s); }
-      { Prof pr(ctx, PK_OTHER, 0, 0); gm_count(ctx->d_active, ctx->d_nj, S, s); }
-      { Prof pr(ctx, PK_OTHER, 0, 0);
-      gm_givens(ctx->d_h, D, ctx->d_hn, D, S, j, m, tol, ctx->d_H, ctx->d_cs, ctx->d_sn, ctx->d_g,
-                ctx->d_vscale, ctx->d_active, ctx->d_resid, ctx->d_bnorm, s); }
+      // w = A z_j, classical Gram-Schmidt applied twice, |w|, Givens update: three passes
+      ArnoldiStep as;
+      as.C = C; as.nrhs = nrhs; as.transpose = transpose;
+      as.z = Zj; as.V = ctx->d_V; as.vstride = (long long)vs; as.nv = j + 1; as.w = ctx->d_w;
+      as.partial = ctx->d_partial; as.cnt = ctx->d_gcnt;
+      as.h1 = ctx->d_h; as.h2 = ctx->d_h2; as.hn = ctx->d_hn;
+      as.nj = ctx->d_nj; as.active = ctx->d_active; as.resid = ctx->d_resid; as.bnorm = ctx->d_bnorm;
+      as.vscale = ctx->d_vscale; as.H = ctx->d_H; as.cs = ctx->d_cs; as.sn = ctx->d_sn; as.g = ctx->d_g;
+      as.m = m; as.tol = tol;
+      const double pf = 8.0 * (j + 1) * N * S, pb = 16.0 * (j + 3) * N * S;
+      { Prof pr(ctx, PK_ARNOLDI, 48.0 * N * S + pf, 40.0 * N * S + 16.0 * (j + 1) * N * S);
+        launch_arnoldi(as, S, 0, s); }
+      { Prof pr(ctx, PK_ARNOLDI, 2.0 * pf, pb); launch_arnoldi(as, S, 1, s); }
+      { Prof pr(ctx, PK_ARNOLDI, pf + 4.0 * N * S, pb); launch_arnoldi(as, S, 2, s); }
       CK(cudaGetLastError());
       ++total;
       jdone = j + 1;
-      // The host looks at the convergence flags only once the iteration count
-      // reaches what the previous solve needed; meanwhile the device-side flags
-      // already freeze converged systems (zero search directions, no updates).
+      // The first cycle stops, without asking the host, once it has done as many
+      // iterations as the previous solve needed: the update and the true residual
+      // of the next cycle then decide (one host synchronisation per solve when
+      // the expectation holds; a restart when it does not).  Later cycles look at
+      // the convergence flags after every iteration; meanwhile the device-side
+      // flags already freeze converged systems (zero search directions, no updates).
+      if (cycle == 0 && total == ctx->gm_expect[transpose ? 1 : 0] && total < ctx->opt.ir_max_iter) break;
       if (total >= ctx->gm_expect[transpose ? 1 : 0] || j + 1 == m || total >= ctx->opt.ir_max_iter) {
         CKS(any_active(ctx, S, &any, &res));
         if (!any) break;
@@ -1509,11 +1482,10 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
   const size_t N = (size_t)n_cells(ctx);
   const size_t es = use64 ? sizeof(double2) : sizeof(float2);
   const size_t vb_bytes = align256(S * (size_t)ctx->plan.vec_total * es);
-  const size_t cvt_bytes = use64 ? 0 : 2 * align256(S * N * sizeof(float2));
   const size_t ctr_bytes = align256(sizeof(int) * (1 + 2 * (size_t)ctx->n_omega * ctx->plan.fronts.size()));
-  if (vb_bytes + cvt_bytes + ctr_bytes > kNoAllocScratchBytes)
+  if (vb_bytes + ctr_bytes > kNoAllocScratchBytes)
     return fail(ctx, FDFD_ERR_ARG,
-                "fdfd_solve_raw_noalloc: this solve needs " + std::to_string(vb_bytes + cvt_bytes + ctr_bytes) +
+                "fdfd_solve_raw_noalloc: this solve needs " + std::to_string(vb_bytes + ctr_bytes) +
                     " bytes of scratch; the fixed device array holds " + std::to_string(kNoAllocScratchBytes));
   int dev = -1;
   CK(cudaGetDevice(&dev));
@@ -1539,16 +1511,9 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
       return fail(ctx, FDFD_ERR_PIVOT,
                   "fdfd_solve_raw_noalloc: FP32 factors exceed the growth bound; call fdfd_solve once first");
   }
-  int* ctr = reinterpret_cast<int*>(scratch + vb_bytes + cvt_bytes);
-  if (use64) {
-    CKS(sweeps_in<double2>(ctx, nrhs, transpose, b_dev, x_dev, scratch, ctr));
-  } else {
-    float2* bT = reinterpret_cast<float2*>(scratch + vb_bytes);
-    float2* xT = reinterpret_cast<float2*>(scratch + vb_bytes + cvt_bytes / 2);
-    launch_cvt_from64<float2>(bT, reinterpret_cast<const double2*>(b_dev), nullptr, (long long)N, (int)S, ctx->stream);
-    CKS(sweeps_in<float2>(ctx, nrhs, transpose, bT, xT, scratch, ctr));
-    launch_cvt_to64<float2>(reinterpret_cast<double2*>(x_dev), xT, nullptr, (long long)N, (int)S, ctx->stream);
-  }
+  int* ctr = reinterpret_cast<int*>(scratch + vb_bytes);
+  if (use64) CKS(sweeps_in<double2>(ctx, nrhs, transpose, b_dev, x_dev, scratch, ctr));
+  else CKS(sweeps_in<float2>(ctx, nrhs, transpose, b_dev, x_dev, scratch, ctr));
   if (ctx->h_flow_err) CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
   CK(cudaGetLastError());

@@ -115,6 +115,8 @@ struct FlowQueue {
   int* err;                // set to 1 by a wait that gives up (never cleared by the kernel)
   int n_fronts;
 };
+// in: right-hand sides, out: solutions, both complex128 [systems][n] whatever the
+// factor precision T (converted where the sweeps gather them and store them).
 template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax,
                                              int grid, const void* in, void* out, cudaStream_t s);
 int flow_blocks_per_sm(int elem_bytes, int vmax);
@@ -127,10 +129,6 @@ cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s);
 // y = A x (op = 0) or r = b - A x (op = 1), FP64 matrix-free stencil, all systems.
 void launch_stencil(const DevCoef& c, int n_omega, int nrhs, int transpose, const double2* x,
                     const double2* b, double2* y, int op, cudaStream_t s);
-template <typename T> void launch_cvt_from64(T* dst, const double2* src, const double* scale,
-                                             long long n, int nsys, cudaStream_t s);
-template <typename T> void launch_cvt_to64(double2* dst, const T* src, const double* scale,
-                                           long long n, int nsys, cudaStream_t s);
 // batched dot products h[s][i] = sum conj(V_i[s]) w[s], i < nv (V_i at V + i*vstride)
 void launch_multidot(const double2* V, long long vstride, int nv, const double2* w, long long n,
                      int nsys, double2* partial, int nblk, double2* out, int out_ld, cudaStream_t s);
@@ -139,17 +137,42 @@ void launch_multiaxpy(const double2* V, long long vstride, int nv, const double2
                       double2* w, long long n, int nsys, const int* active, cudaStream_t s);
 int multidot_blocks(long long n);
 int multidot_max_vectors();
+int arnoldi_blocks(long long n);   // chunks of an Arnoldi pass (partial sums per output)
 
 // FGMRES bookkeeping (one thread per system); see vec.cu
 void gm_start(const double2* rr, int rr_ld, const double2* bb, int bb_ld, int nsys, double tol, int m,
               double2* g, double* vscale, int* active, double* resid, double* bnorm, int first, cudaStream_t s);
-void gm_givens(const double2* h, int h_ld, const double2* hn, int hn_ld, int nsys, int j, int m, double tol,
-               double2* H, double2* cs, double2* sn, double2* g, double* vscale, int* active, double* resid,
-               const double* bnorm, cudaStream_t s);
 void gm_solve(const double2* H, const double2* g, int nsys, int m, const int* njs, double2* ny_out,
               cudaStream_t s);
 void gm_scale(double2* dst, const double2* src, const double* scale, long long n, int nsys, cudaStream_t s);
-void gm_count(const int* active, int* nj, int nsys, cudaStream_t s);
+// One FGMRES Arnoldi step (classical Gram-Schmidt twice, then the Givens
+// update) for every active system in three launches, pass = 0, 1, 2:
+//   0: w = A z (A^T if transpose), h1 = V^H w;  1: w -= V h1, h2 = V^H w;
+//   2: w -= V h2, hn = |w|^2, column nv - 1 of H from h1 + h2 and hn, nj += 1.
+// h1, h2, hn: [nsys][multidot_max_vectors()]; partial: [nsys][multidot_max_vectors()]
+// [arnoldi_blocks(n)];
+// cnt: [nsys] zero, left zero.
+struct ArnoldiStep {
+  DevCoef C;
+  int nrhs, transpose;
+  const double2* z;
+  const double2* V;
+  long long vstride;
+  int nv;                  // V_0 .. V_{nv-1}; the step is j = nv - 1
+  double2* w;
+  double2* partial;
+  int* cnt;
+  double2 *h1, *h2, *hn;
+  int* nj;
+  int* active;
+  double* resid;
+  const double* bnorm;
+  double* vscale;
+  double2 *H, *cs, *sn, *g;
+  int m;
+  double tol;
+};
+void launch_arnoldi(const ArnoldiStep& g, int nsys, int pass, cudaStream_t s);
 
 // objective o = g^T x on a monitor column, F = sum weight |o|^2, adjoint source weight conj(o) g
 void launch_objective(const double2* x, long long N, int ny, const int* cols, const double2* gline,

@@ -10,10 +10,12 @@
 //   U   : x_k = X_U (y - U12 x_m)
 //   U^T : w = X_U^T v_k,                   u = v_m - U12^T w
 //   L^T : x_k = P^T X_L^T (w - L21^T x_m)
-// where v gathers the front's entries of the right-hand side plus the update
+// where v gathers the front's entries of the right-hand side (complex128, cast
+// to the factor precision as it is gathered) plus the update
 // vectors u of its children (through the same inverse extend-add maps as the
 // factorisation) and x_m are the already final values of the boundary
-// variables.  Levels run bottom-up for L / U^T and top-down for U / L^T.
+// variables (the solution is stored in complex128 as it is produced).  Levels
+// run bottom-up for L / U^T and top-down for U / L^T.
 //
 // With the inverses every step is a matrix-vector product.  A small front
 // (n <= 64) is one task done by one warp; a large front is cut into tasks of
@@ -131,11 +133,11 @@ __device__ __forceinline__ Kids load_kids(const SolveLaunch& a, const FrontDesc&
 // Right-hand side entry of local slot src (pivot slots only, when rhs is given)
 // plus the children's update vectors at that slot.
 template <typename T>
-__device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& d, const Kids& kids, const T* rhs,
-                                         const T* vbs, int src) {
+__device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& d, const Kids& kids,
+                                         const double2* rhs, const T* vbs, int src) {
   const int t0 = kids.n > 0 ? a.P.inv[kids.inv_off[0] + src] : -1;
   const int t1 = kids.n > 1 ? a.P.inv[kids.inv_off[1] + src] : -1;
-  T v = (rhs && src < d.k) ? rhs[a.P.idx[d.idx_off + src]] : czero<T>();
+  T v = (rhs && src < d.k) ? cfrom<T>(rhs[a.P.idx[d.idx_off + src]]) : czero<T>();
   if (t0 >= 0) v = cadd(v, ldv(vbs + kids.ubase[0] + t0));
   if (t1 >= 0) v = cadd(v, ldv(vbs + kids.ubase[1] + t1));
   return v;
@@ -227,7 +229,7 @@ __device__ __forceinline__ void warp_cols_dot(const T* __restrict__ A, int ld, i
 
 template <typename T, int SWEEP>
 __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const FrontDesc& d, int w,
-                                                 const T* __restrict__ in, T* __restrict__ out, T* vs) {
+                                                 const double2* __restrict__ in, double2* __restrict__ out, T* vs) {
   const int k = d.k, m = d.m, n = d.n, ldk = d.ldk, ld = d.ld;
   const int lane = threadIdx.x & 31;
   const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
@@ -240,14 +242,14 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
-    T* xo = out + sys * a.n;
+    double2* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
-      const T* rhs = in + sys * a.n;
+      const double2* rhs = in + sys * a.n;
       for (int s = lane; s < n; s += 32) vs[s] = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
     } else {
       for (int s = lane; s < k; s += 32) vs[s] = ldv(vf + s);
       for (int t = lane; t < m; t += 32) {
-        const T x = ldv(xo + idx[k + t]);
+        const T x = cfrom<T>(ldv(xo + idx[k + t]));
         vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
       }
     }
@@ -264,7 +266,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
                     [&](int i, T acc) { ws[i] = csub(vs[i], acc); });
       __syncwarp();
       warp_rows_dot(X, ldk, k, ws, [](int i) { return i; }, [&](int) { return k; },
-                    [&](int i, T acc) { xo[idx[i]] = acc; });
+                    [&](int i, T acc) { xo[idx[i]] = cto64(acc); });
     } else if (SWEEP == 2) {                       // w = X_U^T v_k;  u = v_m - U12^T w
       warp_cols_dot(X, ldk, k, vs, [](int) { return 0; }, [](int j) { return j + 1; },
                     [&](int j, T acc) { ws[j] = acc; });
@@ -277,7 +279,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
                     [&](int j, T acc) { ws[j] = cadd(vs[j], acc); });
       __syncwarp();
       warp_cols_dot(X, ldk, k, ws, [](int j) { return j + 1; }, [&](int) { return k; },
-                    [&](int j, T acc) { xo[idx[Pm[j]]] = cadd(ws[j], acc); });
+                    [&](int j, T acc) { xo[idx[Pm[j]]] = cto64(cadd(ws[j], acc)); });
     }
     __syncwarp();
   }
@@ -286,7 +288,8 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
 // One inverse-block task of a large front (rows or columns from b0).
 template <typename T, int SWEEP>
 __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& d, int b0, int w,
-                                         const T* __restrict__ in, T* __restrict__ out, T* vs, T (*red)[32]) {
+                                         const double2* __restrict__ in, double2* __restrict__ out, T* vs,
+                                         T (*red)[32]) {
   const int k = d.k, ldk = d.ldk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
@@ -298,7 +301,7 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
     if (SWEEP == 0 || SWEEP == 2) {
-      const T* rhs = in + sys * a.n;
+      const double2* rhs = in + sys * a.n;
       for (int s = tid; s < k; s += 2 * kThreads) {
         const int s2 = s + kThreads;
         const T g1 = gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s] : s);
@@ -318,12 +321,12 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
         if (lane == 0) vf[row] = cadd(vs[row], acc);
       }
     } else if (SWEEP == 1) {
-      T* xo = out + sys * a.n;
+      double2* xo = out + sys * a.n;
       for (int rr = warp; rr < kRowBlk; rr += kWarps) {
         const int row = b0 + rr;
         if (row >= k) break;
         const T acc = warp_dot(X + (size_t)row * ldk, vs, row, k, lane);
-        if (lane == 0) xo[idx[row]] = acc;
+        if (lane == 0) xo[idx[row]] = cto64(acc);
       }
     } else if (SWEEP == 2) {
       const int c = b0 + lane;
@@ -331,9 +334,9 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
       if (warp == 0 && c < k) vf[c] = s;
     } else {
       const int c = b0 + lane;
-      T* xo = out + sys * a.n;
+      double2* xo = out + sys * a.n;
       const T s = col_dot(X + c, ldk, vs, b0 + 1, k, c < k, [&](int b) { return b > c; }, red);
-      if (warp == 0 && c < k) xo[idx[Pm[c]]] = cadd(vs[c], s);
+      if (warp == 0 && c < k) xo[idx[Pm[c]]] = cto64(cadd(vs[c], s));
     }
     __syncthreads();
   }
@@ -349,7 +352,7 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
 // One off-diagonal task of a large front (rows or columns from s0).
 template <typename T, int SWEEP>
 __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc& d, int s0, int w,
-                                          T* __restrict__ out, T* vs, T (*red)[32]) {
+                                          double2* __restrict__ out, T* vs, T (*red)[32]) {
   const int k = d.k, m = d.m, ld = d.ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
@@ -359,11 +362,11 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
-    const T* xo = out + sys * a.n;
+    const double2* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
       for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
     } else {
-      for (int t = tid; t < m; t += kThreads) vs[t] = ldv(xo + idx[k + t]);
+      for (int t = tid; t < m; t += kThreads) vs[t] = cfrom<T>(ldv(xo + idx[k + t]));
     }
     __syncthreads();
     if (SWEEP == 0 || SWEEP == 1) {
@@ -372,7 +375,7 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
         if (row >= (SWEEP == 0 ? m : k)) break;
         const T* Frow = SWEEP == 0 ? F + (size_t)(k + row) * ld : F + (size_t)row * ld + k;
         // the value the product is subtracted from, fetched before the product
-        const T g = SWEEP == 0 ? gather_slot(a, d, kids, (const T*)nullptr, vbs, k + row) : ldv(vf + row);
+        const T g = SWEEP == 0 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + row) : ldv(vf + row);
         const T acc = warp_dot(Frow, vs, 0, SWEEP == 0 ? k : m, lane);
         if (lane == 0) vf[SWEEP == 0 ? k + row : row] = csub(g, acc);
       }
@@ -383,7 +386,7 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
       const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
       // the value the product is subtracted from, fetched before the product
       T g = czero<T>();
-      if (warp == 0 && c < cols) g = SWEEP == 2 ? gather_slot(a, d, kids, (const T*)nullptr, vbs, k + c) : ldv(vf + c);
+      if (warp == 0 && c < cols) g = SWEEP == 2 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + c) : ldv(vf + c);
       const T s = col_dot(base, ld, vs, 0, rows, c < cols, [](int) { return true; }, red);
       if (warp == 0 && c < cols) vf[SWEEP == 2 ? k + c : c] = csub(g, s);
     }
@@ -501,7 +504,8 @@ __device__ __forceinline__ void cols_dot(const T* __restrict__ A, int ld, int nc
 
 template <typename T, int SWEEP>
 __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDesc& d, int w,
-                                             const T* __restrict__ in, T* __restrict__ out, T* vs, T (*red)[32]) {
+                                             const double2* __restrict__ in, double2* __restrict__ out, T* vs,
+                                             T (*red)[32]) {
   const int k = d.k, m = d.m, n = d.n, ldk = d.ldk, ld = d.ld;
   const int tid = threadIdx.x;
   const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
@@ -514,9 +518,9 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
     const size_t sys = (size_t)w * a.nrhs + r;
     T* vbs = reinterpret_cast<T*>(a.vb) + sys * a.vec_stride;
     T* vf = vbs + d.v_off;
-    T* xo = out + sys * a.n;
+    double2* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
-      const T* rhs = in + sys * a.n;
+      const double2* rhs = in + sys * a.n;
       for (int s = tid; s < n; s += 2 * kThreads) {
         const int s2 = s + kThreads;
         const T g1 = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
@@ -527,7 +531,7 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
     } else {
       for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
       for (int t = tid; t < m; t += kThreads) {
-        const T x = ldv(xo + idx[k + t]);
+        const T x = cfrom<T>(ldv(xo + idx[k + t]));
         vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
       }
     }
@@ -544,7 +548,7 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
                [&](int i, T acc) { ws[i] = csub(vs[i], acc); });
       __syncthreads();
       rows_dot(X, ldk, k, k, ws, [](int i) { return i; }, [&](int) { return k; },
-               [&](int i, T acc) { xo[idx[i]] = acc; });
+               [&](int i, T acc) { xo[idx[i]] = cto64(acc); });
     } else if (SWEEP == 2) {                       // w = X_U^T v_k;  u = v_m - U12^T w
       cols_dot(X, ldk, k, k, vs, [](int) { return 0; }, [](int j) { return j + 1; },
                [&](int j, T acc) { ws[j] = acc; }, red);
@@ -557,7 +561,7 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
                [&](int j, T acc) { ws[j] = cadd(vs[j], acc); }, red);
       __syncthreads();
       cols_dot(X, ldk, k, k, ws, [](int j) { return j + 1; }, [&](int) { return k; },
-               [&](int j, T acc) { xo[idx[Pm[j]]] = cadd(ws[j], acc); }, red);
+               [&](int j, T acc) { xo[idx[Pm[j]]] = cto64(cadd(ws[j], acc)); }, red);
     }
     __syncthreads();
   }
@@ -608,7 +612,7 @@ constexpr int kCtaWholeMaxN = 320;   // largest front swept whole by one CTA
 
 template <typename T, int SWEEP>
 __global__ void __launch_bounds__(kThreads, FDFD_FLOW_MIN_BLOCKS)
-flow_kernel(SolveLaunch a, FlowQueue q, const T* __restrict__ in, T* __restrict__ out) {
+flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[kWarps][32];
   __shared__ int s_unit, s_ok, s_fail;
@@ -734,8 +738,8 @@ void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int 
                        void* out, cudaStream_t s) {
   if (q.nunits <= 0) return;
   const size_t smem = flow_smem(vmax, sizeof(T));
-  const T* i = reinterpret_cast<const T*>(in);
-  T* o = reinterpret_cast<T*>(out);
+  const double2* i = reinterpret_cast<const double2*>(in);
+  double2* o = reinterpret_cast<double2*>(out);
   switch (sweep) {
     case 0: flow_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
     case 1: flow_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, q, i, o); break;

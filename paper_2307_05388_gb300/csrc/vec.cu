@@ -58,16 +58,11 @@ __global__ void scatter_design_kernel(double* eps, const double* ed, int ny, int
   eps[(size_t)(x0 + i) * ny + y0 + j] = ed[t];
 }
 
-// y = A x (op 0) or y = b - A x (op 1); transpose selects A^T.
-__global__ void stencil_kernel(DevCoef c, int nrhs, int transpose, const double2* __restrict__ x,
-                               const double2* __restrict__ b, double2* __restrict__ y, int op) {
-  const int sys = blockIdx.y;
-  const int w = sys / nrhs;
-  const long long N = (long long)c.nx * c.ny;
-  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= N) return;
-  const int i = (int)(cell / c.ny), j = (int)(cell - (long long)i * c.ny);
-  const double2* X = x + (size_t)sys * N;
+// (A X)[cell] (transpose: A^T) for wavelength w, X one system's vector
+__device__ __forceinline__ double2 stencil_at(const DevCoef& c, int w, int transpose, const double2* __restrict__ X,
+                                              long long cell) {
+  const int ci = (int)cell;                    // grids stay below 2^31 cells
+  const int i = ci / c.ny, j = ci - i * c.ny;
   const double2* cxm = c.cxm + (size_t)w * c.nx;
   const double2* cxp = c.cxp + (size_t)w * c.nx;
   const double2* cym = c.cym + (size_t)w * c.ny;
@@ -87,31 +82,22 @@ __global__ void stencil_kernel(DevCoef c, int nrhs, int transpose, const double2
     if (j > 0) acc = cfma(cyp[j - 1], X[cell - 1], acc);
     if (j + 1 < c.ny) acc = cfma(cym[j + 1], X[cell + 1], acc);
   }
+  return acc;
+}
+
+// y = A x (op 0) or y = b - A x (op 1); transpose selects A^T.
+__global__ void stencil_kernel(DevCoef c, int nrhs, int transpose, const double2* __restrict__ x,
+                               const double2* __restrict__ b, double2* __restrict__ y, int op) {
+  const int sys = blockIdx.y;
+  const long long N = (long long)c.nx * c.ny;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  double2 acc = stencil_at(c, sys / nrhs, transpose, x + (size_t)sys * N, cell);
   if (op == 1) {
     const double2 bb = b[(size_t)sys * N + cell];
     acc = make_double2(bb.x - acc.x, bb.y - acc.y);
   }
   y[(size_t)sys * N + cell] = acc;
-}
-
-template <typename T>
-__global__ void cvt_from64_kernel(T* dst, const double2* src, const double* scale, long long n) {
-  const int sys = blockIdx.y;
-  const double sc = scale ? scale[sys] : 1.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const double2 v = src[(size_t)sys * n + t];
-    dst[(size_t)sys * n + t] = cfrom<T>(make_double2(v.x * sc, v.y * sc));
-  }
-}
-
-template <typename T>
-__global__ void cvt_to64_kernel(double2* dst, const T* src, const double* scale, long long n) {
-  const int sys = blockIdx.y;
-  const double sc = scale ? scale[sys] : 1.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const double2 v = cto64(src[(size_t)sys * n + t]);
-    dst[(size_t)sys * n + t] = make_double2(v.x * sc, v.y * sc);
-  }
 }
 
 constexpr int kDotThreads = 256;
@@ -122,6 +108,8 @@ constexpr int kMaxDot = 17;
 // thread (low register use keeps the FP64 pipes fed by many warps), CTA
 // reduction in a fixed order.
 constexpr int kDotPer = 4;
+constexpr int kArnPer = 2;   // entries per thread of an Arnoldi pass: FP64 FMA is 2 per SM per clock, so
+                             // the CTAs cover every SM while the FP64 adds of the reductions stay few
 
 __global__ void __launch_bounds__(kDotThreads)
 multidot_partial_kernel(const double2* __restrict__ V, long long vstride, int nv,
@@ -217,18 +205,6 @@ void launch_stencil(const DevCoef& c, int n_omega, int nrhs, int transpose, cons
   stencil_kernel<<<dim3((unsigned)((N + 255) / 256), n_omega * nrhs), 256, 0, s>>>(c, nrhs, transpose, x, b, y, op);
 }
 
-template <typename T>
-void launch_cvt_from64(T* dst, const double2* src, const double* scale, long long n, int nsys, cudaStream_t s) {
-  cvt_from64_kernel<T><<<dim3(grid_for(n), nsys), 256, 0, s>>>(dst, src, scale, n);
-}
-template <typename T>
-void launch_cvt_to64(double2* dst, const T* src, const double* scale, long long n, int nsys, cudaStream_t s) {
-  cvt_to64_kernel<T><<<dim3(grid_for(n), nsys), 256, 0, s>>>(dst, src, scale, n);
-}
-template void launch_cvt_from64<float2>(float2*, const double2*, const double*, long long, int, cudaStream_t);
-template void launch_cvt_from64<double2>(double2*, const double2*, const double*, long long, int, cudaStream_t);
-template void launch_cvt_to64<float2>(double2*, const float2*, const double*, long long, int, cudaStream_t);
-template void launch_cvt_to64<double2>(double2*, const double2*, const double*, long long, int, cudaStream_t);
 
 // chunks of kDotPer entries per thread
 int multidot_blocks(long long n) {
@@ -237,6 +213,7 @@ int multidot_blocks(long long n) {
   return (int)b;
 }
 int multidot_max_vectors() { return kMaxDot; }
+int arnoldi_blocks(long long n) { return (int)((n + kDotThreads * kArnPer - 1) / (kDotThreads * kArnPer)); }
 
 void launch_multidot(const double2* V, long long vstride, int nv, const double2* w, long long n, int nsys,
                      double2* partial, int nblk, double2* out, int out_ld, cudaStream_t s) {
@@ -270,15 +247,15 @@ __global__ void gm_start_kernel(const double2* rr, int rr_ld, const double2* bb,
   vscale[s] = act ? 1.0 / beta : 0.0;
 }
 
-// h: [nsys][ld] with h[0..j] the projections and hn2 = |w|^2 in hn[s*ld2].x
-__global__ void gm_givens_kernel(const double2* h, int h_ld, const double2* hn, int hn_ld, int nsys, int j,
-                                 int m, double tol, double2* H, double2* cs, double2* sn, double2* g,
-                                 double* vscale, int* active, double* resid, const double* bnorm) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nsys || !active[s]) return;
+// Column j of the Hessenberg matrix of system s from its projections h[0..j]
+// and hn2 = |w|^2: earlier rotations applied, a new one formed, the residual
+// estimate updated; a system whose estimate meets tol (or breaks down: exact
+// solution) becomes inactive.
+__device__ void givens_step(int s, const double2* hs, double hn2, int j, int m, double tol, double2* H, double2* cs,
+                            double2* sn, double2* g, double* vscale, int* active, double* resid, const double* bnorm) {
   double2* Hc = H + ((size_t)s * m + j) * (m + 1);   // column j of H
-  for (int i = 0; i <= j; ++i) Hc[i] = h[(size_t)s * h_ld + i];
-  const double hnorm = sqrt(fmax(hn[(size_t)s * hn_ld].x, 0.0));
+  for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
+  const double hnorm = sqrt(fmax(hn2, 0.0));
   Hc[j + 1] = make_double2(hnorm, 0);
   double2* C = cs + (size_t)s * m;
   double2* S = sn + (size_t)s * m;
@@ -344,9 +321,101 @@ __global__ void scale_vec_kernel(double2* dst, const double2* src, const double*
   }
 }
 
-__global__ void count_iter_kernel(const int* active, int* nj, int nsys) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < nsys && active[s]) nj[s] += 1;
+
+// One Arnoldi step of FGMRES with classical Gram-Schmidt applied twice, for
+// every active system, in three passes over the vectors (pass p):
+//   0: w = A z_j,             h1_i = V_i^H w
+//   1: w -= sum_i h1_i V_i,   h2_i = V_i^H w
+//   2: w -= sum_i h2_i V_i,   |w|^2, then h = h1 + h2 and the Givens update
+// CTA (chunk of kArnPer * 256 entries, system); each CTA writes its partial
+// sums, and the last CTA of a system (a counter it resets afterwards) adds
+// them in chunk order, so results do not depend on timing.
+__global__ void __launch_bounds__(kDotThreads)
+arnoldi_kernel(ArnoldiStep g, int pass) {
+  __shared__ double2 red[kDotThreads / 32][kMaxDot];
+  __shared__ double2 hc[kMaxDot];
+  __shared__ int s_last;
+  const int sys = blockIdx.y;
+  if (!g.active[sys]) return;
+  const int nv = g.nv, nblk = gridDim.x;
+  const long long n = (long long)g.C.nx * g.C.ny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (pass > 0 && tid < nv) hc[tid] = (pass == 1 ? g.h1 : g.h2)[(size_t)sys * kMaxDot + tid];
+  __syncthreads();
+  double2* W = g.w + (size_t)sys * n;
+  const double2* Vs = g.V + (size_t)sys * n;
+  const long long t0 = (long long)blockIdx.x * (kDotThreads * kArnPer) + tid;
+  double2 wv[kArnPer];
+#pragma unroll
+  for (int u = 0; u < kArnPer; ++u) {
+    const long long t = t0 + (long long)u * kDotThreads;
+    double2 x = make_double2(0, 0);
+    if (t < n) {
+      if (pass == 0) {
+        x = stencil_at(g.C, sys / g.nrhs, g.transpose, g.z + (size_t)sys * n, t);
+      } else {
+        x = W[t];
+        for (int i = 0; i < nv; ++i) x = cfms(hc[i], Vs[(size_t)i * g.vstride + t], x);
+      }
+      W[t] = x;
+    }
+    wv[u] = x;
+  }
+  const int nout = pass < 2 ? nv : 1;
+  for (int i = 0; i < nout; ++i) {
+    double2 acc = make_double2(0, 0);
+    if (pass < 2) {
+#pragma unroll
+      for (int u = 0; u < kArnPer; ++u) {
+        const long long t = t0 + (long long)u * kDotThreads;
+        if (t < n) acc = cfma(cconj(Vs[(size_t)i * g.vstride + t]), wv[u], acc);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < kArnPer; ++u) acc.x += wv[u].x * wv[u].x + wv[u].y * wv[u].y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) red[warp][i] = acc;
+  }
+  __syncthreads();
+  if (tid < nout) {
+    double2 sum = red[0][tid];
+    for (int q = 1; q < kDotThreads / 32; ++q) sum = cadd(sum, red[q][tid]);
+    g.partial[((size_t)sys * kMaxDot + tid) * nblk + blockIdx.x] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&g.cnt[sys], 1) == nblk - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double2* out = pass == 0 ? g.h1 : (pass == 1 ? g.h2 : g.hn);
+  if (warp < nout) {   // warp i adds output i over the chunks: lane-strided, then a shuffle tree
+    const double2* p = g.partial + ((size_t)sys * kMaxDot + warp) * nblk;
+    double2 sum = make_double2(0, 0);
+    for (int b = lane; b < nblk; b += 32) sum = cadd(sum, __ldcg(p + b));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+    }
+    if (lane == 0) out[(size_t)sys * kMaxDot + warp] = sum;
+  }
+  if (tid == 0) g.cnt[sys] = 0;
+  if (pass == 2) {
+    __syncthreads();
+    if (tid == 0) {
+      double2 hs[kMaxDot];
+      for (int i = 0; i < nv; ++i) hs[i] = cadd(g.h1[(size_t)sys * kMaxDot + i], g.h2[(size_t)sys * kMaxDot + i]);
+      g.nj[sys] += 1;
+      givens_step(sys, hs, g.hn[(size_t)sys * kMaxDot].x, nv - 1, g.m, g.tol, g.H, g.cs, g.sn, g.g, g.vscale,
+                  g.active, g.resid, g.bnorm);
+    }
+  }
 }
 
 }  // namespace
@@ -356,12 +425,6 @@ void gm_start(const double2* rr, int rr_ld, const double2* bb, int bb_ld, int ns
   gm_start_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(rr, rr_ld, bb, bb_ld, nsys, tol, m, g, vscale, active, resid,
                                                   bnorm, first);
 }
-void gm_givens(const double2* h, int h_ld, const double2* hn, int hn_ld, int nsys, int j, int m, double tol,
-               double2* H, double2* cs, double2* sn, double2* g, double* vscale, int* active, double* resid,
-               const double* bnorm, cudaStream_t s) {
-  gm_givens_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(h, h_ld, hn, hn_ld, nsys, j, m, tol, H, cs, sn, g, vscale,
-                                                   active, resid, bnorm);
-}
 void gm_solve(const double2* H, const double2* g, int nsys, int m, const int* njs, double2* ny_out,
               cudaStream_t s) {
   gm_solve_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(H, g, nsys, m, njs, ny_out);
@@ -369,8 +432,9 @@ void gm_solve(const double2* H, const double2* g, int nsys, int m, const int* nj
 void gm_scale(double2* dst, const double2* src, const double* scale, long long n, int nsys, cudaStream_t s) {
   scale_vec_kernel<<<dim3(grid_for(n), nsys), 256, 0, s>>>(dst, src, scale, n);
 }
-void gm_count(const int* active, int* nj, int nsys, cudaStream_t s) {
-  count_iter_kernel<<<(nsys + 63) / 64, 64, 0, s>>>(active, nj, nsys);
+void launch_arnoldi(const ArnoldiStep& g, int nsys, int pass, cudaStream_t s) {
+  const long long n = (long long)g.C.nx * g.C.ny;
+  arnoldi_kernel<<<dim3(arnoldi_blocks(n), nsys), kDotThreads, 0, s>>>(g, pass);
 }
 
 // ---------------------------------------------------------------------------
