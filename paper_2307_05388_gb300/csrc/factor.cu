@@ -69,14 +69,34 @@ build_kernel(FactorLaunch a, const int2* __restrict__ tasks) {
     }
   }
   (void)ld0; (void)ld1;
+  // children's rows, gathered through their maps: eight columns per lane in
+  // flight (maps first, then the update-matrix entries they select)
+  constexpr int UN = 8;
+  for (int b0 = lane; b0 < d.n; b0 += 32 * UN) {
+    int i0[UN], i1[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const int b = b0 + 32 * u;
+      i0[u] = (S0 && b < d.n) ? inv0[b] : -1;
+      i1[u] = (S1 && b < d.n) ? inv1[b] : -1;
+    }
+    T v[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      v[u] = czero<T>();
+      if (i0[u] >= 0) v[u] = cadd(v[u], S0[i0[u]]);
+      if (i1[u] >= 0) v[u] = cadd(v[u], S1[i1[u]]);
+    }
+#pragma unroll
+    for (int u = 0; u < UN; ++u)
+      if (b0 + 32 * u < d.n) F[b0 + 32 * u] = v[u];
+  }
+  // the row's original entries (each column at most once), one lane each
+  __syncwarp();
   const int e0 = a.P.orig_ptr[d.orig_off + r], e1 = a.P.orig_ptr[d.orig_off + r + 1];
-  for (int b = lane; b < d.n; b += 32) {
-    T acc = czero<T>();
-    if (S0) { const int ib = inv0[b]; if (ib >= 0) acc = cadd(acc, S0[ib]); }
-    if (S1) { const int ib = inv1[b]; if (ib >= 0) acc = cadd(acc, S1[ib]); }
-    for (int e = e0; e < e1; ++e)
-      if (a.P.orig_col[e] == b) acc = cadd(acc, cfrom<T>(stencil_entry(a.C, w, a.P.orig_code[e])));
-    F[b] = acc;
+  for (int e = e0 + lane; e < e1; e += 32) {
+    const int b = a.P.orig_col[e];
+    F[b] = cadd(F[b], cfrom<T>(stencil_entry(a.C, w, a.P.orig_code[e])));
   }
 }
 
