@@ -18,8 +18,9 @@
 // run bottom-up for L / U^T and top-down for U / L^T.
 //
 // With the inverses every step is a matrix-vector product.  A small front
-// (n <= 64) is one task done by one warp; a large front is cut into tasks of
-// 8 rows (one per warp) or 32 columns (one per lane) of its k x k inverse block
+// (n <= 64) is one task done by one warp, a medium front (n <= 320) one task
+// of a CTA; a large front is cut into tasks of 8 rows (one per warp) or 16
+// columns (two lanes per column in each warp) of its k x k inverse block
 // (phase 1 bottom-up) and of its off-diagonal block (the other phase).  One
 // persistent launch per direction runs every task in elimination-tree order
 // (the dataflow sweep below), so the whole GPU streams the factor with no
@@ -36,7 +37,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRowBlk = kWarps;     // rows per row-type task (one per warp)
-constexpr int kColBlk = 32;         // columns per column-type task (one per lane)
+constexpr int kColBlk = 16;         // columns per column-type task (each column: two lanes per warp)
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -71,35 +72,45 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, i
   return warp_sum(cadd(acc[0], acc[1]));
 }
 
-// Column block product: lane = column, warps split the rows [r0, r1) of a
-// row-major block with stride ld; column c = c0 + lane uses only rows r with
-// lo(c) <= r < hi(c) (triangle masks).  Returns the per-lane column sum,
-// reduced over warps in a fixed order (valid in warp 0).
+// Column block product over kColBlk columns: lane = (column c = lane % kColBlk,
+// row slice lane / kColBlk), the warps' slices split the rows [r0, r1) of a
+// row-major block with stride ld (base points at the lane's column); column c
+// uses only rows r with lo(c) <= r < hi(c) (triangle masks).  Returns the
+// column sum, reduced over the slices and the warps in a fixed order (valid in
+// warp 0, lanes < kColBlk).
 template <typename T, typename Mask>
 __device__ __forceinline__ T col_dot(const T* __restrict__ base, int ld, const T* vec, int r0, int r1,
                                      bool live, Mask inside, T (*red)[32]) {
+  constexpr int SL = 32 / kColBlk;              // row slices per warp
+  constexpr int RS = kWarps * SL;               // row stride of one thread
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int UN = sizeof(T) == 8 ? 16 : 8;
   T a0 = czero<T>(), a1 = czero<T>();
   if (live) {
-    int r = r0 + warp;
-    for (; r + (UN - 1) * kWarps < r1; r += UN * kWarps) {
+    int r = r0 + warp * SL + lane / kColBlk;
+    for (; r + (UN - 1) * RS < r1; r += UN * RS) {
       T f[UN];
 #pragma unroll
-      for (int u = 0; u < UN; ++u) f[u] = base[(size_t)(r + u * kWarps) * ld];
+      for (int u = 0; u < UN; ++u) f[u] = base[(size_t)(r + u * RS) * ld];
 #pragma unroll
       for (int u = 0; u < UN; ++u)
-        if (inside(r + u * kWarps)) {
-          if (u & 1) a1 = cfma(f[u], vec[r + u * kWarps], a1);
-          else a0 = cfma(f[u], vec[r + u * kWarps], a0);
+        if (inside(r + u * RS)) {
+          if (u & 1) a1 = cfma(f[u], vec[r + u * RS], a1);
+          else a0 = cfma(f[u], vec[r + u * RS], a0);
         }
     }
-    for (; r < r1; r += kWarps)
+    for (; r < r1; r += RS)
       if (inside(r)) a0 = cfma(base[(size_t)r * ld], vec[r], a0);
   }
-  red[warp][lane] = cadd(a0, a1);
+  T s = cadd(a0, a1);
+#pragma unroll
+  for (int o = kColBlk; o < 32; o <<= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  red[warp][lane] = s;
   __syncthreads();
-  T s = red[0][lane];
+  s = red[0][lane];
   if (warp == 0)
     for (int q = 1; q < kWarps; ++q) s = cadd(s, red[q][lane]);
   return s;
@@ -329,14 +340,14 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
         if (lane == 0) xo[idx[row]] = cto64(acc);
       }
     } else if (SWEEP == 2) {
-      const int c = b0 + lane;
+      const int c = b0 + (lane & (kColBlk - 1));
       const T s = col_dot(X + c, ldk, vs, 0, min(b0 + kColBlk, k), c < k, [&](int b) { return b <= c; }, red);
-      if (warp == 0 && c < k) vf[c] = s;
+      if (warp == 0 && lane < kColBlk && c < k) vf[c] = s;
     } else {
-      const int c = b0 + lane;
+      const int c = b0 + (lane & (kColBlk - 1));
       double2* xo = out + sys * a.n;
       const T s = col_dot(X + c, ldk, vs, b0 + 1, k, c < k, [&](int b) { return b > c; }, red);
-      if (warp == 0 && c < k) xo[idx[Pm[c]]] = cto64(cadd(vs[c], s));
+      if (warp == 0 && lane < kColBlk && c < k) xo[idx[Pm[c]]] = cto64(cadd(vs[c], s));
     }
     __syncthreads();
   }
@@ -382,13 +393,14 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
     } else {
       const int cols = SWEEP == 2 ? m : k;
       const int rows = SWEEP == 2 ? k : m;
-      const int c = s0 + lane;
+      const int c = s0 + (lane & (kColBlk - 1));
+      const bool mine = warp == 0 && lane < kColBlk && c < cols;
       const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
       // the value the product is subtracted from, fetched before the product
       T g = czero<T>();
-      if (warp == 0 && c < cols) g = SWEEP == 2 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + c) : ldv(vf + c);
+      if (mine) g = SWEEP == 2 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + c) : ldv(vf + c);
       const T s = col_dot(base, ld, vs, 0, rows, c < cols, [](int) { return true; }, red);
-      if (warp == 0 && c < cols) vf[SWEEP == 2 ? k + c : c] = csub(g, s);
+      if (mine) vf[SWEEP == 2 ? k + c : c] = csub(g, s);
     }
     __syncthreads();
   }
