@@ -27,6 +27,14 @@ with target reflection R = 1e-8, PML cells counted inside the grid, e^{+i w t}
 time convention (from the -i omega J right-hand side of Eq. 1), so that
 s = 1 - i sigma / (omega eps0) absorbs outgoing waves.
 
+Design parametrisation before the hot path (Sec. III: a smoothing filter of
+200 nm radius and a sigmoid-like projection binarise the geometry; the paper
+gives neither formula, so the usual forms are read in): a conic density filter
+rho~_i = sum_j w_ij rho_j / sum_j w_ij with w_ij = max(0, R - |x_i - x_j|)
+(distances in cells, sums over the design box), the tanh projection
+rho^ = (tanh(b e) + tanh(b (rho~ - e))) / (tanh(b e) + tanh(b (1 - e))),
+eps = eps_lo + rho^ (eps_hi - eps_lo), and the chain rule back to rho.
+
 Pins (tests/test_oracle.py): dense LAPACK solve on small grids, plane-wave
 dispersion of the Yee stencil, plate-mode propagation constant and PML
 absorption, reciprocity of the symmetrised operator, the bilinear transpose
@@ -211,6 +219,74 @@ def adam_step(rho, grad, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # ---------------------------------------------------------------------------
 # Error metrics used by the parity tests
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Sec. III: smoothing filter and projection of the design density
+# ---------------------------------------------------------------------------
+def filter_offsets(radius: float):
+    """Integer offsets (di, dj) with distance d < radius and their weights radius - d."""
+    r = int(np.ceil(radius))
+    out = []
+    for di in range(-r, r + 1):
+        for dj in range(-r, r + 1):
+            d = float(np.hypot(di, dj))
+            if d < radius:
+                out.append((di, dj, radius - d))
+    return out
+
+
+def _shift_sum(v: np.ndarray, radius: float, weight_in=None):
+    """sum over offsets of weight * v[i + di, j + dj] (entries outside the box count as absent)."""
+    w, h = v.shape
+    acc = np.zeros_like(v, dtype=np.float64)
+    for di, dj, wt in filter_offsets(radius):
+        src = np.zeros_like(v, dtype=np.float64)
+        i0, i1 = max(0, -di), min(w, w - di)
+        j0, j1 = max(0, -dj), min(h, h - dj)
+        if i0 < i1 and j0 < j1:
+            src[i0:i1, j0:j1] = v[i0 + di:i1 + di, j0 + dj:j1 + dj]
+        acc += wt * src
+    return acc
+
+
+def filter_norm(w: int, h: int, radius: float) -> np.ndarray:
+    """N_i = sum of the weights of the pixels of a w x h box around pixel i."""
+    return _shift_sum(np.ones((w, h)), radius)
+
+
+def density_filter(rho: np.ndarray, radius: float) -> np.ndarray:
+    """rho~ = W rho with W_ij = w_ij / N_i (rho: [w, h], x-major like the design box)."""
+    return _shift_sum(rho, radius) / filter_norm(*rho.shape, radius)
+
+
+def density_filter_adjoint(y: np.ndarray, radius: float) -> np.ndarray:
+    """W^T y = sum_i w_ij y_i / N_i (the weights are symmetric in i and j)."""
+    return _shift_sum(y / filter_norm(*y.shape, radius), radius)
+
+
+def projection(rt: np.ndarray, beta: float, eta: float) -> np.ndarray:
+    a = np.tanh(beta * eta)
+    return (a + np.tanh(beta * (rt - eta))) / (a + np.tanh(beta * (1.0 - eta)))
+
+
+def projection_slope(rt: np.ndarray, beta: float, eta: float) -> np.ndarray:
+    a = np.tanh(beta * eta)
+    t = np.tanh(beta * (rt - eta))
+    return beta * (1.0 - t * t) / (a + np.tanh(beta * (1.0 - eta)))
+
+
+def filter_project(rho: np.ndarray, radius: float, beta: float, eta: float, eps_lo: float, eps_hi: float):
+    """eps of the design box from the raw density: filter, project, map to permittivity."""
+    rt = density_filter(rho, radius)
+    return eps_lo + projection(rt, beta, eta) * (eps_hi - eps_lo)
+
+
+def filter_project_grad(rho: np.ndarray, g_eps: np.ndarray, radius: float, beta: float, eta: float,
+                        eps_lo: float, eps_hi: float) -> np.ndarray:
+    """dF/drho from dF/deps by the chain rule through the projection and the filter."""
+    rt = density_filter(rho, radius)
+    return density_filter_adjoint(g_eps * (eps_hi - eps_lo) * projection_slope(rt, beta, eta), radius)
+
+
 def rel_err(x, ref) -> float:
     x = np.asarray(x).ravel()
     ref = np.asarray(ref).ravel()

@@ -183,3 +183,76 @@ def test_c1_oracle_iteration_runs():
     E, Ea = fields[(0, 0)]
     A = O.assemble(wl.nx, wl.ny, wl.eps_full(), wl.k0dx()[0], wl.npml)
     assert O.residual_rel(A, E, wl.source_dense(0)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Sec. III: smoothing filter and projection (the step before the hot path)
+# ---------------------------------------------------------------------------
+def _filter_brute(rho, radius):
+    """rho~ by a double loop over all pixel pairs (independent of the offset form)."""
+    w, h = rho.shape
+    out = np.zeros_like(rho)
+    for i in range(w):
+        for j in range(h):
+            s = n = 0.0
+            for p in range(w):
+                for q in range(h):
+                    wt = max(0.0, radius - float(np.hypot(i - p, j - q)))
+                    s += wt * rho[p, q]
+                    n += wt
+            out[i, j] = s / n
+    return out
+
+
+@pytest.mark.parametrize("w,h,radius", [(9, 7, 2.5), (5, 11, 5.0), (12, 12, 1.2)])
+def test_filter_matches_pair_sum_and_keeps_constants(w, h, radius):
+    """The filter equals the normalised hat-weighted pair sum and leaves a constant density
+    unchanged (catches a missing normalisation, a wrong weight or a boundary slip)."""
+    rho = np.random.default_rng(3).uniform(0, 1, (w, h))
+    assert np.max(np.abs(O.density_filter(rho, radius) - _filter_brute(rho, radius))) < 1e-13
+    assert np.max(np.abs(O.density_filter(np.full((w, h), 0.37), radius) - 0.37)) < 1e-14
+
+
+@pytest.mark.parametrize("w,h,radius", [(9, 7, 2.5), (13, 4, 5.0)])
+def test_filter_adjoint_identity(w, h, radius):
+    """<W x, y> = <x, W^T y> (catches an adjoint without the per-pixel normalisation)."""
+    rng = np.random.default_rng(4)
+    x, y = rng.normal(size=(w, h)), rng.normal(size=(w, h))
+    lhs = np.sum(O.density_filter(x, radius) * y)
+    rhs = np.sum(x * O.density_filter_adjoint(y, radius))
+    assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + 1)
+
+
+def test_projection_closed_forms():
+    """P(0) = 0, P(1) = 1, P(eta) = tanh(b e) / (tanh(b e) + tanh(b (1 - e))), and P(x) -> x as b -> 0."""
+    for beta, eta in [(8.0, 0.5), (32.0, 0.3), (2.0, 0.7)]:
+        assert abs(O.projection(np.array(0.0), beta, eta)) < 1e-15
+        assert abs(O.projection(np.array(1.0), beta, eta) - 1.0) < 1e-15
+        a = np.tanh(beta * eta)
+        assert abs(O.projection(np.array(eta), beta, eta) - a / (a + np.tanh(beta * (1 - eta)))) < 1e-15
+    x = np.linspace(0, 1, 11)
+    assert np.max(np.abs(O.projection(x, 1e-4, 0.5) - x)) < 1e-8
+
+
+def test_projection_slope_central_differences():
+    x = np.linspace(-0.2, 1.2, 29)
+    h = 1e-6
+    for beta, eta in [(8.0, 0.5), (20.0, 0.4)]:
+        fd = (O.projection(x + h, beta, eta) - O.projection(x - h, beta, eta)) / (2 * h)
+        assert np.max(np.abs(fd - O.projection_slope(x, beta, eta))) < 1e-6 * beta
+
+
+def test_filter_project_chain_rule_central_differences():
+    """dF/drho through projection and filter against central differences of F = sum c * eps(rho)."""
+    rng = np.random.default_rng(5)
+    w, h, radius, beta, eta = 10, 8, 3.0, 6.0, 0.5
+    rho = rng.uniform(0, 1, (w, h))
+    c = rng.normal(size=(w, h))
+    F = lambda r: float(np.sum(c * O.filter_project(r, radius, beta, eta, W.EPS_SIO2, W.EPS_SIO2 + W.DELTA_EPS)))
+    g = O.filter_project_grad(rho, c, radius, beta, eta, W.EPS_SIO2, W.EPS_SIO2 + W.DELTA_EPS)
+    step = 1e-6
+    for (i, j) in [(0, 0), (4, 3), (9, 7), (2, 6)]:
+        e = np.zeros_like(rho)
+        e[i, j] = step
+        fd = (F(rho + e) - F(rho - e)) / (2 * step)
+        assert abs(fd - g[i, j]) < 1e-6 * max(1.0, abs(g[i, j]))
