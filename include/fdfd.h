@@ -258,6 +258,29 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
 /* Size in bytes of the fixed scratch array used by fdfd_solve_raw_noalloc. */
 size_t fdfd_noalloc_scratch_bytes(void);
 
+/* Smoothing filter and projection of the design density (Sec. III: a smoothing
+ * filter of 200 nm radius and a sigmoid-like projection binarise the geometry;
+ * the forms used are a conic filter and a tanh projection):
+ *   rho~_i = sum_j w_ij rho_j / N_i,  w_ij = max(0, radius - |p_i - p_j|),  N_i = sum_j w_ij,
+ *   rho^_i = (tanh(beta eta) + tanh(beta (rho~_i - eta))) / (tanh(beta eta) + tanh(beta (1 - eta))),
+ *   eps_i  = eps_lo + rho^_i (eps_hi - eps_lo),
+ * with pixel distances |p_i - p_j| in cells and the sums over the context's
+ * design box (w x h pixels, x-major: pixel (i, j) at i*h + j, the layout of
+ * fdfd_refactor_design).  rho_dev, eps_dev: [w*h] double (device); work_dev:
+ * [2*w*h] double (device, caller-owned), filled with what the adjoint needs
+ * (the slope d eps_i / d rho~_i, then N_i).  FDFD_ERR_ARG unless 0 < radius
+ * <= 25, beta > 0, 0 < eta < 1 and the context has a design box.  Runs on the
+ * context's stream. */
+fdfd_status fdfd_filter_project(fdfd_ctx* ctx, const double* rho_dev, double radius, double beta, double eta,
+                                double eps_lo, double eps_hi, double* eps_dev, double* work_dev);
+
+/* Chain rule of fdfd_filter_project back to the density:
+ *   g_rho_j = sum_i w_ij g_eps_i s_i / N_i
+ * with s_i and N_i from the work_dev of the forward call (same radius).
+ * g_eps_dev, g_rho_dev: [w*h] double (device); g_rho may not alias g_eps. */
+fdfd_status fdfd_filter_project_adjoint(fdfd_ctx* ctx, const double* g_eps_dev, const double* work_dev,
+                                        double radius, double* g_rho_dev);
+
 #ifdef __cplusplus
 }
 #endif

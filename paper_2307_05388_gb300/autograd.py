@@ -1,4 +1,5 @@
-"""torch.autograd.Function over the cached solver (Sec. II, Eq. 3-6).
+"""torch.autograd.Functions over the cached solver (Sec. II, Eq. 3-6) and the
+design parametrisation before it (Sec. III: smoothing filter and projection).
 
 forward(eps_design): design refactor (or a full factorisation on the first
 call), forward solves for all wavelengths and sources, mode-overlap objective
@@ -83,3 +84,26 @@ class FdfdObjective(torch.autograd.Function):
         w = gF.reshape(1).to(torch.float64).expand(nsys).contiguous()
         g = s.grad(x, xa, w)
         return g.reshape(ctx.shape), None
+
+
+class FilterProject(torch.autograd.Function):
+    """Design density -> design-box permittivity through the conic smoothing filter and
+    the tanh projection (Sec. III), with the chain rule back to the density; both
+    directions run in libfdfd's kernels.  Use as eps = FilterProject.apply(rho, solver,
+    radius, beta, eta, eps_lo, eps_hi), then F = problem(eps)."""
+
+    @staticmethod
+    def forward(ctx, rho: torch.Tensor, solver: fdfd.Solver, radius: float, beta: float, eta: float,
+                eps_lo: float, eps_hi: float):
+        eps, work = solver.filter_project(rho.detach(), radius, beta, eta, eps_lo, eps_hi)
+        ctx.solver = solver
+        ctx.radius = radius
+        ctx.shape = rho.shape
+        ctx.save_for_backward(work)
+        return eps.reshape(rho.shape)
+
+    @staticmethod
+    def backward(ctx, g_eps: torch.Tensor):
+        (work,) = ctx.saved_tensors
+        g = ctx.solver.filter_project_adjoint(g_eps.to(torch.float64), work, ctx.radius)
+        return g.reshape(ctx.shape), None, None, None, None, None, None

@@ -95,6 +95,11 @@ struct fdfd_ctx {
   int flow_vmax = 0;               // shared-memory vector entries of the flow kernel
   int* d_flow_ctr = nullptr;       // queue head and per-front counters
   int* d_flow_err = nullptr;       // set by a wait that gave up
+  // taps of the design-density filter (offsets and weights) for radius tap_radius
+  int2* d_taps = nullptr;
+  double* d_tapw = nullptr;
+  int ntap = 0;
+  double tap_radius = 0;
   int* h_flow_err = nullptr;       // pinned copy
   int flow_grid[2] = {0, 0};       // persistent CTAs [precision 0 = c64, 1 = c128]
 
@@ -1280,6 +1285,66 @@ fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_ad
   return FDFD_OK;
 }
 
+// The filter taps for this radius on the device: integer offsets with distance
+// below the radius, row-major over [-r, r]^2, weight radius - distance.
+static fdfd_status ensure_taps(fdfd_ctx* ctx, double radius) {
+  if (ctx->d_taps && ctx->tap_radius == radius) return FDFD_OK;
+  const int r = (int)std::ceil(radius);
+  std::vector<int2> off;
+  std::vector<double> wt;
+  for (int di = -r; di <= r; ++di)
+    for (int dj = -r; dj <= r; ++dj) {
+      const double d = std::hypot((double)di, (double)dj);
+      if (d < radius) {
+        off.push_back(make_int2(di, dj));
+        wt.push_back(radius - d);
+      }
+    }
+  CK(cudaStreamSynchronize(ctx->stream));   // the old taps may still be in use
+  free_ptr(ctx->d_taps);
+  free_ptr(ctx->d_tapw);
+  ctx->d_taps = nullptr;
+  ctx->d_tapw = nullptr;
+  CK(dalloc(&ctx->d_taps, sizeof(int2) * off.size()));
+  CK(dalloc(&ctx->d_tapw, sizeof(double) * wt.size()));
+  CK(cudaMemcpy(ctx->d_taps, off.data(), sizeof(int2) * off.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_tapw, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
+  ctx->ntap = (int)off.size();
+  ctx->tap_radius = radius;
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_filter_project(fdfd_ctx* ctx, const double* rho_dev, double radius, double beta, double eta,
+                                double eps_lo, double eps_hi, double* eps_dev, double* work_dev) {
+  if (!ctx || !rho_dev || !eps_dev || !work_dev || !(radius > 0 && radius <= 25) || !(beta > 0) ||
+      !(eta > 0 && eta < 1))
+    return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->box.w == 0 || ctx->box.h == 0) return fail(ctx, FDFD_ERR_ARG, "context has no design box");
+  CKS(ensure_taps(ctx, radius));
+  const int w = ctx->box.w, h = ctx->box.h;
+  Prof pr(ctx, PK_OTHER, 0, 0);
+  launch_filter_project(rho_dev, w, h, ctx->d_taps, ctx->d_tapw, ctx->ntap, beta, eta, eps_lo, eps_hi - eps_lo,
+                        eps_dev, work_dev, work_dev + (size_t)w * h, ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_filter_project_adjoint(fdfd_ctx* ctx, const double* g_eps_dev, const double* work_dev,
+                                        double radius, double* g_rho_dev) {
+  if (!ctx || !g_eps_dev || !work_dev || !g_rho_dev || g_rho_dev == g_eps_dev || !(radius > 0 && radius <= 25))
+    return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->box.w == 0 || ctx->box.h == 0) return fail(ctx, FDFD_ERR_ARG, "context has no design box");
+  CKS(ensure_taps(ctx, radius));
+  const int w = ctx->box.w, h = ctx->box.h;
+  Prof pr(ctx, PK_OTHER, 0, 0);
+  launch_filter_adjoint(g_eps_dev, work_dev, work_dev + (size_t)w * h, w, h, ctx->d_taps, ctx->d_tapw, ctx->ntap,
+                        g_rho_dev, ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
 fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose) {
   if (!ctx || !x_dev || !y_dev || nrhs <= 0 || x_dev == y_dev) return FDFD_ERR_ARG;
   ctx->err.clear();
@@ -1406,7 +1471,7 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   free_ws(ctx);
   free_gm(ctx);
   void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
-                ctx->d_growth_max, ctx->d_flow_err};
+                ctx->d_growth_max, ctx->d_flow_err, ctx->d_taps, ctx->d_tapw};
   for (void* p : ps) free_ptr(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   drop_graphs(ctx);

@@ -183,4 +183,13 @@ void launch_grad(const double2* xf, const double2* xa, long long N, int ny, int 
                  cudaStream_t s);
 cudaError_t solve_init_attributes();
 
+// ---- design.cu: smoothing filter and projection of the design density (Sec. III)
+// off / wt: the filter taps (integer offsets inside the radius and their weights
+// radius - distance), ntap of them; pixels x-major (i * h + j).
+void launch_filter_project(const double* rho, int w, int h, const int2* off, const double* wt, int ntap,
+                           double beta, double eta, double eps_lo, double deps, double* eps, double* slope,
+                           double* norm, cudaStream_t s);
+void launch_filter_adjoint(const double* g, const double* slope, const double* norm, int w, int h, const int2* off,
+                           const double* wt, int ntap, double* out, cudaStream_t s);
+
 }  // namespace fdfd

@@ -27,7 +27,7 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
-           "fdfd_selftest_wait"]
+           "fdfd_selftest_wait", "fdfd_filter_project", "fdfd_filter_project_adjoint"]
 
 
 class Grid(C.Structure):
@@ -90,13 +90,16 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_solve_raw_noalloc.restype = C.c_int
     lib.fdfd_noalloc_scratch_bytes.argtypes = []
     lib.fdfd_noalloc_scratch_bytes.restype = C.c_size_t
+    lib.fdfd_filter_project.argtypes = [vp, vp, d, d, d, d, d, vp, vp]
+    lib.fdfd_filter_project_adjoint.argtypes = [vp, vp, vp, d, vp]
     lib.fdfd_last_error.argtypes = [vp]
     lib.fdfd_last_error.restype = C.c_char_p
     lib.fdfd_destroy.argtypes = [vp]
     lib.fdfd_destroy.restype = None
     for name in ("fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design", "fdfd_solve",
                  "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
-                 "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get"):
+                 "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get", "fdfd_filter_project",
+                 "fdfd_filter_project_adjoint"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -221,6 +224,26 @@ class Solver:
                                                      device=x_fwd.device)
         self._check(_lib.fdfd_grad(self._h, _ptr(x_fwd), _ptr(x_adj), nrhs, _ptr(weight), _ptr(g),
                                    int(bool(accumulate))), "fdfd_grad")
+        return g
+
+    def filter_project(self, rho: torch.Tensor, radius: float, beta: float, eta: float, eps_lo: float,
+                       eps_hi: float) -> tuple[torch.Tensor, torch.Tensor]:
+        """Design-box permittivity from the density (conic filter, tanh projection): (eps, work)."""
+        n = self.box[2] * self.box[3]
+        rho = rho.reshape(-1).contiguous()
+        eps = torch.empty(n, dtype=torch.float64, device=rho.device)
+        work = torch.empty(2 * n, dtype=torch.float64, device=rho.device)
+        self._check(_lib.fdfd_filter_project(self._h, _ptr(rho), float(radius), float(beta), float(eta),
+                                             float(eps_lo), float(eps_hi), _ptr(eps), _ptr(work)),
+                    "fdfd_filter_project")
+        return eps, work
+
+    def filter_project_adjoint(self, g_eps: torch.Tensor, work: torch.Tensor, radius: float) -> torch.Tensor:
+        """dF/drho from dF/deps through the projection and the filter of filter_project."""
+        g_eps = g_eps.reshape(-1).contiguous()
+        g = torch.empty_like(g_eps)
+        self._check(_lib.fdfd_filter_project_adjoint(self._h, _ptr(g_eps), _ptr(work), float(radius), _ptr(g)),
+                    "fdfd_filter_project_adjoint")
         return g
 
     def apply(self, x: torch.Tensor, transpose: bool = False) -> torch.Tensor:
