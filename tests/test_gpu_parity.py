@@ -277,3 +277,34 @@ def test_filtered_design_gradient_through_autograd():
     g_ref = O.filter_project_grad(wl.rho, g_eps_ref / W.DELTA_EPS, radius, beta, eta, lo, hi)
     assert abs(float(F.detach()) - F_ref) <= 1e-8 * abs(F_ref)
     assert O.rel_err(g, g_ref) <= GRAD_TOL
+
+
+# ---------------------------------------------------------------------------
+# Full-size configurations: a property that holds at any size
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["c2", "c3", "c4", "c5"])
+def test_full_size_design_iteration_residuals(name):
+    """At the full sizes (up to 3.1M unknowns per matrix, several wavelengths and sources) the
+    complex128 residuals of the forward and adjoint solutions of one design iteration, measured with
+    the oracle's own assembly of the operator, meet the refinement tolerance for every system."""
+    wl = W.make(name)
+    prob = U.problem(wl)
+    s = prob.solver
+    prob._load(U.eps_design_tensor(wl, wl.rho))
+    x = s.solve(prob.b)
+    F, o, badj = s.objective(x, prob.cols, prob.g, prob.weight)
+    xa = s.solve(badj, transpose=True)
+    g = s.grad(x, xa)
+    torch.cuda.synchronize()
+    assert np.isfinite(float(F)) and np.all(np.isfinite(g.cpu().numpy()))
+    eps = wl.eps_full()
+    b, ba = prob.b.cpu().numpy(), badj.cpu().numpy()
+    xh, xah = x.cpu().numpy(), xa.cpu().numpy()
+    tol = 2 * s.options.ir_tol
+    for w, k0dx in enumerate(wl.k0dx()):
+        A = O.assemble(wl.nx, wl.ny, eps, k0dx, wl.npml)
+        At = A.T.tocsr()
+        for j in range(wl.n_src):
+            assert O.residual_rel(A, xh[w, j], b[w, j]) <= tol
+            assert O.residual_rel(At, xah[w, j], ba[w, j]) <= tol
+    s.close()
