@@ -100,6 +100,11 @@ typedef struct {
                                   diagonal block of the panel (default; faster, rows below are
                                   eliminated against it).  Small fronts and the FP64 fallback
                                   always use full partial pivoting. */
+  int tensor_form;             /* update matrices S = F22 - L21 U12 of complex FP32 fronts with
+                                  m >= tensor_min_m on the tensor cores (tcgen05, FP32 accumulation):
+                                  0 = off (SIMT FP32), 1 = TF32 operands, 2 = TF32 hi + lo (three
+                                  products), 3 = BF16 three-way split, six products (default) */
+  int tensor_min_m;            /* smallest boundary size m sent to the tensor cores (default 128) */
 } fdfd_options;
 
 typedef struct {
@@ -179,7 +184,8 @@ fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_ad
 fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose);
 
 /* Replaces the solve options (ir_tol, ir_max_iter, gmres_restart) at run time.
- * mode, growth_bound and leaf_area are fixed at creation and ignored here. */
+ * mode, growth_bound, leaf_area, pivoting, tensor_form and tensor_min_m are
+ * fixed at creation and ignored here. */
 fdfd_status fdfd_set_options(fdfd_ctx* ctx, const fdfd_options* opt);
 
 /* Counters and sizes (synchronises the context's stream). */
@@ -223,6 +229,16 @@ void fdfd_reset_counters(fdfd_ctx* ctx);
  * returns FDFD_ERR_TIMEOUT when the wait gave up as designed; the error word
  * is cleared and the context stays usable.  Any other status is a failure. */
 fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx);
+
+/* Self-test of the tensor-core update-matrix product (Sec. II: S = F22 - L21 U12 of
+ * a front), on one caller-supplied front: front_dev is a (k + m) x ld row-major
+ * complex64 matrix in device memory (8-byte aligned, ld >= k + m, interleaved
+ * re/im) whose block [k:, k:] is overwritten with F22 - L21 U12, L21 = rows k..
+ * columns ..k, U12 = rows ..k columns k..; nothing else is written.  planes is
+ * the operand form of tensor_form (1 TF32, 2 TF32 hi + lo, 3 BF16 three-way split).  Runs the same pack and product kernels as the factorisation on
+ * the context's stream and synchronises; FDFD_ERR_ARG on bad arguments,
+ * FDFD_ERR_TIMEOUT if a pipeline wait gave up. */
+fdfd_status fdfd_selftest_schur_tc(fdfd_ctx* ctx, void* front_dev, int k, int m, int ld, int planes);
 
 /* Text of the last error on this context ("" if none); valid until the next call. */
 const char* fdfd_last_error(const fdfd_ctx* ctx);

@@ -23,10 +23,18 @@ cudaError_t launch_growth_max(const float* growth, long long count, float* out, 
 
 namespace {
 
+// k-tiles (of kTcPivots pivots) a tensor-core update matrix sums in tensor memory
+// before its FP32 register sum takes them
+constexpr int kTcChunk = 8;
+
 struct LevelList {
   int task_off = 0, ntasks = 0;      // build tasks (int2) offset / count
   int small_off = 0, nsmall = 0, nmax_small = 0;
   int large_off = 0, nlarge = 0, nmax_large = 0, kmax_large = 0, mmax_large = 0;
+  int simt_off = 0, nsimt = 0, mmax_simt = 0;   // large fronts whose update matrix is formed by SIMT
+  int tcf_off = 0, ntcf = 0;                    // ... on the tensor cores: TcFront records
+  int tcp_off = 0, ntcp = 0;                    // their pack tasks (int4)
+  int tct_off = 0, ntct = 0;                    // their output tiles (int4)
 };
 
 struct TaskList {
@@ -88,6 +96,13 @@ struct fdfd_ctx {
   int* d_orig_code = nullptr;
   int* d_lists = nullptr;          // all per-level lists (ints; build tasks as int pairs)
   std::vector<int> h_lists;
+  // tensor-core update matrices: front records, pack and tile tasks, packed-operand workspace
+  TcFront* d_tcf = nullptr;
+  int4* d_tct = nullptr;
+  unsigned char* d_tcws = nullptr;
+  long long tc_ws_stride = 0;      // bytes per wavelength
+  std::vector<TcFront> h_tcf;
+  std::vector<int4> h_tct;
   std::vector<LevelList> lv_full[2], lv_design[2];   // [precision 0 = c64, 1 = c128]
   std::vector<SolveList> lv_solve;
   // dataflow sweep queues [task type: 0 rows, 1 columns][direction: 0 bottom-up, 1 top-down]
@@ -182,10 +197,11 @@ void free_ptr(void* p) {
 }
 
 enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_STEP, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
+                PK_TC_PACK, PK_LU_SCHUR_TC,
                 PK_SWEEP_L, PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY,
                 PK_ARNOLDI, PK_OTHER, PK_COUNT };
 const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_step", "lu_panel", "lu_trsm", "lu_gemm",
-                                          "lu_schur", "lu_inv",
+                                          "lu_schur", "lu_inv", "lu_schur_pack", "lu_schur_tc",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "gmres_arnoldi", "other"};
 
@@ -222,6 +238,9 @@ void free_plan_device(fdfd_ctx* c) {
   free_ptr(c->d_orig_ptr); free_ptr(c->d_orig_col); free_ptr(c->d_orig_code); free_ptr(c->d_lists);
   c->d_fronts = nullptr; c->d_children = c->d_idx = c->d_inv = c->d_orig_ptr = c->d_orig_col = nullptr;
   c->d_orig_code = c->d_lists = nullptr;
+  free_ptr(c->d_tcf); free_ptr(c->d_tct); free_ptr(c->d_tcws);
+  c->d_tcf = nullptr; c->d_tct = nullptr; c->d_tcws = nullptr;
+  c->tc_ws_stride = 0;
   c->uploaded = false;
 }
 
@@ -301,6 +320,10 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   CKS(upload(ctx, &ctx->d_orig_col, p.orig_col));
   CKS(upload(ctx, &ctx->d_orig_code, p.orig_code));
   std::vector<int> lists;
+  std::vector<TcFront> tcf;
+  std::vector<int4> tct;
+  long long tc_ws = 0;
+  const int planes = ctx->opt.tensor_form;   // form of the tensor-core operands (0 = off)
   const int L = p.n_levels;
   for (int prec = 0; prec < 2; ++prec) {
     const int small_n = lu_small_max_n(prec == 0 ? 8 : 16);
@@ -329,6 +352,49 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
             ll.mmax_large = std::max(ll.mmax_large, p.fronts[f].m);
           }
         ctx->max_nlarge = std::max(ctx->max_nlarge, ll.nlarge);
+        // update matrices: complex64 fronts with m >= tensor_min_m on the tensor cores, the rest SIMT
+        auto on_tc = [&](const FrontDesc& d) {
+          return prec == 0 && planes > 0 && d.n > small_n && d.m >= ctx->opt.tensor_min_m && d.k > 0;
+        };
+        ll.simt_off = (int)lists.size();
+        for (int f : fl)
+          if (p.fronts[f].n > small_n && !on_tc(p.fronts[f]) && p.fronts[f].m > 0) {
+            lists.push_back(f); ll.nsimt++; ll.mmax_simt = std::max(ll.mmax_simt, p.fronts[f].m);
+          }
+        ll.tcf_off = (int)tcf.size();
+        long long wsb = 0;
+        for (int f : fl)
+          if (on_tc(p.fronts[f])) {
+            const FrontDesc& d = p.fronts[f];
+            TcFront r;
+            r.f = f;
+            r.Mt = (d.m + kTcRows - 1) / kTcRows;
+            r.Nt = (d.m + kTcCols - 1) / kTcCols;
+            r.Kt = (d.k + kTcPivots - 1) / kTcPivots;
+            r.aoff = wsb;
+            wsb += (long long)r.Mt * r.Kt * tc_tile_bytes_a(planes);
+            r.boff = wsb;
+            wsb += (long long)r.Nt * r.Kt * tc_tile_bytes_b(planes);
+            tcf.push_back(r);
+          }
+        ll.ntcf = (int)tcf.size() - ll.tcf_off;
+        tc_ws = std::max(tc_ws, wsb);
+        ll.tcp_off = (int)tct.size();
+        for (int sl = 0; sl < ll.ntcf; ++sl) {
+          const TcFront& r = tcf[ll.tcf_off + sl];
+          for (int mt = 0; mt < r.Mt; ++mt)
+            for (int kt = 0; kt < r.Kt; ++kt) tct.push_back(make_int4(sl, 0, mt, kt));
+          for (int nt = 0; nt < r.Nt; ++nt)
+            for (int kt = 0; kt < r.Kt; ++kt) tct.push_back(make_int4(sl, 1, nt, kt));
+        }
+        ll.ntcp = (int)tct.size() - ll.tcp_off;
+        ll.tct_off = (int)tct.size();
+        for (int sl = 0; sl < ll.ntcf; ++sl) {
+          const TcFront& r = tcf[ll.tcf_off + sl];
+          for (int mt = 0; mt < r.Mt; ++mt)
+            for (int nt = 0; nt < r.Nt; ++nt) tct.push_back(make_int4(sl, mt, nt, 0));
+        }
+        ll.ntct = (int)tct.size() - ll.tct_off;
         if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
       }
     }
@@ -453,6 +519,14 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   }
   ctx->h_lists.swap(lists);
   CKS(upload(ctx, &ctx->d_lists, ctx->h_lists));
+  ctx->h_tcf.swap(tcf);
+  ctx->h_tct.swap(tct);
+  if (!ctx->h_tcf.empty()) {
+    CKS(upload(ctx, &ctx->d_tcf, ctx->h_tcf));
+    CKS(upload(ctx, &ctx->d_tct, ctx->h_tct));
+    ctx->tc_ws_stride = tc_ws;
+    CK(dalloc(&ctx->d_tcws, (size_t)tc_ws * ctx->n_omega));
+  }
   ctx->uploaded = true;
   return FDFD_OK;
 }
@@ -462,6 +536,7 @@ fdfd_status ensure_runtime(fdfd_ctx* ctx) {
   if (ctx->device < 0) {
     CK(cudaGetDevice(&ctx->device));
     CK(factor_init_attributes());
+    CK(tc_init_attributes());
     CK(solve_init_attributes());
     CK(dalloc(&ctx->d_cxm, sizeof(double2) * ctx->n_omega * ctx->nx));
     CK(dalloc(&ctx->d_cxp, sizeof(double2) * ctx->n_omega * ctx->nx));
@@ -642,17 +717,48 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
     }
-    if (ll.nlarge > 0 && ll.mmax_large > 0) {
+    if (ll.nsimt > 0) {
       // update matrices of the level's large fronts: S = F22 - L21 U12 (k m^2 complex multiply-adds)
       double sf = 0, sb = 0;
       if (ctx->prof_on)
-        for (int t = 0; t < ll.nlarge; ++t) {
-          const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
+        for (int t = 0; t < ll.nsimt; ++t) {
+          const FrontDesc& d = p.fronts[hl[ll.simt_off + t]];
           sf += 8.0 * (double)d.k * d.m * d.m;
           sb += es * (2.0 * (double)d.m * d.m + 2.0 * (double)d.k * d.m);
         }
       Prof pr(ctx, PK_LU_SCHUR, sf * nwd, sb * nwd);
-      launch_schur_simt<T>(fa, ctx->d_lists + ll.large_off, ll.nlarge, ll.mmax_large, s);
+      launch_schur_simt<T>(fa, ctx->d_lists + ll.simt_off, ll.nsimt, ll.mmax_simt, s);
+    }
+    if (ll.ntct > 0) {
+      // the same on the tensor cores: pack L21 / U12 into TF32 planes, then the tiled product
+      TcLaunch tl;
+      tl.fronts = ctx->d_tcf + ll.tcf_off;
+      tl.ws = ctx->d_tcws;
+      tl.ws_stride = ctx->tc_ws_stride;
+      tl.err = ctx->d_flow_err;
+      tl.chunk = kTcChunk;
+      const int planes = ctx->opt.tensor_form;
+      double sf = 0, sb = 0, pb = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.ntcf; ++t) {
+          const TcFront& r = ctx->h_tcf[ll.tcf_off + t];
+          const FrontDesc& d = p.fronts[r.f];
+          sf += 8.0 * (double)d.k * d.m * d.m;
+          sb += es * 2.0 * (double)d.m * d.m +
+                (double)r.Kt * (r.Mt * r.Nt) * (tc_tile_bytes_a(planes) + tc_tile_bytes_b(planes));
+          pb += es * 2.0 * (double)d.k * d.m +
+                (double)r.Kt * (r.Mt * tc_tile_bytes_a(planes) + r.Nt * tc_tile_bytes_b(planes));
+        }
+      {
+        Prof pr(ctx, PK_TC_PACK, 0, pb * nwd);
+        tl.tasks = ctx->d_tct + ll.tcp_off;
+        launch_schur_tc_pack(fa, tl, ll.ntcp, planes, s);
+      }
+      {
+        Prof pr(ctx, PK_LU_SCHUR_TC, sf * nwd, sb * nwd);
+        tl.tasks = ctx->d_tct + ll.tct_off;
+        launch_schur_tc(fa, tl, ll.ntct, planes, s);
+      }
     }
     if (ll.nlarge > 0 && !local_piv) {
       // triangular inverses of the level's large fronts (2/3 k^3 complex multiply-adds each);
@@ -676,6 +782,7 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   Prof pr_g(ctx, PK_OTHER, 0, 4.0 * p.fronts.size() * ctx->n_omega);
   CK(launch_growth_max(ctx->d_growth, (long long)p.fronts.size() * ctx->n_omega, ctx->d_growth_max, s));
   CK(cudaMemcpyAsync(ctx->h_growth_max, ctx->d_growth_max, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return FDFD_OK;
 }
 
@@ -911,9 +1018,11 @@ fdfd_status ensure_gm(fdfd_ctx* ctx, int nrhs, int m) {
 // (the pinned copy is refreshed at every synchronisation point) and clear it.
 fdfd_status check_flow_err(fdfd_ctx* ctx) {
   if (!ctx->h_flow_err || *ctx->h_flow_err == 0) return FDFD_OK;
+  const int code = *ctx->h_flow_err;
   *ctx->h_flow_err = 0;
   CK(cudaMemsetAsync(ctx->d_flow_err, 0, sizeof(int), ctx->stream));
-  return fail(ctx, FDFD_ERR_TIMEOUT, "a sweep gave up waiting for a front it depends on");
+  return fail(ctx, FDFD_ERR_TIMEOUT, code == 2 ? "a tensor-core update matrix gave up waiting on its copy/MMA pipeline"
+                                                : "a sweep gave up waiting for a front it depends on");
 }
 
 fdfd_status any_active(fdfd_ctx* ctx, int S, bool* any, double* maxres) {
@@ -1037,6 +1146,7 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr) {
   if (!ctx->growth_ready) CK(cudaStreamSynchronize(ctx->stream));
   ctx->growth_pending = false;
   ctx->growth_ready = false;
+  CKS(check_flow_err(ctx));
   const float g = *ctx->h_growth_max;
   ctx->last_growth = g;
   if (!(g <= ctx->opt.growth_bound)) {
@@ -1078,6 +1188,8 @@ void fdfd_default_options(fdfd_options* o) {
   o->growth_bound = 1e6;
   o->leaf_area = 32;
   o->pivoting = 1;
+  o->tensor_form = 3;
+  o->tensor_min_m = 128;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -1111,6 +1223,8 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.gmres_restart > 16) c->opt.gmres_restart = 16;
   if (c->opt.leaf_area < 1) c->opt.leaf_area = 32;
   if (c->opt.pivoting != 0) c->opt.pivoting = 1;
+  if (c->opt.tensor_form < 0 || c->opt.tensor_form > 3) c->opt.tensor_form = 3;
+  if (c->opt.tensor_min_m < 1) c->opt.tensor_min_m = 1;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   *out = c;
@@ -1406,6 +1520,71 @@ fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k, int* m, int* parent, int* le
   }
   if (idx) std::memcpy(idx, p.idx.data(), sizeof(int) * p.idx.size());
   return FDFD_OK;
+}
+
+fdfd_status fdfd_selftest_schur_tc(fdfd_ctx* ctx, void* front_dev, int k, int m, int ld, int planes) {
+  if (!ctx || !front_dev || k < 1 || m < 1 || ld < k + m || planes < 1 || planes > 3 ||
+      (reinterpret_cast<uintptr_t>(front_dev) & 7))
+    return FDFD_ERR_ARG;
+  ctx->err.clear();
+  CKS(ensure_runtime(ctx));
+  CKS(check_flow_err(ctx));
+  FrontDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.k = k; d.m = m; d.n = k + m; d.ld = ld; d.parent = -1;
+  TcFront r;
+  r.f = 0;
+  r.Mt = (m + kTcRows - 1) / kTcRows;
+  r.Nt = (m + kTcCols - 1) / kTcCols;
+  r.Kt = (k + kTcPivots - 1) / kTcPivots;
+  r.aoff = 0;
+  r.boff = (long long)r.Mt * r.Kt * tc_tile_bytes_a(planes);
+  const long long wsb = r.boff + (long long)r.Nt * r.Kt * tc_tile_bytes_b(planes);
+  std::vector<int4> tasks;
+  for (int mt = 0; mt < r.Mt; ++mt)
+    for (int kt = 0; kt < r.Kt; ++kt) tasks.push_back(make_int4(0, 0, mt, kt));
+  for (int nt = 0; nt < r.Nt; ++nt)
+    for (int kt = 0; kt < r.Kt; ++kt) tasks.push_back(make_int4(0, 1, nt, kt));
+  const int npack = (int)tasks.size();
+  for (int mt = 0; mt < r.Mt; ++mt)
+    for (int nt = 0; nt < r.Nt; ++nt) tasks.push_back(make_int4(0, mt, nt, 0));
+  FrontDesc* dd = nullptr;
+  TcFront* dr = nullptr;
+  int4* dt = nullptr;
+  unsigned char* dws = nullptr;
+  cudaError_t e = dalloc(&dd, sizeof(FrontDesc));
+  if (e == cudaSuccess) e = dalloc(&dr, sizeof(TcFront));
+  if (e == cudaSuccess) e = dalloc(&dt, sizeof(int4) * tasks.size());
+  if (e == cudaSuccess) e = dalloc(&dws, (size_t)wsb);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dd, &d, sizeof(d), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, &r, sizeof(r), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dt, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    FactorLaunch fa;
+    std::memset(&fa, 0, sizeof(fa));
+    fa.P.fronts = dd;
+    fa.store = front_dev;
+    fa.n_omega = 1;
+    TcLaunch tl;
+    tl.fronts = dr;
+    tl.ws = dws;
+    tl.ws_stride = wsb;
+    tl.err = ctx->d_flow_err;
+    tl.chunk = kTcChunk;
+    tl.tasks = dt;
+    launch_schur_tc_pack(fa, tl, npack, planes, ctx->stream);
+    tl.tasks = dt + npack;
+    launch_schur_tc(fa, tl, (int)tasks.size() - npack, planes, ctx->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dd); cudaFree(dr); cudaFree(dt); cudaFree(dws);
+  CK(e);
+  CK(es);
+  return check_flow_err(ctx);
 }
 
 fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx) {

@@ -62,6 +62,31 @@ template <typename T> void launch_lu_trsm(const FactorLaunch& a, const int* flis
 // (K = k), SIMT complex FMA; mmax = largest m listed.
 template <typename T> void launch_schur_simt(const FactorLaunch& a, const int* flist, int nf, int mmax,
                                              cudaStream_t s);
+// The same update matrix on the tensor cores (tc_schur.cu), complex64 fronts only:
+// P = L21 U12 as one real GEMM of the interleaved L21 with the 2 x 2 real
+// embedding of U12, FP32 accumulation in tensor memory, S = F22 - P in place.
+// Output tiles are kTcRows x kTcCols complex; the contraction advances kTcPivots
+// pivots per pipeline stage.  form: 1 = TF32, 2 = TF32 hi + lo (three products),
+// 3 = BF16 three-way split (six products).
+constexpr int kTcRows = 128, kTcCols = 128, kTcPivots = 8;
+struct TcFront {           // one front of a tensor-core launch
+  long long aoff, boff;    // byte offsets of its packed L21 / U12 planes in one wavelength's workspace
+  int f;                   // front index
+  int Mt, Nt, Kt;          // row tiles, column tiles, k-tiles (ceil(m/128), ceil(m/128), ceil(k/8))
+};
+struct TcLaunch {
+  const TcFront* fronts;
+  const int4* tasks;       // pack: (slot, 0 = L21 / 1 = U12, row or column tile, k-tile); product: (slot, mt, nt, 0)
+  unsigned char* ws;       // packed planes, [n_omega launched][ws_stride] bytes
+  long long ws_stride;
+  int* err;                // set to 2 when a pipeline wait gives up
+  int chunk;               // k-tiles summed in tensor memory before the FP32 register sum takes them
+};
+long long tc_tile_bytes_a(int form);   // bytes of one packed L21 tile (all planes)
+long long tc_tile_bytes_b(int form);   // bytes of one packed U12 tile (all planes)
+void launch_schur_tc_pack(const FactorLaunch& a, const TcLaunch& t, int ntasks, int form, cudaStream_t s);
+void launch_schur_tc(const FactorLaunch& a, const TcLaunch& t, int ntiles, int form, cudaStream_t s);
+cudaError_t tc_init_attributes();        // once per device, before the first factorisation
 // panel-step trailing update restricted to the pivot-block rows and columns
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);

@@ -27,7 +27,7 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
-           "fdfd_selftest_wait", "fdfd_filter_project", "fdfd_filter_project_adjoint"]
+           "fdfd_selftest_wait", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint"]
 
 
 class Grid(C.Structure):
@@ -45,7 +45,7 @@ class Box(C.Structure):
 class Options(C.Structure):
     _fields_ = [("mode", C.c_int), ("ir_tol", C.c_double), ("ir_max_iter", C.c_int),
                 ("gmres_restart", C.c_int), ("growth_bound", C.c_double), ("leaf_area", C.c_int),
-                ("pivoting", C.c_int)]
+                ("pivoting", C.c_int), ("tensor_form", C.c_int), ("tensor_min_m", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_noalloc_scratch_bytes.restype = C.c_size_t
     lib.fdfd_filter_project.argtypes = [vp, vp, d, d, d, d, d, vp, vp]
     lib.fdfd_filter_project_adjoint.argtypes = [vp, vp, vp, d, vp]
+    lib.fdfd_selftest_schur_tc.argtypes = [vp, vp, i, i, i, i]
     lib.fdfd_last_error.argtypes = [vp]
     lib.fdfd_last_error.restype = C.c_char_p
     lib.fdfd_destroy.argtypes = [vp]
@@ -274,6 +275,19 @@ class Solver:
 
     def reset_counters(self):
         _lib.fdfd_reset_counters(self._h)
+
+    def selftest_schur_tc(self, front, k: int, planes: int = 2):
+        """Tensor-core update matrix of one front in place: front[k:, k:] -= front[k:, :k] @ front[:k, k:].
+
+        front: (k + m) x ld complex64 CUDA tensor (row-major, ld >= k + m; only the
+        first k + m columns are the front).  planes: operand form, 1 = TF32, 2 = TF32 hi + lo,
+        3 = BF16 three-way split."""
+        if front.dtype != torch.complex64 or not front.is_cuda or front.dim() != 2 or front.stride(1) != 1:
+            raise ValueError("front must be a row-major complex64 CUDA matrix")
+        n = front.shape[0]
+        m = n - k
+        self._check(_lib.fdfd_selftest_schur_tc(self._h, C.c_void_p(front.data_ptr()), int(k), int(m),
+                                                int(front.stride(0)), int(planes)), "fdfd_selftest_schur_tc")
 
     def selftest_wait(self) -> int:
         """Runs one bounded sweep wait on a counter nothing sets; returns the status (7 = gave up as designed)."""

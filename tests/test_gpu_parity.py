@@ -209,6 +209,53 @@ def test_nan_permittivity_reports_pivot_error():
     assert e.value.status == 5
 
 
+@pytest.mark.parametrize("k,m,planes", [(16, 128, 3), (5, 129, 3), (37, 200, 3), (37, 200, 2), (37, 200, 1),
+                                         (1, 1, 3), (340, 340, 3), (340, 340, 2), (250, 700, 3), (250, 700, 1),
+                                         (512, 1900, 3)])
+def test_tensor_core_update_matrix(k, m, planes):
+    """The tcgen05 update matrix of one front, S = F22 - L21 U12 (Sec. II), against the same
+    product in complex128: componentwise error relative to |L21| |U12| + |F22| within the
+    bound of the operand form (BF16 three-way split or TF32 hi + lo: FP32-class; TF32: 2^-11);
+    nothing outside F22 is written.  Sizes span one tile, ragged row/column/pivot tails and
+    several tiles."""
+    wl = W.make("c1")
+    s = U.make_solver(wl)
+    n = k + m
+    ld = -(-n // 4) * 4 + 4
+    g = torch.Generator().manual_seed(1000 * k + m)
+    F = torch.complex(torch.randn(n, ld, generator=g), torch.randn(n, ld, generator=g)).to(torch.complex64)
+    F_dev = F.to(DEV)
+    s.selftest_schur_tc(F_dev, k, planes)
+    out = F_dev.cpu()
+    F64 = F.to(torch.complex128)
+    ref = F64[k:n, k:n] - F64[k:n, :k] @ F64[:k, k:n]
+    scale = F64[k:n, :k].abs() @ F64[:k, k:n].abs() + F64[k:n, k:n].abs()
+    err = ((out[k:n, k:n].to(torch.complex128) - ref).abs() / scale).max().item()
+    tol = 2e-3 if planes == 1 else 2e-6
+    print(f"k={k} m={m} planes={planes}: componentwise error {err:.2e} (tol {tol:.0e})")
+    assert err <= tol
+    assert torch.equal(out[:k], F[:k]) and torch.equal(out[:, :k], F[:, :k]) and torch.equal(out[:, n:], F[:, n:])
+
+
+@pytest.mark.parametrize("planes", [3, 2, 1])
+def test_c1_tensor_core_update_matrices_every_front(planes):
+    """Every large front with a boundary sends its update matrix through the tensor cores
+    (tensor_min_m = 1): fields within 1e-8 of the oracle after refinement, forward and
+    transpose; the raw FP32-factor error is reported beside the SIMT form's."""
+    wl = W.make("c1")
+    errs = {}
+    for tp in (False, True):
+        x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, transpose=tp, tensor_form=planes, tensor_min_m=1)
+        err = O.rel_err(x, ref)
+        print(f"planes={planes} transpose={tp}: field err {err:.2e} iters {s.stats()['ir_iters']}")
+        assert err <= FIELD_TOL
+    for tp_planes in (0, planes):
+        x, ref, _ = _solve_case(wl, 1, FD.MODE_MIXED, tensor_form=tp_planes, tensor_min_m=1, ir_max_iter=0)
+        errs[tp_planes] = O.rel_err(x, ref)
+    print(f"raw FP32-factor error: SIMT {errs[0]:.2e}, tensor cores (form {planes}) {errs[planes]:.2e}")
+    assert errs[planes] <= (1e4 if planes == 1 else 10.0) * errs[0]
+
+
 def test_bounded_sweep_wait_gives_up_and_context_survives():
     """A dataflow-sweep wait on a counter nothing sets gives up (FDFD_ERR_TIMEOUT, about a
     second) instead of hanging; the context then still solves correctly."""
