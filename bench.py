@@ -46,6 +46,10 @@ def peaks():
     return dict(hbm=6800.0, bf16=1900.0, sm_max_mhz=2070.0, src="fallback")
 
 
+TENSOR_FORMS = {0: "SIMT complex FP32", 1: "tcgen05 TF32", 2: "tcgen05 TF32 hi+lo (3 products)",
+                3: "tcgen05 BF16 three-way split (6 products), FP32 register sum every 8 pivots"}
+
+
 def workload_config(wl):
     x0, y0, w, h = wl.box
     return {"workload": f"{wl.name}: {wl.nx}x{wl.ny} grid ({wl.n:,} unknowns), dx {wl.dx * 1e3:.0f} nm, "
@@ -148,6 +152,9 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the uncached FP64 arm")
+    ap.add_argument("--tensor-form", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="update matrices on the tensor cores: 0 off (SIMT), 1 TF32, 2 TF32 hi+lo, "
+                         "3 BF16 three-way split (default)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -176,7 +183,8 @@ def main():
     k0 = 2 * np.pi / wl.wavelengths
 
     def make_problem(mode):
-        s = FD.Solver(wl.nx, wl.ny, wl.dx, k0, wl.npml, box=wl.box, options=FD.default_options(mode=mode))
+        s = FD.Solver(wl.nx, wl.ny, wl.dx, k0, wl.npml, box=wl.box,
+                      options=FD.default_options(mode=mode, tensor_form=args.tensor_form))
         b = np.stack([wl.source_dense(i) for i in range(wl.n_src)])
         b = np.broadcast_to(b, (wl.n_omega,) + b.shape).copy()
         cols = np.array([wl.monitors[w][i].col for w in range(wl.n_omega) for i in range(wl.n_src)], np.int32)
@@ -341,7 +349,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic (seeded design density; the paper's devices are not published)",
-            "config": workload_config(wl), "clocks": clk,
+            "config": dict(workload_config(wl), update_matrices=TENSOR_FORMS[args.tensor_form]), "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * bw * bh,
                     "d2h_bytes_per_step": 8 * (bw * bh + 1)},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -350,6 +358,7 @@ def main():
             "solver": {"ir_iters_last_solve": st["ir_iters"], "ir_resid": st["ir_resid"],
                        "n_fronts": st["n_fronts"], "n_levels": st["n_levels"], "max_front": st["max_front"],
                        "factor_gflop": st["flops_factor"] / 1e9, "refactor_gflop": st["flops_design"] / 1e9,
+                       "growth_last": st["growth"], "repivots_fp32": st["repivots"], "fallbacks_fp64": st["fallbacks"],
                        "store_mb": st["store_bytes"] / 1e6, "first_iteration_s": t_setup},
             "kernels": kernels}
     if rank == 0:

@@ -92,8 +92,12 @@ typedef struct {
   int ir_max_iter;             /* FGMRES iterations per solve across restarts (default 40);
                                   0 returns the raw FP32-factor solution */
   int gmres_restart;           /* Krylov vectors per cycle, 1..16 (default 8) */
-  double growth_bound;         /* largest |L| entry tolerated in an FP32 front before the whole
-                                  factorisation is redone in FP64 (default 1e6) */
+  double growth_bound;         /* largest |L| entry tolerated in an FP32 front (default 1e7, where
+                                  the FP32 unit roundoff times the growth reaches about 0.6); above
+                                  it a factorisation with block-local pivoting is redone in FP32
+                                  with partial pivoting over all pivot rows, and if that is still
+                                  above it, in FP64.  A refined solve that does not converge on
+                                  FP32 factors also sends the factorisation to FP64. */
   int leaf_area;               /* nested-dissection leaf size in cells (default 32) */
   int pivoting;                /* row pivoting in large fronts: 0 = partial pivoting over all the
                                   front's pivot rows, 1 = partial pivoting within each 32 x 32
@@ -114,13 +118,15 @@ typedef struct {
   long long sweeps;            /* triangular sweep pairs executed (including refinement) */
   long long ir_iters;          /* FGMRES iterations in the last solve (max over systems) */
   double ir_resid;             /* largest relative residual at the end of the last solve */
-  long long fallbacks;         /* factorisations redone in FP64 after pivot growth */
+  long long fallbacks;         /* factorisations redone in FP64 (pivot growth or no convergence) */
   double growth;               /* largest |L| entry in the last factorisation */
   int n_fronts, n_levels, max_front;
   long long factor_entries;    /* stored L and U entries per wavelength */
   long long store_bytes;       /* device bytes of front storage (all wavelengths) */
   double flops_factor;         /* full factorisation flops per wavelength (8 per complex FMA) */
   double flops_design;         /* flops of a design refactor per wavelength */
+  long long repivots;          /* complex FP32 factorisations redone with partial pivoting over all
+                                  pivot rows after block-local pivoting exceeded growth_bound */
 } fdfd_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -156,8 +162,10 @@ fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev);
 /* Solves A x = b (transpose = 0, Eq. 5) or A^T x = b (transpose = 1, Eq. 4/6)
  * for all wavelengths and nrhs right-hand sides on the cached factors.
  * b_dev, x_dev: [n_omega][nrhs][nx*ny] complex128 (device); x may not alias b.
- * Returns FDFD_ERR_NOT_CONVERGED (x holds the last iterate) when the mixed-mode
- * refinement stops above ir_tol. */
+ * In mixed mode, refinement that stops above ir_tol on the complex FP32 factors
+ * sends the factorisation to FP64 (counted in fdfd_stats.fallbacks) and the solve
+ * is repeated; FDFD_ERR_NOT_CONVERGED (x holds the last iterate) is returned only
+ * when it stops above ir_tol on FP64 factors as well. */
 fdfd_status fdfd_solve(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose);
 
 /* Mode-overlap objective and its adjoint source (Eq. 4):

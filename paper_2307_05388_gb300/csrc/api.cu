@@ -25,7 +25,7 @@ namespace {
 
 // k-tiles (of kTcPivots pivots) a tensor-core update matrix sums in tensor memory
 // before its FP32 register sum takes them
-constexpr int kTcChunk = 8;
+constexpr int kTcChunk = 1;
 
 struct LevelList {
   int task_off = 0, ntasks = 0;      // build tasks (int2) offset / count
@@ -154,6 +154,7 @@ struct fdfd_ctx {
   int *d_active = nullptr, *d_nj = nullptr;
   int* d_gcnt = nullptr;           // per-system counters of the Arnoldi passes (zero between launches)
   int* h_active = nullptr;          // pinned
+  int* h_nj = nullptr;              // pinned: Krylov vectors each system used in the last cycle
   double* h_resid = nullptr;        // pinned
 
   // per-kernel profile (CUDA events around every launch when enabled)
@@ -164,7 +165,7 @@ struct fdfd_ctx {
   std::vector<ProfRec> prof_recs;
 
   // counters
-  long long sf = 0, nf = 0, bs = 0, sweeps = 0, fallbacks = 0;
+  long long sf = 0, nf = 0, bs = 0, sweeps = 0, fallbacks = 0, repivots = 0;
   long long last_iters = 0;
   long long gm_expect[2] = {1, 1};  // FGMRES iterations the previous solve needed [transpose]
   double last_resid = 0;
@@ -1007,6 +1008,7 @@ fdfd_status ensure_gm(fdfd_ctx* ctx, int nrhs, int m) {
   CK(cudaMemsetAsync(ctx->d_gcnt, 0, sizeof(int) * S, ctx->stream));
   if (!ctx->h_active) {
     CK(cudaMallocHost((void**)&ctx->h_active, sizeof(int) * 4096));
+    CK(cudaMallocHost((void**)&ctx->h_nj, sizeof(int) * 4096));
     CK(cudaMallocHost((void**)&ctx->h_resid, sizeof(double) * 4096));
   }
   ctx->gm_nrhs = nrhs;
@@ -1027,6 +1029,7 @@ fdfd_status check_flow_err(fdfd_ctx* ctx) {
 
 fdfd_status any_active(fdfd_ctx* ctx, int S, bool* any, double* maxres) {
   CK(cudaMemcpyAsync(ctx->h_active, ctx->d_active, sizeof(int) * S, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_nj, ctx->d_nj, sizeof(int) * S, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_resid, ctx->d_resid, sizeof(double) * S, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1062,7 +1065,9 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   long long total = 0;
   double res = 0;
   bool converged = false;
+  int cycles = 0;
   for (int cycle = 0;; ++cycle) {
+    cycles = cycle;
     if (cycle > 0) {
       Prof pr(ctx, PK_STENCIL, 48.0 * N * S, 56.0 * N * S);
       launch_stencil(C, ctx->n_omega, nrhs, transpose, x, b, ctx->d_r, 1, s);
@@ -1129,7 +1134,17 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   }
   ctx->last_iters = total;
   ctx->last_resid = res;
-  ctx->gm_expect[transpose ? 1 : 0] = std::max<long long>(1, total);
+  // Next solve's first cycle: as many iterations as this one needed.  When one
+  // cycle sufficed, that is the largest count of Krylov vectors a system used
+  // before its Givens residual met the tolerance (the device stops counting
+  // then), which may be fewer than the iterations run here.
+  long long expect = total;
+  if (converged && cycles == 1) {
+    int mx = 0;
+    for (int i = 0; i < S; ++i) mx = std::max(mx, ctx->h_nj[i]);
+    if (mx > 0) expect = std::min<long long>(expect, mx);
+  }
+  ctx->gm_expect[transpose ? 1 : 0] = std::max<long long>(1, expect);
   if (!converged)
     return fail(ctx, FDFD_ERR_NOT_CONVERGED,
                 "refinement stopped at relative residual " + std::to_string(res) + " after " +
@@ -1137,11 +1152,32 @@ fdfd_status fgmres(fdfd_ctx* ctx, const double2* b, double2* x, int nrhs, int tr
   return FDFD_OK;
 }
 
-// Checks the pivot growth of the last FP32 factorisation; refactors in FP64 if needed.
-// The growth figure is copied to pinned host memory at the end of the
+// The whole factorisation in FP64, partial pivoting over every pivot row of each front.
+fdfd_status refactor_f64(fdfd_ctx* ctx) {
+  ctx->fallbacks += 1;
+  const int piv_saved = ctx->opt.pivoting;
+  ctx->opt.pivoting = 0;
+  const fdfd_status fst = factor_levels<double2>(ctx, false);
+  ctx->opt.pivoting = piv_saved;
+  CKS(fst);
+  CK(cudaStreamSynchronize(ctx->stream));
+  const float g64 = *ctx->h_growth_max;
+  ctx->last_growth = g64;
+  if (!std::isfinite(g64))
+    return fail(ctx, FDFD_ERR_PIVOT, "zero or non-finite pivot in the FP64 factorisation");
+  ctx->valid64 = true;
+  return FDFD_OK;
+}
+
+// Checks the pivot growth of the last FP32 factorisation.  Above the bound, a
+// factorisation with block-local pivoting is first redone in FP32 with partial
+// pivoting over every pivot row of each front; if the growth is still above the
+// bound (or that was already the pivoting used), the factorisation is redone in
+// FP64.  The growth figure is copied to pinned host memory at the end of the
 // factorisation; any later stream synchronisation makes it readable.
-fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr) {
+fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivoted = nullptr) {
   if (fell_back) *fell_back = false;
+  if (repivoted) *repivoted = false;
   if (!ctx->growth_pending) return FDFD_OK;
   if (!ctx->growth_ready) CK(cudaStreamSynchronize(ctx->stream));
   ctx->growth_pending = false;
@@ -1149,23 +1185,23 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr) {
   CKS(check_flow_err(ctx));
   const float g = *ctx->h_growth_max;
   ctx->last_growth = g;
-  if (!(g <= ctx->opt.growth_bound)) {
-    if (fell_back) *fell_back = true;
-    ctx->fallbacks += 1;
-    // the fallback always pivots over every pivot row of each front
-    const int piv_saved = ctx->opt.pivoting;
+  if (g <= ctx->opt.growth_bound) return FDFD_OK;
+  const int piv_saved = ctx->opt.pivoting;
+  if (piv_saved == 1) {
+    ctx->repivots += 1;
+    if (repivoted) *repivoted = true;
     ctx->opt.pivoting = 0;
-    const fdfd_status fst = factor_levels<double2>(ctx, false);
+    const fdfd_status fst = factor_levels<float2>(ctx, false);
     ctx->opt.pivoting = piv_saved;
     CKS(fst);
     CK(cudaStreamSynchronize(ctx->stream));
-    const float g64 = *ctx->h_growth_max;
-    ctx->last_growth = g64;
-    if (!std::isfinite(g64))
-      return fail(ctx, FDFD_ERR_PIVOT, "zero or non-finite pivot in the FP64 factorisation");
-    ctx->valid64 = true;
+    CKS(check_flow_err(ctx));
+    const float g2 = *ctx->h_growth_max;
+    ctx->last_growth = g2;
+    if (g2 <= ctx->opt.growth_bound) return FDFD_OK;
   }
-  return FDFD_OK;
+  if (fell_back) *fell_back = true;
+  return refactor_f64(ctx);
 }
 
 fdfd_status solve_direct(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose,
@@ -1185,7 +1221,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->ir_tol = 1e-9;
   o->ir_max_iter = 40;
   o->gmres_restart = 8;
-  o->growth_bound = 1e6;
+  o->growth_bound = 1e7;
   o->leaf_area = 32;
   o->pivoting = 1;
   o->tensor_form = 3;
@@ -1360,13 +1396,25 @@ fdfd_status solve_refined(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int
   double2* x = reinterpret_cast<double2*>(x_dev);
   // Refinement first: its synchronisations make the growth figure of a fresh
   // FP32 factorisation readable for free.  A front with too much growth sends
-  // the whole factorisation to FP64 and the solve is repeated on it.
+  // the whole factorisation to FP32 with full partial pivoting, then if need be
+  // to FP64, and the solve is repeated on the new factors when needed.
   const fdfd_status st = fgmres(ctx, b, x, nrhs, transpose);
   if (st != FDFD_OK && st != FDFD_ERR_NOT_CONVERGED) return st;
-  bool fell_back = false;
-  CKS(settle_growth(ctx, &fell_back));
-  if (fell_back) return fgmres(ctx, b, x, nrhs, transpose);
-  return st;
+  bool fell_back = false, repivoted = false;
+  CKS(settle_growth(ctx, &fell_back, &repivoted));
+  // a solve that converged on the first factors stands; otherwise it is repeated
+  // on the refactored ones
+  if (fell_back || (repivoted && st == FDFD_ERR_NOT_CONVERGED)) {
+    const fdfd_status st2 = fgmres(ctx, b, x, nrhs, transpose);
+    if (st2 != FDFD_ERR_NOT_CONVERGED || ctx->valid64) return st2;
+  } else if (st != FDFD_ERR_NOT_CONVERGED || ctx->valid64) {
+    return st;
+  }
+  // refinement on complex FP32 factors did not converge: the factorisation is
+  // redone in FP64 and the solve repeated on it
+  ctx->err.clear();
+  CKS(refactor_f64(ctx));
+  return fgmres(ctx, b, x, nrhs, transpose);
 }
 
 }  // namespace
@@ -1489,6 +1537,7 @@ fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* o) {
   o->ir_iters = ctx->last_iters;
   o->ir_resid = ctx->last_resid;
   o->fallbacks = ctx->fallbacks;
+  o->repivots = ctx->repivots;
   o->growth = ctx->last_growth;
   if (ctx->analyzed) {
     const Plan& p = ctx->plan;
@@ -1637,7 +1686,7 @@ fdfd_status fdfd_profile_get(fdfd_ctx* ctx, fdfd_kernel_profile* out, int max_ou
 
 void fdfd_reset_counters(fdfd_ctx* ctx) {
   if (!ctx) return;
-  ctx->sf = ctx->nf = ctx->bs = ctx->sweeps = ctx->fallbacks = 0;
+  ctx->sf = ctx->nf = ctx->bs = ctx->sweeps = ctx->fallbacks = ctx->repivots = 0;
 }
 
 const char* fdfd_last_error(const fdfd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -1669,6 +1718,7 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   if (ctx->h_growth_max) cudaFreeHost(ctx->h_growth_max);
   if (ctx->h_flow_err) cudaFreeHost(ctx->h_flow_err);
   if (ctx->h_active) cudaFreeHost(ctx->h_active);
+  if (ctx->h_nj) cudaFreeHost(ctx->h_nj);
   if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
   delete ctx;
 }

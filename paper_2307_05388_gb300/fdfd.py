@@ -53,7 +53,7 @@ class Stats(C.Structure):
                 ("ir_iters", C.c_longlong), ("ir_resid", C.c_double), ("fallbacks", C.c_longlong),
                 ("growth", C.c_double), ("n_fronts", C.c_int), ("n_levels", C.c_int), ("max_front", C.c_int),
                 ("factor_entries", C.c_longlong), ("store_bytes", C.c_longlong),
-                ("flops_factor", C.c_double), ("flops_design", C.c_double)]
+                ("flops_factor", C.c_double), ("flops_design", C.c_double), ("repivots", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

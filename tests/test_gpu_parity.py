@@ -193,7 +193,43 @@ def test_operation_counts_match_paper():
 def test_growth_fallback_to_f64():
     wl = W.make("c1")
     x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, growth_bound=1e-30)
-    assert s.stats()["fallbacks"] >= 1
+    st = s.stats()
+    assert st["repivots"] >= 1 and st["fallbacks"] >= 1   # the FP32 rung is tried first
+    assert O.rel_err(x, ref) <= FIELD_TOL
+
+
+def test_unconverged_refinement_sends_factorisation_to_f64():
+    """One FGMRES iteration cannot reach 1e-12 on complex FP32 factors: the factorisation is
+    redone in FP64 and the solve repeated, which then converges and matches the oracle."""
+    wl = W.make("c1")
+    x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, ir_max_iter=1, ir_tol=1e-12)
+    st = s.stats()
+    assert st["fallbacks"] == 1 and st["ir_resid"] <= 1e-12
+    assert O.rel_err(x, ref) <= FIELD_TOL
+
+
+def _raw_growth(wl, pivoting):
+    s = U.make_solver(wl, pivoting=pivoting, ir_max_iter=0)
+    s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
+    s.solve(torch.from_numpy(W.random_complex((wl.n_omega, 1, wl.n), 3)).to(DEV))
+    return s.stats()["growth"]
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_growth_repivot_rung_before_f64(name):
+    """Block-local pivoting whose growth exceeds the bound is redone in complex FP32 with
+    partial pivoting over all pivot rows; with that growth inside the bound there is no
+    FP64 fallback, and the refined fields still match the oracle."""
+    wl = W.make(name)
+    g_pp, g_bl = _raw_growth(wl, 0), _raw_growth(wl, 1)
+    print(f"{name}: growth with partial pivoting {g_pp:.3g}, block-local {g_bl:.3g}")
+    if not g_bl > 1.5 * g_pp:
+        pytest.skip("block-local growth not above the partial-pivoting growth here")
+    bound = float(np.sqrt(g_pp * g_bl))
+    x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, growth_bound=bound)
+    st = s.stats()
+    assert st["repivots"] == 1 and st["fallbacks"] == 0
+    assert st["growth"] <= bound
     assert O.rel_err(x, ref) <= FIELD_TOL
 
 
