@@ -294,6 +294,19 @@ def main():
                 "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     roof["kernel"] = dom
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # the tensor-core update matrices: algorithmic rate (8 flops per complex multiply-add) and the
+    # tensor-op rate it takes in the chosen operand form, against the dense peak of that input type
+    roof_tc = None
+    if "lu_schur_tc" in kern:
+        d_tc = kern["lu_schur_tc"]
+        mult = {1: 1, 2: 3, 3: 6}[args.tensor_form]
+        peak_tc = pk["bf16"] * (1.0 if args.tensor_form == 3 else 0.5)
+        ach = d_tc["flops"] / (d_tc["ms"] / 1e3) / 1e12
+        roof_tc = {"kernel": "lu_schur_tc", "bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                   "tensor_op_tflops": ach * mult, "peak": peak_tc, "frac": ach * mult / peak_tc, "traffic": None,
+                   "peak_source": f"{pk['src']} bf16 dense GEMM peak" + ("" if args.tensor_form == 3 else " x 0.5 (TF32)"),
+                   "note": f"achieved counts 8 flops per complex multiply-add; the operand form issues {mult}x "
+                           "as many tensor flops (tile padding not counted)"}
     launches_per_step = sum(v["launches"] for v in kern.values()) / prof_steps
     kernels = {k: {"launches_per_step": v["launches"] / prof_steps, "ms_per_step": v["ms"] / prof_steps,
                    "share": v["ms"] / tot_ms,
@@ -353,7 +366,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * bw * bh,
                     "d2h_bytes_per_step": 8 * (bw * bh + 1)},
             "gpu_launches": int(round(launches_per_step * args.steps)),
-            "roofline": roof, "cpu_baseline": cpu, "accuracy": acc, "uncached_f64": plain,
+            "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "accuracy": acc, "uncached_f64": plain,
             "design_filter": design_filter,
             "solver": {"ir_iters_last_solve": st["ir_iters"], "ir_resid": st["ir_resid"],
                        "n_fronts": st["n_fronts"], "n_levels": st["n_levels"], "max_front": st["max_front"],
