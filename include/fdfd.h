@@ -109,6 +109,10 @@ typedef struct {
                                   0 = off (SIMT FP32), 1 = TF32 operands, 2 = TF32 hi + lo (three
                                   products), 3 = BF16 three-way split, six products (default) */
   int tensor_min_m;            /* smallest boundary size m sent to the tensor cores (default 128) */
+  int tensor_min_tiles;        /* a level's update matrices go to the tensor cores only when its
+                                  eligible fronts make at least this many 128 x 128 output tiles
+                                  over all wavelengths (one CTA each): 0 = the device's SM count,
+                                  one full wave (default); 1 = always.  Below it they run SIMT. */
 } fdfd_options;
 
 typedef struct {
@@ -192,8 +196,8 @@ fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_ad
 fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose);
 
 /* Replaces the solve options (ir_tol, ir_max_iter, gmres_restart) at run time.
- * mode, growth_bound, leaf_area, pivoting, tensor_form and tensor_min_m are
- * fixed at creation and ignored here. */
+ * mode, growth_bound, leaf_area, pivoting and the tensor_* fields are fixed at
+ * creation and ignored here. */
 fdfd_status fdfd_set_options(fdfd_ctx* ctx, const fdfd_options* opt);
 
 /* Counters and sizes (synchronises the context's stream). */

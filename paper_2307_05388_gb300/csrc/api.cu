@@ -325,6 +325,12 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   std::vector<int4> tct;
   long long tc_ws = 0;
   const int planes = ctx->opt.tensor_form;   // form of the tensor-core operands (0 = off)
+  int min_tiles = ctx->opt.tensor_min_tiles;
+  if (min_tiles == 0) {   // one wave: one tile per SM
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&min_tiles, cudaDevAttrMultiProcessorCount, dev));
+  }
   const int L = p.n_levels;
   for (int prec = 0; prec < 2; ++prec) {
     const int small_n = lu_small_max_n(prec == 0 ? 8 : 16);
@@ -354,9 +360,17 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
           }
         ctx->max_nlarge = std::max(ctx->max_nlarge, ll.nlarge);
         // update matrices: complex64 fronts with m >= tensor_min_m on the tensor cores, the rest SIMT
-        auto on_tc = [&](const FrontDesc& d) {
+        auto eligible = [&](const FrontDesc& d) {
           return prec == 0 && planes > 0 && d.n > small_n && d.m >= ctx->opt.tensor_min_m && d.k > 0;
         };
+        long long level_tiles = 0;
+        for (int f : fl)
+          if (eligible(p.fronts[f])) {
+            const long long t = (p.fronts[f].m + kTcRows - 1) / kTcRows;
+            level_tiles += t * t;
+          }
+        const bool level_tc = level_tiles * ctx->n_omega >= min_tiles;
+        auto on_tc = [&](const FrontDesc& d) { return level_tc && eligible(d); };
         ll.simt_off = (int)lists.size();
         for (int f : fl)
           if (p.fronts[f].n > small_n && !on_tc(p.fronts[f]) && p.fronts[f].m > 0) {
@@ -1226,6 +1240,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->pivoting = 1;
   o->tensor_form = 3;
   o->tensor_min_m = 128;
+  o->tensor_min_tiles = 0;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -1261,6 +1276,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.pivoting != 0) c->opt.pivoting = 1;
   if (c->opt.tensor_form < 0 || c->opt.tensor_form > 3) c->opt.tensor_form = 3;
   if (c->opt.tensor_min_m < 1) c->opt.tensor_min_m = 1;
+  if (c->opt.tensor_min_tiles < 0) c->opt.tensor_min_tiles = 0;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   *out = c;

@@ -108,6 +108,14 @@ __device__ __forceinline__ R nanmax(R a, R b) {
   return a > b ? a : b;
 }
 
+// complex value of lane src, for every lane of the warp
+template <typename T>
+__device__ __forceinline__ T shfl_c(T v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  return v;
+}
+
 // warp argmax of |v|^2 with ties going to the smaller index
 template <typename R>
 __device__ __forceinline__ void warp_argmax(R& v, int& i) {
@@ -484,13 +492,6 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
 // warp updates its rows in registers with the pivot row broadcast, and lane
 // jj+1 collects the next column's argmax on the way (2 barriers per column).
 constexpr int kRegWarps = 16;
-
-template <typename T>
-__device__ __forceinline__ T shfl_c(T v, int src) {
-  v.x = __shfl_sync(0xffffffffu, v.x, src);
-  v.y = __shfl_sync(0xffffffffu, v.y, src);
-  return v;
-}
 
 template <typename T, int N>
 __device__ __forceinline__ T pick(const T (&v)[N], int s) {

@@ -276,17 +276,19 @@ def test_tensor_core_update_matrix(k, m, planes):
 @pytest.mark.parametrize("planes", [3, 2, 1])
 def test_c1_tensor_core_update_matrices_every_front(planes):
     """Every large front with a boundary sends its update matrix through the tensor cores
-    (tensor_min_m = 1): fields within 1e-8 of the oracle after refinement, forward and
+    (tensor_min_m = tensor_min_tiles = 1): fields within 1e-8 of the oracle after refinement, forward and
     transpose; the raw FP32-factor error is reported beside the SIMT form's."""
     wl = W.make("c1")
     errs = {}
     for tp in (False, True):
-        x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, transpose=tp, tensor_form=planes, tensor_min_m=1)
+        x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, transpose=tp, tensor_form=planes, tensor_min_m=1,
+                                tensor_min_tiles=1)
         err = O.rel_err(x, ref)
         print(f"planes={planes} transpose={tp}: field err {err:.2e} iters {s.stats()['ir_iters']}")
         assert err <= FIELD_TOL
     for tp_planes in (0, planes):
-        x, ref, _ = _solve_case(wl, 1, FD.MODE_MIXED, tensor_form=tp_planes, tensor_min_m=1, ir_max_iter=0)
+        x, ref, _ = _solve_case(wl, 1, FD.MODE_MIXED, tensor_form=tp_planes, tensor_min_m=1, tensor_min_tiles=1,
+                                ir_max_iter=0)
         errs[tp_planes] = O.rel_err(x, ref)
     print(f"raw FP32-factor error: SIMT {errs[0]:.2e}, tensor cores (form {planes}) {errs[planes]:.2e}")
     assert errs[planes] <= (1e4 if planes == 1 else 10.0) * errs[0]
