@@ -129,9 +129,32 @@ __device__ __forceinline__ void warp_argmax(R& v, int& i) {
 
 // ---------------------------------------------------------------------------
 // Small fronts: the whole front in shared memory, one CTA per front.
+// Partial pivoting over the k pivot rows; each pivot step is two phases: the
+// row swap, then the multipliers with the rank-1 update, during which lane 0 of
+// every warp, which writes the next column's entry of the warp's rows, keeps
+// the best of them as an argmax key (|v|^2 as float in the high word, the row
+// complemented in the low word: the largest value wins, ties go to the smaller
+// row) and posts it, so after the barrier every thread takes the next pivot
+// from the eight keys.  Then the triangular inverses, one warp per row,
+// lanes over the columns, straight from the factors in shared memory into the
+// inverse store:
+//   row i of L11^-1: X[i][i] = 1, X[i][l] = -sum_{l < m <= i} X[i][m] L[m][l], m descending;
+//   row i of U11^-1: X[i][c] = (delta_ic - sum_{i <= l < c} X[i][l] U[l][c]) / U[c][c], l ascending.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 256;
 constexpr int kSmallMaxK = 256;
+constexpr int kSmallSlots = 3;   // columns per lane in the inverse rows (k <= 96)
+
+template <typename R>
+__device__ __forceinline__ unsigned long long piv_key(R v2, int r) {
+  return ((unsigned long long)__float_as_uint((float)v2) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)r);
+}
+__device__ __forceinline__ int key_row(unsigned long long key) { return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)); }
+
+template <typename T>
+__device__ __forceinline__ T pick_slot(const T (&v)[kSmallSlots], int q) {
+  return q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kSmallThreads)
@@ -140,7 +163,7 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
   __shared__ int pm[kSmallMaxK];
-  __shared__ int s_piv;
+  __shared__ unsigned long long s_key[2][kSmallThreads / 32];   // [column parity][warp]
   __shared__ R s_red[kSmallThreads / 32];
   const int w = blockIdx.y + a.w0;
   const int f = flist[blockIdx.x];
@@ -148,26 +171,26 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
   const int n = d.n, k = d.k;
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kSmallThreads / 32;
+  for (int i = tid; i < k; i += blockDim.x) pm[i] = i;
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
     S[e] = F[(size_t)r * d.ld + c];
   }
-  for (int i = tid; i < k; i += blockDim.x) pm[i] = i;
+  __syncthreads();
+  if (warp == 0) {   // pivot candidates of column 0
+    unsigned long long best = 0;
+    for (int r = lane; r < k; r += 32) best = max(best, piv_key(cabs2(S[r * n]), r));
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane < NW) s_key[0][lane] = lane == 0 ? best : 0ull;
+  }
   __syncthreads();
   R gmax = 0;
   for (int j = 0; j < k; ++j) {
-    if (warp == 0) {
-      R best = -1;
-      int bi = j;
-      for (int r = j + lane; r < k; r += 32) {
-        const R v = cabs2(S[r * n + j]);
-        if (v > best) { best = v; bi = r; }
-      }
-      warp_argmax(best, bi);
-      if (lane == 0) s_piv = bi;
-    }
-    __syncthreads();
-    const int piv = s_piv;
+    unsigned long long kb = s_key[j & 1][0];
+#pragma unroll
+    for (int q = 1; q < NW; ++q) kb = max(kb, s_key[j & 1][q]);
+    const int piv = key_row(kb);
     if (piv != j) {
       for (int c = tid; c < n; c += blockDim.x) {
         const T x = S[j * n + c];
@@ -177,74 +200,84 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
       if (tid == 0) { const int x = pm[j]; pm[j] = pm[piv]; pm[piv] = x; }
     }
     __syncthreads();
-    const T inv = crcp(S[j * n + j]);
-    for (int r = j + 1 + tid; r < n; r += blockDim.x) {
+    const T p = S[j * n + j];
+    const T inv = crcp(p);
+    if (tid == 0 && p.x == 0 && p.y == 0) gmax = INFINITY;
+    unsigned long long cand = 0;   // lane 0: best next-column candidate of this warp's rows
+    for (int r = j + 1 + warp; r < n; r += NW) {
       const T l = cmul(S[r * n + j], inv);
-      S[r * n + j] = l;
-      gmax = nanmax(gmax, cabs2(l));
-    }
-    if (S[j * n + j].x == 0 && S[j * n + j].y == 0) gmax = INFINITY;
-    __syncthreads();
-    const int ty = tid >> 5, tx = tid & 31;
-    for (int r = j + 1 + ty; r < n; r += kSmallThreads / 32) {
-      const T l = S[r * n + j];
-      for (int c = j + 1 + tx; c < n; c += 32) S[r * n + c] = cfms(l, S[j * n + c], S[r * n + c]);
-    }
-    __syncthreads();
-  }
-  // Triangular inverses, right-looking, into X (k x k, row stride k): the
-  // strictly lower part holds L11^-1 (unit diagonal implied), the upper part
-  // U11^-1.  X_L[i][c] = -L[i][c] - sum_{l in (c, i)} L[i][l] X_L[l][c]: start
-  // from -L and, once row l is final (step l), subtract L[i][l] X_L[l][c] from
-  // every later row.  X_U from the bottom: row t = k-1-s is final once rows
-  // below it have been folded in, X_U[t][c] = (delta_tc - acc[t][c]) / U[t][t],
-  // and then acc[r][c] += U[r][t] X_U[t][c] for every earlier row r.  The two
-  // triangles never touch each other's entries.
-  T* X = S + n * n;
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int i = e / k, c = e - i * k;
-    X[e] = (i > c) ? csub(czero<T>(), S[i * n + c]) : czero<T>();
-  }
-  __syncthreads();
-  for (int st = 0; st < k; ++st) {
-    const int t = k - 1 - st;
-    {  // finalise row t of X_U
-      const T dinv = crcp(S[t * n + t]);
-      const T one = cmk(R(1), R(0));
-      for (int c = t + tid; c < k; c += blockDim.x) X[t * k + c] = cmul(csub(c == t ? one : czero<T>(), X[t * k + c]), dinv);
-    }
-    __syncthreads();
-    // L: rows i > st, columns c < st, with the final row st;  U: rows r < t, columns c >= t
-    const int nl = (k - st - 1) * st, nu = t * (k - t);
-    for (int e = tid; e < nl + nu; e += blockDim.x) {
-      if (e < nl) {
-        const int i = st + 1 + e / st, c = e - (e / st) * st;
-        X[i * k + c] = cfms(S[i * n + st], X[st * k + c], X[i * k + c]);
-      } else {
-        const int e2 = e - nl, r = e2 / (k - t), c = t + (e2 - r * (k - t));
-        X[r * k + c] = cfma(S[r * n + t], X[t * k + c], X[r * k + c]);
+      for (int c = j + 1 + lane; c < n; c += 32) {
+        const T v = cfms(l, S[j * n + c], S[r * n + c]);
+        S[r * n + c] = v;
+        if (c == j + 1 && r < k) cand = max(cand, piv_key(cabs2(v), r));
+      }
+      __syncwarp();
+      if (lane == 0) {
+        S[r * n + j] = l;
+        gmax = nanmax(gmax, cabs2(l));
       }
     }
+    if (lane == 0) s_key[(j + 1) & 1][warp] = cand;
     __syncthreads();
   }
+  // triangular inverses, rows i = warp, warp + 8, ...; lane holds columns lane + 32 q
+  T* Xg = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const T one = cmk(R(1), R(0));
+  T dinv[kSmallSlots];
+#pragma unroll
+  for (int q = 0; q < kSmallSlots; ++q) {
+    const int c = lane + 32 * q;
+    dinv[q] = c < k ? crcp(S[c * n + c]) : czero<T>();
+  }
+  for (int i = warp; i < k; i += NW) {
+    T acc[kSmallSlots];
+    // row i of L11^-1, columns l < i
+#pragma unroll
+    for (int q = 0; q < kSmallSlots; ++q) acc[q] = czero<T>();
+    for (int m = i; m >= 1; --m) {
+      const T ym = m == i ? one : shfl_c(pick_slot(acc, m >> 5), m & 31);
+#pragma unroll
+      for (int q = 0; q < kSmallSlots; ++q) {
+        const int l = lane + 32 * q;
+        if (l < m) acc[q] = cfms(ym, S[m * n + l], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kSmallSlots; ++q) {
+      const int l = lane + 32 * q;
+      if (l < i) Xg[(size_t)i * d.ldk + l] = acc[q];
+    }
+    // row i of U11^-1, columns c >= i
+#pragma unroll
+    for (int q = 0; q < kSmallSlots; ++q) acc[q] = (lane + 32 * q == i) ? one : czero<T>();
+    for (int l = i; l < k; ++l) {
+      const int q = l >> 5;
+      const T yl = shfl_c(cmul(pick_slot(acc, q), pick_slot(dinv, q)), l & 31);
+#pragma unroll
+      for (int qq = 0; qq < kSmallSlots; ++qq) {
+        const int c = lane + 32 * qq;
+        if (c > l && c < k) acc[qq] = cfms(yl, S[l * n + c], acc[qq]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kSmallSlots; ++q) {
+      const int c = lane + 32 * q;
+      if (c >= i && c < k) Xg[(size_t)i * d.ldk + c] = cmul(acc[q], dinv[q]);
+    }
+  }
+  // the front but its pivot block (L21, U12, S), the permutation, the growth
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
-    F[(size_t)r * d.ld + c] = S[e];
-  }
-  T* Xg = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int r = e / k, c = e - r * k;
-    Xg[(size_t)r * d.ldk + c] = X[e];
+    if (r >= k || c >= k) F[(size_t)r * d.ld + c] = S[e];
   }
   int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   for (int i = tid; i < k; i += blockDim.x) P[i] = pm[i];
-  // growth: block max of |L| (fixed reduction order)
   for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   if (lane == 0) s_red[warp] = gmax;
   __syncthreads();
   if (tid == 0) {
     R g = 0;
-    for (int i = 0; i < kSmallThreads / 32; ++i) g = nanmax(g, s_red[i]);
+    for (int i = 0; i < NW; ++i) g = nanmax(g, s_red[i]);
     a.growth[(size_t)w * a.n_fronts + f] = (float)sqrt((double)g);
   }
 }
@@ -1363,12 +1396,12 @@ cudaError_t launch_growth_max(const float* growth, long long count, float* out, 
 }
 
 cudaError_t factor_init_attributes() {
-  // small fronts: the front plus its k x k inverse block (k <= n)
+  // small fronts: the front in shared memory
   cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 96 * 96 * 8);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 96 * 8);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           2 * 64 * 64 * 16);
+                           64 * 64 * 16);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_step_local_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)step_local_smem(8));
@@ -1393,7 +1426,7 @@ void launch_build(const FactorLaunch& a, const int2* tasks, int ntasks, cudaStre
 template <typename T>
 void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, cudaStream_t s) {
   if (nf <= 0) return;
-  const size_t smem = 2 * (size_t)nmax * nmax * sizeof(T);
+  const size_t smem = (size_t)nmax * nmax * sizeof(T);
   lu_small_kernel<T><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
 }
 
