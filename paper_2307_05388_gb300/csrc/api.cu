@@ -34,7 +34,8 @@ struct LevelList {
   int simt_off = 0, nsimt = 0, mmax_simt = 0;   // large fronts whose update matrix is formed by SIMT
   int tcf_off = 0, ntcf = 0;                    // ... on the tensor cores: TcFront records
   int tcp_off = 0, ntcp = 0;                    // their pack tasks (int4)
-  int tct_off = 0, ntct = 0;                    // their output tiles (int4)
+  int tct_off = 0, ntct = 0;                    // their output tiles and K splits (int4)
+  int tcs_off = 0, ntcs = 0;                    // 16-row sums of their split tiles (int4)
 };
 
 struct TaskList {
@@ -101,6 +102,8 @@ struct fdfd_ctx {
   int4* d_tct = nullptr;
   unsigned char* d_tcws = nullptr;
   long long tc_ws_stride = 0;      // bytes per wavelength
+  float* d_tcpart = nullptr;       // split partial sums
+  long long tc_part_stride = 0;    // floats per wavelength
   std::vector<TcFront> h_tcf;
   std::vector<int4> h_tct;
   std::vector<LevelList> lv_full[2], lv_design[2];   // [precision 0 = c64, 1 = c128]
@@ -198,11 +201,11 @@ void free_ptr(void* p) {
 }
 
 enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_STEP, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
-                PK_TC_PACK, PK_LU_SCHUR_TC,
+                PK_TC_PACK, PK_LU_SCHUR_TC, PK_TC_SUM,
                 PK_SWEEP_L, PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY,
                 PK_ARNOLDI, PK_OTHER, PK_COUNT };
 const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_step", "lu_panel", "lu_trsm", "lu_gemm",
-                                          "lu_schur", "lu_inv", "lu_schur_pack", "lu_schur_tc",
+                                          "lu_schur", "lu_inv", "lu_schur_pack", "lu_schur_tc", "lu_schur_sum",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "gmres_arnoldi", "other"};
 
@@ -239,9 +242,9 @@ void free_plan_device(fdfd_ctx* c) {
   free_ptr(c->d_orig_ptr); free_ptr(c->d_orig_col); free_ptr(c->d_orig_code); free_ptr(c->d_lists);
   c->d_fronts = nullptr; c->d_children = c->d_idx = c->d_inv = c->d_orig_ptr = c->d_orig_col = nullptr;
   c->d_orig_code = c->d_lists = nullptr;
-  free_ptr(c->d_tcf); free_ptr(c->d_tct); free_ptr(c->d_tcws);
-  c->d_tcf = nullptr; c->d_tct = nullptr; c->d_tcws = nullptr;
-  c->tc_ws_stride = 0;
+  free_ptr(c->d_tcf); free_ptr(c->d_tct); free_ptr(c->d_tcws); free_ptr(c->d_tcpart);
+  c->d_tcf = nullptr; c->d_tct = nullptr; c->d_tcws = nullptr; c->d_tcpart = nullptr;
+  c->tc_ws_stride = c->tc_part_stride = 0;
   c->uploaded = false;
 }
 
@@ -323,7 +326,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   std::vector<int> lists;
   std::vector<TcFront> tcf;
   std::vector<int4> tct;
-  long long tc_ws = 0;
+  long long tc_ws = 0, tc_part = 0;
   const int planes = ctx->opt.tensor_form;   // form of the tensor-core operands (0 = off)
   int min_tiles = ctx->opt.tensor_min_tiles;
   if (min_tiles == 0) {   // one wave: one tile per SM
@@ -363,13 +366,26 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         auto eligible = [&](const FrontDesc& d) {
           return prec == 0 && planes > 0 && d.n > small_n && d.m >= ctx->opt.tensor_min_m && d.k > 0;
         };
+        // output tiles of the level over all wavelengths; when they fill less than a wave,
+        // each tile's contraction is split over several CTAs; the level goes to the
+        // tensor cores when the split tiles fill half a wave at least
         long long level_tiles = 0;
         for (int f : fl)
           if (eligible(p.fronts[f])) {
             const long long t = (p.fronts[f].m + kTcRows - 1) / kTcRows;
             level_tiles += t * t;
           }
-        const bool level_tc = level_tiles * ctx->n_omega >= min_tiles;
+        level_tiles *= ctx->n_omega;
+        auto splits_of = [&](const FrontDesc& d) {
+          return tc_splits(level_tiles, (d.k + kTcPivots - 1) / kTcPivots, min_tiles);
+        };
+        long long level_ctas = 0;
+        for (int f : fl)
+          if (eligible(p.fronts[f])) {
+            const long long t = (p.fronts[f].m + kTcRows - 1) / kTcRows;
+            level_ctas += t * t * splits_of(p.fronts[f]) * ctx->n_omega;
+          }
+        const bool level_tc = level_tiles > 0 && 2 * level_ctas >= min_tiles;
         auto on_tc = [&](const FrontDesc& d) { return level_tc && eligible(d); };
         ll.simt_off = (int)lists.size();
         for (int f : fl)
@@ -377,7 +393,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
             lists.push_back(f); ll.nsimt++; ll.mmax_simt = std::max(ll.mmax_simt, p.fronts[f].m);
           }
         ll.tcf_off = (int)tcf.size();
-        long long wsb = 0;
+        long long wsb = 0, pfl = 0;
         for (int f : fl)
           if (on_tc(p.fronts[f])) {
             const FrontDesc& d = p.fronts[f];
@@ -386,14 +402,18 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
             r.Mt = (d.m + kTcRows - 1) / kTcRows;
             r.Nt = (d.m + kTcCols - 1) / kTcCols;
             r.Kt = (d.k + kTcPivots - 1) / kTcPivots;
+            r.nsplit = splits_of(d);
             r.aoff = wsb;
             wsb += (long long)r.Mt * r.Kt * tc_tile_bytes_a(planes);
             r.boff = wsb;
             wsb += (long long)r.Nt * r.Kt * tc_tile_bytes_b(planes);
+            r.poff = pfl;
+            if (r.nsplit > 1) pfl += (long long)r.Mt * r.Nt * r.nsplit * kTcPartFloats;
             tcf.push_back(r);
           }
         ll.ntcf = (int)tcf.size() - ll.tcf_off;
         tc_ws = std::max(tc_ws, wsb);
+        tc_part = std::max(tc_part, pfl);
         ll.tcp_off = (int)tct.size();
         for (int sl = 0; sl < ll.ntcf; ++sl) {
           const TcFront& r = tcf[ll.tcf_off + sl];
@@ -407,9 +427,19 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         for (int sl = 0; sl < ll.ntcf; ++sl) {
           const TcFront& r = tcf[ll.tcf_off + sl];
           for (int mt = 0; mt < r.Mt; ++mt)
-            for (int nt = 0; nt < r.Nt; ++nt) tct.push_back(make_int4(sl, mt, nt, 0));
+            for (int nt = 0; nt < r.Nt; ++nt)
+              for (int sp = 0; sp < r.nsplit; ++sp) tct.push_back(make_int4(sl, mt, nt, sp));
         }
         ll.ntct = (int)tct.size() - ll.tct_off;
+        ll.tcs_off = (int)tct.size();
+        for (int sl = 0; sl < ll.ntcf; ++sl) {
+          const TcFront& r = tcf[ll.tcf_off + sl];
+          if (r.nsplit > 1)
+            for (int mt = 0; mt < r.Mt; ++mt)
+              for (int nt = 0; nt < r.Nt; ++nt)
+                for (int r0 = 0; r0 < kTcRows; r0 += 16) tct.push_back(make_int4(sl, mt, nt, r0));
+        }
+        ll.ntcs = (int)tct.size() - ll.tcs_off;
         if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
       }
     }
@@ -541,6 +571,8 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
     CKS(upload(ctx, &ctx->d_tct, ctx->h_tct));
     ctx->tc_ws_stride = tc_ws;
     CK(dalloc(&ctx->d_tcws, (size_t)tc_ws * ctx->n_omega));
+    ctx->tc_part_stride = std::max<long long>(tc_part, 4);
+    CK(dalloc(&ctx->d_tcpart, sizeof(float) * (size_t)ctx->tc_part_stride * ctx->n_omega));
   }
   ctx->uploaded = true;
   return FDFD_OK;
@@ -752,6 +784,8 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       tl.ws_stride = ctx->tc_ws_stride;
       tl.err = ctx->d_flow_err;
       tl.chunk = kTcChunk;
+      tl.part = ctx->d_tcpart;
+      tl.part_stride = ctx->tc_part_stride;
       const int planes = ctx->opt.tensor_form;
       double sf = 0, sb = 0, pb = 0;
       if (ctx->prof_on)
@@ -773,6 +807,17 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
         Prof pr(ctx, PK_LU_SCHUR_TC, sf * nwd, sb * nwd);
         tl.tasks = ctx->d_tct + ll.tct_off;
         launch_schur_tc(fa, tl, ll.ntct, planes, s);
+      }
+      if (ll.ntcs > 0) {
+        double qb = 0;
+        if (ctx->prof_on)
+          for (int t = 0; t < ll.ntcf; ++t) {
+            const TcFront& r = ctx->h_tcf[ll.tcf_off + t];
+            if (r.nsplit > 1) qb += (double)r.Mt * r.Nt * (4.0 * r.nsplit * kTcPartFloats + 2.0 * es * kTcRows * kTcCols);
+          }
+        Prof pr(ctx, PK_TC_SUM, 0, qb * nwd);
+        tl.tasks = ctx->d_tct + ll.tcs_off;
+        launch_schur_split_sum(fa, tl, ll.ntcs, s);
       }
     }
     if (ll.nlarge > 0 && !local_piv) {
@@ -1602,9 +1647,14 @@ fdfd_status fdfd_selftest_schur_tc(fdfd_ctx* ctx, void* front_dev, int k, int m,
   r.Mt = (m + kTcRows - 1) / kTcRows;
   r.Nt = (m + kTcCols - 1) / kTcCols;
   r.Kt = (k + kTcPivots - 1) / kTcPivots;
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  r.nsplit = tc_splits((long long)r.Mt * r.Nt, r.Kt, nsm);
+  r.poff = 0;
   r.aoff = 0;
   r.boff = (long long)r.Mt * r.Kt * tc_tile_bytes_a(planes);
   const long long wsb = r.boff + (long long)r.Nt * r.Kt * tc_tile_bytes_b(planes);
+  const long long pfl = r.nsplit > 1 ? (long long)r.Mt * r.Nt * r.nsplit * kTcPartFloats : 4;
   std::vector<int4> tasks;
   for (int mt = 0; mt < r.Mt; ++mt)
     for (int kt = 0; kt < r.Kt; ++kt) tasks.push_back(make_int4(0, 0, mt, kt));
@@ -1612,12 +1662,20 @@ fdfd_status fdfd_selftest_schur_tc(fdfd_ctx* ctx, void* front_dev, int k, int m,
     for (int kt = 0; kt < r.Kt; ++kt) tasks.push_back(make_int4(0, 1, nt, kt));
   const int npack = (int)tasks.size();
   for (int mt = 0; mt < r.Mt; ++mt)
-    for (int nt = 0; nt < r.Nt; ++nt) tasks.push_back(make_int4(0, mt, nt, 0));
+    for (int nt = 0; nt < r.Nt; ++nt)
+      for (int sp = 0; sp < r.nsplit; ++sp) tasks.push_back(make_int4(0, mt, nt, sp));
+  const int nprod = (int)tasks.size() - npack;
+  if (r.nsplit > 1)
+    for (int mt = 0; mt < r.Mt; ++mt)
+      for (int nt = 0; nt < r.Nt; ++nt)
+        for (int r0 = 0; r0 < kTcRows; r0 += 16) tasks.push_back(make_int4(0, mt, nt, r0));
   FrontDesc* dd = nullptr;
   TcFront* dr = nullptr;
   int4* dt = nullptr;
   unsigned char* dws = nullptr;
+  float* dpart = nullptr;
   cudaError_t e = dalloc(&dd, sizeof(FrontDesc));
+  if (e == cudaSuccess) e = dalloc(&dpart, sizeof(float) * (size_t)pfl);
   if (e == cudaSuccess) e = dalloc(&dr, sizeof(TcFront));
   if (e == cudaSuccess) e = dalloc(&dt, sizeof(int4) * tasks.size());
   if (e == cudaSuccess) e = dalloc(&dws, (size_t)wsb);
@@ -1637,16 +1695,20 @@ fdfd_status fdfd_selftest_schur_tc(fdfd_ctx* ctx, void* front_dev, int k, int m,
     tl.ws_stride = wsb;
     tl.err = ctx->d_flow_err;
     tl.chunk = kTcChunk;
+    tl.part = dpart;
+    tl.part_stride = pfl;
     tl.tasks = dt;
     launch_schur_tc_pack(fa, tl, npack, planes, ctx->stream);
     tl.tasks = dt + npack;
-    launch_schur_tc(fa, tl, (int)tasks.size() - npack, planes, ctx->stream);
+    launch_schur_tc(fa, tl, nprod, planes, ctx->stream);
+    tl.tasks = dt + npack + nprod;
+    launch_schur_split_sum(fa, tl, (int)tasks.size() - npack - nprod, ctx->stream);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   const cudaError_t es = cudaStreamSynchronize(ctx->stream);
-  cudaFree(dd); cudaFree(dr); cudaFree(dt); cudaFree(dws);
+  cudaFree(dd); cudaFree(dr); cudaFree(dt); cudaFree(dws); cudaFree(dpart);
   CK(e);
   CK(es);
   return check_flow_err(ctx);

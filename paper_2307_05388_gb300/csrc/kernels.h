@@ -71,9 +71,12 @@ template <typename T> void launch_schur_simt(const FactorLaunch& a, const int* f
 constexpr int kTcRows = 128, kTcCols = 128, kTcPivots = 8;
 struct TcFront {           // one front of a tensor-core launch
   long long aoff, boff;    // byte offsets of its packed L21 / U12 planes in one wavelength's workspace
+  long long poff;          // float offset of its split partial sums in one wavelength's partial buffer
   int f;                   // front index
   int Mt, Nt, Kt;          // row tiles, column tiles, k-tiles (ceil(m/128), ceil(m/128), ceil(k/8))
+  int nsplit;              // contraction split over this many CTAs per output tile (1 = none)
 };
+constexpr int kTcPartFloats = kTcRows * 2 * kTcCols;   // one split partial: 128 x 256 FP32
 struct TcLaunch {
   const TcFront* fronts;
   const int4* tasks;       // pack: (slot, 0 = L21 / 1 = U12, row or column tile, k-tile); product: (slot, mt, nt, 0)
@@ -81,11 +84,18 @@ struct TcLaunch {
   long long ws_stride;
   int* err;                // set to 2 when a pipeline wait gives up
   int chunk;               // k-tiles summed in tensor memory before the FP32 register sum takes them
+  float* part;             // split partial sums, [n_omega launched][part_stride] floats
+  long long part_stride;
 };
+// K splits of a front's output tiles so that a launch of `tiles` tiles (over all
+// wavelengths) fills min_ctas CTAs, each split keeping at least 4 k-tiles.
+int tc_splits(long long tiles, int Kt, int min_ctas);
 long long tc_tile_bytes_a(int form);   // bytes of one packed L21 tile (all planes)
 long long tc_tile_bytes_b(int form);   // bytes of one packed U12 tile (all planes)
 void launch_schur_tc_pack(const FactorLaunch& a, const TcLaunch& t, int ntasks, int form, cudaStream_t s);
 void launch_schur_tc(const FactorLaunch& a, const TcLaunch& t, int ntiles, int form, cudaStream_t s);
+// split tiles: S -= the sum of their partials; tasks (slot, mt, nt, first row of 16)
+void launch_schur_split_sum(const FactorLaunch& a, const TcLaunch& t, int ntasks, cudaStream_t s);
 cudaError_t tc_init_attributes();        // once per device, before the first factorisation
 // panel-step trailing update restricted to the pivot-block rows and columns
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,

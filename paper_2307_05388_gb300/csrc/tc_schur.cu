@@ -284,7 +284,9 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
   const int w = blockIdx.y + a.w0;
   const FrontDesc d = a.P.fronts[fr.f];
   const int chunk = t.chunk;
-  const int nk = fr.Kt, nch = (nk + chunk - 1) / chunk;
+  // this CTA's share of the contraction: k-tiles [kb, kb + nk)
+  const int kb = (int)((long long)task.w * fr.Kt / fr.nsplit);
+  const int nk = (int)((long long)(task.w + 1) * fr.Kt / fr.nsplit) - kb, nch = (nk + chunk - 1) / chunk;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t full0 = smem_u32(bar), empty0 = full0 + 8 * S, tfull0 = full0 + 16 * S, tempty0 = tfull0 + 16,
                  done = tfull0 + 32;
@@ -313,8 +315,8 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
   const unsigned char* ws = t.ws + (size_t)blockIdx.y * t.ws_stride;
   if (warp == 0) {
     if (lane == 0) {   // copies: plane tiles of A' row block mt and B' column block nt
-      const unsigned char* ga = ws + fr.aoff + (size_t)task.y * nk * kA;
-      const unsigned char* gb = ws + fr.boff + (size_t)task.z * nk * kB;
+      const unsigned char* ga = ws + fr.aoff + ((size_t)task.y * fr.Kt + kb) * kA;
+      const unsigned char* gb = ws + fr.boff + ((size_t)task.z * fr.Kt + kb) * kB;
       for (int kt = 0; kt < nk; ++kt) {
         const int s = kt % S;
         if (kt >= S && !mbar_wait(empty0 + 8 * s, ((kt / S) - 1) & 1, kRoleWaitNs)) { sh[1] = 1; break; }
@@ -375,26 +377,37 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty0 + 8 * b);
     }
-    if (ok && sh[1] == 0) {
-      const int r = task.y * kTcM + 32 * q + lane;   // row of S
-      if (r < d.m) {
-        float2* row = reinterpret_cast<float2*>(a.store) + (size_t)w * a.store_stride + d.st_off +
-                      (size_t)(d.k + r) * d.ld + d.k;
-        const int j0 = task.z * kTcCols + h * 64;
+    // every accumulation warp reaches this barrier (named, the 256 accumulation threads)
+    if (!ok && lane == 0) sh[1] = 1;
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    const bool good = sh[1] == 0;
+    const int r = task.y * kTcM + 32 * q + lane;   // row of S
+    bool apply = good;
+    if (good && fr.nsplit > 1) {
+      // post this split's partial sum; schur_split_sum_kernel adds the splits in order
+      const size_t tile = (size_t)task.y * fr.Nt + task.z;
+      float* pt = t.part + (size_t)blockIdx.y * t.part_stride + fr.poff + tile * fr.nsplit * kTcPartFloats;
+      float4* mine = reinterpret_cast<float4*>(pt + (size_t)task.w * kTcPartFloats + (32 * q + lane) * kTcN + h * 128);
 #pragma unroll
-        for (int jj = 0; jj < 64; ++jj) {
-          const int j = j0 + jj;
-          if (j < d.m) {
-            float2 sv = row[j];
-            sv.x -= acc[2 * jj];
-            sv.y -= acc[2 * jj + 1];
-            row[j] = sv;
-          }
+      for (int i = 0; i < 32; ++i) mine[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+      apply = false;
+    }
+    if (apply && r < d.m) {
+      float2* row = reinterpret_cast<float2*>(a.store) + (size_t)w * a.store_stride + d.st_off +
+                    (size_t)(d.k + r) * d.ld + d.k;
+      const int j0 = task.z * kTcCols + h * 64;
+#pragma unroll
+      for (int jj = 0; jj < 64; ++jj) {
+        const int j = j0 + jj;
+        if (j < d.m) {
+          float2 sv = row[j];
+          sv.x -= acc[2 * jj];
+          sv.y -= acc[2 * jj + 1];
+          row[j] = sv;
         }
       }
-    } else if (lane == 0) {
-      atomicExch(t.err, 2);
     }
+    if (!good && warp == 2 && lane == 0) atomicExch(t.err, 2);
   }
   tc_fence_before();
   __syncthreads();
@@ -410,7 +423,58 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
   }
 }
 
+// Split update matrices: S = F22 - sum over splits (in split order) of the partial
+// sums, 16 rows of one output tile per CTA, thread = (row, 8 complex columns).
+__global__ void __launch_bounds__(256)
+schur_split_sum_kernel(FactorLaunch a, TcLaunch t) {
+  const int4 task = t.tasks[blockIdx.x];   // (slot, mt, nt, first row of 16)
+  const TcFront fr = t.fronts[task.x];
+  const int w = blockIdx.y + a.w0;
+  const FrontDesc d = a.P.fronts[fr.f];
+  const int rr = task.w + (threadIdx.x >> 4), cq = threadIdx.x & 15;
+  const int r = task.y * kTcM + rr;
+  const float* pt = t.part + (size_t)blockIdx.y * t.part_stride + fr.poff +
+                    ((size_t)task.y * fr.Nt + task.z) * fr.nsplit * kTcPartFloats + (size_t)rr * kTcN + cq * 16;
+  float v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = 0.f;
+  for (int sp = 0; sp < fr.nsplit; ++sp) {
+    const float4* src = reinterpret_cast<const float4*>(pt + (size_t)sp * kTcPartFloats);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 x = __ldcg(src + i);
+      v[4 * i] += x.x; v[4 * i + 1] += x.y; v[4 * i + 2] += x.z; v[4 * i + 3] += x.w;
+    }
+  }
+  if (r >= d.m) return;
+  float2* row = reinterpret_cast<float2*>(a.store) + (size_t)w * a.store_stride + d.st_off + (size_t)(d.k + r) * d.ld +
+                d.k;
+  const int j0 = task.z * kTcCols + cq * 8;
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int j = j0 + jj;
+    if (j < d.m) {
+      float2 sv = row[j];
+      sv.x -= v[2 * jj];
+      sv.y -= v[2 * jj + 1];
+      row[j] = sv;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_schur_split_sum(const FactorLaunch& a, const TcLaunch& t, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return;
+  schur_split_sum_kernel<<<dim3(ntasks, a.n_omega), 256, 0, s>>>(a, t);
+}
+
+int tc_splits(long long tiles, int Kt, int min_ctas) {
+  if (tiles <= 0 || tiles >= min_ctas) return 1;
+  const long long want = (min_ctas + tiles - 1) / tiles;
+  const int most = Kt / 4 < 16 ? Kt / 4 : 16;
+  return most < 1 ? 1 : (int)(want < most ? want : most);
+}
 
 long long tc_tile_bytes_a(int form) {
   return form == 3 ? 3LL * Form<3>::tileA : form == 2 ? 2LL * Form<2>::tileA : (long long)Form<1>::tileA;
