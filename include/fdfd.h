@@ -109,10 +109,12 @@ typedef struct {
                                   0 = off (SIMT FP32), 1 = TF32 operands, 2 = TF32 hi + lo (three
                                   products), 3 = BF16 three-way split, six products (default) */
   int tensor_min_m;            /* smallest boundary size m sent to the tensor cores (default 128) */
-  int tensor_min_tiles;        /* a level's update matrices go to the tensor cores only when its
-                                  eligible fronts make at least this many 128 x 128 output tiles
-                                  over all wavelengths (one CTA each): 0 = the device's SM count,
-                                  one full wave (default); 1 = always.  Below it they run SIMT. */
+  int tensor_min_tiles;        /* CTAs a level's tensor-core update matrices should fill: 0 = the
+                                  device's SM count, one wave (default).  A level whose eligible
+                                  fronts make fewer 128 x 128 output tiles (over all wavelengths)
+                                  splits each tile's contraction over up to 16 CTAs (4 k-tiles of
+                                  8 pivots at least each); if even then it fills less than half
+                                  of them, its update matrices run SIMT.  1 = never split. */
 } fdfd_options;
 
 typedef struct {
