@@ -268,7 +268,7 @@ def main():
                          f"forward + transpose solve, gradient; single-threaded), {dt:.1f} s"}
 
     # ---- end to end through the public API with host buffers -----------------
-    ms_e2e, _ = run_arm(prob, args.steps, 1, host_io=True)
+    ms_e2e, _ = run_arm(prob, args.steps, args.warmup, host_io=True)   # the same design path as the timed arm
     e2e_value = world * args.steps / (ms_e2e / 1e3)
 
     # ---- per-kernel profile (separate pass; events around every launch) -----
