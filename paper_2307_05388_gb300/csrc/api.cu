@@ -345,9 +345,10 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         std::vector<int> fl;
         for (int f : p.level_fronts[l])
           if (!design || p.fronts[f].design) fl.push_back(f);
-        ll.task_off = (int)lists.size();
+        ll.task_off = (int)lists.size();   // build tasks: large fronts only (small ones assemble in their LU)
         for (int f : fl)
-          for (int r0 = 0; r0 < p.fronts[f].n; r0 += 8) { lists.push_back(f); lists.push_back(r0); ll.ntasks++; }
+          if (p.fronts[f].n > small_n)
+            for (int r0 = 0; r0 < p.fronts[f].n; r0 += 8) { lists.push_back(f); lists.push_back(r0); ll.ntasks++; }
         ll.small_off = (int)lists.size();
         for (int f : fl)
           if (p.fronts[f].n <= small_n) {

@@ -128,7 +128,9 @@ __device__ __forceinline__ void warp_argmax(R& v, int& i) {
 }
 
 // ---------------------------------------------------------------------------
-// Small fronts: the whole front in shared memory, one CTA per front.
+// Small fronts: the whole front in shared memory, one CTA per front, assembled
+// there (originals plus the children's update matrices, as the build kernel does
+// for the large fronts) and written back once, factored.
 // Partial pivoting over the k pivot rows; each pivot step is two phases: the
 // row swap, then the multipliers with the rank-1 update, during which lane 0 of
 // every warp, which writes the next column's entry of the warp's rows, keeps
@@ -173,9 +175,32 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kSmallThreads / 32;
   for (int i = tid; i < k; i += blockDim.x) pm[i] = i;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e / n, c = e - r * n;
-    S[e] = F[(size_t)r * d.ld + c];
+  // assemble the front here (no separate build): the children's update-matrix
+  // rows through their inverse extend-add maps, then the row's original entries
+  {
+    const T* st = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride;
+    FrontDesc c0, c1;
+    const int nc = d.nchild;
+    if (nc > 0) c0 = a.P.fronts[a.P.children[d.child0]];
+    if (nc > 1) c1 = a.P.fronts[a.P.children[d.child0 + 1]];
+    for (int r = warp; r < n; r += NW) {
+      const int ia = nc > 0 ? a.P.inv[c0.inv_off + r] : -1;
+      const int ib = nc > 1 ? a.P.inv[c1.inv_off + r] : -1;
+      const T* S0 = ia >= 0 ? st + c0.st_off + (size_t)(c0.k + ia) * c0.ld + c0.k : nullptr;
+      const T* S1 = ib >= 0 ? st + c1.st_off + (size_t)(c1.k + ib) * c1.ld + c1.k : nullptr;
+      for (int c = lane; c < n; c += 32) {
+        T v = czero<T>();
+        if (S0) { const int i0 = a.P.inv[c0.inv_off + c]; if (i0 >= 0) v = cadd(v, S0[i0]); }
+        if (S1) { const int i1 = a.P.inv[c1.inv_off + c]; if (i1 >= 0) v = cadd(v, S1[i1]); }
+        S[r * n + c] = v;
+      }
+      __syncwarp();
+      const int e0 = a.P.orig_ptr[d.orig_off + r], e1 = a.P.orig_ptr[d.orig_off + r + 1];
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const int b = a.P.orig_col[e];
+        S[r * n + b] = cadd(S[r * n + b], cfrom<T>(stencil_entry(a.C, w, a.P.orig_code[e])));
+      }
+    }
   }
   __syncthreads();
   if (warp == 0) {   // pivot candidates of column 0
