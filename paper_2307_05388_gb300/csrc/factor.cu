@@ -144,6 +144,7 @@ __device__ __forceinline__ void warp_argmax(R& v, int& i) {
 //   row i of U11^-1: X[i][c] = (delta_ic - sum_{i <= l < c} X[i][l] U[l][c]) / U[c][c], l ascending.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 256;
+constexpr int kSmallNarrowN = 48;   // fronts up to this size run with kSmallThreads / 2 threads
 constexpr int kSmallMaxK = 256;
 constexpr int kSmallSlots = 3;   // columns per lane in the inverse rows (k <= 96)
 
@@ -158,22 +159,22 @@ __device__ __forceinline__ T pick_slot(const T (&v)[kSmallSlots], int q) {
   return q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kSmallThreads)
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
   using R = typename RealOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
   __shared__ int pm[kSmallMaxK];
-  __shared__ unsigned long long s_key[2][kSmallThreads / 32];   // [column parity][warp]
-  __shared__ R s_red[kSmallThreads / 32];
+  __shared__ unsigned long long s_key[2][THREADS / 32];   // [column parity][warp]
+  __shared__ R s_red[THREADS / 32];
   const int w = blockIdx.y + a.w0;
   const int f = flist[blockIdx.x];
   const FrontDesc d = a.P.fronts[f];
   const int n = d.n, k = d.k;
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = kSmallThreads / 32;
+  constexpr int NW = THREADS / 32;
   for (int i = tid; i < k; i += blockDim.x) pm[i] = i;
   // assemble the front here (no separate build): the children's update-matrix
   // rows through their inverse extend-add maps, then the row's original entries
@@ -1422,10 +1423,10 @@ cudaError_t launch_growth_max(const float* growth, long long count, float* out, 
 
 cudaError_t factor_init_attributes() {
   // small fronts: the front in shared memory
-  cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2>,
+  cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2, kSmallThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 96 * 8);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lu_small_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(lu_small_kernel<double2, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            64 * 64 * 16);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_step_local_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1452,7 +1453,9 @@ template <typename T>
 void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, cudaStream_t s) {
   if (nf <= 0) return;
   const size_t smem = (size_t)nmax * nmax * sizeof(T);
-  lu_small_kernel<T><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
+  // fronts up to kSmallNarrowN: half the threads, so that twice as many fit on an SM
+  if (nmax <= kSmallNarrowN) lu_small_kernel<T, kSmallThreads / 2><<<dim3(nf, a.n_omega), kSmallThreads / 2, smem, s>>>(a, flist);
+  else lu_small_kernel<T, kSmallThreads><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
 }
 
 template <typename T>
