@@ -139,6 +139,7 @@ struct fdfd_ctx {
   float* d_growth = nullptr;
   float* d_growth_max = nullptr;
   int* d_swp = nullptr;            // panel row-swap scratch
+  void* d_dblk = nullptr;          // panel steps' diagonal-block factors
   int max_nlarge = 0;              // longest large-front list of any level
   float* h_growth_max = nullptr;   // pinned
   bool valid32 = false, valid64 = false;
@@ -256,6 +257,8 @@ void free_factor(fdfd_ctx* c) {
   free_ptr(c->d_growth);
   free_ptr(c->d_swp);
   c->d_swp = nullptr;
+  free_ptr(c->d_dblk);
+  c->d_dblk = nullptr;
   c->d_store32 = nullptr; c->d_store64 = nullptr; c->d_perm32 = c->d_perm64 = nullptr; c->d_growth = nullptr;
   c->valid32 = c->valid64 = false;
 }
@@ -644,6 +647,9 @@ fdfd_status ensure_store(fdfd_ctx* ctx, int prec) {
   if (!ctx->d_growth) CK(dalloc(&ctx->d_growth, sizeof(float) * nfr * ctx->n_omega));
   if (!ctx->d_swp)
     CK(dalloc(&ctx->d_swp, sizeof(int) * (size_t)kSwapScratchInts * std::max(1, ctx->max_nlarge) * ctx->n_omega));
+  if (!ctx->d_dblk)
+    CK(dalloc(reinterpret_cast<char**>(&ctx->d_dblk),
+              sizeof(double2) * (size_t)kDiagBlkElems * std::max(1, ctx->max_nlarge) * ctx->n_omega));
   if (prec == 0 && !ctx->d_store32) {
     CK(dalloc(&ctx->d_store32, sizeof(float2) * (size_t)p.store_total * ctx->n_omega));
     CK(dalloc(&ctx->d_perm32, sizeof(int) * (size_t)std::max(1, p.perm_total) * ctx->n_omega));
@@ -675,6 +681,7 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   fa.n_omega = nw < 0 ? ctx->n_omega : nw;
   fa.w0 = w0;
   fa.swp = ctx->d_swp;
+  fa.dblk = ctx->d_dblk;
   fa.swp_stride = std::max(1, ctx->max_nlarge);
   fa.istore = prec == 0 ? (void*)ctx->d_inv32 : (void*)ctx->d_inv64;
   fa.istore_stride = p.inv_total;

@@ -810,9 +810,14 @@ __device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __re
   return g;
 }
 
+// phase 0: every CTA factors the diagonal block itself (one wave or less);
+// phase 1: only the role-0 CTA of each front, which also posts the block's
+//          factors (rows of L\U in pivot order, 1 / U_pp, source rows) to the
+//          front's scratch slot;
+// phase 2: the other roles, which load those factors instead (many waves).
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu) {
+lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nl, int nu, int phase) {
   using R = typename RealOf<T>::type;
   using Blk = T[kMaxNb + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -828,7 +833,10 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   const FrontDesc d = a.P.fronts[f];
   if (j0 >= d.k) return;
   const int nb = min(kMaxNb, d.k - j0), n = d.n, ld = d.ld;
-  const int bx = blockIdx.x;
+  const int bx = blockIdx.x + (phase == 2 ? 1 : 0);
+  const size_t slot = (size_t)blockIdx.z * a.swp_stride + blockIdx.y;
+  T* blk = reinterpret_cast<T*>(a.dblk) + slot * kDiagBlkElems;
+  int* bsrc = a.swp + slot * kSwpInts;
   // role and range; CTAs whose range is empty for this front leave before any work
   int role, lo = 0;
   if (bx == 0) {
@@ -847,7 +855,15 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   R g = 0;
   if (warp < 4) {
-    g = diag_lu_4warps<T>(F, ld, j0, nb, LU, src, dinv, s_l, s_r);
+    if (phase == 2) {
+      for (int e = tid; e < kMaxNb * kMaxNb; e += 128) LU[e >> 5][e & 31] = blk[e];
+      if (tid < kMaxNb) {
+        dinv[tid] = blk[kMaxNb * kMaxNb + tid];
+        src[tid] = bsrc[tid];
+      }
+    } else {
+      g = diag_lu_4warps<T>(F, ld, j0, nb, LU, src, dinv, s_l, s_r);
+    }
   } else if (role == 1) {
     // meanwhile warps 4-7 stage rows [lo, lo + 64) of the block columns
     for (int e = tid - 128; e < kStepRows * kMaxNb; e += 128) {
@@ -863,6 +879,13 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     }
   }
   __syncthreads();
+  if (phase == 1) {
+    for (int e = tid; e < kMaxNb * kMaxNb; e += 256) blk[e] = LU[e >> 5][e & 31];
+    if (tid < kMaxNb) {
+      blk[kMaxNb * kMaxNb + tid] = dinv[tid];
+      bsrc[tid] = src[tid];
+    }
+  }
   // Role D: warp 0 (lane = column c) solves L_JJ x = e_c, warp 1
   // (lane = row r) solves x U_JJ = e_r, with the same substitution code as roles
   // U and L; the columns of L_JJ^-1 and rows of U_JJ^-1 meet in the staging tile.
@@ -1485,8 +1508,25 @@ void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j
   const int span = std::max(0, nmax - j0 - 1);
   const int nl = (span + kStepRows - 1) / kStepRows;
   const int np = (j0 + kStepRows - 1) / kStepRows;
-  lu_step_local_kernel<T><<<dim3(1 + 2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
-      a, flist, j0, nl, nl);
+  static int wave = 0;   // CTAs resident at once: 8 per SM
+  if (wave == 0) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      wave = 8 * nsm;
+    else
+      wave = 1 << 30;
+  }
+  const long long ctas = (long long)(1 + 2 * nl + np) * nf * a.n_omega;
+  if (ctas > wave && a.dblk) {
+    // more than one wave: the diagonal block once per front, then the substitutions
+    lu_step_local_kernel<T><<<dim3(1, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(a, flist, j0, nl, nl, 1);
+    if (2 * nl + np > 0)
+      lu_step_local_kernel<T><<<dim3(2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
+          a, flist, j0, nl, nl, 2);
+  } else {
+    lu_step_local_kernel<T><<<dim3(1 + 2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
+        a, flist, j0, nl, nl, 0);
+  }
 }
 
 template <typename T>

@@ -29,7 +29,9 @@ struct FactorLaunch {
   int swp_stride;          // >= number of fronts in one large-front list
   void* istore;            // triangular inverses (same type as store), [n_omega][istore_stride]
   long long istore_stride;
+  void* dblk;              // a panel step's diagonal-block factors, [n_omega launched][swp_stride][kDiagBlkElems]
 };
+constexpr int kDiagBlkElems = 32 * 32 + 32;   // L\U rows in pivot order, then 1 / U_pp
 // L11^-1 (strictly lower part) and U11^-1 (upper part) of the listed large fronts,
 // one CTA per (front, 32-column block, triangle); kmax = largest k listed.
 template <typename T> void launch_lu_inv(const FactorLaunch& a, const int* flist, int nf, int kmax, cudaStream_t s);
