@@ -152,6 +152,8 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the uncached FP64 arm")
+    ap.add_argument("--omegas", type=int, default=0,
+                    help="run only the first N wavelengths of the workload (0 = all; for small profiling cases)")
     ap.add_argument("--tensor-form", type=int, default=3, choices=[0, 1, 2, 3],
                     help="update matrices on the tensor cores: 0 off (SIMT), 1 TF32, 2 TF32 hi+lo, "
                          "3 BF16 three-way split (default)")
@@ -179,6 +181,9 @@ def main():
     from paper_2307_05388_gb300 import fdfd as FD
 
     wl = W.make(args.workload, seed=rank)
+    if 0 < args.omegas < wl.n_omega:   # a smaller case of the same workload (profiling)
+        wl.wavelengths = wl.wavelengths[:args.omegas]
+        wl.monitors = wl.monitors[:args.omegas]
     x0, y0, bw, bh = wl.box
     k0 = 2 * np.pi / wl.wavelengths
 
