@@ -463,9 +463,30 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   const int whole_n = flow_whole_max_n();   // fronts swept whole by one warp
   const int cta_n = flow_cta_max_n();       // ... or by one CTA
   auto small = [cta_n](const FrontDesc& d) { return d.n <= cta_n; };
+  // Row tasks of a level with many of them take two rows per warp (kSweepTaskTall,
+  // flagged in the task word): fewer, longer tasks with more loads in flight.
+  int sweep_nsm = 0;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sweep_nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sweep_nsm = 1;
+  }
+  auto tall_level = [&](int l) {
+    long long cnt = 0;
+    for (int f : p.level_fronts[l]) {
+      const FrontDesc& d = p.fronts[f];
+      if (small(d)) continue;
+      cnt += (d.k + 7) / 8 + (d.m + 7) / 8;
+    }
+    return cnt * ctx->n_omega >= 16LL * sweep_nsm;
+  };
   auto add_tasks = [&](TaskList& tl, int l, bool rect, bool over_m, int step) {
     if (lists.size() % 2) lists.push_back(0);   // int2 task arrays stay 8-byte aligned
     tl.off = (int)lists.size();
+    const bool tall = step == sweep_row_block() && tall_level(l);
+    const int st = tall ? 2 * step : step;
+    const unsigned flag = tall ? (unsigned)kSweepTaskTall : 0u;
     for (int f : p.level_fronts[l]) {
       const FrontDesc& d = p.fronts[f];
       if (small(d)) {
@@ -478,7 +499,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
       }
       if (rect && d.m == 0) continue;
       const int len = over_m ? d.m : d.k;
-      for (int s0 = 0; s0 < len; s0 += step) { lists.push_back(f); lists.push_back(s0); tl.n++; }
+      for (int s0 = 0; s0 < len; s0 += st) { lists.push_back((int)(flag | (unsigned)f)); lists.push_back(s0); tl.n++; }
     }
   };
   const int steps[2] = {sweep_row_block(), sweep_col_block()};
@@ -517,7 +538,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         for (int i = 0; i < sl.tri[t].n; ++i) {
           const int code = lists[sl.tri[t].off + 2 * i];
           if (code >= 0 || lists[sl.tri[t].off + 2 * i + 1] != 0) continue;   // not a small front
-          const int f = code & 0x7fffffff;
+          const int f = code & kSweepFrontMask;
           if (cnt == 0) first = (int)tasks.size() / 2;
           tasks.push_back(code); tasks.push_back(0);
           all[f]++;
@@ -529,7 +550,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
           if (code >= 0 || lists[sl.tri[t].off + 2 * i + 1] != 1) continue;
           put_unit((int)tasks.size() / 2, 1);
           tasks.push_back(code); tasks.push_back(1);
-          all[code & 0x7fffffff]++;
+          all[code & kSweepFrontMask]++;
         }
       };
       auto put_tri = [&](const SolveList& sl) {
@@ -538,15 +559,16 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
           if (code < 0) continue;                            // whole small front
           put_unit((int)tasks.size() / 2, 1);
           tasks.push_back(code); tasks.push_back(s0);
-          all[code]++;
-          if (dir == 0) ph1[code]++;
+          all[code & kSweepFrontMask]++;
+          if (dir == 0) ph1[code & kSweepFrontMask]++;
         }
       };
       auto put_rect = [&](const TaskList& tl) {
         for (int i = 0; i < tl.n; ++i) {
-          const int f = lists[tl.off + 2 * i], s0 = lists[tl.off + 2 * i + 1];
+          const int code = lists[tl.off + 2 * i], s0 = lists[tl.off + 2 * i + 1];
+          const int f = code & kSweepFrontMask;
           put_unit((int)tasks.size() / 2, 1);
-          tasks.push_back((int)(0x40000000u | (unsigned)f)); tasks.push_back(s0);
+          tasks.push_back((int)(0x40000000u | (unsigned)code)); tasks.push_back(s0);
           all[f]++;
           if (dir == 1) ph1[f]++;
         }
@@ -928,10 +950,11 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
     if (!ctx->prof_on) return;
     for (int t = 0; t < tl.n; ++t) {
       const int e = ctx->h_lists[tl.off + 2 * t];
-      const FrontDesc& d = p.fronts[e & 0x7fffffff];
+      const FrontDesc& d = p.fronts[e & kSweepFrontMask];
       const bool whole = e < 0;
       const int b0 = whole ? 0 : ctx->h_lists[tl.off + 2 * t + 1];
-      const int b1 = whole ? d.k : std::min(d.k, b0 + step);
+      const int rows = (e & kSweepTaskTall) ? 2 * step : step;
+      const int b1 = whole ? d.k : std::min(d.k, b0 + rows);
       double ent = 0;   // entries of this task's rows (or columns) inside the triangle
       for (int r = b0; r < b1; ++r) ent += lower ? r : (d.k - r);
       if (whole) ent += (double)d.k * d.m;   // whole-front tasks also do the off-diagonal block
@@ -943,9 +966,10 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
     *fl = *by = 0;
     if (!ctx->prof_on) return;
     for (int t = 0; t < tl.n; ++t) {
-      const FrontDesc& d = p.fronts[ctx->h_lists[tl.off + 2 * t]];
+      const int e = ctx->h_lists[tl.off + 2 * t];
+      const FrontDesc& d = p.fronts[e & kSweepFrontMask];
       const int s0 = ctx->h_lists[tl.off + 2 * t + 1];
-      const double rows = std::min(step, (over_m ? d.m : d.k) - s0);
+      const double rows = std::min((e & kSweepTaskTall) ? 2 * step : step, (over_m ? d.m : d.k) - s0);
       const double other = over_m ? d.k : d.m;
       *fl += 8.0 * rows * other * nsys;
       *by += es * rows * (other + 1) * nsys;

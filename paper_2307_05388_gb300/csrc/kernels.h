@@ -113,6 +113,11 @@ cudaError_t factor_init_attributes();   // once per device, before the first fac
 int lu_panel_width(int elem_bytes);
 
 // ---- solve.cu: level-scheduled triangular sweeps ---------------------------
+// sweep task words: front index in the low 29 bits; bit 29 = a row task of
+// 2 x sweep_row_block() rows (two per warp); bit 30 = off-diagonal block; bit 31
+// = a whole small or medium front
+constexpr int kSweepFrontMask = 0x1fffffff;
+constexpr int kSweepTaskTall = 0x20000000;
 struct SolveLaunch {
   DevPlan P;
   const void* store;       // factor storage (T), [n_omega][store_stride]

@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRowBlk = kWarps;     // rows per row-type task (one per warp)
+constexpr int kRowBlk = kWarps;     // rows per row-type task (one per warp; tall tasks: two)
 constexpr int kColBlk = 16;         // columns per column-type task (each column: two lanes per warp)
 
 template <typename T>
@@ -70,6 +70,36 @@ __device__ __forceinline__ T warp_dot(const T* __restrict__ row, const T* vec, i
   }
   for (; c < c1; c += 32) acc[0] = cfma(row[c], vec[c], acc[0]);
   return warp_sum(cadd(acc[0], acc[1]));
+}
+
+// Two rows over the same columns at once: sixteen loads per lane in flight.
+template <typename T>
+__device__ __forceinline__ void warp_dot2(const T* __restrict__ ra, const T* __restrict__ rb, const T* vec, int c0,
+                                          int c1, int lane, T& sa, T& sb) {
+  constexpr int UN = 8;
+  T a0[2] = {czero<T>(), czero<T>()}, b0[2] = {czero<T>(), czero<T>()};
+  int c = c0 + lane;
+  for (; c + 32 * (UN - 1) < c1; c += 32 * UN) {
+    T x[UN], y[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      x[u] = ra[c + 32 * u];
+      y[u] = rb[c + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const T v = vec[c + 32 * u];
+      a0[u & 1] = cfma(x[u], v, a0[u & 1]);
+      b0[u & 1] = cfma(y[u], v, b0[u & 1]);
+    }
+  }
+  for (; c < c1; c += 32) {
+    const T v = vec[c];
+    a0[0] = cfma(ra[c], v, a0[0]);
+    b0[0] = cfma(rb[c], v, b0[0]);
+  }
+  sa = warp_sum(cadd(a0[0], a0[1]));
+  sb = warp_sum(cadd(b0[0], b0[1]));
 }
 
 // Column block product over kColBlk columns: lane = (column c = lane % kColBlk,
@@ -298,7 +328,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
 
 // One inverse-block task of a large front (rows or columns from b0).
 template <typename T, int SWEEP>
-__device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& d, int b0, int w,
+__device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& d, int b0, int nrows, int w,
                                          const double2* __restrict__ in, double2* __restrict__ out, T* vs,
                                          T (*red)[32]) {
   const int k = d.k, ldk = d.ldk;
@@ -325,7 +355,7 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
     }
     __syncthreads();
     if (SWEEP == 0) {
-      for (int rr = warp; rr < kRowBlk; rr += kWarps) {
+      for (int rr = warp; rr < nrows; rr += kWarps) {
         const int row = b0 + rr;
         if (row >= k) break;
         const T acc = warp_dot(X + (size_t)row * ldk, vs, 0, row, lane);
@@ -333,7 +363,7 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
       }
     } else if (SWEEP == 1) {
       double2* xo = out + sys * a.n;
-      for (int rr = warp; rr < kRowBlk; rr += kWarps) {
+      for (int rr = warp; rr < nrows; rr += kWarps) {
         const int row = b0 + rr;
         if (row >= k) break;
         const T acc = warp_dot(X + (size_t)row * ldk, vs, row, k, lane);
@@ -362,7 +392,7 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
 // ---------------------------------------------------------------------------
 // One off-diagonal task of a large front (rows or columns from s0).
 template <typename T, int SWEEP>
-__device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc& d, int s0, int w,
+__device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc& d, int s0, int nrows, int w,
                                           double2* __restrict__ out, T* vs, T (*red)[32]) {
   const int k = d.k, m = d.m, ld = d.ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -381,14 +411,26 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
     }
     __syncthreads();
     if (SWEEP == 0 || SWEEP == 1) {
-      for (int rr = warp; rr < kRowBlk; rr += kWarps) {
-        const int row = s0 + rr;
-        if (row >= (SWEEP == 0 ? m : k)) break;
-        const T* Frow = SWEEP == 0 ? F + (size_t)(k + row) * ld : F + (size_t)row * ld + k;
-        // the value the product is subtracted from, fetched before the product
-        const T g = SWEEP == 0 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + row) : ldv(vf + row);
-        const T acc = warp_dot(Frow, vs, 0, SWEEP == 0 ? k : m, lane);
-        if (lane == 0) vf[SWEEP == 0 ? k + row : row] = csub(g, acc);
+      // rows s0 + warp and s0 + warp + kWarps, their loads interleaved
+      const int lim = SWEEP == 0 ? m : k, len = SWEEP == 0 ? k : m;
+      const int ra = s0 + warp, rb = nrows > kWarps ? ra + kWarps : lim;   // a tall task: two rows per warp
+      if (ra < lim) {
+        const T* Fa = SWEEP == 0 ? F + (size_t)(k + ra) * ld : F + (size_t)ra * ld + k;
+        const T* Fb = SWEEP == 0 ? F + (size_t)(k + rb) * ld : F + (size_t)rb * ld + k;
+        // the values the products are subtracted from, fetched before the products
+        const T ga = SWEEP == 0 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + ra) : ldv(vf + ra);
+        if (rb < lim) {
+          const T gb = SWEEP == 0 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + rb) : ldv(vf + rb);
+          T sa, sb;
+          warp_dot2(Fa, Fb, vs, 0, len, lane, sa, sb);
+          if (lane == 0) {
+            vf[SWEEP == 0 ? k + ra : ra] = csub(ga, sa);
+            vf[SWEEP == 0 ? k + rb : rb] = csub(gb, sb);
+          }
+        } else {
+          const T sa = warp_dot(Fa, vs, 0, len, lane);
+          if (lane == 0) vf[SWEEP == 0 ? k + ra : ra] = csub(ga, sa);
+        }
       }
     } else {
       const int cols = SWEEP == 2 ? m : k;
@@ -651,7 +693,7 @@ flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2*
       const int cnt = unit.y & 0xff;
       if (warp < cnt) {
         const int2 task = q.tasks[unit.x + warp];
-        const int f = (int)((unsigned)task.x & 0x3fffffffu);
+        const int f = (int)((unsigned)task.x & (unsigned)kSweepFrontMask);
         const FrontDesc d = a.P.fronts[f];
         bool ok = true;
         if (lane == 0) {
@@ -684,7 +726,8 @@ flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2*
     const unsigned code = (unsigned)task.x;
     const bool med = (code >> 31) != 0;          // a whole medium front
     const bool rect = !med && ((code >> 30) & 1u) != 0;
-    const int f = (int)(code & 0x3fffffffu);
+    const int f = (int)(code & (unsigned)kSweepFrontMask);
+    const int rows = (code & (unsigned)kSweepTaskTall) ? 2 * kRowBlk : kRowBlk;   // row tasks
     const FrontDesc d = a.P.fronts[f];
     if (tid == 0) {
       bool ok = true;
@@ -715,8 +758,8 @@ flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2*
     __syncthreads();
     if (!s_ok) break;
     if (med) medium_front<T, SWEEP>(a, d, w, in, out, vs, red);
-    else if (rect) rect_task<T, SWEEP>(a, d, task.y, w, out, vs, red);
-    else tri_task<T, SWEEP>(a, d, task.y, w, in, out, vs, red);
+    else if (rect) rect_task<T, SWEEP>(a, d, task.y, rows, w, out, vs, red);
+    else tri_task<T, SWEEP>(a, d, task.y, rows, w, in, out, vs, red);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
