@@ -327,6 +327,9 @@ __global__ void scale_vec_kernel(double2* dst, const double2* src, const double*
 //   0: w = A z_j,             h1_i = V_i^H w
 //   1: w -= sum_i h1_i V_i,   h2_i = V_i^H w
 //   2: w -= sum_i h2_i V_i,   |w|^2, then h = h1 + h2 and the Givens update
+// (the second projection is always needed here: with a preconditioner this
+// close to A^-1, A z_j lies almost in the span of V and the first projection
+// cancels most of w).
 // CTA (chunk of kArnPer * 256 entries, system); each CTA writes its partial
 // sums, and the last CTA of a system (a counter it resets afterwards) adds
 // them in chunk order, so results do not depend on timing.
@@ -394,16 +397,16 @@ arnoldi_kernel(ArnoldiStep g, int pass) {
   if (!s_last) return;
   __threadfence();
   double2* out = pass == 0 ? g.h1 : (pass == 1 ? g.h2 : g.hn);
-  if (warp < nout) {   // warp i adds output i over the chunks: lane-strided, then a shuffle tree
-    const double2* p = g.partial + ((size_t)sys * kMaxDot + warp) * nblk;
+  for (int o = warp; o < nout; o += kDotThreads / 32) {   // warp adds outputs o, o + 8, ...: lane-strided, then a shuffle tree
+    const double2* p = g.partial + ((size_t)sys * kMaxDot + o) * nblk;
     double2 sum = make_double2(0, 0);
     for (int b = lane; b < nblk; b += 32) sum = cadd(sum, __ldcg(p + b));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
-      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+    for (int q = 16; q > 0; q >>= 1) {
+      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, q);
+      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, q);
     }
-    if (lane == 0) out[(size_t)sys * kMaxDot + warp] = sum;
+    if (lane == 0) out[(size_t)sys * kMaxDot + o] = sum;
   }
   if (tid == 0) g.cnt[sys] = 0;
   if (pass == 2) {

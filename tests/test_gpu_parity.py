@@ -198,6 +198,23 @@ def test_growth_fallback_to_f64():
     assert O.rel_err(x, ref) <= FIELD_TOL
 
 
+@pytest.mark.parametrize("restart", [8, 16])
+def test_fgmres_long_cycles_with_a_weak_preconditioner(restart):
+    """FGMRES with a cycle of 8 or 16 Krylov vectors on a deliberately weak preconditioner
+    (TF32 update matrices in every front) and a tight tolerance (1e-13): the refined fields
+    still match the oracle, forward and transpose, with no FP64 fallback."""
+    wl = W.make("c1")
+    for tp in (False, True):
+        x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, transpose=tp, tensor_form=1, tensor_min_m=1,
+                                tensor_min_tiles=1, gmres_restart=restart, ir_tol=1e-13)
+        st = s.stats()
+        err = O.rel_err(x, ref)
+        print(f"restart {restart} transpose={tp}: {st['ir_iters']} iterations, residual {st['ir_resid']:.1e}, "
+              f"field err {err:.1e}, FP64 fallbacks {st['fallbacks']}")
+        assert st["ir_resid"] <= 1e-13 and st["fallbacks"] == 0
+        assert err <= FIELD_TOL
+
+
 def test_unconverged_refinement_sends_factorisation_to_f64():
     """One FGMRES iteration cannot reach 1e-12 on complex FP32 factors: the factorisation is
     redone in FP64 and the solve repeated, which then converges and matches the oracle."""
