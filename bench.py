@@ -301,6 +301,16 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     # the tensor-core update matrices: algorithmic rate (8 flops per complex multiply-add) and the
     # tensor-op rate it takes in the chosen operand form, against the dense peak of that input type
+    # the cached solves: the four sweep directions together, algorithmic bytes (every factor entry
+    # of the swept triangle and off-diagonal block once per right-hand side) against the HBM peak
+    sw = [v for k, v in kern.items() if k.startswith("sweep_")]
+    roof_sw = None
+    if sw:
+        sw_ms = sum(v["ms"] for v in sw)
+        sw_gbs = sum(v["bytes"] for v in sw) / (sw_ms / 1e3) / 1e9
+        roof_sw = {"kernels": "flow_kernel (L, U, U^T, L^T)", "bound": "hbm", "achieved": sw_gbs, "unit": "GB/s",
+                   "peak": pk["hbm"], "frac": sw_gbs / pk["hbm"], "ms_per_step": sw_ms / prof_steps,
+                   "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     roof_tc = None
     if "lu_schur_tc" in kern:
         d_tc = kern["lu_schur_tc"]
@@ -371,7 +381,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * bw * bh,
                     "d2h_bytes_per_step": 8 * (bw * bh + 1)},
             "gpu_launches": int(round(launches_per_step * args.steps)),
-            "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "accuracy": acc, "uncached_f64": plain,
+            "roofline": roof, "roofline_tensor": roof_tc, "roofline_sweeps": roof_sw,
+            "solves_per_s": value * 2 * wl.n_omega * wl.n_src, "cpu_baseline": cpu, "accuracy": acc, "uncached_f64": plain,
             "design_filter": design_filter,
             "solver": {"ir_iters_last_solve": st["ir_iters"], "ir_resid": st["ir_resid"],
                        "n_fronts": st["n_fronts"], "n_levels": st["n_levels"], "max_front": st["max_front"],
