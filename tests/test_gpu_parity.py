@@ -215,6 +215,19 @@ def test_fgmres_long_cycles_with_a_weak_preconditioner(restart):
         assert err <= FIELD_TOL
 
 
+def test_fgmres_cycle_beyond_eight_vectors():
+    """C2 with TF32 update matrices in every front and a 1e-13 tolerance needs more than eight
+    Krylov vectors in one 16-vector cycle, so the Arnoldi projections onto V_8.. are formed and
+    reduced; the fields match the oracle."""
+    wl = W.make("c2")
+    x, ref, s = _solve_case(wl, 1, FD.MODE_MIXED, tensor_form=1, tensor_min_m=1, tensor_min_tiles=1,
+                            gmres_restart=16, ir_tol=1e-13)
+    st = s.stats()
+    print(f"{st['ir_iters']} iterations, residual {st['ir_resid']:.1e}, field err {O.rel_err(x, ref):.1e}")
+    assert st["ir_iters"] >= 9 and st["ir_resid"] <= 1e-13 and st["fallbacks"] == 0
+    assert O.rel_err(x, ref) <= FIELD_TOL
+
+
 def test_unconverged_refinement_sends_factorisation_to_f64():
     """One FGMRES iteration cannot reach 1e-12 on complex FP32 factors: the factorisation is
     redone in FP64 and the solve repeated, which then converges and matches the oracle."""
