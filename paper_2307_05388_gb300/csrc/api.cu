@@ -884,6 +884,12 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   return FDFD_OK;
 }
 
+// Sweeps of problems with at least 2^20 unknowns over all wavelengths run the
+// flow-kernel variant with five resident CTAs per SM (more loads in flight);
+// smaller ones keep four, with more registers per thread for their
+// latency-bound tasks.
+bool flow_wide(const fdfd_ctx* ctx) { return (long long)ctx->nx * ctx->ny * ctx->n_omega >= (1LL << 20); }
+
 fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
   if (ctx->ws_nrhs >= nrhs) return FDFD_OK;
   free_ws(ctx);
@@ -893,7 +899,7 @@ fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
   int nsm = 0;
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   for (int prec = 0; prec < 2; ++prec)
-    ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax));
+    ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax), flow_wide(ctx));
   ctx->ws_nrhs = nrhs;
   return FDFD_OK;
 }
@@ -927,7 +933,7 @@ int flow_grid(fdfd_ctx* ctx, int prec) {
   if (ctx->flow_grid[prec] > 0) return ctx->flow_grid[prec];
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm <= 0) nsm = 1;
-  ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax));
+  ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax), flow_wide(ctx));
   return ctx->flow_grid[prec];
 }
 
@@ -1001,7 +1007,7 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
     q.n_fronts = (int)p.fronts.size();
     const int grid = std::max(1, std::min(grid_max, fq.nu * sa.n_omega));
     Prof pr(ctx, dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U), fl, by);
-    launch_sweep_flow<T>(sa, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s);
+    launch_sweep_flow<T>(sa, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s, flow_wide(ctx));
   }
   CK(cudaGetLastError());
   return FDFD_OK;

@@ -658,14 +658,13 @@ __device__ __forceinline__ bool wait_ge(const int* p, int need, int* err) {
 constexpr int kWarpSlice = 128;   // vector entries per warp for a whole small front (n + k, n <= 64)
 constexpr int kCtaWholeMaxN = 320;   // largest front swept whole by one CTA
 
-// resident CTAs per SM the register allocation aims for (more CTAs run more
-// tasks at once; fewer leave more registers for loads in flight)
-#ifndef FDFD_FLOW_MIN_BLOCKS
-#define FDFD_FLOW_MIN_BLOCKS 4
-#endif
+// resident CTAs per SM the register allocation aims for: small problems (few
+// tasks, each latency-bound) keep more registers per thread, large ones (the
+// sweeps bound by loads in flight) run more CTAs
+constexpr int kFlowBlocksNarrow = 4, kFlowBlocksWide = 5;
 
-template <typename T, int SWEEP>
-__global__ void __launch_bounds__(kThreads, FDFD_FLOW_MIN_BLOCKS)
+template <typename T, int SWEEP, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[kWarps][32];
@@ -790,25 +789,34 @@ size_t flow_smem(int vmax, size_t es) {
 
 template <typename T>
 void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax, int grid, const void* in,
-                       void* out, cudaStream_t s) {
+                       void* out, cudaStream_t s, bool wide) {
   if (q.nunits <= 0) return;
   const size_t smem = flow_smem(vmax, sizeof(T));
   const double2* i = reinterpret_cast<const double2*>(in);
   double2* o = reinterpret_cast<double2*>(out);
-  switch (sweep) {
-    case 0: flow_kernel<T, 0><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
-    case 1: flow_kernel<T, 1><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
-    case 2: flow_kernel<T, 2><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
-    default: flow_kernel<T, 3><<<grid, kThreads, smem, s>>>(a, q, i, o); break;
+#define FDFD_FLOW_LAUNCH(B)                                                               \
+  switch (sweep) {                                                                        \
+    case 0: flow_kernel<T, 0, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;         \
+    case 1: flow_kernel<T, 1, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;         \
+    case 2: flow_kernel<T, 2, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;         \
+    default: flow_kernel<T, 3, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;        \
   }
+  if (wide) { FDFD_FLOW_LAUNCH(kFlowBlocksWide) } else { FDFD_FLOW_LAUNCH(kFlowBlocksNarrow) }
+#undef FDFD_FLOW_LAUNCH
 }
 
-int flow_blocks_per_sm(int elem_bytes, int vmax) {
+int flow_blocks_per_sm(int elem_bytes, int vmax, bool wide) {
   int nb = 0;
   const size_t smem = flow_smem(vmax, elem_bytes);
-  const cudaError_t e = elem_bytes == 8
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1>, kThreads, smem)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1>, kThreads, smem);
+  cudaError_t e;
+  if (wide)
+    e = elem_bytes == 8
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksWide>, kThreads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1, kFlowBlocksWide>, kThreads, smem);
+  else
+    e = elem_bytes == 8
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksNarrow>, kThreads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1, kFlowBlocksNarrow>, kThreads, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
@@ -821,8 +829,9 @@ int sweep_col_block() { return kColBlk; }
 cudaError_t solve_init_attributes() {
   const int lim = 160 * 1024;
   cudaError_t e = cudaSuccess;
-#define FDFD_ATTR(K, T, S)                                                                       \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+#define FDFD_ATTR(K, T, S)                                                                             \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S, kFlowBlocksNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S, kFlowBlocksWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   FDFD_ATTR(flow_kernel, float2, 0) FDFD_ATTR(flow_kernel, float2, 1) FDFD_ATTR(flow_kernel, float2, 2)
   FDFD_ATTR(flow_kernel, float2, 3) FDFD_ATTR(flow_kernel, double2, 0) FDFD_ATTR(flow_kernel, double2, 1)
   FDFD_ATTR(flow_kernel, double2, 2) FDFD_ATTR(flow_kernel, double2, 3)
@@ -831,8 +840,8 @@ cudaError_t solve_init_attributes() {
 }
 
 template void launch_sweep_flow<float2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
-                                        cudaStream_t);
+                                        cudaStream_t, bool);
 template void launch_sweep_flow<double2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 
 }  // namespace fdfd
