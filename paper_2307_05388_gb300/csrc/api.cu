@@ -885,7 +885,7 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
 }
 
 // Sweeps of problems with at least 2^20 unknowns over all wavelengths run the
-// flow-kernel variant with five resident CTAs per SM (more loads in flight);
+// flow-kernel variant with six resident CTAs per SM (more loads in flight);
 // smaller ones keep four, with more registers per thread for their
 // latency-bound tasks.
 bool flow_wide(const fdfd_ctx* ctx) { return (long long)ctx->nx * ctx->ny * ctx->n_omega >= (1LL << 20); }

@@ -159,7 +159,7 @@ struct FlowQueue {
 };
 // in: right-hand sides, out: solutions, both complex128 [systems][n] whatever the
 // factor precision T (converted where the sweeps gather them and store them).
-// wide: the variant that keeps five CTAs resident per SM (large problems) instead of four
+// wide: the variant that keeps six CTAs resident per SM (large problems) instead of four
 template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax,
                                              int grid, const void* in, void* out, cudaStream_t s, bool wide);
 int flow_blocks_per_sm(int elem_bytes, int vmax, bool wide);

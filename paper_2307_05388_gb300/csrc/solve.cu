@@ -661,7 +661,7 @@ constexpr int kCtaWholeMaxN = 320;   // largest front swept whole by one CTA
 // resident CTAs per SM the register allocation aims for: small problems (few
 // tasks, each latency-bound) keep more registers per thread, large ones (the
 // sweeps bound by loads in flight) run more CTAs
-constexpr int kFlowBlocksNarrow = 4, kFlowBlocksWide = 5;
+constexpr int kFlowBlocksNarrow = 4, kFlowBlocksWide = 6;
 
 template <typename T, int SWEEP, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
