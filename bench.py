@@ -106,6 +106,16 @@ def oracle_iteration(wl, rho):
     return time.perf_counter() - t, F, g, fields
 
 
+def max_over_ranks(value, dist, device):
+    """The largest value over all ranks (a job's time is its slowest rank's); value itself on one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -247,11 +257,7 @@ def main():
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     ms, clk = run_arm(prob, args.steps, args.warmup, clocks=True)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t)
+    ms_max = max_over_ranks(ms, dist, dev)
     value = world * args.steps / (ms_max / 1e3)
     st = prob.solver.stats()
 
@@ -274,7 +280,7 @@ def main():
 
     # ---- end to end through the public API with host buffers -----------------
     ms_e2e, _ = run_arm(prob, args.steps, args.warmup, host_io=True)   # the same design path as the timed arm
-    e2e_value = world * args.steps / (ms_e2e / 1e3)
+    e2e_value = world * args.steps / (max_over_ranks(ms_e2e, dist, dev) / 1e3)
 
     # ---- per-kernel profile (separate pass; events around every launch) -----
     prof_steps = 3
