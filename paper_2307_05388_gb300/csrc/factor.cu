@@ -1508,14 +1508,12 @@ void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j
   const int span = std::max(0, nmax - j0 - 1);
   const int nl = (span + kStepRows - 1) / kStepRows;
   const int np = (j0 + kStepRows - 1) / kStepRows;
-  static int wave = 0;   // CTAs resident at once: 8 per SM
-  if (wave == 0) {
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      wave = 8 * nsm;
-    else
-      wave = 1 << 30;
-  }
+  // CTAs resident at once on the current device: 8 per SM
+  int dev = 0, nsm = 0;
+  const long long wave =
+      (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+          ? 8LL * nsm
+          : (1LL << 40);
   const long long ctas = (long long)(1 + 2 * nl + np) * nf * a.n_omega;
   if (ctas > wave && a.dblk) {
     // more than one wave: the diagonal block once per front, then the substitutions
