@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--tensor-form", type=int, default=3, choices=[0, 1, 2, 3],
                     help="update matrices on the tensor cores: 0 off (SIMT), 1 TF32, 2 TF32 hi+lo, "
                          "3 BF16 three-way split (default)")
+    ap.add_argument("--autotune", default="", metavar="CACHE.json",
+                    help="choose tensor_form, tensor_min_m, tensor_min_tiles and leaf_area by measured design "
+                         "iterations before the timed run (starting from --tensor-form), cached in this file")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -197,9 +200,9 @@ def main():
     x0, y0, bw, bh = wl.box
     k0 = 2 * np.pi / wl.wavelengths
 
-    def make_problem(mode):
+    def make_problem(mode, opts=None):
         s = FD.Solver(wl.nx, wl.ny, wl.dx, k0, wl.npml, box=wl.box,
-                      options=FD.default_options(mode=mode, tensor_form=args.tensor_form))
+                      options=opts if opts is not None else FD.default_options(mode=mode, tensor_form=args.tensor_form))
         b = np.stack([wl.source_dense(i) for i in range(wl.n_src)])
         b = np.broadcast_to(b, (wl.n_omega,) + b.shape).copy()
         cols = np.array([wl.monitors[w][i].col for w in range(wl.n_omega) for i in range(wl.n_src)], np.int32)
@@ -250,8 +253,22 @@ def main():
         ms = sum(a.elapsed_time(b) for a, b in ev)
         return ms, clk
 
+    # ---- launch parameters: library defaults, or measured by the autotuner (not timed) ----
+    opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form)
+    tuned = None
+    if args.autotune:
+        from paper_2307_05388_gb300 import autotune as AT
+        key = AT.problem_key_for(wl.nx, wl.ny, wl.dx, wl.n_omega, wl.n_src, wl.box, opts)
+        t_tune = time.perf_counter()
+        res = AT.tune(lambda o: make_problem(FD.MODE_MIXED, o), eps_of(rho0), base=opts,
+                      cache_path=args.autotune, key=key)
+        opts = res.options
+        tuned = {"params": res.params, "cached": res.cached, "candidates": len(res.trials),
+                 "seconds": time.perf_counter() - t_tune}
+    form = opts.tensor_form
+
     # ---- cached mixed-precision arm (the headline) --------------------------
-    prob = make_problem(FD.MODE_MIXED)
+    prob = make_problem(FD.MODE_MIXED, opts)
     t_setup = time.perf_counter()
     prob.iteration(eps_of(rho0))
     torch.cuda.synchronize()
@@ -320,12 +337,12 @@ def main():
     roof_tc = None
     if "lu_schur_tc" in kern:
         d_tc = kern["lu_schur_tc"]
-        mult = {1: 1, 2: 3, 3: 6}[args.tensor_form]
-        peak_tc = pk["bf16"] * (1.0 if args.tensor_form == 3 else 0.5)
+        mult = {1: 1, 2: 3, 3: 6}[form]
+        peak_tc = pk["bf16"] * (1.0 if form == 3 else 0.5)
         ach = d_tc["flops"] / (d_tc["ms"] / 1e3) / 1e12
         roof_tc = {"kernel": "lu_schur_tc", "bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
                    "tensor_op_tflops": ach * mult, "peak": peak_tc, "frac": ach * mult / peak_tc, "traffic": None,
-                   "peak_source": f"{pk['src']} bf16 dense GEMM peak" + ("" if args.tensor_form == 3 else " x 0.5 (TF32)"),
+                   "peak_source": f"{pk['src']} bf16 dense GEMM peak" + ("" if form == 3 else " x 0.5 (TF32)"),
                    "note": f"achieved counts 8 flops per complex multiply-add; the operand form issues {mult}x "
                            "as many tensor flops (tile padding not counted)"}
     launches_per_step = sum(v["launches"] for v in kern.values()) / prof_steps
@@ -383,7 +400,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic (seeded design density; the paper's devices are not published)",
-            "config": dict(workload_config(wl), update_matrices=TENSOR_FORMS[args.tensor_form]), "clocks": clk,
+            "config": dict(workload_config(wl), update_matrices=TENSOR_FORMS[form],
+                           launch_parameters={"tensor_min_m": opts.tensor_min_m,
+                                              "tensor_min_tiles": opts.tensor_min_tiles,
+                                              "leaf_area": opts.leaf_area, "autotuned": tuned}),
+            "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * bw * bh,
                     "d2h_bytes_per_step": 8 * (bw * bh + 1)},
             "gpu_launches": int(round(launches_per_step * args.steps)),

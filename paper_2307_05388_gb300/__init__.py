@@ -1,7 +1,8 @@
 """GB300-native cached direct solves for FDFD adjoint inverse design (arXiv 2307.05388).
 
 The compute path is libfdfd.so (CUDA, sm_103a) behind the C ABI in include/fdfd.h;
-`fdfd` is its Python binding and `autograd` the torch.autograd.Function built on it.
+`fdfd` is its Python binding, `autograd` the torch.autograd.Function built on it and
+`autotune` the measured choice of the factorisation's launch parameters.
 Importing `fdfd` raises when the library has not been built.
 """
-__all__ = ["fdfd", "autograd", "build"]
+__all__ = ["fdfd", "autograd", "autotune", "build"]
