@@ -35,10 +35,17 @@ rho~_i = sum_j w_ij rho_j / sum_j w_ij with w_ij = max(0, R - |x_i - x_j|)
 rho^ = (tanh(b e) + tanh(b (rho~ - e))) / (tanh(b e) + tanh(b (1 - e))),
 eps = eps_lo + rho^ (eps_hi - eps_lo), and the chain rule back to rho.
 
+Eigenmode sources (Sec. III's multi-mode devices): guided modes of an
+x-invariant cross-section eps(y) as eigenvectors of the y-part of the same
+stencil (slab_modes).
+
 Pins (tests/test_oracle.py): dense LAPACK solve on small grids, plane-wave
 dispersion of the Yee stencil, plate-mode propagation constant and PML
 absorption, reciprocity of the symmetrised operator, the bilinear transpose
-identity, manufactured solutions, and central finite differences of F.
+identity, manufactured solutions, and central finite differences of F; for
+the modes, the closed-form spectrum of a uniform line, the continuum slab
+dispersion relation (second-order convergence), the mode count of the slab's
+V number, and propagation of a mode through the 2D operator.
 """
 from __future__ import annotations
 
@@ -285,6 +292,46 @@ def filter_project_grad(rho: np.ndarray, g_eps: np.ndarray, radius: float, beta:
     """dF/drho from dF/deps by the chain rule through the projection and the filter."""
     rt = density_filter(rho, radius)
     return density_filter_adjoint(g_eps * (eps_hi - eps_lo) * projection_slope(rt, beta, eta), radius)
+
+
+# ---------------------------------------------------------------------------
+# Eigenmode sources (Sec. III: the multi-mode devices launch and monitor
+# waveguide modes; the paper does not say how they are computed)
+# ---------------------------------------------------------------------------
+def mode_sign(phi: np.ndarray) -> np.ndarray:
+    """Sign convention of a mode profile: the first entry whose magnitude reaches half the
+    largest is positive."""
+    phi = np.asarray(phi, dtype=np.float64)
+    j = int(np.argmax(np.abs(phi) >= 0.5 * np.max(np.abs(phi))))
+    return phi if phi[j] > 0 else -phi
+
+
+def slab_modes(eps_line: np.ndarray, k0dx: float, n_modes: int):
+    """Modes of an x-invariant guide eps[i, j] = eps_line[j] on the grid of Eq. 1-2 (no PML on the
+    cross-section, PEC one cell beyond both ends, as in assemble with npml_y = 0).
+
+    Source-free fields E[i, j] = phi[j] exp(-i theta i) of the operator A satisfy
+        (k0dx^2 diag(eps_line) + D2) phi = mu phi,   D2 = tridiag(1, -2, 1),
+        mu = 2 - 2 cos theta = 4 sin^2(theta / 2)
+    (the x-part of the stencil acting on exp(-i theta i)).  The n_modes largest eigenvalues mu
+    are the most strongly guided modes; a mode is bound when mu > k0dx^2 max(eps at both ends).
+    Library step: SciPy's symmetric tridiagonal eigensolver (LAPACK).
+
+    Returns (mu [n_modes], descending; theta [n_modes], NaN where mu is not in (0, 4);
+    phi [n_modes, ny], unit 2-norm, signs by mode_sign).
+    """
+    import scipy.linalg as sla
+    eps_line = np.asarray(eps_line, dtype=np.float64)
+    ny = eps_line.size
+    d = k0dx ** 2 * eps_line - 2.0
+    e = np.ones(ny - 1)
+    mu, V = sla.eigh_tridiagonal(d, e, select="i", select_range=(ny - n_modes, ny - 1))
+    order = np.argsort(-mu)
+    mu = mu[order]
+    phi = np.stack([mode_sign(V[:, k] / np.linalg.norm(V[:, k])) for k in order])
+    with np.errstate(invalid="ignore"):
+        theta = np.where((mu > 0) & (mu < 4), 2.0 * np.arcsin(np.sqrt(np.clip(mu, 0, 4)) / 2.0), np.nan)
+    return mu, theta, phi
 
 
 def rel_err(x, ref) -> float:

@@ -256,3 +256,96 @@ def test_filter_project_chain_rule_central_differences():
         e[i, j] = step
         fd = (F(rho + e) - F(rho - e)) / (2 * step)
         assert abs(fd - g[i, j]) < 1e-6 * max(1.0, abs(g[i, j]))
+
+
+# ---------------------------------------------------------------------------
+# Eigenmode sources
+# ---------------------------------------------------------------------------
+def test_slab_modes_uniform_line_closed_form():
+    """Uniform line: mu_q = k0dx^2 eps - 4 sin^2(q pi / (2 (n + 1))), phi_q ~ sin(q pi (j + 1) / (n + 1)),
+    q = 1, 2, ... (the Dirichlet second difference).  Pins the stencil, its sign and the PEC ends."""
+    n, eps, k0dx = 37, 2.085, 2 * np.pi * 0.04 / 1.55
+    mu, theta, phi = O.slab_modes(np.full(n, eps), k0dx, 4)
+    q = np.arange(1, 5)
+    np.testing.assert_allclose(mu, k0dx ** 2 * eps - 4 * np.sin(q * np.pi / (2 * (n + 1))) ** 2, rtol=0, atol=1e-13)
+    for k in range(4):
+        s = np.sin((k + 1) * np.pi * (np.arange(n) + 1) / (n + 1))
+        np.testing.assert_allclose(phi[k], O.mode_sign(s / np.linalg.norm(s)), atol=1e-10)
+    prop = mu > 0                                   # evanescent along x where mu <= 0: theta is NaN
+    assert prop[:2].all() and not prop[3] and np.isnan(theta[~prop]).all()
+    np.testing.assert_allclose(4 * np.sin(theta[prop] / 2) ** 2, mu[prop], rtol=1e-12)
+
+
+def _slab(dx, d=0.48, width=4.0):
+    ncore = int(round(d / dx))
+    ny = int(round(width / dx))
+    ny += (ny - ncore) % 2
+    eps = np.full(ny, W.EPS_SIO2)
+    a = (ny - ncore) // 2
+    eps[a:a + ncore] = W.EPS_SI
+    return eps
+
+
+def _slab_neff_continuum(m, d=0.48, lam=1.55):
+    """TE modes of a symmetric slab: tan(kappa d / 2 - m pi / 2) = gamma / kappa (textbook)."""
+    from scipy.optimize import brentq
+    n1, n2, k0 = np.sqrt(W.EPS_SI), np.sqrt(W.EPS_SIO2), 2 * np.pi / lam
+
+    def f(ne):
+        ka, ga = k0 * np.sqrt(n1 ** 2 - ne ** 2), k0 * np.sqrt(ne ** 2 - n2 ** 2)
+        return np.tan(ka * d / 2 - m * np.pi / 2) - ga / ka
+    xs = np.linspace(n2 + 1e-9, n1 - 1e-9, 40001)
+    v = f(xs)
+    for a, b, fa, fb in zip(xs[:-1], xs[1:], v[:-1], v[1:]):
+        if np.sign(fa) != np.sign(fb) and abs(fa) < 50 and abs(fb) < 50:
+            return brentq(f, a, b)
+    raise AssertionError("no root")
+
+
+def test_slab_modes_converge_to_the_continuum_dispersion_at_second_order():
+    """480 nm Si slab in SiO2 at 1.55 um: the grid's effective indices theta / k0dx approach the
+    continuum TE0 / TE1 roots with error ~ dx^2 (ratio 4 per halving); the Richardson value agrees
+    to 1e-4.  A wrong eps term, D2 sign or mu -> theta relation breaks the limit."""
+    for m in (0, 1):
+        ref = _slab_neff_continuum(m)
+        errs = []
+        for dx in (0.02, 0.01):
+            _, theta, _ = O.slab_modes(_slab(dx), 2 * np.pi * dx / 1.55, 2)
+            errs.append(theta[m] / (2 * np.pi * dx / 1.55) - ref)
+        assert 3.5 < errs[0] / errs[1] < 4.5
+        assert abs((4 * errs[1] - errs[0]) / 3) < 1e-4
+
+
+def test_slab_mode_count_parity_and_orthonormality():
+    """V = (k0 d / 2) sqrt(n1^2 - n2^2) = 3.08 gives floor(2 V / pi) + 1 = 2 bound TE modes; TE0 even,
+    TE1 odd about the slab centre; profiles orthonormal."""
+    dx = 0.02
+    eps = _slab(dx)
+    k0dx = 2 * np.pi * dx / 1.55
+    mu, _, phi = O.slab_modes(eps, k0dx, 4)
+    bound = mu > k0dx ** 2 * W.EPS_SIO2
+    V = (np.pi / 1.55 * 0.48) * np.sqrt(W.EPS_SI - W.EPS_SIO2)
+    assert bound.sum() == int(np.floor(2 * V / np.pi)) + 1 == 2
+    np.testing.assert_allclose(phi[0], phi[0][::-1], atol=1e-12)
+    np.testing.assert_allclose(phi[1], -phi[1][::-1], atol=1e-12)
+    np.testing.assert_allclose(phi @ phi.T, np.eye(4), atol=1e-12)
+
+
+def test_slab_mode_propagates_through_the_2d_operator():
+    """A guide along x (PEC walls in y, PML in x) fed by a mode on one column: the field stays
+    phi(y) u(x) and advances by exp(-i theta) per cell away from the source.  Ties slab_modes to
+    assemble: the cross-section operator is exactly the y-part of A."""
+    nx, npml, dx = 200, 20, 0.04
+    eps_line = _slab(dx, width=2.0)
+    ny = eps_line.size
+    k0dx = 2 * np.pi * dx / 1.55
+    _, theta, phi = O.slab_modes(eps_line, k0dx, 2)
+    for m in (0, 1):
+        b = np.zeros((nx, ny), complex)
+        b[40, :] = phi[m]
+        E = O.Factor(O.assemble(nx, ny, np.tile(eps_line, (nx, 1)), k0dx, (npml, 0))).solve(b.ravel())
+        E = E.reshape(nx, ny)
+        u = E @ phi[m]
+        assert np.max(np.abs(E - u[:, None] * phi[m][None, :])) < 1e-10 * np.max(np.abs(E))
+        ratio = u[61:nx - npml - 20] / u[60:nx - npml - 21]
+        assert np.max(np.abs(ratio - np.exp(-1j * theta[m]))) < 1e-4
