@@ -197,6 +197,34 @@ fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_ad
 /* Applies the FP64 operator: y = A x (transpose 0) or A^T x, all systems. */
 fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose);
 
+/* Guided modes of an x-invariant cross-section, for eigenmode sources and mode
+ * monitors (the multi-mode devices of Sec. III).  Host-only: needs no context and
+ * no GPU, and touches no device memory.
+ *
+ * A guide eps[i][j] = eps_line[j] carries source-free fields
+ * E[i][j] = phi[j] exp(-i theta i) of the operator of Eq. 1-2 when
+ * (k0dx^2 diag(eps_line) + tridiag(1, -2, 1)) phi = mu phi with
+ * mu = 4 sin^2(theta / 2): the y-part of the stencil with PEC one cell beyond
+ * both ends and no PML on the cross-section (a bound mode has decayed before it).
+ *
+ *   ny        cells of the cross-section (>= 1)
+ *   k0dx      free-space wavenumber times the cell size
+ *   eps_line  [ny] relative permittivity along y (host)
+ *   n_modes   1..ny: the n_modes largest mu are returned
+ *   mu        [n_modes] out (host), descending; a mode is bound when
+ *             mu > k0dx^2 max(eps_line[0], eps_line[ny-1])
+ *   theta     [n_modes] out (host) or NULL: propagation constant times dx,
+ *             NaN where mu is outside (0, 4) (no propagation along x on the grid)
+ *   phi       [n_modes][ny] out (host), unit 2-norm, sign fixed so that the
+ *             first entry whose magnitude reaches half the largest is positive
+ *
+ * Method: bisection on Sturm counts for mu (full double precision), inverse
+ * iteration with partial pivoting for phi.  Errors: FDFD_ERR_ARG for sizes out
+ * of range, NULL eps_line/mu/phi or non-finite inputs; FDFD_ERR_PIVOT if an
+ * inverse iteration breaks down. */
+fdfd_status fdfd_slab_modes(int ny, double k0dx, const double* eps_line, int n_modes, double* mu,
+                            double* theta, double* phi);
+
 /* Replaces the solve options (ir_tol, ir_max_iter, gmres_restart) at run time.
  * mode, growth_bound, leaf_area, pivoting and the tensor_* fields are fixed at
  * creation and ignored here. */

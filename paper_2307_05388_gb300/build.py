@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdfd.so")
-SOURCES = ["api.cu", "factor.cu", "solve.cu", "vec.cu", "design.cu", "tc_schur.cu", "plan.cpp"]
+SOURCES = ["api.cu", "factor.cu", "solve.cu", "vec.cu", "design.cu", "tc_schur.cu", "plan.cpp", "modes.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

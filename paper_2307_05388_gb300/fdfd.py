@@ -27,7 +27,8 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
-           "fdfd_selftest_wait", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint"]
+           "fdfd_selftest_wait", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
+           "fdfd_slab_modes"]
 
 
 class Grid(C.Structure):
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_filter_project.argtypes = [vp, vp, d, d, d, d, d, vp, vp]
     lib.fdfd_filter_project_adjoint.argtypes = [vp, vp, vp, d, vp]
     lib.fdfd_selftest_schur_tc.argtypes = [vp, vp, i, i, i, i]
+    lib.fdfd_slab_modes.argtypes = [i, d, vp, i, vp, vp, vp]
     lib.fdfd_last_error.argtypes = [vp]
     lib.fdfd_last_error.restype = C.c_char_p
     lib.fdfd_destroy.argtypes = [vp]
@@ -129,6 +131,25 @@ def _ptr(t: torch.Tensor | None):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return C.c_void_p(t.data_ptr())
+
+
+def slab_modes(eps_line, k0dx: float, n_modes: int):
+    """Guided modes of an x-invariant cross-section (host call, no GPU): (mu, theta, phi).
+
+    eps_line: [ny] relative permittivity along y; mu [n_modes] descending, theta [n_modes]
+    (propagation constant times dx, NaN where the mode does not propagate along x), phi
+    [n_modes, ny] unit-norm profiles.  A mode source on column i is b[i, :] = phi[m]; the
+    matching monitor profile is g = phi[m]."""
+    eps_line = np.ascontiguousarray(np.asarray(eps_line, dtype=np.float64).ravel())
+    ny = eps_line.size
+    mu = np.empty(n_modes)
+    theta = np.empty(n_modes)
+    phi = np.empty((n_modes, ny))
+    st = _lib.fdfd_slab_modes(ny, float(k0dx), eps_line.ctypes.data, int(n_modes), mu.ctypes.data,
+                              theta.ctypes.data, phi.ctypes.data)
+    if st != FDFD_OK:
+        raise FdfdError(st, "fdfd_slab_modes rejected its arguments")
+    return mu, theta, phi
 
 
 class Solver:
