@@ -173,9 +173,14 @@ def _store_cache(path: str, key: str, base: dict, params: dict, trials: list):
                             for t in trials]}
     d = os.path.dirname(os.path.abspath(path))
     fd, tmp = tempfile.mkstemp(prefix=".autotune", dir=d)
-    with os.fdopen(fd, "w") as f:
-        json.dump(data, f, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    try:
+        with os.fdopen(fd, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
 
 
 def tune(make_problem: Callable[[fdfd.Options], object], eps_design: torch.Tensor,
@@ -196,6 +201,8 @@ def tune(make_problem: Callable[[fdfd.Options], object], eps_design: torch.Tenso
     stored under the key of the first problem built (``problem_key``).
     Raises RuntimeError if no candidate is admissible.
     """
+    if steps < 1 or warmup < 0:
+        raise ValueError("steps must be >= 1 and warmup >= 0")
     base = base if base is not None else fdfd.default_options()
     if base.mode != fdfd.MODE_MIXED:
         raise ValueError("the tuner chooses parameters of the mixed-precision path (mode 0)")

@@ -198,3 +198,10 @@ def test_key_before_any_solver_matches_the_solver_key():
         assert AT.problem_key(s, 2, device_tag="dev") == k
     finally:
         s.close()
+
+
+def test_bad_step_counts():
+    with pytest.raises(ValueError):
+        _run(_model, steps=0)
+    with pytest.raises(ValueError):
+        _run(_model, warmup=-1)
