@@ -195,3 +195,53 @@ def test_create_rejects_bad_arguments():
         fd.Solver(10, 10, 0.05, [4.0], 2, box=(5, 5, 8, 8))  # box outside the grid
     with pytest.raises(fd.FdfdError):
         fd.Solver(10, 10, 0.05, [-1.0], 2)
+
+
+@pytest.mark.parametrize("nx,ny,npml,box,leaf,binary", [(30, 30, 4, (8, 8, 14, 14), 16, False),
+                                                         (44, 36, 6, (10, 8, 24, 20), 32, True)])
+def test_symmetric_ldlt_in_plan_order_without_pivoting(nx, ny, npml, box, leaf, binary):
+    """The premise of a complex-symmetric variant: D A (symmetric by reciprocity) factors as
+    L diag(d) L^T in the plan's elimination order with no pivoting at all, multifrontally (each
+    front's update matrix extend-added into its parent), with modest growth.  Checked by
+    rebuilding P^T (D A) P from the factors densely."""
+    k0dx = 2 * np.pi * 0.04 / 1.55
+    rng = np.random.default_rng(nx)
+    eps = np.full((nx, ny), W.EPS_SIO2)
+    x0, y0, w, h = box
+    rho = rng.uniform(0, 1, (w, h))
+    eps[x0:x0 + w, y0:y0 + h] += W.DELTA_EPS * ((rho > 0.5) if binary else rho)
+    S = (O.symmetrizer(nx, ny, k0dx, npml)[:, None] * O.assemble(nx, ny, eps, k0dx, npml).toarray())
+    fronts = _plan(nx, ny, box, leaf)
+    n = nx * ny
+    piv = np.concatenate([f["idx"][:f["k"]] for f in fronts])
+    pos = np.empty(n, int)
+    pos[piv] = np.arange(n)
+    L = np.eye(n, dtype=complex)
+    d = np.zeros(n, complex)
+    upd = {}
+    growth = 0.0
+    for fi, f in enumerate(fronts):
+        idx, k = f["idx"], f["k"]
+        F = np.zeros((len(idx), len(idx)), complex)
+        for a in range(k):                         # entries whose earlier variable is a pivot here
+            for b_, q in enumerate(idx):
+                if pos[q] >= pos[idx[a]]:
+                    F[a, b_] = S[idx[a], q]
+                    F[b_, a] = S[q, idx[a]]
+        loc = {c: a for a, c in enumerate(idx)}
+        for c, (cidx, cS) in list(upd.items()):
+            if fronts[c]["parent"] == fi:
+                ia = [loc[x] for x in cidx]
+                F[np.ix_(ia, ia)] += cS
+                del upd[c]
+        for j in range(k):
+            l = F[j + 1:, j] / F[j, j]
+            growth = max(growth, float(np.abs(l).max()) if l.size else 0.0)
+            F[j + 1:, j + 1:] -= np.outer(l, F[j, j + 1:])
+            d[pos[idx[j]]] = F[j, j]
+            L[pos[idx[j + 1:]], pos[idx[j]]] = l
+        upd[fi] = (idx[k:], F[k:, k:].copy())
+    Sp = S[np.ix_(piv, piv)]
+    assert np.allclose(Sp, Sp.T, rtol=0, atol=1e-12)
+    assert np.linalg.norm(L @ np.diag(d) @ L.T - Sp) <= 1e-11 * np.linalg.norm(Sp)
+    assert growth < 1e4
