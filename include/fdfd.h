@@ -116,6 +116,11 @@ typedef struct {
                                   8 pivots at least each); if even then it fills less than half
                                   of them, its update matrices run SIMT.  1 = never split. */
 } fdfd_options;
+/* fdfd_create rejects a mode outside fdfd_mode with FDFD_ERR_ARG and clamps the
+ * other fields: gmres_restart to 1..16, ir_max_iter and tensor_min_tiles to >= 0,
+ * tensor_min_m to >= 1; leaf_area < 1, tensor_form outside 0..3, and ir_tol or
+ * growth_bound that are not positive numbers take their defaults; any nonzero
+ * pivoting means 1. */
 
 typedef struct {
   long long sf;                /* symbolic factorisations performed */

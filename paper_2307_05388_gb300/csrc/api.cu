@@ -1346,6 +1346,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
       (design.x0 < 0 || design.y0 < 0 || design.x0 + design.w > grid.nx || design.y0 + design.h > grid.ny))
     return FDFD_ERR_ARG;
   if ((long long)grid.nx * grid.ny * 5 >= (1LL << 31)) return FDFD_ERR_ARG;
+  if (opt && (opt->mode < FDFD_MODE_MIXED || opt->mode > FDFD_MODE_PLAIN)) return FDFD_ERR_ARG;
   for (int w = 0; w < n_omega; ++w)
     if (!(k0_host[w] > 0)) return FDFD_ERR_ARG;
   fdfd_ctx* c = new fdfd_ctx();
@@ -1369,6 +1370,12 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.tensor_min_m < 1) c->opt.tensor_min_m = 1;
   if (c->opt.tensor_min_tiles < 0) c->opt.tensor_min_tiles = 0;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
+  {
+    fdfd_options def;
+    fdfd_default_options(&def);
+    if (!(c->opt.ir_tol > 0)) c->opt.ir_tol = def.ir_tol;
+    if (!(c->opt.growth_bound > 0)) c->opt.growth_bound = def.growth_bound;
+  }
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   *out = c;
   return FDFD_OK;

@@ -195,6 +195,13 @@ def test_create_rejects_bad_arguments():
         fd.Solver(10, 10, 0.05, [4.0], 2, box=(5, 5, 8, 8))  # box outside the grid
     with pytest.raises(fd.FdfdError):
         fd.Solver(10, 10, 0.05, [-1.0], 2)
+    with pytest.raises(fd.FdfdError):
+        fd.Solver(10, 10, 0.05, [4.0], 2, options=fd.default_options(mode=3))   # no such mode
+    # out-of-range options are clamped, not rejected
+    s = fd.Solver(10, 10, 0.05, [4.0], 2, options=fd.default_options(ir_tol=float("nan"), growth_bound=-1.0,
+                                                                      gmres_restart=99, tensor_form=9))
+    s.analyze()
+    s.close()
 
 
 @pytest.mark.parametrize("nx,ny,npml,box,leaf,binary", [(30, 30, 4, (8, 8, 14, 14), 16, False),
