@@ -36,7 +36,7 @@ def test_autotune_c1(tmp_path):
         return AG.DesignProblem(s, eps_bg, b, cols, g)
 
     path = str(tmp_path / "tune.json")
-    search = (("tensor_form", (3, 2)), ("tensor_min_m", (128, 1)))
+    search = (("tensor_form", (3, 2)), ("tensor_min_m", (128, 256)))   # 256: C1's fronts all SIMT
     res = AT.tune(make, U.eps_design_tensor(wl, wl.rho), search=search, steps=2, warmup=1, cache_path=path)
     ok = [t for t in res.trials if t.ok]
     print("autotune c1:", [(t.params, t.ms, t.status) for t in res.trials])
