@@ -349,3 +349,31 @@ def test_slab_mode_propagates_through_the_2d_operator():
         assert np.max(np.abs(E - u[:, None] * phi[m][None, :])) < 1e-10 * np.max(np.abs(E))
         ratio = u[61:nx - npml - 20] / u[60:nx - npml - 21]
         assert np.max(np.abs(ratio - np.exp(-1j * theta[m]))) < 1e-4
+
+
+def test_mode_overlap_selection_rules_in_a_straight_guide():
+    """Straight symmetric guide (PEC walls in y, PML in x), TE0 launched: the TE1 overlap vanishes by
+    parity, the TE0 overlap keeps its modulus along the guide (lossless, single mode content), and
+    the adjoint gradient of F = |o_TE1|^2 is zero (F is stationary at 0)."""
+    nx, npml, dx = 160, 20, 0.04
+    eps_line = _slab(dx, width=2.0)
+    ny = eps_line.size
+    k0dx = 2 * np.pi * dx / 1.55
+    _, _, phi = O.slab_modes(eps_line, k0dx, 2)
+    fac = O.Factor(O.assemble(nx, ny, np.tile(eps_line, (nx, 1)), k0dx, (npml, 0)))
+    b = np.zeros((nx, ny), complex)
+    b[30, :] = phi[0]
+    E = fac.solve(b.ravel())
+    mags = []
+    for col in range(60, nx - npml - 10, 10):
+        g0 = np.zeros((nx, ny))
+        g0[col] = phi[0]
+        g1 = np.zeros((nx, ny))
+        g1[col] = phi[1]
+        assert abs(O.overlap(E, g1.ravel())) < 1e-12 * abs(O.overlap(E, g0.ravel()))
+        mags.append(abs(O.overlap(E, g0.ravel())))
+    assert (max(mags) - min(mags)) / np.mean(mags) < 1e-4
+    g1 = np.zeros((nx, ny))
+    g1[100] = phi[1]
+    Ea = fac.solve_T(O.adjoint_source(E, g1.ravel()))
+    assert np.max(np.abs(O.grad_eps(E, Ea, k0dx))) < 1e-12
