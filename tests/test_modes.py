@@ -87,3 +87,12 @@ def test_bad_arguments():
         fd.slab_modes(np.array([1.0, np.nan, 1.0]), 0.2, 1)
     with pytest.raises(fd.FdfdError):
         fd.slab_modes(np.ones(4), float("inf"), 1)
+
+
+def test_full_height_cross_section():
+    """A cross-section as tall as the largest grid (1760 cells, 50 nm): three modes of a 480 nm
+    guide, against the oracle."""
+    dx = 0.05
+    eps = np.full(1760, W.EPS_SIO2)
+    eps[870:880] = W.EPS_SI
+    _check(eps, 2 * np.pi * dx / 1.31, 3)
