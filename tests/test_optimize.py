@@ -32,3 +32,47 @@ def test_lbfgsb_minimise_and_callback():
                            maximize=False, callback=lambda k, f, x: seen.append(f))
     np.testing.assert_allclose(rho.numpy(), c.numpy(), atol=1e-6)
     assert F == pytest.approx(0.0, abs=1e-10) and seen and seen[-1] <= seen[0]
+
+
+def _oracle_problem():
+    import workloads as W
+    from paper_2307_05388_gb300 import autograd as AG
+    from tests._oracle_solver import OracleSolver
+    wl = W.make_small(26, 22, 4, (8, 6, 8, 7), n_omega=2, n_src=1, seed=41)
+    s = OracleSolver(wl.nx, wl.ny, wl.dx, 2 * np.pi / np.asarray(wl.wavelengths), wl.npml, wl.box)
+    b = np.stack([wl.source_dense(i) for i in range(wl.n_src)])
+    b = np.broadcast_to(b, (wl.n_omega,) + b.shape).copy()
+    cols = np.array([wl.monitors[w][i].col for w in range(wl.n_omega) for i in range(wl.n_src)], np.int32)
+    g = np.stack([wl.monitors[w][i].values for w in range(wl.n_omega) for i in range(wl.n_src)])
+    prob = AG.DesignProblem(s, torch.from_numpy(wl.eps_bg.reshape(-1).copy()), torch.from_numpy(b),
+                            torch.from_numpy(cols), torch.from_numpy(g.astype(np.complex128)))
+    return wl, prob
+
+
+def test_density_objective_gradient_matches_central_differences():
+    """The chain filter -> projection -> solver Function -> objective, through both autograd
+    Functions, with the oracle standing in for the library (host plumbing only)."""
+    import workloads as W
+    wl, prob = _oracle_problem()
+    f = OPT.density_objective(prob, 1.5, 4.0, 0.5, W.EPS_SIO2, W.EPS_SI)
+    rho = torch.from_numpy(wl.rho.reshape(-1).copy())
+    F, g = f(rho)
+    assert g.shape == rho.shape and float(F) > 0
+    h = 1e-6
+    for p in (0, 17, 55):
+        e = torch.zeros_like(rho)
+        e[p] = h
+        Fp, _ = f(rho + e)
+        Fm, _ = f(rho - e)
+        fd = (float(Fp) - float(Fm)) / (2 * h)
+        assert abs(float(g[p]) - fd) <= 1e-5 * max(abs(fd), 1e-3 * float(g.abs().max()))
+
+
+def test_lbfgsb_on_the_design_objective_ascends():
+    import workloads as W
+    wl, prob = _oracle_problem()
+    f = OPT.density_objective(prob, 1.5, 4.0, 0.5, W.EPS_SIO2, W.EPS_SI)
+    rho0 = torch.from_numpy(wl.rho.reshape(-1).copy())
+    F0, _ = f(rho0)
+    rho, F, res = OPT.lbfgsb(f, rho0, maxiter=6)
+    assert F > float(F0) and float(rho.min()) >= 0.0 and float(rho.max()) <= 1.0
