@@ -205,3 +205,34 @@ def test_bad_step_counts():
         _run(_model, steps=0)
     with pytest.raises(ValueError):
         _run(_model, warmup=-1)
+
+
+def test_tuner_drives_the_real_design_problem_class():
+    """The tuner around autograd.DesignProblem (the class the bench passes it), with the oracle
+    standing in for the library and a virtual clock that prefers TF32 hi+lo."""
+    import numpy as np
+    import workloads as W
+    from tests._oracle_solver import OracleSolver
+    wl = W.make_small(20, 18, 3, (6, 5, 6, 6), n_omega=1, n_src=1, seed=3)
+    b = torch.from_numpy(wl.source_dense(0).reshape(1, 1, -1).copy())
+    cols = torch.tensor([wl.monitors[0][0].col], dtype=torch.int32)
+    g = torch.from_numpy(wl.monitors[0][0].values.astype(np.complex128).reshape(1, -1))
+    eps_bg = torch.from_numpy(wl.eps_bg.reshape(-1).copy())
+    clock = Clock()
+    built = []
+
+    class Timed(AG.DesignProblem):
+        def iteration(self, eps_design, grad_out=None):
+            clock.t += 2.0 if self.solver.options.tensor_form == 2 else 3.0
+            return super().iteration(eps_design, grad_out)
+
+    def make(opts):
+        built.append(opts.tensor_form)
+        s = OracleSolver(wl.nx, wl.ny, wl.dx, 2 * np.pi / np.asarray(wl.wavelengths), wl.npml, wl.box, opts)
+        return Timed(s, eps_bg, b, cols, g)
+
+    eps_d = torch.from_numpy(np.ascontiguousarray(wl.eps_design(wl.rho)).reshape(-1))
+    res = AT.tune(make, eps_d, search=(("tensor_form", (3, 2)),), steps=2, warmup=1, flush_bytes=0,
+                  event=lambda: FakeEvent(clock), sync=lambda: None)
+    assert built == [3, 2] and res.params["tensor_form"] == 2
+    assert [t.ms for t in res.trials] == [3.0, 2.0]
