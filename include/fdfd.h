@@ -277,6 +277,14 @@ void fdfd_reset_counters(fdfd_ctx* ctx);
  * is cleared and the context stays usable.  Any other status is a failure. */
 fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx);
 
+/* The same bounded wait as fdfd_selftest_wait, left for the caller to find: the
+ * probe kernel and the copy of the error word back to the host are queued on the
+ * context's stream and the call returns FDFD_OK without synchronising.  Once the
+ * stream has run them, the next call that checks the error word (fdfd_solve,
+ * fdfd_solve_raw_noalloc, fdfd_selftest_*) returns FDFD_ERR_TIMEOUT and clears
+ * it, exactly as after a sweep whose wait gave up; the context stays usable. */
+fdfd_status fdfd_selftest_wait_async(fdfd_ctx* ctx);
+
 /* Self-test of the tensor-core update-matrix product (Sec. II: S = F22 - L21 U12 of
  * a front), on one caller-supplied front: front_dev is a (k + m) x ld row-major
  * complex64 matrix in device memory (8-byte aligned, ld >= k + m, interleaved
@@ -314,9 +322,15 @@ void fdfd_destroy(fdfd_ctx* ctx);
  * before any stream capture.  Every call shares the array and leaves its last
  * contents there (nothing in it needs to start at zero); calls that overlap on
  * the GPU race on it and must be serialised by the caller.  Requires an earlier
- * fdfd_factor (FDFD_ERR_STATE otherwise); if that FP32 factorisation exceeded
+ * fdfd_factor (FDFD_ERR_STATE otherwise) and the context's device to be the
+ * current device (FDFD_ERR_STATE otherwise); if that FP32 factorisation exceeded
  * the growth bound, returns FDFD_ERR_PIVOT (fdfd_solve redoes it in FP64, which
- * allocates). */
+ * allocates).  The first call after each factorisation synchronises the stream
+ * once to read the factorisation's growth figure; other calls do not synchronise.
+ * A bounded device wait that gave up earlier (in a factorisation or a sweep)
+ * is reported at entry as FDFD_ERR_TIMEOUT; one that gives up in this call's own
+ * sweeps is reported by the next call on the context that checks it (this call
+ * only queues the copy of the error word back to the host). */
 fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int transpose);
 /* Size in bytes of the fixed scratch array used by fdfd_solve_raw_noalloc. */
 size_t fdfd_noalloc_scratch_bytes(void);

@@ -43,9 +43,14 @@ Pins (tests/test_oracle.py): dense LAPACK solve on small grids, plane-wave
 dispersion of the Yee stencil, plate-mode propagation constant and PML
 absorption, reciprocity of the symmetrised operator, the bilinear transpose
 identity, manufactured solutions, and central finite differences of F; for
-the modes, the closed-form spectrum of a uniform line, the continuum slab
-dispersion relation (second-order convergence), the mode count of the slab's
-V number, and propagation of a mode through the 2D operator.
+the PML constants, the textbook normal-incidence reflection integral of the
+graded layer (exact by Simpson's rule) and the decay of a guided wave inside
+the layer; for the modes, the closed-form spectrum of a uniform line, the
+continuum slab dispersion relation (second-order convergence), the mode count
+of the slab's V number, and propagation of a mode through the 2D operator; for
+the optimiser updates, closed forms of the sign step and of Adam's first,
+second and constant-gradient steps; for the rank-one finite differences, the
+plain definition (refactoring the perturbed operator).
 """
 from __future__ import annotations
 
@@ -202,6 +207,40 @@ def design_iteration(wl, rho: np.ndarray, eps_of_rho, delta_eps: float):
             g_eps += design_box_of(grad_eps(E, E_adj, k0dx), wl.nx, wl.ny, wl.box)
             fields[(w, s)] = (E, E_adj)
     return F, delta_eps * g_eps, fields
+
+
+def objective_pixel_differences(wl, rho: np.ndarray, pixels, h: float, delta_eps: float) -> np.ndarray:
+    """Central differences (F(rho + h e_p) - F(rho - h e_p)) / (2 h) of the objective of
+    design_iteration at the listed design pixels p (flat indices into the [w, h] box).
+
+    Raising rho_p by t changes eps at the pixel's cell q by t delta_eps, so A changes by
+    d e_q e_q^T with d = -(k0 dx)^2 t delta_eps (Eq. 1-2): a rank-one change.  Each F(rho +- h e_p)
+    is evaluated exactly on the perturbed operator by the Sherman-Morrison identity
+        (A + d e_q e_q^T)^-1 b = x - d x_q / (1 + d u_q) u,   x = A^-1 b,  u = A^-1 e_q,
+    so that the perturbed overlap is o' = o - d x_q (g^T u) / (1 + d u_q) with g^T u = (A^-T g)_q.
+    Library steps: one SuperLU factorisation per wavelength, solves for x and A^-T g per source,
+    and one solve with the unit vectors of all pixels for the u_q = (A^-1)_qq.
+    """
+    x0, y0, bw, bh = wl.box
+    pixels = np.asarray(pixels, dtype=np.int64)
+    cells = (x0 + pixels // bh) * wl.ny + (y0 + pixels % bh)
+    eps = wl.eps_full(rho).reshape(-1)
+    Fp = np.zeros(len(pixels))
+    Fm = np.zeros(len(pixels))
+    for w, k0dx in enumerate(wl.k0dx()):
+        fac = Factor(assemble(wl.nx, wl.ny, eps, k0dx, wl.npml))
+        unit = np.zeros((wl.n, len(pixels)), dtype=np.complex128)
+        unit[cells, np.arange(len(pixels))] = 1.0
+        uqq = fac.solve(unit)[cells, np.arange(len(pixels))]
+        for s in range(wl.n_src):
+            g = wl.monitor_dense(w, s)
+            E = fac.solve(wl.source_dense(s))
+            o = overlap(E, g)
+            gu = fac.solve_T(g)[cells]
+            for sign, acc in ((1.0, Fp), (-1.0, Fm)):
+                d = -k0dx ** 2 * sign * h * delta_eps
+                acc += np.abs(o - d * E[cells] * gu / (1.0 + d * uqq)) ** 2
+    return (Fp - Fm) / (2.0 * h)
 
 
 # ---------------------------------------------------------------------------

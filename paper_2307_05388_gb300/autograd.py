@@ -31,6 +31,7 @@ class DesignProblem:
         self.g = g.contiguous()
         self.weight = weight
         self.factored = False
+        self.version = 0          # factorisations loaded so far (the backward pass checks it)
         x0, y0, w, h = solver.box
         self._box = (x0, y0, w, h)
         self.x = torch.empty_like(self.b)
@@ -45,6 +46,7 @@ class DesignProblem:
             self.factored = True
         else:
             self.solver.refactor_design(eps_design.reshape(-1).contiguous())
+        self.version += 1
 
     def iteration(self, eps_design: torch.Tensor, grad_out: torch.Tensor | None = None):
         """One forward + adjoint design iteration; returns (F, dF/deps_design [w*h])."""
@@ -69,6 +71,7 @@ class FdfdObjective(torch.autograd.Function):
         x = s.solve(prob.b)
         F, o, badj = s.objective(x, prob.cols, prob.g, prob.weight)
         ctx.prob = prob
+        ctx.version = prob.version
         ctx.save_for_backward(x, badj)
         ctx.shape = eps_design.shape
         return F
@@ -76,6 +79,10 @@ class FdfdObjective(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gF: torch.Tensor):
         prob = ctx.prob
+        if prob.version != ctx.version:
+            # the adjoint solve needs the factors of this forward pass's permittivity
+            raise RuntimeError("the solver was refactored after this forward pass; call backward before "
+                               "evaluating the problem again")
         x, badj = ctx.saved_tensors
         s = prob.solver
         xa = s.solve(badj, transpose=True)

@@ -115,6 +115,7 @@ struct fdfd_ctx {
   int* d_flow_ctr = nullptr;       // queue head and per-front counters
   int* d_flow_err = nullptr;       // set by a wait that gave up
   // taps of the design-density filter (offsets and weights) for radius tap_radius
+  int* d_probe = nullptr;          // counter of the deferred wait self-test (never incremented)
   int2* d_taps = nullptr;
   double* d_tapw = nullptr;
   int ntap = 0;
@@ -1786,6 +1787,19 @@ fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx) {
   return check_flow_err(ctx);
 }
 
+fdfd_status fdfd_selftest_wait_async(fdfd_ctx* ctx) {
+  if (!ctx) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  CKS(ensure_runtime(ctx));
+  CKS(check_flow_err(ctx));
+  if (!ctx->d_probe) CK(dalloc(&ctx->d_probe, sizeof(int)));
+  CK(cudaMemsetAsync(ctx->d_probe, 0, sizeof(int), ctx->stream));
+  CK(launch_wait_probe(ctx->d_probe, ctx->d_flow_err, ctx->stream));
+  // the error word comes back with the stream, as after a sweep that gave up
+  CK(cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  return FDFD_OK;
+}
+
 fdfd_status fdfd_profile_enable(fdfd_ctx* ctx, int on) {
   if (!ctx) return FDFD_ERR_ARG;
   if (ctx->device >= 0) CK(cudaStreamSynchronize(ctx->stream));
@@ -1830,7 +1844,7 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   free_ws(ctx);
   free_gm(ctx);
   void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
-                ctx->d_growth_max, ctx->d_flow_err, ctx->d_taps, ctx->d_tapw};
+                ctx->d_growth_max, ctx->d_flow_err, ctx->d_taps, ctx->d_tapw, ctx->d_probe};
   for (void* p : ps) free_ptr(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   drop_graphs(ctx);
@@ -1912,10 +1926,17 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
     return fail(ctx, FDFD_ERR_ARG,
                 "fdfd_solve_raw_noalloc: this solve needs " + std::to_string(vb_bytes + ctr_bytes) +
                     " bytes of scratch; the fixed device array holds " + std::to_string(kNoAllocScratchBytes));
+  // the context's factors, counters and stream live on ctx->device; the array's
+  // address is per device, so the call runs with that device current
   int dev = -1;
   CK(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return fail(ctx, FDFD_ERR_STATE, "fdfd_solve_raw_noalloc: the current device (" + std::to_string(dev) +
+                                         ") is not the context's device (" + std::to_string(ctx->device) + ")");
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return fail(ctx, FDFD_ERR_ARG, "fdfd_solve_raw_noalloc: device index out of range");
+  // a bounded wait that gave up in an earlier sweep or factorisation is reported here
+  CKS(check_flow_err(ctx));
   unsigned char* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -1932,9 +1953,16 @@ fdfd_status fdfd_solve_raw_noalloc(fdfd_ctx* ctx, const double* b_dev, double* x
     // the factorisation's growth figure decides whether FP32 factors may be used;
     // this call cannot redo the factorisation in FP64 (that allocates)
     if (!ctx->growth_ready) CK(cudaStreamSynchronize(ctx->stream));
-    if (!(*ctx->h_growth_max <= ctx->opt.growth_bound))
+    // the same synchronisation brought back the factorisation's error word
+    CKS(check_flow_err(ctx));
+    const float g = *ctx->h_growth_max;
+    if (!(g <= ctx->opt.growth_bound))
       return fail(ctx, FDFD_ERR_PIVOT,
                   "fdfd_solve_raw_noalloc: FP32 factors exceed the growth bound; call fdfd_solve once first");
+    // checked once per factorisation: later calls on the same factors do not synchronise
+    ctx->growth_pending = false;
+    ctx->growth_ready = false;
+    ctx->last_growth = g;
   }
   int* ctr = reinterpret_cast<int*>(scratch + vb_bytes);
   if (use64) CKS(sweeps_in<double2>(ctx, nrhs, transpose, b_dev, x_dev, scratch, ctr));

@@ -27,7 +27,7 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
-           "fdfd_selftest_wait", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
+           "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
            "fdfd_slab_modes"]
 
 
@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_filter_project.argtypes = [vp, vp, d, d, d, d, d, vp, vp]
     lib.fdfd_filter_project_adjoint.argtypes = [vp, vp, vp, d, vp]
     lib.fdfd_selftest_schur_tc.argtypes = [vp, vp, i, i, i, i]
+    lib.fdfd_selftest_wait.argtypes = [vp]
+    lib.fdfd_selftest_wait_async.argtypes = [vp]
     lib.fdfd_slab_modes.argtypes = [i, d, vp, i, vp, vp, vp]
     lib.fdfd_last_error.argtypes = [vp]
     lib.fdfd_last_error.restype = C.c_char_p
@@ -310,6 +312,11 @@ class Solver:
         m = n - k
         self._check(_lib.fdfd_selftest_schur_tc(self._h, C.c_void_p(front.data_ptr()), int(k), int(m),
                                                 int(front.stride(0)), int(planes)), "fdfd_selftest_schur_tc")
+
+    def selftest_wait_async(self) -> int:
+        """Queues the same wait without synchronising; the next call that checks the error word
+        returns 7 (ERR_TIMEOUT).  Returns this call's status (0)."""
+        return int(_lib.fdfd_selftest_wait_async(self._h))
 
     def selftest_wait(self) -> int:
         """Runs one bounded sweep wait on a counter nothing sets; returns the status (7 = gave up as designed)."""

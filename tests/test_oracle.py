@@ -377,3 +377,138 @@ def test_mode_overlap_selection_rules_in_a_straight_guide():
     g1[100] = phi[1]
     Ea = fac.solve_T(O.adjoint_source(E, g1.ravel()))
     assert np.max(np.abs(O.grad_eps(E, Ea, k0dx))) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# PML constants: the graded profile against the textbook reflection integral and
+# against the decay of a guided wave inside the layer
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,npml,k0dx,order,R", [(100, 10, 2 * np.pi * 0.05 / 1.55, 3.0, 1e-8),
+                                                  (340, 20, 2 * np.pi * 0.04 / 1.55, 3.0, 1e-8),
+                                                  (60, 12, 0.3, 2.0, 1e-6),
+                                                  (45, 7, 0.5, 3.0, 1e-4)])
+def test_pml_profile_meets_the_target_reflection(n, npml, k0dx, order, R):
+    """A graded layer of thickness L in front of a PEC wall reflects a normally incident wave by
+    R = exp(-2 k0 int_0^L sigma(x) / (omega eps0) dx) (Taflove and Hagness, Ch. 7), with
+    -Im s = sigma / (omega eps0).  Simpson's rule on the half-cell lattice of the oracle's
+    s values (centres and half points, spacing dx / 2) integrates a polynomial grade of order <= 3
+    exactly, so 2 k0dx int (-Im s) du over each layer must equal -ln R to rounding.  The interior has
+    s = 1, the real part is 1 everywhere, and Im s <= 0 (absorption for e^{+i w t}).  A factor-2
+    slip in sigma_max, a wrong (order + 1), or the layer on the wrong side fails here."""
+    sc, sh = O.pml_stretch(n, npml, k0dx, ln_R=np.log(R), order=order)
+    assert np.all(sc.real == 1.0) and np.all(sh.real == 1.0)
+    assert np.all(sc.imag <= 0.0) and np.all(sh.imag <= 0.0)
+    assert np.all(sc[npml:n - npml] == 1.0) and np.all(sh[npml:n - npml + 1] == 1.0)
+    for hs, cs in ((sh[:npml + 1], sc[:npml]), (sh[n - npml:], sc[n - npml:])):
+        integral = np.sum((-hs.imag[:-1] - 4.0 * cs.imag - hs.imag[1:]) / 6.0)
+        assert abs(2.0 * k0dx * integral + np.log(R)) < 1e-12 * abs(np.log(R))
+    # the grade vanishes toward the interior and is largest at the wall
+    assert abs(sh[0].imag) > abs(sc[0].imag) > abs(sc[npml - 1].imag) > 0.0
+
+
+def test_pml_decay_profile_of_a_guided_wave():
+    """Inside the layer a wave travelling along x with propagation constant kx goes as
+    exp(-i kx int s du), so its amplitude falls by exp(-kx int_0^u (-Im s) du') with depth u; for the
+    cubic grade the exponent is -kx sigma_max' L d^4 / 4 at depth d = u / L.  The plate mode of
+    test_plate_mode_propagation_and_pml, solved with a 30-cell x-PML, follows this law within 3%
+    at depths 0.2 - 0.75 (deeper, the grade is no longer resolved by the grid).  A quadratic grade
+    or sigma_max off by 2 moves the exponent by 50 - 200%."""
+    npml, ny, eps = 30, 7, 12.11
+    nx = 200 + npml
+    k0dx = 2 * np.pi * 0.04 / 1.55
+    A = O.assemble(nx, ny, np.full((nx, ny), eps), k0dx, (npml, 0))
+    mode = np.sin(np.pi * (np.arange(ny) + 1) / (ny + 1))
+    b = np.zeros((nx, ny), complex)
+    b[40, :] = mode
+    E = O.Factor(A).solve(b.ravel()).reshape(nx, ny)
+    Em = E @ mode / (mode @ mode)
+    kx = 2 * np.arcsin(np.sqrt((k0dx ** 2 * eps - 4 * np.sin(np.pi / (2 * (ny + 1))) ** 2) / 4))
+    smax = -4.0 * np.log(1e-8) / (2 * k0dx * npml)      # textbook sigma_max / (omega eps0), m = 3
+    i0 = nx - npml - 1
+    checked = 0
+    for i in range(nx - npml, nx):
+        d = (i + 0.5 - (nx - npml)) / npml
+        if not 0.2 <= d <= 0.75:
+            continue
+        predicted = -kx * smax * npml * d ** 4 / 4.0
+        measured = np.log(abs(Em[i]) / abs(Em[i0]))
+        assert abs(measured - predicted) <= 0.03 * abs(predicted), (d, measured, predicted)
+        checked += 1
+    assert checked >= 15
+
+
+# ---------------------------------------------------------------------------
+# Optimiser updates between iterations (C1-C3, C5 sign step; C4 Adam)
+# ---------------------------------------------------------------------------
+def test_sign_step_values():
+    """rho + step * sign(grad) with sign(0) = 0 (no move), an ascent direction, clipped to [0, 1]."""
+    rho = np.array([0.5, 0.5, 0.5, 0.02, 0.99, 0.0, 1.0])
+    g = np.array([2.0, -1e-300, 0.0, -5.0, 3.0, -1.0, 1.0])
+    out = O.sign_step(rho, g, 0.05)
+    np.testing.assert_array_equal(out, [0.55, 0.45, 0.5, 0.0, 1.0, 0.0, 1.0])
+
+
+def test_adam_first_step_is_lr_times_sign_for_any_scale():
+    """Adam's bias correction makes the first step lr g / (|g| + eps): lr sign(g) up to eps / |g|,
+    whatever the gradient's scale (Kingma and Ba, Sec. 2.1), as an ascent step."""
+    rho = np.full(4, 0.5)
+    for scale in (1e-3, 1.0, 1e4):
+        g = scale * np.array([1.0, -2.0, 0.5, -7.0])
+        out = O.adam_step(rho, g, {}, lr=0.01)
+        np.testing.assert_allclose(out - rho, 0.01 * np.sign(g), rtol=1e-4 / scale, atol=0)
+
+
+def test_adam_second_step_closed_form():
+    """Unrolling two Adam updates gives m^_2 = (b1 g1 + g2) / (1 + b1) and
+    v^_2 = (b2 g1^2 + g2^2) / (1 + b2); the second step is lr m^_2 / (sqrt(v^_2) + eps).  A bias
+    correction with t - 1, or b and 1 - b swapped in a moving average, fails here."""
+    b1, b2, eps, lr = 0.9, 0.999, 1e-8, 0.01
+    g1 = np.array([0.3, -1.0, 2.0, 0.0])
+    g2 = np.array([-0.1, -1.0, 5.0, 0.4])
+    st = {}
+    r1 = O.adam_step(np.full(4, 0.5), g1, st, lr=lr)
+    r2 = O.adam_step(r1, g2, st, lr=lr)
+    mh = (b1 * g1 + g2) / (1 + b1)
+    vh = (b2 * g1 ** 2 + g2 ** 2) / (1 + b2)
+    np.testing.assert_allclose(r2 - r1, lr * mh / (np.sqrt(vh) + eps), rtol=1e-12, atol=1e-15)
+    assert st["t"] == 2
+
+
+def test_adam_constant_gradient_moves_lr_every_step_until_the_bound():
+    """With a constant gradient both bias-corrected moments equal g and g^2 exactly at every t, so
+    each step is lr (to eps / |g|) until the clip at 1 stops the walk."""
+    rho = np.array([0.0, 0.5])
+    g = np.array([3.0, 3.0])
+    st = {}
+    for t in range(60):
+        new = O.adam_step(rho, g, st, lr=0.01)
+        expect = np.minimum(rho + 0.01, 1.0)
+        np.testing.assert_allclose(new, expect, rtol=0, atol=1e-9)
+        rho = new
+    assert rho[1] == 1.0 and abs(rho[0] - 0.6) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Finite differences of F by rank-one updates (the large-grid gradient check)
+# ---------------------------------------------------------------------------
+def test_pixel_differences_by_rank_one_update_match_refactoring():
+    """objective_pixel_differences evaluates F(rho +- h e_p) by Sherman-Morrison on one
+    factorisation; the plain definition refactors the perturbed operator for each F.  Both agree
+    to rounding on several wavelengths and sources, and the difference quotient approaches the
+    adjoint gradient (Eq. 3)."""
+    wl = W.make_small(22, 19, 4, (6, 5, 8, 7), n_omega=2, n_src=2, seed=31)
+    rng = np.random.default_rng(4)
+    pixels = rng.choice(wl.rho.size, 6, replace=False)
+    h = 1e-3
+    fd = O.objective_pixel_differences(wl, wl.rho, pixels, h, W.DELTA_EPS)
+    brute = []
+    for p in pixels:
+        rp, rm = wl.rho.copy(), wl.rho.copy()
+        rp.flat[p] += h
+        rm.flat[p] -= h
+        Fp, _, _ = O.design_iteration(wl, rp, wl.eps_full, W.DELTA_EPS)
+        Fm, _, _ = O.design_iteration(wl, rm, wl.eps_full, W.DELTA_EPS)
+        brute.append((Fp - Fm) / (2 * h))
+    np.testing.assert_allclose(fd, brute, rtol=1e-9, atol=0)
+    _, g, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    np.testing.assert_allclose(fd, g.ravel()[pixels], rtol=1e-5, atol=0)
