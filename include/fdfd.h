@@ -191,6 +191,17 @@ fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const i
                            const double* g_dev, const double* weight_dev, double* o_dev, double* F_dev,
                            double* b_adj_dev);
 
+/* The same with transmission targets (Sec. III-IV: the duplexer's and the mode
+ * multiplexer's objectives are the differences between calculated and target
+ * transmissions, minimised):
+ *   o_s = sum_j g_s[j] x_s[col_s*ny + j],   F = sum_s weight_s (|o_s|^2 - target_s)^2,
+ *   b_adj_s = 2 weight_s (|o_s|^2 - target_s) conj(o_s) g_s on column col_s, zero elsewhere.
+ * target_dev: [n_omega*nrhs] double (device); NULL gives fdfd_objective's F = sum weight |o|^2.
+ * Other arguments as for fdfd_objective. */
+fdfd_status fdfd_objective_target(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev,
+                                  const double* g_dev, const double* weight_dev, const double* target_dev,
+                                  double* o_dev, double* F_dev, double* b_adj_dev);
+
 /* Pixel gradient (Eq. 3) over the design box:
  *   grad[p] (+)= sum_s weight_s * 2 (k0 dx)^2 Re(x_adj_s[p] x_fwd_s[p]),
  * i.e. dF/deps_p = -2 Re{x_adj^T (dA/deps_p) x_fwd} with dA/deps_p = -(k0 dx)^2 e_p e_p^T,
@@ -198,6 +209,28 @@ fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const i
  * weight_dev: [n_omega*nrhs] or NULL; grad_dev: [w*h]; accumulate = 1 adds. */
 fdfd_status fdfd_grad(fdfd_ctx* ctx, const double* x_fwd_dev, const double* x_adj_dev, int nrhs,
                       const double* weight_dev, double* grad_dev, int accumulate);
+
+/* One whole forward + adjoint design iteration in one call (Sec. II; Eq. 3-6):
+ * design refactor with eps_design ([w*h], the box's permittivity), forward solves
+ * of b_dev for every wavelength and source, the objective of fdfd_objective_target
+ * (target_dev NULL: F = sum weight |o|^2) and its adjoint source, transpose solves
+ * on the same factors, and the pixel gradient dF/deps of fdfd_grad.
+ * flags: FDFD_HOST_EPS = eps_design is host memory (copied to the device inside
+ * the call; pinned memory keeps the copy asynchronous); FDFD_HOST_OUT = F_out
+ * (one double) and grad_out ([w*h]) are host memory, and the call returns after
+ * the stream has written them.  Without the flags those pointers are device
+ * memory written on the context's stream.  x_dev, xadj_dev: [n_omega][nrhs][nx*ny]
+ * complex128 device buffers that receive the forward and adjoint fields, or NULL
+ * (context-owned buffers, kept until the next call).  b_dev, cols_dev, g_dev,
+ * weight_dev, target_dev: as for fdfd_solve and fdfd_objective_target.
+ * Requires an earlier fdfd_factor (the full permittivity) and a design box
+ * (FDFD_ERR_STATE); statuses of the steps pass through. */
+#define FDFD_HOST_EPS 1
+#define FDFD_HOST_OUT 2
+fdfd_status fdfd_design_iteration(fdfd_ctx* ctx, const double* eps_design, const double* b_dev, int nrhs,
+                                  const int* cols_dev, const double* g_dev, const double* weight_dev,
+                                  const double* target_dev, double* F_out, double* grad_out, double* x_dev,
+                                  double* xadj_dev, int flags);
 
 /* Applies the FP64 operator: y = A x (transpose 0) or A^T x, all systems. */
 fdfd_status fdfd_apply(fdfd_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int transpose);

@@ -175,6 +175,18 @@ def adjoint_source(E: np.ndarray, g: np.ndarray, weight: float = 1.0) -> np.ndar
     return weight * np.conj(overlap(E, g)) * g
 
 
+def target_objective(o: complex, target: float, weight: float = 1.0) -> float:
+    """Squared transmission error w (|o|^2 - t)^2 of one port (Sec. III-IV: the devices minimise the
+    difference between calculated and target transmissions)."""
+    return weight * (abs(o) ** 2 - target) ** 2
+
+
+def target_adjoint_source(E: np.ndarray, g: np.ndarray, target: float, weight: float = 1.0) -> np.ndarray:
+    """(dF/dE)^T for F = w (|g^T E|^2 - t)^2 (Wirtinger, E* fixed): 2 w (|o|^2 - t) conj(o) g."""
+    o = overlap(E, g)
+    return 2.0 * weight * (abs(o) ** 2 - target) * np.conj(o) * g
+
+
 def grad_eps(E: np.ndarray, E_adj: np.ndarray, k0dx: float) -> np.ndarray:
     """dF/deps_p = -2 Re{E_adj[p] (dA/deps_p) E[p]} = 2 k0dx^2 Re(E_adj[p] E[p]), Eq. 3."""
     return 2.0 * k0dx ** 2 * np.real(E_adj * E)
@@ -185,11 +197,12 @@ def design_box_of(v: np.ndarray, nx: int, ny: int, box) -> np.ndarray:
     return v.reshape(nx, ny)[x0:x0 + w, y0:y0 + h]
 
 
-def design_iteration(wl, rho: np.ndarray, eps_of_rho, delta_eps: float):
+def design_iteration(wl, rho: np.ndarray, eps_of_rho, delta_eps: float, targets=None):
     """One forward + adjoint iteration (Sec. II), all wavelengths and sources.
 
     wl: a workloads.Workload.  Returns (F, dF/drho [w, h], fields) with
-    F = sum_{omega, s} |g_{omega,s}^T E_{omega,s}|^2 and fields[(w, s)] = (E, E_adj).
+    F = sum_{omega, s} |g_{omega,s}^T E_{omega,s}|^2, or with targets[w][s] given the squared
+    transmission error sum_{omega, s} (|g^T E|^2 - t_{omega,s})^2, and fields[(w, s)] = (E, E_adj).
     """
     eps = eps_of_rho(rho)
     F = 0.0
@@ -202,8 +215,12 @@ def design_iteration(wl, rho: np.ndarray, eps_of_rho, delta_eps: float):
             g = wl.monitor_dense(w, s)
             E = fac.solve(b)
             o = overlap(E, g)
-            F += abs(o) ** 2
-            E_adj = fac.solve_T(adjoint_source(E, g))
+            if targets is None:
+                F += abs(o) ** 2
+                E_adj = fac.solve_T(adjoint_source(E, g))
+            else:
+                F += target_objective(o, targets[w][s])
+                E_adj = fac.solve_T(target_adjoint_source(E, g, targets[w][s]))
             g_eps += design_box_of(grad_eps(E, E_adj, k0dx), wl.nx, wl.ny, wl.box)
             fields[(w, s)] = (E, E_adj)
     return F, delta_eps * g_eps, fields

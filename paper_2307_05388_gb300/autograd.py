@@ -19,17 +19,21 @@ class DesignProblem:
 
     eps_bg: float64 [nx*ny] (device); b: complex128 [n_omega, nrhs, nx*ny];
     cols: int32 [n_omega*nrhs] monitor columns; g: complex128 [n_omega*nrhs, ny]
-    monitor profiles; weight: float64 [n_omega*nrhs] or None.
+    monitor profiles; weight: float64 [n_omega*nrhs] or None; target: float64
+    [n_omega*nrhs] transmission targets or None.  Without targets F = sum w |o|^2;
+    with them F = sum w (|o|^2 - target)^2, the squared transmission error that
+    the paper's devices minimise (Sec. III-IV).
     """
 
     def __init__(self, solver: fdfd.Solver, eps_bg: torch.Tensor, b: torch.Tensor, cols: torch.Tensor,
-                 g: torch.Tensor, weight: torch.Tensor | None = None):
+                 g: torch.Tensor, weight: torch.Tensor | None = None, target: torch.Tensor | None = None):
         self.solver = solver
         self.eps_bg = eps_bg.reshape(-1).contiguous()
         self.b = b.contiguous()
         self.cols = cols.contiguous()
         self.g = g.contiguous()
         self.weight = weight
+        self.target = target
         self.factored = False
         self.version = 0          # factorisations loaded so far (the backward pass checks it)
         x0, y0, w, h = solver.box
@@ -53,7 +57,7 @@ class DesignProblem:
         s = self.solver
         self._load(eps_design)
         s.solve(self.b, out=self.x)
-        F, o, badj = s.objective(self.x, self.cols, self.g, self.weight)
+        F, o, badj = s.objective(self.x, self.cols, self.g, self.weight, target=self.target)
         s.solve(badj, transpose=True, out=self.xa)
         # the adjoint source already carries the per-system weights
         g = s.grad(self.x, self.xa, None, out=grad_out)
@@ -69,7 +73,7 @@ class FdfdObjective(torch.autograd.Function):
         s = prob.solver
         prob._load(eps_design.detach())
         x = s.solve(prob.b)
-        F, o, badj = s.objective(x, prob.cols, prob.g, prob.weight)
+        F, o, badj = s.objective(x, prob.cols, prob.g, prob.weight, target=prob.target)
         ctx.prob = prob
         ctx.version = prob.version
         ctx.save_for_backward(x, badj)

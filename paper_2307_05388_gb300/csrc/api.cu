@@ -116,6 +116,10 @@ struct fdfd_ctx {
   int* d_flow_err = nullptr;       // set by a wait that gave up
   // taps of the design-density filter (offsets and weights) for radius tap_radius
   int* d_probe = nullptr;          // counter of the deferred wait self-test (never incremented)
+  // fdfd_design_iteration's buffers: fields, adjoint source, overlaps, F, gradient, design eps
+  int it_nrhs = 0;
+  double2 *d_itx = nullptr, *d_ita = nullptr, *d_itb = nullptr, *d_ito = nullptr;
+  double *d_itF = nullptr, *d_itg = nullptr, *d_itepsd = nullptr;
   int2* d_taps = nullptr;
   double* d_tapw = nullptr;
   int ntap = 0;
@@ -1536,15 +1540,77 @@ fdfd_status solve_refined(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int
 
 extern "C" {
 
-fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev, const double* g_dev,
-                           const double* weight_dev, double* o_dev, double* F_dev, double* b_adj_dev) {
+fdfd_status fdfd_objective_target(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev,
+                                  const double* g_dev, const double* weight_dev, const double* target_dev,
+                                  double* o_dev, double* F_dev, double* b_adj_dev) {
   if (!ctx || !x_dev || nrhs <= 0 || !cols_dev || !g_dev || !o_dev || !F_dev) return FDFD_ERR_ARG;
   ctx->err.clear();
   Prof pr(ctx, PK_OTHER, 0, 0);
   launch_objective(reinterpret_cast<const double2*>(x_dev), n_cells(ctx), ctx->ny, cols_dev,
-                   reinterpret_cast<const double2*>(g_dev), weight_dev, ctx->n_omega * nrhs,
+                   reinterpret_cast<const double2*>(g_dev), weight_dev, target_dev, ctx->n_omega * nrhs,
                    reinterpret_cast<double2*>(o_dev), F_dev, reinterpret_cast<double2*>(b_adj_dev), ctx->stream);
   CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_objective(fdfd_ctx* ctx, const double* x_dev, int nrhs, const int* cols_dev, const double* g_dev,
+                           const double* weight_dev, double* o_dev, double* F_dev, double* b_adj_dev) {
+  return fdfd_objective_target(ctx, x_dev, nrhs, cols_dev, g_dev, weight_dev, nullptr, o_dev, F_dev, b_adj_dev);
+}
+
+fdfd_status fdfd_design_iteration(fdfd_ctx* ctx, const double* eps_design, const double* b_dev, int nrhs,
+                                  const int* cols_dev, const double* g_dev, const double* weight_dev,
+                                  const double* target_dev, double* F_out, double* grad_out, double* x_dev,
+                                  double* xadj_dev, int flags) {
+  if (!ctx || !eps_design || !b_dev || nrhs <= 0 || !cols_dev || !g_dev || !F_out || !grad_out ||
+      (flags & ~(FDFD_HOST_EPS | FDFD_HOST_OUT)) != 0)
+    return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->have_eps) return fail(ctx, FDFD_ERR_STATE, "fdfd_design_iteration before fdfd_factor");
+  if (ctx->box.w == 0) return fail(ctx, FDFD_ERR_STATE, "context has no design box");
+  if (x_dev && (x_dev == b_dev || x_dev == xadj_dev)) return FDFD_ERR_ARG;
+  CKS(ensure_runtime(ctx));
+  const size_t S = (size_t)ctx->n_omega * nrhs, N = (size_t)n_cells(ctx);
+  const size_t nd = (size_t)ctx->box.w * ctx->box.h;
+  if (ctx->it_nrhs < nrhs) {
+    void* ps[] = {ctx->d_itx, ctx->d_ita, ctx->d_itb, ctx->d_ito};
+    for (void* p : ps) free_ptr(p);
+    ctx->d_itx = ctx->d_ita = ctx->d_itb = ctx->d_ito = nullptr;
+    ctx->it_nrhs = 0;
+    CK(dalloc(&ctx->d_itx, sizeof(double2) * S * N));
+    CK(dalloc(&ctx->d_ita, sizeof(double2) * S * N));
+    CK(dalloc(&ctx->d_itb, sizeof(double2) * S * N));
+    CK(dalloc(&ctx->d_ito, sizeof(double2) * S));
+    ctx->it_nrhs = nrhs;
+  }
+  if (!ctx->d_itF) {
+    CK(dalloc(&ctx->d_itF, sizeof(double)));
+    CK(dalloc(&ctx->d_itg, sizeof(double) * nd));
+    CK(dalloc(&ctx->d_itepsd, sizeof(double) * nd));
+  }
+  const double* epsd = eps_design;
+  if (flags & FDFD_HOST_EPS) {
+    CK(cudaMemcpyAsync(ctx->d_itepsd, eps_design, sizeof(double) * nd, cudaMemcpyHostToDevice, ctx->stream));
+    epsd = ctx->d_itepsd;
+  }
+  const bool host_out = (flags & FDFD_HOST_OUT) != 0;
+  double* x = x_dev ? x_dev : reinterpret_cast<double*>(ctx->d_itx);
+  double* xa = xadj_dev ? xadj_dev : reinterpret_cast<double*>(ctx->d_ita);
+  double* badj = reinterpret_cast<double*>(ctx->d_itb);
+  double* Fd = host_out ? ctx->d_itF : F_out;
+  double* gd = host_out ? ctx->d_itg : grad_out;
+  CKS(fdfd_refactor_design(ctx, epsd));
+  CKS(fdfd_solve(ctx, b_dev, x, nrhs, 0));
+  CKS(fdfd_objective_target(ctx, x, nrhs, cols_dev, g_dev, weight_dev, target_dev,
+                            reinterpret_cast<double*>(ctx->d_ito), Fd, badj));
+  CKS(fdfd_solve(ctx, badj, xa, nrhs, 1));
+  // the adjoint source already carries the per-system weights (and target factors)
+  CKS(fdfd_grad(ctx, x, xa, nrhs, nullptr, gd, 0));
+  if (host_out) {
+    CK(cudaMemcpyAsync(F_out, ctx->d_itF, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(grad_out, ctx->d_itg, sizeof(double) * nd, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   return FDFD_OK;
 }
 
@@ -1844,7 +1910,8 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   free_ws(ctx);
   free_gm(ctx);
   void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
-                ctx->d_growth_max, ctx->d_flow_err, ctx->d_taps, ctx->d_tapw, ctx->d_probe};
+                ctx->d_growth_max, ctx->d_flow_err, ctx->d_taps, ctx->d_tapw, ctx->d_probe,
+                ctx->d_itx, ctx->d_ita, ctx->d_itb, ctx->d_ito, ctx->d_itF, ctx->d_itg, ctx->d_itepsd};
   for (void* p : ps) free_ptr(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   drop_graphs(ctx);

@@ -217,9 +217,11 @@ struct ArnoldiStep {
 };
 void launch_arnoldi(const ArnoldiStep& g, int nsys, int pass, cudaStream_t s);
 
-// objective o = g^T x on a monitor column, F = sum weight |o|^2, adjoint source weight conj(o) g
+// objective o = g^T x on a monitor column, F = sum weight |o|^2 with adjoint source weight conj(o) g,
+// or with target != NULL F = sum weight (|o|^2 - target)^2 with adjoint source 2 weight (|o|^2 - target) conj(o) g
 void launch_objective(const double2* x, long long N, int ny, const int* cols, const double2* gline,
-                      const double* weight, int nsys, double2* o, double* F, double2* badj, cudaStream_t s);
+                      const double* weight, const double* target, int nsys, double2* o, double* F, double2* badj,
+                      cudaStream_t s);
 // dF/deps over the design box: sum weight * 2 (k0dx)^2 Re(x_adj x_fwd)
 void launch_grad(const double2* xf, const double2* xa, long long N, int ny, int x0, int y0, int w, int h,
                  int n_omega, int nrhs, const double* k0dx2, const double* weight, double* grad, int accumulate,

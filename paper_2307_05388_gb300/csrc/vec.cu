@@ -471,19 +471,33 @@ __global__ void overlap_kernel(const double2* __restrict__ x, long long N, int n
   }
 }
 
-__global__ void objective_kernel(const double2* o, const double* weight, int nsys, double* F) {
+// F = sum_q w_q |o_q|^2, or with targets t_q the squared transmission error
+// F = sum_q w_q (|o_q|^2 - t_q)^2 (summed in system order by one thread)
+__global__ void objective_kernel(const double2* o, const double* weight, const double* target, int nsys, double* F) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0;
-  for (int q = 0; q < nsys; ++q) s += (weight ? weight[q] : 1.0) * (o[q].x * o[q].x + o[q].y * o[q].y);
+  for (int q = 0; q < nsys; ++q) {
+    const double p = o[q].x * o[q].x + o[q].y * o[q].y;
+    const double wt = weight ? weight[q] : 1.0;
+    if (target) {
+      const double d = p - target[q];
+      s += wt * d * d;
+    } else {
+      s += wt * p;
+    }
+  }
   *F = s;
 }
 
-__global__ void adjoint_source_kernel(const double2* o, const double* weight, long long N, int ny, const int* cols,
-                                      const double2* __restrict__ gline, double2* badj) {
+// (dF/dE)^T on the monitor column (Wirtinger derivative, E* held fixed):
+// w conj(o) g for F = w |o|^2, and 2 w (|o|^2 - t) conj(o) g for F = w (|o|^2 - t)^2
+__global__ void adjoint_source_kernel(const double2* o, const double* weight, const double* target, long long N,
+                                      int ny, const int* cols, const double2* __restrict__ gline, double2* badj) {
   const int sys = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ny || cols[sys] < 0 || (long long)(cols[sys] + 1) * ny > N) return;
-  const double wt = weight ? weight[sys] : 1.0;
+  double wt = weight ? weight[sys] : 1.0;
+  if (target) wt *= 2.0 * (o[sys].x * o[sys].x + o[sys].y * o[sys].y - target[sys]);
   const double2 oc = make_double2(wt * o[sys].x, -wt * o[sys].y);
   badj[(size_t)sys * N + (size_t)cols[sys] * ny + j] = cmul(oc, gline[(size_t)sys * ny + j]);
 }
@@ -508,12 +522,14 @@ __global__ void grad_kernel(const double2* __restrict__ xf, const double2* __res
 }  // namespace
 
 void launch_objective(const double2* x, long long N, int ny, const int* cols, const double2* gline,
-                      const double* weight, int nsys, double2* o, double* F, double2* badj, cudaStream_t s) {
+                      const double* weight, const double* target, int nsys, double2* o, double* F, double2* badj,
+                      cudaStream_t s) {
   overlap_kernel<<<nsys, 256, 0, s>>>(x, N, ny, cols, gline, o);
-  objective_kernel<<<1, 32, 0, s>>>(o, weight, nsys, F);
+  objective_kernel<<<1, 32, 0, s>>>(o, weight, target, nsys, F);
   if (badj) {
     cudaMemsetAsync(badj, 0, sizeof(double2) * (size_t)nsys * N, s);
-    adjoint_source_kernel<<<dim3((ny + 255) / 256, nsys), 256, 0, s>>>(o, weight, N, ny, cols, gline, badj);
+    adjoint_source_kernel<<<dim3((ny + 255) / 256, nsys), 256, 0, s>>>(o, weight, target, N, ny, cols, gline,
+                                                                        badj);
   }
 }
 

@@ -28,7 +28,8 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
            "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
-           "fdfd_slab_modes"]
+           "fdfd_slab_modes", "fdfd_objective_target", "fdfd_design_iteration"]
+HOST_EPS, HOST_OUT = 1, 2
 
 
 class Grid(C.Structure):
@@ -80,6 +81,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_solve.argtypes = [vp, vp, vp, i, i]
     lib.fdfd_objective.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp]
     lib.fdfd_grad.argtypes = [vp, vp, vp, i, vp, vp, i]
+    lib.fdfd_objective_target.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]
+    lib.fdfd_design_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, i]
     lib.fdfd_apply.argtypes = [vp, vp, vp, i, i]
     lib.fdfd_set_options.argtypes = [vp, C.POINTER(Options)]
     lib.fdfd_stats_get.argtypes = [vp, C.POINTER(Stats)]
@@ -105,7 +108,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     for name in ("fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design", "fdfd_solve",
                  "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
                  "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get", "fdfd_filter_project",
-                 "fdfd_filter_project_adjoint"):
+                 "fdfd_filter_project_adjoint", "fdfd_objective_target", "fdfd_design_iteration",
+                 "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -230,17 +234,47 @@ class Solver:
         return x
 
     def objective(self, x: torch.Tensor, cols: torch.Tensor, g: torch.Tensor, weight: torch.Tensor | None = None,
-                  with_adjoint: bool = True):
+                  with_adjoint: bool = True, target: torch.Tensor | None = None):
+        """F = sum w |o|^2 (target None) or F = sum w (|o|^2 - target)^2, the overlaps o and the adjoint
+        source (fdfd_objective / fdfd_objective_target)."""
         nrhs = x.numel() // (self.n_omega * self.n)
         nsys = self.n_omega * nrhs
         assert cols.dtype == torch.int32 and cols.numel() == nsys
         assert g.dtype == torch.complex128 and g.numel() == nsys * self.ny
+        assert target is None or (target.dtype == torch.float64 and target.numel() == nsys)
         o = torch.empty(nsys, dtype=torch.complex128, device=x.device)
         F = torch.empty((), dtype=torch.float64, device=x.device)
         badj = torch.empty_like(x) if with_adjoint else None
-        self._check(_lib.fdfd_objective(self._h, _ptr(x), nrhs, _ptr(cols), _ptr(g), _ptr(weight), _ptr(o),
-                                        _ptr(F), _ptr(badj)), "fdfd_objective")
+        self._check(_lib.fdfd_objective_target(self._h, _ptr(x), nrhs, _ptr(cols), _ptr(g), _ptr(weight),
+                                               _ptr(target), _ptr(o), _ptr(F), _ptr(badj)),
+                    "fdfd_objective_target")
         return F, o, badj
+
+    def design_iteration(self, eps_design: torch.Tensor, b: torch.Tensor, cols: torch.Tensor, g: torch.Tensor,
+                         weight: torch.Tensor | None = None, target: torch.Tensor | None = None,
+                         F_out: torch.Tensor | None = None, grad_out: torch.Tensor | None = None,
+                         x_out: torch.Tensor | None = None, xadj_out: torch.Tensor | None = None):
+        """fdfd_design_iteration: refactor, forward solve, objective, adjoint solve, gradient in one
+        call.  eps_design, F_out and grad_out may be CPU tensors (pinned for asynchronous copies):
+        the library then copies them itself and returns once F and dF/deps are on the host."""
+        nrhs = b.numel() // (self.n_omega * self.n)
+        nd = self.box[2] * self.box[3]
+        eps_design = eps_design.reshape(-1)
+        assert eps_design.dtype == torch.float64 and eps_design.numel() == nd
+        host_out = F_out is not None and not F_out.is_cuda
+        dev = b.device
+        if F_out is None:
+            F_out = torch.empty((), dtype=torch.float64, device=dev)
+        if grad_out is None:
+            grad_out = torch.empty(nd, dtype=torch.float64, device="cpu" if host_out else dev,
+                                   pin_memory=host_out)
+        assert grad_out.is_cuda != host_out and F_out.numel() == 1 and grad_out.numel() == nd
+        flags = (0 if eps_design.is_cuda else HOST_EPS) | (HOST_OUT if host_out else 0)
+        self._check(_lib.fdfd_design_iteration(self._h, _ptr(eps_design), _ptr(b), nrhs, _ptr(cols), _ptr(g),
+                                               _ptr(weight), _ptr(target), _ptr(F_out), _ptr(grad_out),
+                                               _ptr(x_out), _ptr(xadj_out), flags), "fdfd_design_iteration")
+        self._keep = eps_design
+        return F_out, grad_out
 
     def grad(self, x_fwd: torch.Tensor, x_adj: torch.Tensor, weight: torch.Tensor | None = None,
              out: torch.Tensor | None = None, accumulate: bool = False) -> torch.Tensor:

@@ -40,7 +40,7 @@ class OracleSolver:
             return out
         return t
 
-    def objective(self, x, cols, g, weight=None, with_adjoint=True):
+    def objective(self, x, cols, g, weight=None, with_adjoint=True, target=None):
         xx = x.numpy().reshape(self.n_omega, -1, self.nx, self.ny)
         nrhs = xx.shape[1]
         F, badj, o = 0.0, np.zeros_like(xx), []
@@ -49,8 +49,12 @@ class OracleSolver:
             c, gs = int(cols[s]), g[s].numpy()
             ov = np.sum(gs * xx[w, r, c])
             wt = 1.0 if weight is None else float(weight[s])
-            F += wt * abs(ov) ** 2
-            badj[w, r, c] = wt * np.conj(ov) * gs
+            if target is None:
+                F += wt * abs(ov) ** 2
+                badj[w, r, c] = wt * np.conj(ov) * gs
+            else:
+                F += O.target_objective(ov, float(target[s]), wt)
+                badj[w, r, c] = 2.0 * wt * (abs(ov) ** 2 - float(target[s])) * np.conj(ov) * gs
             o.append(ov)
         return torch.tensor(F, dtype=torch.float64), torch.tensor(np.array(o)), torch.from_numpy(badj.reshape(x.shape))
 

@@ -512,3 +512,38 @@ def test_pixel_differences_by_rank_one_update_match_refactoring():
     np.testing.assert_allclose(fd, brute, rtol=1e-9, atol=0)
     _, g, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
     np.testing.assert_allclose(fd, g.ravel()[pixels], rtol=1e-5, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Transmission-target objective (Sec. III-IV: difference of calculated and target
+# transmissions, minimised)
+# ---------------------------------------------------------------------------
+def test_target_objective_gradient_central_differences():
+    """F = sum (|g^T E|^2 - t)^2 over two wavelengths and two sources: the adjoint gradient
+    (Eq. 3 with the source 2 (|o|^2 - t) conj(o) g of Eq. 4) equals central differences of the
+    oracle's own F on every design pixel, with targets on both sides of the current powers."""
+    wl = W.make_small(16, 15, 3, (5, 4, 5, 6), n_omega=2, n_src=2, seed=8)
+    F0, _, f0 = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    powers = [[abs(O.overlap(f0[(w, s)][0], wl.monitor_dense(w, s))) ** 2 for s in range(2)] for w in range(2)]
+    targets = [[powers[w][s] * (0.5 if (w + s) % 2 else 1.7) for s in range(2)] for w in range(2)]
+    F, g, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS, targets=targets)
+    assert F > 0
+    h = 1e-5
+    fd = np.zeros_like(wl.rho)
+    for idx in np.ndindex(wl.rho.shape):
+        rp, rm = wl.rho.copy(), wl.rho.copy()
+        rp[idx] += h
+        rm[idx] -= h
+        Fp, _, _ = O.design_iteration(wl, rp, wl.eps_full, W.DELTA_EPS, targets=targets)
+        Fm, _, _ = O.design_iteration(wl, rm, wl.eps_full, W.DELTA_EPS, targets=targets)
+        fd[idx] = (Fp - Fm) / (2 * h)
+    assert O.rel_err(g, fd) < 1e-6
+
+
+def test_target_objective_vanishes_at_the_target():
+    """With every target equal to the current port power, F = 0 and its gradient is zero."""
+    wl = W.make_small(14, 13, 3, (4, 4, 5, 4), n_omega=1, n_src=2, seed=9)
+    _, _, f0 = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    targets = [[abs(O.overlap(f0[(0, s)][0], wl.monitor_dense(0, s))) ** 2 for s in range(2)]]
+    F, g, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS, targets=targets)
+    assert F < 1e-24 and np.max(np.abs(g)) < 1e-12
