@@ -1,23 +1,35 @@
 #!/usr/bin/env python3
 """Benchmark: forward + adjoint FDFD design iterations per second on one GB300.
 
-Workload (default "c2"): 340 x 340 grid (12 x 12 um + 20-cell PML at dx = 40 nm,
-115,600 unknowns), lambda = 1.55 um, 250 x 250 design box with 8x8-blurred
-seeded density and Si waveguide stubs, one source.  One step is one design
-iteration: design refactor of the cached factors, forward solve with FGMRES
-refinement, mode-overlap objective and adjoint source, transpose solve on the
-same factors, pixel gradient.  The sign-step update of rho between steps is
-not timed.  The uncached FP64 arm (symbolic + numeric factorisation per solve,
-as in the paper's reference arm) and the CPU oracle are reported beside it.
+Default workload "c5": 1760 x 1760 grid (86 x 86 um + 20-cell PML at dx = 50 nm,
+3,097,600 unknowns per matrix), wavelengths 1.31 and 1.55 um, TE0 and TE1 sources
+(eigenmodes of the 1.2 um input guide, from the library's mode solver), 1680 x 1680
+design box with an 8x8-blurred seeded density: four systems per design iteration.
+One step is one design iteration: the design-box permittivity from the density (a
+library kernel), design refactor of the cached factors of both wavelengths, forward
+solves with FGMRES refinement, mode-overlap objective and adjoint sources, transpose
+solves on the same factors, pixel gradient.  The sign-step update of rho between
+steps is not timed; the L2 is flushed between steps.
 
+Beside the headline (cached complex FP32 factors + FP64 FGMRES refinement):
+  e2e          the same design path through fdfd_design_iteration with host buffers
+               (the host -> device copy of the design and the device -> host copy of
+               F and the gradient inside the timed region)
+  uncached_f64 the paper's reference procedure on the same GPU (symbolic and numeric
+               FP64 factorisation for every solve), and the cached FP64 form
+  factor       full factorisation against design refactor: time, flops, factor memory
+  cpu_baseline the CPU oracle (SciPy SuperLU, nested-dissection order, complex128) on
+               the same workload: one design iteration at the initial design, one
+               process per wavelength, started before the first GPU call; its fields
+               and gradient also give the accuracy of the GPU path element by element.
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-(N > 1 via torch.distributed.run: each rank runs its own seeded replica).
+(N > 1 via torch.distributed.run: the (wavelength, source) pairs of the one problem
+are sharded over the ranks, one all-reduce of [gradient, F] per iteration).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -35,15 +47,17 @@ METRIC = "fwd+adjoint design iterations/s, cached vs uncached FP64, at field err
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20
 FP32_LANES_PER_SM = 128
-N_SM = 152
+DATA = "synthetic (seeded design density and guide; the paper's devices are not published)"
+DTYPE = "c64 factors + c128 refinement"
 
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], sm_max_mhz=d.get("sm_max_mhz", 2070.0), src="measured")
-    return dict(hbm=6800.0, bf16=1900.0, sm_max_mhz=2070.0, src="fallback")
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                    sm_max_mhz=d.get("sm_max_mhz", 2070.0), src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, sm_max_mhz=2070.0, src="fallback")
 
 
 TENSOR_FORMS = {0: "SIMT complex FP32", 1: "tcgen05 TF32", 2: "tcgen05 TF32 hi+lo (3 products)",
@@ -52,9 +66,12 @@ TENSOR_FORMS = {0: "SIMT complex FP32", 1: "tcgen05 TF32", 2: "tcgen05 TF32 hi+l
 
 def workload_config(wl):
     x0, y0, w, h = wl.box
+    srcs = ("TE0/TE1 eigenmodes of the input guide" if any(isinstance(s, W.ModeLine) for s in wl.sources)
+            else "Gaussian line source")
     return {"workload": f"{wl.name}: {wl.nx}x{wl.ny} grid ({wl.n:,} unknowns), dx {wl.dx * 1e3:.0f} nm, "
                         f"{wl.n_omega} wavelength(s) x {wl.n_src} source(s), {w}x{h} design box",
             "nx": wl.nx, "ny": wl.ny, "n_omega": wl.n_omega, "nrhs": wl.n_src, "design_box": [x0, y0, w, h],
+            "wavelengths_um": [float(v) for v in wl.wavelengths], "sources": srcs,
             "factor": "complex FP32 multifrontal + FP64 FGMRES refinement (tol 1e-9)",
             "l2": "flushed between timed steps (512 MB write)"}
 
@@ -97,13 +114,52 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle (baseline leg and reference arm)
+# CPU oracle: the cpu_baseline leg and the reference arm (one process per wavelength)
 # ---------------------------------------------------------------------------
-def oracle_iteration(wl, rho):
+def _oracle_wavelength(name: str, w: int, seed: int, want_fields: bool):
+    """One wavelength's share of an oracle design iteration at the initial design (runs in a
+    spawned child).  Returns (seconds, F_w, dF/drho_w [w, h], {s: (E, E_adj)} or None)."""
     from oracle import fdfd_oracle as O
+    wl = W.with_modes(W.make(name, seed=seed), O.slab_modes).select_wavelengths([w])
     t = time.perf_counter()
-    F, g, fields = O.design_iteration(wl, rho, wl.eps_full, W.DELTA_EPS)
-    return time.perf_counter() - t, F, g, fields
+    F, g, fields = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    dt = time.perf_counter() - t
+    return dt, F, g, ({s: fields[(0, s)] for s in range(wl.n_src)} if want_fields else None)
+
+
+class OracleLeg:
+    """The oracle's design iteration of a workload, its wavelengths in parallel spawned processes
+    (each process gets an equal share of the host cores for its BLAS threads)."""
+
+    def __init__(self, name: str, n_omega: int, want_fields: bool, seed: int = 0):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        # the host cores split over the processes, read by each child's BLAS at start-up
+        threads = str(max(1, (os.cpu_count() or 1) // n_omega))
+        os.environ["OPENBLAS_NUM_THREADS"] = threads
+        os.environ["OMP_NUM_THREADS"] = threads
+        self.ex = cf.ProcessPoolExecutor(max_workers=n_omega, mp_context=mp.get_context("spawn"))
+        self.t0 = time.perf_counter()
+        self.jobs = [self.ex.submit(_oracle_wavelength, name, w, seed, want_fields) for w in range(n_omega)]
+        self.n = n_omega
+
+    def result(self, budget_s: float):
+        """[(seconds, F_w, g_w, fields_w)] per wavelength, or None if the budget ran out."""
+        import concurrent.futures as cf
+        left = max(1.0, budget_s - (time.perf_counter() - self.t0))
+        done, pending = cf.wait(self.jobs, timeout=left)
+        if pending:
+            self.kill()
+            return None
+        return [j.result() for j in self.jobs]
+
+    def kill(self):
+        for p in list(getattr(self.ex, "_processes", {}).values()):
+            try:
+                p.kill()
+            except Exception:
+                pass
+        self.ex.shutdown(wait=False, cancel_futures=True)
 
 
 def max_over_ranks(value, dist, device):
@@ -117,34 +173,40 @@ def max_over_ranks(value, dist, device):
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands, timed on the host cores: each step one full design iteration of the
+    workload at its initial design, one process per wavelength (rank 0 only)."""
     if rank != 0:
         return 0
     wl = W.make(args.workload, seed=0)
-    budget_s = 150.0
-    rho = wl.rho.copy()
-    t_first, F, g, _ = oracle_iteration(wl, rho)   # warm-up / sizing step
+    if 0 < args.omegas < wl.n_omega:
+        wl = wl.select_wavelengths(range(args.omegas))
+    n_w = wl.n_omega
+    budget = args.cpu_budget
     times = []
-    from oracle import fdfd_oracle as O
-    for k in range(max(0, args.warmup - 1)):
-        if t_first * (k + 2) > budget_s / 3:
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        leg = OracleLeg(args.workload, n_w, False)
+        res = leg.result(budget)
+        leg.ex.shutdown(wait=True)
+        if res is None:
             break
-        rho = O.sign_step(rho, g, wl.step)
-        _, F, g, _ = oracle_iteration(wl, rho)
-    steps = max(1, min(args.steps, int(budget_s / max(t_first, 1e-3))))
-    for _ in range(steps):
-        rho = O.sign_step(rho, g, wl.step)
-        dt, F, g, _ = oracle_iteration(wl, rho)
-        times.append(dt)
-    total = sum(times)
-    value = len(times) / total
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "steps_timed": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic (seeded design density; the paper's devices are not published)",
+        times.append(time.perf_counter() - leg.t0)
+        if time.perf_counter() - t_start + times[-1] > budget:
+            break
+    if not times:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"one oracle design iteration of {args.workload} did not finish within {budget:.0f} s"}))
+        return 0
+    per = float(np.mean(times))
+    value = 1.0 / per
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times),
+            "steps_requested": args.steps, "warmup": 0, "ms_per_step": 1e3 * per, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "c128", "data": DATA,
             "config": workload_config(wl), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} full design iterations (SciPy SuperLU complex128, "
-                                       "single-threaded) of the same workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_w, "kind": "oracle",
+                             "sample": f"{len(times)} full design iteration(s) of the workload at its initial "
+                                       f"design (SciPy SuperLU complex128, nested-dissection order, one "
+                                       f"single-threaded process per wavelength)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -159,14 +221,19 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c5")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
-    ap.add_argument("--no-plain", action="store_true", help="skip the uncached FP64 arm")
+    ap.add_argument("--cpu-budget", type=float, default=1500.0,
+                    help="seconds the oracle leg (or the reference arm) may take before it is abandoned")
+    ap.add_argument("--no-plain", action="store_true", help="skip the uncached and cached FP64 arms")
     ap.add_argument("--omegas", type=int, default=0,
                     help="run only the first N wavelengths of the workload (0 = all; for small profiling cases)")
     ap.add_argument("--tensor-form", type=int, default=3, choices=[0, 1, 2, 3],
                     help="update matrices on the tensor cores: 0 off (SIMT), 1 TF32, 2 TF32 hi+lo, "
                          "3 BF16 three-way split (default)")
+    ap.add_argument("--factor-form", type=int, default=0, choices=[0, 1],
+                    help="complex FP32 factors: 0 LU with block-local pivoting (default), 1 symmetric "
+                         "L diag(d) L^T of D A without pivoting")
     ap.add_argument("--autotune", default="", metavar="CACHE.json",
                     help="choose tensor_form, tensor_min_m, tensor_min_tiles and leaf_area by measured design "
                          "iterations before the timed run (starting from --tensor-form), cached in this file")
@@ -176,6 +243,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    wl0 = W.make(args.workload, seed=0)
+    n_omega_run = args.omegas if 0 < args.omegas < wl0.n_omega else wl0.n_omega
+    # the oracle leg starts first: spawned children, before any CUDA call in this process
+    leg = None
+    if args.impl == "ours" and rank == 0 and world == 1 and not args.no_cpu and n_omega_run == wl0.n_omega:
+        leg = OracleLeg(args.workload, wl0.n_omega, True)
 
     import torch
     dist = None
@@ -192,41 +266,51 @@ def main():
     dev = torch.device("cuda", local)
     from paper_2307_05388_gb300 import autograd as AG
     from paper_2307_05388_gb300 import fdfd as FD
+    from paper_2307_05388_gb300 import shard as SH
 
-    wl = W.make(args.workload, seed=rank)
-    if 0 < args.omegas < wl.n_omega:   # a smaller case of the same workload (profiling)
-        wl.wavelengths = wl.wavelengths[:args.omegas]
-        wl.monitors = wl.monitors[:args.omegas]
+    wl = W.with_modes(wl0, FD.slab_modes)
+    if n_omega_run < wl.n_omega:   # a smaller case of the same workload (profiling)
+        wl = wl.select_wavelengths(range(n_omega_run))
     x0, y0, bw, bh = wl.box
-    k0 = 2 * np.pi / wl.wavelengths
+    nd = bw * bh
+    k0 = 2 * np.pi / np.asarray(wl.wavelengths)
+    eps_bg = torch.from_numpy(wl.eps_bg.reshape(-1).copy()).to(dev)
+    lo, hi = W.EPS_SIO2, W.EPS_SIO2 + W.DELTA_EPS
 
-    def make_problem(mode, opts=None):
-        s = FD.Solver(wl.nx, wl.ny, wl.dx, k0, wl.npml, box=wl.box,
-                      options=opts if opts is not None else FD.default_options(mode=mode, tensor_form=args.tensor_form))
-        b = np.stack([wl.source_dense(i) for i in range(wl.n_src)])
-        b = np.broadcast_to(b, (wl.n_omega,) + b.shape).copy()
-        cols = np.array([wl.monitors[w][i].col for w in range(wl.n_omega) for i in range(wl.n_src)], np.int32)
-        g = np.stack([wl.monitors[w][i].values for w in range(wl.n_omega) for i in range(wl.n_src)])
-        return AG.DesignProblem(s, torch.from_numpy(wl.eps_bg.reshape(-1).copy()).to(dev),
-                                torch.from_numpy(b).to(dev), torch.from_numpy(cols).to(dev),
-                                torch.from_numpy(g.astype(np.complex128)).to(dev))
+    def make_problem(ws, ss, opts):
+        s = FD.Solver(wl.nx, wl.ny, wl.dx, k0[ws], wl.npml, box=wl.box, options=opts)
+        b = np.stack([np.stack([wl.source_dense(i, w) for i in ss]) for w in ws])
+        cols = np.array([wl.monitors[w][i].col for w in ws for i in ss], np.int32)
+        g = np.stack([wl.monitors[w][i].values for w in ws for i in ss]).astype(np.complex128)
+        return AG.DesignProblem(s, eps_bg, torch.from_numpy(b).to(dev), torch.from_numpy(cols).to(dev),
+                                torch.from_numpy(g).to(dev))
 
-    def eps_of(rho_t):
-        return (W.EPS_SIO2 + rho_t * W.DELTA_EPS).reshape(-1).contiguous()
+    def build(opts):
+        return SH.ShardedProblem(lambda ws, ss: make_problem(ws, ss, opts), wl.n_omega, wl.n_src, nd, dev,
+                                 group=dist.group.WORLD if dist is not None else None)
+
+    def close(sp):
+        for p in sp.problems:
+            p.solver.close()
 
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    rho0 = torch.from_numpy(wl.rho.copy()).to(dev)
+    rho0 = torch.from_numpy(wl.rho.reshape(-1).copy()).to(dev)
 
-    def run_arm(prob, steps, warmup, clocks=False, host_io=False):
+    def density(sp, rho, out):
+        if sp.problems:
+            sp.problems[0].solver.density_eps(rho, lo, hi, out=out)    # library kernel
+        else:
+            out.copy_(lo + rho * (hi - lo))                           # a rank with no systems
+
+    def run_arm(sp, steps, warmup, clocks=False):
         rho = rho0.clone()
-        grad = torch.empty(bw * bh, dtype=torch.float64, device=dev)
-        h_eps = torch.empty(bw * bh, dtype=torch.float64, pin_memory=True)
-        h_out = torch.empty(bw * bh + 1, dtype=torch.float64, pin_memory=True)
-        d_eps = torch.empty(bw * bh, dtype=torch.float64, device=dev)
+        eps = torch.empty(nd, dtype=torch.float64, device=dev)
+        grad = torch.empty(nd, dtype=torch.float64, device=dev)
         for _ in range(warmup):
-            F, g = prob.iteration(eps_of(rho), grad_out=grad)
-            rho = torch.clamp(rho + wl.step * torch.sign(g.reshape(bw, bh)), 0.0, 1.0)
+            density(sp, rho, eps)
+            F, g = sp.iteration(eps, grad_out=grad)
+            rho = torch.clamp(rho + wl.step * torch.sign(g), 0.0, 1.0)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if dist is not None:
             dist.barrier()
@@ -234,191 +318,288 @@ def main():
         sampler = ClockSampler(local) if clocks else None
         for k in range(steps):
             flush.zero_()                                # L2 flush between timed steps (not timed)
-            if host_io:
-                h_eps.copy_(eps_of(rho).cpu())           # the caller's host-side design (not timed)
             ev[k][0].record(stream)
-            if host_io:
-                d_eps.copy_(h_eps, non_blocking=True)
-                F, g = prob.iteration(d_eps, grad_out=grad)
-                h_out[:bw * bh].copy_(g, non_blocking=True)
-                h_out[bw * bh:].copy_(F.reshape(1), non_blocking=True)
-            else:
-                F, g = prob.iteration(eps_of(rho), grad_out=grad)
+            density(sp, rho, eps)
+            F, g = sp.iteration(eps, grad_out=grad)
             ev[k][1].record(stream)
-            rho = torch.clamp(rho + wl.step * torch.sign(g.reshape(bw, bh)), 0.0, 1.0)
+            rho = torch.clamp(rho + wl.step * torch.sign(g), 0.0, 1.0)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         clk = sampler.stop() if sampler else None
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        return ms, clk
+        return sum(a.elapsed_time(b) for a, b in ev), clk
+
+    def run_e2e(sp, steps, warmup):
+        """Host design in, host F and gradient out, every step; host wall clock."""
+        h_eps = torch.empty(nd, dtype=torch.float64, pin_memory=True)
+        h_F = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        h_g = torch.empty(nd, dtype=torch.float64, pin_memory=True)
+        d_eps = torch.empty(nd, dtype=torch.float64, device=dev)
+        rho = wl.rho.reshape(-1).copy()
+        single = dist is None and len(sp.problems) == 1
+        total = 0.0
+        for k in range(warmup + steps):
+            h_eps.numpy()[:] = lo + rho * (hi - lo)        # the caller's host-side design (not timed)
+            flush.zero_()
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            t = time.perf_counter()
+            if single:
+                p = sp.problems[0]
+                p.solver.design_iteration(h_eps, p.b, p.cols, p.g, F_out=h_F, grad_out=h_g)
+            else:
+                d_eps.copy_(h_eps, non_blocking=True)
+                F, g = sp.iteration(d_eps)
+                h_g.copy_(g, non_blocking=True)
+                h_F.copy_(F.reshape(1), non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+            dt = time.perf_counter() - t
+            if k >= warmup:
+                total += dt
+            rho = np.clip(rho + wl.step * np.sign(h_g.numpy()), 0.0, 1.0)
+        return 1e3 * total
 
     # ---- launch parameters: library defaults, or measured by the autotuner (not timed) ----
-    opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form)
+    opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form, factor_form=args.factor_form)
     tuned = None
     if args.autotune:
         from paper_2307_05388_gb300 import autotune as AT
         key = AT.problem_key_for(wl.nx, wl.ny, wl.dx, wl.n_omega, wl.n_src, wl.box, opts)
         t_tune = time.perf_counter()
-        res = AT.tune(lambda o: make_problem(FD.MODE_MIXED, o), eps_of(rho0), base=opts,
-                      cache_path=args.autotune, key=key)
+        res = AT.tune(lambda o: make_problem(list(range(wl.n_omega)), list(range(wl.n_src)), o),
+                      (lo + rho0 * (hi - lo)), base=opts, cache_path=args.autotune, key=key)
         opts = res.options
         tuned = {"params": res.params, "cached": res.cached, "candidates": len(res.trials),
                  "seconds": time.perf_counter() - t_tune}
     form = opts.tensor_form
 
     # ---- cached mixed-precision arm (the headline) --------------------------
-    prob = make_problem(FD.MODE_MIXED, opts)
+    sp = build(opts)
     t_setup = time.perf_counter()
-    prob.iteration(eps_of(rho0))
+    eps0 = torch.empty(nd, dtype=torch.float64, device=dev)
+    density(sp, rho0, eps0)
+    sp.iteration(eps0)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
-    ms, clk = run_arm(prob, args.steps, args.warmup, clocks=True)
+    ms, clk = run_arm(sp, args.steps, args.warmup, clocks=True)
     ms_max = max_over_ranks(ms, dist, dev)
-    value = world * args.steps / (ms_max / 1e3)
-    st = prob.solver.stats()
-
-    # ---- accuracy of the measured path against the oracle (rank 0, N = 1) ----
-    acc = {}
-    cpu = None
-    run_cpu = (rank == 0 and world == 1 and not args.no_cpu)
-    if run_cpu:
-        F, g = prob.iteration(eps_of(rho0))
-        torch.cuda.synchronize()
-        x_gpu = prob.x.cpu().numpy().reshape(-1)
-        dt, F_ref, g_ref, fields = oracle_iteration(wl, wl.rho.copy())
-        from oracle import fdfd_oracle as O
-        acc = {"field_err": O.rel_err(x_gpu, fields[(0, 0)][0]),
-               "grad_err": O.rel_err(g.cpu().numpy().reshape(bw, bh) * W.DELTA_EPS, g_ref),
-               "objective_err": abs(float(F) - F_ref) / abs(F_ref)}
-        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "1 full design iteration at the initial design (SciPy SuperLU complex128 factor, "
-                         f"forward + transpose solve, gradient; single-threaded), {dt:.1f} s"}
+    value = args.steps / (ms_max / 1e3)
+    stats = [p.solver.stats() for p in sp.problems]
 
     # ---- end to end through the public API with host buffers -----------------
-    ms_e2e, _ = run_arm(prob, args.steps, args.warmup, host_io=True)   # the same design path as the timed arm
-    e2e_value = world * args.steps / (max_over_ranks(ms_e2e, dist, dev) / 1e3)
+    ms_e2e = run_e2e(sp, args.steps, args.warmup)
+    e2e_value = args.steps / (max_over_ranks(ms_e2e, dist, dev) / 1e3)
 
     # ---- per-kernel profile (separate pass; events around every launch) -----
-    prof_steps = 3
-    prob.solver.profile(True)
-    run_arm(prob, prof_steps, 0)
-    prof = prob.solver.profile_get()
-    prob.solver.profile(False)
-    kern = {k: v for k, v in prof.items() if v["launches"] > 0}
-    tot_ms = sum(v["ms"] for v in kern.values())
-    dom = max(kern, key=lambda k: kern[k]["ms"])
+    prof_steps = 2
+    for p in sp.problems:
+        p.solver.profile(True)
+    run_arm(sp, prof_steps, 0)
+    kern = {}
+    for p in sp.problems:
+        for k, v in p.solver.profile_get().items():
+            if v["launches"] > 0:
+                a = kern.setdefault(k, dict(launches=0, ms=0.0, flops=0.0, bytes=0.0))
+                for f in a:
+                    a[f] += v[f]
+        p.solver.profile(False)
     pk = peaks()
-    d = kern[dom]
-    per_launch_ms = d["ms"] / d["launches"]
-    if dom.startswith("lu_"):
-        fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": d["flops"] / d["launches"] / (per_launch_ms / 1e3) / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": f"FP32 SIMT: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk['sm_max_mhz']:.0f} MHz"}
-    else:
-        roof = {"bound": "hbm", "achieved": d["bytes"] / d["launches"] / (per_launch_ms / 1e3) / 1e9,
-                "peak": pk["hbm"], "unit": "GB/s", "traffic": None,
-                "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    roof["kernel"] = dom
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # the tensor-core update matrices: algorithmic rate (8 flops per complex multiply-add) and the
-    # tensor-op rate it takes in the chosen operand form, against the dense peak of that input type
-    # the cached solves: the four sweep directions together, algorithmic bytes (every factor entry
-    # of the swept triangle and off-diagonal block once per right-hand side) against the HBM peak
-    sw = [v for k, v in kern.items() if k.startswith("sweep_")]
-    roof_sw = None
-    if sw:
-        sw_ms = sum(v["ms"] for v in sw)
-        sw_gbs = sum(v["bytes"] for v in sw) / (sw_ms / 1e3) / 1e9
-        roof_sw = {"kernels": "flow_kernel (L, U, U^T, L^T)", "bound": "hbm", "achieved": sw_gbs, "unit": "GB/s",
-                   "peak": pk["hbm"], "frac": sw_gbs / pk["hbm"], "ms_per_step": sw_ms / prof_steps,
-                   "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    roof_tc = None
-    if "lu_schur_tc" in kern:
-        d_tc = kern["lu_schur_tc"]
-        mult = {1: 1, 2: 3, 3: 6}[form]
-        peak_tc = pk["bf16"] * (1.0 if form == 3 else 0.5)
-        ach = d_tc["flops"] / (d_tc["ms"] / 1e3) / 1e12
-        roof_tc = {"kernel": "lu_schur_tc", "bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
-                   "tensor_op_tflops": ach * mult, "peak": peak_tc, "frac": ach * mult / peak_tc, "traffic": None,
-                   "peak_source": f"{pk['src']} bf16 dense GEMM peak" + ("" if form == 3 else " x 0.5 (TF32)"),
-                   "note": f"achieved counts 8 flops per complex multiply-add; the operand form issues {mult}x "
-                           "as many tensor flops (tile padding not counted)"}
-    launches_per_step = sum(v["launches"] for v in kern.values()) / prof_steps
-    kernels = {k: {"launches_per_step": v["launches"] / prof_steps, "ms_per_step": v["ms"] / prof_steps,
-                   "share": v["ms"] / tot_ms,
-                   "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["flops"] else None,
-                   "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] else None}
-               for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])}
+    roof = roof_tc = roof_sw = None
+    kernels = {}
+    launches_per_step = 0.0
+    if kern:
+        tot_ms = sum(v["ms"] for v in kern.values())
+        dom = max(kern, key=lambda k: kern[k]["ms"])
+        d = kern[dom]
+        per_launch_ms = d["ms"] / d["launches"]
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = nsm * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        if dom == "lu_schur_tc":
+            mult = {1: 1, 2: 3, 3: 6}[form]
+            peak_tc = pk["bf16_sus"] * (1.0 if form == 3 else 0.5)
+            ach = d["flops"] / d["launches"] / (per_launch_ms / 1e3) / 1e12 * mult
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": f"{pk['src']} sustained bf16 dense GEMM (MEASURED_PEAKS.json)"}
+        elif dom.startswith("lu_"):
+            roof = {"bound": "alu", "achieved": d["flops"] / d["launches"] / (per_launch_ms / 1e3) / 1e12,
+                    "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": f"FP32 SIMT: {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk['sm_max_mhz']:.0f} MHz"}
+        else:
+            roof = {"bound": "hbm", "achieved": d["bytes"] / d["launches"] / (per_launch_ms / 1e3) / 1e9,
+                    "peak": pk["hbm"], "unit": "GB/s", "traffic": None,
+                    "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        roof["kernel"] = dom
+        roof["launches_per_step"] = d["launches"] / prof_steps
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        sw = [v for k, v in kern.items() if k.startswith("sweep_")]
+        if sw:
+            sw_ms = sum(v["ms"] for v in sw)
+            sw_gbs = sum(v["bytes"] for v in sw) / (sw_ms / 1e3) / 1e9
+            roof_sw = {"kernels": "flow_kernel (L, U, U^T, L^T)", "bound": "hbm", "achieved": sw_gbs, "unit": "GB/s",
+                       "peak": pk["hbm"], "frac": sw_gbs / pk["hbm"], "ms_per_step": sw_ms / prof_steps,
+                       "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        if "lu_schur_tc" in kern:
+            d_tc = kern["lu_schur_tc"]
+            mult = {1: 1, 2: 3, 3: 6}[form]
+            peak_tc = pk["bf16_sus"] * (1.0 if form == 3 else 0.5)
+            ach = d_tc["flops"] / (d_tc["ms"] / 1e3) / 1e12
+            roof_tc = {"kernel": "lu_schur_tc", "bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                       "tensor_op_tflops": ach * mult, "peak": peak_tc, "frac": ach * mult / peak_tc,
+                       "peak_source": f"{pk['src']} sustained bf16 dense GEMM peak" + ("" if form == 3 else " x 0.5 (TF32)"),
+                       "note": f"achieved counts 8 flops per complex multiply-add; the operand form issues {mult}x "
+                               "as many tensor flops (tile padding not counted)"}
+        fac_keys = [k for k in kern if k.startswith("lu_") or k == "front_build"]
+        fac_ms = sum(kern[k]["ms"] for k in fac_keys) / prof_steps
+        fac_fl = sum(kern[k]["flops"] for k in fac_keys) / prof_steps
+        roof_fac = {"kernels": "the whole design refactor (" + ", ".join(sorted(fac_keys)) + ")",
+                    "achieved": fac_fl / (fac_ms / 1e3) / 1e12 if fac_ms else None, "unit": "TFLOP/s",
+                    "ms_per_step": fac_ms, "peak_tf32_tensor": pk["bf16_sus"] * 0.5,
+                    "frac_of_tf32_tensor": (fac_fl / (fac_ms / 1e3) / 1e12) / (pk["bf16_sus"] * 0.5) if fac_ms else None,
+                    "peak_source": f"{pk['src']} sustained bf16 dense GEMM x 0.5"}
+        launches_per_step = sum(v["launches"] for v in kern.values()) / prof_steps
+        kernels = {k: {"launches_per_step": v["launches"] / prof_steps, "ms_per_step": v["ms"] / prof_steps,
+                       "share": v["ms"] / tot_ms,
+                       "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["flops"] else None,
+                       "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["bytes"] else None}
+                   for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])}
+        kernels["_factorisation"] = roof_fac
 
-    # ---- smoothing filter + projection of the design density (Sec. III), C2 box ----
-    radius_cells = 0.2 / wl.dx                       # the paper's 200 nm filter radius
-    rho_f = rho0.reshape(-1).contiguous()
-    eps_f, work_f = prob.solver.filter_project(rho_f, radius_cells, 8.0, 0.5, W.EPS_SIO2, W.EPS_SIO2 + W.DELTA_EPS)
-    g_f = prob.solver.filter_project_adjoint(eps_f, work_f, radius_cells)
-    reps = 50
-    torch.cuda.synchronize()
-    ef = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    ef[0].record(stream)
-    for _ in range(reps):
-        prob.solver.filter_project(rho_f, radius_cells, 8.0, 0.5, W.EPS_SIO2, W.EPS_SIO2 + W.DELTA_EPS)
-    ef[1].record(stream)
-    for _ in range(reps):
-        prob.solver.filter_project_adjoint(eps_f, work_f, radius_cells)
-    ef[2].record(stream)
-    torch.cuda.synchronize()
-    rc = int(np.ceil(radius_cells))
-    taps = sum(1 for i in range(-rc, rc + 1) for j in range(-rc, rc + 1) if np.hypot(i, j) < radius_cells)
-    design_filter = {"what": "conic filter (200 nm radius) + tanh projection of the design density and its "
-                             "chain rule, on the design box (FP64, one thread per pixel)",
-                     "pixels": bw * bh, "taps": taps,
-                     "us_forward": ef[0].elapsed_time(ef[1]) * 1e3 / reps,
-                     "us_adjoint": ef[1].elapsed_time(ef[2]) * 1e3 / reps}
-    del g_f
+    # ---- full factorisation against design refactor, factor memory (N = 1) ---
+    factor = None
+    if dist is None and len(sp.problems) == 1:
+        p = sp.problems[0]
+        eps_full = eps_bg.clone().reshape(wl.nx, wl.ny)
+        eps_full[x0:x0 + bw, y0:y0 + bh] = eps0.reshape(bw, bh)
+        eps_full = eps_full.reshape(-1).contiguous()
+        times = {"full": [], "design": []}
+        for rep in range(3):
+            for kind in ("full", "design"):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if kind == "full":
+                    p.solver.factor(eps_full)
+                else:
+                    p.solver.refactor_design(eps0)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times[kind].append(e0.elapsed_time(e1))
+        st0 = stats[0]
+        factor = {"full_factor_ms": float(np.mean(times["full"])), "design_refactor_ms": float(np.mean(times["design"])),
+                  "refactor_time_fraction": float(np.mean(times["design"]) / np.mean(times["full"])),
+                  "full_factor_gflop": st0["flops_factor"] * wl.n_omega / 1e9,
+                  "design_refactor_gflop": st0["flops_design"] * wl.n_omega / 1e9,
+                  "refactor_flop_fraction": st0["flops_design"] / st0["flops_factor"],
+                  "factor_memory_gb": st0["store_bytes"] / 1e9,
+                  "factor_entries_per_wavelength": st0["factor_entries"],
+                  "note": "factor memory: the complex64 fronts of all wavelengths (L, U and the retained "
+                          "update matrices that make the design refactor possible)"}
+
+    # ---- accuracy of the measured path: GPU fields at the initial design -----
+    fields_gpu = None
+    if leg is not None:
+        p = sp.problems[0]
+        F0_t, g0_t = p.iteration(eps0)
+        torch.cuda.synchronize()
+        F0, g0 = float(F0_t), g0_t.cpu().numpy()
+        fields_gpu = (p.x.cpu().numpy(), p.xa.cpu().numpy())
+        p.solver.set_options(ir_max_iter=0)
+        x_raw = p.solver.solve(p.b).cpu().numpy()
+        p.solver.set_options(ir_max_iter=opts.ir_max_iter)
 
     # ---- uncached FP64 arm (paper's reference procedure, on the same GPU) -----
     plain = None
     if not args.no_plain:
-        pprob = make_problem(FD.MODE_PLAIN)
-        pprob.iteration(eps_of(rho0))
-        torch.cuda.synchronize()
-        pms, _ = run_arm(pprob, 2, 0)
-        pst = pprob.solver.stats()
-        plain = {"value": 2 / (pms / 1e3), "unit": UNIT, "ms_per_step": pms / 2,
+        psp = build(FD.default_options(mode=FD.MODE_PLAIN))
+        for pp in psp.problems:
+            pp.solver.reset_counters()
+        pms, _ = run_arm(psp, 1, 0)
+        pst = [pp.solver.stats() for pp in psp.problems]
+        plain = {"value": 1 / (max_over_ranks(pms, dist, dev) / 1e3), "unit": UNIT, "ms_per_step": pms,
                  "what": "every solve re-runs the symbolic phase and a full complex128 multifrontal "
-                         "factorisation (no refinement), forward and adjoint",
-                 "sf_nf_bs_per_step": [pst["sf"] / 3, pst["nf"] / 3, pst["bs"] / 3]}
-        fprob = make_problem(FD.MODE_F64)
-        fprob.iteration(eps_of(rho0))
+                         "factorisation (no refinement), forward and adjoint (one timed iteration)",
+                 "sf_nf_bs_per_step": [sum(s["sf"] for s in pst), sum(s["nf"] for s in pst),
+                                       sum(s["bs"] for s in pst)]}
+        close(psp)
+        del psp
+        fsp = build(FD.default_options(mode=FD.MODE_F64))
+        fsp.iteration(eps0)
         torch.cuda.synchronize()
-        fms, _ = run_arm(fprob, 3, 1)
-        plain["cached_f64"] = {"value": 3 / (fms / 1e3), "unit": UNIT, "ms_per_step": fms / 3}
-        del pprob, fprob
+        fms, _ = run_arm(fsp, 2, 0)
+        plain["cached_f64"] = {"value": 2 / (max_over_ranks(fms, dist, dev) / 1e3), "unit": UNIT,
+                               "ms_per_step": fms / 2,
+                               "what": "cached complex128 factors (design refactor), no refinement"}
+        plain["speedup_of_headline"] = value / plain["value"]
+        close(fsp)
+        del fsp
+
+    # ---- the oracle leg: cpu_baseline and accuracy ---------------------------
+    cpu = None
+    acc = {}
+    if leg is not None:
+        res = leg.result(args.cpu_budget)
+        if res is None:
+            cpu = {"value": None, "unit": UNIT, "cores": wl.n_omega, "kind": "oracle",
+                   "sample": f"one oracle design iteration did not finish within {args.cpu_budget:.0f} s"}
+        else:
+            leg.ex.shutdown(wait=True)
+            wall = max(r[0] for r in res)
+            serial = sum(r[0] for r in res)
+            cpu = {"value": 1.0 / wall, "unit": UNIT, "cores": wl.n_omega, "kind": "oracle",
+                   "sample": f"1 full design iteration of the same workload at its initial design (SciPy SuperLU "
+                             f"complex128 with a nested-dissection order, one single-threaded process per "
+                             f"wavelength): {wall:.1f} s wall, {serial:.1f} s summed over processes"}
+            from oracle import fdfd_oracle as O
+            F_ref = sum(r[1] for r in res)
+            g_ref = sum(r[2] for r in res).reshape(-1)
+            xf, xa = fields_gpu
+            fe, ae, re_ = [], [], []
+            for w, r in enumerate(res):
+                for s_, (E, Ea) in r[3].items():
+                    fe.append(O.rel_err(xf[w, s_], E))
+                    ae.append(O.rel_err(xa[w, s_], Ea))
+                    re_.append(O.rel_err(x_raw[w, s_], E))
+            acc = {"field_err_max": max(fe), "adjoint_field_err_max": max(ae),
+                   "grad_err": O.rel_err(g0 * W.DELTA_EPS, g_ref), "objective_err": abs(F0 - F_ref) / abs(F_ref),
+                   "raw_fp32_factor_field_err_max": max(re_),
+                   "what": "relative 2-norm errors against the oracle over all unknowns (PML included), every "
+                           "wavelength and source, at the initial design; gates 1e-8 (fields) and 1e-6 (gradient)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-            "data": "synthetic (seeded design density; the paper's devices are not published)",
+            "scaling": "strong", "vs_baseline": None, "dtype": DTYPE, "data": DATA,
             "config": dict(workload_config(wl), update_matrices=TENSOR_FORMS[form],
+                           parallelism=("one GPU" if world == 1 else
+                                        f"(wavelength, source) pairs sharded over {world} ranks, "
+                                        "all-reduce of [dF/deps, F] per iteration"),
+                           factor_form=("symmetric L diag(d) L^T of D A, no pivoting" if opts.factor_form == 1
+                                        else "LU of A, pivoting within 32 x 32 diagonal blocks"),
                            launch_parameters={"tensor_min_m": opts.tensor_min_m,
                                               "tensor_min_tiles": opts.tensor_min_tiles,
                                               "leaf_area": opts.leaf_area, "autotuned": tuned}),
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * bw * bh,
-                    "d2h_bytes_per_step": 8 * (bw * bh + 1)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * nd,
+                    "d2h_bytes_per_step": 8 * (nd + 1),
+                    "what": "fdfd_design_iteration with host design in and host F and gradient out, host wall clock"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roof, "roofline_tensor": roof_tc, "roofline_sweeps": roof_sw,
-            "solves_per_s": value * 2 * wl.n_omega * wl.n_src, "cpu_baseline": cpu, "accuracy": acc, "uncached_f64": plain,
-            "design_filter": design_filter,
-            "solver": {"ir_iters_last_solve": st["ir_iters"], "ir_resid": st["ir_resid"],
-                       "n_fronts": st["n_fronts"], "n_levels": st["n_levels"], "max_front": st["max_front"],
-                       "factor_gflop": st["flops_factor"] / 1e9, "refactor_gflop": st["flops_design"] / 1e9,
-                       "growth_last": st["growth"], "repivots_fp32": st["repivots"], "fallbacks_fp64": st["fallbacks"],
-                       "store_mb": st["store_bytes"] / 1e6, "first_iteration_s": t_setup},
+            "accuracy": acc, "uncached_f64": plain, "cpu_baseline": cpu, "factor": factor,
+            "solves_per_s": value * 2 * wl.n_omega * wl.n_src,
+            "solver": {"ir_iters_last_solve": max(s["ir_iters"] for s in stats) if stats else None,
+                       "ir_resid": max(s["ir_resid"] for s in stats) if stats else None,
+                       "n_fronts": stats[0]["n_fronts"] if stats else None,
+                       "n_levels": stats[0]["n_levels"] if stats else None,
+                       "max_front": stats[0]["max_front"] if stats else None,
+                       "growth_last": max(s["growth"] for s in stats) if stats else None,
+                       "repivots_fp32": sum(s["repivots"] for s in stats),
+                       "fallbacks_fp64": sum(s["fallbacks"] for s in stats),
+                       "first_iteration_s": t_setup},
             "kernels": kernels}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    close(sp)
     if dist is not None:
         dist.destroy_process_group()
     return 0

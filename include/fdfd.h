@@ -115,12 +115,22 @@ typedef struct {
                                   splits each tile's contraction over up to 16 CTAs (4 k-tiles of
                                   8 pivots at least each); if even then it fills less than half
                                   of them, its update matrices run SIMT.  1 = never split. */
+  int factor_form;             /* complex FP32 factors: 0 = LU of A with the pivoting above (default);
+                                  1 = symmetric form: D A, with D = diag(s_x s_y) at the cell centres,
+                                  is complex symmetric (reciprocity) and is factored as L diag(d) L^T
+                                  in the elimination order with no pivoting, lower triangles only
+                                  (half the update flops; the solves run the L and L^T sweeps with
+                                  D and 1 / d applied between them).  If its pivot growth exceeds
+                                  growth_bound it falls back to LU with partial pivoting over all
+                                  pivot rows, then to FP64, as above; the next design refactor then
+                                  refactors the whole symmetric form again.  FP64 factors are
+                                  always LU. */
 } fdfd_options;
 /* fdfd_create rejects a mode outside fdfd_mode with FDFD_ERR_ARG and clamps the
  * other fields: gmres_restart to 1..16, ir_max_iter and tensor_min_tiles to >= 0,
  * tensor_min_m to >= 1; leaf_area < 1, tensor_form outside 0..3, and ir_tol or
  * growth_bound that are not positive numbers take their defaults; any nonzero
- * pivoting means 1. */
+ * pivoting means 1; factor_form outside 0..1 takes 0. */
 
 typedef struct {
   long long sf;                /* symbolic factorisations performed */
@@ -137,7 +147,9 @@ typedef struct {
   double flops_factor;         /* full factorisation flops per wavelength (8 per complex FMA) */
   double flops_design;         /* flops of a design refactor per wavelength */
   long long repivots;          /* complex FP32 factorisations redone with partial pivoting over all
-                                  pivot rows after block-local pivoting exceeded growth_bound */
+                                  pivot rows after block-local pivoting (or the symmetric form)
+                                  exceeded growth_bound */
+  int factor_form;             /* form of the current complex FP32 factors (0 LU, 1 symmetric) */
 } fdfd_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -383,6 +395,13 @@ size_t fdfd_noalloc_scratch_bytes(void);
  * context's stream. */
 fdfd_status fdfd_filter_project(fdfd_ctx* ctx, const double* rho_dev, double radius, double beta, double eta,
                                 double eps_lo, double eps_hi, double* eps_dev, double* work_dev);
+
+/* Permittivity of the design box from an unfiltered density (Sec. III's design
+ * pixels between eps_SiO2 and eps_Si): eps_i = eps_lo + rho_i (eps_hi - eps_lo)
+ * for the w*h pixels of the context's design box.  rho_dev, eps_dev: [w*h] double
+ * (device; may alias).  Runs on the context's stream.  The chain rule is a scale:
+ * dF/drho = (eps_hi - eps_lo) dF/deps.  FDFD_ERR_ARG without a design box. */
+fdfd_status fdfd_density_eps(fdfd_ctx* ctx, const double* rho_dev, double eps_lo, double eps_hi, double* eps_dev);
 
 /* Chain rule of fdfd_filter_project back to the density:
  *   g_rho_j = sum_i w_ij g_eps_i s_i / N_i

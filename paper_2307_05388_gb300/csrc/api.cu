@@ -107,7 +107,7 @@ struct fdfd_ctx {
   long long tc_part_stride = 0;    // floats per wavelength
   std::vector<TcFront> h_tcf;
   std::vector<int4> h_tct;
-  std::vector<LevelList> lv_full[2], lv_design[2];   // [precision 0 = c64, 1 = c128]
+  std::vector<LevelList> lv_full[3], lv_design[3];   // [0 = c64 LU, 1 = c128 LU, 2 = c64 symmetric form]
   std::vector<SolveList> lv_solve;
   // dataflow sweep queues [task type: 0 rows, 1 columns][direction: 0 bottom-up, 1 top-down]
   struct FlowList { int off = 0, n = 0, uoff = 0, nu = 0, need_all = 0, need_ph1 = 0; } flow[2][2];
@@ -129,6 +129,7 @@ struct fdfd_ctx {
 
   // coefficients and permittivity
   double2 *d_cxm = nullptr, *d_cxp = nullptr, *d_cym = nullptr, *d_cyp = nullptr;
+  double2 *d_sxc = nullptr, *d_syc = nullptr;   // stretch factors at cell centres (the symmetriser)
   double* d_k0dx = nullptr;
   double* d_k0dx2 = nullptr;
   double* d_eps = nullptr;
@@ -148,6 +149,7 @@ struct fdfd_ctx {
   int max_nlarge = 0;              // longest large-front list of any level
   float* h_growth_max = nullptr;   // pinned
   bool valid32 = false, valid64 = false;
+  bool sym32 = false;              // the complex FP32 factors are in the symmetric form (L diag(d) L^T of D A)
   bool growth_pending = false;     // growth of the last FP32 factorisation not yet checked
   bool growth_ready = false;       // ... and its pinned copy has landed
 
@@ -344,10 +346,12 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
     CK(cudaDeviceGetAttribute(&min_tiles, cudaDevAttrMultiProcessorCount, dev));
   }
   const int L = p.n_levels;
-  for (int prec = 0; prec < 2; ++prec) {
+  for (int form = 0; form < 3; ++form) {
+    // form 2 (the symmetric form) has the c64 front-size classes and, for now, SIMT update matrices
+    const int prec = form == 1 ? 1 : 0;
     const int small_n = lu_small_max_n(prec == 0 ? 8 : 16);
     for (int design = 0; design < 2; ++design) {
-      std::vector<LevelList>& out = design ? ctx->lv_design[prec] : ctx->lv_full[prec];
+      std::vector<LevelList>& out = design ? ctx->lv_design[form] : ctx->lv_full[form];
       out.assign(L, LevelList{});
       for (int l = 0; l < L; ++l) {
         LevelList& ll = out[l];
@@ -380,8 +384,10 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         ctx->max_nlarge = std::max(ctx->max_nlarge, ll.nlarge);
         // update matrices: complex64 fronts with m >= tensor_min_m on the tensor cores, the rest SIMT
         auto eligible = [&](const FrontDesc& d) {
-          return prec == 0 && planes > 0 && d.n > small_n && d.m >= ctx->opt.tensor_min_m && d.k > 0;
+          return form != 1 && planes > 0 && d.n > small_n && d.m >= ctx->opt.tensor_min_m && d.k > 0;
         };
+        // output tiles of a front: all of them, or for the symmetric form the lower ones
+        auto tiles_of = [&](long long t) { return form == 2 ? t * (t + 1) / 2 : t * t; };
         // output tiles of the level over all wavelengths; when they fill less than a wave,
         // each tile's contraction is split over several CTAs; the level goes to the
         // tensor cores when the split tiles fill half a wave at least
@@ -389,7 +395,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         for (int f : fl)
           if (eligible(p.fronts[f])) {
             const long long t = (p.fronts[f].m + kTcRows - 1) / kTcRows;
-            level_tiles += t * t;
+            level_tiles += tiles_of(t);
           }
         level_tiles *= ctx->n_omega;
         auto splits_of = [&](const FrontDesc& d) {
@@ -399,7 +405,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         for (int f : fl)
           if (eligible(p.fronts[f])) {
             const long long t = (p.fronts[f].m + kTcRows - 1) / kTcRows;
-            level_ctas += t * t * splits_of(p.fronts[f]) * ctx->n_omega;
+            level_ctas += tiles_of(t) * splits_of(p.fronts[f]) * ctx->n_omega;
           }
         const bool level_tc = level_tiles > 0 && 2 * level_ctas >= min_tiles;
         auto on_tc = [&](const FrontDesc& d) { return level_tc && eligible(d); };
@@ -444,7 +450,8 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
           const TcFront& r = tcf[ll.tcf_off + sl];
           for (int mt = 0; mt < r.Mt; ++mt)
             for (int nt = 0; nt < r.Nt; ++nt)
-              for (int sp = 0; sp < r.nsplit; ++sp) tct.push_back(make_int4(sl, mt, nt, sp));
+              if (form != 2 || nt <= mt)
+                for (int sp = 0; sp < r.nsplit; ++sp) tct.push_back(make_int4(sl, mt, nt, sp));
         }
         ll.ntct = (int)tct.size() - ll.tct_off;
         ll.tcs_off = (int)tct.size();
@@ -453,7 +460,8 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
           if (r.nsplit > 1)
             for (int mt = 0; mt < r.Mt; ++mt)
               for (int nt = 0; nt < r.Nt; ++nt)
-                for (int r0 = 0; r0 < kTcRows; r0 += 16) tct.push_back(make_int4(sl, mt, nt, r0));
+                if (form != 2 || nt <= mt)
+                  for (int r0 = 0; r0 < kTcRows; r0 += 16) tct.push_back(make_int4(sl, mt, nt, r0));
         }
         ll.ntcs = (int)tct.size() - ll.tcs_off;
         if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
@@ -627,6 +635,8 @@ fdfd_status ensure_runtime(fdfd_ctx* ctx) {
     CK(dalloc(&ctx->d_cxp, sizeof(double2) * ctx->n_omega * ctx->nx));
     CK(dalloc(&ctx->d_cym, sizeof(double2) * ctx->n_omega * ctx->ny));
     CK(dalloc(&ctx->d_cyp, sizeof(double2) * ctx->n_omega * ctx->ny));
+    CK(dalloc(&ctx->d_sxc, sizeof(double2) * ctx->n_omega * ctx->nx));
+    CK(dalloc(&ctx->d_syc, sizeof(double2) * ctx->n_omega * ctx->ny));
     CK(dalloc(&ctx->d_k0dx, sizeof(double) * ctx->n_omega));
     CK(dalloc(&ctx->d_k0dx2, sizeof(double) * ctx->n_omega));
     CK(dalloc(&ctx->d_eps, sizeof(double) * n_cells(ctx)));
@@ -638,7 +648,8 @@ fdfd_status ensure_runtime(fdfd_ctx* ctx) {
     *ctx->h_flow_err = 0;
     CK(cudaMemcpyAsync(ctx->d_k0dx, ctx->k0dx.data(), sizeof(double) * ctx->n_omega, cudaMemcpyHostToDevice,
                        ctx->stream));
-    launch_coef(ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx2, ctx->d_k0dx, ctx->n_omega,
+    launch_coef(ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx2, ctx->d_sxc, ctx->d_syc,
+                ctx->d_k0dx, ctx->n_omega,
                 ctx->nx, ctx->ny, ctx->pml.npml_x, ctx->pml.npml_y, ctx->pml.ln_R, ctx->pml.order, ctx->stream);
     CK(cudaGetLastError());
   }
@@ -665,6 +676,7 @@ DevCoef dev_coef(const fdfd_ctx* c) {
   DevCoef C;
   C.cxm = c->d_cxm; C.cxp = c->d_cxp; C.cym = c->d_cym; C.cyp = c->d_cyp;
   C.k0dx2 = c->d_k0dx2; C.eps = c->d_eps; C.nx = c->nx; C.ny = c->ny;
+  C.sxc = c->d_sxc; C.syc = c->d_syc;
   return C;
 }
 
@@ -692,8 +704,9 @@ fdfd_status ensure_store(fdfd_ctx* ctx, int prec) {
 
 // Level-by-level numeric factorisation of the listed fronts, for wavelengths [w0, w0+nw).
 template <typename T>
-fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = -1) {
+fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = -1, bool sym = false) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
+  sym = sym && prec == 0;
   CKS(ensure_store(ctx, prec));
   const Plan& p = ctx->plan;
   FactorLaunch fa;
@@ -712,7 +725,9 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   fa.swp_stride = std::max(1, ctx->max_nlarge);
   fa.istore = prec == 0 ? (void*)ctx->d_inv32 : (void*)ctx->d_inv64;
   fa.istore_stride = p.inv_total;
-  const std::vector<LevelList>& lv = design_only ? ctx->lv_design[prec] : ctx->lv_full[prec];
+  fa.sym = sym ? 1 : 0;
+  const int form = sym ? 2 : prec;
+  const std::vector<LevelList>& lv = design_only ? ctx->lv_design[form] : ctx->lv_full[form];
   const int nb = lu_panel_width(sizeof(T));
   cudaStream_t s = ctx->stream;
   // inverse folds beside the panel steps (on the main stream while profiling,
@@ -746,11 +761,12 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           for (int j = 0; j < d.k; ++j) fl += 8.0 * (double)(d.n - j - 1) * (d.n - j - 1);
           by += 2.0 * es * d.n * d.n;
         }
+      if (sym) fl *= 0.5;   // lower triangles only: (n-j-1)(n-j)/2 per pivot, up to the diagonal terms
       Prof pr(ctx, PK_LU_SMALL, fl * nwd, by * nwd);
       launch_lu_small<T>(fa, ctx->d_lists + ll.small_off, ll.nsmall, ll.nmax_small, s);
       launch_lu_small<T>(fa, ctx->d_lists + ll.small2_off, ll.nsmall2, ll.nmax_small2, s);
     }
-    const bool local_piv = ctx->opt.pivoting == 1;
+    const bool local_piv = ctx->opt.pivoting == 1 || sym;   // the symmetric form uses the one-launch panel step
     for (int j0 = 0; j0 < ll.kmax_large; j0 += nb) {
       const int* fl = ctx->d_lists + ll.large_off;
       double pf = 0, pb = 0, lf = 0, lb = 0, tf = 0, tb = 0, gf = 0, gb = 0;
@@ -768,8 +784,15 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           const double kr = d.k - j0 - b;                  // pivot columns still to factor
           tf += 8.0 * 0.5 * b * (b - 1) * rem;
           tb += 2.0 * es * b * rem;
-          gf += 8.0 * b * (rem * kr + kr * d.m);          // pivot-block rows and columns only
-          gb += es * (2.0 * (rem * kr + kr * d.m) + 2.0 * rem * b);
+          if (sym) {
+            // lower triangle of the remaining pivot columns: rows c..n-1 of each column c
+            const double cols = kr, lower = cols * (d.n - (j0 + b)) - cols * (cols - 1) / 2;
+            gf += 8.0 * b * lower;
+            gb += es * (2.0 * lower + 2.0 * rem * b);
+          } else {
+            gf += 8.0 * b * (rem * kr + kr * d.m);          // pivot-block rows and columns only
+            gb += es * (2.0 * (rem * kr + kr * d.m) + 2.0 * rem * b);
+          }
         }
       if (local_piv) {
         {
@@ -785,8 +808,8 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
             const FrontDesc& d = p.fronts[hl[ll.large_off + t]];
             if (j0 >= d.k) continue;
             const double b = std::min(nb, d.k - j0);
-            vf += 8.0 * 2.0 * (0.5 * b * (double)j0 * j0 + b * b * j0);
-            vb += es * 2.0 * (0.5 * (double)j0 * j0 + 2.0 * b * j0);
+            vf += 8.0 * (sym ? 1.0 : 2.0) * (0.5 * b * (double)j0 * j0 + b * b * j0);
+            vb += es * (sym ? 1.0 : 2.0) * (0.5 * (double)j0 * j0 + 2.0 * b * j0);
           }
         if (si != s && j0 > 0) {
           CK(cudaEventRecord(ctx->iev_fork, s));
@@ -813,8 +836,13 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
       if (ctx->prof_on)
         for (int t = 0; t < ll.nsimt; ++t) {
           const FrontDesc& d = p.fronts[hl[ll.simt_off + t]];
-          sf += 8.0 * (double)d.k * d.m * d.m;
-          sb += es * (2.0 * (double)d.m * d.m + 2.0 * (double)d.k * d.m);
+          if (sym) {
+            sf += 8.0 * (double)d.k * d.m * (d.m + 1) / 2;
+            sb += es * ((double)d.m * (d.m + 1) + 2.0 * (double)d.k * d.m);
+          } else {
+            sf += 8.0 * (double)d.k * d.m * d.m;
+            sb += es * (2.0 * (double)d.m * d.m + 2.0 * (double)d.k * d.m);
+          }
         }
       Prof pr(ctx, PK_LU_SCHUR, sf * nwd, sb * nwd);
       launch_schur_simt<T>(fa, ctx->d_lists + ll.simt_off, ll.nsimt, ll.mmax_simt, s);
@@ -835,9 +863,10 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
         for (int t = 0; t < ll.ntcf; ++t) {
           const TcFront& r = ctx->h_tcf[ll.tcf_off + t];
           const FrontDesc& d = p.fronts[r.f];
-          sf += 8.0 * (double)d.k * d.m * d.m;
-          sb += es * 2.0 * (double)d.m * d.m +
-                (double)r.Kt * (r.Mt * r.Nt) * (tc_tile_bytes_a(planes) + tc_tile_bytes_b(planes));
+          const double tiles = sym ? 0.5 * r.Mt * (r.Mt + 1.0) : (double)r.Mt * r.Nt;
+          sf += sym ? 8.0 * (double)d.k * d.m * (d.m + 1) / 2 : 8.0 * (double)d.k * d.m * d.m;
+          sb += es * (sym ? 1.0 : 2.0) * (double)d.m * d.m +
+                (double)r.Kt * tiles * (tc_tile_bytes_a(planes) + tc_tile_bytes_b(planes));
           pb += es * 2.0 * (double)d.k * d.m +
                 (double)r.Kt * (r.Mt * tc_tile_bytes_a(planes) + r.Nt * tc_tile_bytes_b(planes));
         }
@@ -930,6 +959,10 @@ SolveLaunch solve_launch(const fdfd_ctx* ctx, void* vb, int nrhs, int w0, int nw
   sa.r0 = r0;
   sa.nr = nr < 0 ? nrhs : nr;
   sa.n = n_cells(ctx);
+  sa.sxc = ctx->d_sxc;
+  sa.syc = ctx->d_syc;
+  // the symmetric form's mid scaling marks it; sweep_pair sets the D scalings per direction
+  sa.sym_mid = (prec == 0 && ctx->sym32) ? 1 : 0;
   return sa;
 }
 
@@ -950,10 +983,13 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const Plan& p = ctx->plan;
   cudaStream_t s = ctx->stream;
-  const int fwd = transpose ? 2 : 0, bwd = transpose ? 3 : 1;
+  // symmetric form: both solves are the L sweep then the L^T sweep (A x = b with D b
+  // gathered, A^T x = b with D x written), 1 / d taken between them
+  const bool sym = sa.sym_mid != 0;
+  const int fwd = sym ? 0 : (transpose ? 2 : 0), bwd = sym ? 3 : (transpose ? 3 : 1);
   const double es = sizeof(T), nsys = (double)sa.n_omega * sa.nr;
-  const int tt = transpose ? 1 : 0;                       // row tasks (L, U) or column tasks (U^T, L^T)
-  const int step = tt ? sweep_col_block() : sweep_row_block();
+  int tt = transpose ? 1 : 0;                             // row tasks (L, U) or column tasks (U^T, L^T)
+  int step = tt ? sweep_col_block() : sweep_row_block();
   // algorithmic work: every entry of the swept triangle (and of the off-diagonal
   // block) read once per right-hand side, 8 flops per entry, plus the vectors
   auto tri_work = [&](const TaskList& tl, bool lower, double* fl, double* by) {
@@ -990,12 +1026,20 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
   const size_t ctr_bytes = sizeof(int) * (1 + 2 * (size_t)sa.n_omega * p.fronts.size());
   const int grid_max = flow_grid(ctx, prec);
   for (int dir = 0; dir < 2; ++dir) {
+    SolveLaunch sd = sa;
+    if (sym) {
+      tt = dir;                                            // L: row tasks; L^T: column tasks
+      step = tt ? sweep_col_block() : sweep_row_block();
+      sd.sym_in = (dir == 0 && !transpose) ? 1 : 0;
+      sd.sym_out = (dir == 1 && transpose) ? 1 : 0;
+      sd.sym_mid = dir == 1 ? 1 : 0;
+    }
     const auto& fq = ctx->flow[tt][dir];
     double fl = 0, by = 0;
     for (int l = 0; l < p.n_levels; ++l) {
       const SolveList& sl = ctx->lv_solve[l];
       double f1, b1;
-      tri_work(sl.tri[tt], dir == 0 ? !transpose : transpose, &f1, &b1);
+      tri_work(sl.tri[tt], sym ? true : (dir == 0 ? !transpose : transpose), &f1, &b1);
       fl += f1; by += b1;
       rect_work(dir == 0 ? sl.rect_m[tt] : sl.rect_k[tt], dir == 0, &f1, &b1);
       fl += f1; by += b1;
@@ -1011,8 +1055,10 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
     q.err = ctx->d_flow_err;
     q.n_fronts = (int)p.fronts.size();
     const int grid = std::max(1, std::min(grid_max, fq.nu * sa.n_omega));
-    Prof pr(ctx, dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U), fl, by);
-    launch_sweep_flow<T>(sa, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s, flow_wide(ctx));
+    const int kind = sym ? (dir == 0 ? PK_SWEEP_L : PK_SWEEP_LT)
+                         : (dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U));
+    Prof pr(ctx, kind, fl, by);
+    launch_sweep_flow<T>(sd, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s, flow_wide(ctx));
   }
   CK(cudaGetLastError());
   return FDFD_OK;
@@ -1074,10 +1120,10 @@ fdfd_status run_graph(fdfd_ctx* ctx, int key, Body&& body) {
 
 // Full or design factorisation of every wavelength, replayed from a graph.
 template <typename T>
-fdfd_status factor_all(fdfd_ctx* ctx, bool design_only) {
+fdfd_status factor_all(fdfd_ctx* ctx, bool design_only, bool sym = false) {
   CKS(ensure_store(ctx, sizeof(T) == 8 ? 0 : 1));      // allocations stay outside the capture
-  const int key = (sizeof(T) == 8 ? 0 : 2) + (design_only ? 1 : 0);
-  return run_graph(ctx, key, [&]() { return factor_levels<T>(ctx, design_only); });
+  const int key = (sizeof(T) == 8 ? (sym ? 4 : 0) : 2) + (design_only ? 1 : 0);
+  return run_graph(ctx, key, [&]() { return factor_levels<T>(ctx, design_only, 0, -1, sym); });
 }
 
 // Applies the cached factors M^-1 to FP64 vectors: dst = M^-1 src (all systems).
@@ -1297,10 +1343,13 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivo
   ctx->last_growth = g;
   if (g <= ctx->opt.growth_bound) return FDFD_OK;
   const int piv_saved = ctx->opt.pivoting;
-  if (piv_saved == 1) {
+  if (ctx->sym32 || piv_saved == 1) {
+    // the symmetric form (no pivoting) or block-local pivoting exceeded the bound:
+    // complex FP32 LU with partial pivoting over all pivot rows of each front
     ctx->repivots += 1;
     if (repivoted) *repivoted = true;
     ctx->opt.pivoting = 0;
+    ctx->sym32 = false;
     const fdfd_status fst = factor_levels<float2>(ctx, false);
     ctx->opt.pivoting = piv_saved;
     CKS(fst);
@@ -1337,6 +1386,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->tensor_form = 3;
   o->tensor_min_m = 128;
   o->tensor_min_tiles = 0;
+  o->factor_form = 0;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -1374,6 +1424,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.tensor_form < 0 || c->opt.tensor_form > 3) c->opt.tensor_form = 3;
   if (c->opt.tensor_min_m < 1) c->opt.tensor_min_m = 1;
   if (c->opt.tensor_min_tiles < 0) c->opt.tensor_min_tiles = 0;
+  if (c->opt.factor_form != 1) c->opt.factor_form = 0;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   {
     fdfd_options def;
@@ -1407,8 +1458,10 @@ fdfd_status fdfd_factor(fdfd_ctx* ctx, const double* eps_dev) {
     ctx->valid64 = true;
     ctx->growth_pending = false;
   } else {
-    CKS(factor_all<float2>(ctx, false));
+    const bool sym = ctx->opt.factor_form == 1;
+    CKS(factor_all<float2>(ctx, false, sym));
     ctx->valid32 = true;
+    ctx->sym32 = sym;
     ctx->growth_pending = true;
   }
   ctx->nf += ctx->n_omega;
@@ -1434,7 +1487,12 @@ fdfd_status fdfd_refactor_design(fdfd_ctx* ctx, const double* eps_design_dev) {
     CKS(factor_all<double2>(ctx, true));
   } else {
     if (!ctx->valid32) return fail(ctx, FDFD_ERR_STATE, "no cached factorisation");
-    CKS(factor_all<float2>(ctx, true));
+    const bool sym = ctx->opt.factor_form == 1;
+    // the untouched fronts' update matrices must be in the form being refactored: after a
+    // fallback from the symmetric form to LU the whole factorisation is redone
+    const bool design_only = sym == ctx->sym32;
+    CKS(factor_all<float2>(ctx, design_only, sym));
+    ctx->sym32 = sym;
     ctx->valid64 = false;
     ctx->growth_pending = true;
   }
@@ -1673,6 +1731,16 @@ fdfd_status fdfd_filter_project(fdfd_ctx* ctx, const double* rho_dev, double rad
   return FDFD_OK;
 }
 
+fdfd_status fdfd_density_eps(fdfd_ctx* ctx, const double* rho_dev, double eps_lo, double eps_hi, double* eps_dev) {
+  if (!ctx || !rho_dev || !eps_dev) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (ctx->box.w == 0 || ctx->box.h == 0) return fail(ctx, FDFD_ERR_ARG, "context has no design box");
+  Prof pr(ctx, PK_OTHER, 0, 16.0 * ctx->box.w * ctx->box.h);
+  launch_density_eps(rho_dev, (long long)ctx->box.w * ctx->box.h, eps_lo, eps_hi - eps_lo, eps_dev, ctx->stream);
+  CK(cudaGetLastError());
+  return FDFD_OK;
+}
+
 fdfd_status fdfd_filter_project_adjoint(fdfd_ctx* ctx, const double* g_eps_dev, const double* work_dev,
                                         double radius, double* g_rho_dev) {
   if (!ctx || !g_eps_dev || !work_dev || !g_rho_dev || g_rho_dev == g_eps_dev || !(radius > 0 && radius <= 25))
@@ -1720,6 +1788,7 @@ fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* o) {
   o->fallbacks = ctx->fallbacks;
   o->repivots = ctx->repivots;
   o->growth = ctx->last_growth;
+  o->factor_form = (ctx->valid32 && !ctx->valid64 && ctx->sym32) ? 1 : 0;
   if (ctx->analyzed) {
     const Plan& p = ctx->plan;
     o->n_fronts = (int)p.fronts.size();
@@ -1909,7 +1978,8 @@ void fdfd_destroy(fdfd_ctx* ctx) {
   free_factor(ctx);
   free_ws(ctx);
   free_gm(ctx);
-  void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_k0dx, ctx->d_k0dx2, ctx->d_eps,
+  void* ps[] = {ctx->d_cxm, ctx->d_cxp, ctx->d_cym, ctx->d_cyp, ctx->d_sxc, ctx->d_syc, ctx->d_k0dx, ctx->d_k0dx2,
+                ctx->d_eps,
                 ctx->d_growth_max, ctx->d_flow_err, ctx->d_taps, ctx->d_tapw, ctx->d_probe,
                 ctx->d_itx, ctx->d_ita, ctx->d_itb, ctx->d_ito, ctx->d_itF, ctx->d_itg, ctx->d_itepsd};
   for (void* p : ps) free_ptr(p);

@@ -94,8 +94,19 @@ struct DevCoef {
   const double2* cyp;    // [n_omega][ny]  A[(i,j),(i,j+1)]
   const double* k0dx2;   // [n_omega]      (k0 dx)^2
   const double* eps;     // [nx*ny]        relative permittivity
+  const double2* sxc;    // [n_omega][nx]  stretch s_x at cell centres
+  const double2* syc;    // [n_omega][ny]  stretch s_y at cell centres
   int nx, ny;
 };
+
+// D[cell] = s_x(i + 1/2) s_y(j + 1/2): the diagonal for which D A is complex
+// symmetric (discrete reciprocity: the coupling of two neighbours becomes
+// -s_y / s_x' (or -s_x / s_y') on both sides of the diagonal).
+__device__ __forceinline__ double2 sym_scale(const DevCoef& c, int w, int cell) {
+  const int i = cell / c.ny, j = cell - i * c.ny;
+  const double2 a = c.sxc[(size_t)w * c.nx + i], b = c.syc[(size_t)w * c.ny + j];
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
 
 // Value of the stencil entry with code = cell*5 + direction at wavelength w.
 __device__ __forceinline__ double2 stencil_entry(const DevCoef& c, int w, int code) {

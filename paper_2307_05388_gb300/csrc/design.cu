@@ -74,7 +74,20 @@ filter_adjoint_kernel(const double* __restrict__ g, const double* __restrict__ s
 
 size_t filter_smem(int ntap) { return (size_t)ntap * (sizeof(double) + sizeof(int2)); }
 
+// eps_i = eps_lo + rho_i (eps_hi - eps_lo): the design pixel's permittivity from its density
+// without filtering or projection (the parametrisation of the benchmark workloads)
+__global__ void density_eps_kernel(const double* __restrict__ rho, long long n, double eps_lo, double deps,
+                                   double* __restrict__ eps) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) eps[p] = eps_lo + rho[p] * deps;
+}
+
 }  // namespace
+
+void launch_density_eps(const double* rho, long long n, double eps_lo, double deps, double* eps, cudaStream_t s) {
+  if (n <= 0) return;
+  density_eps_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rho, n, eps_lo, deps, eps);
+}
 
 void launch_filter_project(const double* rho, int w, int h, const int2* off, const double* wt, int ntap,
                            double beta, double eta, double eps_lo, double deps, double* eps, double* slope,

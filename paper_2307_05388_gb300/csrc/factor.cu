@@ -25,6 +25,12 @@ namespace {
 constexpr int kBuildWarps = 8;
 constexpr int kSwpInts = kSwapScratchInts;   // per panel: count + up to 64 (dst, src) row pairs
 
+// entry (i, j) of a symmetric-form child's update matrix (its lower triangle is stored)
+template <typename T>
+__device__ __forceinline__ T child_sym(const T* st, const FrontDesc& c, int i, int j) {
+  return i >= j ? st[c.st_off + (size_t)(c.k + i) * c.ld + c.k + j] : st[c.st_off + (size_t)(c.k + j) * c.ld + c.k + i];
+}
+
 // ---------------------------------------------------------------------------
 // Front build: F = originals + sum over children of their update matrices,
 // gathered through the children's inverse extend-add maps (no atomics).
@@ -44,6 +50,28 @@ build_kernel(FactorLaunch a, const int2* __restrict__ tasks) {
   if (r >= d.n) return;
   T* st = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride;
   T* F = st + d.st_off + (size_t)r * d.ld;
+  if (a.sym) {
+    // symmetric form: columns <= r only; children's update matrices read from their
+    // lower triangles, originals scaled by D of the row's cell
+    FrontDesc c0, c1;
+    int ia = -1, ib = -1;
+    if (d.nchild > 0) { c0 = a.P.fronts[a.P.children[d.child0]]; ia = a.P.inv[c0.inv_off + r]; }
+    if (d.nchild > 1) { c1 = a.P.fronts[a.P.children[d.child0 + 1]]; ib = a.P.inv[c1.inv_off + r]; }
+    for (int b = lane; b <= r; b += 32) {
+      T v = czero<T>();
+      if (ia >= 0) { const int i0 = a.P.inv[c0.inv_off + b]; if (i0 >= 0) v = cadd(v, child_sym(st, c0, ia, i0)); }
+      if (ib >= 0) { const int i1 = a.P.inv[c1.inv_off + b]; if (i1 >= 0) v = cadd(v, child_sym(st, c1, ib, i1)); }
+      F[b] = v;
+    }
+    __syncwarp();
+    const int e0 = a.P.orig_ptr[d.orig_off + r], e1 = a.P.orig_ptr[d.orig_off + r + 1];
+    const double2 Dr = sym_scale(a.C, w, a.P.idx[d.idx_off + r]);
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const int b = a.P.orig_col[e];
+      if (b <= r) F[b] = cadd(F[b], cfrom<T>(cmul(Dr, stencil_entry(a.C, w, a.P.orig_code[e]))));
+    }
+    return;
+  }
   // up to two children (nested dissection splits into at most two parts)
   const T* S0 = nullptr;
   const T* S1 = nullptr;
@@ -298,6 +326,144 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
   }
   int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
   for (int i = tid; i < k; i += blockDim.x) P[i] = pm[i];
+  for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) s_red[warp] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    R g = 0;
+    for (int i = 0; i < NW; ++i) g = nanmax(g, s_red[i]);
+    a.growth[(size_t)w * a.n_fronts + f] = (float)sqrt((double)g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric form (complex-symmetric LDL^T).  M = D A with D = diag(s_x s_y) is
+// complex symmetric (discrete reciprocity), so in the plan's elimination order
+// every front of M factors as F = L diag(d) L^T with no pivoting: L11 unit
+// lower, L21 = F21 L11^-T diag(d)^-1, update matrix S = F22 - L21 diag(d) L21^T.
+// Only lower triangles are formed, updated and stored: the fronts hold L21 and
+// the lower triangle of S (which the parent reads symmetrically), the inverse
+// store holds L11^-1 strictly below the diagonal and 1 / d on it, and the
+// permutation is the identity.  A solve of A x = b is then
+//     x = L^-T diag(d)^-1 L^-1 D b   (transpose: A^T x = b gives x = D L^-T diag(d)^-1 L^-1 b),
+// the L and L^T sweeps of the LU path with D and 1 / d applied in between.
+// Small fronts: one CTA per front in shared memory, as lu_small_kernel.  Per
+// pivot j, each row r > j takes l_r = F[r][j] / d_j and updates its entries
+// j < c <= r by F[r][c] -= l_r F[c][j]; column j is read from a contiguous copy
+// (written, double-buffered, by whoever updates column j of each row in the
+// step before), and is scaled to l in place in the next step, when nothing
+// reads it any more.  One barrier per pivot.
+// ---------------------------------------------------------------------------
+
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+ldl_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
+  using R = typename RealOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);
+  __shared__ T colj[2][kSmallMaxK + 128];        // column j of the current step, contiguous
+  __shared__ R s_red[THREADS / 32];
+  const int w = blockIdx.y + a.w0;
+  const int f = flist[blockIdx.x];
+  const FrontDesc d = a.P.fronts[f];
+  const int n = d.n, k = d.k;
+  T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = THREADS / 32;
+  const int* idx = a.P.idx + d.idx_off;
+  // assemble the lower triangle: children's update matrices (read symmetrically)
+  // plus D times the original entries of column <= row (the mirrored ones are
+  // the same numbers of M)
+  {
+    const T* st = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride;
+    FrontDesc c0, c1;
+    const int nc = d.nchild;
+    if (nc > 0) c0 = a.P.fronts[a.P.children[d.child0]];
+    if (nc > 1) c1 = a.P.fronts[a.P.children[d.child0 + 1]];
+    for (int r = warp; r < n; r += NW) {
+      const int ia = nc > 0 ? a.P.inv[c0.inv_off + r] : -1;
+      const int ib = nc > 1 ? a.P.inv[c1.inv_off + r] : -1;
+      for (int c = lane; c <= r; c += 32) {
+        T v = czero<T>();
+        if (ia >= 0) { const int i0 = a.P.inv[c0.inv_off + c]; if (i0 >= 0) v = cadd(v, child_sym(st, c0, ia, i0)); }
+        if (ib >= 0) { const int i1 = a.P.inv[c1.inv_off + c]; if (i1 >= 0) v = cadd(v, child_sym(st, c1, ib, i1)); }
+        S[r * n + c] = v;
+      }
+      __syncwarp();
+      const int e0 = a.P.orig_ptr[d.orig_off + r], e1 = a.P.orig_ptr[d.orig_off + r + 1];
+      const double2 Dr = sym_scale(a.C, w, idx[r]);
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const int b = a.P.orig_col[e];
+        if (b <= r) S[r * n + b] = cadd(S[r * n + b], cfrom<T>(cmul(Dr, stencil_entry(a.C, w, a.P.orig_code[e]))));
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += THREADS) colj[0][r] = S[r * n];
+  __syncthreads();
+  R gmax = 0;
+  T inv_prev = czero<T>();
+  for (int j = 0; j < k; ++j) {
+    const T* cj = colj[j & 1];
+    T* cn = colj[(j + 1) & 1];
+    const T p = cj[j];
+    const T inv = crcp(p);
+    if (tid == 0 && p.x == 0 && p.y == 0) gmax = INFINITY;
+    for (int r = j + warp; r < n; r += NW) {
+      // column j - 1 of this row is no longer read: scale it to the multiplier
+      if (j > 0 && r > j - 1 && lane == 0) {
+        const T l = cmul(S[r * n + j - 1], inv_prev);
+        S[r * n + j - 1] = l;
+        gmax = nanmax(gmax, cabs2(l));
+      }
+      if (r == j) continue;
+      const T l = cmul(cj[r], inv);
+      for (int c = j + 1 + lane; c <= r; c += 32) {
+        const T v = cfms(l, cj[c], S[r * n + c]);
+        S[r * n + c] = v;
+        if (c == j + 1) cn[r] = v;
+      }
+    }
+    inv_prev = inv;
+    __syncthreads();
+  }
+  // the last pivot column
+  if (k > 0)
+    for (int r = k + tid; r < n; r += THREADS) {
+      const T l = cmul(S[r * n + k - 1], inv_prev);
+      S[r * n + k - 1] = l;
+      gmax = nanmax(gmax, cabs2(l));
+    }
+  __syncthreads();
+  // L11^-1 rows (as in lu_small_kernel) and 1 / d on the diagonal of the inverse store
+  T* Xg = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const T one = cmk(R(1), R(0));
+  for (int i = warp; i < k; i += NW) {
+    T acc[kSmallSlots];
+#pragma unroll
+    for (int q = 0; q < kSmallSlots; ++q) acc[q] = czero<T>();
+    for (int m = i; m >= 1; --m) {
+      const T ym = m == i ? one : shfl_c(pick_slot(acc, m >> 5), m & 31);
+#pragma unroll
+      for (int q = 0; q < kSmallSlots; ++q) {
+        const int l = lane + 32 * q;
+        if (l < m) acc[q] = cfms(ym, S[m * n + l], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kSmallSlots; ++q) {
+      const int l = lane + 32 * q;
+      if (l < i) Xg[(size_t)i * d.ldk + l] = acc[q];
+    }
+    if (lane == 0) Xg[(size_t)i * d.ldk + i] = crcp(S[i * n + i]);
+  }
+  // rows below the pivots: L21 and the lower triangle of S
+  for (int e = tid; e < (n - k) * n; e += THREADS) {
+    const int r = k + e / n, c = e - (r - k) * n;
+    if (c <= r) F[(size_t)r * d.ld + c] = S[r * n + c];
+  }
+  int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  for (int i = tid; i < k; i += THREADS) P[i] = i;
   for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   if (lane == 0) s_red[warp] = gmax;
   __syncthreads();
@@ -752,15 +918,18 @@ __device__ __forceinline__ double2 pivot_rcp(double2 z) { return fast_crcp(z); }
 template <typename T>
 __device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __restrict__ F, int ld, int j0, int nb,
                                                                    T (*LU)[kMaxNb + 1], int* src, T* dinv,
-                                                                   T (*s_l)[32], int* s_r) {
+                                                                   T (*s_l)[32], int* s_r, bool sym = false) {
   using R = typename RealOf<T>::type;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T one = cmk(R(1), R(0));
   T a[8];
+  // symmetric form: only the block's lower triangle is current (read it mirrored),
+  // and the pivots are the diagonal in order (no pivoting)
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int j = 8 * warp + c;
-    a[c] = (lane < nb && j < nb) ? F[(size_t)(j0 + lane) * ld + j0 + j] : (lane == j ? one : czero<T>());
+    const int ri = (sym && j > lane) ? j : lane, ci = (sym && j > lane) ? lane : j;
+    a[c] = (lane < nb && j < nb) ? F[(size_t)(j0 + ri) * ld + j0 + ci] : (lane == j ? one : czero<T>());
   }
   bool used = false;
   int myp = lane;                 // padding lanes (>= nb) keep their own position
@@ -776,6 +945,7 @@ __device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __re
       const T myinv = pivot_rcp(ap);    // every lane's candidate, formed beside the redux
       unsigned key = used ? 0u : ((__float_as_uint(v) & ~31u) | (unsigned)(31 - lane));
       if (!used && !(v == v)) key = 0xffffffe0u | (unsigned)(31 - lane);   // NaN wins
+      if (sym) key = lane == p ? 0xffffffffu : 0u;
       const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
       const int r = 31 - (int)(kmax & 31u);
       const T inv = shfl_c(myinv, r);
@@ -862,7 +1032,7 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
         src[tid] = bsrc[tid];
       }
     } else {
-      g = diag_lu_4warps<T>(F, ld, j0, nb, LU, src, dinv, s_l, s_r);
+      g = diag_lu_4warps<T>(F, ld, j0, nb, LU, src, dinv, s_l, s_r, a.sym != 0);
     }
   } else if (role == 1) {
     // meanwhile warps 4-7 stage rows [lo, lo + 64) of the block columns
@@ -1355,7 +1525,8 @@ __global__ void __launch_bounds__(256)
 lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax, int schur) {
   constexpr int KC = GemmKc<T>::v;
   __shared__ T As[kGemmTile][KC + 1];
-  __shared__ T Bs[KC][kGemmTile];
+  __shared__ T Bs[KC][kGemmTile + 1];
+  __shared__ T dks[KC];                                 // symmetric form: d of the contracted pivots
   const int w = blockIdx.z + a.w0;
   const int f = flist[blockIdx.y];
   const FrontDesc d = a.P.fronts[f];
@@ -1370,8 +1541,12 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax,
   const int ti = blockIdx.x / nt, tj = blockIdx.x - ti * nt;
   const int r0 = base + ti * kGemmTile, c0 = base + tj * kGemmTile;
   if (!schur && r0 >= d.k && c0 >= d.k) return;        // tile inside S: deferred to the Schur product
+  // symmetric form: the lower triangle only, and in a panel step only the pivot columns
+  const bool sym = a.sym != 0;
+  if (sym && (r0 + kGemmTile - 1 < c0 || (!schur && c0 >= d.k))) return;
   j0 = kbeg;
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[4][4];
 #pragma unroll
@@ -1384,10 +1559,25 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax,
       const int gr = r0 + r, gk = kc + kk;
       As[r][kk] = (gr < d.n && gk < nb) ? F[(size_t)gr * d.ld + j0 + gk] : czero<T>();
     }
-    for (int e = tid; e < kGemmTile * KC; e += 256) {
-      const int kk = e / kGemmTile, c = e - kk * kGemmTile;
-      const int gc = c0 + c, gk = kc + kk;
-      Bs[kk][c] = (gc < d.n && gk < nb) ? F[(size_t)(j0 + gk) * d.ld + gc] : czero<T>();
+    if (sym) {
+      // B = diag(d) L^T over the contracted pivots j0 + gk: row gc of L (final: the panel step
+      // that wrote it has finished), d from 1 / d on the diagonal of the inverse store
+      if (tid < KC) {
+        const int gk = kc + tid;
+        dks[tid] = gk < nb ? crcp(X[(size_t)(j0 + gk) * d.ldk + j0 + gk]) : czero<T>();
+      }
+      __syncthreads();
+      for (int e = tid; e < kGemmTile * KC; e += 256) {
+        const int c = e / KC, kk = e - c * KC;
+        const int gc = c0 + c, gk = kc + kk;
+        Bs[kk][c] = (gc < d.n && gk < nb) ? cmul(dks[kk], F[(size_t)gc * d.ld + j0 + gk]) : czero<T>();
+      }
+    } else {
+      for (int e = tid; e < kGemmTile * KC; e += 256) {
+        const int kk = e / kGemmTile, c = e - kk * kGemmTile;
+        const int gc = c0 + c, gk = kc + kk;
+        Bs[kk][c] = (gc < d.n && gk < nb) ? F[(size_t)(j0 + gk) * d.ld + gc] : czero<T>();
+      }
     }
     __syncthreads();
 #pragma unroll 4
@@ -1411,7 +1601,8 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gc = c0 + tx + 16 * j;
-      if (gc < d.n && (schur || gr < d.k || gc < d.k)) {
+      const bool live = sym ? (gr >= gc && (schur || gc < d.k)) : (schur || gr < d.k || gc < d.k);
+      if (gc < d.n && live) {
         T* p = F + (size_t)gr * d.ld + gc;
         *p = csub(*p, acc[i][j]);
       }
@@ -1452,6 +1643,9 @@ cudaError_t factor_init_attributes() {
   e = cudaFuncSetAttribute(lu_small_kernel<double2, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            64 * 64 * 16);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(ldl_small_kernel<float2, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           96 * 96 * 8);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_step_local_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)step_local_smem(8));
   if (e != cudaSuccess) return e;
@@ -1477,6 +1671,11 @@ void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, 
   if (nf <= 0) return;
   const size_t smem = (size_t)nmax * nmax * sizeof(T);
   // fronts up to kSmallNarrowN: half the threads, so that twice as many fit on an SM
+  if (a.sym) {
+    if (nmax <= kSmallNarrowN) ldl_small_kernel<T, kSmallThreads / 2><<<dim3(nf, a.n_omega), kSmallThreads / 2, smem, s>>>(a, flist);
+    else ldl_small_kernel<T, kSmallThreads><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
+    return;
+  }
   if (nmax <= kSmallNarrowN) lu_small_kernel<T, kSmallThreads / 2><<<dim3(nf, a.n_omega), kSmallThreads / 2, smem, s>>>(a, flist);
   else lu_small_kernel<T, kSmallThreads><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
 }
@@ -1507,23 +1706,25 @@ void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j
   if (nf <= 0) return;
   const int span = std::max(0, nmax - j0 - 1);
   const int nl = (span + kStepRows - 1) / kStepRows;
-  const int np = (j0 + kStepRows - 1) / kStepRows;
+  // symmetric form: no U rows (the trailing update takes diag(d) L^T instead) and no row permutation
+  const int nu = a.sym ? 0 : nl;
+  const int np = a.sym ? 0 : (j0 + kStepRows - 1) / kStepRows;
   // CTAs resident at once on the current device: 8 per SM
   int dev = 0, nsm = 0;
   const long long wave =
       (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
           ? 8LL * nsm
           : (1LL << 40);
-  const long long ctas = (long long)(1 + 2 * nl + np) * nf * a.n_omega;
+  const long long ctas = (long long)(1 + nl + nu + np) * nf * a.n_omega;
   if (ctas > wave && a.dblk) {
     // more than one wave: the diagonal block once per front, then the substitutions
-    lu_step_local_kernel<T><<<dim3(1, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(a, flist, j0, nl, nl, 1);
-    if (2 * nl + np > 0)
-      lu_step_local_kernel<T><<<dim3(2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
-          a, flist, j0, nl, nl, 2);
+    lu_step_local_kernel<T><<<dim3(1, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(a, flist, j0, nl, nu, 1);
+    if (nl + nu + np > 0)
+      lu_step_local_kernel<T><<<dim3(nl + nu + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
+          a, flist, j0, nl, nu, 2);
   } else {
-    lu_step_local_kernel<T><<<dim3(1 + 2 * nl + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
-        a, flist, j0, nl, nl, 0);
+    lu_step_local_kernel<T><<<dim3(1 + nl + nu + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
+        a, flist, j0, nl, nu, 0);
   }
 }
 
@@ -1559,7 +1760,8 @@ template <typename T>
 void launch_lu_inv_fold(const FactorLaunch& a, const int* flist, int nf, int j0, cudaStream_t s) {
   const int nq = (j0 + 31) / 32;
   if (nf <= 0 || nq <= 0) return;
-  lu_inv_fold_kernel<T><<<dim3(2 * nq, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nq);
+  // the symmetric form needs L11^-1 only (the first nq CTAs)
+  lu_inv_fold_kernel<T><<<dim3(a.sym ? nq : 2 * nq, nf, a.n_omega), 256, 0, s>>>(a, flist, j0, nq);
 }
 
 template <typename T>

@@ -7,8 +7,9 @@
 namespace fdfd {
 
 // ---- assembly.cu: stencil coefficients (Eq. 1-2 with SC-PML) ---------------
-void launch_coef(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2,
-                 const double* k0dx_dev, int n_omega, int nx, int ny, int npml_x, int npml_y,
+// (sxc, syc: the stretch factors at cell centres, whose product is the symmetriser D)
+void launch_coef(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2, double2* sxc,
+                 double2* syc, const double* k0dx_dev, int n_omega, int nx, int ny, int npml_x, int npml_y,
                  double ln_R, double order, cudaStream_t s);
 void launch_scatter_design(double* eps, const double* eps_design, int ny, int x0, int y0, int w,
                            int h, cudaStream_t s);
@@ -30,6 +31,7 @@ struct FactorLaunch {
   void* istore;            // triangular inverses (same type as store), [n_omega][istore_stride]
   long long istore_stride;
   void* dblk;              // a panel step's diagonal-block factors, [n_omega launched][swp_stride][kDiagBlkElems]
+  int sym;                 // 1: symmetric form, M = D A = L diag(d) L^T without pivoting (see factor.cu)
 };
 constexpr int kDiagBlkElems = 32 * 32 + 32;   // L\U rows in pivot order, then 1 / U_pp
 // L11^-1 (strictly lower part) and U11^-1 (upper part) of the listed large fronts,
@@ -131,6 +133,12 @@ struct SolveLaunch {
   int n_omega, nrhs;       // wavelengths launched [w0, w0 + n_omega); nrhs = layout stride
   int w0, r0, nr;          // right-hand sides processed: [r0, r0 + nr)
   long long n;             // unknowns per system
+  // symmetric-form factors (L diag(d) L^T of D A): the L sweep gathers D b
+  // (sym_in), the L^T sweep takes w = y / d where it first reads a front's y
+  // (sym_mid) and writes D x (sym_out); D from the stretch tables below
+  int sym_in = 0, sym_mid = 0, sym_out = 0;
+  const double2* sxc = nullptr;   // [n_omega][nx]
+  const double2* syc = nullptr;   // [n_omega][ny]
 };
 // sweep: 0 = L (forward, non-transposed), 1 = U (backward, non-transposed),
 //        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
@@ -234,6 +242,8 @@ cudaError_t solve_init_attributes();
 void launch_filter_project(const double* rho, int w, int h, const int2* off, const double* wt, int ntap,
                            double beta, double eta, double eps_lo, double deps, double* eps, double* slope,
                            double* norm, cudaStream_t s);
+// eps = eps_lo + rho * deps over n pixels
+void launch_density_eps(const double* rho, long long n, double eps_lo, double deps, double* eps, cudaStream_t s);
 void launch_filter_adjoint(const double* g, const double* slope, const double* norm, int w, int h, const int2* off,
                            const double* wt, int ntap, double* out, cudaStream_t s);
 

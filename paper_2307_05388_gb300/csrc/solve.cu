@@ -171,14 +171,38 @@ __device__ __forceinline__ Kids load_kids(const SolveLaunch& a, const FrontDesc&
   return c;
 }
 
-// Right-hand side entry of local slot src (pivot slots only, when rhs is given)
-// plus the children's update vectors at that slot.
+// D[cell] of the symmetric form (stretch factors at the cell centre)
+__device__ __forceinline__ double2 sym_d(const SolveLaunch& a, int w, int cell) {
+  const int i = cell / a.P.ny, j = cell - i * a.P.ny;
+  return cmul(a.sxc[(size_t)w * a.P.nx + i], a.syc[(size_t)w * a.P.ny + j]);
+}
+
+// The solution value written for cell: x, or D x for the transposed symmetric-form solve.
+template <typename T>
+__device__ __forceinline__ double2 out_val(const SolveLaunch& a, int w, int cell, T v) {
+  const double2 x = cto64(v);
+  return a.sym_out ? cmul(sym_d(a, w, cell), x) : x;
+}
+
+// w = y / d for the symmetric form (1 / d on the diagonal of the inverse store)
+template <typename T>
+__device__ __forceinline__ T mid_val(const SolveLaunch& a, const T* X, int ldk, int s, T v) {
+  return a.sym_mid ? cmul(v, X[(size_t)s * ldk + s]) : v;
+}
+
+// Right-hand side entry of local slot src (pivot slots only, when rhs is given;
+// times D for the symmetric form) plus the children's update vectors at that slot.
 template <typename T>
 __device__ __forceinline__ T gather_slot(const SolveLaunch& a, const FrontDesc& d, const Kids& kids,
-                                         const double2* rhs, const T* vbs, int src) {
+                                         const double2* rhs, const T* vbs, int src, int w = 0) {
   const int t0 = kids.n > 0 ? a.P.inv[kids.inv_off[0] + src] : -1;
   const int t1 = kids.n > 1 ? a.P.inv[kids.inv_off[1] + src] : -1;
-  T v = (rhs && src < d.k) ? cfrom<T>(rhs[a.P.idx[d.idx_off + src]]) : czero<T>();
+  T v = czero<T>();
+  if (rhs && src < d.k) {
+    const int cell = a.P.idx[d.idx_off + src];
+    const double2 b = rhs[cell];
+    v = cfrom<T>(a.sym_in ? cmul(sym_d(a, w, cell), b) : b);
+  }
   if (t0 >= 0) v = cadd(v, ldv(vbs + kids.ubase[0] + t0));
   if (t1 >= 0) v = cadd(v, ldv(vbs + kids.ubase[1] + t1));
   return v;
@@ -286,9 +310,10 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
     double2* xo = out + sys * a.n;
     if (SWEEP == 0 || SWEEP == 2) {
       const double2* rhs = in + sys * a.n;
-      for (int s = lane; s < n; s += 32) vs[s] = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
+      for (int s = lane; s < n; s += 32)
+        vs[s] = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s, w);
     } else {
-      for (int s = lane; s < k; s += 32) vs[s] = ldv(vf + s);
+      for (int s = lane; s < k; s += 32) vs[s] = SWEEP == 3 ? mid_val(a, X, ldk, s, ldv(vf + s)) : ldv(vf + s);
       for (int t = lane; t < m; t += 32) {
         const T x = cfrom<T>(ldv(xo + idx[k + t]));
         vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
@@ -320,7 +345,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
                     [&](int j, T acc) { ws[j] = cadd(vs[j], acc); });
       __syncwarp();
       warp_cols_dot(X, ldk, k, ws, [](int j) { return j + 1; }, [&](int) { return k; },
-                    [&](int j, T acc) { xo[idx[Pm[j]]] = cto64(cadd(ws[j], acc)); });
+                    [&](int j, T acc) { xo[idx[Pm[j]]] = out_val(a, w, idx[Pm[j]], cadd(ws[j], acc)); });
     }
     __syncwarp();
   }
@@ -345,13 +370,15 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
       const double2* rhs = in + sys * a.n;
       for (int s = tid; s < k; s += 2 * kThreads) {
         const int s2 = s + kThreads;
-        const T g1 = gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s] : s);
-        const T g2 = s2 < k ? gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s2] : s2) : czero<T>();
+        const T g1 = gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s] : s, w);
+        const T g2 = s2 < k ? gather_slot(a, d, kids, rhs, vbs, SWEEP == 0 ? Pm[s2] : s2, w) : czero<T>();
         vs[s] = g1;
         if (s2 < k) vs[s2] = g2;
       }
     } else {
-      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
+      // without an off-diagonal block (m = 0) the L^T sweep reads y here first
+      for (int s = tid; s < k; s += kThreads)
+        vs[s] = (SWEEP == 3 && d.m == 0) ? mid_val(a, X, ldk, s, ldv(vf + s)) : ldv(vf + s);
     }
     __syncthreads();
     if (SWEEP == 0) {
@@ -377,7 +404,7 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
       const int c = b0 + (lane & (kColBlk - 1));
       double2* xo = out + sys * a.n;
       const T s = col_dot(X + c, ldk, vs, b0 + 1, k, c < k, [&](int b) { return b > c; }, red);
-      if (warp == 0 && lane < kColBlk && c < k) xo[idx[Pm[c]]] = cto64(cadd(vs[c], s));
+      if (warp == 0 && lane < kColBlk && c < k) xo[idx[Pm[c]]] = out_val(a, w, idx[Pm[c]], cadd(vs[c], s));
     }
     __syncthreads();
   }
@@ -440,7 +467,10 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
       const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
       // the value the product is subtracted from, fetched before the product
       T g = czero<T>();
-      if (mine) g = SWEEP == 2 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + c) : ldv(vf + c);
+      if (mine)
+        g = SWEEP == 2 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs, k + c)
+                       : mid_val(a, reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off,
+                                 d.ldk, c, ldv(vf + c));
       const T s = col_dot(base, ld, vs, 0, rows, c < cols, [](int) { return true; }, red);
       if (mine) vf[SWEEP == 2 ? k + c : c] = csub(g, s);
     }
@@ -577,13 +607,14 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
       const double2* rhs = in + sys * a.n;
       for (int s = tid; s < n; s += 2 * kThreads) {
         const int s2 = s + kThreads;
-        const T g1 = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s);
-        const T g2 = s2 < n ? gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s2 < k) ? Pm[s2] : s2) : czero<T>();
+        const T g1 = gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s < k) ? Pm[s] : s, w);
+        const T g2 = s2 < n ? gather_slot(a, d, kids, rhs, vbs, (SWEEP == 0 && s2 < k) ? Pm[s2] : s2, w)
+                            : czero<T>();
         vs[s] = g1;
         if (s2 < n) vs[s2] = g2;
       }
     } else {
-      for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
+      for (int s = tid; s < k; s += kThreads) vs[s] = SWEEP == 3 ? mid_val(a, X, ldk, s, ldv(vf + s)) : ldv(vf + s);
       for (int t = tid; t < m; t += kThreads) {
         const T x = cfrom<T>(ldv(xo + idx[k + t]));
         vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
@@ -615,7 +646,7 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
                [&](int j, T acc) { ws[j] = cadd(vs[j], acc); }, red);
       __syncthreads();
       cols_dot(X, ldk, k, k, ws, [](int j) { return j + 1; }, [&](int) { return k; },
-               [&](int j, T acc) { xo[idx[Pm[j]]] = cto64(cadd(ws[j], acc)); }, red);
+               [&](int j, T acc) { xo[idx[Pm[j]]] = out_val(a, w, idx[Pm[j]], cadd(ws[j], acc)); }, red);
     }
     __syncthreads();
   }

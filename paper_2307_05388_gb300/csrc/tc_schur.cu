@@ -209,13 +209,18 @@ schur_pack_kernel(FactorLaunch a, TcLaunch t) {
         x[2 * i + 1] = v.y;
       }
     } else {
-      // B' (K-major) row n = 2 j + tt: (Re U, -Im U) per pivot for tt = 0, (Im U, Re U) for tt = 1
+      // B' (K-major) row n = 2 j + tt: (Re U, -Im U) per pivot for tt = 0, (Im U, Re U) for tt = 1;
+      // the symmetric form's U12 is diag(d) L21^T: d_l L21[j][l], 1 / d_l on the inverse store diagonal
       const int nrow = g * 8 + rr;
       const int j = task.z * kTcCols + (nrow >> 1), tt = nrow & 1;
+      const float2* X = reinterpret_cast<const float2*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
 #pragma unroll
       for (int i = 0; i < CU; ++i) {
         float2 v = make_float2(0.f, 0.f);
-        if (j < d.m && l0 + i < d.k) v = F[(size_t)(l0 + i) * d.ld + d.k + j];
+        if (j < d.m && l0 + i < d.k) {
+          const int l = l0 + i;
+          v = a.sym ? cmul(crcp(X[(size_t)l * d.ldk + l]), F[(size_t)(d.k + j) * d.ld + l]) : F[(size_t)l * d.ld + d.k + j];
+        }
         x[2 * i] = tt ? v.y : v.x;
         x[2 * i + 1] = tt ? v.x : -v.y;
       }

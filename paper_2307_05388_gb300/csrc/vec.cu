@@ -33,8 +33,8 @@ __device__ double2 neg_inv_prod(double2 a, double2 b) {
 }
 
 __global__ void coef_kernel(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2,
-                            const double* k0dx, int n_omega, int nx, int ny, int px, int py,
-                            double ln_R, double order) {
+                            double2* sxc, double2* syc, const double* k0dx, int n_omega, int nx, int ny, int px,
+                            int py, double ln_R, double order) {
   const int w = blockIdx.y;
   const double kd = k0dx[w];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,11 +43,13 @@ __global__ void coef_kernel(double2* cxm, double2* cxp, double2* cym, double2* c
     const double2 sc = stretch(t + 0.5, nx, px, kd, ln_R, order);
     cxm[(size_t)w * nx + t] = neg_inv_prod(sc, stretch(t, nx, px, kd, ln_R, order));
     cxp[(size_t)w * nx + t] = neg_inv_prod(sc, stretch(t + 1.0, nx, px, kd, ln_R, order));
+    sxc[(size_t)w * nx + t] = sc;
   }
   if (t < ny) {
     const double2 sc = stretch(t + 0.5, ny, py, kd, ln_R, order);
     cym[(size_t)w * ny + t] = neg_inv_prod(sc, stretch(t, ny, py, kd, ln_R, order));
     cyp[(size_t)w * ny + t] = neg_inv_prod(sc, stretch(t + 1.0, ny, py, kd, ln_R, order));
+    syc[(size_t)w * ny + t] = sc;
   }
 }
 
@@ -184,11 +186,11 @@ int grid_for(long long n) {
 
 }  // namespace
 
-void launch_coef(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2,
-                 const double* k0dx_dev, int n_omega, int nx, int ny, int npml_x, int npml_y,
+void launch_coef(double2* cxm, double2* cxp, double2* cym, double2* cyp, double* k0dx2, double2* sxc,
+                 double2* syc, const double* k0dx_dev, int n_omega, int nx, int ny, int npml_x, int npml_y,
                  double ln_R, double order, cudaStream_t s) {
   const int nmax = nx > ny ? nx : ny;
-  coef_kernel<<<dim3((nmax + 127) / 128, n_omega), 128, 0, s>>>(cxm, cxp, cym, cyp, k0dx2, k0dx_dev,
+  coef_kernel<<<dim3((nmax + 127) / 128, n_omega), 128, 0, s>>>(cxm, cxp, cym, cyp, k0dx2, sxc, syc, k0dx_dev,
                                                                n_omega, nx, ny, npml_x, npml_y, ln_R, order);
 }
 

@@ -21,6 +21,7 @@ FDFD_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_OOM", 4: "ERR_CUDA", 5: "ERR_PIVOT",
                 6: "ERR_NOT_CONVERGED", 7: "ERR_TIMEOUT"}
 MODE_MIXED, MODE_F64, MODE_PLAIN = 0, 1, 2
+FORM_LU, FORM_SYMMETRIC = 0, 1
 
 # Every symbol include/fdfd.h declares (the CPU test checks the library exports them).
 EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor", "fdfd_refactor_design",
@@ -28,7 +29,7 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
            "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
-           "fdfd_slab_modes", "fdfd_objective_target", "fdfd_design_iteration"]
+           "fdfd_slab_modes", "fdfd_objective_target", "fdfd_design_iteration", "fdfd_density_eps"]
 HOST_EPS, HOST_OUT = 1, 2
 
 
@@ -48,7 +49,7 @@ class Options(C.Structure):
     _fields_ = [("mode", C.c_int), ("ir_tol", C.c_double), ("ir_max_iter", C.c_int),
                 ("gmres_restart", C.c_int), ("growth_bound", C.c_double), ("leaf_area", C.c_int),
                 ("pivoting", C.c_int), ("tensor_form", C.c_int), ("tensor_min_m", C.c_int),
-                ("tensor_min_tiles", C.c_int)]
+                ("tensor_min_tiles", C.c_int), ("factor_form", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -56,7 +57,8 @@ class Stats(C.Structure):
                 ("ir_iters", C.c_longlong), ("ir_resid", C.c_double), ("fallbacks", C.c_longlong),
                 ("growth", C.c_double), ("n_fronts", C.c_int), ("n_levels", C.c_int), ("max_front", C.c_int),
                 ("factor_entries", C.c_longlong), ("store_bytes", C.c_longlong),
-                ("flops_factor", C.c_double), ("flops_design", C.c_double), ("repivots", C.c_longlong)]
+                ("flops_factor", C.c_double), ("flops_design", C.c_double), ("repivots", C.c_longlong),
+                ("factor_form", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_objective.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp]
     lib.fdfd_grad.argtypes = [vp, vp, vp, i, vp, vp, i]
     lib.fdfd_objective_target.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]
+    lib.fdfd_density_eps.argtypes = [vp, vp, d, d, vp]
     lib.fdfd_design_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, i]
     lib.fdfd_apply.argtypes = [vp, vp, vp, i, i]
     lib.fdfd_set_options.argtypes = [vp, C.POINTER(Options)]
@@ -109,7 +112,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                  "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
                  "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get", "fdfd_filter_project",
                  "fdfd_filter_project_adjoint", "fdfd_objective_target", "fdfd_design_iteration",
-                 "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
+                 "fdfd_density_eps", "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -296,6 +299,15 @@ class Solver:
                                              float(eps_lo), float(eps_hi), _ptr(eps), _ptr(work)),
                     "fdfd_filter_project")
         return eps, work
+
+    def density_eps(self, rho: torch.Tensor, eps_lo: float, eps_hi: float, out: torch.Tensor | None = None):
+        """Design-box permittivity eps_lo + rho (eps_hi - eps_lo) (fdfd_density_eps)."""
+        rho = rho.reshape(-1).contiguous()
+        assert rho.dtype == torch.float64 and rho.numel() == self.box[2] * self.box[3]
+        eps = out if out is not None else torch.empty_like(rho)
+        self._check(_lib.fdfd_density_eps(self._h, _ptr(rho), float(eps_lo), float(eps_hi), _ptr(eps)),
+                    "fdfd_density_eps")
+        return eps
 
     def filter_project_adjoint(self, g_eps: torch.Tensor, work: torch.Tensor, radius: float) -> torch.Tensor:
         """dF/drho from dF/deps through the projection and the filter of filter_project."""

@@ -2,6 +2,8 @@
 import numpy as np
 import torch
 
+import workloads as W
+
 from paper_2307_05388_gb300 import autograd as AG
 from paper_2307_05388_gb300 import fdfd as FD
 
@@ -15,9 +17,11 @@ def make_solver(wl, **opts):
 
 
 def rhs_tensor(wl, dev="cuda"):
-    """[n_omega, n_src, N] complex128: the same sources at every wavelength."""
-    b = np.stack([wl.source_dense(s) for s in range(wl.n_src)])
-    b = np.broadcast_to(b, (wl.n_omega,) + b.shape).copy()
+    """[n_omega, n_src, N] complex128: every source at every wavelength (mode sources resolved per
+    wavelength by the library's mode solver)."""
+    if any(isinstance(src, W.ModeLine) for src in wl.sources) and "mode_profiles" not in wl.extra:
+        wl = W.with_modes(wl, FD.slab_modes)
+    b = np.stack([np.stack([wl.source_dense(s, w) for s in range(wl.n_src)]) for w in range(wl.n_omega)])
     return torch.from_numpy(b).to(dev)
 
 

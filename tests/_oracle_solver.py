@@ -23,7 +23,8 @@ class OracleSolver:
 
     def factor(self, eps):
         self.eps = eps.detach().reshape(self.nx, self.ny).numpy().copy()
-        self.facs = [O.Factor(O.assemble(self.nx, self.ny, self.eps, k * self.dx, self.npml)) for k in self.k0]
+        self.facs = [O.Factor(O.assemble(self.nx, self.ny, self.eps, k * self.dx, self.npml), (self.nx, self.ny))
+                     for k in self.k0]
 
     def refactor_design(self, eps_design):
         x0, y0, w, h = self.box

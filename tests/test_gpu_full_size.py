@@ -4,8 +4,9 @@
   times: tensor-core update matrices in the BF16 three-way split form with the contraction
   split over several CTAs on its small levels.  Forward and transpose fields against
   SuperLU, element by element, at 1e-8; the raw complex FP32-factor error is printed.
-* C3 (540 x 540, two sources) and C4 (1040 x 1040), each restricted to its first
-  wavelength: the same comparison on 292k and 1.08M unknowns.
+* C3 (540 x 540, TE0 and TE1 sources of its input guide) and C4 (1040 x 1040), each
+  restricted to its first wavelength: the same comparison on 292k and 1.08M unknowns.  Each
+  side builds the mode sources with its own mode solver.
 * C4's gradient (four wavelengths) on 32 seeded design pixels against central differences
   of the oracle's objective with step 1e-4 in rho (Eq. 3), every perturbed F evaluated
   exactly by a rank-one update of the oracle's factorisation.
@@ -65,10 +66,18 @@ def _compare(name, x, raw, ref_f, ref_t):
             assert rerr < 1e-1
 
 
+def _gpu_rhs(name, random_seed=None):
+    """The same right-hand sides as the oracle job's, sources built with the library's mode solver."""
+    wl = W.with_modes(W.make(name), FD.slab_modes).select_wavelengths([0])
+    rows = [wl.source_dense(s, 0) for s in range(wl.n_src)]
+    if random_seed is not None:
+        rows.append(W.random_complex(wl.n, random_seed))
+    return wl, np.stack(rows)
+
+
 def test_c2_default_options_fields_match_the_oracle(pool):
-    wl = W.make("c2")
-    rhs = np.stack([wl.source_dense(0), W.random_complex(wl.n, 41)])
-    job = pool.submit(J.fields, "c2", 0, rhs)
+    job = pool.submit(J.fields, "c2", 0, 41)
+    wl, rhs = _gpu_rhs("c2", 41)
     s = U.make_solver(wl)
     s.profile(True)
     s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
@@ -84,9 +93,8 @@ def test_c2_default_options_fields_match_the_oracle(pool):
 
 @pytest.mark.parametrize("name", ["c3", "c4"])
 def test_first_wavelength_fields_match_the_oracle(pool, name):
-    wl = J.one_wavelength(name, 0)
-    rhs = np.stack([wl.source_dense(i) for i in range(wl.n_src)])
-    job = pool.submit(J.fields, name, 0, rhs)
+    job = pool.submit(J.fields, name, 0)
+    wl, rhs = _gpu_rhs(name)
     s = U.make_solver(wl)
     s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
     x, raw = _fields_on_gpu(s, torch.from_numpy(rhs[None].copy()).to(DEV))

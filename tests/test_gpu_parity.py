@@ -31,7 +31,7 @@ DEV = "cuda"
 def _oracle_fields(wl, eps, transpose=False, b=None):
     out = []
     for w, k0dx in enumerate(wl.k0dx()):
-        fac = O.Factor(O.assemble(wl.nx, wl.ny, eps, k0dx, wl.npml))
+        fac = O.Factor(O.assemble(wl.nx, wl.ny, eps, k0dx, wl.npml), (wl.nx, wl.ny))
         for s in range(b.shape[1]):
             out.append(fac.solve_T(b[w, s]) if transpose else fac.solve(b[w, s]))
     return np.stack(out).reshape(b.shape)

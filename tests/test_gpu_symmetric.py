@@ -1,0 +1,130 @@
+"""The symmetric factor form (factor_form = 1): D A = L diag(d) L^T without pivoting.
+
+D A is complex symmetric for D = diag(s_x s_y) (the oracle pins this symmetry), so
+each front factors as L diag(d) L^T in the plan's elimination order, lower
+triangles only, and a solve is the L sweep, 1 / d, then the L^T sweep with D
+applied at the gather (A x = b) or at the output (A^T x = b).  Checked against the
+oracle like the LU form: fields at 1e-8 after refinement (forward and transpose,
+ragged small grids and C1/C2), the design gradient at 1e-6, a design refactor bit
+for bit equal to a fresh factorisation, and the fallback to LU when the pivot growth
+exceeds the bound."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import fdfd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2307_05388_gb300 import fdfd as FD  # noqa: E402
+from tests import _gpu_util as U  # noqa: E402
+
+FIELD_TOL = 1e-8
+GRAD_TOL = 1e-6
+DEV = "cuda"
+SYM = dict(factor_form=FD.FORM_SYMMETRIC)
+
+
+def _fields(wl, nrhs, transpose, seed=5, **opts):
+    s = U.make_solver(wl, **SYM, **opts)
+    eps = wl.eps_full()
+    s.factor(torch.from_numpy(eps.reshape(-1).copy()).to(DEV))
+    b = W.random_complex((wl.n_omega, nrhs, wl.n), seed)
+    x = s.solve(torch.from_numpy(b).to(DEV), transpose=transpose).cpu().numpy()
+    ref = []
+    for w, k0dx in enumerate(wl.k0dx()):
+        fac = O.Factor(O.assemble(wl.nx, wl.ny, eps, k0dx, wl.npml), (wl.nx, wl.ny))
+        for r in range(nrhs):
+            ref.append(fac.solve_T(b[w, r]) if transpose else fac.solve(b[w, r]))
+    return x, np.stack(ref).reshape(b.shape), s
+
+
+@pytest.mark.parametrize("nx,ny,npml,box,n_omega,nrhs,leaf", [
+    (37, 29, 5, (9, 7, 15, 11), 2, 3, 32),     # ragged, several wavelengths and sources
+    (61, 45, 8, (13, 10, 30, 20), 1, 2, 16),   # more levels, large-front path
+    (130, 97, 10, (20, 15, 90, 60), 1, 1, 32), # fronts above the shared-memory size, several panel steps
+    (1, 40, 0, (0, 5, 1, 20), 1, 1, 4),        # one column, no PML
+    (2, 2, 0, (0, 0, 2, 2), 1, 1, 1),          # degenerate 2 x 2
+])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_symmetric_form_small_grids(nx, ny, npml, box, n_omega, nrhs, leaf, transpose):
+    wl = W.make_small(nx, ny, npml, box, n_omega=n_omega, n_src=1, seed=7)
+    x, ref, s = _fields(wl, nrhs, transpose, leaf_area=leaf)
+    st = s.stats()
+    err = O.rel_err(x, ref)
+    print(f"{nx}x{ny} transpose={transpose}: field err {err:.2e}, form {st['factor_form']}, "
+          f"growth {st['growth']:.3g}, iterations {st['ir_iters']}")
+    assert st["factor_form"] == 1 and st["repivots"] == 0 and st["fallbacks"] == 0
+    assert err <= FIELD_TOL
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_symmetric_form_workloads_fields_and_raw_error(name):
+    wl = W.make(name)
+    errs = {}
+    for tr in (False, True):
+        x, ref, s = _fields(wl, 2, tr, seed=11)
+        st = s.stats()
+        assert st["factor_form"] == 1 and st["fallbacks"] == 0
+        errs[tr] = O.rel_err(x, ref)
+        assert errs[tr] <= FIELD_TOL
+    xr, ref, _ = _fields(wl, 1, False, seed=12, ir_max_iter=0)
+    print(f"{name}: symmetric form field errors {errs}, raw FP32-factor error {O.rel_err(xr, ref):.2e}")
+    assert O.rel_err(xr, ref) < 1e-2
+
+
+def test_symmetric_form_design_iteration_c1():
+    wl = W.make("c1")
+    prob = U.problem(wl, **SYM)
+    rho = wl.rho.copy()
+    for it in range(3):
+        F, g = prob.iteration(U.eps_design_tensor(wl, rho))
+        torch.cuda.synchronize()
+        F_ref, g_ref, _ = O.design_iteration(wl, rho, wl.eps_full, W.DELTA_EPS)
+        assert abs(float(F) - F_ref) <= 1e-8 * abs(F_ref)
+        assert O.rel_err(g.cpu().numpy().reshape(wl.rho.shape) * W.DELTA_EPS, g_ref) <= GRAD_TOL
+        assert prob.solver.stats()["factor_form"] == 1
+        rho = O.sign_step(rho, g_ref, wl.step)
+
+
+def test_symmetric_form_multiwavelength_gradient():
+    wl = W.make_small(40, 36, 6, (10, 9, 18, 16), n_omega=3, n_src=2, seed=13)
+    prob = U.problem(wl, **SYM)
+    F, g = prob.iteration(U.eps_design_tensor(wl, wl.rho))
+    F_ref, g_ref, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS)
+    assert abs(float(F) - F_ref) <= 1e-8 * abs(F_ref)
+    assert O.rel_err(g.cpu().numpy().reshape(wl.rho.shape) * W.DELTA_EPS, g_ref) <= GRAD_TOL
+
+
+def test_symmetric_form_refactor_is_bitwise_fresh_factor():
+    wl = W.make("c1")
+    rho2 = np.random.default_rng(9).uniform(0, 1, wl.rho.shape)
+    s1 = U.make_solver(wl, ir_max_iter=0, **SYM)
+    s1.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
+    s1.refactor_design(U.eps_design_tensor(wl, rho2))
+    s2 = U.make_solver(wl, ir_max_iter=0, **SYM)
+    s2.factor(torch.from_numpy(wl.eps_full(rho2).reshape(-1).copy()).to(DEV))
+    b = torch.from_numpy(W.random_complex((1, 2, wl.n), 3)).to(DEV)
+    for tr in (False, True):
+        assert torch.equal(s1.solve(b, transpose=tr), s2.solve(b, transpose=tr))
+
+
+def test_symmetric_form_falls_back_to_lu_when_growth_exceeds_the_bound():
+    """A growth bound below any real growth sends the symmetric factors to complex FP32 LU with
+    partial pivoting over all pivot rows, then to FP64; the refined fields still match the oracle
+    and the next design refactor starts the symmetric form again."""
+    wl = W.make("c1")
+    x, ref, s = _fields(wl, 1, False, growth_bound=1e-30)
+    st = s.stats()
+    assert st["repivots"] >= 1 and st["fallbacks"] >= 1
+    assert O.rel_err(x, ref) <= FIELD_TOL
+    s.set_options(ir_max_iter=40)
+    s.refactor_design(U.eps_design_tensor(wl, wl.rho))
+    b = torch.from_numpy(W.random_complex((1, 1, wl.n), 7)).to(DEV)
+    x2 = s.solve(b).cpu().numpy()
+    fac = O.Factor(O.assemble(wl.nx, wl.ny, wl.eps_full(), wl.k0dx()[0], wl.npml), (wl.nx, wl.ny))
+    assert O.rel_err(x2.reshape(-1), fac.solve(b.cpu().numpy().reshape(-1))) <= FIELD_TOL

@@ -547,3 +547,21 @@ def test_target_objective_vanishes_at_the_target():
     targets = [[abs(O.overlap(f0[(0, s)][0], wl.monitor_dense(0, s))) ** 2 for s in range(2)]]
     F, g, _ = O.design_iteration(wl, wl.rho, wl.eps_full, W.DELTA_EPS, targets=targets)
     assert F < 1e-24 and np.max(np.abs(g)) < 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,npml", [(12, 17, 3), (31, 9, 2), (20, 20, 4), (1, 13, 0), (40, 1, 0)])
+def test_nested_dissection_factor_matches_dense_lapack(nx, ny, npml):
+    """The nested-dissection order is a permutation of the grid with every separator line after
+    the two halves it separates; SuperLU on the permuted matrix (threshold pivoting, one
+    refinement step) gives the dense LAPACK solutions of Eq. 5 and 6."""
+    p = O.nested_dissection(nx, ny, leaf=8)
+    assert np.array_equal(np.sort(p), np.arange(nx * ny))
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 11), k0dx, npml)
+    b = W.random_complex(nx * ny, 12)
+    fac = O.Factor(A, (nx, ny))
+    Ad = A.toarray()
+    assert O.rel_err(fac.solve(b), np.linalg.solve(Ad, b)) < 1e-12
+    assert O.rel_err(fac.solve_T(b), np.linalg.solve(Ad.T, b)) < 1e-12
+    B = np.stack([b, W.random_complex(nx * ny, 13)], axis=1)
+    np.testing.assert_allclose(fac.solve(B), np.linalg.solve(Ad, B), rtol=0, atol=1e-12 * np.abs(B).max() * 1e3)

@@ -102,7 +102,7 @@ def test_noalloc_f64_matches_the_oracle():
     wl = W.make_small(48, 41, 6, (12, 10, 20, 18), n_omega=2, n_src=1, seed=21)
     s = _solver(wl, FD.MODE_F64)
     eps = wl.eps_full()
-    facs = [O.Factor(O.assemble(wl.nx, wl.ny, eps, k0dx, wl.npml)) for k0dx in wl.k0dx()]
+    facs = [O.Factor(O.assemble(wl.nx, wl.ny, eps, k0dx, wl.npml), (wl.nx, wl.ny)) for k0dx in wl.k0dx()]
     for call, transpose in enumerate((False, True, False)):
         b = W.random_complex((wl.n_omega, 2, wl.n), 200 + call)
         st, x = _noalloc(s, torch.from_numpy(b).cuda(), transpose)

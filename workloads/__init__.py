@@ -33,6 +33,18 @@ class Line:
 
 
 @dataclass
+class ModeLine:
+    """A guided-mode source on one grid column: amplitude * phi_mode[j] at cell (col, j), where
+    phi_mode is the mode-th guided mode (0 = TE0, 1 = TE1, ...) of the cross-section eps_line at
+    each wavelength.  The profile is not computed here: each consumer resolves it with its own
+    mode solver (with_modes)."""
+    col: int
+    eps_line: np.ndarray        # float64 [ny]
+    mode: int
+    amplitude: complex = -1j
+
+
+@dataclass
 class Workload:
     name: str
     nx: int
@@ -43,7 +55,7 @@ class Workload:
     box: tuple                  # design box (x0, y0, w, h) in cells
     eps_bg: np.ndarray          # float64 [nx, ny], permittivity outside the design box
     rho: np.ndarray             # float64 [w, h] initial design density in [0, 1]
-    sources: list               # [n_src] Line: right-hand side b (dimensionless)
+    sources: list               # [n_src] Line (same at every wavelength) or ModeLine (resolved per wavelength)
     monitors: list              # [n_omega][n_src] Line: overlap weights g
     iterations: int
     optimizer: str              # "sign" or "adam"
@@ -80,9 +92,32 @@ class Workload:
         eps[x0:x0 + w, y0:y0 + h] = self.eps_design(rho)
         return eps
 
-    def source_dense(self, s: int) -> np.ndarray:
-        """Source s as a dense complex128 vector of length nx*ny (flat n = i*ny + j)."""
-        return line_dense(self.sources[s], self.nx, self.ny)
+    def source_line(self, s: int, w: int = 0) -> Line:
+        src = self.sources[s]
+        if isinstance(src, ModeLine):
+            prof = self.extra.get("mode_profiles")
+            if prof is None:
+                raise ValueError("mode sources not resolved: call with_modes(workload, mode_solver) first")
+            return Line(src.col, src.amplitude * prof[(s, w)])
+        return src
+
+    def source_dense(self, s: int, w: int = 0) -> np.ndarray:
+        """Source s at wavelength w as a dense complex128 vector of length nx*ny (flat n = i*ny + j)."""
+        return line_dense(self.source_line(s, w), self.nx, self.ny)
+
+    def select_wavelengths(self, ws) -> "Workload":
+        """A copy restricted to the listed wavelengths (resolved mode profiles follow)."""
+        import copy
+        out = copy.copy(self)
+        ws = list(ws)
+        out.wavelengths = np.asarray(self.wavelengths)[ws]
+        out.monitors = [self.monitors[w] for w in ws]
+        out.extra = dict(self.extra)
+        prof = self.extra.get("mode_profiles")
+        if prof is not None:
+            out.extra["mode_profiles"] = {(s, i): prof[(s, w)] for i, w in enumerate(ws)
+                                          for s in range(self.n_src) if (s, w) in prof}
+        return out
 
     def monitor_dense(self, w: int, s: int) -> np.ndarray:
         return line_dense(self.monitors[w][s], self.nx, self.ny)
@@ -115,19 +150,22 @@ def gaussian_profile(ny: int, dx: float, center: float, w0: float, lo: int, hi: 
     return g
 
 
-def hermite_gauss_profile(ny: int, dx: float, center: float, w0: float, order: int,
-                          lo: int, hi: int) -> np.ndarray:
-    """TE0/TE1-shaped input profiles: Gaussian (order 0) and its first odd Hermite mode."""
-    y = (np.arange(ny) + 0.5) * dx
-    u = (y - center) / w0
-    g = np.exp(-u * u)
-    if order == 1:
-        g = 2.0 * u * g
-    elif order != 0:
-        raise ValueError("order must be 0 or 1")
-    g[:lo] = 0.0
-    g[hi:] = 0.0
-    return g / np.max(np.abs(g))
+def with_modes(wl: Workload, mode_solver) -> Workload:
+    """A copy of wl whose ModeLine sources are resolved at every wavelength by
+    mode_solver(eps_line, k0dx, n_modes) -> (mu, theta, phi) (the library's slab_modes or the
+    oracle's: each side brings its own).  phi[mode] becomes the source profile."""
+    import copy
+    out = copy.copy(wl)
+    out.extra = dict(wl.extra)
+    prof = {}
+    for s, src in enumerate(wl.sources):
+        if not isinstance(src, ModeLine):
+            continue
+        for w, k0dx in enumerate(wl.k0dx()):
+            _, _, phi = mode_solver(src.eps_line, float(k0dx), src.mode + 1)
+            prof[(s, w)] = np.asarray(phi[src.mode], dtype=np.float64).copy()
+    out.extra["mode_profiles"] = prof
+    return out
 
 
 def _centred_box(nx: int, ny: int, w: int, h: int) -> tuple:
@@ -192,8 +230,8 @@ def make(name: str, seed: int = 0) -> Workload:
         if modes == 1:
             srcs = [Line(npml, -1j * gaussian_profile(ny, dx, yc, 0.5, lo, hi))]
         else:
-            srcs = [Line(npml, -1j * hermite_gauss_profile(ny, dx, yc, 0.6, m, lo, hi))
-                    for m in range(modes)]
+            # TE0 / TE1 of the 1.2 um input guide, launched on the first non-PML column
+            srcs = [ModeLine(npml, eps_bg[npml].copy(), m) for m in range(modes)]
         nw = len(wls)
         if name == "c3":
             # 8 Gaussian ports evenly on the right monitor column; port 2*(l//2) + m.
