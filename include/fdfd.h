@@ -322,6 +322,16 @@ void fdfd_reset_counters(fdfd_ctx* ctx);
  * is cleared and the context stays usable.  Any other status is a failure. */
 fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx);
 
+/* Self-test of the failure path of the tensor-core update-matrix pipeline (the paper
+ * has no counterpart).  The copy, MMA and accumulation roles of that kernel wait on
+ * shared-memory mbarriers with a bounded wait (by global time); a wait that gives up
+ * sets the context's error word to 2 and the CTA frees its tensor memory and returns.
+ * This call runs that same bounded wait, with a 1 ms limit, on an mbarrier that
+ * nothing arrives at (one small kernel on the context's stream, synchronised), and
+ * returns FDFD_ERR_TIMEOUT when it gave up as designed; the error word is cleared and
+ * the context stays usable.  Any other status is a failure. */
+fdfd_status fdfd_selftest_mbar_wait(fdfd_ctx* ctx);
+
 /* The same bounded wait as fdfd_selftest_wait, left for the caller to find: the
  * probe kernel and the copy of the error word back to the host are queued on the
  * context's stream and the call returns FDFD_OK without synchronising.  Once the

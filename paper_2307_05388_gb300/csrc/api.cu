@@ -1922,6 +1922,21 @@ fdfd_status fdfd_selftest_wait(fdfd_ctx* ctx) {
   return check_flow_err(ctx);
 }
 
+fdfd_status fdfd_selftest_mbar_wait(fdfd_ctx* ctx) {
+  if (!ctx) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  CKS(ensure_runtime(ctx));
+  CKS(check_flow_err(ctx));
+  const cudaError_t e1 = launch_mbar_probe(ctx->d_flow_err, ctx->stream);
+  const cudaError_t e2 = e1 == cudaSuccess ? cudaMemcpyAsync(ctx->h_flow_err, ctx->d_flow_err, sizeof(int),
+                                                             cudaMemcpyDeviceToHost, ctx->stream)
+                                           : e1;
+  const cudaError_t e3 = cudaStreamSynchronize(ctx->stream);
+  CK(e2);
+  CK(e3);
+  return check_flow_err(ctx);
+}
+
 fdfd_status fdfd_selftest_wait_async(fdfd_ctx* ctx) {
   if (!ctx) return FDFD_ERR_ARG;
   ctx->err.clear();

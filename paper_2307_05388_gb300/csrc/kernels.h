@@ -101,6 +101,8 @@ void launch_schur_tc(const FactorLaunch& a, const TcLaunch& t, int ntiles, int f
 // split tiles: S -= the sum of their partials; tasks (slot, mt, nt, first row of 16)
 void launch_schur_split_sum(const FactorLaunch& a, const TcLaunch& t, int ntasks, cudaStream_t s);
 cudaError_t tc_init_attributes();        // once per device, before the first factorisation
+// one bounded mbarrier wait (the product kernel's) on a barrier nothing arrives at; sets *err = 2
+cudaError_t launch_mbar_probe(int* err, cudaStream_t s);
 // panel-step trailing update restricted to the pivot-block rows and columns
 template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flist, int nf, int j0,
                                           int nb, int nmax, cudaStream_t s);

@@ -484,6 +484,25 @@ int tc_splits(long long tiles, int Kt, int min_ctas) {
 long long tc_tile_bytes_a(int form) {
   return form == 3 ? 3LL * Form<3>::tileA : form == 2 ? 2LL * Form<2>::tileA : (long long)Form<1>::tileA;
 }
+namespace {
+// Self-test of the pipeline's bounded waits: one mbarrier that nothing arrives at,
+// waited on by the product kernel's own mbar_wait with a 1 ms limit.  The wait gives
+// up and the error word is set to 2, exactly as by a product CTA whose copy or MMA
+// never completed; the CTA then returns.
+__global__ void mbar_probe_kernel(int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(b, 0, 1000000ull)) atomicExch(err, 2);
+}
+}  // namespace
+
+cudaError_t launch_mbar_probe(int* err, cudaStream_t s) {
+  mbar_probe_kernel<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
+}
+
 long long tc_tile_bytes_b(int form) {
   return form == 3 ? 3LL * Form<3>::tileB : form == 2 ? 2LL * Form<2>::tileB : (long long)Form<1>::tileB;
 }

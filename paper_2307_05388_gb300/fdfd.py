@@ -28,7 +28,7 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_solve", "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
-           "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
+           "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_mbar_wait", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
            "fdfd_slab_modes", "fdfd_objective_target", "fdfd_design_iteration", "fdfd_density_eps"]
 HOST_EPS, HOST_OUT = 1, 2
 
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_selftest_schur_tc.argtypes = [vp, vp, i, i, i, i]
     lib.fdfd_selftest_wait.argtypes = [vp]
     lib.fdfd_selftest_wait_async.argtypes = [vp]
+    lib.fdfd_selftest_mbar_wait.argtypes = [vp]
     lib.fdfd_slab_modes.argtypes = [i, d, vp, i, vp, vp, vp]
     lib.fdfd_last_error.argtypes = [vp]
     lib.fdfd_last_error.restype = C.c_char_p
@@ -112,7 +113,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                  "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
                  "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get", "fdfd_filter_project",
                  "fdfd_filter_project_adjoint", "fdfd_objective_target", "fdfd_design_iteration",
-                 "fdfd_density_eps", "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
+                 "fdfd_density_eps", "fdfd_selftest_mbar_wait", "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -358,6 +359,11 @@ class Solver:
         m = n - k
         self._check(_lib.fdfd_selftest_schur_tc(self._h, C.c_void_p(front.data_ptr()), int(k), int(m),
                                                 int(front.stride(0)), int(planes)), "fdfd_selftest_schur_tc")
+
+    def selftest_mbar_wait(self) -> int:
+        """Runs the tensor-core pipeline's bounded mbarrier wait on a barrier nothing arrives at;
+        returns the status (7 = gave up as designed)."""
+        return int(_lib.fdfd_selftest_mbar_wait(self._h))
 
     def selftest_wait_async(self) -> int:
         """Queues the same wait without synchronising; the next call that checks the error word

@@ -341,6 +341,21 @@ def test_bounded_sweep_wait_gives_up_and_context_survives():
     assert O.rel_err(x2, ref2) <= FIELD_TOL
 
 
+def test_tensor_core_pipeline_wait_gives_up_and_context_survives():
+    """The tensor-core update matrix's bounded mbarrier wait, run on a barrier nothing arrives at
+    (1 ms limit), gives up with FDFD_ERR_TIMEOUT instead of hanging; the context then factorises
+    (with the tensor-core update matrices) and solves correctly."""
+    wl = W.make("c1")
+    s = U.make_solver(wl, tensor_min_m=1, tensor_min_tiles=1)
+    assert s.selftest_mbar_wait() == 7
+    assert s.selftest_mbar_wait() == 7
+    s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
+    b = torch.from_numpy(W.random_complex((1, 1, wl.n), 5)).to(DEV)
+    x = s.solve(b).cpu().numpy()
+    ref = _oracle_fields(wl, wl.eps_full(), False, b.cpu().numpy())
+    assert O.rel_err(x, ref) <= FIELD_TOL
+
+
 def test_solve_before_factor_is_state_error():
     wl = W.make_small(12, 12, 2, (3, 3, 4, 4), seed=2)
     s = U.make_solver(wl)

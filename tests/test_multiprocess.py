@@ -53,7 +53,7 @@ def test_reference_arm_under_torchrun_two_ranks():
     (rank 0's) is printed, with the contract's keys."""
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--workload", "c1",
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--cpu-sample", "c1",
            "--steps", "1", "--warmup", "3"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
