@@ -291,6 +291,20 @@ fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* out);
 fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k_host, int* m_host, int* parent_host, int* level_host,
                              int* design_host, int* idx_host);
 
+/* More plan introspection: per front its size n = k + m, the row stride ld of its
+ * storage and the row stride ldk of its inverse block (host memory; NULL skips). */
+fdfd_status fdfd_plan_sizes(fdfd_ctx* ctx, int* n_host, int* ld_host, int* ldk_host);
+
+/* Factor introspection for tests: copies front f of wavelength w of the current
+ * factorisation to host memory (synchronises the stream): front_host receives
+ * n x ld entries (row-major; complex64, or complex128 if the factorisation is in
+ * FP64: L21 below the pivot rows, U12 right of them (LU form only) and the update
+ * matrix S in the trailing block, lower triangle only in the symmetric form), inv_host
+ * k x ldk entries of the inverse block (L11^-1 strictly below the diagonal; U11^-1 on
+ * and above it in the LU form, 1 / d on the diagonal in the symmetric form).  Either
+ * pointer may be NULL.  FDFD_ERR_STATE before a factorisation. */
+fdfd_status fdfd_front_copy(fdfd_ctx* ctx, int w, int f, void* front_host, void* inv_host);
+
 /* Per-kernel profile: while enabled, every kernel launch of the solver is
  * bracketed by CUDA events on the context's stream and its algorithmic work
  * (flops at 8 per complex multiply-add, and the bytes the method must move) is

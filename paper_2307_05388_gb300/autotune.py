@@ -17,6 +17,10 @@ is spread over the SMs.  The tuner picks these per problem:
   split the contraction (1).
 * ``leaf_area``: the nested-dissection leaf size.  It sets how many small
   fronts there are, and how large the separators above them get.
+* ``factor_form``: LU of A with block-local pivoting (0), or the symmetric form
+  L diag(d) L^T of D A without pivoting (1: half the update work; admitted only
+  where its pivot growth stays inside the bound, which the accuracy gate below
+  checks through the absence of fallbacks).
 
 Each candidate is measured the way a design iteration runs.  A solver is built
 with the candidate's options and gets a full factorisation, followed by timed
@@ -47,6 +51,7 @@ from . import fdfd
 
 #: (option, values) in search order; the first value of each is the library default.
 SEARCH = (
+    ("factor_form", (0, 1)),
     ("tensor_form", (3, 2, 1, 0)),
     ("tensor_min_m", (128, 256, 512)),
     ("tensor_min_tiles", (0, 1)),
@@ -150,9 +155,11 @@ def measure(prob, eps_design: torch.Tensor, steps: int, warmup: int, flush: torc
     return sum(a.elapsed_time(b) for a, b in evs) / steps
 
 
-def _admission(stats: dict, ir_tol: float) -> str:
+def _admission(stats: dict, ir_tol: float, params: dict | None = None) -> str:
     if stats["fallbacks"] > 0:
         return f"FP64 refactorisation ({stats['fallbacks']}): the FP32 factors did not carry refinement"
+    if params and params.get("factor_form") == 1 and stats.get("factor_form", 1) != 1:
+        return "the symmetric form exceeded the growth bound and fell back to pivoted LU"
     if not stats["ir_resid"] <= ir_tol:
         return f"residual {stats['ir_resid']:.3g} above ir_tol {ir_tol:.3g}"
     return "ok"
@@ -232,7 +239,7 @@ def tune(make_problem: Callable[[fdfd.Options], object], eps_design: torch.Tenso
                 key = problem_key(prob.solver, prob.b.shape[1] if hasattr(prob, "b") else 1)
             ms = measure(prob, eps_design, steps, warmup, flush, event, sync)
             st = prob.solver.stats()
-            status = _admission(st, opts.ir_tol)
+            status = _admission(st, opts.ir_tol, params)
             t = Trial(params, ms, status, int(st["ir_iters"]), float(st["growth"]))
         except RuntimeError as e:
             t = Trial(params, None, f"error: {e}")

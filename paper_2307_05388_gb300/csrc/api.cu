@@ -1805,6 +1805,18 @@ fdfd_status fdfd_stats_get(fdfd_ctx* ctx, fdfd_stats* o) {
   return FDFD_OK;
 }
 
+fdfd_status fdfd_plan_sizes(fdfd_ctx* ctx, int* n_host, int* ld_host, int* ldk_host) {
+  if (!ctx) return FDFD_ERR_ARG;
+  if (!ctx->analyzed) return fail(ctx, FDFD_ERR_STATE, "plan requested before fdfd_analyze");
+  const Plan& p = ctx->plan;
+  for (size_t f = 0; f < p.fronts.size(); ++f) {
+    if (n_host) n_host[f] = p.fronts[f].n;
+    if (ld_host) ld_host[f] = p.fronts[f].ld;
+    if (ldk_host) ldk_host[f] = p.fronts[f].ldk;
+  }
+  return FDFD_OK;
+}
+
 fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k, int* m, int* parent, int* level, int* design, int* idx) {
   if (!ctx) return FDFD_ERR_ARG;
   if (!ctx->analyzed) return fail(ctx, FDFD_ERR_STATE, "plan requested before fdfd_analyze");
@@ -1818,6 +1830,26 @@ fdfd_status fdfd_plan_fronts(fdfd_ctx* ctx, int* k, int* m, int* parent, int* le
     if (design) design[f] = d.design;
   }
   if (idx) std::memcpy(idx, p.idx.data(), sizeof(int) * p.idx.size());
+  return FDFD_OK;
+}
+
+fdfd_status fdfd_front_copy(fdfd_ctx* ctx, int w, int f, void* front_host, void* inv_host) {
+  if (!ctx || w < 0 || w >= ctx->n_omega || f < 0) return FDFD_ERR_ARG;
+  ctx->err.clear();
+  if (!ctx->analyzed || f >= (int)ctx->plan.fronts.size()) return fail(ctx, FDFD_ERR_ARG, "no such front");
+  if (!ctx->valid32 && !ctx->valid64) return fail(ctx, FDFD_ERR_STATE, "no factorisation");
+  const FrontDesc& d = ctx->plan.fronts[f];
+  const bool f64 = ctx->valid64;
+  const size_t es = f64 ? sizeof(double2) : sizeof(float2);
+  const char* st = f64 ? reinterpret_cast<const char*>(ctx->d_store64) : reinterpret_cast<const char*>(ctx->d_store32);
+  const char* iv = f64 ? reinterpret_cast<const char*>(ctx->d_inv64) : reinterpret_cast<const char*>(ctx->d_inv32);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (front_host)
+    CK(cudaMemcpy(front_host, st + es * ((size_t)w * ctx->plan.store_total + d.st_off), es * (size_t)d.n * d.ld,
+                  cudaMemcpyDeviceToHost));
+  if (inv_host)
+    CK(cudaMemcpy(inv_host, iv + es * ((size_t)w * ctx->plan.inv_total + d.iv_off), es * (size_t)d.k * d.ldk,
+                  cudaMemcpyDeviceToHost));
   return FDFD_OK;
 }
 

@@ -945,7 +945,7 @@ __device__ __forceinline__ typename RealOf<T>::type diag_lu_4warps(const T* __re
       const T myinv = pivot_rcp(ap);    // every lane's candidate, formed beside the redux
       unsigned key = used ? 0u : ((__float_as_uint(v) & ~31u) | (unsigned)(31 - lane));
       if (!used && !(v == v)) key = 0xffffffe0u | (unsigned)(31 - lane);   // NaN wins
-      if (sym) key = lane == p ? 0xffffffffu : 0u;
+      if (sym) key = lane == p ? (0xffffffe0u | (unsigned)(31 - lane)) : 0u;   // the diagonal, in order
       const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
       const int r = 31 - (int)(kmax & 31u);
       const T inv = shfl_c(myinv, r);

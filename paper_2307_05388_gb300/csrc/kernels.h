@@ -142,6 +142,8 @@ struct SolveLaunch {
   const double2* sxc = nullptr;   // [n_omega][nx]
   const double2* syc = nullptr;   // [n_omega][ny]
 };
+// With sym_out the L^T sweep writes D x; the fronts below read their boundary values x_m
+// back from the output, so they divide D out again.
 // sweep: 0 = L (forward, non-transposed), 1 = U (backward, non-transposed),
 //        2 = U^T (forward of the transpose solve), 3 = L^T (backward of the transpose solve).
 // Large fronts are cut into row tasks of sweep_row_block() rows (sweeps 0, 1)

@@ -184,6 +184,15 @@ __device__ __forceinline__ double2 out_val(const SolveLaunch& a, int w, int cell
   return a.sym_out ? cmul(sym_d(a, w, cell), x) : x;
 }
 
+// x_m of a front below, read back from the output: D x was written there for the
+// transposed symmetric-form solve
+__device__ __forceinline__ double2 xm_val(const SolveLaunch& a, int w, int cell, double2 x) {
+  if (!a.sym_out) return x;
+  const double2 d = sym_d(a, w, cell);
+  const double q = 1.0 / (d.x * d.x + d.y * d.y);
+  return cmul(x, make_double2(d.x * q, -d.y * q));
+}
+
 // w = y / d for the symmetric form (1 / d on the diagonal of the inverse store)
 template <typename T>
 __device__ __forceinline__ T mid_val(const SolveLaunch& a, const T* X, int ldk, int s, T v) {
@@ -315,7 +324,7 @@ __device__ __forceinline__ void whole_front_warp(const SolveLaunch& a, const Fro
     } else {
       for (int s = lane; s < k; s += 32) vs[s] = SWEEP == 3 ? mid_val(a, X, ldk, s, ldv(vf + s)) : ldv(vf + s);
       for (int t = lane; t < m; t += 32) {
-        const T x = cfrom<T>(ldv(xo + idx[k + t]));
+        const T x = cfrom<T>(SWEEP == 3 ? xm_val(a, w, idx[k + t], ldv(xo + idx[k + t])) : ldv(xo + idx[k + t]));
         vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
       }
     }
@@ -434,7 +443,8 @@ __device__ __forceinline__ void rect_task(const SolveLaunch& a, const FrontDesc&
     if (SWEEP == 0 || SWEEP == 2) {
       for (int s = tid; s < k; s += kThreads) vs[s] = ldv(vf + s);
     } else {
-      for (int t = tid; t < m; t += kThreads) vs[t] = cfrom<T>(ldv(xo + idx[k + t]));
+      for (int t = tid; t < m; t += kThreads)
+        vs[t] = cfrom<T>(SWEEP == 3 ? xm_val(a, w, idx[k + t], ldv(xo + idx[k + t])) : ldv(xo + idx[k + t]));
     }
     __syncthreads();
     if (SWEEP == 0 || SWEEP == 1) {
@@ -616,7 +626,7 @@ __device__ __forceinline__ void medium_front(const SolveLaunch& a, const FrontDe
     } else {
       for (int s = tid; s < k; s += kThreads) vs[s] = SWEEP == 3 ? mid_val(a, X, ldk, s, ldv(vf + s)) : ldv(vf + s);
       for (int t = tid; t < m; t += kThreads) {
-        const T x = cfrom<T>(ldv(xo + idx[k + t]));
+        const T x = cfrom<T>(SWEEP == 3 ? xm_val(a, w, idx[k + t], ldv(xo + idx[k + t])) : ldv(xo + idx[k + t]));
         vs[k + t] = SWEEP == 3 ? csub(czero<T>(), x) : x;
       }
     }

@@ -238,8 +238,11 @@ __global__ void gm_start_kernel(const double2* rr, int rr_ld, const double2* bb,
                                 double* bnorm, int first) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nsys) return;
-  const double beta = sqrt(fmax(rr[(size_t)s * rr_ld].x, 0.0));
-  if (first) bnorm[s] = sqrt(fmax(bb[(size_t)s * bb_ld].x, 0.0));
+  // norms from sums of squares; a NaN stays NaN (fmax would turn it into 0, and a
+  // poisoned solve would then look converged)
+  const double rr2 = rr[(size_t)s * rr_ld].x, bb2 = bb[(size_t)s * bb_ld].x;
+  const double beta = rr2 > 0.0 ? sqrt(rr2) : (rr2 == rr2 ? 0.0 : rr2);
+  if (first) bnorm[s] = bb2 > 0.0 ? sqrt(bb2) : (bb2 == bb2 ? 0.0 : bb2);
   const double bn = bnorm[s];
   for (int i = 0; i <= m; ++i) g[(size_t)s * (m + 1) + i] = make_double2(0, 0);
   g[(size_t)s * (m + 1)] = make_double2(beta, 0);
@@ -257,7 +260,7 @@ __device__ void givens_step(int s, const double2* hs, double hn2, int j, int m, 
                             double2* sn, double2* g, double* vscale, int* active, double* resid, const double* bnorm) {
   double2* Hc = H + ((size_t)s * m + j) * (m + 1);   // column j of H
   for (int i = 0; i <= j; ++i) Hc[i] = hs[i];
-  const double hnorm = sqrt(fmax(hn2, 0.0));
+  const double hnorm = hn2 > 0.0 ? sqrt(hn2) : (hn2 == hn2 ? 0.0 : hn2);
   Hc[j + 1] = make_double2(hnorm, 0);
   double2* C = cs + (size_t)s * m;
   double2* S = sn + (size_t)s * m;

@@ -29,7 +29,8 @@ EXPORTS = ["fdfd_default_options", "fdfd_create", "fdfd_analyze", "fdfd_factor",
            "fdfd_plan_fronts", "fdfd_reset_counters", "fdfd_last_error", "fdfd_destroy",
            "fdfd_profile_enable", "fdfd_profile_get", "fdfd_solve_raw_noalloc", "fdfd_noalloc_scratch_bytes",
            "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_mbar_wait", "fdfd_selftest_schur_tc", "fdfd_filter_project", "fdfd_filter_project_adjoint",
-           "fdfd_slab_modes", "fdfd_objective_target", "fdfd_design_iteration", "fdfd_density_eps"]
+           "fdfd_slab_modes", "fdfd_objective_target", "fdfd_design_iteration", "fdfd_density_eps", "fdfd_front_copy",
+           "fdfd_plan_sizes"]
 HOST_EPS, HOST_OUT = 1, 2
 
 
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.fdfd_grad.argtypes = [vp, vp, vp, i, vp, vp, i]
     lib.fdfd_objective_target.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]
     lib.fdfd_density_eps.argtypes = [vp, vp, d, d, vp]
+    lib.fdfd_front_copy.argtypes = [vp, i, i, vp, vp]
+    lib.fdfd_plan_sizes.argtypes = [vp, vp, vp, vp]
     lib.fdfd_design_iteration.argtypes = [vp, vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp, i]
     lib.fdfd_apply.argtypes = [vp, vp, vp, i, i]
     lib.fdfd_set_options.argtypes = [vp, C.POINTER(Options)]
@@ -113,7 +116,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                  "fdfd_objective", "fdfd_grad", "fdfd_apply", "fdfd_set_options", "fdfd_stats_get",
                  "fdfd_plan_fronts", "fdfd_profile_enable", "fdfd_profile_get", "fdfd_filter_project",
                  "fdfd_filter_project_adjoint", "fdfd_objective_target", "fdfd_design_iteration",
-                 "fdfd_density_eps", "fdfd_selftest_mbar_wait", "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
+                 "fdfd_density_eps", "fdfd_front_copy", "fdfd_plan_sizes", "fdfd_selftest_mbar_wait", "fdfd_selftest_wait", "fdfd_selftest_wait_async", "fdfd_selftest_schur_tc", "fdfd_slab_modes"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -373,6 +376,18 @@ class Solver:
     def selftest_wait(self) -> int:
         """Runs one bounded sweep wait on a counter nothing sets; returns the status (7 = gave up as designed)."""
         return int(_lib.fdfd_selftest_wait(self._h))
+
+    def front_data(self, f: int, w: int = 0, f64: bool = False):
+        """(front [n, ld], inverse block [k, ldk]) of front f at wavelength w as numpy complex arrays."""
+        k, m, *_ = self.plan_fronts()
+        n = np.zeros(len(k), np.int32); ld = np.zeros(len(k), np.int32); ldk = np.zeros(len(k), np.int32)
+        self._check(_lib.fdfd_plan_sizes(self._h, n.ctypes.data, ld.ctypes.data, ldk.ctypes.data),
+                    "fdfd_plan_sizes")
+        dt = np.complex128 if f64 else np.complex64
+        fr = np.zeros((int(n[f]), int(ld[f])), dt)
+        iv = np.zeros((int(k[f]), max(1, int(ldk[f]))), dt)
+        self._check(_lib.fdfd_front_copy(self._h, int(w), int(f), fr.ctypes.data, iv.ctypes.data), "fdfd_front_copy")
+        return fr, iv
 
     def plan_fronts(self):
         """(k, m, parent, level, design, idx) of the symbolic plan as numpy arrays."""

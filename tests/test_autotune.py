@@ -46,7 +46,7 @@ class FakeSolver:
         p = {k: getattr(self.options, k) for k in AT.TUNED}
         r = self.model(p)
         return {"fallbacks": r.get("fallbacks", 0), "ir_resid": r.get("resid", 1e-10),
-                "ir_iters": r.get("iters", 3), "growth": 10.0}
+                "ir_iters": r.get("iters", 3), "growth": 10.0, "factor_form": r.get("form", p["factor_form"])}
 
     def close(self):
         self.closed = True
@@ -97,7 +97,8 @@ def _model(p):
 
 def test_search_picks_fastest_admissible_and_gates_on_refinement():
     res, book = _run(_model)
-    assert res.params == {"tensor_form": 3, "tensor_min_m": 256, "tensor_min_tiles": 1, "leaf_area": 32}
+    assert res.params == {"factor_form": 0, "tensor_form": 3, "tensor_min_m": 256, "tensor_min_tiles": 1,
+                          "leaf_area": 32}
     assert not res.cached
     ok = [t for t in res.trials if t.ok]
     assert min(t.ms for t in ok) == pytest.approx(10.0 - 1.5 - 0.25)
@@ -129,6 +130,17 @@ def test_residual_gate():
     assert res.params["tensor_form"] != 2
     bad = [t for t in res.trials if t.params["tensor_form"] == 2]
     assert bad and "residual" in bad[0].status
+
+
+def test_symmetric_form_taken_only_while_it_stays_symmetric():
+    """The symmetric form wins when it is faster and its factors stay symmetric; a symmetric
+    candidate whose growth sent it back to pivoted LU is rejected."""
+    res, _ = _run(lambda p: {"ms": 4.0 if p["factor_form"] == 1 else 6.0})
+    assert res.params["factor_form"] == 1 and res.options.factor_form == 1
+    res, _ = _run(lambda p: {"ms": 4.0, "form": 0} if p["factor_form"] == 1 else {"ms": 6.0})
+    assert res.params["factor_form"] == 0
+    bad = [t for t in res.trials if t.params["factor_form"] == 1]
+    assert bad and "symmetric form" in bad[0].status
 
 
 def test_no_admissible_candidate_raises():
