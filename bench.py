@@ -255,6 +255,8 @@ def main():
     ap.add_argument("--factor-form", type=int, default=0, choices=[0, 1],
                     help="complex FP32 factors: 0 LU with block-local pivoting (default), 1 symmetric "
                          "L diag(d) L^T of D A without pivoting")
+    ap.add_argument("--rhs-pairs", type=int, default=0, choices=[0, 1],
+                    help="sweeps take a wavelength's right-hand sides two at a time (1) or one at a time (0, default)")
     ap.add_argument("--autotune", default="", metavar="CACHE.json",
                     help="choose tensor_form, tensor_min_m, tensor_min_tiles and leaf_area by measured design "
                          "iterations before the timed run (starting from --tensor-form), cached in this file")
@@ -383,7 +385,8 @@ def main():
         return 1e3 * total
 
     # ---- launch parameters: library defaults, or measured by the autotuner (not timed) ----
-    opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form, factor_form=args.factor_form)
+    opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form, factor_form=args.factor_form,
+                              sweep_rhs_pairs=args.rhs_pairs)
     tuned = None
     if args.autotune:
         from paper_2307_05388_gb300 import autotune as AT

@@ -221,6 +221,22 @@ class Factor:
         return self._solve(b, "T")
 
 
+def symmetric_ldlt(M: np.ndarray, order: np.ndarray):
+    """M[order][:, order] = L diag(d) L^T for a complex symmetric dense M, by Gaussian elimination
+    without pivoting in the given order (L unit lower triangular, plain transpose).  The reference
+    for the factors of the symmetric form of D A (reciprocity makes D A complex symmetric).
+    Returns (L, d) in the permuted order."""
+    Mp = np.array(M, dtype=np.complex128)[np.ix_(order, order)]
+    n = Mp.shape[0]
+    d = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        d[j] = Mp[j, j]
+        Mp[j + 1:, j] /= d[j]
+        Mp[j + 1:, j + 1:] -= np.outer(Mp[j + 1:, j], Mp[j + 1:, j]) * d[j]
+    L = np.tril(Mp, -1) + np.eye(n)
+    return L, d
+
+
 # ---------------------------------------------------------------------------
 # Eq. 3-4: objective, adjoint source and pixel gradient
 # ---------------------------------------------------------------------------

@@ -52,15 +52,17 @@ class DesignProblem:
             self.solver.refactor_design(eps_design.reshape(-1).contiguous())
         self.version += 1
 
-    def iteration(self, eps_design: torch.Tensor, grad_out: torch.Tensor | None = None):
-        """One forward + adjoint design iteration; returns (F, dF/deps_design [w*h])."""
+    def iteration(self, eps_design: torch.Tensor, grad_out: torch.Tensor | None = None,
+                  accumulate: bool = False):
+        """One forward + adjoint design iteration; returns (F, dF/deps_design [w*h]).  With
+        accumulate the gradient is added to grad_out instead of overwriting it."""
         s = self.solver
         self._load(eps_design)
         s.solve(self.b, out=self.x)
         F, o, badj = s.objective(self.x, self.cols, self.g, self.weight, target=self.target)
         s.solve(badj, transpose=True, out=self.xa)
         # the adjoint source already carries the per-system weights
-        g = s.grad(self.x, self.xa, None, out=grad_out)
+        g = s.grad(self.x, self.xa, None, out=grad_out, accumulate=accumulate)
         return F, g
 
     def __call__(self, eps_design: torch.Tensor) -> torch.Tensor:

@@ -125,7 +125,7 @@ struct fdfd_ctx {
   int ntap = 0;
   double tap_radius = 0;
   int* h_flow_err = nullptr;       // pinned copy
-  int flow_grid[2] = {0, 0};       // persistent CTAs [precision 0 = c64, 1 = c128]
+  int flow_grid[3] = {0, 0, 0};    // persistent CTAs [0 = c64, 1 = c128, 2 = c64 with right-hand sides in pairs]
 
   // coefficients and permittivity
   double2 *d_cxm = nullptr, *d_cxp = nullptr, *d_cym = nullptr, *d_cyp = nullptr;
@@ -932,8 +932,8 @@ fdfd_status ensure_ws(fdfd_ctx* ctx, int nrhs) {
   CK(dalloc(&ctx->d_flow_ctr, sizeof(int) * (1 + 2 * (size_t)ctx->n_omega * ctx->plan.fronts.size())));
   int nsm = 0;
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
-  for (int prec = 0; prec < 2; ++prec)
-    ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax), flow_wide(ctx));
+  for (int v = 0; v < 3; ++v)
+    ctx->flow_grid[v] = nsm * flow_blocks_per_sm(v == 1 ? 16 : 8, std::max(1, ctx->flow_vmax), flow_wide(ctx), v == 2);
   ctx->ws_nrhs = nrhs;
   return FDFD_OK;
 }
@@ -968,10 +968,11 @@ SolveLaunch solve_launch(const fdfd_ctx* ctx, void* vb, int nrhs, int w0, int nw
 
 // Persistent CTAs of the dataflow sweep for precision prec (host queries only).
 int flow_grid(fdfd_ctx* ctx, int prec) {
-  if (ctx->flow_grid[prec] > 0) return ctx->flow_grid[prec];
+  if (ctx->flow_grid[prec] > 0) return ctx->flow_grid[prec];   // prec 2: the paired-RHS variant of c64
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm <= 0) nsm = 1;
-  ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 0 ? 8 : 16, std::max(1, ctx->flow_vmax), flow_wide(ctx));
+  ctx->flow_grid[prec] = nsm * flow_blocks_per_sm(prec == 1 ? 16 : 8, std::max(1, ctx->flow_vmax), flow_wide(ctx),
+                                                  prec == 2);
   return ctx->flow_grid[prec];
 }
 
@@ -1024,7 +1025,9 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
   };
   const int* dl = ctx->d_lists;
   const size_t ctr_bytes = sizeof(int) * (1 + 2 * (size_t)sa.n_omega * p.fronts.size());
-  const int grid_max = flow_grid(ctx, prec);
+  // complex64 factors with an even number of right-hand sides per wavelength: the paired variant
+  const bool pairs = prec == 0 && ctx->opt.sweep_rhs_pairs && sa.nr >= 2 && sa.nr % 2 == 0;
+  const int grid_max = flow_grid(ctx, pairs ? 2 : prec);
   for (int dir = 0; dir < 2; ++dir) {
     SolveLaunch sd = sa;
     if (sym) {
@@ -1058,7 +1061,8 @@ fdfd_status sweep_pair(fdfd_ctx* ctx, const SolveLaunch& sa, int transpose, cons
     const int kind = sym ? (dir == 0 ? PK_SWEEP_L : PK_SWEEP_LT)
                          : (dir == 0 ? (transpose ? PK_SWEEP_UT : PK_SWEEP_L) : (transpose ? PK_SWEEP_LT : PK_SWEEP_U));
     Prof pr(ctx, kind, fl, by);
-    launch_sweep_flow<T>(sd, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s, flow_wide(ctx));
+    launch_sweep_flow<T>(sd, dir == 0 ? fwd : bwd, q, std::max(1, ctx->flow_vmax), grid, in, out, s, flow_wide(ctx),
+                         pairs);
   }
   CK(cudaGetLastError());
   return FDFD_OK;
@@ -1387,6 +1391,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->tensor_min_m = 128;
   o->tensor_min_tiles = 0;
   o->factor_form = 0;
+  o->sweep_rhs_pairs = 0;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -1425,6 +1430,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.tensor_min_m < 1) c->opt.tensor_min_m = 1;
   if (c->opt.tensor_min_tiles < 0) c->opt.tensor_min_tiles = 0;
   if (c->opt.factor_form != 1) c->opt.factor_form = 0;
+  if (c->opt.sweep_rhs_pairs != 0) c->opt.sweep_rhs_pairs = 1;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   {
     fdfd_options def;

@@ -172,9 +172,12 @@ struct FlowQueue {
 // in: right-hand sides, out: solutions, both complex128 [systems][n] whatever the
 // factor precision T (converted where the sweeps gather them and store them).
 // wide: the variant that keeps six CTAs resident per SM (large problems) instead of four
+// pairs: allow the paired-RHS variant (complex64 factors, even count per wavelength)
 template <typename T> void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax,
-                                             int grid, const void* in, void* out, cudaStream_t s, bool wide);
-int flow_blocks_per_sm(int elem_bytes, int vmax, bool wide);
+                                             int grid, const void* in, void* out, cudaStream_t s, bool wide,
+                                             bool pairs);
+// pair: the variant that takes right-hand sides in pairs (complex64 factors, even count per wavelength)
+int flow_blocks_per_sm(int elem_bytes, int vmax, bool wide, bool pair = false);
 int flow_whole_max_n();   // largest front the flow kernel runs as a one-warp whole-front task
 int flow_cta_max_n();     // largest front it runs as one whole-front task of a CTA
 // one bounded wait on a zero flag (gives up, sets *err); for the self-test entry point

@@ -146,6 +146,82 @@ __device__ __forceinline__ T col_dot(const T* __restrict__ base, int ld, const T
   return s;
 }
 
+// Two right-hand sides at once: each factor entry is loaded once and multiplied into
+// both systems' vectors (v0, v1).  Row form of warp_dot.
+template <typename T>
+__device__ __forceinline__ void warp_dot_pair(const T* __restrict__ row, const T* v0, const T* v1, int c0, int c1,
+                                              int lane, T& s0, T& s1) {
+  constexpr int UN = 8;
+  T a0 = czero<T>(), a1 = czero<T>();
+  int c = c0 + lane;
+  for (; c + 32 * (UN - 1) < c1; c += 32 * UN) {
+    T r[UN];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) r[u] = row[c + 32 * u];
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      a0 = cfma(r[u], v0[c + 32 * u], a0);
+      a1 = cfma(r[u], v1[c + 32 * u], a1);
+    }
+  }
+  for (; c < c1; c += 32) {
+    const T rv = row[c];
+    a0 = cfma(rv, v0[c], a0);
+    a1 = cfma(rv, v1[c], a1);
+  }
+  s0 = warp_sum(a0);
+  s1 = warp_sum(a1);
+}
+
+// Column form (col_dot) for two right-hand sides; red0 / red1 are separate reduction tiles.
+template <typename T, typename Mask>
+__device__ __forceinline__ void col_dot_pair(const T* __restrict__ base, int ld, const T* v0, const T* v1, int r0,
+                                             int r1, bool live, Mask inside, T (*red0)[32], T (*red1)[32], T& s0,
+                                             T& s1) {
+  constexpr int SL = 32 / kColBlk;
+  constexpr int RS = kWarps * SL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int UN = sizeof(T) == 8 ? 8 : 4;
+  T a0 = czero<T>(), a1 = czero<T>();
+  if (live) {
+    int r = r0 + warp * SL + lane / kColBlk;
+    for (; r + (UN - 1) * RS < r1; r += UN * RS) {
+      T f[UN];
+#pragma unroll
+      for (int u = 0; u < UN; ++u) f[u] = base[(size_t)(r + u * RS) * ld];
+#pragma unroll
+      for (int u = 0; u < UN; ++u)
+        if (inside(r + u * RS)) {
+          a0 = cfma(f[u], v0[r + u * RS], a0);
+          a1 = cfma(f[u], v1[r + u * RS], a1);
+        }
+    }
+    for (; r < r1; r += RS)
+      if (inside(r)) {
+        const T fv = base[(size_t)r * ld];
+        a0 = cfma(fv, v0[r], a0);
+        a1 = cfma(fv, v1[r], a1);
+      }
+  }
+#pragma unroll
+  for (int o = kColBlk; o < 32; o <<= 1) {
+    a0.x += __shfl_xor_sync(0xffffffffu, a0.x, o);
+    a0.y += __shfl_xor_sync(0xffffffffu, a0.y, o);
+    a1.x += __shfl_xor_sync(0xffffffffu, a1.x, o);
+    a1.y += __shfl_xor_sync(0xffffffffu, a1.y, o);
+  }
+  red0[warp][lane] = a0;
+  red1[warp][lane] = a1;
+  __syncthreads();
+  s0 = red0[0][lane];
+  s1 = red1[0][lane];
+  if (warp == 0)
+    for (int q = 1; q < kWarps; ++q) {
+      s0 = cadd(s0, red0[q][lane]);
+      s1 = cadd(s1, red1[q][lane]);
+    }
+}
+
 // The two (at most) children of a front as the gathers need them: where their
 // extend-add maps start and where their update vectors sit in a system's
 // front-vector buffer.  Loaded once per task instead of once per slot.
@@ -414,6 +490,160 @@ __device__ __forceinline__ void tri_task(const SolveLaunch& a, const FrontDesc& 
       double2* xo = out + sys * a.n;
       const T s = col_dot(X + c, ldk, vs, b0 + 1, k, c < k, [&](int b) { return b > c; }, red);
       if (warp == 0 && lane < kColBlk && c < k) xo[idx[Pm[c]]] = out_val(a, w, idx[Pm[c]], cadd(vs[c], s));
+    }
+    __syncthreads();
+  }
+}
+
+// tri_task for right-hand sides in pairs (r, r + 1): the same products, each inverse-block
+// entry loaded once for both systems; v1 = vs + vstride holds the second system's vector.
+template <typename T, int SWEEP>
+__device__ __forceinline__ void tri_task_pair(const SolveLaunch& a, const FrontDesc& d, int b0, int nrows, int w,
+                                              const double2* __restrict__ in, double2* __restrict__ out, T* vs,
+                                              int vstride, T (*red0)[32], T (*red1)[32]) {
+  const int k = d.k, ldk = d.ldk;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
+  const int* idx = a.P.idx + d.idx_off;
+  const Kids kids = load_kids(a, d);
+  T* v0 = vs;
+  T* v1 = vs + vstride;
+  for (int r = a.r0; r < a.r0 + a.nr; r += 2) {
+    const size_t sys0 = (size_t)w * a.nrhs + r, sys1 = sys0 + 1;
+    T* vbs0 = reinterpret_cast<T*>(a.vb) + sys0 * a.vec_stride;
+    T* vbs1 = reinterpret_cast<T*>(a.vb) + sys1 * a.vec_stride;
+    T* vf0 = vbs0 + d.v_off;
+    T* vf1 = vbs1 + d.v_off;
+    if (SWEEP == 0 || SWEEP == 2) {
+      const double2* rhs0 = in + sys0 * a.n;
+      const double2* rhs1 = in + sys1 * a.n;
+      for (int s = tid; s < k; s += kThreads) {
+        const int src = SWEEP == 0 ? Pm[s] : s;
+        v0[s] = gather_slot(a, d, kids, rhs0, vbs0, src, w);
+        v1[s] = gather_slot(a, d, kids, rhs1, vbs1, src, w);
+      }
+    } else {
+      for (int s = tid; s < k; s += kThreads) {
+        const bool mid = SWEEP == 3 && d.m == 0;
+        v0[s] = mid ? mid_val(a, X, ldk, s, ldv(vf0 + s)) : ldv(vf0 + s);
+        v1[s] = mid ? mid_val(a, X, ldk, s, ldv(vf1 + s)) : ldv(vf1 + s);
+      }
+    }
+    __syncthreads();
+    if (SWEEP == 0 || SWEEP == 1) {
+      double2* xo0 = out + sys0 * a.n;
+      double2* xo1 = out + sys1 * a.n;
+      for (int rr = warp; rr < nrows; rr += kWarps) {
+        const int row = b0 + rr;
+        if (row >= k) break;
+        T s0, s1;
+        warp_dot_pair(X + (size_t)row * ldk, v0, v1, SWEEP == 0 ? 0 : row, SWEEP == 0 ? row : k, lane, s0, s1);
+        if (lane == 0) {
+          if (SWEEP == 0) {
+            vf0[row] = cadd(v0[row], s0);
+            vf1[row] = cadd(v1[row], s1);
+          } else {
+            xo0[idx[row]] = cto64(s0);
+            xo1[idx[row]] = cto64(s1);
+          }
+        }
+      }
+    } else {
+      const int c = b0 + (lane & (kColBlk - 1));
+      T s0, s1;
+      if (SWEEP == 2) {
+        col_dot_pair(X + c, ldk, v0, v1, 0, min(b0 + kColBlk, k), c < k, [&](int b) { return b <= c; }, red0, red1,
+                     s0, s1);
+        if (warp == 0 && lane < kColBlk && c < k) {
+          vf0[c] = s0;
+          vf1[c] = s1;
+        }
+      } else {
+        col_dot_pair(X + c, ldk, v0, v1, b0 + 1, k, c < k, [&](int b) { return b > c; }, red0, red1, s0, s1);
+        if (warp == 0 && lane < kColBlk && c < k) {
+          const int cell = idx[Pm[c]];
+          out[sys0 * a.n + cell] = out_val(a, w, cell, cadd(v0[c], s0));
+          out[sys1 * a.n + cell] = out_val(a, w, cell, cadd(v1[c], s1));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// rect_task for right-hand sides in pairs (each off-diagonal entry loaded once for both).
+template <typename T, int SWEEP>
+__device__ __forceinline__ void rect_task_pair(const SolveLaunch& a, const FrontDesc& d, int s0, int nrows, int w,
+                                               double2* __restrict__ out, T* vs, int vstride, T (*red0)[32],
+                                               T (*red1)[32]) {
+  const int k = d.k, m = d.m, ld = d.ld;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* F = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+  const T* X = reinterpret_cast<const T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+  const int* idx = a.P.idx + d.idx_off;
+  const Kids kids = load_kids(a, d);
+  T* v0 = vs;
+  T* v1 = vs + vstride;
+  for (int r = a.r0; r < a.r0 + a.nr; r += 2) {
+    const size_t sys0 = (size_t)w * a.nrhs + r, sys1 = sys0 + 1;
+    T* vbs0 = reinterpret_cast<T*>(a.vb) + sys0 * a.vec_stride;
+    T* vbs1 = reinterpret_cast<T*>(a.vb) + sys1 * a.vec_stride;
+    T* vf0 = vbs0 + d.v_off;
+    T* vf1 = vbs1 + d.v_off;
+    const double2* xo0 = out + sys0 * a.n;
+    const double2* xo1 = out + sys1 * a.n;
+    if (SWEEP == 0 || SWEEP == 2) {
+      for (int q = tid; q < k; q += kThreads) {
+        v0[q] = ldv(vf0 + q);
+        v1[q] = ldv(vf1 + q);
+      }
+    } else {
+      for (int t = tid; t < m; t += kThreads) {
+        const int cell = idx[k + t];
+        v0[t] = cfrom<T>(SWEEP == 3 ? xm_val(a, w, cell, ldv(xo0 + cell)) : ldv(xo0 + cell));
+        v1[t] = cfrom<T>(SWEEP == 3 ? xm_val(a, w, cell, ldv(xo1 + cell)) : ldv(xo1 + cell));
+      }
+    }
+    __syncthreads();
+    if (SWEEP == 0 || SWEEP == 1) {
+      // rows s0 + warp (and s0 + warp + kWarps in a tall task), one at a time, both systems per load
+      const int lim = SWEEP == 0 ? m : k, len = SWEEP == 0 ? k : m;
+      for (int rr = warp; rr < nrows; rr += kWarps) {
+        const int ro = s0 + rr;
+        if (ro >= lim) break;
+        const T* Fr = SWEEP == 0 ? F + (size_t)(k + ro) * ld : F + (size_t)ro * ld + k;
+        const T g0 = SWEEP == 0 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs0, k + ro) : ldv(vf0 + ro);
+        const T g1 = SWEEP == 0 ? gather_slot(a, d, kids, (const double2*)nullptr, vbs1, k + ro) : ldv(vf1 + ro);
+        T p0, p1;
+        warp_dot_pair(Fr, v0, v1, 0, len, lane, p0, p1);
+        if (lane == 0) {
+          vf0[SWEEP == 0 ? k + ro : ro] = csub(g0, p0);
+          vf1[SWEEP == 0 ? k + ro : ro] = csub(g1, p1);
+        }
+      }
+    } else {
+      const int cols = SWEEP == 2 ? m : k;
+      const int rows = SWEEP == 2 ? k : m;
+      const int c = s0 + (lane & (kColBlk - 1));
+      const bool mine = warp == 0 && lane < kColBlk && c < cols;
+      const T* base = SWEEP == 2 ? F + k + c : F + (size_t)k * ld + c;
+      T g0 = czero<T>(), g1 = czero<T>();
+      if (mine) {
+        if (SWEEP == 2) {
+          g0 = gather_slot(a, d, kids, (const double2*)nullptr, vbs0, k + c);
+          g1 = gather_slot(a, d, kids, (const double2*)nullptr, vbs1, k + c);
+        } else {
+          g0 = mid_val(a, X, d.ldk, c, ldv(vf0 + c));
+          g1 = mid_val(a, X, d.ldk, c, ldv(vf1 + c));
+        }
+      }
+      T p0, p1;
+      col_dot_pair(base, ld, v0, v1, 0, rows, c < cols, [](int) { return true; }, red0, red1, p0, p1);
+      if (mine) {
+        vf0[SWEEP == 2 ? k + c : c] = csub(g0, p0);
+        vf1[SWEEP == 2 ? k + c : c] = csub(g1, p1);
+      }
     }
     __syncthreads();
   }
@@ -704,11 +934,14 @@ constexpr int kCtaWholeMaxN = 320;   // largest front swept whole by one CTA
 // sweeps bound by loads in flight) run more CTAs
 constexpr int kFlowBlocksNarrow = 4, kFlowBlocksWide = 6;
 
-template <typename T, int SWEEP, int MINB>
+// NRP = 2: large-front tasks take the right-hand sides in pairs (the launch's count of
+// them per wavelength is even); the second vector of a pair sits vstride entries above
+// the first in shared memory.
+template <typename T, int SWEEP, int MINB, int NRP>
 __global__ void __launch_bounds__(kThreads, MINB)
-flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2* __restrict__ out) {
+flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2* __restrict__ out, int vstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[kWarps][32];
+  __shared__ T red[NRP][kWarps][32];
   __shared__ int s_unit, s_ok, s_fail;
   T* vs = reinterpret_cast<T*>(smem_raw);
   constexpr bool kUp = SWEEP == 0 || SWEEP == 2;
@@ -797,9 +1030,11 @@ flow_kernel(SolveLaunch a, FlowQueue q, const double2* __restrict__ in, double2*
     }
     __syncthreads();
     if (!s_ok) break;
-    if (med) medium_front<T, SWEEP>(a, d, w, in, out, vs, red);
-    else if (rect) rect_task<T, SWEEP>(a, d, task.y, rows, w, out, vs, red);
-    else tri_task<T, SWEEP>(a, d, task.y, rows, w, in, out, vs, red);
+    if (med) medium_front<T, SWEEP>(a, d, w, in, out, vs, red[0]);
+    else if (NRP == 2 && rect) rect_task_pair<T, SWEEP>(a, d, task.y, rows, w, out, vs, vstride, red[0], red[NRP - 1]);
+    else if (NRP == 2) tri_task_pair<T, SWEEP>(a, d, task.y, rows, w, in, out, vs, vstride, red[0], red[NRP - 1]);
+    else if (rect) rect_task<T, SWEEP>(a, d, task.y, rows, w, out, vs, red[0]);
+    else tri_task<T, SWEEP>(a, d, task.y, rows, w, in, out, vs, red[0]);
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -823,41 +1058,53 @@ cudaError_t launch_wait_probe(const int* flag, int* err, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t flow_smem(int vmax, size_t es) {
-  const int e = vmax > kWarps * kWarpSlice ? vmax : kWarps * kWarpSlice;
-  return (size_t)e * es;
-}
+// vector entries of one shared-memory slot (a pair variant holds two slots)
+int flow_slot(int vmax) { return vmax > kWarps * kWarpSlice ? vmax : kWarps * kWarpSlice; }
+size_t flow_smem(int vmax, size_t es, bool pair) { return (size_t)flow_slot(vmax) * es * (pair ? 2 : 1); }
 
 template <typename T>
 void launch_sweep_flow(const SolveLaunch& a, int sweep, const FlowQueue& q, int vmax, int grid, const void* in,
-                       void* out, cudaStream_t s, bool wide) {
+                       void* out, cudaStream_t s, bool wide, bool pairs) {
   if (q.nunits <= 0) return;
-  const size_t smem = flow_smem(vmax, sizeof(T));
+  // right-hand sides in pairs for the complex64 factors when the count per wavelength is even
+  const bool pair = pairs && sizeof(T) == 8 && a.nr >= 2 && a.nr % 2 == 0;
+  const size_t smem = flow_smem(vmax, sizeof(T), pair);
+  const int vst = flow_slot(vmax);
   const double2* i = reinterpret_cast<const double2*>(in);
   double2* o = reinterpret_cast<double2*>(out);
-#define FDFD_FLOW_LAUNCH(B)                                                               \
-  switch (sweep) {                                                                        \
-    case 0: flow_kernel<T, 0, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;         \
-    case 1: flow_kernel<T, 1, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;         \
-    case 2: flow_kernel<T, 2, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;         \
-    default: flow_kernel<T, 3, B><<<grid, kThreads, smem, s>>>(a, q, i, o); break;        \
+#define FDFD_FLOW_LAUNCH(B, P)                                                                 \
+  switch (sweep) {                                                                             \
+    case 0: flow_kernel<T, 0, B, P><<<grid, kThreads, smem, s>>>(a, q, i, o, vst); break;      \
+    case 1: flow_kernel<T, 1, B, P><<<grid, kThreads, smem, s>>>(a, q, i, o, vst); break;      \
+    case 2: flow_kernel<T, 2, B, P><<<grid, kThreads, smem, s>>>(a, q, i, o, vst); break;      \
+    default: flow_kernel<T, 3, B, P><<<grid, kThreads, smem, s>>>(a, q, i, o, vst); break;     \
   }
-  if (wide) { FDFD_FLOW_LAUNCH(kFlowBlocksWide) } else { FDFD_FLOW_LAUNCH(kFlowBlocksNarrow) }
+  if constexpr (sizeof(T) == 8) {
+    if (pair) {
+      if (wide) { FDFD_FLOW_LAUNCH(kFlowBlocksWide, 2) } else { FDFD_FLOW_LAUNCH(kFlowBlocksNarrow, 2) }
+      return;
+    }
+  }
+  if (wide) { FDFD_FLOW_LAUNCH(kFlowBlocksWide, 1) } else { FDFD_FLOW_LAUNCH(kFlowBlocksNarrow, 1) }
 #undef FDFD_FLOW_LAUNCH
 }
 
-int flow_blocks_per_sm(int elem_bytes, int vmax, bool wide) {
+int flow_blocks_per_sm(int elem_bytes, int vmax, bool wide, bool pair) {
   int nb = 0;
-  const size_t smem = flow_smem(vmax, elem_bytes);
+  pair = pair && elem_bytes == 8;
+  const size_t smem = flow_smem(vmax, elem_bytes, pair);
   cudaError_t e;
-  if (wide)
+  if (pair)
+    e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksWide, 2>, kThreads, smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksNarrow, 2>, kThreads, smem);
+  else if (wide)
     e = elem_bytes == 8
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksWide>, kThreads, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1, kFlowBlocksWide>, kThreads, smem);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksWide, 1>, kThreads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1, kFlowBlocksWide, 1>, kThreads, smem);
   else
     e = elem_bytes == 8
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksNarrow>, kThreads, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1, kFlowBlocksNarrow>, kThreads, smem);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<float2, 1, kFlowBlocksNarrow, 1>, kThreads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, flow_kernel<double2, 1, kFlowBlocksNarrow, 1>, kThreads, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
@@ -870,19 +1117,21 @@ int sweep_col_block() { return kColBlk; }
 cudaError_t solve_init_attributes() {
   const int lim = 160 * 1024;
   cudaError_t e = cudaSuccess;
-#define FDFD_ATTR(K, T, S)                                                                             \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S, kFlowBlocksNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S, kFlowBlocksWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  FDFD_ATTR(flow_kernel, float2, 0) FDFD_ATTR(flow_kernel, float2, 1) FDFD_ATTR(flow_kernel, float2, 2)
-  FDFD_ATTR(flow_kernel, float2, 3) FDFD_ATTR(flow_kernel, double2, 0) FDFD_ATTR(flow_kernel, double2, 1)
-  FDFD_ATTR(flow_kernel, double2, 2) FDFD_ATTR(flow_kernel, double2, 3)
+#define FDFD_ATTR(K, T, S, P)                                                                          \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S, kFlowBlocksNarrow, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K<T, S, kFlowBlocksWide, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  FDFD_ATTR(flow_kernel, float2, 0, 1) FDFD_ATTR(flow_kernel, float2, 1, 1) FDFD_ATTR(flow_kernel, float2, 2, 1)
+  FDFD_ATTR(flow_kernel, float2, 3, 1) FDFD_ATTR(flow_kernel, double2, 0, 1) FDFD_ATTR(flow_kernel, double2, 1, 1)
+  FDFD_ATTR(flow_kernel, double2, 2, 1) FDFD_ATTR(flow_kernel, double2, 3, 1)
+  FDFD_ATTR(flow_kernel, float2, 0, 2) FDFD_ATTR(flow_kernel, float2, 1, 2) FDFD_ATTR(flow_kernel, float2, 2, 2)
+  FDFD_ATTR(flow_kernel, float2, 3, 2)
 #undef FDFD_ATTR
   return e;
 }
 
 template void launch_sweep_flow<float2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
-                                        cudaStream_t, bool);
+                                        cudaStream_t, bool, bool);
 template void launch_sweep_flow<double2>(const SolveLaunch&, int, const FlowQueue&, int, int, const void*, void*,
-                                         cudaStream_t, bool);
+                                         cudaStream_t, bool, bool);
 
 }  // namespace fdfd

@@ -75,14 +75,22 @@ class ShardedProblem:
 
     def iteration(self, eps_design: torch.Tensor, grad_out: torch.Tensor | None = None):
         """One design iteration of the whole problem: (F, dF/deps), the same on every rank."""
-        self.acc.zero_()
-        for p in self.problems:
-            F, g = p.iteration(eps_design)
-            self.acc[:self.n_design] += g.reshape(-1)
-            self.acc[self.n_design] += F.reshape(())
-        if self.dist is not None and self.dist.get_world_size(self.group) > 1:
-            self.dist.all_reduce(self.acc, op=self.dist.ReduceOp.SUM, group=self.group)
+        reduce = self.dist is not None and self.dist.get_world_size(self.group) > 1
+        if len(self.problems) == 1 and not reduce:
+            # a single context and no exchange: its gradient kernel writes the result in place
+            return self.problems[0].iteration(eps_design, grad_out=grad_out)
         g = self.acc[:self.n_design]
+        if not self.problems:
+            self.acc.zero_()
+        for k, p in enumerate(self.problems):
+            # the gradient kernel sums the contexts' shares into the reduction buffer itself
+            F, _ = p.iteration(eps_design, grad_out=g, accumulate=k > 0)
+            if k == 0:
+                self.acc[self.n_design:].copy_(F.reshape(1))
+            else:
+                self.acc[self.n_design] += F.reshape(())
+        if reduce:
+            self.dist.all_reduce(self.acc, op=self.dist.ReduceOp.SUM, group=self.group)
         if grad_out is not None:
             grad_out.copy_(g)
             g = grad_out

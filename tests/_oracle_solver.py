@@ -70,7 +70,10 @@ class OracleSolver:
                 g += wt * O.design_box_of(O.grad_eps(a[w, r], b[w, r], self.k0[w] * self.dx), self.nx, self.ny, self.box)
         t = torch.from_numpy(g.reshape(-1).copy())
         if out is not None:
-            out.copy_(t)
+            if accumulate:
+                out.add_(t)
+            else:
+                out.copy_(t)
             return out
         return t
 

@@ -129,3 +129,40 @@ def test_symmetric_form_falls_back_to_lu_when_growth_exceeds_the_bound():
     x2 = s.solve(b).cpu().numpy()
     fac = O.Factor(O.assemble(wl.nx, wl.ny, wl.eps_full(), wl.k0dx()[0], wl.npml), (wl.nx, wl.ny))
     assert O.rel_err(x2.reshape(-1), fac.solve(b.cpu().numpy().reshape(-1))) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("nx,ny,npml,box,leaf", [(37, 29, 5, (9, 7, 15, 11), 32),    # small fronts only
+                                                 (61, 45, 8, (13, 10, 30, 20), 16),   # panel steps, nb < 32
+                                                 (61, 45, 8, (13, 10, 30, 20), 64)])
+def test_symmetric_form_fronts_match_dense_ldlt(nx, ny, npml, box, leaf):
+    """Every front's L21 and 1/d (complex FP32) against the oracle's dense LDL^T of D A without
+    pivoting in the plan's elimination order (children before parents): the small-front kernel, the
+    panel steps and the update matrices all feed these factors."""
+    wl = W.make_small(nx, ny, npml, box, n_omega=1, n_src=1, seed=7)
+    s = U.make_solver(wl, ir_max_iter=0, growth_bound=1e38, leaf_area=leaf, **SYM)
+    s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
+    k, m, par, lev, des, idx = s.plan_fronts()
+    k0dx = wl.k0dx()[0]
+    A = O.assemble(wl.nx, wl.ny, wl.eps_full(), k0dx, wl.npml).toarray()
+    M = O.symmetrizer(wl.nx, wl.ny, k0dx, wl.npml)[:, None] * A
+    offs = np.concatenate([[0], np.cumsum(k + m)])
+    ch = [f for f in range(len(k)) if par[f] >= 0][0]
+    up = lev[ch] < lev[par[ch]]
+    forder = sorted(range(len(k)), key=lambda f: (lev[f] if up else -lev[f], f))
+    order = np.concatenate([idx[offs[f]:offs[f] + k[f]] for f in forder])
+    pos = np.empty(wl.n, np.int64)
+    pos[order] = np.arange(wl.n)
+    L, d = O.symmetric_ldlt(M, order)
+    worst_l = worst_d = 0.0
+    for f in range(len(k)):
+        fr, iv = s.front_data(f)
+        kk, mm = int(k[f]), int(m[f])
+        P = pos[idx[offs[f]:offs[f] + kk]]
+        B = pos[idx[offs[f] + kk:offs[f] + kk + mm]]
+        if kk and mm:
+            Lref = L[np.ix_(B, P)]
+            worst_l = max(worst_l, np.abs(fr[kk:kk + mm, :kk] - Lref).max() / np.abs(Lref).max())
+        if kk:
+            worst_d = max(worst_d, np.abs(np.diag(iv[:, :kk]) - 1 / d[P]).max() / np.abs(1 / d[P]).max())
+    print(f"{nx}x{ny} leaf {leaf}: worst front L21 error {worst_l:.2e}, 1/d error {worst_d:.2e}")
+    assert worst_l < 1e-3 and worst_d < 1e-3

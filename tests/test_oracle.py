@@ -565,3 +565,24 @@ def test_nested_dissection_factor_matches_dense_lapack(nx, ny, npml):
     assert O.rel_err(fac.solve_T(b), np.linalg.solve(Ad.T, b)) < 1e-12
     B = np.stack([b, W.random_complex(nx * ny, 13)], axis=1)
     np.testing.assert_allclose(fac.solve(B), np.linalg.solve(Ad, B), rtol=0, atol=1e-12 * np.abs(B).max() * 1e3)
+
+
+def test_symmetric_ldlt_reconstructs_and_solves():
+    """symmetric_ldlt: unit lower L and d with L diag(d) L^T = (D A)[order, order] to rounding, and the
+    solve x = L^-T d^-1 L^-1 D b (in the permuted order) equals the dense LAPACK solve of A x = b."""
+    nx, ny, npml = 9, 8, 2
+    k0dx = 2 * np.pi * 0.05 / 1.55
+    A = O.assemble(nx, ny, _rand_eps(nx, ny, 21), k0dx, npml).toarray()
+    D = O.symmetrizer(nx, ny, k0dx, npml)
+    M = D[:, None] * A
+    order = O.nested_dissection(nx, ny, leaf=8)
+    L, d = O.symmetric_ldlt(M, order)
+    assert np.allclose(np.diag(L), 1) and np.abs(np.triu(L, 1)).max() == 0
+    Mp = M[np.ix_(order, order)]
+    assert np.abs(L @ np.diag(d) @ L.T - Mp).max() < 1e-12 * np.abs(Mp).max()
+    b = W.random_complex(nx * ny, 22)
+    y = np.linalg.solve(L, (D * b)[order])
+    xp = np.linalg.solve(L.T, y / d)
+    x = np.empty_like(xp)
+    x[order] = xp
+    assert O.rel_err(x, np.linalg.solve(A, b)) < 1e-11
