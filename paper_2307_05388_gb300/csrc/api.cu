@@ -29,8 +29,7 @@ constexpr int kTcChunk = 1;
 
 struct LevelList {
   int task_off = 0, ntasks = 0;      // build tasks (int2) offset / count
-  int small_off = 0, nsmall = 0, nmax_small = 0;      // small fronts with n <= 48
-  int small2_off = 0, nsmall2 = 0, nmax_small2 = 0;   // the other small fronts
+  int small_off[kSmallClasses] = {}, nsmall[kSmallClasses] = {}, nmax_small[kSmallClasses] = {};   // small fronts by size class
   int large_off = 0, nlarge = 0, nmax_large = 0, kmax_large = 0, mmax_large = 0;
   int simt_off = 0, nsimt = 0, mmax_simt = 0;   // large fronts whose update matrix is formed by SIMT
   int tcf_off = 0, ntcf = 0;                    // ... on the tensor cores: TcFront records
@@ -362,17 +361,15 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
         for (int f : fl)
           if (p.fronts[f].n > small_n)
             for (int r0 = 0; r0 < p.fronts[f].n; r0 += 8) { lists.push_back(f); lists.push_back(r0); ll.ntasks++; }
-        // small fronts in two launches: up to 48 (narrow CTAs) and above
-        ll.small_off = (int)lists.size();
-        for (int f : fl)
-          if (p.fronts[f].n <= std::min(small_n, 48)) {
-            lists.push_back(f); ll.nsmall++; ll.nmax_small = std::max(ll.nmax_small, p.fronts[f].n);
-          }
-        ll.small2_off = (int)lists.size();
-        for (int f : fl)
-          if (p.fronts[f].n > 48 && p.fronts[f].n <= small_n) {
-            lists.push_back(f); ll.nsmall2++; ll.nmax_small2 = std::max(ll.nmax_small2, p.fronts[f].n);
-          }
+        // small fronts in one launch per size class
+        for (int c = 0, lo = 0; c < kSmallClasses; lo = lu_small_class_n(c), ++c) {
+          const int hi = std::min(small_n, lu_small_class_n(c));
+          ll.small_off[c] = (int)lists.size();
+          for (int f : fl)
+            if (p.fronts[f].n > lo && p.fronts[f].n <= hi) {
+              lists.push_back(f); ll.nsmall[c]++; ll.nmax_small[c] = std::max(ll.nmax_small[c], p.fronts[f].n);
+            }
+        }
         ll.large_off = (int)lists.size();
         for (int f : fl)
           if (p.fronts[f].n > small_n) {
@@ -756,15 +753,16 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
     {
       double fl = 0, by = 0;
       if (ctx->prof_on)
-        for (int t = 0; t < ll.nsmall + ll.nsmall2; ++t) {
-          const FrontDesc& d = p.fronts[hl[t < ll.nsmall ? ll.small_off + t : ll.small2_off + t - ll.nsmall]];
-          for (int j = 0; j < d.k; ++j) fl += 8.0 * (double)(d.n - j - 1) * (d.n - j - 1);
-          by += 2.0 * es * d.n * d.n;
-        }
+        for (int c = 0; c < kSmallClasses; ++c)
+          for (int t = 0; t < ll.nsmall[c]; ++t) {
+            const FrontDesc& d = p.fronts[hl[ll.small_off[c] + t]];
+            for (int j = 0; j < d.k; ++j) fl += 8.0 * (double)(d.n - j - 1) * (d.n - j - 1);
+            by += 2.0 * es * d.n * d.n;
+          }
       if (sym) fl *= 0.5;   // lower triangles only: (n-j-1)(n-j)/2 per pivot, up to the diagonal terms
       Prof pr(ctx, PK_LU_SMALL, fl * nwd, by * nwd);
-      launch_lu_small<T>(fa, ctx->d_lists + ll.small_off, ll.nsmall, ll.nmax_small, s);
-      launch_lu_small<T>(fa, ctx->d_lists + ll.small2_off, ll.nsmall2, ll.nmax_small2, s);
+      for (int c = 0; c < kSmallClasses; ++c)
+        launch_lu_small<T>(fa, ctx->d_lists + ll.small_off[c], ll.nsmall[c], ll.nmax_small[c], s);
     }
     const bool local_piv = ctx->opt.pivoting == 1 || sym;   // the symmetric form uses the one-launch panel step
     for (int j0 = 0; j0 < ll.kmax_large; j0 += nb) {

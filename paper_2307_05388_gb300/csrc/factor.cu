@@ -156,144 +156,258 @@ __device__ __forceinline__ void warp_argmax(R& v, int& i) {
 }
 
 // ---------------------------------------------------------------------------
-// Small fronts: the whole front in shared memory, one CTA per front, assembled
-// there (originals plus the children's update matrices, as the build kernel does
-// for the large fronts) and written back once, factored.
-// Partial pivoting over the k pivot rows; each pivot step is two phases: the
-// row swap, then the multipliers with the rank-1 update, during which lane 0 of
-// every warp, which writes the next column's entry of the warp's rows, keeps
-// the best of them as an argmax key (|v|^2 as float in the high word, the row
-// complemented in the low word: the largest value wins, ties go to the smaller
-// row) and posts it, so after the barrier every thread takes the next pivot
-// from the eight keys.  Then the triangular inverses, one warp per row,
-// lanes over the columns, straight from the factors in shared memory into the
-// inverse store:
+// Small fronts: one CTA per front, assembled in shared memory (the children's
+// update matrices, then the original entries, one thread per row), factored in
+// registers and written back once with its triangular inverses.
+//
+// The factorisation holds the front with lanes over rows and warps over
+// columns: thread (lane, warp) owns the entries (lane + 32 i, warp + NWARP jj),
+// i < RI, jj < RJ.  Partial pivoting over the k pivot rows moves no rows: step j
+// takes the unused pivot row p_j with the largest |F[r][j]| (ties to the smaller
+// row), every other unused row takes l_r = F[r][j] / F[p_j][j], updates
+// F[r][c] -= l_r F[p_j][c] for c > j, and l_r goes to column j of the shared
+// copy.  The warp owning column j + 1 publishes its entries and the argmax key
+// of the unused candidates (|v|^2 as float with its 7 low bits replaced by
+// 127 - row: the larger magnitude wins to 16 bits, ties to the smaller row, NaN
+// wins) while it finishes step j; after one barrier every warp takes p_j, the
+// lane holding row p_j hands the warp its pivot-row entries through shared
+// memory, and every thread updates its tile.  At the end the tile goes back to
+// the shared copy where the multipliers are not: row p_j is pivot row j of
+// L11\U11 and U12, rows >= k are L21 and the update matrix S in place.
+//
+// Then the triangular inverses, one warp per row, lanes over the columns,
+// from the factors in shared memory into the inverse store:
 //   row i of L11^-1: X[i][i] = 1, X[i][l] = -sum_{l < m <= i} X[i][m] L[m][l], m descending;
 //   row i of U11^-1: X[i][c] = (delta_ic - sum_{i <= l < c} X[i][l] U[l][c]) / U[c][c], l ascending.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 256;
-constexpr int kSmallNarrowN = 48;   // fronts up to this size run with kSmallThreads / 2 threads
+constexpr int kSmallNarrowN = 48;   // symmetric-form fronts up to this size run with kSmallThreads / 2 threads
 constexpr int kSmallMaxK = 256;
-constexpr int kSmallSlots = 3;   // columns per lane in the inverse rows (k <= 96)
-
-template <typename R>
-__device__ __forceinline__ unsigned long long piv_key(R v2, int r) {
-  return ((unsigned long long)__float_as_uint((float)v2) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)r);
-}
-__device__ __forceinline__ int key_row(unsigned long long key) { return (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)); }
+constexpr int kSmallSlots = 3;      // columns per lane in the inverse rows (k <= 96)
+constexpr int kSmallMaxN = 96;      // largest complex64 front of the small path (complex128: 64)
 
 template <typename T>
 __device__ __forceinline__ T pick_slot(const T (&v)[kSmallSlots], int q) {
   return q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
 }
 
-template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+// 1 / z as conj(z) / |z|^2 with a correctly rounded reciprocal (pivots here are
+// far from the over/underflow range; a zero pivot gives inf/NaN, flagged as growth)
+__device__ __forceinline__ float2 fast_crcp(float2 z) {
+  const float s = __frcp_rn(z.x * z.x + z.y * z.y);
+  return make_float2(z.x * s, -z.y * s);
+}
+__device__ __forceinline__ double2 fast_crcp(double2 z) {
+  const double s = __drcp_rn(z.x * z.x + z.y * z.y);
+  return make_double2(z.x * s, -z.y * s);
+}
+
+// 1 / z for a pivot: conj(z) / |z|^2 with the hardware reciprocal estimate of
+// |z|^2 refined by one Newton-Raphson step (double: the correctly rounded one)
+__device__ __forceinline__ float2 pivot_rcp(float2 z) {
+  const float dd = z.x * z.x + z.y * z.y;
+  float s0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s0) : "f"(dd));
+  const float sc = fmaf(s0, fmaf(-dd, s0, 1.0f), s0);
+  return make_float2(z.x * sc, -z.y * sc);
+}
+__device__ __forceinline__ double2 pivot_rcp(double2 z) { return fast_crcp(z); }
+
+// argmax key of a pivot candidate in row r < 128: |v|^2 (as float) with its 7
+// low bits replaced by 127 - r; 0 means no candidate
+template <typename R>
+__device__ __forceinline__ unsigned small_key(R v2, int r) {
+  return (__float_as_uint((float)v2) & ~127u) | (unsigned)(127 - r);
+}
+
+// The warp owning column jn posts the column's entries to col and the argmax
+// key of its unused pivot candidates (rows < k) to *key.
+template <typename T, int NWARP, int RI, int RJ>
+__device__ __forceinline__ void small_post_column(const T (&x)[RI][RJ], unsigned done, int jn, int n, int k, int lane,
+                                                  T* col, unsigned* key) {
+  using R = typename RealOf<T>::type;
+  const int jq = jn / NWARP;
+  unsigned best = 0;
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const int r = lane + 32 * i;
+    T v = x[i][0];
+#pragma unroll
+    for (int jj = 1; jj < RJ; ++jj)
+      if (jj == jq) v = x[i][jj];
+    if (r < n) col[r] = v;
+    if (r < k && !((done >> i) & 1u)) {
+      const R a2 = cabs2(v);
+      best = max(best, a2 == a2 ? small_key(a2, r) : (0xffffff80u | (unsigned)(127 - r)));
+    }
+  }
+  best = __reduce_max_sync(0xffffffffu, best);
+  if (lane == 0) *key = best;
+}
+
+template <typename T, int NWARP, int RI, int RJ, int MINB>
+__global__ void __launch_bounds__(NWARP * 32, MINB)
 lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
   using R = typename RealOf<T>::type;
+  constexpr int THREADS = NWARP * 32, NMAX = 32 * RI < NWARP * RJ ? 32 * RI : NWARP * RJ;
+  static_assert(NMAX <= 128, "the argmax key holds the row in 7 bits");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);
-  __shared__ int pm[kSmallMaxK];
-  __shared__ unsigned long long s_key[2][THREADS / 32];   // [column parity][warp]
-  __shared__ R s_red[THREADS / 32];
+  T* S = reinterpret_cast<T*>(smem_raw);       // n x ls, ls = n | 1 (odd: rows by lane are conflict-free)
+  __shared__ T s_col[2][NMAX];                 // column j of the step, double-buffered
+  __shared__ __align__(16) T s_u[NWARP][RJ];   // each warp's columns of the pivot row
+  __shared__ int s_i0[NMAX], s_i1[NMAX];       // the children's extend-add maps
+  __shared__ int s_op[NMAX + 1];               // the rows' original-entry offsets
+  __shared__ int s_pm[NMAX];                   // p_j: the row that became pivot row j
+  __shared__ int s_pos[NMAX];                  // j for row p_j, k for the other rows
+  __shared__ unsigned s_key[2];
+  __shared__ R s_red[NWARP];
   const int w = blockIdx.y + a.w0;
   const int f = flist[blockIdx.x];
   const FrontDesc d = a.P.fronts[f];
-  const int n = d.n, k = d.k;
+  const int n = d.n, k = d.k, ls = n | 1;
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = THREADS / 32;
-  for (int i = tid; i < k; i += blockDim.x) pm[i] = i;
-  // assemble the front here (no separate build): the children's update-matrix
-  // rows through their inverse extend-add maps, then the row's original entries
+  // assemble the front in shared memory
   {
     const T* st = reinterpret_cast<const T*>(a.store) + (size_t)w * a.store_stride;
     FrontDesc c0, c1;
     const int nc = d.nchild;
     if (nc > 0) c0 = a.P.fronts[a.P.children[d.child0]];
     if (nc > 1) c1 = a.P.fronts[a.P.children[d.child0 + 1]];
-    for (int r = warp; r < n; r += NW) {
-      const int ia = nc > 0 ? a.P.inv[c0.inv_off + r] : -1;
-      const int ib = nc > 1 ? a.P.inv[c1.inv_off + r] : -1;
+    for (int c = tid; c <= n; c += THREADS) {
+      if (c < n) {
+        s_i0[c] = nc > 0 ? a.P.inv[c0.inv_off + c] : -1;
+        s_i1[c] = nc > 1 ? a.P.inv[c1.inv_off + c] : -1;
+        s_pos[c] = k;
+      }
+      s_op[c] = a.P.orig_ptr[d.orig_off + c];
+    }
+    __syncthreads();
+    // the children's update-matrix rows through their inverse extend-add maps
+#pragma unroll 2
+    for (int r = warp; r < n; r += NWARP) {
+      const int ia = s_i0[r], ib = s_i1[r];
       const T* S0 = ia >= 0 ? st + c0.st_off + (size_t)(c0.k + ia) * c0.ld + c0.k : nullptr;
       const T* S1 = ib >= 0 ? st + c1.st_off + (size_t)(c1.k + ib) * c1.ld + c1.k : nullptr;
       for (int c = lane; c < n; c += 32) {
         T v = czero<T>();
-        if (S0) { const int i0 = a.P.inv[c0.inv_off + c]; if (i0 >= 0) v = cadd(v, S0[i0]); }
-        if (S1) { const int i1 = a.P.inv[c1.inv_off + c]; if (i1 >= 0) v = cadd(v, S1[i1]); }
-        S[r * n + c] = v;
+        if (S0) { const int i0 = s_i0[c]; if (i0 >= 0) v = cadd(v, S0[i0]); }
+        if (S1) { const int i1 = s_i1[c]; if (i1 >= 0) v = cadd(v, S1[i1]); }
+        S[r * ls + c] = v;
       }
-      __syncwarp();
-      const int e0 = a.P.orig_ptr[d.orig_off + r], e1 = a.P.orig_ptr[d.orig_off + r + 1];
-      for (int e = e0 + lane; e < e1; e += 32) {
+    }
+    __syncthreads();
+    // the original entries, one thread per row (each column at most once per row)
+    for (int r = tid; r < n; r += THREADS) {
+      const int e0 = s_op[r], e1 = s_op[r + 1];
+      for (int e = e0; e < e1; ++e) {
         const int b = a.P.orig_col[e];
-        S[r * n + b] = cadd(S[r * n + b], cfrom<T>(stencil_entry(a.C, w, a.P.orig_code[e])));
+        S[r * ls + b] = cadd(S[r * ls + b], cfrom<T>(stencil_entry(a.C, w, a.P.orig_code[e])));
       }
     }
   }
   __syncthreads();
-  if (warp == 0) {   // pivot candidates of column 0
-    unsigned long long best = 0;
-    for (int r = lane; r < k; r += 32) best = max(best, piv_key(cabs2(S[r * n]), r));
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane < NW) s_key[0][lane] = lane == 0 ? best : 0ull;
-  }
-  __syncthreads();
-  R gmax = 0;
-  for (int j = 0; j < k; ++j) {
-    unsigned long long kb = s_key[j & 1][0];
+  T x[RI][RJ];
 #pragma unroll
-    for (int q = 1; q < NW; ++q) kb = max(kb, s_key[j & 1][q]);
-    const int piv = key_row(kb);
-    if (piv != j) {
-      for (int c = tid; c < n; c += blockDim.x) {
-        const T x = S[j * n + c];
-        S[j * n + c] = S[piv * n + c];
-        S[piv * n + c] = x;
-      }
-      if (tid == 0) { const int x = pm[j]; pm[j] = pm[piv]; pm[piv] = x; }
+  for (int i = 0; i < RI; ++i)
+#pragma unroll
+    for (int jj = 0; jj < RJ; ++jj) {
+      const int r = lane + 32 * i, c = warp + NWARP * jj;
+      x[i][jj] = (r < n && c < n) ? S[r * ls + c] : czero<T>();
     }
-    __syncthreads();
-    const T p = S[j * n + j];
-    const T inv = crcp(p);
-    if (tid == 0 && p.x == 0 && p.y == 0) gmax = INFINITY;
-    unsigned long long cand = 0;   // lane 0: best next-column candidate of this warp's rows
-    for (int r = j + 1 + warp; r < n; r += NW) {
-      const T l = cmul(S[r * n + j], inv);
-      for (int c = j + 1 + lane; c < n; c += 32) {
-        const T v = cfms(l, S[j * n + c], S[r * n + c]);
-        S[r * n + c] = v;
-        if (c == j + 1 && r < k) cand = max(cand, piv_key(cabs2(v), r));
+  unsigned done = 0;   // bit i: row lane + 32 i has been taken as a pivot row
+  R gmax = 0;
+  if (k > 0 && warp == 0) small_post_column<T, NWARP, RI, RJ>(x, done, 0, n, k, lane, s_col[0], &s_key[0]);
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    const int par = j & 1;
+    const int p = min(127 - (int)(s_key[par] & 127u), n - 1);   // (a candidate always exists)
+    const T pv = s_col[par][p];
+    const T inv = pivot_rcp(pv);
+    if (tid == 0) {
+      if (pv.x == 0 && pv.y == 0) gmax = INFINITY;
+      s_pm[j] = p;
+      s_pos[p] = j;
+    }
+    // the lane holding row p hands its warp the pivot row's entries in the warp's columns
+    if (lane == (p & 31)) {
+      const int pi = p >> 5;
+#pragma unroll
+      for (int jj = 0; jj < RJ; ++jj) {
+        T v = x[0][jj];
+#pragma unroll
+        for (int i = 1; i < RI; ++i)
+          if (i == pi) v = x[i][jj];
+        s_u[warp][jj] = v;
       }
-      __syncwarp();
-      if (lane == 0) {
-        S[r * n + j] = l;
-        gmax = nanmax(gmax, cabs2(l));
+      done |= 1u << pi;
+    }
+    __syncwarp();
+    T l[RI];
+    bool act[RI];
+#pragma unroll
+    for (int i = 0; i < RI; ++i) {
+      const int r = lane + 32 * i;
+      act[i] = r < n && !((done >> i) & 1u);
+      l[i] = act[i] ? cmul(s_col[par][r], inv) : czero<T>();
+    }
+    if (warp == j % NWARP) {
+      // the multipliers take column j of the shared copy
+#pragma unroll
+      for (int i = 0; i < RI; ++i)
+        if (act[i]) {
+          S[(lane + 32 * i) * ls + j] = l[i];
+          gmax = nanmax(gmax, cabs2(l[i]));
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < RJ; ++jj) {
+      const int c = warp + NWARP * jj;
+      if (c > j && c < n) {
+        const T u = s_u[warp][jj];
+#pragma unroll
+        for (int i = 0; i < RI; ++i)
+          if (act[i]) x[i][jj] = cfms(l[i], u, x[i][jj]);
       }
     }
-    if (lane == 0) s_key[(j + 1) & 1][warp] = cand;
+    if (j + 1 < k && warp == (j + 1) % NWARP)
+      small_post_column<T, NWARP, RI, RJ>(x, done, j + 1, n, k, lane, s_col[par ^ 1], &s_key[par ^ 1]);
     __syncthreads();
   }
-  // triangular inverses, rows i = warp, warp + 8, ...; lane holds columns lane + 32 q
+  // the tile back to the shared copy, except where the multipliers are (columns
+  // before the row's own pivot step; every column < k of the boundary rows)
+#pragma unroll
+  for (int i = 0; i < RI; ++i) {
+    const int r = lane + 32 * i;
+    const int lim = r < n ? s_pos[r] : 0;
+#pragma unroll
+    for (int jj = 0; jj < RJ; ++jj) {
+      const int c = warp + NWARP * jj;
+      if (r < n && c < n && c >= lim) S[r * ls + c] = x[i][jj];
+    }
+  }
+  __syncthreads();
+  // triangular inverses, rows i = warp, warp + NWARP, ...; lane holds columns lane + 32 q
   T* Xg = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const T one = cmk(R(1), R(0));
   T dinv[kSmallSlots];
 #pragma unroll
   for (int q = 0; q < kSmallSlots; ++q) {
     const int c = lane + 32 * q;
-    dinv[q] = c < k ? crcp(S[c * n + c]) : czero<T>();
+    dinv[q] = c < k ? pivot_rcp(S[s_pm[c] * ls + c]) : czero<T>();
   }
-  for (int i = warp; i < k; i += NW) {
+  for (int i = warp; i < k; i += NWARP) {
     T acc[kSmallSlots];
     // row i of L11^-1, columns l < i
 #pragma unroll
     for (int q = 0; q < kSmallSlots; ++q) acc[q] = czero<T>();
     for (int m = i; m >= 1; --m) {
       const T ym = m == i ? one : shfl_c(pick_slot(acc, m >> 5), m & 31);
+      const T* Lm = S + s_pm[m] * ls;
 #pragma unroll
       for (int q = 0; q < kSmallSlots; ++q) {
         const int l = lane + 32 * q;
-        if (l < m) acc[q] = cfms(ym, S[m * n + l], acc[q]);
+        if (l < m) acc[q] = cfms(ym, Lm[l], acc[q]);
       }
     }
 #pragma unroll
@@ -307,10 +421,11 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
     for (int l = i; l < k; ++l) {
       const int q = l >> 5;
       const T yl = shfl_c(cmul(pick_slot(acc, q), pick_slot(dinv, q)), l & 31);
+      const T* Ul = S + s_pm[l] * ls;
 #pragma unroll
       for (int qq = 0; qq < kSmallSlots; ++qq) {
         const int c = lane + 32 * qq;
-        if (c > l && c < k) acc[qq] = cfms(yl, S[l * n + c], acc[qq]);
+        if (c > l && c < k) acc[qq] = cfms(yl, Ul[c], acc[qq]);
       }
     }
 #pragma unroll
@@ -319,22 +434,43 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
       if (c >= i && c < k) Xg[(size_t)i * d.ldk + c] = cmul(acc[q], dinv[q]);
     }
   }
-  // the front but its pivot block (L21, U12, S), the permutation, the growth
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e / n, c = e - r * n;
-    if (r >= k || c >= k) F[(size_t)r * d.ld + c] = S[e];
+  // the front but its pivot block (U12 in pivot order, L21, S), the permutation, the growth
+  for (int r = warp; r < n; r += NWARP) {
+    const T* Sr = S + (r < k ? s_pm[r] : r) * ls;
+    T* Fr = F + (size_t)r * d.ld;
+    for (int c = (r < k ? k : 0) + lane; c < n; c += 32) Fr[c] = Sr[c];
   }
   int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
-  for (int i = tid; i < k; i += blockDim.x) P[i] = pm[i];
+  for (int i = tid; i < k; i += THREADS) P[i] = s_pm[i];
   for (int o = 16; o > 0; o >>= 1) gmax = nanmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   if (lane == 0) s_red[warp] = gmax;
   __syncthreads();
   if (tid == 0) {
     R g = 0;
-    for (int i = 0; i < NW; ++i) g = nanmax(g, s_red[i]);
+    for (int i = 0; i < NWARP; ++i) g = nanmax(g, s_red[i]);
     a.growth[(size_t)w * a.n_fronts + f] = (float)sqrt((double)g);
   }
 }
+
+// Warps and tile per size class (largest n of the class): NWARP warps, RI x RJ
+// entries per thread, MINB CTAs per SM for the register budget.
+template <typename T, int N> struct SmallCfg;
+template <typename T> struct SmallCfg<T, 32> {
+  static constexpr int kThreads = 64;
+  static auto kernel() { return lu_small_kernel<T, 2, 1, 16, 8>; }
+};
+template <typename T> struct SmallCfg<T, 48> {
+  static constexpr int kThreads = 128;
+  static auto kernel() { return lu_small_kernel<T, 4, 2, 12, 4>; }
+};
+template <typename T> struct SmallCfg<T, 64> {
+  static constexpr int kThreads = 256;
+  static auto kernel() { return lu_small_kernel<T, 8, 2, 8, 2>; }
+};
+template <typename T> struct SmallCfg<T, 96> {
+  static constexpr int kThreads = 256;
+  static auto kernel() { return lu_small_kernel<T, 8, 3, 12, 2>; }
+};
 
 // ---------------------------------------------------------------------------
 // Symmetric form (complex-symmetric LDL^T).  M = D A with D = diag(s_x s_y) is
@@ -882,28 +1018,6 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
 // entries of F and read B only, so the CTAs are independent.
 // ---------------------------------------------------------------------------
 constexpr int kStepRows = 64;
-
-// 1 / z as conj(z) / |z|^2 with a correctly rounded reciprocal (pivots here are
-// far from the over/underflow range; a zero pivot gives inf/NaN, flagged as growth)
-__device__ __forceinline__ float2 fast_crcp(float2 z) {
-  const float s = __frcp_rn(z.x * z.x + z.y * z.y);
-  return make_float2(z.x * s, -z.y * s);
-}
-__device__ __forceinline__ double2 fast_crcp(double2 z) {
-  const double s = __drcp_rn(z.x * z.x + z.y * z.y);
-  return make_double2(z.x * s, -z.y * s);
-}
-
-// 1 / z for a pivot: conj(z) / |z|^2 with the hardware reciprocal estimate of
-// |z|^2 refined by one Newton-Raphson step (double: the correctly rounded one)
-__device__ __forceinline__ float2 pivot_rcp(float2 z) {
-  const float dd = z.x * z.x + z.y * z.y;
-  float s0;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s0) : "f"(dd));
-  const float sc = fmaf(s0, fmaf(-dd, s0, 1.0f), s0);
-  return make_float2(z.x * sc, -z.y * sc);
-}
-__device__ __forceinline__ double2 pivot_rcp(double2 z) { return fast_crcp(z); }
 
 // LU of the nb x nb block at (j0, j0) with row pivoting inside the block, by
 // warps 0-3 (lane = row; warp w holds columns 8w..8w+7 in registers).  No rows
@@ -1612,7 +1726,8 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax,
 
 }  // namespace
 
-int lu_small_max_n(int elem_bytes) { return elem_bytes == 8 ? 96 : 64; }
+int lu_small_max_n(int elem_bytes) { return elem_bytes == 8 ? kSmallMaxN : 64; }
+int lu_small_class_n(int c) { return c == 0 ? 32 : c == 1 ? 48 : c == 2 ? 64 : kSmallMaxN; }
 
 namespace {
 __global__ void growth_max_kernel(const float* g, long long count, float* out) {
@@ -1637,11 +1752,10 @@ cudaError_t launch_growth_max(const float* growth, long long count, float* out, 
 
 cudaError_t factor_init_attributes() {
   // small fronts: the front in shared memory
-  cudaError_t e = cudaFuncSetAttribute(lu_small_kernel<float2, kSmallThreads>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 96 * 8);
+  cudaError_t e = cudaFuncSetAttribute(SmallCfg<float2, 96>::kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       96 * 97 * 8);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lu_small_kernel<double2, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           64 * 64 * 16);
+  e = cudaFuncSetAttribute(SmallCfg<double2, 64>::kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 65 * 16);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(ldl_small_kernel<float2, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            96 * 96 * 8);
@@ -1669,15 +1783,19 @@ void launch_build(const FactorLaunch& a, const int2* tasks, int ntasks, cudaStre
 template <typename T>
 void launch_lu_small(const FactorLaunch& a, const int* flist, int nf, int nmax, cudaStream_t s) {
   if (nf <= 0) return;
-  const size_t smem = (size_t)nmax * nmax * sizeof(T);
   // fronts up to kSmallNarrowN: half the threads, so that twice as many fit on an SM
   if (a.sym) {
+    const size_t smem = (size_t)nmax * nmax * sizeof(T);
     if (nmax <= kSmallNarrowN) ldl_small_kernel<T, kSmallThreads / 2><<<dim3(nf, a.n_omega), kSmallThreads / 2, smem, s>>>(a, flist);
     else ldl_small_kernel<T, kSmallThreads><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
     return;
   }
-  if (nmax <= kSmallNarrowN) lu_small_kernel<T, kSmallThreads / 2><<<dim3(nf, a.n_omega), kSmallThreads / 2, smem, s>>>(a, flist);
-  else lu_small_kernel<T, kSmallThreads><<<dim3(nf, a.n_omega), kSmallThreads, smem, s>>>(a, flist);
+  const dim3 grid(nf, a.n_omega);
+  const size_t smem = (size_t)nmax * (nmax | 1) * sizeof(T);   // rows of odd stride
+  if (nmax <= 32) SmallCfg<T, 32>::kernel()<<<grid, SmallCfg<T, 32>::kThreads, smem, s>>>(a, flist);
+  else if (nmax <= 48) SmallCfg<T, 48>::kernel()<<<grid, SmallCfg<T, 48>::kThreads, smem, s>>>(a, flist);
+  else if (nmax <= 64) SmallCfg<T, 64>::kernel()<<<grid, SmallCfg<T, 64>::kThreads, smem, s>>>(a, flist);
+  else if constexpr (sizeof(T) == 8) SmallCfg<T, 96>::kernel()<<<grid, SmallCfg<T, 96>::kThreads, smem, s>>>(a, flist);
 }
 
 template <typename T>

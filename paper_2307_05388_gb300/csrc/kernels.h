@@ -113,6 +113,9 @@ template <typename T> void launch_lu_gemm(const FactorLaunch& a, const int* flis
 template <typename T> void launch_lu_inv_fold(const FactorLaunch& a, const int* flist, int nf, int j0,
                                               cudaStream_t s);
 int lu_small_max_n(int elem_bytes);
+// largest n of small-front size class c (0..kSmallClasses-1); each class is one launch per level
+constexpr int kSmallClasses = 4;
+int lu_small_class_n(int c);
 cudaError_t factor_init_attributes();   // once per device, before the first factorisation
 int lu_panel_width(int elem_bytes);
 
