@@ -255,6 +255,9 @@ def main():
     ap.add_argument("--factor-form", type=int, default=0, choices=[0, 1],
                     help="complex FP32 factors: 0 LU with block-local pivoting (default), 1 symmetric "
                          "L diag(d) L^T of D A without pivoting")
+    ap.add_argument("--pivoting", type=int, default=1, choices=[0, 1],
+                    help="LU pivot search: 1 within 32 x 32 diagonal blocks (default), 0 partial pivoting over "
+                         "all pivot rows of a front")
     ap.add_argument("--rhs-pairs", type=int, default=0, choices=[0, 1],
                     help="sweeps take a wavelength's right-hand sides two at a time (1) or one at a time (0, default)")
     ap.add_argument("--autotune", default="", metavar="CACHE.json",
@@ -386,7 +389,7 @@ def main():
 
     # ---- launch parameters: library defaults, or measured by the autotuner (not timed) ----
     opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form, factor_form=args.factor_form,
-                              sweep_rhs_pairs=args.rhs_pairs)
+                              sweep_rhs_pairs=args.rhs_pairs, pivoting=args.pivoting)
     tuned = None
     if args.autotune:
         from paper_2307_05388_gb300 import autotune as AT
@@ -607,7 +610,8 @@ def main():
                                         f"(wavelength, source) pairs sharded over {world} ranks, "
                                         "all-reduce of [dF/deps, F] per iteration"),
                            factor_form=("symmetric L diag(d) L^T of D A, no pivoting" if opts.factor_form == 1
-                                        else "LU of A, pivoting within 32 x 32 diagonal blocks"),
+                                        else "LU of A, pivoting within 32 x 32 diagonal blocks" if opts.pivoting == 1
+                                        else "LU of A, partial pivoting over each front's pivot rows"),
                            launch_parameters={"tensor_min_m": opts.tensor_min_m,
                                               "tensor_min_tiles": opts.tensor_min_tiles,
                                               "leaf_area": opts.leaf_area, "autotuned": tuned}),

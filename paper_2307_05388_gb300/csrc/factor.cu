@@ -453,19 +453,21 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
 }
 
 // Warps and tile per size class (largest n of the class): NWARP warps, RI x RJ
-// entries per thread, MINB CTAs per SM for the register budget.
+// entries per thread, MINB CTAs per SM: complex64 classes up to n = 64 are held
+// to 64 registers (twice the resident warps of an unbounded build, without
+// spilling); complex128 keeps its registers.
 template <typename T, int N> struct SmallCfg;
 template <typename T> struct SmallCfg<T, 32> {
   static constexpr int kThreads = 64;
-  static auto kernel() { return lu_small_kernel<T, 2, 1, 16, 8>; }
+  static auto kernel() { return lu_small_kernel<T, 2, 1, 16, sizeof(T) == 8 ? 16 : 8>; }
 };
 template <typename T> struct SmallCfg<T, 48> {
   static constexpr int kThreads = 128;
-  static auto kernel() { return lu_small_kernel<T, 4, 2, 12, 4>; }
+  static auto kernel() { return lu_small_kernel<T, 4, 2, 12, sizeof(T) == 8 ? 8 : 4>; }
 };
 template <typename T> struct SmallCfg<T, 64> {
   static constexpr int kThreads = 256;
-  static auto kernel() { return lu_small_kernel<T, 8, 2, 8, 2>; }
+  static auto kernel() { return lu_small_kernel<T, 8, 2, 8, sizeof(T) == 8 ? 4 : 2>; }
 };
 template <typename T> struct SmallCfg<T, 96> {
   static constexpr int kThreads = 256;
