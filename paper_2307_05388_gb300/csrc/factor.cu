@@ -190,13 +190,17 @@ template <typename T>
 __device__ __forceinline__ T pick_slot(const T (&v)[kSmallSlots], int q) {
   return q == 0 ? v[0] : (q == 1 ? v[1] : v[2]);
 }
+template <typename T, int KS>
+__device__ __forceinline__ T pick_slot(const T (&v)[KS], int q) {
+  T r = v[0];
+#pragma unroll
+  for (int t = 1; t < KS; ++t)
+    if (q == t) r = v[t];
+  return r;
+}
 
 // 1 / z as conj(z) / |z|^2 with a correctly rounded reciprocal (pivots here are
 // far from the over/underflow range; a zero pivot gives inf/NaN, flagged as growth)
-__device__ __forceinline__ float2 fast_crcp(float2 z) {
-  const float s = __frcp_rn(z.x * z.x + z.y * z.y);
-  return make_float2(z.x * s, -z.y * s);
-}
 __device__ __forceinline__ double2 fast_crcp(double2 z) {
   const double s = __drcp_rn(z.x * z.x + z.y * z.y);
   return make_double2(z.x * s, -z.y * s);
@@ -220,21 +224,35 @@ __device__ __forceinline__ unsigned small_key(R v2, int r) {
   return (__float_as_uint((float)v2) & ~127u) | (unsigned)(127 - r);
 }
 
-// The warp owning column jn posts the column's entries to col and the argmax
-// key of its unused pivot candidates (rows < k) to *key.
-template <typename T, int NWARP, int RI, int RJ>
-__device__ __forceinline__ void small_post_column(const T (&x)[RI][RJ], unsigned done, int jn, int n, int k, int lane,
+// x[jq] for a slot index known only at run time (uniform over the warp): one
+// indexed branch instead of a chain of selects over the row's RJ registers
+template <typename T, int RJ>
+__device__ __forceinline__ T tile_slot(const T (&x)[RJ], int jq) {
+  static_assert(RJ <= 16, "tile rows of at most 16 slots");
+#define FDFD_SLOT(q) \
+  case q:            \
+    if constexpr (q < RJ) return x[q]; \
+    break;
+  switch (jq) {
+    FDFD_SLOT(0) FDFD_SLOT(1) FDFD_SLOT(2) FDFD_SLOT(3) FDFD_SLOT(4) FDFD_SLOT(5) FDFD_SLOT(6) FDFD_SLOT(7)
+    FDFD_SLOT(8) FDFD_SLOT(9) FDFD_SLOT(10) FDFD_SLOT(11) FDFD_SLOT(12) FDFD_SLOT(13) FDFD_SLOT(14) FDFD_SLOT(15)
+    default: break;
+  }
+#undef FDFD_SLOT
+  return x[0];
+}
+
+// The warp owning column jn posts the column's entries (its slot jq) to col and
+// the argmax key of its unused pivot candidates (rows < k) to *key.
+template <typename T, int RI, int RJ>
+__device__ __forceinline__ void small_post_column(const T (&x)[RI][RJ], unsigned done, int jq, int n, int k, int lane,
                                                   T* col, unsigned* key) {
   using R = typename RealOf<T>::type;
-  const int jq = jn / NWARP;
   unsigned best = 0;
 #pragma unroll
   for (int i = 0; i < RI; ++i) {
     const int r = lane + 32 * i;
-    T v = x[i][0];
-#pragma unroll
-    for (int jj = 1; jj < RJ; ++jj)
-      if (jj == jq) v = x[i][jj];
+    const T v = tile_slot(x[i], jq);
     if (r < n) col[r] = v;
     if (r < k && !((done >> i) & 1u)) {
       const R a2 = cabs2(v);
@@ -317,10 +335,10 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
     }
   unsigned done = 0;   // bit i: row lane + 32 i has been taken as a pivot row
   R gmax = 0;
-  if (k > 0 && warp == 0) small_post_column<T, NWARP, RI, RJ>(x, done, 0, n, k, lane, s_col[0], &s_key[0]);
+  if (k > 0 && warp == 0) small_post_column<T, RI, RJ>(x, done, 0, n, k, lane, s_col[0], &s_key[0]);
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    const int par = j & 1;
+    const int par = j & 1, sw = j % NWARP;   // column j is slot j / NWARP of warp sw
     const int p = min(127 - (int)(s_key[par] & 127u), n - 1);   // (a candidate always exists)
     const T pv = s_col[par][p];
     const T inv = pivot_rcp(pv);
@@ -333,13 +351,11 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
     if (lane == (p & 31)) {
       const int pi = p >> 5;
 #pragma unroll
-      for (int jj = 0; jj < RJ; ++jj) {
-        T v = x[0][jj];
+      for (int i = 0; i < RI; ++i)
+        if (i == pi) {
 #pragma unroll
-        for (int i = 1; i < RI; ++i)
-          if (i == pi) v = x[i][jj];
-        s_u[warp][jj] = v;
-      }
+          for (int jj = 0; jj < RJ; ++jj) s_u[warp][jj] = x[i][jj];
+        }
       done |= 1u << pi;
     }
     __syncwarp();
@@ -351,7 +367,7 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
       act[i] = r < n && !((done >> i) & 1u);
       l[i] = act[i] ? cmul(s_col[par][r], inv) : czero<T>();
     }
-    if (warp == j % NWARP) {
+    if (warp == sw) {
       // the multipliers take column j of the shared copy
 #pragma unroll
       for (int i = 0; i < RI; ++i)
@@ -360,18 +376,17 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
           gmax = nanmax(gmax, cabs2(l[i]));
         }
     }
+    // every column of the unused rows: the ones up to j are below the row's own
+    // pivot step (or < k), so they are never written back
 #pragma unroll
     for (int jj = 0; jj < RJ; ++jj) {
-      const int c = warp + NWARP * jj;
-      if (c > j && c < n) {
-        const T u = s_u[warp][jj];
+      const T u = s_u[warp][jj];
 #pragma unroll
-        for (int i = 0; i < RI; ++i)
-          if (act[i]) x[i][jj] = cfms(l[i], u, x[i][jj]);
-      }
+      for (int i = 0; i < RI; ++i)
+        if (act[i]) x[i][jj] = cfms(l[i], u, x[i][jj]);
     }
     if (j + 1 < k && warp == (j + 1) % NWARP)
-      small_post_column<T, NWARP, RI, RJ>(x, done, j + 1, n, k, lane, s_col[par ^ 1], &s_key[par ^ 1]);
+      small_post_column<T, RI, RJ>(x, done, (j + 1) / NWARP, n, k, lane, s_col[par ^ 1], &s_key[par ^ 1]);
     __syncthreads();
   }
   // the tile back to the shared copy, except where the multipliers are (columns
@@ -387,49 +402,50 @@ lu_small_kernel(FactorLaunch a, const int* __restrict__ flist) {
     }
   }
   __syncthreads();
-  // triangular inverses, rows i = warp, warp + NWARP, ...; lane holds columns lane + 32 q
+  // triangular inverses, rows i = warp, warp + NWARP, ...; lane holds columns lane + 32 q (KS slots: k <= 32 KS)
+  constexpr int KS = (NMAX + 31) / 32;
   T* Xg = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
   const T one = cmk(R(1), R(0));
-  T dinv[kSmallSlots];
+  T dinv[KS];
 #pragma unroll
-  for (int q = 0; q < kSmallSlots; ++q) {
+  for (int q = 0; q < KS; ++q) {
     const int c = lane + 32 * q;
     dinv[q] = c < k ? pivot_rcp(S[s_pm[c] * ls + c]) : czero<T>();
   }
   for (int i = warp; i < k; i += NWARP) {
-    T acc[kSmallSlots];
+    T acc[KS];
     // row i of L11^-1, columns l < i
 #pragma unroll
-    for (int q = 0; q < kSmallSlots; ++q) acc[q] = czero<T>();
+    for (int q = 0; q < KS; ++q) acc[q] = czero<T>();
     for (int m = i; m >= 1; --m) {
-      const T ym = m == i ? one : shfl_c(pick_slot(acc, m >> 5), m & 31);
+      const T ym = m == i ? one : shfl_c(pick_slot<T, KS>(acc, m >> 5), m & 31);
       const T* Lm = S + s_pm[m] * ls;
 #pragma unroll
-      for (int q = 0; q < kSmallSlots; ++q) {
+      for (int q = 0; q < KS; ++q) {
         const int l = lane + 32 * q;
         if (l < m) acc[q] = cfms(ym, Lm[l], acc[q]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kSmallSlots; ++q) {
+    for (int q = 0; q < KS; ++q) {
       const int l = lane + 32 * q;
       if (l < i) Xg[(size_t)i * d.ldk + l] = acc[q];
     }
     // row i of U11^-1, columns c >= i
 #pragma unroll
-    for (int q = 0; q < kSmallSlots; ++q) acc[q] = (lane + 32 * q == i) ? one : czero<T>();
+    for (int q = 0; q < KS; ++q) acc[q] = (lane + 32 * q == i) ? one : czero<T>();
     for (int l = i; l < k; ++l) {
       const int q = l >> 5;
-      const T yl = shfl_c(cmul(pick_slot(acc, q), pick_slot(dinv, q)), l & 31);
+      const T yl = shfl_c(cmul(pick_slot<T, KS>(acc, q), pick_slot<T, KS>(dinv, q)), l & 31);
       const T* Ul = S + s_pm[l] * ls;
 #pragma unroll
-      for (int qq = 0; qq < kSmallSlots; ++qq) {
+      for (int qq = 0; qq < KS; ++qq) {
         const int c = lane + 32 * qq;
         if (c > l && c < k) acc[qq] = cfms(yl, Ul[c], acc[qq]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kSmallSlots; ++q) {
+    for (int q = 0; q < KS; ++q) {
       const int c = lane + 32 * q;
       if (c >= i && c < k) Xg[(size_t)i * d.ldk + c] = cmul(acc[q], dinv[q]);
     }
@@ -726,7 +742,7 @@ lu_panel_smem_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   const FrontDesc d = a.P.fronts[f];
   if (j0 >= d.k) return;
   const int nb = min(nbmax, d.k - j0);
-  const int n = d.n, k = d.k, ld = d.ld;
+  const int k = d.k, ld = d.ld;
   const int R_ = k - j0, ldp = nb + 1;
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
   int* P = a.perm + (size_t)w * a.perm_stride + d.piv_off;
