@@ -258,6 +258,9 @@ def main():
     ap.add_argument("--pivoting", type=int, default=1, choices=[0, 1],
                     help="LU pivot search: 1 within 32 x 32 diagonal blocks (default), 0 partial pivoting over "
                          "all pivot rows of a front")
+    ap.add_argument("--offdiag-tc", type=int, default=0, choices=[0, 1],
+                    help="L21 and U12 of tensor-core fronts as products with the triangular inverses on the "
+                         "tensor cores (1) or by substitution in the panel steps (0, default)")
     ap.add_argument("--rhs-pairs", type=int, default=0, choices=[0, 1],
                     help="sweeps take a wavelength's right-hand sides two at a time (1) or one at a time (0, default)")
     ap.add_argument("--autotune", default="", metavar="CACHE.json",
@@ -389,7 +392,8 @@ def main():
 
     # ---- launch parameters: library defaults, or measured by the autotuner (not timed) ----
     opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form, factor_form=args.factor_form,
-                              sweep_rhs_pairs=args.rhs_pairs, pivoting=args.pivoting)
+                              sweep_rhs_pairs=args.rhs_pairs, pivoting=args.pivoting,
+                              tensor_offdiag=args.offdiag_tc)
     tuned = None
     if args.autotune:
         from paper_2307_05388_gb300 import autotune as AT

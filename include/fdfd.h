@@ -130,12 +130,19 @@ typedef struct {
                                   loaded once for both; twice the shared memory per CTA); 0: one at a
                                   time (default: the second system's reads mostly hit the caches, and
                                   the pairs' shared memory lowers residency; measured C3 +1%, C5 -7%). */
+  int tensor_offdiag;          /* 1: complex FP32 LU fronts whose update matrices go to the tensor cores
+                                  (tensor_form > 0, block-local pivoting) also form L21 = F21 U11^-1 and
+                                  U12 = L11^-1 P F12 there, as products with the triangular inverses, and
+                                  their panel steps factor only the pivot block; 0 (default): the panel
+                                  steps form L21 and U12 by substitution.  The products are faster but
+                                  carry the conditioning of U11 and L11 into the factors (more FGMRES
+                                  iterations on ill-conditioned fronts). */
 } fdfd_options;
 /* fdfd_create rejects a mode outside fdfd_mode with FDFD_ERR_ARG and clamps the
  * other fields: gmres_restart to 1..16, ir_max_iter and tensor_min_tiles to >= 0,
  * tensor_min_m to >= 1; leaf_area < 1, tensor_form outside 0..3, and ir_tol or
  * growth_bound that are not positive numbers take their defaults; any nonzero
- * pivoting means 1; factor_form outside 0..1 takes 0; any nonzero sweep_rhs_pairs means 1. */
+ * pivoting means 1; factor_form outside 0..1 takes 0; any nonzero sweep_rhs_pairs or tensor_offdiag means 1. */
 
 typedef struct {
   long long sf;                /* symbolic factorisations performed */

@@ -36,6 +36,11 @@ struct LevelList {
   int tcp_off = 0, ntcp = 0;                    // their pack tasks (int4)
   int tct_off = 0, ntct = 0;                    // their output tiles and K splits (int4)
   int tcs_off = 0, ntcs = 0;                    // 16-row sums of their split tiles (int4)
+  // c64 LU fronts on the tensor cores: their L21 and U12 too (TcFront modes 1, 2), after
+  // panel steps over the pivot block only
+  int tqf_off = 0, ntqf = 0;                    // TcFront records (two per front)
+  int tqp_off = 0, ntqp = 0;                    // their pack tasks
+  int tqt_off = 0, ntqt = 0;                    // their output tiles
 };
 
 struct TaskList {
@@ -106,6 +111,8 @@ struct fdfd_ctx {
   long long tc_part_stride = 0;    // floats per wavelength
   std::vector<TcFront> h_tcf;
   std::vector<int4> h_tct;
+  unsigned char* d_pivonly = nullptr;   // [full, design][front]: c64 LU panel steps over the pivot block only
+  std::vector<unsigned char> h_pivonly;
   std::vector<LevelList> lv_full[3], lv_design[3];   // [0 = c64 LU, 1 = c128 LU, 2 = c64 symmetric form]
   std::vector<SolveList> lv_solve;
   // dataflow sweep queues [task type: 0 rows, 1 columns][direction: 0 bottom-up, 1 top-down]
@@ -209,11 +216,12 @@ void free_ptr(void* p) {
 }
 
 enum ProfKind { PK_BUILD = 0, PK_LU_SMALL, PK_LU_STEP, PK_LU_PANEL, PK_LU_TRSM, PK_LU_GEMM, PK_LU_SCHUR, PK_LU_INV,
-                PK_TC_PACK, PK_LU_SCHUR_TC, PK_TC_SUM,
+                PK_TC_PACK, PK_LU_SCHUR_TC, PK_TC_SUM, PK_LU_TRSM_TC,
                 PK_SWEEP_L, PK_SWEEP_U, PK_SWEEP_UT, PK_SWEEP_LT, PK_SWEEP_RECT, PK_STENCIL, PK_DOT, PK_AXPY,
                 PK_ARNOLDI, PK_OTHER, PK_COUNT };
 const char* const kProfNames[PK_COUNT] = {"front_build", "lu_small", "lu_step", "lu_panel", "lu_trsm", "lu_gemm",
                                           "lu_schur", "lu_inv", "lu_schur_pack", "lu_schur_tc", "lu_schur_sum",
+                                          "lu_trsm_tc",
                                           "sweep_L", "sweep_U", "sweep_Ut", "sweep_Lt", "sweep_rect", "stencil_f64",
                                           "gmres_dot", "gmres_axpy", "gmres_arnoldi", "other"};
 
@@ -250,8 +258,8 @@ void free_plan_device(fdfd_ctx* c) {
   free_ptr(c->d_orig_ptr); free_ptr(c->d_orig_col); free_ptr(c->d_orig_code); free_ptr(c->d_lists);
   c->d_fronts = nullptr; c->d_children = c->d_idx = c->d_inv = c->d_orig_ptr = c->d_orig_col = nullptr;
   c->d_orig_code = c->d_lists = nullptr;
-  free_ptr(c->d_tcf); free_ptr(c->d_tct); free_ptr(c->d_tcws); free_ptr(c->d_tcpart);
-  c->d_tcf = nullptr; c->d_tct = nullptr; c->d_tcws = nullptr; c->d_tcpart = nullptr;
+  free_ptr(c->d_tcf); free_ptr(c->d_tct); free_ptr(c->d_tcws); free_ptr(c->d_tcpart); free_ptr(c->d_pivonly);
+  c->d_tcf = nullptr; c->d_tct = nullptr; c->d_tcws = nullptr; c->d_tcpart = nullptr; c->d_pivonly = nullptr;
   c->tc_ws_stride = c->tc_part_stride = 0;
   c->uploaded = false;
 }
@@ -336,6 +344,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   std::vector<int> lists;
   std::vector<TcFront> tcf;
   std::vector<int4> tct;
+  std::vector<unsigned char> pivonly(2 * p.fronts.size(), 0);
   long long tc_ws = 0, tc_part = 0;
   const int planes = ctx->opt.tensor_form;   // form of the tensor-core operands (0 = off)
   int min_tiles = ctx->opt.tensor_min_tiles;
@@ -418,6 +427,7 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
             const FrontDesc& d = p.fronts[f];
             TcFront r;
             r.f = f;
+            r.mode = 0;
             r.Mt = (d.m + kTcRows - 1) / kTcRows;
             r.Nt = (d.m + kTcCols - 1) / kTcCols;
             r.Kt = (d.k + kTcPivots - 1) / kTcPivots;
@@ -461,6 +471,55 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
                   for (int r0 = 0; r0 < kTcRows; r0 += 16) tct.push_back(make_int4(sl, mt, nt, r0));
         }
         ll.ntcs = (int)tct.size() - ll.tcs_off;
+        if (form == 0) {
+          // L21 = F21 U11^-1 and U12 = L11^-1 (P F12) of the same fronts, before their
+          // update matrices (the workspace is free then: its planes start at 0)
+          ll.tqf_off = (int)tcf.size();
+          long long wsq = 0;
+          for (int f : fl)
+            if (on_tc(p.fronts[f])) {
+              const FrontDesc& d = p.fronts[f];
+              pivonly[(size_t)design * p.fronts.size() + f] = 1;
+              const int tk = (d.k + kTcRows - 1) / kTcRows, tm = (d.m + kTcRows - 1) / kTcRows;
+              for (int mode = 1; mode <= 2; ++mode) {
+                TcFront r;
+                r.f = f;
+                r.mode = mode;
+                r.Mt = mode == 1 ? tm : tk;
+                r.Nt = mode == 1 ? tk : tm;
+                r.Kt = (d.k + kTcPivots - 1) / kTcPivots;
+                r.nsplit = 1;
+                r.aoff = wsq;
+                wsq += (long long)r.Mt * r.Kt * tc_tile_bytes_a(planes);
+                r.boff = wsq;
+                wsq += (long long)r.Nt * r.Kt * tc_tile_bytes_b(planes);
+                r.poff = 0;
+                tcf.push_back(r);
+              }
+            }
+          ll.ntqf = (int)tcf.size() - ll.tqf_off;
+          tc_ws = std::max(tc_ws, wsq);
+          // pack tasks: the triangular operand's tiles only up to its last nonzero k-tile
+          constexpr int kTri = kTcRows / kTcPivots;   // k-tiles per 128 pivots
+          ll.tqp_off = (int)tct.size();
+          for (int sl = 0; sl < ll.ntqf; ++sl) {
+            const TcFront& r = tcf[ll.tqf_off + sl];
+            for (int mt = 0; mt < r.Mt; ++mt)
+              for (int kt = 0; kt < (r.mode == 2 ? std::min(r.Kt, kTri * (mt + 1)) : r.Kt); ++kt)
+                tct.push_back(make_int4(sl, 0, mt, kt));
+            for (int nt = 0; nt < r.Nt; ++nt)
+              for (int kt = 0; kt < (r.mode == 1 ? std::min(r.Kt, kTri * (nt + 1)) : r.Kt); ++kt)
+                tct.push_back(make_int4(sl, 1, nt, kt));
+          }
+          ll.ntqp = (int)tct.size() - ll.tqp_off;
+          ll.tqt_off = (int)tct.size();
+          for (int sl = 0; sl < ll.ntqf; ++sl) {
+            const TcFront& r = tcf[ll.tqf_off + sl];
+            for (int mt = 0; mt < r.Mt; ++mt)
+              for (int nt = 0; nt < r.Nt; ++nt) tct.push_back(make_int4(sl, mt, nt, 0));
+          }
+          ll.ntqt = (int)tct.size() - ll.tqt_off;
+        }
         if (lists.size() % 2) lists.push_back(0);   // keep int2 task arrays 8-byte aligned
       }
     }
@@ -612,6 +671,8 @@ fdfd_status upload_plan(fdfd_ctx* ctx) {
   if (!ctx->h_tcf.empty()) {
     CKS(upload(ctx, &ctx->d_tcf, ctx->h_tcf));
     CKS(upload(ctx, &ctx->d_tct, ctx->h_tct));
+    ctx->h_pivonly.swap(pivonly);
+    CKS(upload(ctx, &ctx->d_pivonly, ctx->h_pivonly));
     ctx->tc_ws_stride = tc_ws;
     CK(dalloc(&ctx->d_tcws, (size_t)tc_ws * ctx->n_omega));
     ctx->tc_part_stride = std::max<long long>(tc_part, 4);
@@ -724,6 +785,11 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
   fa.istore_stride = p.inv_total;
   fa.sym = sym ? 1 : 0;
   const int form = sym ? 2 : prec;
+  // complex64 LU with block-local pivoting: the fronts whose update matrices go to the
+  // tensor cores take their L21 and U12 from there too (panel steps over the pivot block)
+  const bool trsm_tc = prec == 0 && !sym && ctx->opt.pivoting == 1 && ctx->opt.tensor_offdiag == 1 &&
+                       ctx->d_pivonly != nullptr;
+  fa.pivonly = trsm_tc ? ctx->d_pivonly + (design_only ? p.fronts.size() : 0) : nullptr;
   const std::vector<LevelList>& lv = design_only ? ctx->lv_design[form] : ctx->lv_full[form];
   const int nb = lu_panel_width(sizeof(T));
   cudaStream_t s = ctx->stream;
@@ -827,6 +893,44 @@ fdfd_status factor_levels(fdfd_ctx* ctx, bool design_only, int w0 = 0, int nw = 
           launch_lu_trsm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
       }
       { Prof pr(ctx, PK_LU_GEMM, gf * nwd, gb * nwd); launch_lu_gemm<T>(fa, fl, ll.nlarge, j0, nb, ll.nmax_large, s); }
+    }
+    if (trsm_tc && ll.ntqf > 0) {
+      // L21 = F21 U11^-1 and U12 = L11^-1 (P F12) on the tensor cores: the inverse folds of
+      // the last panel steps (side stream) must have finished
+      if (forked) {
+        CK(cudaEventRecord(ctx->iev_join, si));
+        CK(cudaStreamWaitEvent(s, ctx->iev_join, 0));
+      }
+      TcLaunch tq;
+      tq.fronts = ctx->d_tcf + ll.tqf_off;
+      tq.ws = ctx->d_tcws;
+      tq.ws_stride = ctx->tc_ws_stride;
+      tq.err = ctx->d_flow_err;
+      tq.chunk = kTcChunk;
+      tq.part = ctx->d_tcpart;
+      tq.part_stride = ctx->tc_part_stride;
+      const int planes = ctx->opt.tensor_form;
+      double qf = 0, qb = 0, qp = 0;
+      if (ctx->prof_on)
+        for (int t = 0; t < ll.ntqf; ++t) {
+          const TcFront& r = ctx->h_tcf[ll.tqf_off + t];
+          const FrontDesc& d = p.fronts[r.f];
+          qf += 8.0 * 0.5 * (double)d.k * d.k * d.m;              // a triangular solve's multiply-adds
+          qb += es * (2.0 * (double)d.k * d.m + 0.5 * (double)d.k * d.k) +
+                (double)r.Kt * r.Mt * r.Nt * 0.5 * (tc_tile_bytes_a(planes) + tc_tile_bytes_b(planes));
+          qp += es * ((double)d.k * d.m + 0.5 * (double)d.k * d.k) +
+                (double)r.Kt * (r.Mt * tc_tile_bytes_a(planes) + r.Nt * tc_tile_bytes_b(planes));
+        }
+      {
+        Prof pr(ctx, PK_TC_PACK, 0, qp * nwd);
+        tq.tasks = ctx->d_tct + ll.tqp_off;
+        launch_schur_tc_pack(fa, tq, ll.ntqp, planes, s);
+      }
+      {
+        Prof pr(ctx, PK_LU_TRSM_TC, qf * nwd, qb * nwd);
+        tq.tasks = ctx->d_tct + ll.tqt_off;
+        launch_schur_tc(fa, tq, ll.ntqt, planes, s);
+      }
     }
     if (ll.nsimt > 0) {
       // update matrices of the level's large fronts: S = F22 - L21 U12 (k m^2 complex multiply-adds)
@@ -1390,6 +1494,7 @@ void fdfd_default_options(fdfd_options* o) {
   o->tensor_min_tiles = 0;
   o->factor_form = 0;
   o->sweep_rhs_pairs = 0;
+  o->tensor_offdiag = 0;
 }
 
 fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double* k0_host, int n_omega,
@@ -1429,6 +1534,7 @@ fdfd_status fdfd_create(fdfd_ctx** out, fdfd_grid grid, double dx, const double*
   if (c->opt.tensor_min_tiles < 0) c->opt.tensor_min_tiles = 0;
   if (c->opt.factor_form != 1) c->opt.factor_form = 0;
   if (c->opt.sweep_rhs_pairs != 0) c->opt.sweep_rhs_pairs = 1;
+  if (c->opt.tensor_offdiag != 0) c->opt.tensor_offdiag = 1;
   if (c->opt.ir_max_iter < 0) c->opt.ir_max_iter = 0;
   {
     fdfd_options def;

@@ -1134,7 +1134,9 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   const int f = flist[blockIdx.y];
   const FrontDesc d = a.P.fronts[f];
   if (j0 >= d.k) return;
-  const int nb = min(kMaxNb, d.k - j0), n = d.n, ld = d.ld;
+  // L rows and U columns up to n; a front whose off-diagonal blocks come from the
+  // tensor cores stops at its pivot block
+  const int nb = min(kMaxNb, d.k - j0), n = (a.pivonly && a.pivonly[f]) ? d.k : d.n, ld = d.ld;
   const int bx = blockIdx.x + (phase == 2 ? 1 : 0);
   const size_t slot = (size_t)blockIdx.z * a.swp_stride + blockIdx.y;
   T* blk = reinterpret_cast<T*>(a.dblk) + slot * kDiagBlkElems;
@@ -1673,6 +1675,9 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax,
   const int ti = blockIdx.x / nt, tj = blockIdx.x - ti * nt;
   const int r0 = base + ti * kGemmTile, c0 = base + tj * kGemmTile;
   if (!schur && r0 >= d.k && c0 >= d.k) return;        // tile inside S: deferred to the Schur product
+  // a front whose off-diagonal blocks come from the tensor cores: the pivot block only
+  const bool pivonly = !schur && a.pivonly && a.pivonly[f];
+  if (pivonly && (r0 >= d.k || c0 >= d.k)) return;
   // symmetric form: the lower triangle only, and in a panel step only the pivot columns
   const bool sym = a.sym != 0;
   if (sym && (r0 + kGemmTile - 1 < c0 || (!schur && c0 >= d.k))) return;
@@ -1733,7 +1738,9 @@ lu_gemm_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int nbmax,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gc = c0 + tx + 16 * j;
-      const bool live = sym ? (gr >= gc && (schur || gc < d.k)) : (schur || gr < d.k || gc < d.k);
+      const bool live = sym       ? (gr >= gc && (schur || gc < d.k))
+                        : pivonly ? (gr < d.k && gc < d.k)
+                                  : (schur || gr < d.k || gc < d.k);
       if (gc < d.n && live) {
         T* p = F + (size_t)gr * d.ld + gc;
         *p = csub(*p, acc[i][j]);

@@ -32,6 +32,9 @@ struct FactorLaunch {
   long long istore_stride;
   void* dblk;              // a panel step's diagonal-block factors, [n_omega launched][swp_stride][kDiagBlkElems]
   int sym;                 // 1: symmetric form, M = D A = L diag(d) L^T without pivoting (see factor.cu)
+  const unsigned char* pivonly = nullptr;   // per front, or null: 1 = the panel steps factor the k x k pivot block
+                                            // only; L21 and U12 then come from the tensor cores
+                                            // (TcFront modes 1, 2)
 };
 constexpr int kDiagBlkElems = 32 * 32 + 32;   // L\U rows in pivot order, then 1 / U_pp
 // L11^-1 (strictly lower part) and U11^-1 (upper part) of the listed large fronts,
@@ -73,12 +76,21 @@ template <typename T> void launch_schur_simt(const FactorLaunch& a, const int* f
 // pivots per pipeline stage.  form: 1 = TF32, 2 = TF32 hi + lo (three products),
 // 3 = BF16 three-way split (six products).
 constexpr int kTcRows = 128, kTcCols = 128, kTcPivots = 8;
+// The same pipeline also forms the off-diagonal blocks of a front whose panel
+// steps factored only its pivot block (P F11 = L11 U11, inverses in the inverse
+// store), as products with the triangular inverses:
+//   mode 1: L21 = F21 U11^-1      (m x k, written over F21; its largest |entry| is growth)
+//   mode 2: U12 = L11^-1 (P F12)  (k x m, written over F12; rows of F12 gathered by perm)
+// A triangular operand's zero blocks are skipped: an output tile of columns
+// (mode 1) or rows (mode 2) below 128 (t + 1) contracts over the first 128 (t + 1)
+// pivots only.
 struct TcFront {           // one front of a tensor-core launch
-  long long aoff, boff;    // byte offsets of its packed L21 / U12 planes in one wavelength's workspace
+  long long aoff, boff;    // byte offsets of its packed A / B planes in one wavelength's workspace
   long long poff;          // float offset of its split partial sums in one wavelength's partial buffer
   int f;                   // front index
-  int Mt, Nt, Kt;          // row tiles, column tiles, k-tiles (ceil(m/128), ceil(m/128), ceil(k/8))
-  int nsplit;              // contraction split over this many CTAs per output tile (1 = none)
+  int Mt, Nt, Kt;          // row tiles, column tiles, k-tiles (mode 0: ceil(m/128), ceil(m/128), ceil(k/8))
+  int nsplit;              // contraction split over this many CTAs per output tile (1 = none; modes 1, 2: 1)
+  int mode = 0;            // 0: S = F22 - L21 U12; 1: L21; 2: U12
 };
 constexpr int kTcPartFloats = kTcRows * 2 * kTcCols;   // one split partial: 128 x 256 FP32
 struct TcLaunch {

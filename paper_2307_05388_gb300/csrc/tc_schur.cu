@@ -198,28 +198,39 @@ schur_pack_kernel(FactorLaunch a, TcLaunch t) {
     const int rr = u & 7, c = (u >> 3) % Fm::upr, g = (u >> 3) / Fm::upr;
     const int l0 = task.w * kTcPivots + c * CU;   // first complex pivot of the unit
     float x[RU];
+    const float2* X = reinterpret_cast<const float2*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
     if (isA) {
-      // A' row r: (Re, Im) of L21[r][l0..]
+      // A' row r: (Re, Im) of L21[r][l0..] (mode 0), of F21[r][l0..] (mode 1), of L11^-1[r][l0..] (mode 2)
       const int r = task.z * kTcM + g * 8 + rr;
 #pragma unroll
       for (int i = 0; i < CU; ++i) {
+        const int l = l0 + i;
         float2 v = make_float2(0.f, 0.f);
-        if (r < d.m && l0 + i < d.k) v = F[(size_t)(d.k + r) * d.ld + l0 + i];
+        if (fr.mode == 2) {
+          if (r < d.k && l <= r) v = l == r ? make_float2(1.f, 0.f) : X[(size_t)r * d.ldk + l];
+        } else if (r < d.m && l < d.k) {
+          v = F[(size_t)(d.k + r) * d.ld + l];
+        }
         x[2 * i] = v.x;
         x[2 * i + 1] = v.y;
       }
     } else {
-      // B' (K-major) row n = 2 j + tt: (Re U, -Im U) per pivot for tt = 0, (Im U, Re U) for tt = 1;
-      // the symmetric form's U12 is diag(d) L21^T: d_l L21[j][l], 1 / d_l on the inverse store diagonal
+      // B' (K-major) row n = 2 j + tt: (Re U, -Im U) per pivot for tt = 0, (Im U, Re U) for tt = 1,
+      // U = U12[l][j] (mode 0), U11^-1[l][j] (mode 1), F12[perm l][j] (mode 2); the symmetric
+      // form's U12 is diag(d) L21^T: d_l L21[j][l], 1 / d_l on the inverse store diagonal
       const int nrow = g * 8 + rr;
       const int j = task.z * kTcCols + (nrow >> 1), tt = nrow & 1;
-      const float2* X = reinterpret_cast<const float2*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
+      const int* Pm = a.perm + (size_t)w * a.perm_stride + d.piv_off;
 #pragma unroll
       for (int i = 0; i < CU; ++i) {
+        const int l = l0 + i;
         float2 v = make_float2(0.f, 0.f);
-        if (j < d.m && l0 + i < d.k) {
-          const int l = l0 + i;
-          v = a.sym ? cmul(crcp(X[(size_t)l * d.ldk + l]), F[(size_t)(d.k + j) * d.ld + l]) : F[(size_t)l * d.ld + d.k + j];
+        if (fr.mode == 1) {
+          if (j < d.k && l <= j) v = X[(size_t)l * d.ldk + j];
+        } else if (j < d.m && l < d.k) {
+          v = fr.mode == 2 ? F[(size_t)Pm[l] * d.ld + d.k + j]
+              : a.sym     ? cmul(crcp(X[(size_t)l * d.ldk + l]), F[(size_t)(d.k + j) * d.ld + l])
+                          : F[(size_t)l * d.ld + d.k + j];
         }
         x[2 * i] = tt ? v.y : v.x;
         x[2 * i + 1] = tt ? v.x : -v.y;
@@ -289,9 +300,12 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
   const int w = blockIdx.y + a.w0;
   const FrontDesc d = a.P.fronts[fr.f];
   const int chunk = t.chunk;
-  // this CTA's share of the contraction: k-tiles [kb, kb + nk)
-  const int kb = (int)((long long)task.w * fr.Kt / fr.nsplit);
-  const int nk = (int)((long long)(task.w + 1) * fr.Kt / fr.nsplit) - kb, nch = (nk + chunk - 1) / chunk;
+  // this CTA's share of the contraction: k-tiles [kb, kb + nk); a triangular operand
+  // (modes 1, 2) is zero beyond pivot 128 (t + 1) of output column / row tile t
+  const int kt_hi = fr.mode == 1 ? min(fr.Kt, (kTcCols / kTcPivots) * (task.z + 1))
+                    : fr.mode == 2 ? min(fr.Kt, (kTcRows / kTcPivots) * (task.y + 1)) : fr.Kt;
+  const int kb = (int)((long long)task.w * kt_hi / fr.nsplit);
+  const int nk = (int)((long long)(task.w + 1) * kt_hi / fr.nsplit) - kb, nch = (nk + chunk - 1) / chunk;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t full0 = smem_u32(bar), empty0 = full0 + 8 * S, tfull0 = full0 + 16 * S, tempty0 = tfull0 + 16,
                  done = tfull0 + 32;
@@ -386,7 +400,7 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
     if (!ok && lane == 0) sh[1] = 1;
     asm volatile("bar.sync 1, 256;" ::: "memory");
     const bool good = sh[1] == 0;
-    const int r = task.y * kTcM + 32 * q + lane;   // row of S
+    const int r = task.y * kTcM + 32 * q + lane;   // row of the output block
     bool apply = good;
     if (good && fr.nsplit > 1) {
       // post this split's partial sum; schur_split_sum_kernel adds the splits in order
@@ -397,18 +411,50 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
       for (int i = 0; i < 32; ++i) mine[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
       apply = false;
     }
-    if (apply && r < d.m) {
-      float2* row = reinterpret_cast<float2*>(a.store) + (size_t)w * a.store_stride + d.st_off +
-                    (size_t)(d.k + r) * d.ld + d.k;
-      const int j0 = task.z * kTcCols + h * 64;
+    float2* const F = reinterpret_cast<float2*>(a.store) + (size_t)w * a.store_stride + d.st_off;
+    const int j0 = task.z * kTcCols + h * 64;
+    if (fr.mode == 0) {
+      if (apply && r < d.m) {
+        float2* row = F + (size_t)(d.k + r) * d.ld + d.k;
 #pragma unroll
-      for (int jj = 0; jj < 64; ++jj) {
-        const int j = j0 + jj;
-        if (j < d.m) {
-          float2 sv = row[j];
-          sv.x -= acc[2 * jj];
-          sv.y -= acc[2 * jj + 1];
-          row[j] = sv;
+        for (int jj = 0; jj < 64; ++jj) {
+          const int j = j0 + jj;
+          if (j < d.m) {
+            float2 sv = row[j];
+            sv.x -= acc[2 * jj];
+            sv.y -= acc[2 * jj + 1];
+            row[j] = sv;
+          }
+        }
+      }
+    } else {
+      // modes 1, 2: the product is the block itself (rows of L21 / of U12)
+      const int nr = fr.mode == 1 ? d.m : d.k, nc = fr.mode == 1 ? d.k : d.m;
+      float g2 = 0.f;
+      if (apply && r < nr) {
+        float2* row = fr.mode == 1 ? F + (size_t)(d.k + r) * d.ld : F + (size_t)r * d.ld + d.k;
+#pragma unroll
+        for (int jj = 0; jj < 64; ++jj) {
+          const int j = j0 + jj;
+          if (j < nc) {
+            const float2 v = make_float2(acc[2 * jj], acc[2 * jj + 1]);
+            row[j] = v;
+            const float a2 = v.x * v.x + v.y * v.y;
+            g2 = (a2 == a2) ? fmaxf(g2, a2) : INFINITY;
+          }
+        }
+      }
+      if (fr.mode == 1) {
+        // growth: the largest |L21| entry (NaN -> inf), as the panel steps record it
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float og = __shfl_xor_sync(0xffffffffu, g2, o);
+          g2 = og > g2 ? og : g2;
+        }
+        if (lane == 0 && g2 > 0.f) {
+          float gv = sqrtf(g2);
+          if (!(gv == gv)) gv = INFINITY;
+          atomicMax(reinterpret_cast<int*>(a.growth + (size_t)w * a.n_fronts + fr.f), __float_as_int(gv));
         }
       }
     }

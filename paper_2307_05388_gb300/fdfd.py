@@ -50,7 +50,8 @@ class Options(C.Structure):
     _fields_ = [("mode", C.c_int), ("ir_tol", C.c_double), ("ir_max_iter", C.c_int),
                 ("gmres_restart", C.c_int), ("growth_bound", C.c_double), ("leaf_area", C.c_int),
                 ("pivoting", C.c_int), ("tensor_form", C.c_int), ("tensor_min_m", C.c_int),
-                ("tensor_min_tiles", C.c_int), ("factor_form", C.c_int), ("sweep_rhs_pairs", C.c_int)]
+                ("tensor_min_tiles", C.c_int), ("factor_form", C.c_int), ("sweep_rhs_pairs", C.c_int),
+                ("tensor_offdiag", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -4,6 +4,7 @@
   times: tensor-core update matrices in the BF16 three-way split form with the contraction
   split over several CTAs on its small levels.  Forward and transpose fields against
   SuperLU, element by element, at 1e-8; the raw complex FP32-factor error is printed.
+  Also with L21 and U12 formed on the tensor cores (option tensor_offdiag), at C2 and C3.
 * C3 (540 x 540, TE0 and TE1 sources of its input guide) and C4 (1040 x 1040), each
   restricted to its first wavelength: the same comparison on 292k and 1.08M unknowns.  Each
   side builds the mode sources with its own mode solver.
@@ -75,31 +76,35 @@ def _gpu_rhs(name, random_seed=None):
     return wl, np.stack(rows)
 
 
-def test_c2_default_options_fields_match_the_oracle(pool):
+@pytest.mark.parametrize("offdiag", [0, 1])
+def test_c2_default_options_fields_match_the_oracle(pool, offdiag):
+    """offdiag 1: L21 and U12 of the tensor-core fronts as products with the triangular inverses
+    on the tensor cores, the panel steps over the pivot blocks only."""
     job = pool.submit(J.fields, "c2", 0, 41)
     wl, rhs = _gpu_rhs("c2", 41)
-    s = U.make_solver(wl)
+    s = U.make_solver(wl, tensor_offdiag=offdiag)
     s.profile(True)
     s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
     prof = s.profile_get()
     s.profile(False)
     # the benchmarked path: update matrices on the tensor cores with split contractions
     assert prof["lu_schur_tc"]["launches"] > 0 and prof["lu_schur_sum"]["launches"] > 0
+    assert (prof.get("lu_trsm_tc", {}).get("launches", 0) > 0) == bool(offdiag)
     x, raw = _fields_on_gpu(s, torch.from_numpy(rhs[None].copy()).to(DEV))
     ref_f, ref_t = job.result()
-    _compare("c2", x, raw, ref_f, ref_t)
+    _compare(f"c2 (offdiag {offdiag})", x, raw, ref_f, ref_t)
     s.close()
 
 
-@pytest.mark.parametrize("name", ["c3", "c4"])
-def test_first_wavelength_fields_match_the_oracle(pool, name):
+@pytest.mark.parametrize("name,offdiag", [("c3", 0), ("c3", 1), ("c4", 0)])
+def test_first_wavelength_fields_match_the_oracle(pool, name, offdiag):
     job = pool.submit(J.fields, name, 0)
     wl, rhs = _gpu_rhs(name)
-    s = U.make_solver(wl)
+    s = U.make_solver(wl, tensor_offdiag=offdiag)
     s.factor(torch.from_numpy(wl.eps_full().reshape(-1).copy()).to(DEV))
     x, raw = _fields_on_gpu(s, torch.from_numpy(rhs[None].copy()).to(DEV))
     ref_f, ref_t = job.result()
-    _compare(f"{name} (first wavelength)", x, raw, ref_f, ref_t)
+    _compare(f"{name} (first wavelength, offdiag {offdiag})", x, raw, ref_f, ref_t)
     s.close()
 
 
