@@ -47,6 +47,11 @@ METRIC = "fwd+adjoint design iterations/s, cached vs uncached FP64, at field err
 UNIT = "iterations/s"
 L2_FLUSH_BYTES = 512 << 20
 FP32_LANES_PER_SM = 128
+FP64_FMA_PER_SM = 2       # FP64 FMAs per SM per clock on this part (ncu dfma peak_sustained)
+# DRAM bytes (read + write) of one sweep launch over its algorithmic bytes, from the ncu capture of
+# a C4 one-wavelength L sweep (profiles/flow_sweep_c4_one_wavelength.md: 927.9 + 99.3 MB against
+# 559.8 MB of L11^-1 and L21 entries); a full launch's traffic is scaled from it by its algorithmic bytes
+SWEEP_TRAFFIC_RATIO = (927.9 + 99.3) / 559.8
 DATA = "synthetic (seeded design density and guide; the paper's devices are not published)"
 DTYPE = "c64 factors + c128 refinement"
 
@@ -442,12 +447,33 @@ def main():
     launches_per_step = 0.0
     if kern:
         tot_ms = sum(v["ms"] for v in kern.values())
-        dom = max(kern, key=lambda k: kern[k]["ms"])
-        d = kern[dom]
+        # the four sweep directions are one kernel (flow_kernel, one template instance per direction)
+        classes = {k: v for k, v in kern.items() if not k.startswith("sweep_")}
+        sweeps = [v for k, v in kern.items() if k.startswith("sweep_")]
+        if sweeps:
+            classes["flow_kernel"] = {f: sum(v[f] for v in sweeps) for f in ("launches", "ms", "flops", "bytes")}
+        dom = max(classes, key=lambda k: classes[k]["ms"])
+        d = classes[dom]
         per_launch_ms = d["ms"] / d["launches"]
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = nsm * FP32_LANES_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-        if dom == "lu_schur_tc":
+        fp64_peak = nsm * FP64_FMA_PER_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        if dom == "flow_kernel":
+            per_launch_bytes = d["bytes"] / d["launches"]
+            roof = {"bound": "hbm", "achieved": per_launch_bytes / (per_launch_ms / 1e3) / 1e9,
+                    "peak": pk["hbm"], "unit": "GB/s",
+                    "traffic": per_launch_bytes * SWEEP_TRAFFIC_RATIO,
+                    "traffic_unit": "bytes per launch",
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a C4 one-wavelength L "
+                                      "sweep (1.027 GB against 0.560 GB algorithmic), scaled to this launch by its "
+                                      "algorithmic bytes",
+                    "algorithmic_bytes_per_launch": per_launch_bytes,
+                    "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+        elif dom.startswith("gmres_"):
+            roof = {"bound": "alu", "achieved": d["flops"] / d["launches"] / (per_launch_ms / 1e3) / 1e12,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": f"FP64 FMA: {nsm} SMs x {FP64_FMA_PER_SM} x 2 x {pk['sm_max_mhz']:.0f} MHz"}
+        elif dom == "lu_schur_tc":
             mult = {1: 1, 2: 3, 3: 6}[form]
             peak_tc = pk["bf16_sus"] * (1.0 if form == 3 else 0.5)
             ach = d["flops"] / d["launches"] / (per_launch_ms / 1e3) / 1e12 * mult

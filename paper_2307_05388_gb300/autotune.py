@@ -10,6 +10,10 @@ is spread over the SMs.  The tuner picks these per problem:
   S = F22 - L21 U12 (3 = BF16 three-way split, 2 = TF32 hi + lo, 1 = TF32), or
   0 = SIMT FP32.  The cheaper forms are accepted only where refinement still
   converges on the FP32 factors.
+* ``tensor_offdiag``: whether the tensor-core fronts also form L21 and U12 on
+  the tensor cores, as products with the triangular inverses (1), or by
+  substitution in their panel steps (0).  Faster factors, but the inverses'
+  conditioning can cost FGMRES iterations, which the timed iterations include.
 * ``tensor_min_m``: the smallest front boundary size m sent to the tensor
   cores.  This is the front-size bucket boundary between SIMT and tensor-core
   update matrices.
@@ -53,6 +57,7 @@ from . import fdfd
 SEARCH = (
     ("factor_form", (0, 1)),
     ("tensor_form", (3, 2, 1, 0)),
+    ("tensor_offdiag", (0, 1)),
     ("tensor_min_m", (128, 256, 512)),
     ("tensor_min_tiles", (0, 1)),
     ("leaf_area", (32, 16, 64)),
@@ -128,6 +133,7 @@ def _normalise(params: dict, base: dict) -> dict:
     if p["tensor_form"] == 0:
         p["tensor_min_m"] = base["tensor_min_m"]
         p["tensor_min_tiles"] = base["tensor_min_tiles"]
+        p["tensor_offdiag"] = base["tensor_offdiag"]
     return p
 
 
@@ -195,7 +201,8 @@ def tune(make_problem: Callable[[fdfd.Options], object], eps_design: torch.Tenso
          cache_path: str | None = None, key: str | None = None, flush_bytes: int = L2_FLUSH_BYTES,
          event: Callable = _cuda_event, sync: Callable = torch.cuda.synchronize,
          log: Callable[[str], None] | None = None) -> TuneResult:
-    """Chooses tensor_form, tensor_min_m, tensor_min_tiles and leaf_area for one design problem.
+    """Chooses factor_form, tensor_form, tensor_offdiag, tensor_min_m, tensor_min_tiles and leaf_area
+    for one design problem.
 
     make_problem(options) builds a fresh problem with those options: an object with
     ``iteration(eps_design)`` and a ``solver`` (an ``fdfd.Solver``), e.g. an

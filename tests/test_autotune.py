@@ -97,8 +97,8 @@ def _model(p):
 
 def test_search_picks_fastest_admissible_and_gates_on_refinement():
     res, book = _run(_model)
-    assert res.params == {"factor_form": 0, "tensor_form": 3, "tensor_min_m": 256, "tensor_min_tiles": 1,
-                          "leaf_area": 32}
+    assert res.params == {"factor_form": 0, "tensor_form": 3, "tensor_offdiag": 0, "tensor_min_m": 256,
+                          "tensor_min_tiles": 1, "leaf_area": 32}
     assert not res.cached
     ok = [t for t in res.trials if t.ok]
     assert min(t.ms for t in ok) == pytest.approx(10.0 - 1.5 - 0.25)
