@@ -92,12 +92,14 @@ typedef struct {
   int ir_max_iter;             /* FGMRES iterations per solve across restarts (default 40);
                                   0 returns the raw FP32-factor solution */
   int gmres_restart;           /* Krylov vectors per cycle, 1..16 (default 8) */
-  double growth_bound;         /* largest |L| entry tolerated in an FP32 front (default 1e7, where
+  double growth_bound;         /* largest |L| entry expected of an FP32 front (default 1e7, where
                                   the FP32 unit roundoff times the growth reaches about 0.6); above
-                                  it a factorisation with block-local pivoting is redone in FP32
-                                  with partial pivoting over all pivot rows, and if that is still
-                                  above it, in FP64.  A refined solve that does not converge on
-                                  FP32 factors also sends the factorisation to FP64. */
+                                  it a factorisation with block-local pivoting (or the symmetric
+                                  form) is redone in FP32 with partial pivoting over all pivot
+                                  rows.  FP32 factors whose growth stays finite are then kept for
+                                  refined solves: one that does not converge on them sends the
+                                  factorisation to FP64, as does an infinite or NaN growth (a zero
+                                  or non-finite pivot), or a raw solve (ir_max_iter = 0). */
   int leaf_area;               /* nested-dissection leaf size in cells (default 32) */
   int pivoting;                /* row pivoting in large fronts: 0 = partial pivoting over all the
                                   front's pivot rows, 1 = partial pivoting within each 32 x 32

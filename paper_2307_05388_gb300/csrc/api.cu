@@ -1437,7 +1437,11 @@ fdfd_status refactor_f64(fdfd_ctx* ctx) {
 // bound (or that was already the pivoting used), the factorisation is redone in
 // FP64.  The growth figure is copied to pinned host memory at the end of the
 // factorisation; any later stream synchronisation makes it readable.
-fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivoted = nullptr) {
+// refined: the caller refines the solve on these factors (FGMRES with the FP64 residual), so
+// factors with finite growth above the bound can be kept after the repivot; a raw solve
+// (no refinement to judge them) sends them to FP64 instead.
+fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivoted = nullptr,
+                          bool refined = false) {
   if (fell_back) *fell_back = false;
   if (repivoted) *repivoted = false;
   if (!ctx->growth_pending) return FDFD_OK;
@@ -1445,7 +1449,7 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivo
   ctx->growth_pending = false;
   ctx->growth_ready = false;
   CKS(check_flow_err(ctx));
-  const float g = *ctx->h_growth_max;
+  float g = *ctx->h_growth_max;
   ctx->last_growth = g;
   if (g <= ctx->opt.growth_bound) return FDFD_OK;
   const int piv_saved = ctx->opt.pivoting;
@@ -1461,10 +1465,15 @@ fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivo
     CKS(fst);
     CK(cudaStreamSynchronize(ctx->stream));
     CKS(check_flow_err(ctx));
-    const float g2 = *ctx->h_growth_max;
-    ctx->last_growth = g2;
-    if (g2 <= ctx->opt.growth_bound) return FDFD_OK;
+    g = *ctx->h_growth_max;
+    ctx->last_growth = g;
+    if (g <= ctx->opt.growth_bound) return FDFD_OK;
   }
+  // Finite growth above the bound with partial pivoting over all pivot rows: for a refined
+  // solve the complex FP32 factors are kept, and refinement, which measures the FP64 residual,
+  // decides (a solve that does not converge on them sends the factorisation to FP64).  A zero
+  // or non-finite pivot (inf / NaN growth), or a raw solve, goes to FP64 at once.
+  if (refined && g < INFINITY) return FDFD_OK;
   if (fell_back) *fell_back = true;
   return refactor_f64(ctx);
 }
@@ -1688,7 +1697,7 @@ fdfd_status solve_refined(fdfd_ctx* ctx, const double* b_dev, double* x_dev, int
   const fdfd_status st = fgmres(ctx, b, x, nrhs, transpose);
   if (st != FDFD_OK && st != FDFD_ERR_NOT_CONVERGED) return st;
   bool fell_back = false, repivoted = false;
-  CKS(settle_growth(ctx, &fell_back, &repivoted));
+  CKS(settle_growth(ctx, &fell_back, &repivoted, true));
   // a solve that converged on the first factors stands; otherwise it is repeated
   // on the refactored ones
   if (fell_back || (repivoted && st == FDFD_ERR_NOT_CONVERGED)) {
