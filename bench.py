@@ -266,6 +266,8 @@ def main():
     ap.add_argument("--offdiag-tc", type=int, default=0, choices=[0, 1],
                     help="L21 and U12 of tensor-core fronts as products with the triangular inverses on the "
                          "tensor cores (1) or by substitution in the panel steps (0, default)")
+    ap.add_argument("--gmres-restart", type=int, default=0,
+                    help="Krylov vectors per FGMRES cycle (0: the library default, 8)")
     ap.add_argument("--rhs-pairs", type=int, default=0, choices=[0, 1],
                     help="sweeps take a wavelength's right-hand sides two at a time (1) or one at a time (0, default)")
     ap.add_argument("--autotune", default="", metavar="CACHE.json",
@@ -399,6 +401,8 @@ def main():
     opts = FD.default_options(mode=FD.MODE_MIXED, tensor_form=args.tensor_form, factor_form=args.factor_form,
                               sweep_rhs_pairs=args.rhs_pairs, pivoting=args.pivoting,
                               tensor_offdiag=args.offdiag_tc)
+    if args.gmres_restart > 0:
+        opts.gmres_restart = args.gmres_restart
     tuned = None
     if args.autotune:
         from paper_2307_05388_gb300 import autotune as AT
