@@ -364,7 +364,8 @@ def main():
         if dist is not None:
             dist.barrier()
         clk = sampler.stop() if sampler else None
-        return sum(a.elapsed_time(b) for a, b in ev), clk
+        run_arm.step_ms = [a.elapsed_time(b) for a, b in ev]
+        return sum(run_arm.step_ms), clk
 
     def run_e2e(sp, steps, warmup):
         """Host design in, host F and gradient out, every step; host wall clock."""
@@ -424,6 +425,9 @@ def main():
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     ms, clk = run_arm(sp, args.steps, args.warmup, clocks=True)
+    step_ms = sorted(run_arm.step_ms)
+    step_pct = {"p50": float(np.percentile(step_ms, 50)), "p90": float(np.percentile(step_ms, 90)),
+                "min": step_ms[0], "max": step_ms[-1]}
     ms_max = max_over_ranks(ms, dist, dev)
     value = args.steps / (ms_max / 1e3)
     stats = [p.solver.stats() for p in sp.problems]
@@ -498,9 +502,12 @@ def main():
         if sw:
             sw_ms = sum(v["ms"] for v in sw)
             sw_gbs = sum(v["bytes"] for v in sw) / (sw_ms / 1e3) / 1e9
+            sw_tf = sum(v["flops"] for v in sw) / (sw_ms / 1e3) / 1e12
             roof_sw = {"kernels": "flow_kernel (L, U, U^T, L^T)", "bound": "hbm", "achieved": sw_gbs, "unit": "GB/s",
                        "peak": pk["hbm"], "frac": sw_gbs / pk["hbm"], "ms_per_step": sw_ms / prof_steps,
-                       "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+                       "alu_tflops": sw_tf, "alu_frac": sw_tf / fp32_peak,
+                       "peak_source": f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs); alu_frac "
+                                      "against the FP32 SIMT peak"}
         if "lu_schur_tc" in kern:
             d_tc = kern["lu_schur_tc"]
             mult = {1: 1, 2: 3, 3: 6}[form]
@@ -514,7 +521,9 @@ def main():
         fac_keys = [k for k in kern if k.startswith("lu_") or k == "front_build"]
         fac_ms = sum(kern[k]["ms"] for k in fac_keys) / prof_steps
         fac_fl = sum(kern[k]["flops"] for k in fac_keys) / prof_steps
+        tc_fl = sum(kern[k]["flops"] for k in ("lu_schur_tc", "lu_trsm_tc") if k in kern) / prof_steps
         roof_fac = {"kernels": "the whole design refactor (" + ", ".join(sorted(fac_keys)) + ")",
+                    "tensor_core_flop_share": tc_fl / fac_fl if fac_fl else None,
                     "achieved": fac_fl / (fac_ms / 1e3) / 1e12 if fac_ms else None, "unit": "TFLOP/s",
                     "ms_per_step": fac_ms, "peak_tf32_tensor": pk["bf16_sus"] * 0.5,
                     "frac_of_tf32_tensor": (fac_fl / (fac_ms / 1e3) / 1e12) / (pk["bf16_sus"] * 0.5) if fac_ms else None,
@@ -637,7 +646,8 @@ def main():
                        "(tolerance 1e-9); element-wise parity with the oracle at C1-C4 sizes is in the -m gpu tests, "
                        "and --cpu-accuracy adds it here for the benchmarked workload"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "step_ms_this_rank": step_pct,
+            "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": DTYPE, "data": DATA,
             "config": dict(workload_config(wl), update_matrices=TENSOR_FORMS[form],
                            parallelism=("one GPU" if world == 1 else
