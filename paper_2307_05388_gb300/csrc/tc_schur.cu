@@ -43,6 +43,7 @@ constexpr int kTcRingMax = 196608;         // shared-memory ring bytes at most
 constexpr int kTcTmemCols = 512;           // two FP32 accumulators of MMA N = 256 columns
 constexpr int kTcThreads = 320;            // copy warp, MMA warp, 8 accumulation warps
 constexpr int kTcAccWarps = 8;
+constexpr int kTileStride = 2 * kTcCols + 1;   // floats per staged output row (odd: rows in distinct banks)
 
 template <int FORM> struct Form {
   static_assert(FORM >= 1 && FORM <= 3, "forms 1-3");
@@ -413,7 +414,50 @@ schur_tc_kernel(FactorLaunch a, TcLaunch t) {
     }
     float2* const F = reinterpret_cast<float2*>(a.store) + (size_t)w * a.store_stride + d.st_off;
     const int j0 = task.z * kTcCols + h * 64;
-    if (fr.mode == 0) {
+    if (fr.mode == 0 && fr.nsplit == 1) {
+      // the tile through shared memory (the ring is idle once every k-tile has been
+      // consumed), so that F22 is read and written a row at a time by whole warps:
+      // thread (row 32 q + lane, half h) stores its 128 reals, then each warp takes rows
+      static_assert(Fm::ring >= kTcM * kTileStride * 4, "the staged tile fits in the ring");
+      float* tile = reinterpret_cast<float*>(smem);
+      if (apply) {
+        float* mine = tile + (size_t)(32 * q + lane) * kTileStride + h * 128;
+#pragma unroll
+        for (int i = 0; i < 128; ++i) mine[i] = acc[i];
+      }
+      asm volatile("bar.sync 2, 256;" ::: "memory");   // every accumulation thread, good or not
+      if (apply) {
+        // warp aw takes rows aw, aw + 8, ...: four rows' loads (16 per lane) issued together
+        constexpr int RB = 4, CU = kTcCols / 32;
+        const int aw = warp - 2;                         // accumulation warp 0..7
+        const int c0 = task.z * kTcCols;
+        for (int rb = aw; rb < kTcM; rb += kTcAccWarps * RB) {
+          float2 v[RB][CU];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) {
+            const int rr = task.y * kTcM + rb + kTcAccWarps * t;
+            const float2* row = F + (size_t)(d.k + rr) * d.ld + d.k + c0;
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+              const int jc = lane + 32 * u;
+              v[t][u] = (rr < d.m && c0 + jc < d.m) ? row[jc] : make_float2(0.f, 0.f);
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < RB; ++t) {
+            const int rl = rb + kTcAccWarps * t, rr = task.y * kTcM + rl;
+            float2* row = F + (size_t)(d.k + rr) * d.ld + d.k + c0;
+            const float* src = tile + (size_t)rl * kTileStride;
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+              const int jc = lane + 32 * u;
+              if (rr < d.m && c0 + jc < d.m)
+                row[jc] = make_float2(v[t][u].x - src[2 * jc], v[t][u].y - src[2 * jc + 1]);
+            }
+          }
+        }
+      }
+    } else if (fr.mode == 0) {
       if (apply && r < d.m) {
         float2* row = F + (size_t)(d.k + r) * d.ld + d.k;
 #pragma unroll
