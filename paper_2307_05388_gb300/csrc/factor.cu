@@ -1035,7 +1035,9 @@ lu_panel_reg_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int n
 // the sweeps and lu_inv_fold use the inverse store).  Roles touch disjoint
 // entries of F and read B only, so the CTAs are independent.
 // ---------------------------------------------------------------------------
-constexpr int kStepRows = 64;
+constexpr int kStepRows = 256;   // roles L and U: rows / columns per CTA, one per thread
+constexpr int kStepCols = 64;    // role P: columns per CTA
+static_assert(kStepRows == 1 << 8 && kStepCols == 1 << 6, "the staging loops shift by 8 and 6");
 
 // LU of the nb x nb block at (j0, j0) with row pivoting inside the block, by
 // warps 0-3 (lane = row; warp w holds columns 8w..8w+7 in registers).  No rows
@@ -1152,7 +1154,7 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     role = 2; lo = j0 + nb + (bx - 1 - nl) * kStepRows;
     if (lo >= n) return;
   } else {
-    role = 3; lo = (bx - 1 - nl - nu) * kStepRows;
+    role = 3; lo = (bx - 1 - nl - nu) * kStepCols;
     if (lo >= j0) return;
   }
   T* F = reinterpret_cast<T*>(a.store) + (size_t)w * a.store_stride + d.st_off;
@@ -1169,16 +1171,17 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
       g = diag_lu_4warps<T>(F, ld, j0, nb, LU, src, dinv, s_l, s_r, a.sym != 0);
     }
   } else if (role == 1) {
-    // meanwhile warps 4-7 stage rows [lo, lo + 64) of the block columns
+    // meanwhile warps 4-7 stage rows [lo, lo + kStepRows) of the block columns
     for (int e = tid - 128; e < kStepRows * kMaxNb; e += 128) {
       const int rr = e >> 5, l = e & 31, r = lo + rr;
       Ws[rr][l] = (r < n && l < nb) ? F[(size_t)r * ld + j0 + l] : czero<T>();
     }
   } else if (role >= 2) {
-    // ... or the block rows (not yet permuted) over columns [lo, lo + 64)
+    // ... or the block rows (not yet permuted) over columns [lo, lo + width)
     const int hi = role == 2 ? n : j0;
-    for (int e = tid - 128; e < kStepRows * kMaxNb; e += 128) {
-      const int p = e >> 6, cc = e & 63, c = lo + cc;
+    const int lw = role == 2 ? 8 : 6;   // log2 of the width: kStepRows (role U) or kStepCols (role P)
+    for (int e = tid - 128; e < (kMaxNb << lw); e += 128) {
+      const int p = e >> lw, cc = e & ((1 << lw) - 1), c = lo + cc;
       Ws[cc][p] = (c < hi && p < nb) ? F[(size_t)(j0 + p) * ld + c] : czero<T>();
     }
   }
@@ -1851,12 +1854,14 @@ void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j
   const int nl = (span + kStepRows - 1) / kStepRows;
   // symmetric form: no U rows (the trailing update takes diag(d) L^T instead) and no row permutation
   const int nu = a.sym ? 0 : nl;
-  const int np = a.sym ? 0 : (j0 + kStepRows - 1) / kStepRows;
-  // CTAs resident at once on the current device: 8 per SM
-  int dev = 0, nsm = 0;
+  const int np = a.sym ? 0 : (j0 + kStepCols - 1) / kStepCols;
+  // CTAs resident at once on the current device
+  int dev = 0, nsm = 0, per_sm = 0;
   const long long wave =
-      (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-          ? 8LL * nsm
+      (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_step_local_kernel<T>, 256, step_local_smem(sizeof(T))) ==
+           cudaSuccess)
+          ? (long long)std::max(1, per_sm) * nsm
           : (1LL << 40);
   const long long ctas = (long long)(1 + nl + nu + np) * nf * a.n_omega;
   if (ctas > wave && a.dblk) {
