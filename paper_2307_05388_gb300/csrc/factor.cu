@@ -1125,10 +1125,11 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   using R = typename RealOf<T>::type;
   using Blk = T[kMaxNb + 1];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Blk* LU = reinterpret_cast<Blk*>(smem_raw);     // [32][33]
-  Blk* Ws = LU + kMaxNb;                          // [64][33]: role L 64 rows x J; roles U, P: [c][p]
-  T* dinv = reinterpret_cast<T*>(Ws + kStepRows);
+  Blk* LU = reinterpret_cast<Blk*>(smem_raw);                  // [32][33]
+  T* dinv = reinterpret_cast<T*>(LU + kMaxNb);                 // [32]
   T (*s_l)[32] = reinterpret_cast<T (*)[32]>(dinv + kMaxNb);   // [2][32] multipliers of a step
+  Blk* Ws = reinterpret_cast<Blk*>(s_l + 2);   // [kStepRows][33]: role L rows x J; roles U, P: [c][p];
+                                               // role D its first 64 rows (a phase-1 launch has only those)
   __shared__ int src[kMaxNb];
   __shared__ int s_r[2];
   __shared__ R s_g[8];
@@ -1187,7 +1188,7 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
   }
   __syncthreads();
   if (phase == 1) {
-    for (int e = tid; e < kMaxNb * kMaxNb; e += 256) blk[e] = LU[e >> 5][e & 31];
+    for (int e = tid; e < kMaxNb * kMaxNb; e += blockDim.x) blk[e] = LU[e >> 5][e & 31];
     if (tid < kMaxNb) {
       blk[kMaxNb * kMaxNb + tid] = dinv[tid];
       bsrc[tid] = src[tid];
@@ -1262,7 +1263,7 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     // diagonal, U_JJ^-1 on and above it
     T* X = reinterpret_cast<T*>(a.istore) + (size_t)w * a.istore_stride + d.iv_off;
     __syncthreads();
-    for (int e = tid; e < nb * nb; e += 256) {
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
       const int i = e / nb, j = e - i * nb;
       X[(size_t)(j0 + i) * d.ldk + j0 + j] = i > j ? Ws[i][j] : Ws[kMaxNb + i][j];
     }
@@ -1273,7 +1274,7 @@ lu_step_local_kernel(FactorLaunch a, const int* __restrict__ flist, int j0, int 
     __syncthreads();
     if (tid == 0) {
       R gg = 0;
-      for (int i = 0; i < 8; ++i) gg = nanmax(gg, s_g[i]);
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) gg = nanmax(gg, s_g[i]);
       float gv = (float)sqrt((double)gg);
       if (!(gv == gv)) gv = INFINITY;
       // max of non-negative floats is order independent as an int max
@@ -1419,6 +1420,10 @@ lu_inv_kernel(FactorLaunch a, const int* __restrict__ flist, int nblk) {
 // the multipliers of one step (double-buffered)
 size_t step_local_smem(size_t es) {
   return ((size_t)(kMaxNb + kStepRows) * (kMaxNb + 1) + kMaxNb + 2 * 32) * es;
+}
+// a phase-1 launch (the diagonal block and role D only): the staging tile's first 64 rows
+size_t step_diag_smem(size_t es) {
+  return ((size_t)(kMaxNb + 2 * kMaxNb) * (kMaxNb + 1) + kMaxNb + 2 * 32) * es;
 }
 
 // Boundary rows of the panel: L21[:, j0:j0+nb] = A21[:, j0:j0+nb] U_jj^-1 (right
@@ -1865,8 +1870,9 @@ void launch_lu_step_local(const FactorLaunch& a, const int* flist, int nf, int j
           : (1LL << 40);
   const long long ctas = (long long)(1 + nl + nu + np) * nf * a.n_omega;
   if (ctas > wave && a.dblk) {
-    // more than one wave: the diagonal block once per front, then the substitutions
-    lu_step_local_kernel<T><<<dim3(1, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(a, flist, j0, nl, nu, 1);
+    // more than one wave: the diagonal block once per front (four warps: the block LU, then
+    // role D; a smaller footprint, so that more fronts share an SM), then the substitutions
+    lu_step_local_kernel<T><<<dim3(1, nf, a.n_omega), 128, step_diag_smem(sizeof(T)), s>>>(a, flist, j0, nl, nu, 1);
     if (nl + nu + np > 0)
       lu_step_local_kernel<T><<<dim3(nl + nu + np, nf, a.n_omega), 256, step_local_smem(sizeof(T)), s>>>(
           a, flist, j0, nl, nu, 2);
