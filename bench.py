@@ -270,6 +270,9 @@ def main():
                     help="Krylov vectors per FGMRES cycle (0: the library default, 8)")
     ap.add_argument("--rhs-pairs", type=int, default=0, choices=[0, 1],
                     help="sweeps take a wavelength's right-hand sides two at a time (1) or one at a time (0, default)")
+    ap.add_argument("--optimizer", default="workload", choices=["workload", "sign", "adam"],
+                    help="the design update between iterations (not timed): the workload's own (default; "
+                         "Adam at lr 0.01 for c4, a sign step for the others), or the one named")
     ap.add_argument("--autotune", default="", metavar="CACHE.json",
                     help="choose tensor_form, tensor_min_m, tensor_min_tiles and leaf_area by measured design "
                          "iterations before the timed run (starting from --tensor-form), cached in this file")
@@ -303,6 +306,7 @@ def main():
     dev = torch.device("cuda", local)
     from paper_2307_05388_gb300 import autograd as AG
     from paper_2307_05388_gb300 import fdfd as FD
+    from paper_2307_05388_gb300 import optimize as OPT
     from paper_2307_05388_gb300 import shard as SH
 
     wl = W.with_modes(wl0, FD.slab_modes)
@@ -310,6 +314,7 @@ def main():
         wl = wl.select_wavelengths(range(n_omega_run))
     x0, y0, bw, bh = wl.box
     nd = bw * bh
+    optimizer = wl.optimizer if args.optimizer == "workload" else args.optimizer
     k0 = 2 * np.pi / np.asarray(wl.wavelengths)
     eps_bg = torch.from_numpy(wl.eps_bg.reshape(-1).copy()).to(dev)
     lo, hi = W.EPS_SIO2, W.EPS_SIO2 + W.DELTA_EPS
@@ -342,12 +347,13 @@ def main():
 
     def run_arm(sp, steps, warmup, clocks=False):
         rho = rho0.clone()
+        upd = OPT.design_optimizer(optimizer, wl.step)      # state on the device
         eps = torch.empty(nd, dtype=torch.float64, device=dev)
         grad = torch.empty(nd, dtype=torch.float64, device=dev)
         for _ in range(warmup):
             density(sp, rho, eps)
             F, g = sp.iteration(eps, grad_out=grad)
-            rho = torch.clamp(rho + wl.step * torch.sign(g), 0.0, 1.0)
+            rho = upd.step(rho, g)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         if dist is not None:
             dist.barrier()
@@ -359,7 +365,7 @@ def main():
             density(sp, rho, eps)
             F, g = sp.iteration(eps, grad_out=grad)
             ev[k][1].record(stream)
-            rho = torch.clamp(rho + wl.step * torch.sign(g), 0.0, 1.0)
+            rho = upd.step(rho, g)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -373,11 +379,12 @@ def main():
         h_F = torch.empty(1, dtype=torch.float64, pin_memory=True)
         h_g = torch.empty(nd, dtype=torch.float64, pin_memory=True)
         d_eps = torch.empty(nd, dtype=torch.float64, device=dev)
-        rho = wl.rho.reshape(-1).copy()
+        rho = torch.from_numpy(wl.rho.reshape(-1).copy())
+        upd = OPT.design_optimizer(optimizer, wl.step)      # the caller's host-side loop
         single = dist is None and len(sp.problems) == 1
         total = 0.0
         for k in range(warmup + steps):
-            h_eps.numpy()[:] = lo + rho * (hi - lo)        # the caller's host-side design (not timed)
+            h_eps.numpy()[:] = lo + rho.numpy() * (hi - lo)   # the caller's host-side design (not timed)
             flush.zero_()
             torch.cuda.synchronize()
             if dist is not None:
@@ -395,7 +402,7 @@ def main():
             dt = time.perf_counter() - t
             if k >= warmup:
                 total += dt
-            rho = np.clip(rho + wl.step * np.sign(h_g.numpy()), 0.0, 1.0)
+            rho = upd.step(rho, h_g)
         return 1e3 * total
 
     # ---- launch parameters: library defaults, or measured by the autotuner (not timed) ----
@@ -656,6 +663,8 @@ def main():
                            factor_form=("symmetric L diag(d) L^T of D A, no pivoting" if opts.factor_form == 1
                                         else "LU of A, pivoting within 32 x 32 diagonal blocks" if opts.pivoting == 1
                                         else "LU of A, partial pivoting over each front's pivot rows"),
+                           design_update=(f"Adam, lr {wl.step}, ascent, clipped to [0, 1]" if optimizer == "adam"
+                                          else f"sign step {wl.step}, clipped to [0, 1]") + " (not timed)",
                            launch_parameters={"tensor_min_m": opts.tensor_min_m,
                                               "tensor_min_tiles": opts.tensor_min_tiles,
                                               "leaf_area": opts.leaf_area, "autotuned": tuned}),

@@ -138,6 +138,54 @@ def test_design_iteration_c1_objective_and_gradient():
         rho = O.sign_step(rho, g_ref, wl.step)       # same rho on both sides for the next step
 
 
+def test_c2_design_loop_three_steps_lock_step():
+    """The first three sign steps of C2's loop (340 x 340, the library's default options, the design
+    refactor from the second step on): F at 1e-8 and dF/drho at 1e-6 of the oracle at every step,
+    both sides stepping from the oracle's gradient so that they see the same design."""
+    wl = W.make("c2")
+    prob = U.problem(wl)
+    rho = wl.rho.copy()
+    for it in range(3):
+        F, g = prob.iteration(U.eps_design_tensor(wl, rho))
+        torch.cuda.synchronize()
+        F_ref, g_ref, _ = O.design_iteration(wl, rho, wl.eps_full, W.DELTA_EPS)
+        err = O.rel_err(g.cpu().numpy().reshape(wl.rho.shape) * W.DELTA_EPS, g_ref)
+        print(f"c2 step {it}: F {float(F):.10g} (oracle {F_ref:.10g}), gradient error {err:.2e}")
+        assert abs(float(F) - F_ref) <= 1e-8 * abs(F_ref)
+        assert err <= GRAD_TOL
+        rho = O.sign_step(rho, g_ref, wl.step)
+
+
+def test_c4_recipe_adam_loop_through_the_autograd_function():
+    """C4's differentiable loop -- four wavelengths 1.53-1.57 um at dx = 40 nm, Adam at lr 0.01
+    ascending F, the gradient from FdfdObjective's backward (the transpose solves on the forward
+    pass's cached factors) chained to rho by autograd -- on a 200 x 200 grid with a 150 x 150
+    design, four steps in lock step with the oracle: F and dF/drho at every step, and the device
+    Adam update of the device gradient against the oracle's Adam update of its own."""
+    from paper_2307_05388_gb300 import optimize as OPT
+    wl = W.make("c4", grid=200, design=150)
+    assert wl.optimizer == "adam" and wl.n_omega == 4
+    prob = U.problem(wl)
+    opt, state = OPT.Adam(wl.step), {}
+    rho = wl.rho.copy()
+    for it in range(4):
+        r = torch.from_numpy(rho.reshape(-1).copy()).to(DEV).requires_grad_(True)
+        F = prob(W.EPS_SIO2 + W.DELTA_EPS * r)
+        F.backward()
+        F = F.detach()
+        F_ref, g_ref, _ = O.design_iteration(wl, rho, wl.eps_full, W.DELTA_EPS)
+        g = r.grad.cpu().numpy().reshape(wl.rho.shape)
+        err = O.rel_err(g, g_ref)
+        nxt = opt.step(r.detach(), r.grad).cpu().numpy().reshape(wl.rho.shape)
+        rho = O.adam_step(rho, g_ref, state, lr=wl.step)
+        step_err = np.abs(nxt - rho).max()
+        print(f"c4@200 Adam step {it}: F {float(F):.10g} (oracle {F_ref:.10g}), gradient error {err:.2e}, "
+              f"update difference {step_err:.1e}")
+        assert abs(float(F) - F_ref) <= 1e-8 * abs(F_ref)
+        assert err <= GRAD_TOL
+        assert step_err <= 1e-7
+
+
 def test_multiwavelength_multisource_gradient():
     wl = W.make_small(40, 36, 6, (10, 9, 18, 16), n_omega=3, n_src=2, seed=13)
     prob = U.problem(wl)

@@ -1,5 +1,6 @@
 """The L-BFGS-B host loop on the CPU, with an objective whose optimum under the box bounds is
-known in closed form (the GPU objective chain it drives is covered by the parity tests)."""
+known in closed form (the GPU objective chain it drives is covered by the parity tests), and the
+per-step sign and Adam updates against the oracle's."""
 import numpy as np
 import pytest
 import torch
@@ -76,3 +77,64 @@ def test_lbfgsb_on_the_design_objective_ascends():
     F0, _ = f(rho0)
     rho, F, res = OPT.lbfgsb(f, rho0, maxiter=6)
     assert F > float(F0) and float(rho.min()) >= 0.0 and float(rho.max()) <= 1.0
+
+
+# ---------------------------------------------------------------------------
+# The per-step updates of the workloads' loops (SignStep, Adam), against the oracle's
+# sign_step and adam_step, which tests/test_oracle.py pins by closed forms.
+# ---------------------------------------------------------------------------
+def _gradients(n, steps, seed):
+    rng = np.random.default_rng(seed)
+    # magnitudes from 1e-12 to 1e2, zeros included: Adam's eps and sign(0) both matter
+    out = []
+    for _ in range(steps):
+        g = rng.standard_normal(n) * 10.0 ** rng.uniform(-12, 2, n)
+        g[rng.integers(0, n, 3)] = 0.0
+        out.append(g)
+    return out
+
+
+def test_adam_matches_the_oracle_over_a_trajectory():
+    from oracle import fdfd_oracle as O
+    rho = np.random.default_rng(1).uniform(0, 1, 64)
+    st, opt = {}, OPT.Adam(0.01)
+    r = torch.from_numpy(rho.copy())
+    for g in _gradients(64, 12, 2):
+        rho = O.adam_step(rho, g, st, lr=0.01)
+        r = opt.step(r, torch.from_numpy(g))
+        np.testing.assert_allclose(r.numpy(), rho, rtol=0, atol=1e-15)
+    assert opt.t == 12 and r.min() >= 0 and r.max() <= 1
+
+
+def test_adam_minimise_descends_and_state_round_trips():
+    """Minimising mirrors maximising with the gradient negated; a loop resumed from state_dict
+    continues exactly where an unbroken one goes."""
+    gs = [torch.from_numpy(g) for g in _gradients(32, 6, 3)]
+    rho0 = torch.full((32,), 0.5, dtype=torch.float64)
+    up, down = OPT.Adam(0.02), OPT.Adam(0.02, maximize=False)
+    a, b = rho0, rho0
+    for g in gs:
+        a, b = up.step(a, g), down.step(b, -g)
+    torch.testing.assert_close(a, b, rtol=0, atol=0)
+    whole, first = OPT.Adam(0.02), OPT.Adam(0.02)
+    w, f = rho0, rho0
+    for g in gs[:3]:
+        w, f = whole.step(w, g), first.step(f, g)
+    resumed = OPT.Adam(0.02)
+    resumed.load_state_dict(first.state_dict())
+    for g in gs[3:]:
+        w, f = whole.step(w, g), resumed.step(f, g)
+    torch.testing.assert_close(w, f, rtol=0, atol=0)
+
+
+def test_sign_step_matches_the_oracle():
+    from oracle import fdfd_oracle as O
+    rho = np.random.default_rng(4).uniform(0, 1, 64)
+    opt = OPT.design_optimizer("sign", 0.05)
+    for g in _gradients(64, 5, 5):
+        ref = O.sign_step(rho, g, 0.05)
+        np.testing.assert_array_equal(opt.step(torch.from_numpy(rho), torch.from_numpy(g)).numpy(), ref)
+        rho = ref
+    assert isinstance(OPT.design_optimizer("adam", 0.01), OPT.Adam)
+    with pytest.raises(ValueError):
+        OPT.design_optimizer("sgd", 0.1)

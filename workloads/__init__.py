@@ -187,8 +187,12 @@ def _stub_eps(nx: int, ny: int, npml: int, box: tuple, dx: float, width_um: floa
     return eps
 
 
-def make(name: str, seed: int = 0) -> Workload:
-    """The five seeded workloads, by name: 'c1' .. 'c5' (sizes in each docstring line)."""
+def make(name: str, seed: int = 0, grid: int | None = None, design: int | None = None) -> Workload:
+    """The five seeded workloads, by name: 'c1' .. 'c5' (sizes in each docstring line).
+
+    For c2 .. c5, grid and design (cells) replace the square grid's and the centred design box's
+    sizes while dx, the PML, the wavelengths, sources, monitors and optimiser stay those of the
+    workload: the same recipe at a size a test's oracle finishes in seconds."""
     rng = np.random.default_rng(seed)
     name = name.lower()
     if name == "c1":
@@ -221,6 +225,11 @@ def make(name: str, seed: int = 0) -> Workload:
             nx, dx, npml, dsz = 1760, 0.05, 20, 1680
             wls = np.array([1.31, 1.55])
             modes, iters, opt, step = 2, 20, "sign", 0.05
+        if grid is not None or design is not None:
+            nx, dsz = grid or nx, design or dsz
+            if not 0 < dsz <= nx - 2 * npml - 4:
+                raise ValueError(f"design {dsz} does not fit a {nx}-cell grid with {npml} PML cells")
+            name = f"{name}@{nx}"
         ny = nx
         box = _centred_box(nx, ny, dsz, dsz)
         rho = _blurred_rho(rng, dsz, dsz)
@@ -233,7 +242,7 @@ def make(name: str, seed: int = 0) -> Workload:
             # TE0 / TE1 of the 1.2 um input guide, launched on the first non-PML column
             srcs = [ModeLine(npml, eps_bg[npml].copy(), m) for m in range(modes)]
         nw = len(wls)
-        if name == "c3":
+        if name.startswith("c3"):
             # 8 Gaussian ports evenly on the right monitor column; port 2*(l//2) + m.
             span = (hi - lo) * dx
             centres = lo * dx + span * (np.arange(8) + 0.5) / 8.0
