@@ -1439,7 +1439,7 @@ fdfd_status refactor_f64(fdfd_ctx* ctx) {
 // factorisation; any later stream synchronisation makes it readable.
 // refined: the caller refines the solve on these factors (FGMRES with the FP64 residual), so
 // factors with finite growth above the bound can be kept after the repivot; a raw solve
-// (no refinement to judge them) sends them to FP64 instead.
+// (no refinement to check them) sends them to FP64 instead.
 fdfd_status settle_growth(fdfd_ctx* ctx, bool* fell_back = nullptr, bool* repivoted = nullptr,
                           bool refined = false) {
   if (fell_back) *fell_back = false;
