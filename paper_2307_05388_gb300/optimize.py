@@ -14,6 +14,9 @@ to the solves.
 """
 from __future__ import annotations
 
+import json
+import os
+import time
 from typing import Callable
 
 import numpy as np
@@ -32,6 +35,21 @@ def density_objective(prob, radius: float, beta: float, eta: float, eps_lo: floa
         F = prob(eps)
         F.backward()
         return F.detach(), rho.grad.detach()
+    return f
+
+
+def linear_density_objective(prob, eps_lo: float, eps_hi: float):
+    """F(rho) and dF/drho for the unfiltered design map eps = eps_lo + rho (eps_hi - eps_lo):
+    the library's density map (fdfd_density_eps), one design iteration (refactor, forward solves,
+    objective, adjoint solves, gradient) and the chain rule dF/drho = (eps_hi - eps_lo) dF/deps.
+
+    prob: an autograd.DesignProblem; rho is the design-box density [w*h] (float64, device)."""
+    scale = float(eps_hi) - float(eps_lo)
+
+    def f(rho: torch.Tensor):
+        eps = prob.solver.density_eps(rho, eps_lo, eps_hi)
+        F, g = prob.iteration(eps)
+        return F, g * scale
     return f
 
 
@@ -138,3 +156,86 @@ def design_optimizer(kind: str, step: float):
     if kind == "adam":
         return Adam(step)
     raise ValueError(f"unknown optimiser {kind!r}")
+
+
+def _state_to(state, device):
+    if isinstance(state, torch.Tensor):
+        return state.to(device)
+    if isinstance(state, dict):
+        return {k: _state_to(v, device) for k, v in state.items()}
+    return state
+
+
+class DesignLoop:
+    """The design loop rho <- optimizer.step(rho, dF/drho(rho)), with checkpoint / resume and one
+    JSON record per iteration.
+
+    objective(rho) -> (F, dF/drho) on rho's device (density_objective, linear_density_objective);
+    optimizer: SignStep, Adam, or any object with step(rho, g), state_dict() and load_state_dict().
+
+    checkpoint: a path.  Every `every` iterations the loop writes the iteration count, rho, the
+    optimizer's state and the history of F there (torch.save to a temporary file, then an atomic
+    rename, so that an interrupted write leaves the previous checkpoint).  The loop draws no random
+    numbers, so that is all its state.  Factor caches are not saved: the first iteration after a
+    resume factors from scratch (one analysis and one full factorisation in a new solver), after
+    which the loop follows the same trajectory.  On the GPU, FGMRES sizes its first cycle from the
+    previous solve, so a resumed loop agrees with an unbroken one to rounding, not bit for bit.
+
+    log: a path.  One JSON object per iteration is appended to it: the iteration, F, the 2-norm of
+    dF/drho, the wall time, and whatever stats() returns (for a solver: refinement iterations, the
+    final residual, pivot growth, repivots, FP64 fallbacks).  After a resume the iterations since the
+    last checkpoint appear twice, the second time as recomputed."""
+
+    def __init__(self, objective: Callable[[torch.Tensor], tuple], optimizer, rho0: torch.Tensor,
+                 checkpoint: str | None = None, every: int = 1, log: str | None = None,
+                 stats: Callable[[], dict] | None = None):
+        if every < 1:
+            raise ValueError("every must be at least 1")
+        self.objective = objective
+        self.optimizer = optimizer
+        self.rho = rho0.detach().clone()
+        self.iteration = 0
+        self.history: list = []
+        self.checkpoint = checkpoint
+        self.every = int(every)
+        self.log = log
+        self.stats = stats
+
+    def run(self, iterations: int) -> torch.Tensor:
+        """Runs that many more iterations; returns the current density."""
+        for _ in range(int(iterations)):
+            t0 = time.perf_counter()
+            F, g = self.objective(self.rho)
+            Fv = float(F)
+            rec = {"iteration": self.iteration, "F": Fv, "grad_norm": float(torch.linalg.vector_norm(g))}
+            self.rho = self.optimizer.step(self.rho, g)
+            self.iteration += 1
+            self.history.append(Fv)
+            rec["seconds"] = time.perf_counter() - t0
+            if self.log is not None:
+                if self.stats is not None:
+                    rec.update(self.stats())
+                with open(self.log, "a") as fh:
+                    fh.write(json.dumps(rec, default=float) + "\n")
+            if self.checkpoint is not None and self.iteration % self.every == 0:
+                self.save(self.checkpoint)
+        return self.rho
+
+    def save(self, path: str) -> None:
+        state = {"iteration": self.iteration, "rho": self.rho.detach().cpu(),
+                 "optimizer": _state_to(self.optimizer.state_dict(), "cpu"), "history": list(self.history)}
+        tmp = f"{path}.tmp"
+        torch.save(state, tmp)
+        os.replace(tmp, path)
+
+    @classmethod
+    def resume(cls, path: str, objective: Callable[[torch.Tensor], tuple], optimizer,
+               device: str | torch.device = "cpu", **kw) -> "DesignLoop":
+        """A loop restored from a checkpoint: rho and the optimizer's state on `device`; kw as for
+        the constructor (checkpoint, every, log, stats)."""
+        state = torch.load(path, map_location="cpu")
+        optimizer.load_state_dict(_state_to(state["optimizer"], device))
+        loop = cls(objective, optimizer, state["rho"].to(device), **kw)
+        loop.iteration = int(state["iteration"])
+        loop.history = [float(v) for v in state["history"]]
+        return loop

@@ -77,6 +77,13 @@ class OracleSolver:
             return out
         return t
 
+    def density_eps(self, rho, eps_lo, eps_hi, out=None):
+        eps = eps_lo + rho.reshape(-1) * (eps_hi - eps_lo)
+        if out is not None:
+            out.copy_(eps)
+            return out
+        return eps
+
     def filter_project(self, rho, radius, beta, eta, eps_lo, eps_hi):
         w, h = self.box[2], self.box[3]
         r = rho.detach().reshape(w, h).numpy()

@@ -186,6 +186,42 @@ def test_c4_recipe_adam_loop_through_the_autograd_function():
         assert step_err <= 1e-7
 
 
+def test_design_loop_checkpoint_resume_c1(tmp_path):
+    """C1's loop with Adam (lr 0.05) through the library: four iterations without a break against
+    two with a checkpoint, then a resume into a new solver (analysis and full factorisation again)
+    and two more.  The densities agree to rounding: FGMRES sizes its first cycle from the solver's
+    previous solve, which a new solver does not have, while a lost moment or step count would move
+    pixels by lr.  The resumed loop's last F matches the oracle's F at its density."""
+    from paper_2307_05388_gb300 import optimize as OPT
+    wl = W.make("c1")
+    rho0 = torch.from_numpy(wl.rho.reshape(-1).copy()).to(DEV)
+
+    def loop_objective():
+        p = U.problem(wl)
+        return p, OPT.linear_density_objective(p, W.EPS_SIO2, W.EPS_SI)
+
+    p1, f1 = loop_objective()
+    whole = OPT.DesignLoop(f1, OPT.Adam(0.05), rho0)
+    whole.run(4)
+    ck = str(tmp_path / "c1_loop.pt")
+    p2, f2 = loop_objective()
+    OPT.DesignLoop(f2, OPT.Adam(0.05), rho0, checkpoint=ck, every=2).run(2)
+    p3, f3 = loop_objective()
+    resumed = OPT.DesignLoop.resume(ck, f3, OPT.Adam(0.05), device=DEV)
+    assert resumed.iteration == 2 and resumed.rho.is_cuda
+    resumed.run(2)
+    diff = float((resumed.rho - whole.rho).abs().max())
+    print(f"c1 loop resumed after 2 of 4 Adam steps: largest density difference {diff:.1e}")
+    assert diff <= 1e-6
+    assert np.allclose(resumed.history, whole.history, rtol=1e-8, atol=0)
+    rho = resumed.rho.cpu().numpy().reshape(wl.rho.shape)
+    F, _ = f3(resumed.rho)
+    F_ref, _, _ = O.design_iteration(wl, rho, wl.eps_full, W.DELTA_EPS)
+    assert abs(float(F) - F_ref) <= 1e-8 * abs(F_ref)
+    for p in (p1, p2, p3):
+        p.solver.close()
+
+
 def test_multiwavelength_multisource_gradient():
     wl = W.make_small(40, 36, 6, (10, 9, 18, 16), n_omega=3, n_src=2, seed=13)
     prob = U.problem(wl)

@@ -138,3 +138,58 @@ def test_sign_step_matches_the_oracle():
     assert isinstance(OPT.design_optimizer("adam", 0.01), OPT.Adam)
     with pytest.raises(ValueError):
         OPT.design_optimizer("sgd", 0.1)
+
+
+# ---------------------------------------------------------------------------
+# The checkpointed design loop (DesignLoop), with the oracle standing in for the library
+# ---------------------------------------------------------------------------
+def test_design_loop_resumes_on_the_same_trajectory(tmp_path):
+    """Five Adam iterations without a break against three with a checkpoint every two, then a
+    resume (a new problem, its factors from scratch) and three more: the same densities and the
+    same F history, bit for bit (the stand-in solver is deterministic); the log shows every
+    iteration, those since the last checkpoint twice."""
+    import json
+    import workloads as W
+    wl, prob = _oracle_problem()
+    rho0 = torch.from_numpy(wl.rho.reshape(-1).copy())
+    f = OPT.linear_density_objective(prob, W.EPS_SIO2, W.EPS_SI)
+    whole = OPT.DesignLoop(f, OPT.Adam(0.05), rho0)
+    whole.run(5)
+    ck, log = str(tmp_path / "loop.pt"), str(tmp_path / "loop.jsonl")
+    first = OPT.DesignLoop(f, OPT.Adam(0.05), rho0, checkpoint=ck, every=2, log=log, stats=prob.solver.stats)
+    first.run(3)
+    assert first.iteration == 3 and not (tmp_path / "loop.pt.tmp").exists()
+    wl2, prob2 = _oracle_problem()
+    f2 = OPT.linear_density_objective(prob2, W.EPS_SIO2, W.EPS_SI)
+    resumed = OPT.DesignLoop.resume(ck, f2, OPT.Adam(0.05), checkpoint=ck, every=2, log=log,
+                                    stats=prob2.solver.stats)
+    assert resumed.iteration == 2 and resumed.optimizer.t == 2 and len(resumed.history) == 2
+    resumed.run(3)
+    torch.testing.assert_close(resumed.rho, whole.rho, rtol=0, atol=0)
+    assert resumed.history == whole.history
+    recs = [json.loads(line) for line in open(log)]
+    assert [r["iteration"] for r in recs] == [0, 1, 2, 2, 3, 4]
+    assert [r["F"] for r in recs[3:]] == whole.history[2:]
+    assert all({"F", "grad_norm", "seconds", "ir_iters", "growth", "fallbacks"} <= set(r) for r in recs)
+    assert torch.load(ck)["iteration"] == 4
+
+
+def test_linear_density_objective_chain_rule():
+    """dF/drho of the unfiltered map is (eps_hi - eps_lo) dF/deps: against central differences of
+    the stand-in's F."""
+    import workloads as W
+    wl, prob = _oracle_problem()
+    f = OPT.linear_density_objective(prob, W.EPS_SIO2, W.EPS_SI)
+    rho = torch.from_numpy(wl.rho.reshape(-1).copy())
+    F, g = f(rho)
+    h = 1e-6
+    for p in (3, 29):
+        e = torch.zeros_like(rho)
+        e[p] = h
+        fd = (float(f(rho + e)[0]) - float(f(rho - e)[0])) / (2 * h)
+        assert abs(float(g[p]) - fd) <= 1e-5 * max(abs(fd), 1e-3 * float(g.abs().max()))
+
+
+def test_design_loop_rejects_a_zero_interval():
+    with pytest.raises(ValueError):
+        OPT.DesignLoop(lambda r: (r.sum(), r), OPT.SignStep(0.1), torch.zeros(3, dtype=torch.float64), every=0)
