@@ -193,3 +193,22 @@ def test_linear_density_objective_chain_rule():
 def test_design_loop_rejects_a_zero_interval():
     with pytest.raises(ValueError):
         OPT.DesignLoop(lambda r: (r.sum(), r), OPT.SignStep(0.1), torch.zeros(3, dtype=torch.float64), every=0)
+
+
+# ---------------------------------------------------------------------------
+# The seeded workload recipe at test size (the GPU loop tests run C4's recipe at 200^2)
+# ---------------------------------------------------------------------------
+def test_workload_recipe_at_a_smaller_grid():
+    """make(name, grid=, design=) keeps the workload's recipe (dx, PML, wavelengths, sources,
+    optimiser) on a smaller centred box, and refuses a design that does not fit."""
+    import workloads as W
+    full, small = W.make("c4"), W.make("c4", grid=200, design=150)
+    assert (small.nx, small.ny, small.box) == (200, 200, (25, 25, 150, 150))
+    assert small.dx == full.dx and small.npml == full.npml and small.optimizer == full.optimizer == "adam"
+    np.testing.assert_array_equal(small.wavelengths, full.wavelengths)
+    assert small.rho.shape == (150, 150) and 0 <= small.rho.min() and small.rho.max() <= 1
+    assert small.eps_bg.shape == (200, 200) and small.name == "c4@200"
+    c3 = W.make("c3", grid=240, design=180)
+    assert len(c3.monitors) == 8 and len({m[0].values.argmax() for m in c3.monitors}) == 4
+    with pytest.raises(ValueError):
+        W.make("c2", grid=100, design=90)
